@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Throughput of the batched FP32 Kalman-filter track fit on one GB300.
+
+Workload (default): 200 events x 20000 tracks, 10 barrel layers (r = 4..40 cm,
+Bz = 3.8 T), seeded synthetic events (see paper_1605_05508_gb300/synth.py).
+A step fits the whole batch: one graph of 10 per-layer kernel launches
+(propagate + Kalman update of every track). Metric: track-layer
+propagate+update steps per second. Inputs (1.2 GB) exceed the 129 MB L2, so
+no flush runs between steps.
+
+Also reported on the same line: the end-to-end number through kf_fit_host
+(host buffers, copies inside the timed region), the fused all-layers kernel,
+the plain per-event FP64 form on the same GPU (events/s factor), the roofline
+of the per-layer kernel, the oracle on the host cores (cpu_baseline), and the
+SM clocks sampled during the timed region.
+
+`--impl reference` times the FP64 CPU oracle (as it stands) on the host cores
+on bounded samples of the same workload and prints its own line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "track-layer prop+update steps/s and served events/s, p50/p99 ms vs plain FP64"
+UNIT = "track-layer steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--events", type=int, default=200)
+    ap.add_argument("--tracks", type=int, default=20000)
+    ap.add_argument("--layers", type=int, default=10)
+    ap.add_argument("--seed", type=int, default=1606)
+    ap.add_argument("--no-extras", action="store_true", help="headline only (no e2e/f64/fused/cpu legs)")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def workload_config(a):
+    return {"workload": f"batched FP32 fit: {a.events} events x {a.tracks} tracks, {a.layers} barrel layers "
+                        f"r=4..{4 * a.layers} cm, Bz=3.8 T",
+            "events_per_gpu": a.events, "tracks_per_event": a.tracks, "layers": a.layers,
+            "l2": "inputs larger than L2 (no flush)", "seed": a.seed}
+
+
+def make_inputs(a, rank):
+    from paper_1605_05508_gb300 import synth as S
+    det = S.barrel(a.layers)
+    ev = S.make_fit_batch(a.seed + 1000 * rank, a.events * a.tracks, det, keep_truth=False)
+    return det, ev
+
+
+# --------------------------------------------------------------------------- reference arm
+
+def run_reference(a):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_1605_05508_gb300 import synth as S
+    det = S.barrel(a.layers)
+    sample_tracks = min(2 * a.tracks, a.events * a.tracks)
+    ev = S.make_fit_batch(a.seed, sample_tracks, det, keep_truth=False)
+    cores = os.cpu_count() or 1
+    O.lib()
+
+    def step():
+        O.fit(ev.seeds.par, ev.seeds.cov, ev.seeds.charge, ev.hits.xyz, ev.hits.valid, det.radii, det.bz,
+              det.sigma_xy, det.sigma_z, n_threads=cores)
+    for _ in range(a.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        step()
+    dt = (time.perf_counter() - t0) / max(a.steps, 1)
+    value = sample_tracks * a.layers / dt
+    sample = f"{sample_tracks} tracks x {a.layers} layers of the workload per step (FP64 oracle, OpenMP)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(a),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- helpers
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.15)
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in out.splitlines():
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 10:
+                continue
+            try:
+                sm.append(float(f[2]))
+                smax.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[6:10]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("kf_fit.cu", "kf_math.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1605_05508_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(n_tracks):
+    """DRAM bytes per fit-layer launch from the committed ncu summary, scaled to
+    n_tracks; None if absent or taken on a different kernel source."""
+    p = os.path.join(ROOT, "profiles", "fit_layer_kernel.traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    return float(d["dram_bytes_per_track"]) * n_tracks
+
+
+def fit_bytes_per_track_layer(L, seeds_have_lo, have_valid, have_chi2):
+    """Algorithmic HBM bytes of one track-layer step of the per-layer kernel,
+    averaged over the L launches of a step (first launch reads the seeds)."""
+    rd = 24 + 84 + 1 + 12 + (1 if have_valid else 0)  # par, cov, charge, hit, valid
+    rd_lo = 12 * ((L - 1) + (1 if seeds_have_lo else 0)) / L
+    rd_status = 4 * (L - 1) / L
+    wr = 24 + 12 + 84 + (4 if have_chi2 else 0)  # par, lo, cov, chi2
+    wr_status = 4 * min(L, 2) / L
+    return rd + rd_lo + rd_status + wr + wr_status
+
+
+# --------------------------------------------------------------------------- our arm
+
+def run_ours(a):
+    import torch
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1605_05508_gb300 import build as B
+    B.build()
+    from paper_1605_05508_gb300 import kf
+
+    det, ev = make_inputs(a, rank)
+    n, L = ev.seeds.par.shape[1], det.n_layers
+    dev = torch.device("cuda", local_rank)
+    T = lambda x, dt=None: torch.from_numpy(np.ascontiguousarray(x)).to(dev, dtype=dt)
+    seeds = kf.Tracks(T(ev.seeds.par), T(ev.seeds.cov), T(ev.seeds.charge))
+    hits = kf.TrackHits(T(ev.hits.xyz), T(ev.hits.valid))
+    out = kf.Tracks(torch.empty((6, n), device=dev), torch.empty((21, n), device=dev), seeds.charge,
+                    torch.empty((3, n), device=dev))
+    chi2 = torch.empty((L, n), device=dev)
+    status = torch.empty(n, dtype=torch.int32, device=dev)
+    ctx = kf.Context(det.radii, det.bz, det.sigma_xy, det.sigma_z, device=local_rank)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        kf.kf_fit(ctx, seeds, hits, out, chi2, status, stream)
+
+    for _ in range(max(a.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    smi_index = int(vis.split(",")[local_rank]) if vis and vis.split(",")[local_rank].strip().isdigit() else local_rank
+    clocks = ClockSampler(smi_index)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    t_ms = e0.elapsed_time(e1)
+    if dist:
+        tt = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    ms_per_step = t_ms / a.steps
+    value = world * n * L / (ms_per_step / 1e3)
+
+    # roofline of the per-layer kernel: the graph holds only the L layer launches
+    launch_s = ms_per_step / 1e3 / L
+    bpt = fit_bytes_per_track_layer(L, False, True, True)
+    achieved = bpt * n / launch_s / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = ncu_traffic(n)
+    roof = {"kernel": "fit_layer_kernel", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+            "algorithmic_bytes_per_track_layer": bpt, "launch_us": launch_s * 1e6}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (positions as float pairs)",
+            "data": "synthetic (seeded generator, helix hits + Gaussian smear)",
+            "config": workload_config(a), "roofline": roof, "clocks": clk, "gpu_launches": a.steps * L}
+
+    if not a.no_extras:
+        line.update(extras(a, ctx, kf, torch, dev, det, ev, seeds, hits, out, chi2, status, stream, value,
+                           ms_per_step, rank, world, dist))
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def extras(a, ctx, kf, torch, dev, det, ev, seeds, hits, out, chi2, status, stream, value, ms_per_step, rank, world,
+           dist):
+    n, L = ev.seeds.par.shape[1], det.n_layers
+    res = {}
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, k):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(k):
+            fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / k
+
+    # fused all-layers kernel
+    ms_f = timed(lambda: kf.kf_fit_fused(ctx, seeds, hits, out, chi2, status, stream), max(3, a.steps // 4))
+    res["fused"] = {"value": n * L / (ms_f / 1e3), "unit": UNIT, "ms_per_step": ms_f,
+                    "note": "one launch, track kept in registers across layers"}
+
+    # end to end through the public C ABI with pinned host buffers
+    pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+    hs = kf.Tracks(pin(ev.seeds.par), pin(ev.seeds.cov), pin(ev.seeds.charge))
+    hh = kf.TrackHits(pin(ev.hits.xyz), pin(ev.hits.valid))
+    ho = kf.Tracks(torch.empty((6, n)).pin_memory(), torch.empty((21, n)).pin_memory(), hs.charge,
+                   torch.empty((3, n)).pin_memory())
+    hc = torch.empty((L, n)).pin_memory()
+    hst = torch.empty(n, dtype=torch.int32).pin_memory()
+    kf.kf_fit_host(ctx, hs, hh, ho, hc, hst, stream)
+    k_e2e = max(3, min(20, a.steps // 10))
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        kf.kf_fit_host(ctx, hs, hh, ho, hc, hst, stream)
+    dt = (time.perf_counter() - t0) / k_e2e
+    h2d = n * (6 * 4 + 21 * 4 + 1) + L * n * (3 * 4 + 1)
+    d2h = n * (6 * 4 + 3 * 4 + 21 * 4 + 4) + L * n * 4
+    res["e2e"] = {"value": world * n * L / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                  "ms_per_step": dt * 1e3, "api": "kf_fit_host (pinned host buffers)"}
+
+    # plain per-event FP64 form on the same GPU
+    s64 = kf.Tracks(seeds.par.double(), seeds.cov.double(), seeds.charge)
+    o64 = kf.Tracks(torch.empty((6, n), dtype=torch.float64, device=dev),
+                    torch.empty((21, n), dtype=torch.float64, device=dev), seeds.charge)
+    c64 = torch.empty((L, n), dtype=torch.float64, device=dev)
+    offs = [e * a.tracks for e in range(a.events + 1)]
+    ms64 = timed(lambda: kf.kf_fit_f64(ctx, s64, hits, o64, offs, c64, status, stream), 2)
+    events_s = a.events / (ms64 / 1e3)
+    res["plain_f64"] = {"value": n * L / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
+                        "events_per_s": events_s, "launches_per_step": a.events * L,
+                        "fp32_batched_events_per_s": a.events / (ms_per_step / 1e3),
+                        "speedup_events_per_s": (a.events / (ms_per_step / 1e3)) / events_s}
+
+    # oracle on the host cores, bounded sample of the same workload
+    if rank == 0:
+        import oracle as O
+        cores = os.cpu_count() or 1
+        m = min(n, 10 * a.tracks)
+        O.lib()
+        t0 = time.perf_counter()
+        O.fit(ev.seeds.par[:, :m], ev.seeds.cov[:, :m], ev.seeds.charge[:m], ev.hits.xyz[:, :, :m],
+              ev.hits.valid[:, :m], det.radii, det.bz, det.sigma_xy, det.sigma_z, n_threads=cores)
+        dtc = time.perf_counter() - t0
+        res["cpu_baseline"] = {"value": m * L / dtc, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"first {m} tracks ({m // a.tracks} events) x {L} layers, FP64 oracle, "
+                                         f"{cores} OpenMP threads, {dtc:.2f} s wall"}
+    return res
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

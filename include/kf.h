@@ -1,0 +1,146 @@
+/*
+ * kf.h -- C ABI of libkf: Kalman-filter track fitting and combinatorial track
+ * building on one GPU (Cerati et al., "Kalman Filter Tracking on Parallel
+ * Architectures", CTD2016).
+ *
+ * Conventions for every entry point:
+ *  - Units: cm, GeV, tesla.  A track state is (x, y, z, px, py, pz).
+ *  - Layouts are structure-of-arrays: component c of track i is at
+ *    ptr[c * n + i].  Covariances are packed lower triangles, row-major:
+ *    element (i, j), j <= i, is component i(i+1)/2 + j of 21.
+ *  - Positions may carry a low-order part: the position is the unevaluated
+ *    float sum par[0..2] + par_lo[0..2] (|lo| <= half an ulp of hi).  Inputs
+ *    with par_lo == NULL are read as lo = 0.
+ *  - Pointers named "device" are CUDA device (or managed) memory of the
+ *    context's device; the caller owns every buffer it passes and the library
+ *    never frees caller memory.  `stream` is a cudaStream_t (NULL = legacy
+ *    default stream); calls are asynchronous on it unless stated otherwise.
+ *  - Return value: KF_OK (0) or a negative KF_E* code; no C++ exception
+ *    crosses this interface.  KF_ECUDA leaves the CUDA error in
+ *    kf_last_cuda_error().
+ *  - A kf_ctx is not thread-safe; use one per host thread.
+ */
+#ifndef KF_H_
+#define KF_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KF_OK 0
+#define KF_EINVAL (-1)    /* bad argument: null pointer, size, layout */
+#define KF_ENOMEM (-2)    /* device memory or the context budget exhausted */
+#define KF_EAGAIN (-3)    /* not admitted / result not ready yet */
+#define KF_ETIMEDOUT (-4) /* a wait ran out */
+#define KF_ECUDA (-5)     /* a CUDA runtime call failed */
+#define KF_ENOTSUP (-6)   /* not supported on this device / build */
+
+/* Per-track status bits (int32 status words). */
+#define KF_ST_NOT_REACHED 1 /* the helix never reaches the next layer radius;
+                               the track stops there */
+#define KF_ST_NEWTON_FAIL 2 /* the path-length solve did not converge; stops */
+#define KF_ST_TANGENT 4     /* crossing within direction cosine 0.01 of the
+                               tangent (dg/ds ~ 0); stops */
+#define KF_ST_NOT_PD 8      /* final covariance failed the positive-definite check */
+#define KF_ST_NO_HIT 16     /* at least one layer had no hit (propagated only) */
+#define KF_ST_STOPPED (KF_ST_NOT_REACHED | KF_ST_NEWTON_FAIL | KF_ST_TANGENT)
+
+typedef struct kf_ctx kf_ctx;
+
+/* Detector and algorithm constants (copied by kf_create). */
+typedef struct {
+    float bz_tesla;          /* uniform solenoidal field along z (non-zero) */
+    int32_t n_layers;        /* barrel layers, 1 .. 64 */
+    const float *radius_cm;  /* [n_layers] host, strictly increasing, > 0 */
+    float sigma_xy_cm;       /* transverse hit smear (x and y each) */
+    float sigma_z_cm;        /* longitudinal hit smear */
+    float chi2_cut;          /* building: keep hits with chi2 increment < cut */
+    int32_t max_cands;       /* building: candidates kept per seed, 1 .. 8 */
+} kf_config;
+
+/* A batch of tracks, single precision (device pointers). */
+typedef struct {
+    int64_t n;
+    float *par;     /* [6][n] */
+    float *par_lo;  /* [3][n] low parts of x, y, z, or NULL */
+    float *cov;     /* [21][n] packed lower triangle */
+    int8_t *charge; /* [n] +1 or -1 */
+} kf_tracks;
+
+/* A batch of tracks, double precision (device pointers), for kf_fit_f64. */
+typedef struct {
+    int64_t n;
+    double *par;    /* [6][n] */
+    double *cov;    /* [21][n] */
+    int8_t *charge; /* [n] */
+} kf_tracks_f64;
+
+/* The hits of a fixed hit set, one per track and layer (device pointers). */
+typedef struct {
+    int64_t n_tracks;
+    int32_t n_layers;     /* fit layers 0 .. n_layers-1 of the configuration */
+    const float *xyz;     /* [n_layers][3][n_tracks] */
+    const uint8_t *valid; /* [n_layers][n_tracks], 0 = no hit; NULL = all hits */
+} kf_track_hits;
+
+/* Create a context on CUDA device `device`.  `mem_budget_bytes` bounds the
+ * device memory the context itself allocates (0 = no bound). */
+int kf_create(kf_ctx **out, const kf_config *cfg, int device, size_t mem_budget_bytes);
+
+/* Destroy a context (synchronises the device work it issued). */
+void kf_destroy(kf_ctx *ctx);
+
+/* Message for a KF_* return code (static storage). */
+const char *kf_strerror(int code);
+
+/* Last CUDA error code recorded by a KF_ECUDA return of this context. */
+int kf_last_cuda_error(const kf_ctx *ctx);
+
+/*
+ * Track fit (Sec. 2 of the paper: with the hit set fixed after building, the
+ * filter is applied layer by layer without branching).  For every track and
+ * layer l = 0 .. hits->n_layers-1: propagate the helix to radius[l] (Newton
+ * solve for the path length, surface transport Jacobian J, C' = J C J^T);
+ * if the hit is valid, chi2[l] = r^T S^-1 r with r = m - H x',
+ * S = H C' H^T + V, then the Kalman update with the symmetrised Joseph form.
+ *
+ * seeds (device, read only), out (device, written; may alias seeds),
+ * chi2 [n_layers][n] (device, -1 where no update happened, may be NULL),
+ * status [n] (device, KF_ST_* bits, may be NULL).
+ * out->par_lo may be NULL (then the low parts are dropped on output).
+ * Executed as one graph of n_layers kernel launches (one per layer step),
+ * captured once per argument set and replayed.
+ * Errors: KF_EINVAL (sizes, null pointers, n_layers > config),
+ * KF_ENOMEM (scratch), KF_ECUDA.
+ */
+int kf_fit(kf_ctx *ctx, const kf_tracks *seeds, const kf_track_hits *hits, kf_tracks *out,
+           float *chi2, int32_t *status, void *stream);
+
+/* Same result as kf_fit, computed by a single launch that keeps each track in
+ * registers across all layers (no per-layer state round trip). */
+int kf_fit_fused(kf_ctx *ctx, const kf_tracks *seeds, const kf_track_hits *hits, kf_tracks *out,
+                 float *chi2, int32_t *status, void *stream);
+
+/* The plain double-precision form of the same fit: the same steps in FP64,
+ * launched once per event and per layer (events = contiguous track ranges
+ * event_off[e] .. event_off[e+1], host array [n_events+1]).
+ * seeds/out (device, may alias), chi2 [n_layers][n] double (may be NULL),
+ * status [n] (may be NULL). */
+int kf_fit_f64(kf_ctx *ctx, const kf_tracks_f64 *seeds, const kf_track_hits *hits,
+               kf_tracks_f64 *out, double *chi2, int32_t *status, const int64_t *event_off,
+               int32_t n_events, void *stream);
+
+/* kf_fit with HOST buffers: copies the inputs to context-owned device
+ * buffers, fits, copies the results back, and synchronises `stream`.
+ * All pointers in seeds/hits/out/chi2/status are host memory (pinned memory
+ * gives full copy bandwidth). */
+int kf_fit_host(kf_ctx *ctx, const kf_tracks *seeds, const kf_track_hits *hits, kf_tracks *out,
+                float *chi2, int32_t *status, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KF_H_ */

@@ -1,0 +1,357 @@
+// kf_capi.cu -- context management and the C entry points of the track fit
+// (declared in include/kf.h).
+#include <algorithm>
+#include <cmath>
+#include <new>
+
+#include "kf_internal.h"
+
+namespace kfi {
+
+int scratch_reserve(kf_ctx* ctx, Scratch& s, size_t bytes) {
+  if (bytes <= s.bytes) return KF_OK;
+  const size_t want = std::max(bytes, s.bytes + s.bytes / 2);
+  const size_t grow = want - s.bytes;
+  if (ctx->budget && ctx->allocated + grow > ctx->budget) return KF_ENOMEM;
+  if (s.ptr) {
+    KF_CUDA_TRY(ctx, cudaDeviceSynchronize());
+    cudaFree(s.ptr);
+    ctx->allocated -= s.bytes;
+    s.ptr = nullptr;
+    s.bytes = 0;
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, want);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return KF_ENOMEM;
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e);
+  s.ptr = p;
+  s.bytes = want;
+  ctx->allocated += want;
+  // cached graphs may hold the old pointer
+  for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+  ctx->graphs.clear();
+  return KF_OK;
+}
+
+static void scratch_free(kf_ctx* ctx, Scratch& s) {
+  if (s.ptr) cudaFree(s.ptr);
+  ctx->allocated -= s.bytes;
+  s.ptr = nullptr;
+  s.bytes = 0;
+}
+
+static bool tracks_ok(const kf_tracks* t, bool need_lo) {
+  return t && t->n >= 0 && t->par && t->cov && t->charge && (!need_lo || t->par_lo);
+}
+
+// Validate a fit request against the configuration.
+static int check_fit(kf_ctx* ctx, const kf_tracks* seeds, const kf_track_hits* hits,
+                     const kf_tracks* out) {
+  if (!ctx || !tracks_ok(seeds, false) || !hits || !out) return KF_EINVAL;
+  if (!out->par || !out->cov) return KF_EINVAL;
+  if (out->n != seeds->n || hits->n_tracks != seeds->n) return KF_EINVAL;
+  if (hits->n_layers < 1 || hits->n_layers > ctx->cfg.n_layers) return KF_EINVAL;
+  if (seeds->n > 0 && !hits->xyz) return KF_EINVAL;
+  return KF_OK;
+}
+
+}  // namespace kfi
+
+using namespace kfi;
+
+extern "C" {
+
+const char* kf_strerror(int code) {
+  switch (code) {
+    case KF_OK: return "ok";
+    case KF_EINVAL: return "invalid argument";
+    case KF_ENOMEM: return "out of device memory or context budget";
+    case KF_EAGAIN: return "not ready / not admitted yet";
+    case KF_ETIMEDOUT: return "timed out";
+    case KF_ECUDA: return "CUDA runtime error";
+    case KF_ENOTSUP: return "not supported";
+    default: return "unknown error";
+  }
+}
+
+int kf_last_cuda_error(const kf_ctx* ctx) { return ctx ? ctx->last_cuda : 0; }
+
+int kf_create(kf_ctx** out, const kf_config* cfg, int device, size_t mem_budget_bytes) {
+  if (!out || !cfg) return KF_EINVAL;
+  *out = nullptr;
+  if (cfg->n_layers < 1 || cfg->n_layers > kMaxLayers || !cfg->radius_cm) return KF_EINVAL;
+  if (!(cfg->bz_tesla != 0.f) || !std::isfinite(cfg->bz_tesla)) return KF_EINVAL;
+  if (!(cfg->sigma_xy_cm > 0.f) || !(cfg->sigma_z_cm > 0.f)) return KF_EINVAL;
+  if (cfg->max_cands < 1 || cfg->max_cands > 8 || !(cfg->chi2_cut > 0.f)) return KF_EINVAL;
+  float prev = 0.f;
+  for (int l = 0; l < cfg->n_layers; ++l) {
+    if (!(cfg->radius_cm[l] > prev) || !std::isfinite(cfg->radius_cm[l])) return KF_EINVAL;
+    prev = cfg->radius_cm[l];
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return KF_ENOTSUP;
+  }
+  kf_ctx* ctx = new (std::nothrow) kf_ctx();
+  if (!ctx) return KF_ENOMEM;
+  ctx->cfg = *cfg;
+  for (int l = 0; l < cfg->n_layers; ++l) ctx->radius[l] = cfg->radius_cm[l];
+  ctx->cfg.radius_cm = ctx->radius;
+  ctx->device = device;
+  ctx->budget = mem_budget_bytes;
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return KF_ECUDA;
+  }
+  *out = ctx;
+  return KF_OK;
+}
+
+}  // extern "C"
+void kf_serve_shutdown_internal(kf_ctx* ctx);
+extern "C" {
+
+void kf_destroy(kf_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  kf_serve_shutdown_internal(ctx);
+  cudaDeviceSynchronize();
+  for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+  scratch_free(ctx, ctx->s_status);
+  scratch_free(ctx, ctx->s_lo);
+  scratch_free(ctx, ctx->s_host_in);
+  scratch_free(ctx, ctx->s_host_out);
+  if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+  delete ctx;
+}
+
+// Per-layer fit replayed from a captured graph (one kernel node per layer).
+int kf_fit(kf_ctx* ctx, const kf_tracks* seeds, const kf_track_hits* hits, kf_tracks* out, float* chi2,
+           int32_t* status, void* stream) {
+  int rc = check_fit(ctx, seeds, hits, out);
+  if (rc) return rc;
+  const int64_t n = seeds->n;
+  if (n == 0) return KF_OK;
+  KF_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  int32_t* st = status;
+  if (!st) {
+    rc = scratch_reserve(ctx, ctx->s_status, size_t(n) * sizeof(int32_t));
+    if (rc) return rc;
+    st = static_cast<int32_t*>(ctx->s_status.ptr);
+  }
+  float* lo = out->par_lo;
+  if (!lo) {
+    rc = scratch_reserve(ctx, ctx->s_lo, size_t(n) * 3 * sizeof(float));
+    if (rc) return rc;
+    lo = static_cast<float*>(ctx->s_lo.ptr);
+  }
+  const int L = hits->n_layers;
+  const float a_scale = float(kCLight * double(ctx->cfg.bz_tesla));
+  const float v0 = ctx->cfg.sigma_xy_cm * ctx->cfg.sigma_xy_cm;
+  const float v2 = ctx->cfg.sigma_z_cm * ctx->cfg.sigma_z_cm;
+  const int grid = fit_grid(ctx, n);
+  std::vector<uint64_t> key = {1,
+                               uint64_t(n),
+                               uint64_t(L),
+                               uint64_t(grid),
+                               reinterpret_cast<uint64_t>(seeds->par),
+                               reinterpret_cast<uint64_t>(seeds->par_lo),
+                               reinterpret_cast<uint64_t>(seeds->cov),
+                               reinterpret_cast<uint64_t>(seeds->charge),
+                               reinterpret_cast<uint64_t>(out->par),
+                               reinterpret_cast<uint64_t>(lo),
+                               reinterpret_cast<uint64_t>(out->cov),
+                               reinterpret_cast<uint64_t>(hits->xyz),
+                               reinterpret_cast<uint64_t>(hits->valid),
+                               reinterpret_cast<uint64_t>(chi2),
+                               reinterpret_cast<uint64_t>(st)};
+  cudaStream_t user = static_cast<cudaStream_t>(stream);
+  GraphEntry* hit_entry = nullptr;
+  for (auto& g : ctx->graphs)
+    if (g.key == key) hit_entry = &g;
+  if (!hit_entry) {
+    cudaStream_t cs = ctx->capture_stream;
+    KF_CUDA_TRY(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t le = cudaSuccess;
+    for (int l = 0; l < L && le == cudaSuccess; ++l) {
+      FitLayerArgs a;
+      a.in_par = l == 0 ? seeds->par : out->par;
+      a.in_lo = l == 0 ? seeds->par_lo : lo;
+      a.in_cov = l == 0 ? seeds->cov : out->cov;
+      a.charge = seeds->charge;
+      a.out_par = out->par;
+      a.out_lo = lo;
+      a.out_cov = out->cov;
+      a.hit = hits->xyz + int64_t(l) * 3 * n;
+      a.valid = hits->valid ? hits->valid + int64_t(l) * n : nullptr;
+      a.chi2 = chi2 ? chi2 + int64_t(l) * n : nullptr;
+      a.status = st;
+      a.n = n;
+      a.a_scale = a_scale;
+      a.R = ctx->radius[l];
+      a.v0 = v0;
+      a.v1 = v0;
+      a.v2 = v2;
+      a.first = l == 0;
+      a.last = l == L - 1;
+      le = launch_fit_layer(a, grid, cs);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+    if (le != cudaSuccess) return cuda_fail(ctx, le);
+    if (ee != cudaSuccess) return cuda_fail(ctx, ee);
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return cuda_fail(ctx, ie);
+    if (ctx->graphs.size() >= 16) {
+      auto old = std::min_element(ctx->graphs.begin(), ctx->graphs.end(),
+                                  [](const GraphEntry& x, const GraphEntry& y) { return x.last_use < y.last_use; });
+      cudaGraphExecDestroy(old->exec);
+      ctx->graphs.erase(old);
+    }
+    ctx->graphs.push_back(GraphEntry{key, exec, 0});
+    hit_entry = &ctx->graphs.back();
+  }
+  hit_entry->last_use = ++ctx->use_clock;
+  KF_CUDA_TRY(ctx, cudaGraphLaunch(hit_entry->exec, user));
+  return KF_OK;
+}
+
+int kf_fit_fused(kf_ctx* ctx, const kf_tracks* seeds, const kf_track_hits* hits, kf_tracks* out, float* chi2,
+                 int32_t* status, void* stream) {
+  int rc = check_fit(ctx, seeds, hits, out);
+  if (rc) return rc;
+  const int64_t n = seeds->n;
+  if (n == 0) return KF_OK;
+  KF_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  FitFusedArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.in_par = seeds->par;
+  a.in_lo = seeds->par_lo;
+  a.in_cov = seeds->cov;
+  a.charge = seeds->charge;
+  a.out_par = out->par;
+  a.out_lo = out->par_lo;
+  a.out_cov = out->cov;
+  a.hits = hits->xyz;
+  a.valid = hits->valid;
+  a.chi2 = chi2;
+  a.status = status;
+  a.n = n;
+  a.n_layers = hits->n_layers;
+  a.a_scale = float(kCLight * double(ctx->cfg.bz_tesla));
+  a.v0 = a.v1 = ctx->cfg.sigma_xy_cm * ctx->cfg.sigma_xy_cm;
+  a.v2 = ctx->cfg.sigma_z_cm * ctx->cfg.sigma_z_cm;
+  for (int l = 0; l < hits->n_layers; ++l) a.R[l] = ctx->radius[l];
+  KF_CUDA_TRY(ctx, launch_fit_fused(a, fit_grid(ctx, n), static_cast<cudaStream_t>(stream)));
+  return KF_OK;
+}
+
+int kf_fit_f64(kf_ctx* ctx, const kf_tracks_f64* seeds, const kf_track_hits* hits, kf_tracks_f64* out,
+               double* chi2, int32_t* status, const int64_t* event_off, int32_t n_events, void* stream) {
+  if (!ctx || !seeds || !hits || !out || !event_off || n_events < 0) return KF_EINVAL;
+  if (!seeds->par || !seeds->cov || !seeds->charge || !out->par || !out->cov) return KF_EINVAL;
+  const int64_t n = seeds->n;
+  if (n < 0 || out->n != n || hits->n_tracks != n) return KF_EINVAL;
+  if (hits->n_layers < 1 || hits->n_layers > ctx->cfg.n_layers) return KF_EINVAL;
+  if (event_off[0] != 0 || event_off[n_events] != n) return KF_EINVAL;
+  for (int e = 0; e < n_events; ++e)
+    if (event_off[e + 1] < event_off[e]) return KF_EINVAL;
+  if (n == 0) return KF_OK;
+  KF_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  int32_t* st = status;
+  if (!st) {
+    int rc = scratch_reserve(ctx, ctx->s_status, size_t(n) * sizeof(int32_t));
+    if (rc) return rc;
+    st = static_cast<int32_t*>(ctx->s_status.ptr);
+  }
+  const double bz = ctx->cfg.bz_tesla;
+  const double sxy = ctx->cfg.sigma_xy_cm, sz = ctx->cfg.sigma_z_cm;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int L = hits->n_layers;
+  for (int e = 0; e < n_events; ++e) {
+    for (int l = 0; l < L; ++l) {
+      FitF64Args a;
+      a.in_par = l == 0 ? seeds->par : out->par;
+      a.in_cov = l == 0 ? seeds->cov : out->cov;
+      a.charge = seeds->charge;
+      a.out_par = out->par;
+      a.out_cov = out->cov;
+      a.hit = hits->xyz + int64_t(l) * 3 * n;
+      a.valid = hits->valid ? hits->valid + int64_t(l) * n : nullptr;
+      a.chi2 = chi2 ? chi2 + int64_t(l) * n : nullptr;
+      a.status = st;
+      a.n = n;
+      a.begin = event_off[e];
+      a.end = event_off[e + 1];
+      a.a_scale = kCLight * bz;
+      a.R = double(ctx->radius[l]);
+      a.v0 = a.v1 = sxy * sxy;
+      a.v2 = sz * sz;
+      a.first = l == 0;
+      a.last = l == L - 1;
+      KF_CUDA_TRY(ctx, launch_fit_f64(a, s));
+    }
+  }
+  return KF_OK;
+}
+
+int kf_fit_host(kf_ctx* ctx, const kf_tracks* seeds, const kf_track_hits* hits, kf_tracks* out, float* chi2,
+                int32_t* status, void* stream) {
+  int rc = check_fit(ctx, seeds, hits, out);
+  if (rc) return rc;
+  const int64_t n = seeds->n;
+  if (n == 0) return KF_OK;
+  KF_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  const int L = hits->n_layers;
+  // device staging: inputs [par 6n, lo 3n, cov 21n, hits 3Ln] floats + charge n + valid Ln bytes;
+  // outputs [par 6n, lo 3n, cov 21n, chi2 Ln] floats + status n int32
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t b_par = al(6 * n * 4), b_lo = al(3 * n * 4), b_cov = al(21 * n * 4), b_hit = al(size_t(3) * L * n * 4),
+               b_q = al(n), b_val = al(size_t(L) * n), b_chi = al(size_t(L) * n * 4), b_st = al(n * 4);
+  const size_t in_bytes = b_par + b_lo + b_cov + b_hit + b_q + b_val;
+  const size_t out_bytes = b_par + b_lo + b_cov + b_chi + b_st;
+  rc = scratch_reserve(ctx, ctx->s_host_in, in_bytes);
+  if (rc) return rc;
+  rc = scratch_reserve(ctx, ctx->s_host_out, out_bytes);
+  if (rc) return rc;
+  char* di = static_cast<char*>(ctx->s_host_in.ptr);
+  char* dout = static_cast<char*>(ctx->s_host_out.ptr);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  kf_tracks ds{n, reinterpret_cast<float*>(di), seeds->par_lo ? reinterpret_cast<float*>(di + b_par) : nullptr,
+               reinterpret_cast<float*>(di + b_par + b_lo), reinterpret_cast<int8_t*>(di + b_par + b_lo + b_cov + b_hit)};
+  float* dhit = reinterpret_cast<float*>(di + b_par + b_lo + b_cov);
+  uint8_t* dval = hits->valid ? reinterpret_cast<uint8_t*>(di + b_par + b_lo + b_cov + b_hit + b_q) : nullptr;
+  kf_tracks dout_t{n, reinterpret_cast<float*>(dout), reinterpret_cast<float*>(dout + b_par),
+                   reinterpret_cast<float*>(dout + b_par + b_lo), ds.charge};
+  float* dchi = reinterpret_cast<float*>(dout + b_par + b_lo + b_cov);
+  int32_t* dst = reinterpret_cast<int32_t*>(dout + b_par + b_lo + b_cov + b_chi);
+  KF_CUDA_TRY(ctx, cudaMemcpyAsync(ds.par, seeds->par, 6 * n * 4, cudaMemcpyHostToDevice, s));
+  if (seeds->par_lo) KF_CUDA_TRY(ctx, cudaMemcpyAsync(ds.par_lo, seeds->par_lo, 3 * n * 4, cudaMemcpyHostToDevice, s));
+  KF_CUDA_TRY(ctx, cudaMemcpyAsync(ds.cov, seeds->cov, 21 * n * 4, cudaMemcpyHostToDevice, s));
+  KF_CUDA_TRY(ctx, cudaMemcpyAsync(ds.charge, seeds->charge, n, cudaMemcpyHostToDevice, s));
+  KF_CUDA_TRY(ctx, cudaMemcpyAsync(dhit, hits->xyz, size_t(3) * L * n * 4, cudaMemcpyHostToDevice, s));
+  if (dval) KF_CUDA_TRY(ctx, cudaMemcpyAsync(dval, hits->valid, size_t(L) * n, cudaMemcpyHostToDevice, s));
+  kf_track_hits dh{n, L, dhit, dval};
+  rc = kf_fit(ctx, &ds, &dh, &dout_t, dchi, dst, stream);
+  if (rc) return rc;
+  KF_CUDA_TRY(ctx, cudaMemcpyAsync(out->par, dout_t.par, 6 * n * 4, cudaMemcpyDeviceToHost, s));
+  if (out->par_lo) KF_CUDA_TRY(ctx, cudaMemcpyAsync(out->par_lo, dout_t.par_lo, 3 * n * 4, cudaMemcpyDeviceToHost, s));
+  KF_CUDA_TRY(ctx, cudaMemcpyAsync(out->cov, dout_t.cov, 21 * n * 4, cudaMemcpyDeviceToHost, s));
+  if (out->charge && out->charge != seeds->charge)
+    KF_CUDA_TRY(ctx, cudaMemcpyAsync(out->charge, ds.charge, n, cudaMemcpyDeviceToHost, s));
+  if (chi2) KF_CUDA_TRY(ctx, cudaMemcpyAsync(chi2, dchi, size_t(L) * n * 4, cudaMemcpyDeviceToHost, s));
+  if (status) KF_CUDA_TRY(ctx, cudaMemcpyAsync(status, dst, n * 4, cudaMemcpyDeviceToHost, s));
+  KF_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  return KF_OK;
+}
+
+}  // extern "C"

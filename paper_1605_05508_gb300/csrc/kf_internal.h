@@ -1,0 +1,134 @@
+// kf_internal.h -- context object and launch helpers shared by the .cu files
+// of libkf (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/kf.h"
+
+namespace kfi {
+
+constexpr int kMaxLayers = 64;
+constexpr double kCLight = 0.00299792458;  // GeV / (T cm)
+
+// A device allocation owned by the context, grown on demand.
+struct Scratch {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+// One captured and instantiated CUDA graph, keyed by the exact argument set.
+struct GraphEntry {
+  std::vector<uint64_t> key;
+  cudaGraphExec_t exec = nullptr;
+  uint64_t last_use = 0;
+};
+
+struct Serve;  // serving loop state (kf_serve.cu)
+
+}  // namespace kfi
+
+struct kf_ctx {
+  kf_config cfg;
+  float radius[kfi::kMaxLayers];
+  int device = 0;
+  int num_sms = 0;
+  size_t budget = 0;     // 0 = unbounded
+  size_t allocated = 0;  // bytes of context-owned device memory
+  int last_cuda = 0;
+  cudaStream_t capture_stream = nullptr;
+  // scratch pools
+  kfi::Scratch s_status, s_lo, s_host_in, s_host_out;
+  // graph cache
+  std::vector<kfi::GraphEntry> graphs;
+  uint64_t use_clock = 0;
+  kfi::Serve* serve = nullptr;
+};
+
+namespace kfi {
+
+// Record a CUDA error on the context and turn it into KF_ECUDA.
+inline int cuda_fail(kf_ctx* ctx, cudaError_t e) {
+  if (ctx) ctx->last_cuda = static_cast<int>(e);
+  return KF_ECUDA;
+}
+
+#define KF_CUDA_TRY(ctx, expr)                          \
+  do {                                                  \
+    cudaError_t e__ = (expr);                           \
+    if (e__ != cudaSuccess) return kfi::cuda_fail(ctx, e__); \
+  } while (0)
+
+// Grow a scratch buffer to at least `bytes` (under the context budget).
+int scratch_reserve(kf_ctx* ctx, Scratch& s, size_t bytes);
+
+// Arguments of one fit layer step (single precision).
+struct FitLayerArgs {
+  const float* in_par;
+  const float* in_lo;  // may be null (lo = 0)
+  const float* in_cov;
+  const int8_t* charge;
+  float* out_par;
+  float* out_lo;
+  float* out_cov;
+  const float* hit;      // [3][n] of this layer
+  const uint8_t* valid;  // [n] of this layer or null
+  float* chi2;           // [n] of this layer or null
+  int32_t* status;       // [n], required
+  int64_t n;
+  float a_scale;  // C_LIGHT * Bz
+  float R, v0, v1, v2;
+  int first;  // 1: initialise status, always write the state
+  int last;   // 1: run the positive-definite check
+};
+
+struct FitFusedArgs {
+  const float* in_par;
+  const float* in_lo;
+  const float* in_cov;
+  const int8_t* charge;
+  float* out_par;
+  float* out_lo;  // may be null
+  float* out_cov;
+  const float* hits;     // [L][3][n]
+  const uint8_t* valid;  // [L][n] or null
+  float* chi2;           // [L][n] or null
+  int32_t* status;       // [n] or null
+  int64_t n;
+  int n_layers;
+  float a_scale;
+  float v0, v1, v2;
+  float R[kMaxLayers];  // layer radii, by value
+};
+
+struct FitF64Args {
+  const double* in_par;
+  const double* in_cov;
+  const int8_t* charge;
+  double* out_par;
+  double* out_cov;
+  const float* hit;      // [3][n] of this layer (whole batch)
+  const uint8_t* valid;  // [n] of this layer or null
+  double* chi2;          // [n] of this layer or null
+  int32_t* status;
+  int64_t n;       // whole batch (row stride)
+  int64_t begin;   // this launch: tracks [begin, end)
+  int64_t end;
+  double a_scale;
+  double R, v0, v1, v2;
+  int first, last;
+};
+
+// kernel launchers (kf_fit.cu)
+cudaError_t launch_fit_layer(const FitLayerArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_fit_fused(const FitFusedArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_fit_f64(const FitF64Args& a, cudaStream_t st);
+int fit_grid(kf_ctx* ctx, int64_t n);
+
+}  // namespace kfi

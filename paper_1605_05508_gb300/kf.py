@@ -1,0 +1,199 @@
+"""Python binding of libkf (include/kf.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of its own: it packs torch tensors (device memory, or pinned host
+memory for the *_host calls) into the ABI's plain structs and raises
+`KfError` on a negative return code. PyTorch provides allocation and streams.
+
+The CUDA library must have been built (`paper_1605_05508_gb300.build`); a
+missing library raises immediately - there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libkf.so")
+
+KF_OK, KF_EINVAL, KF_ENOMEM, KF_EAGAIN, KF_ETIMEDOUT, KF_ECUDA, KF_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
+ST_NOT_REACHED, ST_NEWTON_FAIL, ST_TANGENT, ST_NOT_PD, ST_NO_HIT = 1, 2, 4, 8, 16
+ST_STOPPED = ST_NOT_REACHED | ST_NEWTON_FAIL | ST_TANGENT
+
+
+class KfError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+        self.code = code
+
+
+class kf_config(C.Structure):
+    _fields_ = [("bz_tesla", C.c_float), ("n_layers", C.c_int32), ("radius_cm", C.POINTER(C.c_float)),
+                ("sigma_xy_cm", C.c_float), ("sigma_z_cm", C.c_float), ("chi2_cut", C.c_float),
+                ("max_cands", C.c_int32)]
+
+
+class kf_tracks(C.Structure):
+    _fields_ = [("n", C.c_int64), ("par", C.c_void_p), ("par_lo", C.c_void_p), ("cov", C.c_void_p),
+                ("charge", C.c_void_p)]
+
+
+class kf_tracks_f64(C.Structure):
+    _fields_ = [("n", C.c_int64), ("par", C.c_void_p), ("cov", C.c_void_p), ("charge", C.c_void_p)]
+
+
+class kf_track_hits(C.Structure):
+    _fields_ = [("n_tracks", C.c_int64), ("n_layers", C.c_int32), ("xyz", C.c_void_p), ("valid", C.c_void_p)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libkf.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libkf is not built ({LIB_PATH} missing): run paper_1605_05508_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+        L.kf_create.argtypes = [C.POINTER(vp), C.POINTER(kf_config), C.c_int, C.c_size_t]
+        L.kf_destroy.argtypes = [vp]
+        L.kf_destroy.restype = None
+        L.kf_strerror.argtypes = [C.c_int]
+        L.kf_strerror.restype = C.c_char_p
+        L.kf_last_cuda_error.argtypes = [vp]
+        for name in ("kf_fit", "kf_fit_fused", "kf_fit_host"):
+            getattr(L, name).argtypes = [vp, C.POINTER(kf_tracks), C.POINTER(kf_track_hits), C.POINTER(kf_tracks),
+                                         vp, vp, vp]
+        L.kf_fit_f64.argtypes = [vp, C.POINTER(kf_tracks_f64), C.POINTER(kf_track_hits), C.POINTER(kf_tracks_f64),
+                                 vp, vp, C.POINTER(i64), i32, vp]
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return lib().kf_strerror(code).decode()
+    except RuntimeError:
+        return f"code {code}"
+
+
+def _check(rc: int, what: str, ctx=None):
+    if rc != KF_OK:
+        err = KfError(rc, what)
+        if rc == KF_ECUDA and ctx is not None:
+            err.cuda_error = lib().kf_last_cuda_error(ctx)
+        raise err
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+@dataclass
+class Tracks:
+    """SoA track batch: par [6, n], par_lo [3, n] or None, cov [21, n], charge [n] int8."""
+    par: object
+    cov: object
+    charge: object
+    par_lo: object = None
+
+    @property
+    def n(self) -> int:
+        return int(self.par.shape[1])
+
+    def abi(self) -> kf_tracks:
+        return kf_tracks(self.n, _ptr(self.par), _ptr(self.par_lo), _ptr(self.cov), _ptr(self.charge))
+
+    def abi_f64(self) -> kf_tracks_f64:
+        return kf_tracks_f64(self.n, _ptr(self.par), _ptr(self.cov), _ptr(self.charge))
+
+
+@dataclass
+class TrackHits:
+    """xyz [L, 3, n] float32, valid [L, n] uint8 or None."""
+    xyz: object
+    valid: object = None
+
+    def abi(self) -> kf_track_hits:
+        L, _, n = self.xyz.shape
+        return kf_track_hits(n, L, _ptr(self.xyz), _ptr(self.valid))
+
+
+class Context:
+    """Owns a kf_ctx; `handle` is the opaque pointer."""
+
+    def __init__(self, radii, bz=3.8, sigma_xy=0.01, sigma_z=0.1, chi2_cut=30.0, max_cands=6, device=0,
+                 mem_budget_bytes=0):
+        self._radii = (C.c_float * len(radii))(*[float(r) for r in radii])
+        self.cfg = kf_config(float(bz), len(radii), self._radii, float(sigma_xy), float(sigma_z), float(chi2_cut),
+                             int(max_cands))
+        self.handle = kf_create(self.cfg, device, mem_budget_bytes)
+
+    def close(self):
+        if self.handle:
+            kf_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def kf_create(cfg: kf_config, device: int = 0, mem_budget_bytes: int = 0):
+    h = C.c_void_p()
+    _check(lib().kf_create(C.byref(h), C.byref(cfg), device, mem_budget_bytes), "kf_create")
+    return h
+
+
+def kf_destroy(handle):
+    lib().kf_destroy(handle)
+
+
+def _h(ctx):
+    return ctx.handle if isinstance(ctx, Context) else ctx
+
+
+def kf_fit(ctx, seeds: Tracks, hits: TrackHits, out: Tracks, chi2=None, status=None, stream=None):
+    s, h, o = seeds.abi(), hits.abi(), out.abi()
+    _check(lib().kf_fit(_h(ctx), C.byref(s), C.byref(h), C.byref(o), _ptr(chi2), _ptr(status), _stream(stream)),
+           "kf_fit", _h(ctx))
+
+
+def kf_fit_fused(ctx, seeds: Tracks, hits: TrackHits, out: Tracks, chi2=None, status=None, stream=None):
+    s, h, o = seeds.abi(), hits.abi(), out.abi()
+    _check(lib().kf_fit_fused(_h(ctx), C.byref(s), C.byref(h), C.byref(o), _ptr(chi2), _ptr(status),
+                              _stream(stream)), "kf_fit_fused", _h(ctx))
+
+
+def kf_fit_host(ctx, seeds: Tracks, hits: TrackHits, out: Tracks, chi2=None, status=None, stream=None):
+    s, h, o = seeds.abi(), hits.abi(), out.abi()
+    _check(lib().kf_fit_host(_h(ctx), C.byref(s), C.byref(h), C.byref(o), _ptr(chi2), _ptr(status),
+                             _stream(stream)), "kf_fit_host", _h(ctx))
+
+
+def kf_fit_f64(ctx, seeds: Tracks, hits: TrackHits, out: Tracks, event_off, chi2=None, status=None, stream=None):
+    """event_off: sequence of n_events + 1 track offsets (host)."""
+    offs = (C.c_int64 * len(event_off))(*[int(v) for v in event_off])
+    s, h, o = seeds.abi_f64(), hits.abi(), out.abi_f64()
+    _check(lib().kf_fit_f64(_h(ctx), C.byref(s), C.byref(h), C.byref(o), _ptr(chi2), _ptr(status), offs,
+                            len(event_off) - 1, _stream(stream)), "kf_fit_f64", _h(ctx))

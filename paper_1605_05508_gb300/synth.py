@@ -175,18 +175,21 @@ def helix_crossing(vertex: np.ndarray, mom: np.ndarray, charge: np.ndarray,
     return out, reached
 
 
-def simulate_hits(rng: np.random.Generator, parts: Particles, det: Detector) -> TrackHits:
-    """Truth crossings on every layer plus the Gaussian hit smear."""
+def simulate_hits(rng: np.random.Generator, parts: Particles, det: Detector,
+                  keep_truth: bool = True) -> TrackHits:
+    """Truth crossings on every layer plus the Gaussian hit smear.
+    `keep_truth=False` skips the [L, n, 6] float64 truth array (large batches)."""
     L, n = det.n_layers, parts.n
     xyz = np.zeros((L, 3, n), dtype=np.float32)
     valid = np.zeros((L, n), dtype=np.uint8)
-    truth = np.full((L, n, 6), np.nan)
+    truth = np.full((L, n, 6), np.nan) if keep_truth else None
     alive = np.ones(n, dtype=bool)
     for li, R in enumerate(det.radii):
         st, ok = helix_crossing(parts.vertex, parts.mom, parts.charge, det.bz, R)
         ok &= alive
         alive = ok  # a particle that misses layer l misses every outer layer too
-        truth[li][ok] = st[ok]
+        if keep_truth:
+            truth[li][ok] = st[ok]
         smear = np.stack([rng.normal(0.0, det.sigma_xy, n), rng.normal(0.0, det.sigma_xy, n),
                           rng.normal(0.0, det.sigma_z, n)], axis=1)
         h = np.where(ok[:, None], st[:, :3] + smear, 0.0)
@@ -298,7 +301,8 @@ class FitEvent:
 
 def make_fit_batch(seed: int, n_tracks: int, det: Detector | None = None,
                    seed_mode: str = "truth_smeared", smear_scale: float = 1.0,
-                   pt_range=(0.5, 10.0), pt_mix=None, hit_noise: bool = True) -> FitEvent:
+                   pt_range=(0.5, 10.0), pt_mix=None, hit_noise: bool = True,
+                   keep_truth: bool = True) -> FitEvent:
     """All tracks of a fit batch (events are independent, so a batch of E events
     of T tracks is one draw of E*T tracks with per-event offsets kept by the
     caller). `hit_noise=False` places hits at the exact crossings."""
@@ -306,9 +310,9 @@ def make_fit_batch(seed: int, n_tracks: int, det: Detector | None = None,
     rng = np.random.default_rng(seed)
     parts = draw_particles(rng, n_tracks, pt_range=pt_range, pt_mix=pt_mix)
     if hit_noise:
-        hits = simulate_hits(rng, parts, det)
+        hits = simulate_hits(rng, parts, det, keep_truth)
     else:
-        hits = simulate_hits(rng, parts, Detector(det.radii, det.bz, 0.0, 0.0))
+        hits = simulate_hits(rng, parts, Detector(det.radii, det.bz, 0.0, 0.0), keep_truth)
     if seed_mode == "hits123":
         seeds = seeds_from_hits(hits, det.bz)
     elif seed_mode == "truth_smeared":

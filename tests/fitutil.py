@@ -1,0 +1,86 @@
+"""Shared helpers of the GPU parity tests: run the CUDA fit through the
+binding on seeded inputs, run the oracle on the same inputs, and compare
+with the stated tolerances:
+  parameters  |d| <= 1e-4 x scale (R_last for positions, |p| for momenta)
+  covariance  |dC_ij| <= 1e-3 sqrt(C_ii C_jj)
+  chi2        |d| <= 1e-3 absolute; FP32 leaves a floor near 4e-4 sqrt(chi2)
+              (momentum and path-length roundings at ~2e-7 cm), so at most a
+              1e-4 fraction of increments may exceed it, none beyond 3e-3
+  status      bits identical."""
+import numpy as np
+
+import oracle as O
+
+PAR_TOL = 1e-4
+COV_TOL = 1e-3
+CHI2_TOL = 1e-3
+CHI2_TOL_FRAC = 1e-4
+CHI2_TOL_MAX = 3e-3
+
+
+def to_dev(a, dtype=None):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def gpu_fit(ctx, seeds, hits_xyz, hits_valid, mode="graph", with_lo=True, sample=None):
+    """Fit on the GPU. Returns numpy dict(par [n,6] = hi + lo, cov [n,6,6], chi2 [L,n], status [n]);
+    `sample` (index array) keeps only those tracks."""
+    import torch
+    from paper_1605_05508_gb300 import kf
+    n = seeds.par.shape[1]
+    L = hits_xyz.shape[0]
+    s = kf.Tracks(to_dev(seeds.par), to_dev(seeds.cov), to_dev(seeds.charge))
+    out = kf.Tracks(torch.empty((6, n), device="cuda"), torch.empty((21, n), device="cuda"), s.charge,
+                    torch.empty((3, n), device="cuda") if with_lo else None)
+    h = kf.TrackHits(to_dev(hits_xyz), to_dev(hits_valid))
+    chi2 = torch.empty((L, n), device="cuda")
+    st = torch.empty(n, dtype=torch.int32, device="cuda")
+    if mode == "graph":
+        kf.kf_fit(ctx, s, h, out, chi2, st)
+    elif mode == "fused":
+        kf.kf_fit_fused(ctx, s, h, out, chi2, st)
+    else:
+        raise ValueError(mode)
+    torch.cuda.synchronize()
+    if sample is not None:
+        ix = torch.from_numpy(np.asarray(sample)).cuda()
+        out = kf.Tracks(out.par[:, ix], out.cov[:, ix], None, out.par_lo[:, ix] if with_lo else None)
+        chi2, st = chi2[:, ix], st[ix]
+    return unpack(out, chi2, st)
+
+
+def unpack(out, chi2, st):
+    par = out.par.double().cpu().numpy().T.copy()
+    if out.par_lo is not None:
+        par[:, :3] += out.par_lo.double().cpu().numpy().T
+    cov = O.full_cov_from_packed(out.cov.double().cpu().numpy())
+    return dict(par=par, cov=cov, chi2=chi2.double().cpu().numpy(), status=st.cpu().numpy())
+
+
+def oracle_fit(seeds, hits_xyz, hits_valid, det, n_threads=0):
+    return O.fit(seeds.par, seeds.cov, seeds.charge, hits_xyz, hits_valid, det.radii[:hits_xyz.shape[0]], det.bz,
+                 det.sigma_xy, det.sigma_z, n_threads=n_threads)
+
+
+def compare(g, r, radius_scale, chi2_frac=CHI2_TOL_FRAC, label=""):
+    """Assert parity; returns a dict of the observed errors."""
+    np.testing.assert_array_equal(g["status"], r["status"], err_msg=f"{label} status bits")
+    pscale = np.concatenate([np.full((len(r["par"]), 3), radius_scale),
+                             np.repeat(np.linalg.norm(r["par"][:, 3:], axis=1)[:, None], 3, axis=1)], axis=1)
+    perr = np.abs(g["par"] - r["par"]) / pscale
+    sd = np.sqrt(np.abs(np.diagonal(r["cov"], axis1=1, axis2=2)))
+    cerr = np.abs(g["cov"] - r["cov"]) / (sd[:, :, None] * sd[:, None, :] + 1e-300)
+    both = (g["chi2"] >= 0) & (r["chi2"] >= 0)
+    np.testing.assert_array_equal(g["chi2"] >= 0, r["chi2"] >= 0, err_msg=f"{label} update pattern")
+    cer = np.abs(g["chi2"] - r["chi2"])[both]
+    over = int((cer > CHI2_TOL).sum())
+    stats = dict(par_max=float(perr.max(initial=0)), cov_max=float(cerr.max(initial=0)),
+                 chi2_max=float(cer.max(initial=0)), chi2_over=over, n_chi2=int(both.sum()))
+    assert stats["par_max"] <= PAR_TOL, (label, stats)
+    assert stats["cov_max"] <= COV_TOL, (label, stats)
+    assert over <= max(0, int(chi2_frac * cer.size)) and stats["chi2_max"] <= CHI2_TOL_MAX, (label, stats)
+    return stats

@@ -1,0 +1,58 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports
+every entry point include/*.h declares (no compute calls here)."""
+import ctypes
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[ \t]*(?:const\s+)?[A-Za-z_][\w]*[\s\*]+(kf_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1605_05508_gb300 import build as B
+    return B.build()
+
+
+def test_header_declares_the_fit_entry_points():
+    names = declared_functions()
+    for n in ("kf_create", "kf_destroy", "kf_fit", "kf_fit_fused", "kf_fit_f64", "kf_fit_host", "kf_strerror"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if ln.strip()}
+    assert set(declared_functions()) <= exported
+
+
+def test_strerror_and_argument_checks_need_no_gpu(libpath):
+    from paper_1605_05508_gb300 import kf
+    lib = kf.lib()
+    assert lib.kf_strerror(kf.KF_EINVAL) == b"invalid argument"
+    assert lib.kf_strerror(0) == b"ok"
+    # rejected before any CUDA call
+    assert lib.kf_create(None, None, 0, 0) == kf.KF_EINVAL
+    radii = (ctypes.c_float * 3)(4.0, 3.0, 8.0)  # not increasing
+    cfg = kf.kf_config(3.8, 3, radii, 0.01, 0.1, 30.0, 6)
+    h = ctypes.c_void_p()
+    assert lib.kf_create(ctypes.byref(h), ctypes.byref(cfg), 0, 0) == kf.KF_EINVAL
+    cfg = kf.kf_config(3.8, 3, (ctypes.c_float * 3)(4.0, 8.0, 12.0), 0.01, 0.1, 30.0, 9)  # max_cands > 8
+    assert lib.kf_create(ctypes.byref(h), ctypes.byref(cfg), 0, 0) == kf.KF_EINVAL
+    assert lib.kf_fit(None, None, None, None, None, None, None) == kf.KF_EINVAL
