@@ -334,7 +334,7 @@ def extras(a, ctx, kf, torch, dev, det, ev, seeds, hits, out, chi2, status, stre
     if rank == 0:
         import oracle as O
         cores = os.cpu_count() or 1
-        m = min(n, 10 * a.tracks)
+        m = min(n, 50 * a.tracks)
         O.lib()
         t0 = time.perf_counter()
         O.fit(ev.seeds.par[:, :m], ev.seeds.cov[:, :m], ev.seeds.charge[:m], ev.hits.xyz[:, :, :m],

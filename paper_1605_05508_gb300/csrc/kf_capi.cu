@@ -48,13 +48,14 @@ static bool tracks_ok(const kf_tracks* t, bool need_lo) {
 }
 
 // Validate a fit request against the configuration.
+// An empty batch (n = 0) is valid with any pointers.
 static int check_fit(kf_ctx* ctx, const kf_tracks* seeds, const kf_track_hits* hits,
                      const kf_tracks* out) {
-  if (!ctx || !tracks_ok(seeds, false) || !hits || !out) return KF_EINVAL;
-  if (!out->par || !out->cov) return KF_EINVAL;
-  if (out->n != seeds->n || hits->n_tracks != seeds->n) return KF_EINVAL;
+  if (!ctx || !seeds || !hits || !out) return KF_EINVAL;
+  if (seeds->n < 0 || out->n != seeds->n || hits->n_tracks != seeds->n) return KF_EINVAL;
   if (hits->n_layers < 1 || hits->n_layers > ctx->cfg.n_layers) return KF_EINVAL;
-  if (seeds->n > 0 && !hits->xyz) return KF_EINVAL;
+  if (seeds->n == 0) return KF_OK;
+  if (!tracks_ok(seeds, false) || !out->par || !out->cov || !hits->xyz) return KF_EINVAL;
   return KF_OK;
 }
 
@@ -258,9 +259,10 @@ int kf_fit_fused(kf_ctx* ctx, const kf_tracks* seeds, const kf_track_hits* hits,
 int kf_fit_f64(kf_ctx* ctx, const kf_tracks_f64* seeds, const kf_track_hits* hits, kf_tracks_f64* out,
                double* chi2, int32_t* status, const int64_t* event_off, int32_t n_events, void* stream) {
   if (!ctx || !seeds || !hits || !out || !event_off || n_events < 0) return KF_EINVAL;
-  if (!seeds->par || !seeds->cov || !seeds->charge || !out->par || !out->cov) return KF_EINVAL;
   const int64_t n = seeds->n;
   if (n < 0 || out->n != n || hits->n_tracks != n) return KF_EINVAL;
+  if (n > 0 && (!seeds->par || !seeds->cov || !seeds->charge || !out->par || !out->cov || !hits->xyz))
+    return KF_EINVAL;
   if (hits->n_layers < 1 || hits->n_layers > ctx->cfg.n_layers) return KF_EINVAL;
   if (event_off[0] != 0 || event_off[n_events] != n) return KF_EINVAL;
   for (int e = 0; e < n_events; ++e)

@@ -16,8 +16,8 @@
 namespace kfi {
 
 constexpr int kFitThreads = 256;
-constexpr int kNewtonF32 = 3;  // Newton iterations from the straight-line guess
-constexpr int kNewtonF64 = 4;
+constexpr int kNewtonF32 = 12;  // iteration cap of the safeguarded Newton solve
+constexpr int kNewtonF64 = 16;
 
 // Positive-definiteness of the rank-5 covariance: Cholesky of P C P^T where P
 // maps to (t . pos, z, px, py, pz), t the transverse tangent of the cylinder

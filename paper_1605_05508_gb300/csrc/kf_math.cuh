@@ -51,8 +51,6 @@ constexpr double kTangentCos = 0.01;
 // packed lower-triangle index, row-major: (i, j) -> i(i+1)/2 + j for j <= i
 KF_HD constexpr int sym(int i, int j) { return i >= j ? (i * (i + 1)) / 2 + j : (j * (j + 1)) / 2 + i; }
 
-KF_HD void sincos_t(float x, float* s, float* c) { sincosf(x, s, c); }
-KF_HD void sincos_t(double x, double* s, double* c) { sincos(x, s, c); }
 KF_HD float sqrt_t(float x) { return sqrtf(x); }
 KF_HD double sqrt_t(double x) { return sqrt(x); }
 KF_HD float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
@@ -60,11 +58,49 @@ KF_HD double fma_t(double a, double b, double c) { return fma(a, b, c); }
 KF_HD float abs_t(float x) { return fabsf(x); }
 KF_HD double abs_t(double x) { return fabs(x); }
 
-// sin(h)/h: Taylor 1 - h^2/6 (+ h^4/120) below the threshold, else sin/h
-template <typename T>
-KF_HD T sinc_of(T h, T sh) {
-  const T h2 = h * h;
-  return abs_t(h) < T(1e-2) ? T(1) - h2 * (T(1) / T(6)) * (T(1) - h2 * (T(1) / T(20))) : sh / h;
+// Reciprocal (correctly rounded) and a fast quotient for self-correcting
+// steps (Newton updates, Jacobian-only terms); plain division on the host.
+KF_HD float rcp_t(float x) {
+#ifdef __CUDA_ARCH__
+  return __frcp_rn(x);
+#else
+  return 1.0f / x;
+#endif
+}
+KF_HD double rcp_t(double x) { return 1.0 / x; }
+KF_HD float div_fast(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fdividef(a, b);
+#else
+  return a / b;
+#endif
+}
+KF_HD double div_fast(double a, double b) { return a / b; }
+
+// sin(h)/h and cos(h).  Single precision: for |h| <= 1/2 the Taylor series
+// 1 - h^2/3! + h^4/5! - h^6/7! + h^8/9!  and  1 - h^2/2! + ... - h^10/10!
+// (alternating, so the truncation error is below the first omitted term:
+// 2.5e-11 and 4e-13 at |h| = 1/2, far under float resolution); beyond that
+// the library sincosf.  Double precision always uses the library sincos.
+KF_HD void sinc_cos(float h, float& sch, float& ch) {
+  if (fabsf(h) <= 0.5f) {
+    const float h2 = h * h;
+    sch = fmaf(h2, fmaf(h2, fmaf(h2, fmaf(h2, 1.0f / 362880.0f, -1.0f / 5040.0f), 1.0f / 120.0f), -1.0f / 6.0f), 1.0f);
+    ch = fmaf(h2,
+              fmaf(h2, fmaf(h2, fmaf(h2, fmaf(h2, -1.0f / 3628800.0f, 1.0f / 40320.0f), -1.0f / 720.0f), 1.0f / 24.0f),
+                   -0.5f),
+              1.0f);
+  } else {
+    float sh;
+    sincosf(h, &sh, &ch);
+    sch = sh / h;
+  }
+}
+KF_HD void sinc_cos(double h, double& sch, double& ch) {
+  double sh;
+  sincos(h, &sh, &ch);
+  const double h2 = h * h;
+  sch = fabs(h) < 1e-4 ? 1.0 - h2 / 6.0 : sh / h;
 }
 
 // Error-free transformations (Knuth TwoSum, FMA TwoProd): a + b = s + e and
@@ -95,9 +131,9 @@ KF_HD HelixPoint<T> helix_eval(T px, T py, T k /*a/p*/, T ip /*1/p*/, T s) {
   HelixPoint<T> hp;
   const T th = k * s;
   const T h = T(0.5) * th;
-  T sh, ch;
-  sincos_t(h, &sh, &ch);
-  const T sch = sinc_of(h, sh);
+  T sch, ch;
+  sinc_cos(h, sch, ch);
+  const T sh = h * sch;
   const T sp = s * ip;
   hp.sa = sp * sch * ch;
   hp.ca = sp * h * sch * sch;
@@ -126,13 +162,13 @@ KF_HD int propagate(T p[6], T lo[3], T C[21], T a, T R) {
   const T pt2 = px * px + py * py;
   const T pp2 = pt2 + pz * pz;
   const T pmag = sqrt_t(pp2);
-  const T ip = T(1) / pmag;
-  const T ipt = T(1) / sqrt_t(pt2);
+  const T ip = rcp_t(pmag);
+  const T ipt = rcp_t(sqrt_t(pt2));
   const T k = a * ip;
   // reachability: the transverse circle (centre x + py/a, y - px/a, radius
   // pT/|a|) reaches at most radius d + rho
   if (a != T(0)) {
-    const T ia = T(1) / a;
+    const T ia = rcp_t(a);
     const T cx = x + py * ia, cy = y - px * ia;
     const T rho = sqrt_t(pt2) * abs_t(ia);
     if (R > sqrt_t(cx * cx + cy * cy) + rho) return ST_NOT_REACHED;
@@ -155,14 +191,20 @@ KF_HD int propagate(T p[6], T lo[3], T C[21], T a, T R) {
   T disc = b * b - (g0h + g0l);
   disc = disc > T(0) ? disc : T(0);
   T s = (sqrt_t(disc) - b) * pmag * ipt;
-  // Newton on g(s) = |r0 + d(s)|^2 - R^2 = G0 + 2 r0.d + |d|^2, with the
-  // large terms of the last iteration summed error-free
-#pragma unroll
+  // Safeguarded Newton on g(s) = |r0 + d(s)|^2 - R^2 = G0 + 2 r0.d + |d|^2,
+  // the large terms summed error-free when the position is a float pair.
+  // [lo, hi] brackets the first crossing: g < 0 on the way out below it; a
+  // point with g >= 0, or past the turning point (dg <= 0), bounds it from
+  // above.  A step leaving the bracket is replaced by bisection.  Newton
+  // converges quadratically (next error ~ ds^2 g''/2g'), so the loop stops
+  // once ds^2 |p| <= 1e-7 (r.p): the remaining error is below float
+  // resolution of the displacement.
+  T lo_s = T(0), hi_s = T(-1);  // hi_s < 0: no upper bound yet
   for (int it = 0; it < NEWTON; ++it) {
     const HelixPoint<T> hp = helix_eval(px, py, k, ip, s);
     const T U = xl + hp.dX, W = yl + hp.dY;
     T g;
-    if (EXT && it == NEWTON - 1) {
+    if (EXT) {
       T h1, l1, h2, l2, s1, e1, s2, e2;
       two_prod(T(2) * x, U, h1, l1);
       two_prod(T(2) * y, W, h2, l2);
@@ -172,9 +214,19 @@ KF_HD int propagate(T p[6], T lo[3], T C[21], T a, T R) {
     } else {
       g = g0h + (g0l + T(2) * (x * U + y * W) + (U * U + W * W));
     }
-    const T X = x + U, Y = y + W;
-    const T dg = T(2) * (X * hp.PX + Y * hp.PY) * ip;
-    s = s - g / dg;
+    const T rp = (x + U) * hp.PX + (y + W) * hp.PY;  // r.p at s
+    const T dg = T(2) * rp * ip;
+    if (g < T(0) && dg > T(0)) {
+      lo_s = s > lo_s ? s : lo_s;
+    } else {
+      hi_s = (hi_s < T(0) || s < hi_s) ? s : hi_s;
+    }
+    T sn = dg > T(0) ? s - div_fast(g, dg) : T(-1);
+    const bool in_bracket = sn >= lo_s && (hi_s < T(0) || sn <= hi_s);
+    if (!in_bracket) sn = hi_s >= T(0) ? T(0.5) * (lo_s + hi_s) : T(2) * s;
+    const T ds = sn - s;
+    s = sn;
+    if (in_bracket && ds * ds * pmag <= (sizeof(T) == 4 ? T(1e-7) : T(1e-20)) * rp) break;
   }
   const HelixPoint<T> hp = helix_eval(px, py, k, ip, s);
   const T X = x + (xl + hp.dX), Y = y + (yl + hp.dY);
@@ -183,7 +235,16 @@ KF_HD int propagate(T p[6], T lo[3], T C[21], T a, T R) {
   // remaining Newton step |g| p / (2 r.p) below 1e-5 R
   const T gres = X * X + Y * Y - R * R;
   if (!(rdotp > T(0)) || !(s > T(0))) return ST_NOT_REACHED;
-  if (!(abs_t(gres) * pmag <= T(2e-5) * R * rdotp)) return ST_NEWTON_FAIL;
+  if (!(abs_t(gres) * pmag <= T(2e-5) * R * rdotp)) {
+    // no convergence: a layer at (or within rounding of) the largest radius
+    // of the helix is not reached; anything else is a solver failure
+    if (a != T(0)) {
+      const T ia = T(1) / a;
+      const T cx = x + py * ia, cy = y - px * ia;
+      if (R > (sqrt_t(cx * cx + cy * cy) + sqrt_t(pt2) * abs_t(ia)) * (T(1) - T(1e-4))) return ST_NOT_REACHED;
+    }
+    return ST_NEWTON_FAIL;
+  }
   if (rdotp < T(kTangentCos) * R * sqrt_t(pt2)) return ST_TANGENT;
 
   // ---- surface Jacobian
@@ -203,7 +264,7 @@ KF_HD int propagate(T p[6], T lo[3], T C[21], T a, T R) {
     D[4][kk] = (kk == 0 ? -hp.sth : kk == 1 ? hp.cth : T(0)) + hp.PX * thp2 * pk;
   }
   // w_j = (dg/dx0_j)/(dg/ds) = (X dX/dx0_j + Y dY/dx0_j) p / (X PX + Y PY)
-  const T irp = T(1) / rdotp;
+  const T irp = rcp_t(rdotp);
   const T iden = pmag * irp;
   T w[6];
   w[0] = X * iden;
@@ -304,7 +365,7 @@ KF_HD T inverse_S(const T C[21], T v0, T v1, T v2, T Si[6]) {
   const T c10 = s21 * s20 - s10 * s22;
   const T c20 = s10 * s21 - s11 * s20;
   const T det = s00 * c00 + s10 * c10 + s20 * c20;
-  const T id = T(1) / det;
+  const T id = rcp_t(det);
   Si[0] = c00 * id;
   Si[1] = c10 * id;
   Si[2] = (s00 * s22 - s20 * s20) * id;

@@ -2,7 +2,10 @@
 binding on seeded inputs, run the oracle on the same inputs, and compare
 with the stated tolerances:
   parameters  |d| <= 1e-4 x scale (R_last for positions, |p| for momenta)
-  covariance  |dC_ij| <= 1e-3 sqrt(C_ii C_jj)
+  covariance  |dC_ij| <= 1e-3 sqrt(C_ii C_jj) in the local frame (n, t, z, px,
+              py, pz), n the radial direction at the oracle's position: after a
+              surface propagation the covariance is rank 5 with n exactly in its
+              null space, so the n row is measured against the t scale
   chi2        |d| <= 1e-3 absolute; FP32 leaves a floor near 4e-4 sqrt(chi2)
               (momentum and path-length roundings at ~2e-7 cm), so at most a
               1e-4 fraction of increments may exceed it, none beyond 3e-3
@@ -61,9 +64,37 @@ def unpack(out, chi2, st):
     return dict(par=par, cov=cov, chi2=chi2.double().cpu().numpy(), status=st.cpu().numpy())
 
 
+def f32(v):
+    """The float32 value the library receives for a configuration constant."""
+    return float(np.float32(v))
+
+
 def oracle_fit(seeds, hits_xyz, hits_valid, det, n_threads=0):
-    return O.fit(seeds.par, seeds.cov, seeds.charge, hits_xyz, hits_valid, det.radii[:hits_xyz.shape[0]], det.bz,
-                 det.sigma_xy, det.sigma_z, n_threads=n_threads)
+    """The oracle on the same inputs the library gets: float32 hits and seeds
+    and the float32-rounded field, smears and radii of kf_config."""
+    L = hits_xyz.shape[0]
+    return O.fit(seeds.par, seeds.cov, seeds.charge, hits_xyz, hits_valid, [f32(r) for r in det.radii[:L]],
+                 f32(det.bz), f32(det.sigma_xy), f32(det.sigma_z), n_threads=n_threads)
+
+
+def local_frame(par):
+    """[n, 6, 6] rotations to (n, t, z, px, py, pz) at the given positions."""
+    phi = np.arctan2(par[:, 1], par[:, 0])
+    c, s = np.cos(phi), np.sin(phi)
+    Q = np.zeros((len(par), 6, 6))
+    Q[:, 0, 0], Q[:, 0, 1] = c, s
+    Q[:, 1, 0], Q[:, 1, 1] = -s, c
+    Q[:, 2, 2] = Q[:, 3, 3] = Q[:, 4, 4] = Q[:, 5, 5] = 1.0
+    return Q
+
+
+def cov_error(g_cov, r_cov, r_par):
+    Q = local_frame(r_par)
+    gl = np.einsum("nij,njk,nlk->nil", Q, g_cov, Q)
+    rl = np.einsum("nij,njk,nlk->nil", Q, r_cov, Q)
+    sd = np.sqrt(np.abs(np.diagonal(rl, axis1=1, axis2=2))).copy()
+    sd[:, 0] = sd[:, 1]  # radial row: against the tangential scale
+    return np.abs(gl - rl) / (sd[:, :, None] * sd[:, None, :] + 1e-300)
 
 
 def compare(g, r, radius_scale, chi2_frac=CHI2_TOL_FRAC, label=""):
@@ -72,8 +103,7 @@ def compare(g, r, radius_scale, chi2_frac=CHI2_TOL_FRAC, label=""):
     pscale = np.concatenate([np.full((len(r["par"]), 3), radius_scale),
                              np.repeat(np.linalg.norm(r["par"][:, 3:], axis=1)[:, None], 3, axis=1)], axis=1)
     perr = np.abs(g["par"] - r["par"]) / pscale
-    sd = np.sqrt(np.abs(np.diagonal(r["cov"], axis1=1, axis2=2)))
-    cerr = np.abs(g["cov"] - r["cov"]) / (sd[:, :, None] * sd[:, None, :] + 1e-300)
+    cerr = cov_error(g["cov"], r["cov"], r["par"])
     both = (g["chi2"] >= 0) & (r["chi2"] >= 0)
     np.testing.assert_array_equal(g["chi2"] >= 0, r["chi2"] >= 0, err_msg=f"{label} update pattern")
     cer = np.abs(g["chi2"] - r["chi2"])[both]
