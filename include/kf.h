@@ -140,6 +140,37 @@ int kf_fit_f64(kf_ctx *ctx, const kf_tracks_f64 *seeds, const kf_track_hits *hit
 int kf_fit_host(kf_ctx *ctx, const kf_tracks *seeds, const kf_track_hits *hits, kf_tracks *out,
                 float *chi2, int32_t *status, void *stream);
 
+/* Largest batch (tracks) that kf_fit_noalloc accepts. */
+#define KF_NOALLOC_MAX_TRACKS 262144
+
+/*
+ * kf_fit for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this is a deployment variant of kf_fit.
+ *
+ * Who needs it: a caller whose device memory is planned up front and must not
+ * change afterwards -- e.g. an online trigger process that reserves all of the
+ * GPU at start-up and treats any later cudaMalloc as a fault, a host framework
+ * whose own caching allocator owns the device memory, or a plug-in that its
+ * host application forbids to allocate.  kf_fit, when `status` or
+ * `out->par_lo` is NULL, takes per-track scratch from the context and grows it
+ * with cudaMalloc on first use; this entry point takes that scratch from a
+ * fixed array in libkf's static device memory instead (KF_NOALLOC_MAX_TRACKS
+ * x 16 bytes = 4 MiB, held by every GPU that loads the library until the
+ * process exits) and performs no allocation or free of any kind.
+ *
+ * Arguments, layouts, results and errors are those of kf_fit, except:
+ *  - seeds->n > KF_NOALLOC_MAX_TRACKS returns KF_EINVAL (split the batch);
+ *  - the layer steps are issued as plain kernel launches on `stream`.
+ * The first call on a device looks up the array's device address (with the
+ * context's device current) and caches it; make that first call before any
+ * stream capture begins.  Every call shares the one array and leaves its
+ * contents behind; each call's first layer launch rewrites what the later
+ * launches read, so no clearing is needed.  Calls that overlap on the GPU
+ * (other streams, other host threads) race on the array: serialise them.
+ */
+int kf_fit_noalloc(kf_ctx *ctx, const kf_tracks *seeds, const kf_track_hits *hits, kf_tracks *out,
+                   float *chi2, int32_t *status, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libkf.so")
 KF_OK, KF_EINVAL, KF_ENOMEM, KF_EAGAIN, KF_ETIMEDOUT, KF_ECUDA, KF_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
 ST_NOT_REACHED, ST_NEWTON_FAIL, ST_TANGENT, ST_NOT_PD, ST_NO_HIT = 1, 2, 4, 8, 16
 ST_STOPPED = ST_NOT_REACHED | ST_NEWTON_FAIL | ST_TANGENT
+NOALLOC_MAX_TRACKS = 262144  # KF_NOALLOC_MAX_TRACKS
 
 
 class KfError(RuntimeError):
@@ -64,7 +65,7 @@ def lib() -> C.CDLL:
         L.kf_strerror.argtypes = [C.c_int]
         L.kf_strerror.restype = C.c_char_p
         L.kf_last_cuda_error.argtypes = [vp]
-        for name in ("kf_fit", "kf_fit_fused", "kf_fit_host"):
+        for name in ("kf_fit", "kf_fit_fused", "kf_fit_host", "kf_fit_noalloc"):
             getattr(L, name).argtypes = [vp, C.POINTER(kf_tracks), C.POINTER(kf_track_hits), C.POINTER(kf_tracks),
                                          vp, vp, vp]
         L.kf_fit_f64.argtypes = [vp, C.POINTER(kf_tracks_f64), C.POINTER(kf_track_hits), C.POINTER(kf_tracks_f64),
@@ -189,6 +190,14 @@ def kf_fit_host(ctx, seeds: Tracks, hits: TrackHits, out: Tracks, chi2=None, sta
     s, h, o = seeds.abi(), hits.abi(), out.abi()
     _check(lib().kf_fit_host(_h(ctx), C.byref(s), C.byref(h), C.byref(o), _ptr(chi2), _ptr(status),
                              _stream(stream)), "kf_fit_host", _h(ctx))
+
+
+def kf_fit_noalloc(ctx, seeds: Tracks, hits: TrackHits, out: Tracks, chi2=None, status=None, stream=None):
+    """kf_fit with its per-track scratch in libkf's static device memory: no
+    allocation (batches up to NOALLOC_MAX_TRACKS)."""
+    s, h, o = seeds.abi(), hits.abi(), out.abi()
+    _check(lib().kf_fit_noalloc(_h(ctx), C.byref(s), C.byref(h), C.byref(o), _ptr(chi2), _ptr(status),
+                                _stream(stream)), "kf_fit_noalloc", _h(ctx))
 
 
 def kf_fit_f64(ctx, seeds: Tracks, hits: TrackHits, out: Tracks, event_off, chi2=None, status=None, stream=None):
