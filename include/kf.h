@@ -140,6 +140,95 @@ int kf_fit_f64(kf_ctx *ctx, const kf_tracks_f64 *seeds, const kf_track_hits *hit
 int kf_fit_host(kf_ctx *ctx, const kf_tracks *seeds, const kf_track_hits *hits, kf_tracks *out,
                 float *chi2, int32_t *status, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Combinatorial track building (Sec. 3): spatial hit bins, chi2 windows and
+ * the clone engine.
+ */
+
+/* Hit bins per layer: directionally projective eta x phi bins (Sec. 3).
+ * eta = asinh(z / r) over [-KF_BIN_ETA_MAX, KF_BIN_ETA_MAX) in KF_BIN_ETA
+ * bins (points beyond go to the edge bins), phi = atan2(y, x) over [-pi, pi)
+ * in KF_BIN_PHI bins.  Bin b = ieta * KF_BIN_PHI + iphi. */
+#define KF_BIN_ETA 64
+#define KF_BIN_PHI 256
+#define KF_BIN_ETA_MAX 1.5f
+#define KF_NBINS (KF_BIN_ETA * KF_BIN_PHI)
+/* Largest number of hits in one (event, layer) segment. */
+#define KF_MAX_HITS_PER_SEGMENT ((1 << 21) - 2)
+
+/* Raw hits of a batch of events on the building layers (device pointers).
+ * Segment s = e * n_layers + l holds the hits of event e on build layer l
+ * (configuration layer first_layer + l): xyz[c][seg_off[s] .. seg_off[s+1]).
+ * A hit's id is its index within its segment. */
+typedef struct {
+    int32_t n_events;
+    int32_t n_layers;        /* building layers */
+    int32_t first_layer;     /* configuration index of build layer 0 */
+    int64_t n_hits;          /* seg_off[n_events * n_layers] */
+    const float *xyz;        /* [3][n_hits] */
+    const int64_t *seg_off;  /* [n_events * n_layers + 1], device */
+} kf_layer_hits;
+
+/* Binned hits (output of kf_bin_hits, input of kf_build; device pointers).
+ * Within each segment the hits are ordered by bin, and by id inside a bin. */
+typedef struct {
+    int32_t n_events;
+    int32_t n_layers;
+    int32_t first_layer;
+    int64_t n_hits;
+    float *hits;             /* [n_hits][4]: x, y, z, and the hit id (int32 bits) */
+    int32_t *bin_off;        /* [n_events * n_layers][KF_NBINS + 1]: bin starts within the segment */
+    const int64_t *seg_off;  /* [n_events * n_layers + 1], as in kf_layer_hits */
+} kf_layer_hit_bins;
+
+/* Sort every segment's hits into the eta x phi bins (Sec. 3: hits sorted in
+ * phi within eta bins per layer, phi bins for fast look-up): a counting sort,
+ * one thread block per segment.  `out->hits` and `out->bin_off` are
+ * caller-allocated with the sizes above; the other fields of `out` are set
+ * from `in`.  Segments must hold at most KF_MAX_HITS_PER_SEGMENT hits (not
+ * checked here: seg_off is device memory; kf_build ignores hits beyond it).
+ * Errors: KF_EINVAL (sizes, null pointers), KF_ECUDA. */
+int kf_bin_hits(kf_ctx *ctx, const kf_layer_hits *in, kf_layer_hit_bins *out, void *stream);
+
+/* Result of kf_build (device pointers, caller-allocated). */
+typedef struct {
+    kf_tracks best;          /* [n_seeds] best candidate: par, par_lo (may be NULL), cov;
+                                best.charge is not written (charge does not change) */
+    float *chi2_tot;         /* [n_seeds] sum of the chi2 increments of the kept hits */
+    int32_t *n_hits;         /* [n_seeds] hits added on the building layers */
+    int32_t *status;         /* [n_seeds] KF_ST_* bits of the best candidate */
+    int32_t *hit_idx;        /* [n_layers][n_seeds] hit id per build layer, -1 = none */
+    /* optional (NULL to skip): every candidate alive after the last layer,
+     * in rank order, candidate k of seed i at i * max_cands + k */
+    int32_t *n_cands;        /* [n_seeds] */
+    int32_t *cand_hit_idx;   /* [n_layers][n_seeds * max_cands], -1 = none or absent */
+    float *cand_chi2_tot;    /* [n_seeds * max_cands] */
+    int32_t *cand_n_hits;    /* [n_seeds * max_cands] */
+} kf_build_result;
+
+/*
+ * Combinatorial track building with the clone engine (Sec. 3).  For build
+ * layer l = 0 .. bins->n_layers-1, every live candidate of every seed is
+ * propagated to the layer radius; the chi2 increment of every hit in its
+ * window is computed; every hit with chi2 < cfg.chi2_cut becomes a child
+ * (parent, hit, chi2_tot, nHits) in a bookkeeping list, and a candidate with
+ * no such hit gives one child without a hit (propagated, not updated).  The
+ * children of a seed are ranked by (nHits desc, chi2_tot asc, parent rank
+ * asc, hit id asc) and only the best max_cands are copied and updated.
+ * max_cands = 1 is the best-hit approach.  The window is the set of bins
+ * that a hit with chi2 < cut can fall in (chi2 >= (u.r)^2 / (u^T S u) for
+ * every direction u), widened by one bin, so binning never changes the
+ * result.  Seeds are processed in (eta, phi) bin order within each event.
+ *
+ * seeds: [n_seeds] starting states at or inside the first build layer (the
+ * seeds' charge is read); seeds of event e are seed_off[e] .. seed_off[e+1]
+ * (device, [n_events + 1]); bins: from kf_bin_hits; max_cands: 1 .. 8.
+ * Scratch (candidates, histories) is taken from the context.
+ * Errors: KF_EINVAL, KF_ENOMEM (budget), KF_ECUDA.
+ */
+int kf_build(kf_ctx *ctx, const kf_tracks *seeds, const int64_t *seed_off, const kf_layer_hit_bins *bins,
+             int32_t max_cands, kf_build_result *out, void *stream);
+
 /* Largest batch (tracks) that kf_fit_noalloc accepts. */
 #define KF_NOALLOC_MAX_TRACKS 262144
 

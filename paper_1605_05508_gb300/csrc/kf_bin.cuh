@@ -1,0 +1,44 @@
+// kf_bin.cuh -- the eta x phi bin of a point, shared by the binning kernel
+// and the build's window look-up.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "../../include/kf.h"
+
+namespace kfi {
+
+constexpr float kPi = 3.14159265358979323846f;
+
+// phi bin of an angle in [-pi, pi], clamped to [0, KF_BIN_PHI - 1]
+__device__ __forceinline__ int phi_bin(float phi) {
+  int b = __float2int_rd((phi + kPi) * (float(KF_BIN_PHI) / (2.0f * kPi)));
+  return b < 0 ? 0 : (b >= KF_BIN_PHI ? KF_BIN_PHI - 1 : b);
+}
+
+// eta bin of eta, clamped to [0, KF_BIN_ETA - 1]
+__device__ __forceinline__ int eta_bin(float eta) {
+  int b = __float2int_rd((eta + KF_BIN_ETA_MAX) * (float(KF_BIN_ETA) / (2.0f * KF_BIN_ETA_MAX)));
+  return b < 0 ? 0 : (b >= KF_BIN_ETA ? KF_BIN_ETA - 1 : b);
+}
+
+// Bin of a point: eta = asinh(z / r), phi = atan2(y, x).
+__device__ __forceinline__ int bin_of(float x, float y, float z) {
+  const float r = sqrtf(x * x + y * y);
+  const float eta = r > 0.f ? asinhf(z / r) : (z >= 0.f ? 1e30f : -1e30f);
+  return eta_bin(eta) * KF_BIN_PHI + phi_bin(atan2f(y, x));
+}
+
+struct BinArgs {
+  const float* xyz;        // [3][stride]
+  int64_t stride;
+  const int64_t* seg_off;  // [n_seg + 1]
+  int32_t* bin_off;        // [n_seg][KF_NBINS + 1] or null
+  float4* out_pts;         // [total] or null
+  int32_t* out_id;         // [total] required: id within the segment, bin order
+  int32_t* out_seg;        // [total] or null
+};
+
+cudaError_t launch_bin_points(const BinArgs& a, int n_segments, cudaStream_t st);
+
+}  // namespace kfi

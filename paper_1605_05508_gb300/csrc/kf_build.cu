@@ -1,0 +1,523 @@
+// kf_build.cu -- combinatorial track building with the clone engine
+// (Cerati et al., Sec. 3).
+//
+// One launch per building layer.  An 8-lane group of a warp owns one seed;
+// lane k holds the seed's candidate of rank k (up to max_cands <= 8).  Per
+// layer each live lane
+//   1. propagates its candidate to the layer radius (kf::propagate),
+//   2. derives the hit window: chi2 >= (u.r)^2 / (u^T S u) for every unit u,
+//      so a hit with chi2 < cut lies within sqrt(cut u^T S u) of the
+//      prediction along the tangent, the normal and z; those bounds are
+//      mapped to eta x phi bins and widened by one bin,
+//   3. computes the chi2 increment of every hit in the window and keeps its
+//      best children in a sorted register list (the bookkeeping list of the
+//      clone engine: parent, hit, chi2_tot, nHits -- no state is copied),
+//   4. the group merges its lanes' lists by shuffles into the seed's best
+//      max_cands children, ranked by (nHits desc, chi2_tot asc, parent rank
+//      asc, hit id asc), encoded as one 64-bit key,
+//   5. only then are the winners materialised: lane k pulls the predicted
+//      state of its parent by shuffles and applies the Kalman update with its
+//      hit (a candidate with no compatible hit continues unchanged after
+//      propagation).
+// The hit history is kept as per-layer back-pointers (parent rank, hit id)
+// and resolved once at the end, instead of copying index arrays per child.
+#include "kf_bin.cuh"
+#include "kf_internal.h"
+#include "kf_math.cuh"
+
+namespace kfi {
+
+constexpr int kGroup = 8;           // lanes (candidate slots) per seed
+constexpr int kBuildThreads = 128;  // 16 seeds per block
+constexpr int kNewtonBuild = 12;
+constexpr int kParN = 9;  // x y z px py pz + low parts of x y z
+constexpr uint64_t kNoKey = ~0ull;
+constexpr unsigned kFull = 0xffffffffu;
+
+struct CandBuf {
+  float* par;      // [9][S8]
+  float* cov;      // [21][S8]
+  float* chi2;     // [S8] chi2_tot
+  int32_t* meta;   // [S8] nHits | status << 8
+  int8_t* ncand;   // [S]
+};
+
+struct BuildStepArgs {
+  CandBuf in, out;
+  int8_t* hist_parent;  // [S8] of this layer
+  int32_t* hist_hit;    // [S8] of this layer
+  const int32_t* seed_evt;  // [S] sorted position -> event
+  const int32_t* seed_perm; // [S] sorted position -> seed index
+  const int8_t* charge;     // [n_seeds]
+  const float4* hits;
+  const int32_t* bin_off;
+  const int64_t* seg_off;
+  int64_t S;
+  int layer, n_layers, max_cands;
+  float a_scale, R, v0, v1, v2, cut;
+};
+
+__device__ __forceinline__ uint64_t make_key(int nhits, float chi2tot, int parent, int hit_plus1) {
+  return (uint64_t(255 - nhits) << 56) | (uint64_t(__float_as_uint(chi2tot)) << 24) | (uint64_t(parent) << 21) |
+         uint64_t(hit_plus1);
+}
+
+// insert (key, pos) into the ascending list L/P (kGroup entries, last dropped)
+__device__ __forceinline__ void list_insert(uint64_t (&L)[kGroup], int (&P)[kGroup], uint64_t key, int pos) {
+#pragma unroll
+  for (int t = 0; t < kGroup; ++t) {
+    if (key < L[t]) {
+      const uint64_t tk = L[t];
+      const int tp = P[t];
+      L[t] = key;
+      P[t] = pos;
+      key = tk;
+      pos = tp;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBuildThreads) build_step_kernel(const BuildStepArgs A) {
+  const int lane = threadIdx.x & 31;
+  const int k = lane & (kGroup - 1);
+  const int gbase = lane & ~(kGroup - 1);
+  const int64_t j = (int64_t(blockIdx.x) * kBuildThreads + threadIdx.x) / kGroup;
+  const int64_t S8 = A.S * kGroup;
+  const bool seed_ok = j < A.S;
+  const int nc = seed_ok ? A.in.ncand[j] : 0;
+  const bool active = k < nc;
+  const int64_t slot = j * kGroup + k;
+
+  float p[6], lo[3], C[21];
+  float chi2tot = 0.f;
+  int nh = 0;
+  int32_t st = 0;
+  if (active) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) p[c] = A.in.par[c * S8 + slot];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) lo[c] = A.in.par[(6 + c) * S8 + slot];
+#pragma unroll
+    for (int c = 0; c < 21; ++c) C[c] = A.in.cov[c * S8 + slot];
+    chi2tot = A.in.chi2[slot];
+    const int32_t meta = A.in.meta[slot];
+    nh = meta & 0xff;
+    st = meta >> 8;
+  } else {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) p[c] = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) lo[c] = 0.f;
+#pragma unroll
+    for (int c = 0; c < 21; ++c) C[c] = 0.f;
+  }
+  const int e = seed_ok ? A.seed_evt[j] : 0;
+  const float a = A.a_scale * (seed_ok ? float(A.charge[A.seed_perm[j]]) : 1.f);
+  const int seg = e * A.n_layers + A.layer;
+  const int64_t h0 = seed_ok ? A.seg_off[seg] : 0;
+  bool stopped = (st & KF_ST_STOPPED) != 0;
+  if (active && !stopped) {
+    const int r = kf::propagate<float, kNewtonBuild, true>(p, lo, C, a, A.R);
+    if (r) {
+      st |= r;
+      stopped = true;
+    }
+  }
+
+  // ---- bookkeeping list of this parent's children (keys only)
+  uint64_t L[kGroup];
+  int P[kGroup];
+#pragma unroll
+  for (int t = 0; t < kGroup; ++t) {
+    L[t] = kNoKey;
+    P[t] = -1;
+  }
+  if (active) {
+    bool any = false;
+    if (!stopped) {
+      float Si[6];
+      kf::inverse_S(C, A.v0, A.v1, A.v2, Si);
+      const float X = p[0] + lo[0], Y = p[1] + lo[1], Z = p[2] + lo[2];
+      const float rr = sqrtf(X * X + Y * Y);
+      const float cph = X / rr, sph = Y / rr;
+      const float s00 = C[0] + A.v0, s10 = C[1], s11 = C[2] + A.v1, s22 = C[5] + A.v2;
+      const float Stt = sph * sph * s00 - 2.f * sph * cph * s10 + cph * cph * s11;
+      const float Snn = cph * cph * s00 + 2.f * sph * cph * s10 + sph * sph * s11;
+      const float wt = sqrtf(A.cut * fmaxf(Stt, 0.f));
+      const float wn = sqrtf(A.cut * fmaxf(Snn, 0.f));
+      const float wz = sqrtf(A.cut * fmaxf(s22, 0.f));
+      // phi bins: |dphi| <= atan(wt / (R - wn)), one bin of margin each side
+      int fa0 = 0, fa1 = KF_BIN_PHI - 1, fb0 = 0, fb1 = -1;
+      const float rin = A.R - wn;
+      if (rin > 0.5f * A.R && wt < rin) {
+        const float phic = atan2f(Y, X);
+        const float dphi = atanf(wt / rin);
+        const float scale = float(KF_BIN_PHI) / (2.0f * kPi);
+        const int f0 = __float2int_rd((phic - dphi + kPi) * scale) - 1;
+        const int f1 = __float2int_rd((phic + dphi + kPi) * scale) + 1;
+        if (f1 - f0 + 1 < KF_BIN_PHI) {
+          if (f0 < 0) {
+            fa0 = f0 + KF_BIN_PHI;
+            fa1 = KF_BIN_PHI - 1;
+            fb0 = 0;
+            fb1 = f1;
+          } else if (f1 >= KF_BIN_PHI) {
+            fa0 = f0;
+            fa1 = KF_BIN_PHI - 1;
+            fb0 = 0;
+            fb1 = f1 - KF_BIN_PHI;
+          } else {
+            fa0 = f0;
+            fa1 = f1;
+          }
+        }
+      }
+      // eta bins: z within Z +- wz and the hit radius within R +- wn
+      int e0 = 0, e1 = KF_BIN_ETA - 1;
+      const float rlo = A.R - wn, rhi = A.R + wn;
+      if (rlo > 0.f) {
+        const float zlo = Z - wz, zhi = Z + wz;
+        const float tmin = zlo >= 0.f ? zlo / rhi : zlo / rlo;
+        const float tmax = zhi >= 0.f ? zhi / rlo : zhi / rhi;
+        e0 = max(eta_bin(asinhf(tmin)) - 1, 0);
+        e1 = min(eta_bin(asinhf(tmax)) + 1, KF_BIN_ETA - 1);
+      }
+      const int32_t* boff = A.bin_off + int64_t(seg) * (KF_NBINS + 1);
+      const float4* hs = A.hits + h0;
+      for (int er = e0; er <= e1; ++er) {
+        for (int part = 0; part < 2; ++part) {
+          const int f0 = part == 0 ? fa0 : fb0, f1 = part == 0 ? fa1 : fb1;
+          if (f1 < f0) continue;
+          const int u0 = boff[er * KF_BIN_PHI + f0], u1 = boff[er * KF_BIN_PHI + f1 + 1];
+          for (int u = u0; u < u1; ++u) {
+            const float4 m = hs[u];
+            const float r0 = (m.x - p[0]) - lo[0], r1 = (m.y - p[1]) - lo[1], r2 = (m.z - p[2]) - lo[2];
+            const float c2 = kf::chi2_of(r0, r1, r2, Si);
+            if (c2 < A.cut) {
+              const int id = __float_as_int(m.w);
+              if (id < KF_MAX_HITS_PER_SEGMENT) {
+                list_insert(L, P, make_key(nh + 1, chi2tot + c2, k, id + 1), u);
+                any = true;
+              }
+            }
+          }
+        }
+      }
+    }
+    // no compatible hit (or a stopped candidate): one child without a hit
+    if (!any) list_insert(L, P, make_key(nh, chi2tot, k, 0), -1);
+  }
+
+  // ---- clone engine: merge the group's lists into the best max_cands
+  uint64_t my_key = kNoKey;
+  int my_parent = 0, my_pos = -1, n_win = 0;
+#pragma unroll
+  for (int r = 0; r < kGroup; ++r) {
+    if (r < A.max_cands) {  // uniform over the launch
+      uint64_t m = L[0];
+#pragma unroll
+      for (int d = kGroup / 2; d >= 1; d >>= 1) {
+        const uint64_t o = __shfl_xor_sync(kFull, m, d);
+        m = o < m ? o : m;
+      }
+      const bool mine = (L[0] == m) && (m != kNoKey);
+      const unsigned bal = (__ballot_sync(kFull, mine) >> gbase) & 0xffu;
+      const int wl = bal ? __ffs(bal) - 1 : 0;
+      const int wpos = __shfl_sync(kFull, P[0], gbase + wl);
+      if (mine) {
+#pragma unroll
+        for (int t = 0; t < kGroup - 1; ++t) {
+          L[t] = L[t + 1];
+          P[t] = P[t + 1];
+        }
+        L[kGroup - 1] = kNoKey;
+        P[kGroup - 1] = -1;
+      }
+      if (m != kNoKey) {
+        if (k == r) {
+          my_key = m;
+          my_parent = wl;
+          my_pos = wpos;
+        }
+        ++n_win;
+      }
+    }
+  }
+
+  // ---- materialise the winners: pull the parent's predicted state
+  const int src = gbase + my_parent;
+  float q[6], ql[3], qC[21];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) q[c] = __shfl_sync(kFull, p[c], src);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) ql[c] = __shfl_sync(kFull, lo[c], src);
+#pragma unroll
+  for (int c = 0; c < 21; ++c) qC[c] = __shfl_sync(kFull, C[c], src);
+  const int32_t pst = __shfl_sync(kFull, st, src);
+  const int pstopped = __shfl_sync(kFull, int(stopped), src);
+  if (seed_ok && k < n_win) {
+    const int nh_new = 255 - int(my_key >> 56);
+    const float chi2_new = __uint_as_float(uint32_t(my_key >> 24));
+    const int hit_plus1 = int(my_key & 0x1fffffu);
+    int32_t st_new = pst;
+    if (hit_plus1 > 0) {
+      const float4 m = A.hits[h0 + my_pos];
+      float Si[6];
+      kf::inverse_S(qC, A.v0, A.v1, A.v2, Si);
+      float r0, r1, r2;
+      kf::residual<float, true>(q, ql, m.x, m.y, m.z, r0, r1, r2);
+      kf::kalman_update<float, true>(q, ql, qC, Si, r0, r1, r2, A.v0, A.v1, A.v2);
+    } else if (!pstopped) {
+      st_new |= KF_ST_NO_HIT;
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) A.out.par[c * S8 + slot] = q[c];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) A.out.par[(6 + c) * S8 + slot] = ql[c];
+#pragma unroll
+    for (int c = 0; c < 21; ++c) A.out.cov[c * S8 + slot] = qC[c];
+    A.out.chi2[slot] = chi2_new;
+    A.out.meta[slot] = nh_new | (st_new << 8);
+    A.hist_parent[slot] = int8_t(my_parent);
+    A.hist_hit[slot] = hit_plus1 - 1;
+  }
+  if (seed_ok && k == 0) A.out.ncand[j] = int8_t(n_win);
+}
+
+struct BuildInitArgs {
+  CandBuf out;
+  const float* par;
+  const float* lo;
+  const float* cov;
+  const int32_t* seed_perm;
+  int64_t n;  // seeds (stride of the seed arrays)
+  int64_t S;
+};
+
+__global__ void build_init_kernel(const BuildInitArgs A) {
+  const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (j >= A.S) return;
+  const int64_t s = A.seed_perm[j];
+  const int64_t S8 = A.S * kGroup, slot = j * kGroup;
+  for (int c = 0; c < 6; ++c) A.out.par[c * S8 + slot] = A.par[c * A.n + s];
+  for (int c = 0; c < 3; ++c) A.out.par[(6 + c) * S8 + slot] = A.lo ? A.lo[c * A.n + s] : 0.f;
+  for (int c = 0; c < 21; ++c) A.out.cov[c * S8 + slot] = A.cov[c * A.n + s];
+  A.out.chi2[slot] = 0.f;
+  A.out.meta[slot] = 0;
+  A.out.ncand[j] = 1;
+}
+
+struct BuildFinalArgs {
+  CandBuf cand;
+  const int8_t* hist_parent;  // [L][S8]
+  const int32_t* hist_hit;    // [L][S8]
+  const int32_t* seed_perm;
+  int64_t S;
+  int n_layers, max_cands;
+  kf_build_result out;
+};
+
+template <typename T>
+__device__ bool pd5_final(const T p[6], const T C[21]) {
+  using kf::sym;
+  const T r = sqrtf(p[0] * p[0] + p[1] * p[1]);
+  const T t0 = r > T(0) ? -p[1] / r : T(0), t1 = r > T(0) ? p[0] / r : T(1);
+  T M[5][5];
+  M[0][0] = t0 * t0 * C[sym(0, 0)] + T(2) * t0 * t1 * C[sym(1, 0)] + t1 * t1 * C[sym(1, 1)];
+  for (int jj = 1; jj < 5; ++jj) {
+    M[jj][0] = t0 * C[sym(0, jj + 1)] + t1 * C[sym(1, jj + 1)];
+    for (int kk = 1; kk <= jj; ++kk) M[jj][kk] = C[sym(jj + 1, kk + 1)];
+  }
+  T Lc[5][5];
+  for (int jj = 0; jj < 5; ++jj) {
+    T d = M[jj][jj];
+    for (int kk = 0; kk < jj; ++kk) d -= Lc[jj][kk] * Lc[jj][kk];
+    if (!(d > T(0))) return false;
+    Lc[jj][jj] = sqrtf(d);
+    for (int ii = jj + 1; ii < 5; ++ii) {
+      T v = M[ii][jj];
+      for (int kk = 0; kk < jj; ++kk) v -= Lc[ii][kk] * Lc[jj][kk];
+      Lc[ii][jj] = v / Lc[jj][jj];
+    }
+  }
+  return true;
+}
+
+__global__ void build_final_kernel(const BuildFinalArgs A) {
+  const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (j >= A.S) return;
+  const int64_t seed = A.seed_perm[j];
+  const int64_t S8 = A.S * kGroup;
+  const int nc = A.cand.ncand[j];
+  const kf_build_result& o = A.out;
+  // best candidate: rank 0
+  {
+    const int64_t slot = j * kGroup;
+    float p[6], C[21];
+    for (int c = 0; c < 6; ++c) p[c] = A.cand.par[c * S8 + slot];
+    for (int c = 0; c < 21; ++c) C[c] = A.cand.cov[c * S8 + slot];
+    for (int c = 0; c < 6; ++c) o.best.par[c * A.S + seed] = p[c];
+    if (o.best.par_lo)
+      for (int c = 0; c < 3; ++c) o.best.par_lo[c * A.S + seed] = A.cand.par[(6 + c) * S8 + slot];
+    for (int c = 0; c < 21; ++c) o.best.cov[c * A.S + seed] = C[c];
+    const int32_t meta = A.cand.meta[slot];
+    float pf[6];
+    for (int c = 0; c < 3; ++c) pf[c] = p[c] + A.cand.par[(6 + c) * S8 + slot];
+    for (int c = 3; c < 6; ++c) pf[c] = p[c];
+    int32_t st = meta >> 8;
+    if (!pd5_final(pf, C)) st |= KF_ST_NOT_PD;
+    if (o.chi2_tot) o.chi2_tot[seed] = A.cand.chi2[slot];
+    if (o.n_hits) o.n_hits[seed] = meta & 0xff;
+    if (o.status) o.status[seed] = st;
+    if (o.hit_idx) {
+      int kk = 0;
+      for (int l = A.n_layers - 1; l >= 0; --l) {
+        const int64_t sl = int64_t(l) * S8 + j * kGroup + kk;
+        o.hit_idx[int64_t(l) * A.S + seed] = A.hist_hit[sl];
+        kk = A.hist_parent[sl];
+      }
+    }
+  }
+  if (o.n_cands) o.n_cands[seed] = nc;
+  for (int c = 0; c < A.max_cands; ++c) {
+    const int64_t oc = seed * A.max_cands + c;
+    const int64_t slot = j * kGroup + c;
+    if (o.cand_chi2_tot) o.cand_chi2_tot[oc] = c < nc ? A.cand.chi2[slot] : 0.f;
+    if (o.cand_n_hits) o.cand_n_hits[oc] = c < nc ? (A.cand.meta[slot] & 0xff) : 0;
+    if (o.cand_hit_idx) {
+      int kk = c;
+      for (int l = A.n_layers - 1; l >= 0; --l) {
+        int32_t h = -1;
+        if (c < nc) {
+          const int64_t sl = int64_t(l) * S8 + j * kGroup + kk;
+          h = A.hist_hit[sl];
+          kk = A.hist_parent[sl];
+        }
+        o.cand_hit_idx[int64_t(l) * A.S * A.max_cands + oc] = h;
+      }
+    }
+  }
+}
+
+__global__ void globalise_perm_kernel(int32_t* perm, const int32_t* evt, const int64_t* seed_off, int64_t S) {
+  const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (j < S) perm[j] = int32_t(seed_off[evt[j]] + perm[j]);
+}
+
+}  // namespace kfi
+
+using namespace kfi;
+
+namespace {
+size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
+}  // namespace
+
+extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed_off, const kf_layer_hit_bins* bins,
+                        int32_t max_cands, kf_build_result* out, void* stream) {
+  if (!ctx || !seeds || !seed_off || !bins || !out) return KF_EINVAL;
+  if (max_cands < 1 || max_cands > kGroup) return KF_EINVAL;
+  if (seeds->n < 0 || bins->n_events < 0 || bins->n_layers < 1 || bins->first_layer < 0 ||
+      bins->first_layer + bins->n_layers > ctx->cfg.n_layers)
+    return KF_EINVAL;
+  const int64_t S = seeds->n;
+  if (S == 0) return KF_OK;
+  if (!seeds->par || !seeds->cov || !seeds->charge || !bins->bin_off || !bins->seg_off) return KF_EINVAL;
+  if (bins->n_hits > 0 && !bins->hits) return KF_EINVAL;
+  if (!out->best.par || !out->best.cov) return KF_EINVAL;
+  if (bins->n_events == 0) return KF_EINVAL;
+  KF_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  const int L = bins->n_layers;
+  const int64_t S8 = S * kGroup;
+  // scratch layout
+  const size_t b_perm = al256(S * 4), b_evt = al256(S * 4), b_candf = al256(S8 * 4), b_nc = al256(S);
+  const size_t b_cand = (kParN + 21 + 2) * b_candf + b_nc;  // par, cov, chi2, meta + ncand
+  const size_t b_hp = al256(size_t(L) * S8), b_hh = al256(size_t(L) * S8 * 4);
+  const size_t total = b_perm + b_evt + 2 * b_cand + b_hp + b_hh;
+  int rc = scratch_reserve(ctx, ctx->s_build, total);
+  if (rc) return rc;
+  char* base = static_cast<char*>(ctx->s_build.ptr);
+  int32_t* perm = reinterpret_cast<int32_t*>(base);
+  int32_t* evt = reinterpret_cast<int32_t*>(base + b_perm);
+  auto cand_at = [&](char* q) {
+    CandBuf c;
+    c.par = reinterpret_cast<float*>(q);
+    c.cov = reinterpret_cast<float*>(q + kParN * b_candf);
+    c.chi2 = reinterpret_cast<float*>(q + (kParN + 21) * b_candf);
+    c.meta = reinterpret_cast<int32_t*>(q + (kParN + 22) * b_candf);
+    c.ncand = reinterpret_cast<int8_t*>(q + (kParN + 23) * b_candf);
+    return c;
+  };
+  CandBuf bufA = cand_at(base + b_perm + b_evt);
+  CandBuf bufB = cand_at(base + b_perm + b_evt + b_cand);
+  int8_t* hist_parent = reinterpret_cast<int8_t*>(base + b_perm + b_evt + 2 * b_cand);
+  int32_t* hist_hit = reinterpret_cast<int32_t*>(base + b_perm + b_evt + 2 * b_cand + b_hp);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+  // seeds in (eta, phi) bin order within each event
+  BinArgs ba;
+  ba.xyz = seeds->par;
+  ba.stride = S;
+  ba.seg_off = seed_off;
+  ba.bin_off = nullptr;
+  ba.out_pts = nullptr;
+  ba.out_id = perm;
+  ba.out_seg = evt;
+  KF_CUDA_TRY(ctx, launch_bin_points(ba, bins->n_events, s));
+  // perm holds ids within each event: make them global seed indices
+  // (the seeds of event e start at seed_off[e])
+  globalise_perm_kernel<<<int((S + 255) / 256), 256, 0, s>>>(perm, evt, seed_off, S);
+  KF_CUDA_TRY(ctx, cudaGetLastError());
+  {
+    BuildInitArgs ia;
+    ia.out = bufA;
+    ia.par = seeds->par;
+    ia.lo = seeds->par_lo;
+    ia.cov = seeds->cov;
+    ia.seed_perm = perm;
+    ia.n = S;
+    ia.S = S;
+    build_init_kernel<<<int((S + 255) / 256), 256, 0, s>>>(ia);
+    KF_CUDA_TRY(ctx, cudaGetLastError());
+  }
+  const float v0 = ctx->cfg.sigma_xy_cm * ctx->cfg.sigma_xy_cm;
+  const float v2 = ctx->cfg.sigma_z_cm * ctx->cfg.sigma_z_cm;
+  const int grid = int((S8 + kBuildThreads - 1) / kBuildThreads);
+  for (int l = 0; l < L; ++l) {
+    BuildStepArgs a;
+    a.in = (l % 2 == 0) ? bufA : bufB;
+    a.out = (l % 2 == 0) ? bufB : bufA;
+    a.hist_parent = hist_parent + int64_t(l) * S8;
+    a.hist_hit = hist_hit + int64_t(l) * S8;
+    a.seed_evt = evt;
+    a.seed_perm = perm;
+    a.charge = seeds->charge;
+    a.hits = reinterpret_cast<const float4*>(bins->hits);
+    a.bin_off = bins->bin_off;
+    a.seg_off = bins->seg_off;
+    a.S = S;
+    a.layer = l;
+    a.n_layers = L;
+    a.max_cands = max_cands;
+    a.a_scale = float(kCLight * double(ctx->cfg.bz_tesla));
+    a.R = ctx->radius[bins->first_layer + l];
+    a.v0 = v0;
+    a.v1 = v0;
+    a.v2 = v2;
+    a.cut = ctx->cfg.chi2_cut;
+    build_step_kernel<<<grid, kBuildThreads, 0, s>>>(a);
+    KF_CUDA_TRY(ctx, cudaGetLastError());
+  }
+  BuildFinalArgs fa;
+  fa.cand = (L % 2 == 0) ? bufA : bufB;
+  fa.hist_parent = hist_parent;
+  fa.hist_hit = hist_hit;
+  fa.seed_perm = perm;
+  fa.S = S;
+  fa.n_layers = L;
+  fa.max_cands = max_cands;
+  fa.out = *out;
+  build_final_kernel<<<int((S + 127) / 128), 128, 0, s>>>(fa);
+  KF_CUDA_TRY(ctx, cudaGetLastError());
+  return KF_OK;
+}
+

@@ -129,6 +129,8 @@ void kf_destroy(kf_ctx* ctx) {
   scratch_free(ctx, ctx->s_lo);
   scratch_free(ctx, ctx->s_host_in);
   scratch_free(ctx, ctx->s_host_out);
+  scratch_free(ctx, ctx->s_bin_id);
+  scratch_free(ctx, ctx->s_build);
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   delete ctx;
 }

@@ -48,6 +48,25 @@ class kf_track_hits(C.Structure):
     _fields_ = [("n_tracks", C.c_int64), ("n_layers", C.c_int32), ("xyz", C.c_void_p), ("valid", C.c_void_p)]
 
 
+class kf_layer_hits(C.Structure):
+    _fields_ = [("n_events", C.c_int32), ("n_layers", C.c_int32), ("first_layer", C.c_int32), ("n_hits", C.c_int64),
+                ("xyz", C.c_void_p), ("seg_off", C.c_void_p)]
+
+
+class kf_layer_hit_bins(C.Structure):
+    _fields_ = [("n_events", C.c_int32), ("n_layers", C.c_int32), ("first_layer", C.c_int32), ("n_hits", C.c_int64),
+                ("hits", C.c_void_p), ("bin_off", C.c_void_p), ("seg_off", C.c_void_p)]
+
+
+class kf_build_result(C.Structure):
+    _fields_ = [("best", kf_tracks), ("chi2_tot", C.c_void_p), ("n_hits", C.c_void_p), ("status", C.c_void_p),
+                ("hit_idx", C.c_void_p), ("n_cands", C.c_void_p), ("cand_hit_idx", C.c_void_p),
+                ("cand_chi2_tot", C.c_void_p), ("cand_n_hits", C.c_void_p)]
+
+
+BIN_ETA, BIN_PHI, BIN_ETA_MAX = 64, 256, 1.5  # KF_BIN_ETA, KF_BIN_PHI, KF_BIN_ETA_MAX
+NBINS = BIN_ETA * BIN_PHI
+
 _lib = None
 
 
@@ -70,6 +89,9 @@ def lib() -> C.CDLL:
                                          vp, vp, vp]
         L.kf_fit_f64.argtypes = [vp, C.POINTER(kf_tracks_f64), C.POINTER(kf_track_hits), C.POINTER(kf_tracks_f64),
                                  vp, vp, C.POINTER(i64), i32, vp]
+        L.kf_bin_hits.argtypes = [vp, C.POINTER(kf_layer_hits), C.POINTER(kf_layer_hit_bins), vp]
+        L.kf_build.argtypes = [vp, C.POINTER(kf_tracks), vp, C.POINTER(kf_layer_hit_bins), i32,
+                               C.POINTER(kf_build_result), vp]
         _lib = L
     return _lib
 
@@ -206,3 +228,65 @@ def kf_fit_f64(ctx, seeds: Tracks, hits: TrackHits, out: Tracks, event_off, chi2
     s, h, o = seeds.abi_f64(), hits.abi(), out.abi_f64()
     _check(lib().kf_fit_f64(_h(ctx), C.byref(s), C.byref(h), C.byref(o), _ptr(chi2), _ptr(status), offs,
                             len(event_off) - 1, _stream(stream)), "kf_fit_f64", _h(ctx))
+
+
+@dataclass
+class LayerHits:
+    """Raw hits of the building layers: xyz [3, n_hits] float32, seg_off int64
+    [n_events * n_layers + 1] (device), segment e * n_layers + l = event e on
+    build layer l (configuration layer first_layer + l)."""
+    xyz: object
+    seg_off: object
+    n_events: int
+    n_layers: int
+    first_layer: int
+
+    def abi(self) -> kf_layer_hits:
+        return kf_layer_hits(self.n_events, self.n_layers, self.first_layer, int(self.xyz.shape[1]), _ptr(self.xyz),
+                             _ptr(self.seg_off))
+
+
+@dataclass
+class HitBins:
+    """hits [n_hits, 4] float32 (x, y, z, id bits), bin_off [n_seg, NBINS + 1] int32."""
+    hits: object
+    bin_off: object
+    seg_off: object = None
+    n_events: int = 0
+    n_layers: int = 0
+    first_layer: int = 0
+
+    def abi(self) -> kf_layer_hit_bins:
+        return kf_layer_hit_bins(self.n_events, self.n_layers, self.first_layer, int(self.hits.shape[0]),
+                                 _ptr(self.hits), _ptr(self.bin_off), _ptr(self.seg_off))
+
+
+@dataclass
+class BuildResult:
+    best: Tracks
+    chi2_tot: object
+    n_hits: object
+    status: object
+    hit_idx: object
+    n_cands: object = None
+    cand_hit_idx: object = None
+    cand_chi2_tot: object = None
+    cand_n_hits: object = None
+
+    def abi(self) -> kf_build_result:
+        return kf_build_result(self.best.abi(), _ptr(self.chi2_tot), _ptr(self.n_hits), _ptr(self.status),
+                               _ptr(self.hit_idx), _ptr(self.n_cands), _ptr(self.cand_hit_idx),
+                               _ptr(self.cand_chi2_tot), _ptr(self.cand_n_hits))
+
+
+def kf_bin_hits(ctx, hits: LayerHits, bins: HitBins, stream=None):
+    i, o = hits.abi(), bins.abi()
+    _check(lib().kf_bin_hits(_h(ctx), C.byref(i), C.byref(o), _stream(stream)), "kf_bin_hits", _h(ctx))
+    bins.seg_off, bins.n_events, bins.n_layers, bins.first_layer = hits.seg_off, hits.n_events, hits.n_layers, \
+        hits.first_layer
+
+
+def kf_build(ctx, seeds: Tracks, seed_off, bins: HitBins, max_cands: int, out: BuildResult, stream=None):
+    s, b, o = seeds.abi(), bins.abi(), out.abi()
+    _check(lib().kf_build(_h(ctx), C.byref(s), _ptr(seed_off), C.byref(b), int(max_cands), C.byref(o),
+                          _stream(stream)), "kf_build", _h(ctx))

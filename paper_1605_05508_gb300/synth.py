@@ -98,7 +98,7 @@ class Seeds:
 
 
 def draw_particles(rng: np.random.Generator, n: int, pt_range=(0.5, 10.0),
-                   eta_max: float = 1.0, pt_mix=None) -> Particles:
+                   eta_max: float = 1.0, pt_mix=None, phi_range=(0.0, 2.0 * np.pi)) -> Particles:
     """Draw n particles. `pt_mix` = list of (fraction, (lo, hi)) overrides pt_range."""
     q = rng.choice(np.array([-1, 1], dtype=np.int8), size=n)
     if pt_mix is None:
@@ -115,7 +115,7 @@ def draw_particles(rng: np.random.Generator, n: int, pt_range=(0.5, 10.0),
         if sel.any():
             lo, hi = pt_mix[-1][1]
             pt[sel] = rng.uniform(lo, hi, size=int(sel.sum()))
-    phi = rng.uniform(0.0, 2.0 * np.pi, size=n)
+    phi = rng.uniform(phi_range[0], phi_range[1], size=n)
     eta = rng.uniform(-eta_max, eta_max, size=n)
     vtx = np.stack([rng.normal(0.0, 0.01, n), rng.normal(0.0, 0.01, n),
                     rng.normal(0.0, 1.0, n)], axis=1)
@@ -332,7 +332,8 @@ def make_fit_batch(seed: int, n_tracks: int, det: Detector | None = None,
 class BuildBatch:
     """Inputs of a batched build over `n_events` events.
 
-    seeds: 3-hit seeds of every event's tracks (event-major order);
+    seeds: vertex seeds of every event's tracks (event-major order), to be
+      fitted over the seeding layers before building;
     seed_event: int32 [n_seeds] event of each seed;
     fit_hits: per-track hits on the seeding layers (for the seed fit);
     layer_xyz: float32 [3, n_hits_total] raw hits of every (event, build layer)
@@ -357,7 +358,11 @@ class BuildBatch:
 
 def make_build_batch(seed: int, n_events: int, tracks_per_event: int,
                      det: Detector | None = None, noise_factor: float = 3.0,
-                     n_seed_layers: int = 3, pt_range=(0.5, 10.0)) -> BuildBatch:
+                     n_seed_layers: int = 3, pt_range=(0.5, 10.0), noise_near: int = 0,
+                     noise_near_sigma: float = 0.0, phi_range=(0.0, 2.0 * np.pi)) -> BuildBatch:
+    """`noise_near` extra hits per track hit, displaced by N(0, noise_near_sigma)
+    in x, y and N(0, 10 noise_near_sigma) in z (dense, branching-heavy
+    tiny cases)."""
     det = det or barrel()
     rng = np.random.default_rng(seed)
     L = det.n_layers
@@ -366,11 +371,11 @@ def make_build_batch(seed: int, n_events: int, tracks_per_event: int,
     segs, truths, offs = [], [], [0]
     all_seeds, all_hits, ev_of_seed, parts_list = [], [], [], []
     for e in range(n_events):
-        parts = draw_particles(rng, tracks_per_event, pt_range=pt_range)
+        parts = draw_particles(rng, tracks_per_event, pt_range=pt_range, phi_range=phi_range)
         hits = simulate_hits(rng, parts, det)
         parts_list.append(parts)
         all_hits.append(hits)
-        all_seeds.append(seeds_from_hits(hits, det.bz, seed_layers))
+        all_seeds.append(seeds_truth_smeared(rng, parts))
         ev_of_seed.append(np.full(tracks_per_event, e, dtype=np.int32))
         n_noise = int(round(noise_factor * tracks_per_event))
         for li in build_layers:
@@ -384,8 +389,15 @@ def make_build_batch(seed: int, n_events: int, tracks_per_event: int,
             nz = np.stack([R * np.cos(phi) + rng.normal(0.0, det.sigma_xy, n_noise),
                            R * np.sin(phi) + rng.normal(0.0, det.sigma_xy, n_noise),
                            zz + rng.normal(0.0, det.sigma_z, n_noise)]).astype(np.float32)
-            xyz = np.concatenate([trk, nz], axis=1)
-            tt = np.concatenate([tid, np.full(n_noise, -1, dtype=np.int32)])
+            parts_xyz, parts_t = [trk, nz], [tid, np.full(n_noise, -1, dtype=np.int32)]
+            for _ in range(noise_near):
+                d = np.stack([rng.normal(0.0, noise_near_sigma, trk.shape[1]),
+                              rng.normal(0.0, noise_near_sigma, trk.shape[1]),
+                              rng.normal(0.0, 10 * noise_near_sigma, trk.shape[1])])
+                parts_xyz.append((trk + d).astype(np.float32))
+                parts_t.append(np.full(trk.shape[1], -1, dtype=np.int32))
+            xyz = np.concatenate(parts_xyz, axis=1)
+            tt = np.concatenate(parts_t)
             perm = rng.permutation(xyz.shape[1])
             segs.append(xyz[:, perm])
             truths.append(tt[perm])

@@ -1,0 +1,164 @@
+"""GPU parity of hit binning (kf_bin_hits) and the clone-engine build
+(kf_build) against the FP64 oracle, which scans every hit of a layer (no
+bins): equal results also show that the chi2 window never drops a hit."""
+import numpy as np
+import pytest
+
+from buildutil import classify, gpu_build, oracle_build
+from fitutil import to_dev
+from paper_1605_05508_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+
+def _ref_bins(x, y, z):
+    """Bins from FP64 eta, phi; and the distance to the nearest bin edge."""
+    r = np.hypot(x, y)
+    eta = np.arcsinh(z / r)
+    phi = np.arctan2(y, x)
+    fe = (eta + 1.5) * 64 / 3.0
+    fp = (phi + np.pi) * 256 / (2 * np.pi)
+    ie = np.clip(np.floor(fe), 0, 63).astype(int)
+    ip = np.clip(np.floor(fp), 0, 255).astype(int)
+    edge = np.minimum(np.abs(fe - np.round(fe)), np.abs(fp - np.round(fp)))
+    return ie * 256 + ip, edge
+
+
+def test_bin_hits_is_a_deterministic_counting_sort(cuda_ctx_factory):
+    import torch
+    from paper_1605_05508_gb300 import kf
+    det = S.barrel()
+    ctx = cuda_ctx_factory(det.radii)
+    b = S.make_build_batch(5, 3, 700)
+    E, Lb = b.n_events, len(b.build_layers)
+    lh = kf.LayerHits(to_dev(b.layer_xyz), to_dev(b.layer_off), E, Lb, b.build_layers[0])
+    nh = b.layer_xyz.shape[1]
+    bins = kf.HitBins(torch.empty((nh, 4), device="cuda"),
+                      torch.empty((E * Lb, kf.NBINS + 1), dtype=torch.int32, device="cuda"))
+    kf.kf_bin_hits(ctx, lh, bins)
+    torch.cuda.synchronize()
+    hits = bins.hits.cpu().numpy()
+    ids = hits[:, 3].view(np.int32)
+    boff = bins.bin_off.cpu().numpy()
+    for s in range(E * Lb):
+        lo, hi = b.layer_off[s], b.layer_off[s + 1]
+        n = hi - lo
+        sid = ids[lo:hi]
+        assert np.array_equal(np.sort(sid), np.arange(n))  # a permutation
+        np.testing.assert_array_equal(hits[lo:hi, :3], b.layer_xyz[:, lo + sid].T)
+        off = boff[s]
+        assert off[0] == 0 and off[-1] == n and np.all(np.diff(off) >= 0)
+        assigned = np.repeat(np.arange(kf.NBINS), np.diff(off))
+        ref, edge = _ref_bins(*b.layer_xyz[:, lo + sid].astype(np.float64))
+        ok = (assigned == ref) | (edge < 1e-4)
+        assert ok.all(), np.nonzero(~ok)
+        for bb in np.nonzero(np.diff(off) > 1)[0]:  # ids ascending inside a bin
+            assert np.all(np.diff(sid[off[bb]:off[bb + 1]]) > 0)
+    # run to run identical
+    again = kf.HitBins(torch.empty_like(bins.hits), torch.empty_like(bins.bin_off))
+    kf.kf_bin_hits(ctx, lh, again)
+    torch.cuda.synchronize()
+    assert torch.equal(again.hits, bins.hits) and torch.equal(again.bin_off, bins.bin_off)
+
+
+def _check_build(batch, g, r, max_bad=0, tie_frac=0.01, label=""):
+    same, ties, bad = classify(batch, g, r)
+    n = len(r["n_cands"])
+    print(f"{label}: {same}/{n} identical best paths, {len(ties)} near ties, {len(bad)} other")
+    assert len(bad) <= max_bad, bad[:5]
+    assert len(ties) <= max(2, tie_frac * n), ties[:5]
+    agree = np.array([np.array_equal(g["hits"][i], r["hits"][i, 0]) for i in range(n)])
+    # on identical paths: hit count, chi2_tot and the state agree
+    assert np.array_equal(g["nhits"][agree], r["nhits"][agree, 0])
+    assert np.all(np.abs(g["chi2"][agree] - r["chi2"][agree, 0]) <= 1e-3 * np.maximum(1, r["nhits"][agree, 0]))
+    pscale = np.concatenate([np.full((agree.sum(), 3), 40.0),
+                             np.repeat(np.linalg.norm(r["par"][agree, 0, 3:], axis=1)[:, None], 3, axis=1)], axis=1)
+    assert np.all(np.abs(g["par"][agree] - r["par"][agree, 0]) <= 1e-4 * pscale)
+    return agree
+
+
+@pytest.mark.parametrize("max_cands", [6, 1])
+def test_build_small_batch_matches_oracle(cuda_ctx_factory, max_cands):
+    det = S.barrel()
+    ctx = cuda_ctx_factory(det.radii, max_cands=8)
+    batch = S.make_build_batch(1607 + max_cands, 3, 400)
+    g = gpu_build(ctx, batch, max_cands)
+    r = oracle_build(batch, max_cands)
+    assert np.all(g["fit_status"] == 0)
+    agree = _check_build(batch, g, r, label=f"N={max_cands}")
+    # every kept candidate agrees where the best path does
+    for i in np.nonzero(agree)[0][:200]:
+        nc = r["n_cands"][i]
+        if g["n_cands"][i] == nc and np.array_equal(g["cand_hits"][i, :nc], r["hits"][i, :nc]):
+            np.testing.assert_array_equal(g["cand_nhits"][i, :nc], r["nhits"][i, :nc])
+
+
+def test_build_dense_branching_tiny(cuda_ctx_factory):
+    """Every hit has two near neighbours: heavy branching, N = 6 truncation."""
+    det = S.barrel()
+    ctx = cuda_ctx_factory(det.radii)
+    batch = S.make_build_batch(77, 2, 60, noise_factor=0.5, noise_near=2, noise_near_sigma=0.012)
+    g = gpu_build(ctx, batch, 6)
+    r = oracle_build(batch, 6)
+    _check_build(batch, g, r, tie_frac=0.05, label="dense")
+
+
+def test_build_phi_wraparound_and_eta_edges(cuda_ctx_factory):
+    """All tracks within 0.06 rad of phi = +-pi (every window is split across
+    the wrap of the phi bins), |eta| up to 1 (edge eta bins)."""
+    det = S.barrel()
+    ctx = cuda_ctx_factory(det.radii)
+    batch = S.make_build_batch(88, 2, 300, phi_range=(np.pi - 0.06, np.pi + 0.06))
+    g = gpu_build(ctx, batch, 6)
+    r = oracle_build(batch, 6)
+    _check_build(batch, g, r, label="wrap")
+
+
+def test_build_config3_full_size_sampled(cuda_ctx_factory):
+    """50 events x 5000 seeds, 15000 noise + 5000 track hits per layer, N = 6,
+    building on layers 4-10; a sample of seeds is checked against the
+    oracle's all-hits build."""
+    det = S.barrel()
+    ctx = cuda_ctx_factory(det.radii)
+    batch = S.make_build_batch(1608, 50, 5000)
+    g = gpu_build(ctx, batch, 6, want_cands=False)
+    rng = np.random.default_rng(1)
+    idx = np.sort(rng.choice(50 * 5000, 240, replace=False))
+    r = oracle_build(batch, 6, idx=idx)
+    same, ties, bad = classify(batch, g, r, idx=idx)
+    print(f"config3 sample: {same}/{len(idx)} identical, {len(ties)} near ties, {len(bad)} other")
+    assert not bad, bad[:3]
+    assert len(ties) <= max(2, 0.02 * len(idx))
+    assert np.all(g["nhits"] >= 0) and np.all(g["nhits"] <= 7)
+    # efficiency sanity: most seeds pick up most of the 7 layers
+    assert np.mean(g["nhits"]) > 6.0
+
+
+def test_build_edge_cases(cuda_ctx_factory):
+    import torch
+    from paper_1605_05508_gb300 import kf
+    det = S.barrel()
+    ctx = cuda_ctx_factory(det.radii)
+    # an event whose layers hold no hit at all: every candidate continues without hits
+    batch = S.make_build_batch(99, 2, 50)
+    Lb = len(batch.build_layers)
+    keep = np.ones(batch.layer_xyz.shape[1], dtype=bool)
+    offs = batch.layer_off.copy()
+    for l in range(Lb):  # empty event 1
+        keep[offs[Lb + l]:offs[Lb + l + 1]] = False
+    new_counts = [0 if s >= Lb else offs[s + 1] - offs[s] for s in range(2 * Lb)]
+    batch.layer_xyz = np.ascontiguousarray(batch.layer_xyz[:, keep])
+    batch.layer_off = np.concatenate([[0], np.cumsum(new_counts)]).astype(np.int64)
+    g = gpu_build(ctx, batch, 6)
+    r = oracle_build(batch, 6)
+    ev1 = batch.seed_event == 1
+    assert np.all(g["nhits"][ev1] == 0) and np.all(g["hits"][ev1] == -1)
+    assert np.all(g["status"][ev1] & kf.ST_NO_HIT)
+    _check_build(batch, g, r, label="empty event")
+    # zero seeds: a no-op
+    z = kf.Tracks(torch.empty((6, 0), device="cuda"), torch.empty((21, 0), device="cuda"),
+                  torch.empty(0, dtype=torch.int8, device="cuda"))
+    out = kf.BuildResult(best=z, chi2_tot=None, n_hits=None, status=None, hit_idx=None)
+    kf.kf_build(ctx, z, to_dev(np.zeros(1, np.int64)), g["bins"], 6, out)
+    with pytest.raises(kf.KfError):
+        kf.kf_build(ctx, z, to_dev(np.zeros(1, np.int64)), g["bins"], 9, out)  # max_cands > 8
