@@ -20,8 +20,11 @@ __global__ void __launch_bounds__(kBinThreads) bin_points_kernel(const BinArgs A
   int* cnt = smem;               // [KF_NBINS] counts, then cursors
   int* warp_tot = smem + KF_NBINS;  // [32]
   const int seg = blockIdx.x;
-  const int64_t p0 = A.seg_off[seg];
-  const int n = int(A.seg_off[seg + 1] - p0);
+  // offsets are clamped to the point arrays, so malformed ones cannot index past them
+  int64_t p0 = A.seg_off[seg], p1 = A.seg_off[seg + 1];
+  p0 = p0 < 0 ? 0 : (p0 > A.stride ? A.stride : p0);
+  p1 = p1 < p0 ? p0 : (p1 > A.stride ? A.stride : p1);
+  const int n = int(p1 - p0);
   const int tid = threadIdx.x;
   for (int b = tid; b < KF_NBINS; b += kBinThreads) cnt[b] = 0;
   __syncthreads();

@@ -149,9 +149,9 @@ __global__ void __launch_bounds__(kBuildThreads) build_step_kernel(const BuildSt
       // phi bins: |dphi| <= atan(wt / (R - wn)), one bin of margin each side
       int fa0 = 0, fa1 = KF_BIN_PHI - 1, fb0 = 0, fb1 = -1;
       const float rin = A.R - wn;
-      if (rin > 0.5f * A.R && wt < rin) {
-        const float phic = atan2f(Y, X);
-        const float dphi = atanf(wt / rin);
+      const float phic = atan2f(Y, X);
+      const float dphi = (rin > 0.5f * A.R && wt < rin) ? atanf(wt / rin) : 10.f;
+      if (dphi < 1.f && phic >= -kPi && phic <= kPi) {  // also false for NaN
         const float scale = float(KF_BIN_PHI) / (2.0f * kPi);
         const int f0 = __float2int_rd((phic - dphi + kPi) * scale) - 1;
         const int f1 = __float2int_rd((phic + dphi + kPi) * scale) + 1;
