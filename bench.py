@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--layers", type=int, default=10)
     ap.add_argument("--seed", type=int, default=1606)
     ap.add_argument("--no-extras", action="store_true", help="headline only (no e2e/f64/fused/cpu legs)")
+    ap.add_argument("--no-build", action="store_true", help="skip the combinatorial-build leg")
+    ap.add_argument("--build-events", type=int, default=50)
+    ap.add_argument("--build-seeds", type=int, default=5000)
     return ap.parse_args()
 
 
@@ -269,6 +272,10 @@ def run_ours(a):
     if not a.no_extras:
         line.update(extras(a, ctx, kf, torch, dev, det, ev, seeds, hits, out, chi2, status, stream, value,
                            ms_per_step, rank, world, dist))
+    if not a.no_build:
+        del seeds, hits, out, chi2, status
+        torch.cuda.empty_cache()
+        line["build"] = build_leg(a, kf, torch, dev, stream, rank, world, dist)
     ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -343,6 +350,94 @@ def extras(a, ctx, kf, torch, dev, det, ev, seeds, hits, out, chi2, status, stre
         res["cpu_baseline"] = {"value": m * L / dtc, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": f"first {m} tracks ({m // a.tracks} events) x {L} layers, FP64 oracle, "
                                          f"{cores} OpenMP threads, {dtc:.2f} s wall"}
+    return res
+
+
+def build_leg(a, kf, torch, dev, stream, rank, world, dist):
+    """Combinatorial build (clone engine, N = 6; and best-hit N = 1) on
+    `build_events` events x `build_seeds` seeds with 3x noise hits per layer,
+    64 x 256 bins, chi2 < 30; a step = seed fit over layers 1-3 + hit binning
+    + the build over layers 4-10 + final selection."""
+    from paper_1605_05508_gb300 import synth as S
+    E, T = a.build_events, a.build_seeds
+    batch = S.make_build_batch(a.seed + 2 + 1000 * rank, E, T)
+    det = batch.det
+    n = batch.seeds.par.shape[1]
+    Lb = len(batch.build_layers)
+    D = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    ctx = kf.Context(det.radii, det.bz, det.sigma_xy, det.sigma_z, device=dev.index)
+    s = kf.Tracks(D(batch.seeds.par), D(batch.seeds.cov), D(batch.seeds.charge))
+    fo = kf.Tracks(torch.empty((6, n), device=dev), torch.empty((21, n), device=dev), s.charge,
+                   torch.empty((3, n), device=dev))
+    fst = torch.empty(n, dtype=torch.int32, device=dev)
+    fh = kf.TrackHits(D(batch.fit_hits.xyz), D(batch.fit_hits.valid))
+    lh = kf.LayerHits(D(batch.layer_xyz), D(batch.layer_off), E, Lb, batch.build_layers[0])
+    nh = batch.layer_xyz.shape[1]
+    bins = kf.HitBins(torch.empty((nh, 4), device=dev), torch.empty((E * Lb, kf.NBINS + 1), dtype=torch.int32,
+                                                                     device=dev))
+    seed_off = D(np.searchsorted(batch.seed_event, np.arange(E + 1)).astype(np.int64))
+    i32 = dict(dtype=torch.int32, device=dev)
+    out = kf.BuildResult(best=kf.Tracks(torch.empty((6, n), device=dev), torch.empty((21, n), device=dev), s.charge,
+                                        torch.empty((3, n), device=dev)),
+                         chi2_tot=torch.empty(n, device=dev), n_hits=torch.empty(n, **i32),
+                         status=torch.empty(n, **i32), hit_idx=torch.empty((Lb, n), **i32))
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+    def run(N, k):
+        for _ in range(3):
+            kf.kf_fit(ctx, s, fh, fo, None, fst, stream)
+            kf.kf_bin_hits(ctx, lh, bins, stream)
+            kf.kf_build(ctx, fo, seed_off, bins, N, out, stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t = np.zeros(3)
+        for _ in range(k):
+            evs[0].record(stream)
+            kf.kf_fit(ctx, s, fh, fo, None, fst, stream)
+            evs[1].record(stream)
+            kf.kf_bin_hits(ctx, lh, bins, stream)
+            evs[2].record(stream)
+            kf.kf_build(ctx, fo, seed_off, bins, N, out, stream)
+            evs[3].record(stream)
+            torch.cuda.synchronize()
+            t += [evs[0].elapsed_time(evs[1]), evs[1].elapsed_time(evs[2]), evs[2].elapsed_time(evs[3])]
+        t /= k
+        tot = float(t.sum())
+        if dist:
+            tt = torch.tensor([tot], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            tot = float(tt.item())
+        return tot, t
+
+    k = max(5, min(50, a.steps // 4))
+    tot6, t6 = run(6, k)
+    mean_hits = float(out.n_hits.float().mean())
+    tot1, t1 = run(1, k)
+    res = {"workload": f"combinatorial build: {E} events x {T} seeds, {int(3 * T)} noise + <= {T} track hits per "
+                       f"layer, 64x256 eta-phi bins, chi2 < 30, N = 6, seed fit on layers 1-3, build on 4-10",
+           "value": world * n * Lb / (tot6 / 1e3), "unit": "seed-layer steps/s", "ms_per_step": tot6,
+           "events_per_s": world * E / (tot6 / 1e3), "seeds_per_s": world * n / (tot6 / 1e3),
+           "phases_ms": {"seed_fit": float(t6[0]), "bin_hits": float(t6[1]), "build": float(t6[2])},
+           "build_ms_per_layer": float(t6[2]) / Lb, "mean_hits_found": mean_hits, "max_cands": 6,
+           "best_hit_N1": {"ms_per_step": tot1, "value": world * n * Lb / (tot1 / 1e3), "build_ms": float(t1[2])},
+           "gpu_launches_per_step": 3 + 1 + (3 + Lb + 1)}
+    if rank == 0 and not a.no_extras:
+        import oracle as O
+        cores = os.cpu_count() or 1
+        m = min(n, 1000)
+        idx = np.arange(m)
+        fr = O.fit(batch.seeds.par[:, idx], batch.seeds.cov[:, idx], batch.seeds.charge[idx], batch.fit_hits.xyz[:, :, idx],
+                   batch.fit_hits.valid[:, idx], det.radii[:3], det.bz, det.sigma_xy, det.sigma_z, n_threads=cores)
+        t0 = time.perf_counter()
+        O.build_tracks(fr["par"], fr["cov"], batch.seeds.charge[idx], batch.seed_event[idx], batch.layer_xyz,
+                       batch.layer_off, [det.radii[l] for l in batch.build_layers], det.bz, det.sigma_xy, det.sigma_z,
+                       30.0, 6, n_threads=cores)
+        dtc = time.perf_counter() - t0
+        res["cpu_baseline"] = {"value": m * Lb / dtc, "unit": "seed-layer steps/s", "cores": cores, "kind": "oracle",
+                               "sample": f"first {m} seeds of event 0 x {Lb} layers, N = 6, all-hits chi2 scan "
+                                         f"(the oracle bins nothing), {cores} OpenMP threads, {dtc:.2f} s wall"}
+    ctx.close()
     return res
 
 
