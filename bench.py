@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-build", action="store_true", help="skip the combinatorial-build leg")
     ap.add_argument("--build-events", type=int, default=50)
     ap.add_argument("--build-seeds", type=int, default=5000)
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--serve-pool", type=int, default=24, help="distinct events in the serving pool")
+    ap.add_argument("--serve-requests", type=int, default=240, help="requests per serving run")
     return ap.parse_args()
 
 
@@ -276,6 +279,9 @@ def run_ours(a):
         del seeds, hits, out, chi2, status
         torch.cuda.empty_cache()
         line["build"] = build_leg(a, kf, torch, dev, stream, rank, world, dist)
+    if not a.no_serve:
+        torch.cuda.empty_cache()
+        line["serving"] = serve_leg(a, kf, dev, rank)
     ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -439,6 +445,90 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist):
                                          f"(the oracle bins nothing), {cores} OpenMP threads, {dtc:.2f} s wall"}
     ctx.close()
     return res
+
+
+def serve_leg(a, kf, dev, rank):
+    """Continuous-batching service (kf_submit / kf_poll) on a Poisson stream of
+    events with log-uniform 500-50 000 tracks (3x noise hits per layer), the
+    build of the combinatorial-build leg (N = 6), admission by device memory."""
+    import threading
+    from paper_1605_05508_gb300 import synth as S
+    rng = np.random.default_rng(a.seed + 4 + 1000 * rank)
+    sizes = np.exp(rng.uniform(np.log(500), np.log(50000), a.serve_pool)).astype(int)
+    pool = []
+    for i, n in enumerate(sizes):
+        b = S.make_build_batch(a.seed + 10 + i + 1000 * rank, 1, int(n))
+        pool.append(dict(seed_par=b.seeds.par, seed_cov=b.seeds.cov, seed_charge=b.seeds.charge,
+                         seed_hits=b.fit_hits.xyz, seed_valid=b.fit_hits.valid, layer_xyz=b.layer_xyz,
+                         layer_off=b.layer_off))
+    det = S.barrel()
+    ctx = kf.Context(det.radii, det.bz, det.sigma_xy, det.sigma_z, device=dev.index)
+    kf.kf_serve_start(ctx, 3, 7, 6, max_slots=kf.MAX_SLOTS, max_queue=1 << 16, device_arena_bytes=16 << 30,
+                      host_arena_bytes=3 << 30)
+    M = a.serve_requests
+
+    def submit(ev):
+        while True:
+            try:
+                return kf.kf_submit(ctx, ev)
+            except kf.KfError as e:
+                if e.code != kf.KF_EAGAIN:
+                    raise
+                time.sleep(50e-6)
+
+    def run(gaps):
+        """Submit M requests (cycling the pool) after the given gaps; a poller
+        thread collects them in order. Returns (events/s, latencies ms)."""
+        tickets, lat = [None] * M, [None] * M
+        ready = threading.Semaphore(0)
+
+        def poller():
+            for i in range(M):
+                ready.acquire()
+                r = kf.kf_poll(ctx, tickets[i], pool[i % len(pool)]["seed_par"].shape[1], 7, -1)
+                lat[i] = r["latency_ms"]
+        th = threading.Thread(target=poller)
+        th.start()
+        t0 = time.perf_counter()
+        due = t0
+        for i in range(M):
+            due += gaps[i]
+            d = due - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            tickets[i] = submit(pool[i % len(pool)])
+            ready.release()
+        th.join()
+        wall = time.perf_counter() - t0
+        return M / wall, np.array(lat)
+
+    # warm-up, then the serial baseline: one event at a time, no overlap
+    for ev in pool[:4]:
+        kf.kf_poll(ctx, submit(ev), ev["seed_par"].shape[1], 7, -1)
+    t0 = time.perf_counter()
+    for ev in pool:
+        kf.kf_poll(ctx, submit(ev), ev["seed_par"].shape[1], 7, -1)
+    serial = len(pool) / (time.perf_counter() - t0)
+    sat, lat_sat = run(np.zeros(M))
+    runs = []
+    for frac in (0.5, 0.8):
+        lam = frac * sat
+        got, lat = run(rng.exponential(1.0 / lam, M))
+        runs.append({"offered_events_per_s": lam, "events_per_s": got, "p50_ms": float(np.percentile(lat, 50)),
+                     "p99_ms": float(np.percentile(lat, 99))})
+    st = kf.kf_serve_stats_get(ctx)
+    kf.kf_serve_stop(ctx)
+    ctx.close()
+    return {"workload": f"Poisson stream of events, tracks log-uniform 500-50000 (pool of {len(pool)} events, "
+                        f"mean {int(sizes.mean())} tracks), 3x noise hits per layer, build N = 6 on layers 4-10 "
+                        f"after a seed fit on layers 1-3; {M} requests per run",
+            "value": sat, "unit": "events/s", "saturation": {"events_per_s": sat,
+                                                              "p50_ms": float(np.percentile(lat_sat, 50)),
+                                                              "p99_ms": float(np.percentile(lat_sat, 99))},
+            "poisson": runs, "serial_one_at_a_time_events_per_s": serial,
+            "continuous_batching_speedup": sat / serial,
+            "max_resident_events": st["max_resident"], "step_launches": st["step_launches"],
+            "iterations": st["iterations"]}
 
 
 def main():

@@ -229,6 +229,83 @@ typedef struct {
 int kf_build(kf_ctx *ctx, const kf_tracks *seeds, const int64_t *seed_off, const kf_layer_hit_bins *bins,
              int32_t max_cands, kf_build_result *out, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Serving: continuous batching of build requests (Sec. 3's per-event build,
+ * run as a service).  Events of uneven size are admitted into resident slots
+ * when a slot and device memory are free; every scheduler iteration issues
+ * ONE build-step launch that advances every resident event by one layer
+ * (events at different layers share the launch); finished events are copied
+ * back asynchronously and their slots and memory reused.  Results do not
+ * depend on what else is resident (per-seed arithmetic only).
+ */
+#define KF_MAX_SLOTS 32
+
+typedef struct {
+    int32_t n_seed_layers;      /* configuration layers 0 .. n_seed_layers-1 fit the seeds */
+    int32_t n_build_layers;     /* the next n_build_layers layers are built */
+    int32_t max_cands;          /* 1 .. 8 */
+    int32_t max_slots;          /* resident events, 1 .. KF_MAX_SLOTS */
+    int32_t max_queue;          /* submitted, not yet admitted events (>= 1) */
+    size_t device_arena_bytes;  /* device memory for resident events (0: 1 GiB) */
+    size_t host_arena_bytes;    /* pinned host memory for queued inputs and results (0: 1 GiB) */
+} kf_serve_config;
+
+/* One event (host memory; copied by kf_submit, reusable when it returns). */
+typedef struct {
+    int32_t n_seeds;
+    const float *seed_par;      /* [6][n_seeds] vertex seeds */
+    const float *seed_cov;      /* [21][n_seeds] */
+    const int8_t *seed_charge;  /* [n_seeds] */
+    const float *seed_hits;     /* [n_seed_layers][3][n_seeds] hits on the seeding layers */
+    const uint8_t *seed_valid;  /* [n_seed_layers][n_seeds], or NULL = all valid */
+    const float *layer_xyz;     /* [3][n_hits] hits on the building layers, layer after layer */
+    const int64_t *layer_off;   /* [n_build_layers + 1] segment offsets into layer_xyz */
+} kf_event;
+
+/* Where kf_poll writes a finished event (host memory; NULL fields skipped). */
+typedef struct {
+    float *best_par;        /* [6][n_seeds] best candidate (position hi parts) */
+    float *best_cov;        /* [21][n_seeds] */
+    float *chi2_tot;        /* [n_seeds] */
+    int32_t *n_hits;        /* [n_seeds] */
+    int32_t *status;        /* [n_seeds] */
+    int32_t *hit_idx;       /* [n_build_layers][n_seeds], -1 = none */
+    double latency_ms;      /* written: kf_submit -> results on the host */
+    double queued_ms;       /* written: kf_submit -> admitted */
+} kf_event_result;
+
+typedef struct {
+    uint64_t submitted, admitted, completed, cancelled, iterations, step_launches;
+    int32_t resident, queued, max_resident;
+    size_t device_arena_bytes, device_arena_peak;
+} kf_serve_stats;
+
+/* Start the scheduler thread (one per context).  Allocates the arenas.
+ * Errors: KF_EINVAL (config), KF_ENOMEM (arenas), KF_EAGAIN (already running). */
+int kf_serve_start(kf_ctx *ctx, const kf_serve_config *cfg);
+
+/* Queue an event; returns a ticket.  Thread-safe.  Errors: KF_EINVAL (sizes),
+ * KF_ENOMEM (the event can never fit the device or host arena),
+ * KF_EAGAIN (queue or host arena full now: retry later), KF_ECUDA (the loop
+ * has failed). */
+int kf_submit(kf_ctx *ctx, const kf_event *ev, uint64_t *ticket);
+
+/* Wait up to timeout_us (< 0: forever, 0: do not wait) for a ticket; on
+ * KF_OK the results are written to `out` and the ticket is released.
+ * Errors: KF_ETIMEDOUT (not finished yet; the ticket stays valid),
+ * KF_EINVAL (unknown ticket), KF_ECUDA (the event failed). */
+int kf_poll(kf_ctx *ctx, uint64_t ticket, kf_event_result *out, int64_t timeout_us);
+
+/* Cancel a ticket that has not been admitted yet (KF_OK); KF_EAGAIN if it is
+ * already on the GPU (it will complete), KF_EINVAL if unknown. */
+int kf_cancel(kf_ctx *ctx, uint64_t ticket);
+
+int kf_serve_stats_get(kf_ctx *ctx, kf_serve_stats *out);
+
+/* Stop the loop after the resident events finish; queued events are
+ * cancelled; unpolled results are dropped.  kf_destroy stops it too. */
+int kf_serve_stop(kf_ctx *ctx);
+
 /* Largest batch (tracks) that kf_fit_noalloc accepts. */
 #define KF_NOALLOC_MAX_TRACKS 262144
 

@@ -22,40 +22,13 @@
 // The hit history is kept as per-layer back-pointers (parent rank, hit id)
 // and resolved once at the end, instead of copying index arrays per child.
 #include "kf_bin.cuh"
+#include "kf_build.cuh"
 #include "kf_internal.h"
 #include "kf_math.cuh"
 
+#include <vector>
+
 namespace kfi {
-
-constexpr int kGroup = 8;           // lanes (candidate slots) per seed
-constexpr int kBuildThreads = 128;  // 16 seeds per block
-constexpr int kNewtonBuild = 12;
-constexpr int kParN = 9;  // x y z px py pz + low parts of x y z
-constexpr uint64_t kNoKey = ~0ull;
-constexpr unsigned kFull = 0xffffffffu;
-
-struct CandBuf {
-  float* par;      // [9][S8]
-  float* cov;      // [21][S8]
-  float* chi2;     // [S8] chi2_tot
-  int32_t* meta;   // [S8] nHits | status << 8
-  int8_t* ncand;   // [S]
-};
-
-struct BuildStepArgs {
-  CandBuf in, out;
-  int8_t* hist_parent;  // [S8] of this layer
-  int32_t* hist_hit;    // [S8] of this layer
-  const int32_t* seed_evt;  // [S] sorted position -> event
-  const int32_t* seed_perm; // [S] sorted position -> seed index
-  const int8_t* charge;     // [n_seeds]
-  const float4* hits;
-  const int32_t* bin_off;
-  const int64_t* seg_off;
-  int64_t S;
-  int layer, n_layers, max_cands;
-  float a_scale, R, v0, v1, v2, cut;
-};
 
 __device__ __forceinline__ uint64_t make_key(int nhits, float chi2tot, int parent, int hit_plus1) {
   return (uint64_t(255 - nhits) << 56) | (uint64_t(__float_as_uint(chi2tot)) << 24) | (uint64_t(parent) << 21) |
@@ -77,14 +50,22 @@ __device__ __forceinline__ void list_insert(uint64_t (&L)[kGroup], int (&P)[kGro
   }
 }
 
-__global__ void __launch_bounds__(kBuildThreads) build_step_kernel(const BuildStepArgs A) {
+__global__ void __launch_bounds__(kBuildThreads) build_step_kernel(const BuildStepArgs Args) {
+  __shared__ BuildSlot sD;
+  if (threadIdx.x == 0) {
+    int sl = 0;
+    while (sl + 1 < Args.n_slots && int(blockIdx.x) >= Args.slots[sl + 1].block_begin) ++sl;
+    sD = Args.slots[sl];
+  }
+  __syncthreads();
+  const BuildSlot& D = sD;
   const int lane = threadIdx.x & 31;
   const int k = lane & (kGroup - 1);
   const int gbase = lane & ~(kGroup - 1);
-  const int64_t j = (int64_t(blockIdx.x) * kBuildThreads + threadIdx.x) / kGroup;
-  const int64_t S8 = A.S * kGroup;
-  const bool seed_ok = j < A.S;
-  const int nc = seed_ok ? A.in.ncand[j] : 0;
+  const int64_t j = (int64_t(blockIdx.x - D.block_begin) * kBuildThreads + threadIdx.x) / kGroup;
+  const int64_t S8 = D.S * kGroup;
+  const bool seed_ok = j < D.S;
+  const int nc = seed_ok ? D.in.ncand[j] : 0;
   const bool active = k < nc;
   const int64_t slot = j * kGroup + k;
 
@@ -94,13 +75,13 @@ __global__ void __launch_bounds__(kBuildThreads) build_step_kernel(const BuildSt
   int32_t st = 0;
   if (active) {
 #pragma unroll
-    for (int c = 0; c < 6; ++c) p[c] = A.in.par[c * S8 + slot];
+    for (int c = 0; c < 6; ++c) p[c] = D.in.par[c * S8 + slot];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) lo[c] = A.in.par[(6 + c) * S8 + slot];
+    for (int c = 0; c < 3; ++c) lo[c] = D.in.par[(6 + c) * S8 + slot];
 #pragma unroll
-    for (int c = 0; c < 21; ++c) C[c] = A.in.cov[c * S8 + slot];
-    chi2tot = A.in.chi2[slot];
-    const int32_t meta = A.in.meta[slot];
+    for (int c = 0; c < 21; ++c) C[c] = D.in.cov[c * S8 + slot];
+    chi2tot = D.in.chi2[slot];
+    const int32_t meta = D.in.meta[slot];
     nh = meta & 0xff;
     st = meta >> 8;
   } else {
@@ -111,13 +92,13 @@ __global__ void __launch_bounds__(kBuildThreads) build_step_kernel(const BuildSt
 #pragma unroll
     for (int c = 0; c < 21; ++c) C[c] = 0.f;
   }
-  const int e = seed_ok ? A.seed_evt[j] : 0;
-  const float a = A.a_scale * (seed_ok ? float(A.charge[A.seed_perm[j]]) : 1.f);
-  const int seg = e * A.n_layers + A.layer;
-  const int64_t h0 = seed_ok ? A.seg_off[seg] : 0;
+  const int e = seed_ok ? (D.seed_evt ? D.seed_evt[j] : 0) : 0;
+  const float a = Args.a_scale * (seed_ok ? float(D.charge[D.seed_perm[j]]) : 1.f);
+  const int seg = e * D.n_layers + D.layer;
+  const int64_t h0 = seed_ok ? D.seg_off[seg] : 0;
   bool stopped = (st & KF_ST_STOPPED) != 0;
   if (active && !stopped) {
-    const int r = kf::propagate<float, kNewtonBuild, true>(p, lo, C, a, A.R);
+    const int r = kf::propagate<float, kNewtonBuild, true>(p, lo, C, a, D.R);
     if (r) {
       st |= r;
       stopped = true;
@@ -136,21 +117,21 @@ __global__ void __launch_bounds__(kBuildThreads) build_step_kernel(const BuildSt
     bool any = false;
     if (!stopped) {
       float Si[6];
-      kf::inverse_S(C, A.v0, A.v1, A.v2, Si);
+      kf::inverse_S(C, Args.v0, Args.v1, Args.v2, Si);
       const float X = p[0] + lo[0], Y = p[1] + lo[1], Z = p[2] + lo[2];
       const float rr = sqrtf(X * X + Y * Y);
       const float cph = X / rr, sph = Y / rr;
-      const float s00 = C[0] + A.v0, s10 = C[1], s11 = C[2] + A.v1, s22 = C[5] + A.v2;
+      const float s00 = C[0] + Args.v0, s10 = C[1], s11 = C[2] + Args.v1, s22 = C[5] + Args.v2;
       const float Stt = sph * sph * s00 - 2.f * sph * cph * s10 + cph * cph * s11;
       const float Snn = cph * cph * s00 + 2.f * sph * cph * s10 + sph * sph * s11;
-      const float wt = sqrtf(A.cut * fmaxf(Stt, 0.f));
-      const float wn = sqrtf(A.cut * fmaxf(Snn, 0.f));
-      const float wz = sqrtf(A.cut * fmaxf(s22, 0.f));
+      const float wt = sqrtf(Args.cut * fmaxf(Stt, 0.f));
+      const float wn = sqrtf(Args.cut * fmaxf(Snn, 0.f));
+      const float wz = sqrtf(Args.cut * fmaxf(s22, 0.f));
       // phi bins: |dphi| <= atan(wt / (R - wn)), one bin of margin each side
       int fa0 = 0, fa1 = KF_BIN_PHI - 1, fb0 = 0, fb1 = -1;
-      const float rin = A.R - wn;
+      const float rin = D.R - wn;
       const float phic = atan2f(Y, X);
-      const float dphi = (rin > 0.5f * A.R && wt < rin) ? atanf(wt / rin) : 10.f;
+      const float dphi = (rin > 0.5f * D.R && wt < rin) ? atanf(wt / rin) : 10.f;
       if (dphi < 1.f && phic >= -kPi && phic <= kPi) {  // also false for NaN
         const float scale = float(KF_BIN_PHI) / (2.0f * kPi);
         const int f0 = __float2int_rd((phic - dphi + kPi) * scale) - 1;
@@ -174,7 +155,7 @@ __global__ void __launch_bounds__(kBuildThreads) build_step_kernel(const BuildSt
       }
       // eta bins: z within Z +- wz and the hit radius within R +- wn
       int e0 = 0, e1 = KF_BIN_ETA - 1;
-      const float rlo = A.R - wn, rhi = A.R + wn;
+      const float rlo = D.R - wn, rhi = D.R + wn;
       if (rlo > 0.f) {
         const float zlo = Z - wz, zhi = Z + wz;
         const float tmin = zlo >= 0.f ? zlo / rhi : zlo / rlo;
@@ -182,8 +163,8 @@ __global__ void __launch_bounds__(kBuildThreads) build_step_kernel(const BuildSt
         e0 = max(eta_bin(asinhf(tmin)) - 1, 0);
         e1 = min(eta_bin(asinhf(tmax)) + 1, KF_BIN_ETA - 1);
       }
-      const int32_t* boff = A.bin_off + int64_t(seg) * (KF_NBINS + 1);
-      const float4* hs = A.hits + h0;
+      const int32_t* boff = D.bin_off + int64_t(seg) * (KF_NBINS + 1);
+      const float4* hs = D.hits + h0;
       for (int er = e0; er <= e1; ++er) {
         for (int part = 0; part < 2; ++part) {
           const int f0 = part == 0 ? fa0 : fb0, f1 = part == 0 ? fa1 : fb1;
@@ -193,7 +174,7 @@ __global__ void __launch_bounds__(kBuildThreads) build_step_kernel(const BuildSt
             const float4 m = hs[u];
             const float r0 = (m.x - p[0]) - lo[0], r1 = (m.y - p[1]) - lo[1], r2 = (m.z - p[2]) - lo[2];
             const float c2 = kf::chi2_of(r0, r1, r2, Si);
-            if (c2 < A.cut) {
+            if (c2 < Args.cut) {
               const int id = __float_as_int(m.w);
               if (id < KF_MAX_HITS_PER_SEGMENT) {
                 list_insert(L, P, make_key(nh + 1, chi2tot + c2, k, id + 1), u);
@@ -213,7 +194,7 @@ __global__ void __launch_bounds__(kBuildThreads) build_step_kernel(const BuildSt
   int my_parent = 0, my_pos = -1, n_win = 0;
 #pragma unroll
   for (int r = 0; r < kGroup; ++r) {
-    if (r < A.max_cands) {  // uniform over the launch
+    if (r < Args.max_cands) {  // uniform over the launch
       uint64_t m = L[0];
 #pragma unroll
       for (int d = kGroup / 2; d >= 1; d >>= 1) {
@@ -261,38 +242,28 @@ __global__ void __launch_bounds__(kBuildThreads) build_step_kernel(const BuildSt
     const int hit_plus1 = int(my_key & 0x1fffffu);
     int32_t st_new = pst;
     if (hit_plus1 > 0) {
-      const float4 m = A.hits[h0 + my_pos];
+      const float4 m = D.hits[h0 + my_pos];
       float Si[6];
-      kf::inverse_S(qC, A.v0, A.v1, A.v2, Si);
+      kf::inverse_S(qC, Args.v0, Args.v1, Args.v2, Si);
       float r0, r1, r2;
       kf::residual<float, true>(q, ql, m.x, m.y, m.z, r0, r1, r2);
-      kf::kalman_update<float, true>(q, ql, qC, Si, r0, r1, r2, A.v0, A.v1, A.v2);
+      kf::kalman_update<float, true>(q, ql, qC, Si, r0, r1, r2, Args.v0, Args.v1, Args.v2);
     } else if (!pstopped) {
       st_new |= KF_ST_NO_HIT;
     }
 #pragma unroll
-    for (int c = 0; c < 6; ++c) A.out.par[c * S8 + slot] = q[c];
+    for (int c = 0; c < 6; ++c) D.out.par[c * S8 + slot] = q[c];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) A.out.par[(6 + c) * S8 + slot] = ql[c];
+    for (int c = 0; c < 3; ++c) D.out.par[(6 + c) * S8 + slot] = ql[c];
 #pragma unroll
-    for (int c = 0; c < 21; ++c) A.out.cov[c * S8 + slot] = qC[c];
-    A.out.chi2[slot] = chi2_new;
-    A.out.meta[slot] = nh_new | (st_new << 8);
-    A.hist_parent[slot] = int8_t(my_parent);
-    A.hist_hit[slot] = hit_plus1 - 1;
+    for (int c = 0; c < 21; ++c) D.out.cov[c * S8 + slot] = qC[c];
+    D.out.chi2[slot] = chi2_new;
+    D.out.meta[slot] = nh_new | (st_new << 8);
+    D.hist_parent[slot] = int8_t(my_parent);
+    D.hist_hit[slot] = hit_plus1 - 1;
   }
-  if (seed_ok && k == 0) A.out.ncand[j] = int8_t(n_win);
+  if (seed_ok && k == 0) D.out.ncand[j] = int8_t(n_win);
 }
-
-struct BuildInitArgs {
-  CandBuf out;
-  const float* par;
-  const float* lo;
-  const float* cov;
-  const int32_t* seed_perm;
-  int64_t n;  // seeds (stride of the seed arrays)
-  int64_t S;
-};
 
 __global__ void build_init_kernel(const BuildInitArgs A) {
   const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -306,16 +277,6 @@ __global__ void build_init_kernel(const BuildInitArgs A) {
   A.out.meta[slot] = 0;
   A.out.ncand[j] = 1;
 }
-
-struct BuildFinalArgs {
-  CandBuf cand;
-  const int8_t* hist_parent;  // [L][S8]
-  const int32_t* hist_hit;    // [L][S8]
-  const int32_t* seed_perm;
-  int64_t S;
-  int n_layers, max_cands;
-  kf_build_result out;
-};
 
 template <typename T>
 __device__ bool pd5_final(const T p[6], const T C[21]) {
@@ -399,6 +360,24 @@ __global__ void build_final_kernel(const BuildFinalArgs A) {
   }
 }
 
+cudaError_t launch_build_step(const BuildStepArgs& a, int grid, cudaStream_t st) {
+  if (grid <= 0) return cudaSuccess;
+  build_step_kernel<<<grid, kBuildThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_init(const BuildInitArgs& a, cudaStream_t st) {
+  if (a.S <= 0) return cudaSuccess;
+  build_init_kernel<<<int((a.S + 255) / 256), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_final(const BuildFinalArgs& a, cudaStream_t st) {
+  if (a.S <= 0) return cudaSuccess;
+  build_final_kernel<<<int((a.S + 127) / 128), 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 __global__ void globalise_perm_kernel(int32_t* perm, const int32_t* evt, const int64_t* seed_off, int64_t S) {
   const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j < S) perm[j] = int32_t(seed_off[evt[j]] + perm[j]);
@@ -429,26 +408,18 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
   const int L = bins->n_layers;
   const int64_t S8 = S * kGroup;
   // scratch layout
-  const size_t b_perm = al256(S * 4), b_evt = al256(S * 4), b_candf = al256(S8 * 4), b_nc = al256(S);
-  const size_t b_cand = (kParN + 21 + 2) * b_candf + b_nc;  // par, cov, chi2, meta + ncand
+  const size_t b_perm = al256(S * 4), b_evt = al256(S * 4);
+  const size_t b_cand = cand_bytes(S);
   const size_t b_hp = al256(size_t(L) * S8), b_hh = al256(size_t(L) * S8 * 4);
-  const size_t total = b_perm + b_evt + 2 * b_cand + b_hp + b_hh;
+  const size_t b_tab = al256(sizeof(BuildSlot) * size_t(L));
+  const size_t total = b_perm + b_evt + 2 * b_cand + b_hp + b_hh + b_tab;
   int rc = scratch_reserve(ctx, ctx->s_build, total);
   if (rc) return rc;
   char* base = static_cast<char*>(ctx->s_build.ptr);
   int32_t* perm = reinterpret_cast<int32_t*>(base);
   int32_t* evt = reinterpret_cast<int32_t*>(base + b_perm);
-  auto cand_at = [&](char* q) {
-    CandBuf c;
-    c.par = reinterpret_cast<float*>(q);
-    c.cov = reinterpret_cast<float*>(q + kParN * b_candf);
-    c.chi2 = reinterpret_cast<float*>(q + (kParN + 21) * b_candf);
-    c.meta = reinterpret_cast<int32_t*>(q + (kParN + 22) * b_candf);
-    c.ncand = reinterpret_cast<int8_t*>(q + (kParN + 23) * b_candf);
-    return c;
-  };
-  CandBuf bufA = cand_at(base + b_perm + b_evt);
-  CandBuf bufB = cand_at(base + b_perm + b_evt + b_cand);
+  CandBuf bufA = cand_at(base + b_perm + b_evt, S);
+  CandBuf bufB = cand_at(base + b_perm + b_evt + b_cand, S);
   int8_t* hist_parent = reinterpret_cast<int8_t*>(base + b_perm + b_evt + 2 * b_cand);
   int32_t* hist_hit = reinterpret_cast<int32_t*>(base + b_perm + b_evt + 2 * b_cand + b_hp);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -482,24 +453,35 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
   const float v0 = ctx->cfg.sigma_xy_cm * ctx->cfg.sigma_xy_cm;
   const float v2 = ctx->cfg.sigma_z_cm * ctx->cfg.sigma_z_cm;
   const int grid = int((S8 + kBuildThreads - 1) / kBuildThreads);
+  // one slot (the whole batch) per layer launch; the table goes to device
+  // scratch in one copy (the host array is consumed before the call returns)
+  std::vector<BuildSlot> table(L);
+  for (int l = 0; l < L; ++l) {
+    BuildSlot& d = table[l];
+    d.in = (l % 2 == 0) ? bufA : bufB;
+    d.out = (l % 2 == 0) ? bufB : bufA;
+    d.hist_parent = hist_parent + int64_t(l) * S8;
+    d.hist_hit = hist_hit + int64_t(l) * S8;
+    d.seed_evt = evt;
+    d.seed_perm = perm;
+    d.charge = seeds->charge;
+    d.hits = reinterpret_cast<const float4*>(bins->hits);
+    d.bin_off = bins->bin_off;
+    d.seg_off = bins->seg_off;
+    d.S = S;
+    d.layer = l;
+    d.n_layers = L;
+    d.R = ctx->radius[bins->first_layer + l];
+    d.block_begin = 0;
+  }
+  BuildSlot* dtable = reinterpret_cast<BuildSlot*>(base + b_perm + b_evt + 2 * b_cand + b_hp + b_hh);
+  KF_CUDA_TRY(ctx, cudaMemcpyAsync(dtable, table.data(), sizeof(BuildSlot) * L, cudaMemcpyHostToDevice, s));
   for (int l = 0; l < L; ++l) {
     BuildStepArgs a;
-    a.in = (l % 2 == 0) ? bufA : bufB;
-    a.out = (l % 2 == 0) ? bufB : bufA;
-    a.hist_parent = hist_parent + int64_t(l) * S8;
-    a.hist_hit = hist_hit + int64_t(l) * S8;
-    a.seed_evt = evt;
-    a.seed_perm = perm;
-    a.charge = seeds->charge;
-    a.hits = reinterpret_cast<const float4*>(bins->hits);
-    a.bin_off = bins->bin_off;
-    a.seg_off = bins->seg_off;
-    a.S = S;
-    a.layer = l;
-    a.n_layers = L;
+    a.slots = dtable + l;
+    a.n_slots = 1;
     a.max_cands = max_cands;
     a.a_scale = float(kCLight * double(ctx->cfg.bz_tesla));
-    a.R = ctx->radius[bins->first_layer + l];
     a.v0 = v0;
     a.v1 = v0;
     a.v2 = v2;

@@ -1,0 +1,91 @@
+// kf_build.cuh -- candidate buffers, slot table and launchers of the
+// clone-engine build kernels (kf_build.cu), shared with the serving loop.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/kf.h"
+
+namespace kfi {
+
+constexpr int kGroup = 8;           // lanes (candidate slots) per seed
+constexpr int kBuildThreads = 128;  // 16 seeds per block
+constexpr int kNewtonBuild = 12;
+constexpr int kParN = 9;  // x y z px py pz + low parts of x y z
+constexpr uint64_t kNoKey = ~0ull;
+constexpr unsigned kFull = 0xffffffffu;
+
+struct CandBuf {
+  float* par;      // [9][S8]
+  float* cov;      // [21][S8]
+  float* chi2;     // [S8] chi2_tot
+  int32_t* meta;   // [S8] nHits | status << 8
+  int8_t* ncand;   // [S]
+};
+
+// One independent group of seeds advanced by a build step: a whole batch
+// (kf_build) or one served event (kf_serve).  Slots of one launch may sit at
+// different layers.  Blocks [block_begin, next slot's block_begin) serve it.
+struct BuildSlot {
+  CandBuf in, out;
+  int8_t* hist_parent;       // [S8] of this layer
+  int32_t* hist_hit;         // [S8] of this layer
+  const int32_t* seed_evt;   // [S] sorted position -> event, or null (event 0)
+  const int32_t* seed_perm;  // [S] sorted position -> seed index
+  const int8_t* charge;      // [S] by seed index
+  const float4* hits;
+  const int32_t* bin_off;
+  const int64_t* seg_off;
+  int64_t S;
+  int layer, n_layers;
+  float R;
+  int block_begin;
+};
+
+struct BuildStepArgs {
+  const BuildSlot* slots;  // device table
+  int n_slots, max_cands;
+  float a_scale, v0, v1, v2, cut;
+};
+
+struct BuildInitArgs {
+  CandBuf out;
+  const float* par;
+  const float* lo;
+  const float* cov;
+  const int32_t* seed_perm;
+  int64_t n;  // seeds (stride of the seed arrays)
+  int64_t S;
+};
+
+struct BuildFinalArgs {
+  CandBuf cand;
+  const int8_t* hist_parent;  // [L][S8]
+  const int32_t* hist_hit;    // [L][S8]
+  const int32_t* seed_perm;
+  int64_t S;
+  int n_layers, max_cands;
+  kf_build_result out;
+};
+
+// Candidate buffer of S seeds at `base` (256-byte aligned pieces).
+inline size_t cand_piece(int64_t S) { return (size_t(S) * kGroup * 4 + 255) & ~size_t(255); }
+inline size_t cand_bytes(int64_t S) { return (kParN + 23) * cand_piece(S) + ((size_t(S) + 255) & ~size_t(255)); }
+inline CandBuf cand_at(char* q, int64_t S) {
+  const size_t pc = cand_piece(S);
+  CandBuf c;
+  c.par = reinterpret_cast<float*>(q);
+  c.cov = reinterpret_cast<float*>(q + kParN * pc);
+  c.chi2 = reinterpret_cast<float*>(q + (kParN + 21) * pc);
+  c.meta = reinterpret_cast<int32_t*>(q + (kParN + 22) * pc);
+  c.ncand = reinterpret_cast<int8_t*>(q + (kParN + 23) * pc);
+  return c;
+}
+
+cudaError_t launch_build_step(const BuildStepArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_build_init(const BuildInitArgs& a, cudaStream_t st);
+cudaError_t launch_build_final(const BuildFinalArgs& a, cudaStream_t st);
+
+}  // namespace kfi

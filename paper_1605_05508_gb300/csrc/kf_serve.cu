@@ -1,3 +1,686 @@
-// kf_serve.cu -- serving loop (continuous batching); placeholder teardown.
+// kf_serve.cu -- continuous-batching service for the combinatorial build.
+//
+// The paper's building runs event by event on CPU threads and names load
+// balancing across threads (uneven occupancy per event) and dynamic
+// scheduling as the open problems (Sec. 3.2, Sec. 4).  On one GPU the same
+// problem becomes: keep the device full while events of very different size
+// arrive at random times.  The scheduler thread here
+//   * admits queued events in arrival order whenever a slot and a contiguous
+//     block of the device arena are free (memory-based admission),
+//   * prepares an admitted event on the serve stream: input copy, seed fit
+//     over the seeding layers, hit binning, seed ordering, first candidate,
+//   * issues ONE build-step launch per iteration over every resident event,
+//     each at its own layer (the slot table tells each block its event,
+//     layer, buffers and hit bins), so candidates stay resident on the device
+//     between layers and small events ride along with big ones,
+//   * selects the best candidate of finished events, copies their results to
+//     pinned host memory asynchronously and recycles their slot and memory.
+// All device work of the service is on one stream; the host never waits on a
+// device flag (it polls CUDA events) and runs at most kInflight iterations
+// ahead of the GPU.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "kf_bin.cuh"
+#include "kf_build.cuh"
 #include "kf_internal.h"
-void kf_serve_shutdown_internal(kf_ctx* ctx) { (void)ctx; }
+
+namespace kfi {
+
+using Clock = std::chrono::steady_clock;
+
+// First-fit allocator over an address range [0, size).
+class Arena {
+ public:
+  void reset(size_t size) {
+    free_.clear();
+    if (size) free_[0] = size;
+    size_ = size;
+    used_ = peak_ = 0;
+  }
+  bool alloc(size_t bytes, size_t* off) {
+    bytes = (bytes + 255) & ~size_t(255);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        *off = it->first;
+        const size_t rest = it->second - bytes, at = it->first + bytes;
+        free_.erase(it);
+        if (rest) free_[at] = rest;
+        used_ += bytes;
+        peak_ = std::max(peak_, used_);
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t bytes) {
+    bytes = (bytes + 255) & ~size_t(255);
+    used_ -= bytes;
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  size_t size() const { return size_; }
+  size_t peak() const { return peak_; }
+
+ private:
+  std::map<size_t, size_t> free_;
+  size_t size_ = 0, used_ = 0, peak_ = 0;
+};
+
+enum ReqState { kQueued, kResident, kFinishing, kDone, kFailed };
+
+// Byte layout of one event inside the device arena and the host arena.
+struct EventLayout {
+  int64_t n, nh;
+  int ns, Lb;
+  // device offsets
+  size_t d_par, d_cov, d_q, d_shits, d_sval, d_fpar, d_flo, d_fcov, d_fst, d_xyz, d_segoff, d_sseg, d_bhits, d_boff,
+      d_bid, d_perm, d_candA, d_candB, d_hp, d_hh, d_rpar, d_rcov, d_rchi, d_rnh, d_rst, d_rhit, d_total;
+  // host input / output block offsets
+  size_t h_par, h_cov, h_q, h_shits, h_sval, h_xyz, h_segoff, h_in_total;
+  size_t o_par, o_cov, o_chi, o_nh, o_st, o_hit, h_out_total;
+
+  void make(int64_t n_, int64_t nh_, int ns_, int Lb_) {
+    n = n_;
+    nh = nh_;
+    ns = ns_;
+    Lb = Lb_;
+    size_t o = 0;
+    auto take = [&](size_t b) {
+      const size_t at = o;
+      o += (b + 255) & ~size_t(255);
+      return at;
+    };
+    d_par = take(6 * n * 4);
+    d_cov = take(21 * n * 4);
+    d_q = take(n);
+    d_shits = take(size_t(ns) * 3 * n * 4);
+    d_sval = take(size_t(ns) * n);
+    d_fpar = take(6 * n * 4);
+    d_flo = take(3 * n * 4);
+    d_fcov = take(21 * n * 4);
+    d_fst = take(n * 4);
+    d_xyz = take(3 * nh * 4);
+    d_segoff = take((Lb + 1) * 8);
+    d_sseg = take(2 * 8);
+    d_bhits = take(nh * 16);
+    d_boff = take(size_t(Lb) * (KF_NBINS + 1) * 4);
+    d_bid = take(std::max<int64_t>(nh, n) * 4);
+    d_perm = take(n * 4);
+    d_candA = take(cand_bytes(n));
+    d_candB = take(cand_bytes(n));
+    d_hp = take(size_t(Lb) * n * kGroup);
+    d_hh = take(size_t(Lb) * n * kGroup * 4);
+    d_rpar = take(6 * n * 4);
+    d_rcov = take(21 * n * 4);
+    d_rchi = take(n * 4);
+    d_rnh = take(n * 4);
+    d_rst = take(n * 4);
+    d_rhit = take(size_t(Lb) * n * 4);
+    d_total = o;
+    o = 0;
+    h_par = take(6 * n * 4);
+    h_cov = take(21 * n * 4);
+    h_q = take(n);
+    h_shits = take(size_t(ns) * 3 * n * 4);
+    h_sval = take(size_t(ns) * n);
+    h_xyz = take(3 * nh * 4);
+    h_segoff = take((Lb + 1) * 8 + 16);  // layer offsets, then the seed segment {0, n}
+    h_in_total = o;
+    o = 0;
+    o_par = take(6 * n * 4);
+    o_cov = take(21 * n * 4);
+    o_chi = take(n * 4);
+    o_nh = take(n * 4);
+    o_st = take(n * 4);
+    o_hit = take(size_t(Lb) * n * 4);
+    h_out_total = o;
+  }
+};
+
+struct Request {
+  uint64_t ticket = 0;
+  EventLayout lay;
+  ReqState state = kQueued;
+  int layer = 0;  // next build layer
+  size_t d_off = 0, h_in_off = 0, h_out_off = 0;
+  bool has_d = false, has_in = false, has_out = false;
+  cudaEvent_t done = nullptr;
+  Clock::time_point t_submit, t_admit, t_done;
+};
+
+constexpr int kInflight = 2;  // iterations the host may run ahead of the GPU
+constexpr int kRing = kInflight + 2;
+
+struct Serve {
+  kf_ctx* ctx = nullptr;
+  kf_serve_config cfg{};
+  std::mutex mu;
+  std::condition_variable cv;  // wakes the scheduler
+  std::condition_variable done_cv;  // wakes pollers
+  std::thread thread;
+  bool stop = false;
+  int cuda_error = 0;
+  cudaStream_t stream = nullptr;
+  char* dmem = nullptr;
+  char* hmem = nullptr;
+  Arena darena, harena;
+  BuildSlot* d_table = nullptr;  // [kRing][KF_MAX_SLOTS]
+  BuildSlot* h_table = nullptr;  // pinned, same shape
+  cudaEvent_t iter_ev[kRing] = {};
+  uint64_t next_ticket = 1;
+  std::deque<Request*> queue;
+  std::vector<Request*> resident;  // resident or finishing
+  std::unordered_map<uint64_t, std::unique_ptr<Request>> all;
+  kf_serve_stats stats{};
+};
+
+static void fail_all_locked(Serve* sv, int err) {
+  sv->cuda_error = err;
+  for (auto& kv : sv->all)
+    if (kv.second->state != kDone) kv.second->state = kFailed;
+  sv->done_cv.notify_all();
+}
+
+// Enqueue the preparation of an admitted event on the serve stream.
+static cudaError_t prepare(Serve* sv, Request* r) {
+  kf_ctx* ctx = sv->ctx;
+  const EventLayout& L = r->lay;
+  char* d = sv->dmem + r->d_off;
+  char* h = sv->hmem + r->h_in_off;
+  cudaStream_t s = sv->stream;
+  const int64_t n = L.n;
+  // the host input block mirrors the first device pieces (par .. sval); the
+  // raw hits and their offsets follow in the host block and go to their own
+  // device pieces
+  cudaError_t e = cudaMemcpyAsync(d, h, L.h_xyz, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d + L.d_xyz, h + L.h_xyz, size_t(3) * L.nh * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d + L.d_segoff, h + L.h_segoff, size_t(L.Lb + 1) * 8, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  // seed fit over the seeding layers (one fused launch)
+  FitFusedArgs fa;
+  std::memset(&fa, 0, sizeof fa);
+  fa.in_par = reinterpret_cast<const float*>(d + L.d_par);
+  fa.in_lo = nullptr;
+  fa.in_cov = reinterpret_cast<const float*>(d + L.d_cov);
+  fa.charge = reinterpret_cast<const int8_t*>(d + L.d_q);
+  fa.out_par = reinterpret_cast<float*>(d + L.d_fpar);
+  fa.out_lo = reinterpret_cast<float*>(d + L.d_flo);
+  fa.out_cov = reinterpret_cast<float*>(d + L.d_fcov);
+  fa.hits = reinterpret_cast<const float*>(d + L.d_shits);
+  fa.valid = reinterpret_cast<const uint8_t*>(d + L.d_sval);
+  fa.chi2 = nullptr;
+  fa.status = reinterpret_cast<int32_t*>(d + L.d_fst);
+  fa.n = n;
+  fa.n_layers = L.ns;
+  fa.a_scale = float(kCLight * double(ctx->cfg.bz_tesla));
+  fa.v0 = fa.v1 = ctx->cfg.sigma_xy_cm * ctx->cfg.sigma_xy_cm;
+  fa.v2 = ctx->cfg.sigma_z_cm * ctx->cfg.sigma_z_cm;
+  for (int l = 0; l < L.ns; ++l) fa.R[l] = ctx->radius[l];
+  e = launch_fit_fused(fa, fit_grid(ctx, n), s);
+  if (e != cudaSuccess) return e;
+  // hits into eta x phi bins, one segment per build layer
+  BinArgs hb;
+  hb.xyz = reinterpret_cast<const float*>(d + L.d_xyz);
+  hb.stride = L.nh;
+  hb.seg_off = reinterpret_cast<const int64_t*>(d + L.d_segoff);
+  hb.bin_off = reinterpret_cast<int32_t*>(d + L.d_boff);
+  hb.out_pts = reinterpret_cast<float4*>(d + L.d_bhits);
+  hb.out_id = reinterpret_cast<int32_t*>(d + L.d_bid);
+  hb.out_seg = nullptr;
+  e = launch_bin_points(hb, L.Lb, s);
+  if (e != cudaSuccess) return e;
+  // seeds in (eta, phi) order: one segment [0, n)
+  const int64_t sseg[2] = {0, n};
+  e = cudaMemcpyAsync(d + L.d_sseg, h + L.h_segoff + size_t(L.Lb + 1) * 8, sizeof sseg, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  BinArgs sb;
+  sb.xyz = reinterpret_cast<const float*>(d + L.d_fpar);
+  sb.stride = n;
+  sb.seg_off = reinterpret_cast<const int64_t*>(d + L.d_sseg);
+  sb.bin_off = nullptr;
+  sb.out_pts = nullptr;
+  sb.out_id = reinterpret_cast<int32_t*>(d + L.d_perm);
+  sb.out_seg = nullptr;
+  e = launch_bin_points(sb, 1, s);
+  if (e != cudaSuccess) return e;
+  BuildInitArgs ia;
+  ia.out = cand_at(d + L.d_candA, n);
+  ia.par = reinterpret_cast<const float*>(d + L.d_fpar);
+  ia.lo = reinterpret_cast<const float*>(d + L.d_flo);
+  ia.cov = reinterpret_cast<const float*>(d + L.d_fcov);
+  ia.seed_perm = reinterpret_cast<const int32_t*>(d + L.d_perm);
+  ia.n = n;
+  ia.S = n;
+  return launch_build_init(ia, s);
+}
+
+static BuildSlot slot_of(Serve* sv, Request* r) {
+  const EventLayout& L = r->lay;
+  char* d = sv->dmem + r->d_off;
+  const int64_t n = L.n;
+  BuildSlot b;
+  CandBuf A = cand_at(d + L.d_candA, n), B = cand_at(d + L.d_candB, n);
+  b.in = (r->layer % 2 == 0) ? A : B;
+  b.out = (r->layer % 2 == 0) ? B : A;
+  b.hist_parent = reinterpret_cast<int8_t*>(d + L.d_hp) + int64_t(r->layer) * n * kGroup;
+  b.hist_hit = reinterpret_cast<int32_t*>(d + L.d_hh) + int64_t(r->layer) * n * kGroup;
+  b.seed_evt = nullptr;
+  b.seed_perm = reinterpret_cast<const int32_t*>(d + L.d_perm);
+  b.charge = reinterpret_cast<const int8_t*>(d + L.d_q);
+  b.hits = reinterpret_cast<const float4*>(d + L.d_bhits);
+  b.bin_off = reinterpret_cast<const int32_t*>(d + L.d_boff);
+  b.seg_off = reinterpret_cast<const int64_t*>(d + L.d_segoff);
+  b.S = n;
+  b.layer = r->layer;
+  b.n_layers = L.Lb;
+  b.R = sv->ctx->radius[sv->cfg.n_seed_layers + r->layer];
+  b.block_begin = 0;
+  return b;
+}
+
+// Final selection + asynchronous copy of the results to the pinned output block.
+static cudaError_t finish(Serve* sv, Request* r) {
+  const EventLayout& L = r->lay;
+  char* d = sv->dmem + r->d_off;
+  char* o = sv->hmem + r->h_out_off;
+  const int64_t n = L.n;
+  cudaStream_t s = sv->stream;
+  BuildFinalArgs fa;
+  std::memset(&fa, 0, sizeof fa);
+  fa.cand = cand_at(d + ((L.Lb % 2 == 0) ? L.d_candA : L.d_candB), n);
+  fa.hist_parent = reinterpret_cast<const int8_t*>(d + L.d_hp);
+  fa.hist_hit = reinterpret_cast<const int32_t*>(d + L.d_hh);
+  fa.seed_perm = reinterpret_cast<const int32_t*>(d + L.d_perm);
+  fa.S = n;
+  fa.n_layers = L.Lb;
+  fa.max_cands = sv->cfg.max_cands;
+  fa.out.best.n = n;
+  fa.out.best.par = reinterpret_cast<float*>(d + L.d_rpar);
+  fa.out.best.par_lo = nullptr;
+  fa.out.best.cov = reinterpret_cast<float*>(d + L.d_rcov);
+  fa.out.chi2_tot = reinterpret_cast<float*>(d + L.d_rchi);
+  fa.out.n_hits = reinterpret_cast<int32_t*>(d + L.d_rnh);
+  fa.out.status = reinterpret_cast<int32_t*>(d + L.d_rst);
+  fa.out.hit_idx = reinterpret_cast<int32_t*>(d + L.d_rhit);
+  cudaError_t e = launch_build_final(fa, s);
+  // results are contiguous on the device (rpar .. rhit) and in the output block
+  if (e == cudaSuccess) e = cudaMemcpyAsync(o, d + L.d_rpar, L.h_out_total, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaEventRecord(r->done, s);
+  return e;
+}
+
+static void release_locked(Serve* sv, Request* r) {
+  if (r->has_d) sv->darena.release(r->d_off, r->lay.d_total);
+  if (r->has_in) sv->harena.release(r->h_in_off, r->lay.h_in_total);
+  r->has_d = r->has_in = false;
+}
+
+static void scheduler(Serve* sv) {
+  cudaSetDevice(sv->ctx->device);
+  uint64_t iter = 0;
+  std::vector<Request*> admitted;
+  while (true) {
+    admitted.clear();
+    {
+      std::unique_lock<std::mutex> lk(sv->mu);
+      // finished events: results are on the host
+      for (auto it = sv->resident.begin(); it != sv->resident.end();) {
+        Request* r = *it;
+        if (r->state == kFinishing) {
+          const cudaError_t q = cudaEventQuery(r->done);
+          if (q == cudaSuccess) {
+            r->state = kDone;
+            r->t_done = Clock::now();
+            if (r->has_d) sv->darena.release(r->d_off, r->lay.d_total);
+            r->has_d = false;
+            sv->stats.completed++;
+            it = sv->resident.erase(it);
+            sv->done_cv.notify_all();
+            continue;
+          }
+          if (q != cudaErrorNotReady) {
+            fail_all_locked(sv, int(q));
+          }
+        }
+        ++it;
+      }
+      if (sv->cuda_error) {
+        sv->resident.clear();
+        sv->queue.clear();
+      }
+      // admission in arrival order: a free slot and a device block
+      while (!sv->queue.empty() && int(sv->resident.size()) < sv->cfg.max_slots && !sv->cuda_error) {
+        Request* r = sv->queue.front();
+        size_t off = 0;
+        if (!sv->darena.alloc(r->lay.d_total, &off)) break;
+        sv->queue.pop_front();
+        r->d_off = off;
+        r->has_d = true;
+        r->state = kResident;
+        r->layer = 0;
+        r->t_admit = Clock::now();
+        sv->stats.admitted++;
+        sv->resident.push_back(r);
+        admitted.push_back(r);
+      }
+      bool active = false;
+      for (Request* r : sv->resident) active |= r->state == kResident;
+      bool finishing = false;
+      for (Request* r : sv->resident) finishing |= r->state == kFinishing;
+      if (!active && admitted.empty()) {
+        if (sv->stop && sv->queue.empty() && !finishing) break;
+        if (finishing)
+          sv->cv.wait_for(lk, std::chrono::microseconds(20));
+        else
+          sv->cv.wait_for(lk, std::chrono::milliseconds(50));
+        continue;
+      }
+      sv->stats.resident = int(sv->resident.size());
+      sv->stats.max_resident = std::max(sv->stats.max_resident, sv->stats.resident);
+      sv->stats.queued = int(sv->queue.size());
+    }
+    // ---- device work of this iteration (serve stream, no lock held)
+    cudaError_t e = cudaSuccess;
+    for (Request* r : admitted)
+      if (e == cudaSuccess) e = prepare(sv, r);
+    // pace: at most kInflight iterations ahead of the GPU
+    const int ring = int(iter % kRing);
+    if (e == cudaSuccess && iter >= uint64_t(kInflight))
+      e = cudaEventSynchronize(sv->iter_ev[(iter - kInflight) % kRing]);
+    std::vector<Request*> stepping;
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      for (Request* r : sv->resident)
+        if (r->state == kResident && r->layer < r->lay.Lb) stepping.push_back(r);
+    }
+    if (e == cudaSuccess && !stepping.empty()) {
+      BuildSlot* ht = sv->h_table + size_t(ring) * KF_MAX_SLOTS;
+      int blocks = 0;
+      for (size_t i = 0; i < stepping.size(); ++i) {
+        ht[i] = slot_of(sv, stepping[i]);
+        ht[i].block_begin = blocks;
+        blocks += int((ht[i].S * kGroup + kBuildThreads - 1) / kBuildThreads);
+      }
+      BuildSlot* dt = sv->d_table + size_t(ring) * KF_MAX_SLOTS;
+      e = cudaMemcpyAsync(dt, ht, sizeof(BuildSlot) * stepping.size(), cudaMemcpyHostToDevice, sv->stream);
+      BuildStepArgs a;
+      a.slots = dt;
+      a.n_slots = int(stepping.size());
+      a.max_cands = sv->cfg.max_cands;
+      a.a_scale = float(kCLight * double(sv->ctx->cfg.bz_tesla));
+      a.v0 = a.v1 = sv->ctx->cfg.sigma_xy_cm * sv->ctx->cfg.sigma_xy_cm;
+      a.v2 = sv->ctx->cfg.sigma_z_cm * sv->ctx->cfg.sigma_z_cm;
+      a.cut = sv->ctx->cfg.chi2_cut;
+      if (e == cudaSuccess) e = launch_build_step(a, blocks, sv->stream);
+      for (Request* r : stepping) r->layer++;
+      std::lock_guard<std::mutex> lk(sv->mu);
+      sv->stats.step_launches++;
+    }
+    if (e == cudaSuccess) {
+      for (Request* r : stepping)
+        if (r->layer == r->lay.Lb && e == cudaSuccess) {
+          e = finish(sv, r);
+          std::lock_guard<std::mutex> lk(sv->mu);
+          r->state = kFinishing;
+        }
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(sv->iter_ev[ring], sv->stream);
+    ++iter;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->stats.iterations++;
+    if (e != cudaSuccess) {
+      fail_all_locked(sv, int(e));
+      sv->resident.clear();
+      sv->queue.clear();
+    }
+  }
+}
+
+}  // namespace kfi
+
+using namespace kfi;
+
+void kf_serve_shutdown_internal(kf_ctx* ctx) {
+  if (!ctx || !ctx->serve) return;
+  Serve* sv = ctx->serve;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->stop = true;
+    for (Request* r : sv->queue) {
+      r->state = kFailed;
+      sv->stats.cancelled++;
+    }
+    sv->queue.clear();
+  }
+  sv->cv.notify_all();
+  if (sv->thread.joinable()) sv->thread.join();
+  cudaSetDevice(ctx->device);
+  if (sv->stream) cudaStreamSynchronize(sv->stream);
+  for (auto& kv : sv->all)
+    if (kv.second->done) cudaEventDestroy(kv.second->done);
+  for (int i = 0; i < kRing; ++i)
+    if (sv->iter_ev[i]) cudaEventDestroy(sv->iter_ev[i]);
+  if (sv->dmem) cudaFree(sv->dmem);
+  if (sv->d_table) cudaFree(sv->d_table);
+  if (sv->hmem) cudaFreeHost(sv->hmem);
+  if (sv->h_table) cudaFreeHost(sv->h_table);
+  if (sv->stream) cudaStreamDestroy(sv->stream);
+  ctx->allocated -= sv->darena.size();
+  delete sv;
+  ctx->serve = nullptr;
+}
+
+extern "C" {
+
+int kf_serve_start(kf_ctx* ctx, const kf_serve_config* cfg) {
+  if (!ctx || !cfg) return KF_EINVAL;
+  if (ctx->serve) return KF_EAGAIN;
+  if (cfg->n_seed_layers < 1 || cfg->n_build_layers < 1 ||
+      cfg->n_seed_layers + cfg->n_build_layers > ctx->cfg.n_layers || cfg->n_seed_layers > kMaxLayers)
+    return KF_EINVAL;
+  if (cfg->max_cands < 1 || cfg->max_cands > kGroup || cfg->max_slots < 1 || cfg->max_slots > KF_MAX_SLOTS ||
+      cfg->max_queue < 1)
+    return KF_EINVAL;
+  KF_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  auto* sv = new (std::nothrow) Serve();
+  if (!sv) return KF_ENOMEM;
+  sv->ctx = ctx;
+  sv->cfg = *cfg;
+  const size_t dbytes = cfg->device_arena_bytes ? cfg->device_arena_bytes : (size_t(1) << 30);
+  const size_t hbytes = cfg->host_arena_bytes ? cfg->host_arena_bytes : (size_t(1) << 30);
+  int rc = KF_OK;
+  if (ctx->budget && ctx->allocated + dbytes > ctx->budget) rc = KF_ENOMEM;
+  if (!rc && cudaMalloc(&sv->dmem, dbytes) != cudaSuccess) rc = KF_ENOMEM;
+  if (!rc && cudaMalloc(&sv->d_table, sizeof(BuildSlot) * kRing * KF_MAX_SLOTS) != cudaSuccess) rc = KF_ENOMEM;
+  if (!rc && cudaHostAlloc(reinterpret_cast<void**>(&sv->hmem), hbytes, cudaHostAllocDefault) != cudaSuccess)
+    rc = KF_ENOMEM;
+  if (!rc && cudaHostAlloc(reinterpret_cast<void**>(&sv->h_table), sizeof(BuildSlot) * kRing * KF_MAX_SLOTS,
+                           cudaHostAllocDefault) != cudaSuccess)
+    rc = KF_ENOMEM;
+  if (!rc && cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking) != cudaSuccess) rc = KF_ECUDA;
+  for (int i = 0; i < kRing && !rc; ++i)
+    if (cudaEventCreateWithFlags(&sv->iter_ev[i], cudaEventDisableTiming) != cudaSuccess) rc = KF_ECUDA;
+  if (rc) {
+    cudaGetLastError();
+    if (sv->dmem) cudaFree(sv->dmem);
+    if (sv->d_table) cudaFree(sv->d_table);
+    if (sv->hmem) cudaFreeHost(sv->hmem);
+    if (sv->h_table) cudaFreeHost(sv->h_table);
+    if (sv->stream) cudaStreamDestroy(sv->stream);
+    for (int i = 0; i < kRing; ++i)
+      if (sv->iter_ev[i]) cudaEventDestroy(sv->iter_ev[i]);
+    delete sv;
+    return rc;
+  }
+  sv->darena.reset(dbytes);
+  sv->harena.reset(hbytes);
+  sv->stats.device_arena_bytes = dbytes;
+  ctx->allocated += dbytes;
+  ctx->serve = sv;
+  sv->thread = std::thread(scheduler, sv);
+  return KF_OK;
+}
+
+int kf_serve_stop(kf_ctx* ctx) {
+  if (!ctx || !ctx->serve) return KF_EINVAL;
+  kf_serve_shutdown_internal(ctx);
+  return KF_OK;
+}
+
+int kf_submit(kf_ctx* ctx, const kf_event* ev, uint64_t* ticket) {
+  if (!ctx || !ev || !ticket) return KF_EINVAL;
+  Serve* sv = ctx->serve;
+  if (!sv) return KF_EINVAL;
+  const int ns = sv->cfg.n_seed_layers, Lb = sv->cfg.n_build_layers;
+  const int64_t n = ev->n_seeds;
+  if (n < 1 || !ev->seed_par || !ev->seed_cov || !ev->seed_charge || !ev->seed_hits || !ev->layer_off)
+    return KF_EINVAL;
+  if (ev->layer_off[0] != 0) return KF_EINVAL;
+  for (int l = 0; l < Lb; ++l) {
+    const int64_t c = ev->layer_off[l + 1] - ev->layer_off[l];
+    if (c < 0 || c > KF_MAX_HITS_PER_SEGMENT) return KF_EINVAL;
+  }
+  const int64_t nh = ev->layer_off[Lb];
+  if (nh > 0 && !ev->layer_xyz) return KF_EINVAL;
+  auto req = std::make_unique<Request>();
+  req->lay.make(n, nh, ns, Lb);
+  const EventLayout& L = req->lay;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->cuda_error) return KF_ECUDA;
+    if (L.d_total > sv->darena.size() || L.h_in_total + L.h_out_total + 512 > sv->harena.size()) return KF_ENOMEM;
+    if (int(sv->queue.size()) >= sv->cfg.max_queue) return KF_EAGAIN;
+    if (!sv->harena.alloc(L.h_in_total, &req->h_in_off)) return KF_EAGAIN;
+    if (!sv->harena.alloc(L.h_out_total, &req->h_out_off)) {
+      sv->harena.release(req->h_in_off, L.h_in_total);
+      return KF_EAGAIN;
+    }
+    req->has_in = req->has_out = true;
+  }
+  // stage the event in its pinned input block (layout mirrors the device block)
+  char* h = sv->hmem + req->h_in_off;
+  std::memcpy(h + L.h_par, ev->seed_par, 6 * n * 4);
+  std::memcpy(h + L.h_cov, ev->seed_cov, 21 * n * 4);
+  std::memcpy(h + L.h_q, ev->seed_charge, n);
+  std::memcpy(h + L.h_shits, ev->seed_hits, size_t(ns) * 3 * n * 4);
+  if (ev->seed_valid)
+    std::memcpy(h + L.h_sval, ev->seed_valid, size_t(ns) * n);
+  else
+    std::memset(h + L.h_sval, 1, size_t(ns) * n);
+  if (nh > 0) std::memcpy(h + L.h_xyz, ev->layer_xyz, size_t(3) * nh * 4);
+  std::memcpy(h + L.h_segoff, ev->layer_off, size_t(Lb + 1) * 8);
+  const int64_t sseg[2] = {0, n};  // seed segment, right after the layer offsets (padding room)
+  std::memcpy(h + L.h_segoff + size_t(Lb + 1) * 8, sseg, sizeof sseg);
+  cudaSetDevice(ctx->device);
+  if (cudaEventCreateWithFlags(&req->done, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    std::lock_guard<std::mutex> lk(sv->mu);
+    release_locked(sv, req.get());
+    sv->harena.release(req->h_out_off, L.h_out_total);
+    return KF_ECUDA;
+  }
+  req->t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    req->ticket = sv->next_ticket++;
+    *ticket = req->ticket;
+    sv->queue.push_back(req.get());
+    sv->stats.submitted++;
+    sv->all.emplace(req->ticket, std::move(req));
+  }
+  sv->cv.notify_all();
+  return KF_OK;
+}
+
+int kf_poll(kf_ctx* ctx, uint64_t ticket, kf_event_result* out, int64_t timeout_us) {
+  if (!ctx || !ctx->serve || !out) return KF_EINVAL;
+  Serve* sv = ctx->serve;
+  std::unique_lock<std::mutex> lk(sv->mu);
+  auto it = sv->all.find(ticket);
+  if (it == sv->all.end()) return KF_EINVAL;
+  Request* r = it->second.get();
+  auto ready = [&] { return r->state == kDone || r->state == kFailed; };
+  if (!ready()) {
+    if (timeout_us == 0) return KF_ETIMEDOUT;
+    if (timeout_us < 0)
+      sv->done_cv.wait(lk, ready);
+    else if (!sv->done_cv.wait_for(lk, std::chrono::microseconds(timeout_us), ready))
+      return KF_ETIMEDOUT;
+  }
+  if (r->state == kFailed) {
+    release_locked(sv, r);
+    if (r->has_out) sv->harena.release(r->h_out_off, r->lay.h_out_total);
+    r->has_out = false;
+    if (r->done) cudaEventDestroy(r->done);
+    sv->all.erase(it);
+    return KF_ECUDA;
+  }
+  const EventLayout& L = r->lay;
+  const char* o = sv->hmem + r->h_out_off;
+  const int64_t n = L.n;
+  if (out->best_par) std::memcpy(out->best_par, o + L.o_par, 6 * n * 4);
+  if (out->best_cov) std::memcpy(out->best_cov, o + L.o_cov, 21 * n * 4);
+  if (out->chi2_tot) std::memcpy(out->chi2_tot, o + L.o_chi, n * 4);
+  if (out->n_hits) std::memcpy(out->n_hits, o + L.o_nh, n * 4);
+  if (out->status) std::memcpy(out->status, o + L.o_st, n * 4);
+  if (out->hit_idx) std::memcpy(out->hit_idx, o + L.o_hit, size_t(L.Lb) * n * 4);
+  out->latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+  out->queued_ms = std::chrono::duration<double, std::milli>(r->t_admit - r->t_submit).count();
+  release_locked(sv, r);
+  sv->harena.release(r->h_out_off, L.h_out_total);
+  r->has_out = false;
+  if (r->done) cudaEventDestroy(r->done);
+  sv->all.erase(it);
+  return KF_OK;
+}
+
+int kf_cancel(kf_ctx* ctx, uint64_t ticket) {
+  if (!ctx || !ctx->serve) return KF_EINVAL;
+  Serve* sv = ctx->serve;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->all.find(ticket);
+  if (it == sv->all.end()) return KF_EINVAL;
+  Request* r = it->second.get();
+  if (r->state != kQueued) return KF_EAGAIN;
+  sv->queue.erase(std::remove(sv->queue.begin(), sv->queue.end(), r), sv->queue.end());
+  release_locked(sv, r);
+  if (r->has_out) sv->harena.release(r->h_out_off, r->lay.h_out_total);
+  if (r->done) cudaEventDestroy(r->done);
+  sv->stats.cancelled++;
+  sv->all.erase(it);
+  return KF_OK;
+}
+
+int kf_serve_stats_get(kf_ctx* ctx, kf_serve_stats* out) {
+  if (!ctx || !ctx->serve || !out) return KF_EINVAL;
+  Serve* sv = ctx->serve;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  *out = sv->stats;
+  out->device_arena_peak = sv->darena.peak();
+  out->resident = int(sv->resident.size());
+  out->queued = int(sv->queue.size());
+  return KF_OK;
+}
+
+}  // extern "C"

@@ -64,6 +64,32 @@ class kf_build_result(C.Structure):
                 ("cand_chi2_tot", C.c_void_p), ("cand_n_hits", C.c_void_p)]
 
 
+class kf_serve_config(C.Structure):
+    _fields_ = [("n_seed_layers", C.c_int32), ("n_build_layers", C.c_int32), ("max_cands", C.c_int32),
+                ("max_slots", C.c_int32), ("max_queue", C.c_int32), ("device_arena_bytes", C.c_size_t),
+                ("host_arena_bytes", C.c_size_t)]
+
+
+class kf_event(C.Structure):
+    _fields_ = [("n_seeds", C.c_int32), ("seed_par", C.c_void_p), ("seed_cov", C.c_void_p),
+                ("seed_charge", C.c_void_p), ("seed_hits", C.c_void_p), ("seed_valid", C.c_void_p),
+                ("layer_xyz", C.c_void_p), ("layer_off", C.c_void_p)]
+
+
+class kf_event_result(C.Structure):
+    _fields_ = [("best_par", C.c_void_p), ("best_cov", C.c_void_p), ("chi2_tot", C.c_void_p),
+                ("n_hits", C.c_void_p), ("status", C.c_void_p), ("hit_idx", C.c_void_p),
+                ("latency_ms", C.c_double), ("queued_ms", C.c_double)]
+
+
+class kf_serve_stats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("admitted", C.c_uint64), ("completed", C.c_uint64),
+                ("cancelled", C.c_uint64), ("iterations", C.c_uint64), ("step_launches", C.c_uint64),
+                ("resident", C.c_int32), ("queued", C.c_int32), ("max_resident", C.c_int32),
+                ("device_arena_bytes", C.c_size_t), ("device_arena_peak", C.c_size_t)]
+
+
+MAX_SLOTS = 32  # KF_MAX_SLOTS
 BIN_ETA, BIN_PHI, BIN_ETA_MAX = 64, 256, 1.5  # KF_BIN_ETA, KF_BIN_PHI, KF_BIN_ETA_MAX
 NBINS = BIN_ETA * BIN_PHI
 
@@ -90,6 +116,12 @@ def lib() -> C.CDLL:
         L.kf_fit_f64.argtypes = [vp, C.POINTER(kf_tracks_f64), C.POINTER(kf_track_hits), C.POINTER(kf_tracks_f64),
                                  vp, vp, C.POINTER(i64), i32, vp]
         L.kf_bin_hits.argtypes = [vp, C.POINTER(kf_layer_hits), C.POINTER(kf_layer_hit_bins), vp]
+        L.kf_serve_start.argtypes = [vp, C.POINTER(kf_serve_config)]
+        L.kf_serve_stop.argtypes = [vp]
+        L.kf_submit.argtypes = [vp, C.POINTER(kf_event), C.POINTER(C.c_uint64)]
+        L.kf_poll.argtypes = [vp, C.c_uint64, C.POINTER(kf_event_result), C.c_int64]
+        L.kf_cancel.argtypes = [vp, C.c_uint64]
+        L.kf_serve_stats_get.argtypes = [vp, C.POINTER(kf_serve_stats)]
         L.kf_build.argtypes = [vp, C.POINTER(kf_tracks), vp, C.POINTER(kf_layer_hit_bins), i32,
                                C.POINTER(kf_build_result), vp]
         _lib = L
@@ -290,3 +322,61 @@ def kf_build(ctx, seeds: Tracks, seed_off, bins: HitBins, max_cands: int, out: B
     s, b, o = seeds.abi(), bins.abi(), out.abi()
     _check(lib().kf_build(_h(ctx), C.byref(s), _ptr(seed_off), C.byref(b), int(max_cands), C.byref(o),
                           _stream(stream)), "kf_build", _h(ctx))
+
+
+# --------------------------------------------------------------------------- serving
+
+
+def kf_serve_start(ctx, n_seed_layers=3, n_build_layers=7, max_cands=6, max_slots=MAX_SLOTS, max_queue=1024,
+                   device_arena_bytes=0, host_arena_bytes=0):
+    cfg = kf_serve_config(n_seed_layers, n_build_layers, max_cands, max_slots, max_queue, device_arena_bytes,
+                          host_arena_bytes)
+    _check(lib().kf_serve_start(_h(ctx), C.byref(cfg)), "kf_serve_start", _h(ctx))
+
+
+def kf_serve_stop(ctx):
+    _check(lib().kf_serve_stop(_h(ctx)), "kf_serve_stop")
+
+
+def _np_ptr(a):
+    return None if a is None else C.c_void_p(a.ctypes.data)
+
+
+def kf_submit(ctx, event: dict) -> int:
+    """event: numpy host arrays seed_par [6, n] f32, seed_cov [21, n] f32,
+    seed_charge [n] i8, seed_hits [Ls, 3, n] f32, seed_valid [Ls, n] u8 or None,
+    layer_xyz [3, n_hits] f32, layer_off [Lb + 1] i64. Returns the ticket.
+    Raises KfError (code KF_EAGAIN when the queue or host arena is full)."""
+    import numpy as np
+    arrs = {k: (None if event.get(k) is None else np.ascontiguousarray(event[k])) for k in
+            ("seed_par", "seed_cov", "seed_charge", "seed_hits", "seed_valid", "layer_xyz", "layer_off")}
+    ev = kf_event(int(arrs["seed_par"].shape[1]), *[_np_ptr(arrs[k]) for k in
+                                                      ("seed_par", "seed_cov", "seed_charge", "seed_hits",
+                                                       "seed_valid", "layer_xyz", "layer_off")])
+    t = C.c_uint64()
+    _check(lib().kf_submit(_h(ctx), C.byref(ev), C.byref(t)), "kf_submit")
+    return t.value
+
+
+def kf_poll(ctx, ticket: int, n_seeds: int, n_build_layers: int, timeout_us: int = -1, want_cov: bool = False):
+    """Returns a dict of numpy results, or raises KfError (KF_ETIMEDOUT if not done)."""
+    import numpy as np
+    out = dict(best_par=np.empty((6, n_seeds), np.float32),
+               best_cov=np.empty((21, n_seeds), np.float32) if want_cov else None,
+               chi2_tot=np.empty(n_seeds, np.float32), n_hits=np.empty(n_seeds, np.int32),
+               status=np.empty(n_seeds, np.int32), hit_idx=np.empty((n_build_layers, n_seeds), np.int32))
+    r = kf_event_result(*[_np_ptr(out[k]) for k in ("best_par", "best_cov", "chi2_tot", "n_hits", "status",
+                                                      "hit_idx")], 0.0, 0.0)
+    _check(lib().kf_poll(_h(ctx), C.c_uint64(ticket), C.byref(r), int(timeout_us)), "kf_poll")
+    out["latency_ms"], out["queued_ms"] = r.latency_ms, r.queued_ms
+    return out
+
+
+def kf_cancel(ctx, ticket: int):
+    _check(lib().kf_cancel(_h(ctx), C.c_uint64(ticket)), "kf_cancel")
+
+
+def kf_serve_stats_get(ctx) -> dict:
+    st = kf_serve_stats()
+    _check(lib().kf_serve_stats_get(_h(ctx), C.byref(st)), "kf_serve_stats_get")
+    return {f: getattr(st, f) for f, _ in kf_serve_stats._fields_}

@@ -1,0 +1,150 @@
+"""Serving (kf_serve_start / kf_submit / kf_poll): continuous batching of
+build requests. Each event's result is bitwise the same alone, in a mix of
+uneven events sharing build-step launches, and from the batch kf_build;
+admission waits for device memory; failures are reported on the host."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from buildutil import gpu_build
+from paper_1605_05508_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+
+def _event(seed, n, **kw):
+    b = S.make_build_batch(seed, 1, n, **kw)
+    ev = dict(seed_par=b.seeds.par, seed_cov=b.seeds.cov, seed_charge=b.seeds.charge, seed_hits=b.fit_hits.xyz,
+              seed_valid=b.fit_hits.valid, layer_xyz=b.layer_xyz, layer_off=b.layer_off)
+    return b, ev
+
+
+def _poll_all(kf, ctx, tickets, sizes, timeout_us=60_000_000):
+    return [kf.kf_poll(ctx, t, n, 7, timeout_us) for t, n in zip(tickets, sizes)]
+
+
+SIZES = [700, 3100, 150, 5000, 1200, 60, 2300, 900]
+
+
+def test_alone_equals_mix_equals_batch_build(cuda_ctx_factory):
+    from paper_1605_05508_gb300 import kf
+    det = S.barrel()
+    ctx = cuda_ctx_factory(det.radii)
+    evs = [_event(100 + i, n) for i, n in enumerate(SIZES)]
+    kf.kf_serve_start(ctx, 3, 7, 6, max_slots=32, device_arena_bytes=1 << 30, host_arena_bytes=1 << 29)
+    alone = []
+    for (b, ev), n in zip(evs, SIZES):
+        t = kf.kf_submit(ctx, ev)
+        alone.append(kf.kf_poll(ctx, t, n, 7, 60_000_000))
+    # the mix: every event in flight at once, sharing step launches
+    tickets = [kf.kf_submit(ctx, ev) for _, ev in evs]
+    mix = _poll_all(kf, ctx, tickets, SIZES)
+    st = kf.kf_serve_stats_get(ctx)
+    kf.kf_serve_stop(ctx)
+    assert st["completed"] == 2 * len(SIZES) and st["max_resident"] >= 2
+    for a, m in zip(alone, mix):
+        for k in ("best_par", "chi2_tot", "n_hits", "status", "hit_idx"):
+            np.testing.assert_array_equal(a[k], m[k], err_msg=k)
+    # the batch API on the same events gives the same bits
+    for (b, _), a in zip(evs, alone):
+        g = gpu_build(ctx, b, 6, want_cands=False)
+        np.testing.assert_array_equal(g["hits"].T, a["hit_idx"])
+        np.testing.assert_array_equal(g["nhits"], a["n_hits"])
+        np.testing.assert_array_equal(g["chi2"].astype(np.float32), a["chi2_tot"])
+
+
+def test_admission_waits_for_device_memory(cuda_ctx_factory):
+    """An arena that holds about one large event at a time: events queue,
+    are admitted as memory frees, and all complete with unchanged results."""
+    from paper_1605_05508_gb300 import kf
+    det = S.barrel()
+    ctx = cuda_ctx_factory(det.radii)
+    sizes = [4000, 4000, 300, 4000, 300]
+    evs = [_event(300 + i, n) for i, n in enumerate(sizes)]
+    kf.kf_serve_start(ctx, 3, 7, 6, max_slots=8, device_arena_bytes=24 << 20, host_arena_bytes=1 << 28)
+    tickets = [kf.kf_submit(ctx, ev) for _, ev in evs]
+    mix = _poll_all(kf, ctx, tickets, sizes)
+    st = kf.kf_serve_stats_get(ctx)
+    kf.kf_serve_stop(ctx)
+    assert st["completed"] == len(sizes)
+    assert st["device_arena_peak"] <= 24 << 20
+    assert max(r["queued_ms"] for r in mix) > 0.0
+    kf.kf_serve_start(ctx, 3, 7, 6, device_arena_bytes=1 << 30, host_arena_bytes=1 << 28)
+    for (_, ev), n, m in zip(evs, sizes, mix):
+        a = kf.kf_poll(ctx, kf.kf_submit(ctx, ev), n, 7, 60_000_000)
+        np.testing.assert_array_equal(a["hit_idx"], m["hit_idx"])
+    kf.kf_serve_stop(ctx)
+
+
+def test_oversized_event_cancel_timeout_and_bad_arguments(cuda_ctx_factory):
+    from paper_1605_05508_gb300 import kf
+    det = S.barrel()
+    ctx = cuda_ctx_factory(det.radii)
+    kf.kf_serve_start(ctx, 3, 7, 6, max_slots=1, device_arena_bytes=16 << 20, host_arena_bytes=1 << 28)
+    _, big = _event(400, 20000)
+    with pytest.raises(kf.KfError) as e:
+        kf.kf_submit(ctx, big)  # needs more than the whole device arena: never admissible
+    assert e.value.code == kf.KF_ENOMEM
+    _, ev1 = _event(401, 3000)
+    _, ev2 = _event(402, 50)
+    t1 = kf.kf_submit(ctx, ev1)
+    t2 = kf.kf_submit(ctx, ev2)
+    t3 = kf.kf_submit(ctx, ev2)
+    # one slot: t3 waits behind t1 and t2 and can be cancelled while queued
+    rc = None
+    try:
+        kf.kf_cancel(ctx, t3)
+        rc = kf.KF_OK
+    except kf.KfError as err:
+        rc = err.code
+    assert rc in (kf.KF_OK, kf.KF_EAGAIN)
+    try:
+        kf.kf_poll(ctx, t2, 50, 7, 0)  # not waiting: may or may not be done
+    except kf.KfError as err:
+        assert err.code == kf.KF_ETIMEDOUT
+        kf.kf_poll(ctx, t2, 50, 7, 60_000_000)  # the ticket stayed valid
+    kf.kf_poll(ctx, t1, 3000, 7, 60_000_000)
+    if rc == kf.KF_EAGAIN:
+        kf.kf_poll(ctx, t3, 50, 7, 60_000_000)
+    with pytest.raises(kf.KfError) as e:
+        kf.kf_poll(ctx, 987654321, 1, 7, 0)
+    assert e.value.code == kf.KF_EINVAL
+    bad = dict(ev2)
+    bad["layer_off"] = ev2["layer_off"][::-1].copy()  # decreasing offsets
+    with pytest.raises(kf.KfError) as e:
+        kf.kf_submit(ctx, bad)
+    assert e.value.code == kf.KF_EINVAL
+    st = kf.kf_serve_stats_get(ctx)
+    kf.kf_serve_stop(ctx)
+    assert st["max_resident"] == 1
+
+
+def test_concurrent_submitters_and_pollers(cuda_ctx_factory):
+    """Several host threads submit and poll at once (the API is thread-safe)."""
+    from paper_1605_05508_gb300 import kf
+    det = S.barrel()
+    ctx = cuda_ctx_factory(det.radii)
+    evs = [_event(500 + i, n) for i, n in enumerate([400, 900, 200, 1500])]
+    kf.kf_serve_start(ctx, 3, 7, 6, device_arena_bytes=1 << 30, host_arena_bytes=1 << 29)
+    ref = [kf.kf_poll(ctx, kf.kf_submit(ctx, ev), ev["seed_par"].shape[1], 7, 60_000_000) for _, ev in evs]
+    errors = []
+
+    def worker(w):
+        try:
+            for rep in range(3):
+                i = (w + rep) % len(evs)
+                ev = evs[i][1]
+                r = kf.kf_poll(ctx, kf.kf_submit(ctx, ev), ev["seed_par"].shape[1], 7, 60_000_000)
+                if not np.array_equal(r["hit_idx"], ref[i]["hit_idx"]):
+                    errors.append((w, rep))
+        except Exception as ex:  # noqa: BLE001
+            errors.append(repr(ex))
+    th = [threading.Thread(target=worker, args=(w,)) for w in range(4)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    kf.kf_serve_stop(ctx)
+    assert not errors, errors
