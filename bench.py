@@ -485,7 +485,7 @@ def serve_leg(a, kf, dev, rank):
         def poller():
             for i in range(M):
                 ready.acquire()
-                r = kf.kf_poll(ctx, tickets[i], pool[i % len(pool)]["seed_par"].shape[1], 7, -1)
+                r = kf.kf_poll(ctx, tickets[i], pool[i % len(pool)]["seed_par"].shape[1], 7, 120_000_000)
                 lat[i] = r["latency_ms"]
         th = threading.Thread(target=poller)
         th.start()
@@ -504,10 +504,10 @@ def serve_leg(a, kf, dev, rank):
 
     # warm-up, then the serial baseline: one event at a time, no overlap
     for ev in pool[:4]:
-        kf.kf_poll(ctx, submit(ev), ev["seed_par"].shape[1], 7, -1)
+        kf.kf_poll(ctx, submit(ev), ev["seed_par"].shape[1], 7, 120_000_000)
     t0 = time.perf_counter()
     for ev in pool:
-        kf.kf_poll(ctx, submit(ev), ev["seed_par"].shape[1], 7, -1)
+        kf.kf_poll(ctx, submit(ev), ev["seed_par"].shape[1], 7, 120_000_000)
     serial = len(pool) / (time.perf_counter() - t0)
     sat, lat_sat = run(np.zeros(M))
     runs = []
