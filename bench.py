@@ -279,6 +279,9 @@ def run_ours(a):
         del seeds, hits, out, chi2, status
         torch.cuda.empty_cache()
         line["build"] = build_leg(a, kf, torch, dev, stream, rank, world, dist)
+    if not a.no_extras:
+        torch.cuda.empty_cache()
+        line["precision"] = precision_leg(a, kf, torch, dev, stream, rank)
     if not a.no_serve:
         torch.cuda.empty_cache()
         line["serving"] = serve_leg(a, kf, dev, rank)
@@ -443,6 +446,61 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist):
         res["cpu_baseline"] = {"value": m * Lb / dtc, "unit": "seed-layer steps/s", "cores": cores, "kind": "oracle",
                                "sample": f"first {m} seeds of event 0 x {Lb} layers, N = 6, all-hits chi2 scan "
                                          f"(the oracle bins nothing), {cores} OpenMP threads, {dtc:.2f} s wall"}
+    ctx.close()
+    return res
+
+
+def precision_leg(a, kf, torch, dev, stream, rank):
+    """1 M tracks, 50 % pT U[0.2, 1] and 50 % U[10, 100] GeV, 20 layers to
+    r = 80 cm: FP32 Joseph (kf_fit) vs S^-1 and downdate in FP64
+    (kf_fit_mixed); PD failures over all tracks, errors vs the oracle on a
+    sample."""
+    from paper_1605_05508_gb300 import synth as S
+    import oracle as O
+    det = S.barrel(20)
+    n = 1_000_000
+    ev = S.make_fit_batch(a.seed + 5 + 1000 * rank, n, det=det, pt_mix=[(0.5, (0.2, 1.0)), (0.5, (10.0, 100.0))],
+                          keep_truth=False)
+    D = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    ctx = kf.Context(det.radii, det.bz, det.sigma_xy, det.sigma_z, device=dev.index)
+    s = kf.Tracks(D(ev.seeds.par), D(ev.seeds.cov), D(ev.seeds.charge))
+    h = kf.TrackHits(D(ev.hits.xyz), D(ev.hits.valid))
+    out = kf.Tracks(torch.empty((6, n), device=dev), torch.empty((21, n), device=dev), s.charge,
+                    torch.empty((3, n), device=dev))
+    chi2 = torch.empty((20, n), device=dev)
+    st = torch.empty(n, dtype=torch.int32, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    idx = np.sort(np.random.default_rng(3).choice(n, 5000, replace=False))
+    r = O.fit(ev.seeds.par[:, idx], ev.seeds.cov[:, idx], ev.seeds.charge[idx], ev.hits.xyz[:, :, idx],
+              ev.hits.valid[:, idx], [float(np.float32(x)) for x in det.radii], float(np.float32(det.bz)),
+              float(np.float32(det.sigma_xy)), float(np.float32(det.sigma_z)))
+    res = {"workload": f"{n} tracks, 50% pT U[0.2,1] + 50% U[10,100] GeV, 20 layers r=4..80 cm",
+           "oracle_sample_tracks": len(idx)}
+    for name, fn in (("fp32_joseph", kf.kf_fit), ("fp64_inverse_downdate", kf.kf_fit_mixed)):
+        for _ in range(2):
+            fn(ctx, s, h, out, chi2, st, stream)
+        e0.record(stream)
+        for _ in range(5):
+            fn(ctx, s, h, out, chi2, st, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 5
+        stat = st.cpu().numpy()
+        c2 = chi2[:, torch.from_numpy(idx).to(dev)].double().cpu().numpy()
+        par = out.par[:, torch.from_numpy(idx).to(dev)].double().cpu().numpy().T
+        par[:, :3] += out.par_lo[:, torch.from_numpy(idx).to(dev)].double().cpu().numpy().T
+        same = stat[idx] == r["status"]
+        both = (c2 >= 0) & (r["chi2"] >= 0) & same[None]
+        ce = np.abs(c2 - r["chi2"])[both]
+        pscale = np.concatenate([np.full((same.sum(), 3), 80.0),
+                                 np.repeat(np.linalg.norm(r["par"][same, 3:], axis=1)[:, None], 3, axis=1)], axis=1)
+        res[name] = {"ms_per_step": ms, "track_layer_steps_per_s": n * 20 / (ms / 1e3),
+                     "not_pd": int(np.count_nonzero(stat & kf.ST_NOT_PD)),
+                     "stopped_loopers": int(np.count_nonzero(stat & kf.ST_STOPPED)),
+                     "status_mismatch_vs_oracle": int((~same).sum()),
+                     "param_rel_err_max": float((np.abs(par[same] - r["par"][same]) / pscale).max()),
+                     "chi2_abs_err_max": float(ce.max()), "chi2_abs_err_p99": float(np.quantile(ce, 0.99)),
+                     "chi2_frac_above_1e-3": float((ce > 1e-3).mean())}
     ctx.close()
     return res
 

@@ -124,6 +124,12 @@ int kf_fit(kf_ctx *ctx, const kf_tracks *seeds, const kf_track_hits *hits, kf_tr
 int kf_fit_fused(kf_ctx *ctx, const kf_tracks *seeds, const kf_track_hits *hits, kf_tracks *out,
                  float *chi2, int32_t *status, void *stream);
 
+/* kf_fit_fused with mixed precision: propagation, transport and residuals in
+ * FP32 (position pairs), the 3x3 inverse of S = H C' H^T + V, the gain and the
+ * Joseph covariance downdate in FP64.  The precision comparison form. */
+int kf_fit_mixed(kf_ctx *ctx, const kf_tracks *seeds, const kf_track_hits *hits, kf_tracks *out,
+                 float *chi2, int32_t *status, void *stream);
+
 /* The plain double-precision form of the same fit: the same steps in FP64,
  * launched once per event and per layer (events = contiguous track ranges
  * event_off[e] .. event_off[e+1], host array [n_events+1]).

@@ -228,8 +228,21 @@ int kf_fit(kf_ctx* ctx, const kf_tracks* seeds, const kf_track_hits* hits, kf_tr
   return KF_OK;
 }
 
+static int fit_fused_impl(kf_ctx* ctx, const kf_tracks* seeds, const kf_track_hits* hits, kf_tracks* out, float* chi2,
+                          int32_t* status, void* stream, bool upd64);
+
 int kf_fit_fused(kf_ctx* ctx, const kf_tracks* seeds, const kf_track_hits* hits, kf_tracks* out, float* chi2,
                  int32_t* status, void* stream) {
+  return fit_fused_impl(ctx, seeds, hits, out, chi2, status, stream, false);
+}
+
+int kf_fit_mixed(kf_ctx* ctx, const kf_tracks* seeds, const kf_track_hits* hits, kf_tracks* out, float* chi2,
+                 int32_t* status, void* stream) {
+  return fit_fused_impl(ctx, seeds, hits, out, chi2, status, stream, true);
+}
+
+static int fit_fused_impl(kf_ctx* ctx, const kf_tracks* seeds, const kf_track_hits* hits, kf_tracks* out, float* chi2,
+                          int32_t* status, void* stream, bool upd64) {
   int rc = check_fit(ctx, seeds, hits, out);
   if (rc) return rc;
   const int64_t n = seeds->n;
@@ -254,7 +267,7 @@ int kf_fit_fused(kf_ctx* ctx, const kf_tracks* seeds, const kf_track_hits* hits,
   a.v0 = a.v1 = ctx->cfg.sigma_xy_cm * ctx->cfg.sigma_xy_cm;
   a.v2 = ctx->cfg.sigma_z_cm * ctx->cfg.sigma_z_cm;
   for (int l = 0; l < hits->n_layers; ++l) a.R[l] = ctx->radius[l];
-  KF_CUDA_TRY(ctx, launch_fit_fused(a, fit_grid(ctx, n), static_cast<cudaStream_t>(stream)));
+  KF_CUDA_TRY(ctx, launch_fit_fused(a, fit_grid(ctx, n), static_cast<cudaStream_t>(stream), upd64));
   return KF_OK;
 }
 

@@ -58,20 +58,25 @@ __device__ __forceinline__ bool pd5(const T p[6], const T C[21]) {
 }
 
 // One propagate + (optional) update step of one track.  Returns the status
-// bits raised; writes chi2 (-1 when no update).
-template <typename T, int NEWTON, bool EXT>
+// bits raised; writes chi2 (-1 when no update).  UPD64: S^-1 and the
+// covariance downdate in FP64 (single-precision state only).
+template <typename T, int NEWTON, bool EXT, bool UPD64 = false>
 __device__ __forceinline__ int32_t track_step(T p[6], T lo[3], T C[21], T a, T R, bool has_hit,
                                               T m0, T m1, T m2, T v0, T v1, T v2, T& chi2) {
   chi2 = T(-1);
   const int st = kf::propagate<T, NEWTON, EXT>(p, lo, C, a, R);
   if (st) return st;
   if (!has_hit) return kf::ST_NO_HIT;
-  T Si[6];
-  kf::inverse_S(C, v0, v1, v2, Si);
   T r0, r1, r2;
   kf::residual<T, EXT>(p, lo, m0, m1, m2, r0, r1, r2);
-  chi2 = kf::chi2_of(r0, r1, r2, Si);
-  kf::kalman_update<T, EXT>(p, lo, C, Si, r0, r1, r2, v0, v1, v2);
+  if constexpr (UPD64) {
+    chi2 = kf::kalman_update_f64(p, lo, C, r0, r1, r2, v0, v1, v2);
+  } else {
+    T Si[6];
+    kf::inverse_S(C, v0, v1, v2, Si);
+    chi2 = kf::chi2_of(r0, r1, r2, Si);
+    kf::kalman_update<T, EXT>(p, lo, C, Si, r0, r1, r2, v0, v1, v2);
+  }
   return 0;
 }
 
@@ -113,6 +118,7 @@ __global__ void __launch_bounds__(kFitThreads) fit_layer_kernel(const FitLayerAr
   }
 }
 
+template <bool UPD64>
 __global__ void __launch_bounds__(kFitThreads) fit_fused_kernel(const FitFusedArgs A) {
   const int64_t n = A.n;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
@@ -131,8 +137,8 @@ __global__ void __launch_bounds__(kFitThreads) fit_fused_kernel(const FitFusedAr
       if (!(st & KF_ST_STOPPED)) {
         const float* h = A.hits + int64_t(l) * 3 * n;
         const bool has_hit = A.valid ? A.valid[int64_t(l) * n + i] != 0 : true;
-        st |= track_step<float, kNewtonF32, true>(p, lo, C, a, A.R[l], has_hit, h[i], h[n + i], h[2 * n + i],
-                                                  A.v0, A.v1, A.v2, chi2);
+        st |= track_step<float, kNewtonF32, true, UPD64>(p, lo, C, a, A.R[l], has_hit, h[i], h[n + i],
+                                                         h[2 * n + i], A.v0, A.v1, A.v2, chi2);
       }
       if (A.chi2) A.chi2[int64_t(l) * n + i] = chi2;
     }
@@ -199,8 +205,11 @@ cudaError_t launch_fit_layer(const FitLayerArgs& a, int grid, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_fit_fused(const FitFusedArgs& a, int grid, cudaStream_t st) {
-  fit_fused_kernel<<<grid, kFitThreads, 0, st>>>(a);
+cudaError_t launch_fit_fused(const FitFusedArgs& a, int grid, cudaStream_t st, bool upd64) {
+  if (upd64)
+    fit_fused_kernel<true><<<grid, kFitThreads, 0, st>>>(a);
+  else
+    fit_fused_kernel<false><<<grid, kFitThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 

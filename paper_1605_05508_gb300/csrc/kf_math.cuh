@@ -428,4 +428,33 @@ KF_HD void kalman_update(T p[6], T lo[3], T C[21], const T Si[6], T r0, T r1, T 
     }
 }
 
+// Mixed precision: the same update with S^-1, the gain and the Joseph
+// covariance downdate in FP64 (inputs and outputs stay float; the position
+// correction is added to the hi + lo pair).  Returns the chi2 increment.
+KF_HD float kalman_update_f64(float p[6], float lo[3], float C[21], float r0, float r1, float r2, float v0, float v1,
+                              float v2) {
+  double Cd[21];
+#pragma unroll
+  for (int e = 0; e < 21; ++e) Cd[e] = C[e];
+  double Si[6];
+  inverse_S<double>(Cd, v0, v1, v2, Si);
+  const double c2 = chi2_of<double>(r0, r1, r2, Si);
+  double dx[6] = {0, 0, 0, 0, 0, 0}, dlo[3] = {0, 0, 0};
+  kalman_update<double, false>(dx, dlo, Cd, Si, r0, r1, r2, v0, v1, v2);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    if (i < 3) {
+      float h, e;
+      two_sum(p[i], lo[i] + float(dx[i]), h, e);
+      p[i] = h;
+      lo[i] = e;
+    } else {
+      p[i] = p[i] + float(dx[i]);
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < 21; ++e) C[e] = float(Cd[e]);
+  return float(c2);
+}
+
 }  // namespace kf

@@ -110,7 +110,7 @@ def lib() -> C.CDLL:
         L.kf_strerror.argtypes = [C.c_int]
         L.kf_strerror.restype = C.c_char_p
         L.kf_last_cuda_error.argtypes = [vp]
-        for name in ("kf_fit", "kf_fit_fused", "kf_fit_host", "kf_fit_noalloc"):
+        for name in ("kf_fit", "kf_fit_fused", "kf_fit_host", "kf_fit_noalloc", "kf_fit_mixed"):
             getattr(L, name).argtypes = [vp, C.POINTER(kf_tracks), C.POINTER(kf_track_hits), C.POINTER(kf_tracks),
                                          vp, vp, vp]
         L.kf_fit_f64.argtypes = [vp, C.POINTER(kf_tracks_f64), C.POINTER(kf_track_hits), C.POINTER(kf_tracks_f64),
@@ -238,6 +238,12 @@ def kf_fit_fused(ctx, seeds: Tracks, hits: TrackHits, out: Tracks, chi2=None, st
     s, h, o = seeds.abi(), hits.abi(), out.abi()
     _check(lib().kf_fit_fused(_h(ctx), C.byref(s), C.byref(h), C.byref(o), _ptr(chi2), _ptr(status),
                               _stream(stream)), "kf_fit_fused", _h(ctx))
+
+
+def kf_fit_mixed(ctx, seeds: Tracks, hits: TrackHits, out: Tracks, chi2=None, status=None, stream=None):
+    s, h, o = seeds.abi(), hits.abi(), out.abi()
+    _check(lib().kf_fit_mixed(_h(ctx), C.byref(s), C.byref(h), C.byref(o), _ptr(chi2), _ptr(status),
+                              _stream(stream)), "kf_fit_mixed", _h(ctx))
 
 
 def kf_fit_host(ctx, seeds: Tracks, hits: TrackHits, out: Tracks, chi2=None, status=None, stream=None):
