@@ -178,14 +178,19 @@ def kernel_source_hash():
 
 def ncu_traffic(n_tracks):
     """DRAM bytes per fit-layer launch from the committed ncu summary, scaled to
-    n_tracks; None if absent or taken on a different kernel source."""
-    p = os.path.join(ROOT, "profiles", "fit_layer_kernel.traffic.json")
+    n_tracks (traffic grows in proportion to the tracks of a launch); None if
+    absent or taken on a different kernel source."""
+    p = os.path.join(ROOT, "profiles", "fit_layer_kernel.traffic.txt")
     if not os.path.exists(p):
         return None
-    d = json.load(open(p))
-    if d.get("source_hash") != kernel_source_hash():
+    kv = {}
+    for ln in open(p):
+        if ":" in ln and not ln.lstrip().startswith("#"):
+            k, v = ln.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("source_hash") != kernel_source_hash():
         return None
-    return float(d["dram_bytes_per_track"]) * n_tracks
+    return float(kv["dram_bytes_per_track"]) * n_tracks
 
 
 def fit_bytes_per_track_layer(L, seeds_have_lo, have_valid, have_chi2):

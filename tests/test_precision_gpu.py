@@ -48,23 +48,37 @@ def test_precision_sweep_fp32_joseph_vs_fp64_update(cuda_ctx_factory):
     g32 = _run(ctx, kf, ev, kf.kf_fit)
     g64 = _run(ctx, kf, ev, kf.kf_fit_mixed)
     pt = np.hypot(ev.parts.mom[:, 0], ev.parts.mom[:, 1])
-    # PD and pulls over every track, at its last updated layer
+    # PD over every track; pulls at each track's last updated layer. A few
+    # low-pT loopers that stop near their turning radius have pulls in the
+    # hundreds (the linearised crossing breaks down there, in the oracle too),
+    # so the width is the half-distance of the 15.87 / 84.13 % quantiles.
     for g in (g32, g64):
         assert not np.any(g["status"] & kf.ST_NOT_PD)
     upd = g32["chi2"] >= 0
     last = np.where(upd.any(0), upd.shape[0] - 1 - np.argmax(upd[::-1], axis=0), -1)
     good = last >= 0
     truth_last = ev.hits.truth[last[good], np.nonzero(good)[0]]
+    pulls = {}
     for name, g in (("fp32", g32), ("mixed", g64)):
         pl = _pulls(g, truth_last, good)
+        pulls[name] = pl
         for cls, m in (("pT<1", pt[good] < 5), ("pT>10", pt[good] > 5)):
-            mu, sd = pl[m].mean(0), pl[m].std(0)
-            print(f"{name} {cls}: pull mean {np.round(mu, 3)} width {np.round(sd, 3)}")
-            assert np.all(np.abs(mu) < 0.03) and np.all(np.abs(sd - 1) < 0.03)
+            q = np.quantile(pl[m], [0.1587, 0.5, 0.8413], axis=0)
+            med, wid = q[1], (q[2] - q[0]) / 2
+            print(f"{name} {cls}: pull median {np.round(med, 3)} width {np.round(wid, 3)}")
+            assert np.all(np.abs(med) < 0.03) and np.all(np.abs(wid - 1) < 0.03)
+
     # errors against the oracle on a sample
     idx = np.sort(np.random.default_rng(2).choice(n, 15000, replace=False))
     sub = S.Seeds(ev.seeds.par[:, idx], ev.seeds.cov[:, idx], ev.seeds.charge[idx])
     r = oracle_fit(sub, ev.hits.xyz[:, :, idx], ev.hits.valid[:, idx], det)
+    # the same tracks' pulls from the oracle: the GPU forms reproduce them
+    sel = good[idx]
+    pos = np.cumsum(good) - 1
+    po = _pulls(r, truth_last[pos[idx[sel]]], sel)
+    for name in ("fp32", "mixed"):
+        pg = pulls[name][pos[idx[sel]]]
+        assert np.quantile(np.abs(pg - po), 0.99) < 0.02, name
     for name, g in (("fp32", g32), ("mixed", g64)):
         gs = {k: (v[:, idx] if k == "chi2" else v[idx]) for k, v in g.items()}
         same = gs["status"] == r["status"]
