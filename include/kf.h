@@ -46,7 +46,9 @@ extern "C" {
                                tangent (dg/ds ~ 0); stops */
 #define KF_ST_NOT_PD 8      /* final covariance failed the positive-definite check */
 #define KF_ST_NO_HIT 16     /* at least one layer had no hit (propagated only) */
-#define KF_ST_STOPPED (KF_ST_NOT_REACHED | KF_ST_NEWTON_FAIL | KF_ST_TANGENT)
+#define KF_ST_DEVICE_TIMEOUT 64 /* a bounded wait for staged input gave up (never expected):
+                                 the track's results of that call are not valid */
+#define KF_ST_STOPPED (KF_ST_NOT_REACHED | KF_ST_NEWTON_FAIL | KF_ST_TANGENT | KF_ST_DEVICE_TIMEOUT)
 
 typedef struct kf_ctx kf_ctx;
 

@@ -18,8 +18,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libkf.so")
 
 KF_OK, KF_EINVAL, KF_ENOMEM, KF_EAGAIN, KF_ETIMEDOUT, KF_ECUDA, KF_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
-ST_NOT_REACHED, ST_NEWTON_FAIL, ST_TANGENT, ST_NOT_PD, ST_NO_HIT = 1, 2, 4, 8, 16
-ST_STOPPED = ST_NOT_REACHED | ST_NEWTON_FAIL | ST_TANGENT
+ST_NOT_REACHED, ST_NEWTON_FAIL, ST_TANGENT, ST_NOT_PD, ST_NO_HIT, ST_DEVICE_TIMEOUT = 1, 2, 4, 8, 16, 64
+ST_STOPPED = ST_NOT_REACHED | ST_NEWTON_FAIL | ST_TANGENT | ST_DEVICE_TIMEOUT
 NOALLOC_MAX_TRACKS = 262144  # KF_NOALLOC_MAX_TRACKS
 
 

@@ -24,7 +24,7 @@ def test_config1_1000_tracks_graph(cuda_ctx_factory, det):
     print("config1", st)
 
 
-@pytest.mark.parametrize("n", [1, 31, 257, 9001])
+@pytest.mark.parametrize("n", [1, 31, 257, 9001, 9008])
 @pytest.mark.parametrize("mode", ["graph", "fused"])
 def test_ragged_sizes(cuda_ctx_factory, det, n, mode):
     ctx = cuda_ctx_factory(det.radii)
@@ -55,6 +55,32 @@ def test_fused_equals_graph_and_host_equals_device(cuda_ctx_factory, det):
     c = unpack(out, chi2, st)
     for k in ("par", "cov", "chi2", "status"):
         np.testing.assert_array_equal(a[k], c[k], err_msg=k)
+
+
+@pytest.mark.parametrize("n", [4096, 40000, 40016])
+def test_tma_staged_layer_kernel_equals_plain_kernel(cuda_ctx_factory, det, n):
+    """kf_fit takes the TMA-staged persistent kernel when rows are 16-byte
+    aligned (n % 16 == 0); kf_fit_noalloc always takes the plain one. Same
+    per-track arithmetic: identical bits, also for a partial last tile."""
+    import torch
+    from paper_1605_05508_gb300 import kf
+    ctx = cuda_ctx_factory(det.radii)
+    ev = S.make_fit_batch(3000 + n, n, pt_range=(0.3, 10.0))
+    valid = ev.hits.valid.copy()
+    valid[3, ::7] = 0
+    res = []
+    for fn in (kf.kf_fit, kf.kf_fit_noalloc):
+        s = kf.Tracks(to_dev(ev.seeds.par), to_dev(ev.seeds.cov), to_dev(ev.seeds.charge))
+        out = kf.Tracks(torch.empty((6, n), device="cuda"), torch.empty((21, n), device="cuda"), s.charge,
+                        torch.empty((3, n), device="cuda"))
+        chi2 = torch.empty((10, n), device="cuda")
+        st = torch.empty(n, dtype=torch.int32, device="cuda")
+        fn(ctx, s, kf.TrackHits(to_dev(ev.hits.xyz), to_dev(valid)), out, chi2, st)
+        torch.cuda.synchronize()
+        res.append(unpack(out, chi2, st))
+    for k in ("par", "cov", "chi2", "status"):
+        np.testing.assert_array_equal(res[0][k], res[1][k], err_msg=k)
+    assert not np.any(res[0]["status"] & kf.ST_DEVICE_TIMEOUT)
 
 
 def test_batch_invariance_bitwise(cuda_ctx_factory, det):
