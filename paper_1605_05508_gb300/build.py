@@ -16,9 +16,6 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-DNDEBUG",
               "--expt-relaxed-constexpr", "-I", INCLUDE]
-# the fit kernels write every fused multiply-add explicitly; no implicit
-# contraction, so their one-track and two-track forms round identically
-PER_FILE_FLAGS = {"kf_fit.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:
@@ -46,7 +43,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     for s in srcs:
         o = os.path.join(OUT_DIR, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
-        cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *PER_FILE_FLAGS.get(os.path.basename(s), []), *extra, "-c", s, "-o", o]
+        cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-c", s, "-o", o]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         procs.append((s, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)))

@@ -267,7 +267,7 @@ static int fit_fused_impl(kf_ctx* ctx, const kf_tracks* seeds, const kf_track_hi
   a.v0 = a.v1 = ctx->cfg.sigma_xy_cm * ctx->cfg.sigma_xy_cm;
   a.v2 = ctx->cfg.sigma_z_cm * ctx->cfg.sigma_z_cm;
   for (int l = 0; l < hits->n_layers; ++l) a.R[l] = ctx->radius[l];
-  KF_CUDA_TRY(ctx, launch_fit_fused(ctx, a, static_cast<cudaStream_t>(stream), upd64));
+  KF_CUDA_TRY(ctx, launch_fit_fused(a, fit_grid(ctx, n), static_cast<cudaStream_t>(stream), upd64));
   return KF_OK;
 }
 

@@ -1,24 +1,15 @@
-// kf_fit.cu -- track-fit kernels: state and covariance in registers,
-// structure-of-arrays global layout (coalesced 128-byte warp transactions
-// per component).
+// kf_fit.cu -- track-fit kernels: one thread per track, state and covariance
+// in registers, structure-of-arrays global layout (coalesced 128-byte warp
+// transactions per component).
 //
 // Track fitting is the branch-free part of Kalman-filter tracking (Cerati et
 // al., Sec. 2): with the hit set fixed, every track runs propagate + update
-// over the layers.  Forms:
-//   fit_layer_pair_kernel  one layer step over the whole batch, two tracks
-//                          per thread (paired FP32 instructions), inputs
-//                          staged tile by tile in shared memory by TMA bulk
-//                          copies; kf_fit replays one launch per layer from a
-//                          captured CUDA graph;
-//   fit_layer_kernel       the same step, one track per thread, plain loads
-//                          (batches whose rows are not 16-byte aligned, and
-//                          kf_fit_noalloc);
-//   fit_fused_pair_kernel  all layers in one launch, tracks kept in registers;
-//   fit_fused_kernel       the mixed-precision form (FP64 S^-1 and downdate);
-//   fit_f64_kernel         the plain FP64 form, per event and per layer.
-// This file is compiled without implicit multiply-add contraction: every
-// fused multiply-add is written out, so the one-track and two-track kernels
-// produce the same bits.
+// over the layers.  Three forms:
+//   fit_layer_kernel  one layer step over the whole batch (persistent
+//                     grid-stride launch; kf_fit replays one per layer from a
+//                     captured CUDA graph);
+//   fit_fused_kernel  all layers in one launch, the track held in registers;
+//   fit_f64_kernel    the plain FP64 form, launched per event and per layer.
 #include "kf_internal.h"
 #include "kf_math.cuh"
 #include "kf_tma.cuh"
@@ -67,47 +58,27 @@ __device__ __forceinline__ bool pd5(const T p[6], const T C[21]) {
   return true;
 }
 
-// One propagate + (optional) update step in the lanes of `live`.  Returns the
-// status bits raised per lane; chi2 = -1 in lanes without an update.
-template <typename T, int NEWTON, bool EXT>
-__device__ __forceinline__ typename kf::Lanes<T>::I track_step_lanes(T p[6], T lo[3], T C[21], T a, T R,
-                                                                     typename kf::Lanes<T>::M live,
-                                                                     typename kf::Lanes<T>::M has_hit, T m0, T m1,
-                                                                     T m2, T v0, T v1, T v2, T& chi2) {
-  using M = typename kf::Lanes<T>::M;
-  using I = typename kf::Lanes<T>::I;
-  chi2 = T(-1.0f);
-  I st = kf::propagate_lanes<T, NEWTON, EXT>(p, lo, C, a, R, live);
-  const M ok = live & kf::is_zero(st);
-  st = kf::set_bits(st, ok & !has_hit, kf::ST_NO_HIT);
-  const M upd = ok & has_hit;
-  if (!kf::any(upd)) return st;
-  T r0, r1, r2;
-  kf::residual<T, EXT>(p, lo, m0, m1, m2, r0, r1, r2);
-  T Si[6];
-  kf::inverse_S(C, v0, v1, v2, Si);
-  const T c2 = kf::chi2_of(r0, r1, r2, Si);
-  kf::kalman_update_lanes<T, EXT>(p, lo, C, Si, r0, r1, r2, v0, v1, v2, upd);
-  chi2 = kf::sel(upd, c2, T(-1.0f));
-  return st;
-}
-
-// One track.  UPD64: S^-1 and the covariance downdate in FP64.
+// One propagate + (optional) update step of one track.  Returns the status
+// bits raised; writes chi2 (-1 when no update).  UPD64: S^-1 and the
+// covariance downdate in FP64 (single-precision state only).
 template <typename T, int NEWTON, bool EXT, bool UPD64 = false>
 __device__ __forceinline__ int32_t track_step(T p[6], T lo[3], T C[21], T a, T R, bool has_hit,
                                               T m0, T m1, T m2, T v0, T v1, T v2, T& chi2) {
+  chi2 = T(-1);
+  const int st = kf::propagate<T, NEWTON, EXT>(p, lo, C, a, R);
+  if (st) return st;
+  if (!has_hit) return kf::ST_NO_HIT;
+  T r0, r1, r2;
+  kf::residual<T, EXT>(p, lo, m0, m1, m2, r0, r1, r2);
   if constexpr (UPD64) {
-    chi2 = T(-1);
-    const int st = kf::propagate<T, NEWTON, EXT>(p, lo, C, a, R);
-    if (st) return st;
-    if (!has_hit) return kf::ST_NO_HIT;
-    T r0, r1, r2;
-    kf::residual<T, EXT>(p, lo, m0, m1, m2, r0, r1, r2);
     chi2 = kf::kalman_update_f64(p, lo, C, r0, r1, r2, v0, v1, v2);
-    return 0;
   } else {
-    return track_step_lanes<T, NEWTON, EXT>(p, lo, C, a, R, true, has_hit, m0, m1, m2, v0, v1, v2, chi2);
+    T Si[6];
+    kf::inverse_S(C, v0, v1, v2, Si);
+    chi2 = kf::chi2_of(r0, r1, r2, Si);
+    kf::kalman_update<T, EXT>(p, lo, C, Si, r0, r1, r2, v0, v1, v2);
   }
+  return 0;
 }
 
 // The step of track i given its inputs; writes its outputs (shared by the
@@ -157,82 +128,29 @@ __global__ void __launch_bounds__(kFitThreads) fit_layer_kernel(const FitLayerAr
   }
 }
 
-// Two tracks per thread: lane x is track i[0], lane y track i[1].  Same
-// per-lane semantics as fit_layer_track.
-__device__ __forceinline__ float lane_of(kf::f2 v, int k) { return k ? v.v.y : v.v.x; }
-
-__device__ __forceinline__ void fit_layer_pair(const FitLayerArgs& A, const int64_t i[2], const bool valid[2],
-                                               const int32_t st_in[2], kf::f2 p[6], kf::f2 lo[3], kf::f2 C[21],
-                                               const int8_t q[2], const bool hh[2], kf::f2 m0, kf::f2 m1,
-                                               kf::f2 m2) {
-  const int64_t n = A.n;
-  const kf::m2 live = {valid[0] && !(st_in[0] & KF_ST_STOPPED), valid[1] && !(st_in[1] & KF_ST_STOPPED)};
-  kf::f2 chi2(-1.0f);
-  kf::i2 raised = {0, 0};
-  if (kf::any(live)) {
-    const kf::f2 a(A.a_scale * float(q[0]), A.a_scale * float(q[1]));
-    raised = track_step_lanes<kf::f2, kNewtonF32, true>(p, lo, C, a, kf::f2(A.R), live, kf::m2{hh[0], hh[1]}, m0,
-                                                        m1, m2, kf::f2(A.v0), kf::f2(A.v1), kf::f2(A.v2), chi2);
-  }
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    if (!valid[k]) continue;
-    const int64_t t = i[k];
-    if (!(k ? live.y : live.x)) {  // stopped at an earlier layer
-      if (A.chi2) A.chi2[t] = -1.f;
-      continue;
-    }
-    const int32_t r = k ? raised.y : raised.x;
-    const bool stopped = (r & KF_ST_STOPPED) != 0;
-    if (!stopped || A.first) {
-#pragma unroll
-      for (int c = 0; c < 6; ++c) A.out_par[c * n + t] = lane_of(p[c], k);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) A.out_lo[c * n + t] = lane_of(lo[c], k);
-#pragma unroll
-      for (int c = 0; c < 21; ++c) A.out_cov[c * n + t] = lane_of(C[c], k);
-    }
-    if (A.chi2) A.chi2[t] = lane_of(chi2, k);
-    int32_t st = st_in[k] | r;
-    if (A.last || stopped) {
-      float pk[6], Ck[21];
-#pragma unroll
-      for (int c = 0; c < 6; ++c) pk[c] = lane_of(p[c], k);
-#pragma unroll
-      for (int c = 0; c < 21; ++c) Ck[c] = lane_of(C[c], k);
-      if (!pd5(pk, Ck)) st |= KF_ST_NOT_PD;
-    }
-    if (A.first || r || A.last) A.status[t] = st;
-  }
-}
-
 // ---------------------------------------------------------------------------
-// TMA-staged, two-tracks-per-thread layer step: a persistent block of
-// kPairThreads threads walks over tiles of kTile tracks (thread t takes
-// tracks t and t + kPairThreads of a tile); one elected thread streams the
-// next tile's inputs (33 float rows of 1 KB, the charge, hit-validity and
-// status rows) into the other half of a double buffer with cp.async.bulk
-// while the block computes the current tile from shared memory.  Requires
-// 16-byte aligned rows: n % 16 == 0 and every base pointer 16-byte aligned
-// (checked on the host).
-constexpr int kPairThreads = 128;
-constexpr int kTile = 2 * kPairThreads;
+// TMA-staged form of the layer step: a persistent block walks over tiles of
+// kFitThreads tracks; one elected thread streams the next tile's inputs
+// (33 float rows of 1 KB, the charge, hit-validity and status rows) into the
+// other half of a double buffer with cp.async.bulk while the block computes
+// the current tile from shared memory.  Requires 16-byte aligned rows:
+// n % 16 == 0 and every base pointer 16-byte aligned (checked on the host).
 
 struct __align__(16) FitTile {
-  float par[6][kTile];
-  float lo[3][kTile];
-  float cov[21][kTile];
-  float hit[3][kTile];
-  int32_t status[kTile];
-  int8_t charge[kTile];
-  uint8_t valid[kTile];
+  float par[6][kFitThreads];
+  float lo[3][kFitThreads];
+  float cov[21][kFitThreads];
+  float hit[3][kFitThreads];
+  int32_t status[kFitThreads];
+  int8_t charge[kFitThreads];
+  uint8_t valid[kFitThreads];
 };
 constexpr size_t kFitTmaSmem = 2 * sizeof(FitTile) + 16;
 constexpr uint32_t kWaitLimit = 1u << 22;  // bounded mbarrier polls (far above any real copy time)
 
 __device__ __forceinline__ uint32_t issue_tile(const FitLayerArgs& A, FitTile& T, uint64_t* bar, int64_t i0) {
   const int64_t n = A.n;
-  const int64_t cnt = (n - i0) < kTile ? (n - i0) : kTile;
+  const int64_t cnt = (n - i0) < kFitThreads ? (n - i0) : kFitThreads;
   const uint32_t kb = uint32_t(cnt) * 4u, k1 = uint32_t(cnt);
   uint32_t bytes = (6 + 21 + 3) * kb + k1;
   if (A.in_lo) bytes += 3 * kb;
@@ -254,13 +172,13 @@ __device__ __forceinline__ uint32_t issue_tile(const FitLayerArgs& A, FitTile& T
   return bytes;
 }
 
-__global__ void __launch_bounds__(kPairThreads) fit_layer_pair_kernel(const FitLayerArgs A) {
+__global__ void __launch_bounds__(kFitThreads) fit_layer_tma_kernel(const FitLayerArgs A) {
   extern __shared__ __align__(128) unsigned char fit_smem[];
   FitTile* tiles = reinterpret_cast<FitTile*>(fit_smem);
   uint64_t* bar = reinterpret_cast<uint64_t*>(fit_smem + 2 * sizeof(FitTile));
   const int tid = threadIdx.x;
   const int64_t n = A.n;
-  const int64_t n_tiles = (n + kTile - 1) / kTile;
+  const int64_t n_tiles = (n + kFitThreads - 1) / kFitThreads;
   int64_t tile = blockIdx.x;
   if (tile >= n_tiles) return;
   if (tid == 0) {
@@ -269,99 +187,38 @@ __global__ void __launch_bounds__(kPairThreads) fit_layer_pair_kernel(const FitL
     mbar_init_fence();
   }
   __syncthreads();
-  if (tid == 0) issue_tile(A, tiles[0], &bar[0], tile * kTile);
+  if (tid == 0) issue_tile(A, tiles[0], &bar[0], tile * kFitThreads);
   uint32_t use[2] = {0, 0};  // completed phases per buffer
   for (int s = 0; tile < n_tiles; s ^= 1, tile += gridDim.x) {
     const int64_t next = tile + gridDim.x;
     if (tid == 0 && next < n_tiles) {
       fence_proxy_async_smem();  // the other buffer was read by the generic proxy
-      issue_tile(A, tiles[s ^ 1], &bar[s ^ 1], next * kTile);
+      issue_tile(A, tiles[s ^ 1], &bar[s ^ 1], next * kFitThreads);
     }
     const bool ok = mbar_wait_bounded(&bar[s], use[s] & 1u, kWaitLimit);
     use[s]++;
-    const int64_t i[2] = {tile * kTile + tid, tile * kTile + tid + kPairThreads};
-    const bool valid[2] = {i[0] < n, i[1] < n};
     if (__syncthreads_or(!ok)) {
       // a copy did not complete: flag the tile's tracks, drain, leave
-      if (valid[0]) A.status[i[0]] = KF_ST_DEVICE_TIMEOUT;
-      if (valid[1]) A.status[i[1]] = KF_ST_DEVICE_TIMEOUT;
+      const int64_t i = tile * kFitThreads + tid;
+      if (i < n) A.status[i] = KF_ST_DEVICE_TIMEOUT;
       if (next < n_tiles) mbar_wait_bounded(&bar[s ^ 1], use[s ^ 1] & 1u, kWaitLimit);
       return;
     }
     const FitTile& T = tiles[s];
-    const int u = tid, v = tid + kPairThreads;
-    const int32_t st[2] = {A.first ? 0 : T.status[u], A.first ? 0 : T.status[v]};
-    kf::f2 p[6], lo[3], C[21];
+    const int64_t i = tile * kFitThreads + tid;
+    if (i < n) {
+      const int32_t st = A.first ? 0 : T.status[tid];
+      float p[6], lo[3], C[21];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) p[c] = kf::f2(T.par[c][u], T.par[c][v]);
+      for (int c = 0; c < 6; ++c) p[c] = T.par[c][tid];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) lo[c] = A.in_lo ? kf::f2(T.lo[c][u], T.lo[c][v]) : kf::f2(0.f);
+      for (int c = 0; c < 3; ++c) lo[c] = A.in_lo ? T.lo[c][tid] : 0.f;
 #pragma unroll
-    for (int c = 0; c < 21; ++c) C[c] = kf::f2(T.cov[c][u], T.cov[c][v]);
-    const int8_t q[2] = {T.charge[u], T.charge[v]};
-    const bool hh[2] = {A.valid ? T.valid[u] != 0 : true, A.valid ? T.valid[v] != 0 : true};
-    fit_layer_pair(A, i, valid, st, p, lo, C, q, hh, kf::f2(T.hit[0][u], T.hit[0][v]),
-                   kf::f2(T.hit[1][u], T.hit[1][v]), kf::f2(T.hit[2][u], T.hit[2][v]));
+      for (int c = 0; c < 21; ++c) C[c] = T.cov[c][tid];
+      const bool has_hit = A.valid ? T.valid[tid] != 0 : true;
+      fit_layer_track(A, i, st, p, lo, C, T.charge[tid], has_hit, T.hit[0][tid], T.hit[1][tid], T.hit[2][tid]);
+    }
     __syncthreads();  // buffer s is free for the tile after next
-  }
-}
-
-// All layers in one launch, two tracks per thread.
-__global__ void __launch_bounds__(kPairThreads) fit_fused_pair_kernel(const FitFusedArgs A) {
-  const int64_t n = A.n;
-  const int64_t n_tiles = (n + kTile - 1) / kTile;
-  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const int64_t i[2] = {tile * kTile + threadIdx.x, tile * kTile + threadIdx.x + kPairThreads};
-    const bool valid[2] = {i[0] < n, i[1] < n};
-    if (!valid[0]) continue;
-    const int64_t j1 = valid[1] ? i[1] : i[0];  // an absent second lane mirrors the first
-    kf::f2 p[6], lo[3], C[21];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) p[c] = kf::f2(A.in_par[c * n + i[0]], A.in_par[c * n + j1]);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) lo[c] = A.in_lo ? kf::f2(A.in_lo[c * n + i[0]], A.in_lo[c * n + j1]) : kf::f2(0.f);
-#pragma unroll
-    for (int c = 0; c < 21; ++c) C[c] = kf::f2(A.in_cov[c * n + i[0]], A.in_cov[c * n + j1]);
-    const kf::f2 a(A.a_scale * float(A.charge[i[0]]), A.a_scale * float(A.charge[j1]));
-    kf::i2 st = {0, 0};
-    for (int l = 0; l < A.n_layers; ++l) {
-      const kf::m2 live = {!(st.x & KF_ST_STOPPED), valid[1] && !(st.y & KF_ST_STOPPED)};
-      kf::f2 chi2(-1.0f);
-      if (kf::any(live)) {
-        const float* h = A.hits + int64_t(l) * 3 * n;
-        const kf::m2 hh = {A.valid ? A.valid[int64_t(l) * n + i[0]] != 0 : true,
-                           A.valid ? A.valid[int64_t(l) * n + j1] != 0 : true};
-        const kf::i2 r = track_step_lanes<kf::f2, kNewtonF32, true>(
-            p, lo, C, a, kf::f2(A.R[l]), live, hh, kf::f2(h[i[0]], h[j1]), kf::f2(h[n + i[0]], h[n + j1]),
-            kf::f2(h[2 * n + i[0]], h[2 * n + j1]), kf::f2(A.v0), kf::f2(A.v1), kf::f2(A.v2), chi2);
-        st.x |= r.x;
-        st.y |= r.y;
-      }
-      if (A.chi2) {
-        A.chi2[int64_t(l) * n + i[0]] = chi2.v.x;
-        if (valid[1]) A.chi2[int64_t(l) * n + i[1]] = chi2.v.y;
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      if (!valid[k]) continue;
-      const int64_t t = i[k];
-      float pk[6], Ck[21];
-#pragma unroll
-      for (int c = 0; c < 6; ++c) pk[c] = lane_of(p[c], k);
-#pragma unroll
-      for (int c = 0; c < 21; ++c) Ck[c] = lane_of(C[c], k);
-      int32_t s = k ? st.y : st.x;
-      if (!pd5(pk, Ck)) s |= KF_ST_NOT_PD;
-#pragma unroll
-      for (int c = 0; c < 6; ++c) A.out_par[c * n + t] = pk[c];
-      if (A.out_lo)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) A.out_lo[c * n + t] = lane_of(lo[c], k);
-#pragma unroll
-      for (int c = 0; c < 21; ++c) A.out_cov[c * n + t] = Ck[c];
-      if (A.status) A.status[t] = s;
-    }
   }
 }
 
@@ -463,43 +320,29 @@ int fit_tma_grid(kf_ctx* ctx, int64_t n) {
   static int blocks_per_sm = 0;
   if (blocks_per_sm == 0) {
     int b = 0;
-    if (cudaFuncSetAttribute(fit_layer_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kFitTmaSmem)) !=
+    if (cudaFuncSetAttribute(fit_layer_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kFitTmaSmem)) !=
             cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fit_layer_pair_kernel, kPairThreads, kFitTmaSmem) !=
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fit_layer_tma_kernel, kFitThreads, kFitTmaSmem) !=
             cudaSuccess ||
         b < 1)
       b = 1;
     blocks_per_sm = b;
   }
-  const int64_t tiles = (n + kTile - 1) / kTile;
+  const int64_t tiles = (n + kFitThreads - 1) / kFitThreads;
   const int64_t cap = int64_t(ctx->num_sms) * blocks_per_sm;
   return int(tiles < cap ? (tiles > 0 ? tiles : 1) : cap);
 }
 
 cudaError_t launch_fit_layer_tma(const FitLayerArgs& a, int grid, cudaStream_t st) {
-  fit_layer_pair_kernel<<<grid, kPairThreads, kFitTmaSmem, st>>>(a);
+  fit_layer_tma_kernel<<<grid, kFitThreads, kFitTmaSmem, st>>>(a);
   return cudaGetLastError();
 }
 
-static int fused_pair_grid(kf_ctx* ctx, int64_t n) {
-  static int blocks_per_sm = 0;
-  if (blocks_per_sm == 0) {
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fit_fused_pair_kernel, kPairThreads, 0) != cudaSuccess ||
-        b < 1)
-      b = 1;
-    blocks_per_sm = b;
-  }
-  const int64_t tiles = (n + kTile - 1) / kTile;
-  const int64_t cap = int64_t(ctx->num_sms) * blocks_per_sm;
-  return int(tiles < cap ? (tiles > 0 ? tiles : 1) : cap);
-}
-
-cudaError_t launch_fit_fused(kf_ctx* ctx, const FitFusedArgs& a, cudaStream_t st, bool upd64) {
+cudaError_t launch_fit_fused(const FitFusedArgs& a, int grid, cudaStream_t st, bool upd64) {
   if (upd64)
-    fit_fused_kernel<true><<<fit_grid(ctx, a.n), kFitThreads, 0, st>>>(a);
+    fit_fused_kernel<true><<<grid, kFitThreads, 0, st>>>(a);
   else
-    fit_fused_pair_kernel<<<fused_pair_grid(ctx, a.n), kPairThreads, 0, st>>>(a);
+    fit_fused_kernel<false><<<grid, kFitThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -132,7 +132,7 @@ cudaError_t launch_fit_layer(const FitLayerArgs& a, int grid, cudaStream_t st);
 bool fit_tma_ok(const FitLayerArgs& a);
 int fit_tma_grid(kf_ctx* ctx, int64_t n);
 cudaError_t launch_fit_layer_tma(const FitLayerArgs& a, int grid, cudaStream_t st);
-cudaError_t launch_fit_fused(kf_ctx* ctx, const FitFusedArgs& a, cudaStream_t st, bool upd64 = false);
+cudaError_t launch_fit_fused(const FitFusedArgs& a, int grid, cudaStream_t st, bool upd64 = false);
 cudaError_t launch_fit_f64(const FitF64Args& a, cudaStream_t st);
 int fit_grid(kf_ctx* ctx, int64_t n);
 

@@ -237,7 +237,7 @@ static cudaError_t prepare(Serve* sv, Request* r) {
   fa.v0 = fa.v1 = ctx->cfg.sigma_xy_cm * ctx->cfg.sigma_xy_cm;
   fa.v2 = ctx->cfg.sigma_z_cm * ctx->cfg.sigma_z_cm;
   for (int l = 0; l < L.ns; ++l) fa.R[l] = ctx->radius[l];
-  e = launch_fit_fused(ctx, fa, s);
+  e = launch_fit_fused(fa, fit_grid(ctx, n), s);
   if (e != cudaSuccess) return e;
   // hits into eta x phi bins, one segment per build layer
   BinArgs hb;
