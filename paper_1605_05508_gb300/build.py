@@ -14,7 +14,9 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libkf.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-DNDEBUG",
+# -fmad=false: the kernels write every fused multiply-add explicitly; without
+# implicit contraction each kernel form rounds a track identically
+NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-DNDEBUG", "-fmad=false",
               "--expt-relaxed-constexpr", "-I", INCLUDE]
 
 

@@ -204,7 +204,7 @@ int kf_fit(kf_ctx* ctx, const kf_tracks* seeds, const kf_track_hits* hits, kf_tr
       a.v2 = v2;
       a.first = l == 0;
       a.last = l == L - 1;
-      le = fit_tma_ok(a) ? launch_fit_layer_tma(a, fit_tma_grid(ctx, n), cs) : launch_fit_layer(a, grid, cs);
+      le = launch_fit_layer(a, grid, cs);
     }
     cudaGraph_t graph = nullptr;
     cudaError_t ee = cudaStreamEndCapture(cs, &graph);

@@ -4,19 +4,23 @@
 //
 // Track fitting is the branch-free part of Kalman-filter tracking (Cerati et
 // al., Sec. 2): with the hit set fixed, every track runs propagate + update
-// over the layers.  Three forms:
+// over the layers.  Forms:
 //   fit_layer_kernel  one layer step over the whole batch (persistent
 //                     grid-stride launch; kf_fit replays one per layer from a
 //                     captured CUDA graph);
-//   fit_fused_kernel  all layers in one launch, the track held in registers;
+//   fit_fused_kernel  all layers in one launch, the track held in registers
+//                     (also the mixed-precision form);
 //   fit_f64_kernel    the plain FP64 form, launched per event and per layer.
+// Loads are plain coalesced row reads: 20 resident warps per SM hide their
+// latency, and staging the rows in shared memory with bulk copies (per block
+// or per warp) measured slower.
 #include "kf_internal.h"
 #include "kf_math.cuh"
-#include "kf_tma.cuh"
 
 namespace kfi {
 
-constexpr int kFitThreads = 256;
+constexpr int kFitThreads = 128;
+constexpr int kFitMinBlocks = 5;  // 20 resident warps per SM: caps a thread at 96 registers
 constexpr int kNewtonF32 = 12;  // iteration cap of the safeguarded Newton solve
 constexpr int kNewtonF64 = 16;
 
@@ -81,8 +85,7 @@ __device__ __forceinline__ int32_t track_step(T p[6], T lo[3], T C[21], T a, T R
   return 0;
 }
 
-// The step of track i given its inputs; writes its outputs (shared by the
-// plain and the TMA-staged kernels, so both give the same bits).
+// The step of track i given its inputs; writes its outputs.
 __device__ __forceinline__ void fit_layer_track(const FitLayerArgs& A, int64_t i, int32_t st, float p[6], float lo[3],
                                                 float C[21], int8_t q, bool has_hit, float m0, float m1, float m2) {
   const int64_t n = A.n;
@@ -109,7 +112,7 @@ __device__ __forceinline__ void fit_layer_track(const FitLayerArgs& A, int64_t i
   if (A.first || raised || A.last) A.status[i] = st;
 }
 
-__global__ void __launch_bounds__(kFitThreads) fit_layer_kernel(const FitLayerArgs A) {
+__global__ void __launch_bounds__(kFitThreads, kFitMinBlocks) fit_layer_kernel(const FitLayerArgs A) {
   const int64_t n = A.n;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -128,102 +131,8 @@ __global__ void __launch_bounds__(kFitThreads) fit_layer_kernel(const FitLayerAr
   }
 }
 
-// ---------------------------------------------------------------------------
-// TMA-staged form of the layer step: a persistent block walks over tiles of
-// kFitThreads tracks; one elected thread streams the next tile's inputs
-// (33 float rows of 1 KB, the charge, hit-validity and status rows) into the
-// other half of a double buffer with cp.async.bulk while the block computes
-// the current tile from shared memory.  Requires 16-byte aligned rows:
-// n % 16 == 0 and every base pointer 16-byte aligned (checked on the host).
-
-struct __align__(16) FitTile {
-  float par[6][kFitThreads];
-  float lo[3][kFitThreads];
-  float cov[21][kFitThreads];
-  float hit[3][kFitThreads];
-  int32_t status[kFitThreads];
-  int8_t charge[kFitThreads];
-  uint8_t valid[kFitThreads];
-};
-constexpr size_t kFitTmaSmem = 2 * sizeof(FitTile) + 16;
-constexpr uint32_t kWaitLimit = 1u << 22;  // bounded mbarrier polls (far above any real copy time)
-
-__device__ __forceinline__ uint32_t issue_tile(const FitLayerArgs& A, FitTile& T, uint64_t* bar, int64_t i0) {
-  const int64_t n = A.n;
-  const int64_t cnt = (n - i0) < kFitThreads ? (n - i0) : kFitThreads;
-  const uint32_t kb = uint32_t(cnt) * 4u, k1 = uint32_t(cnt);
-  uint32_t bytes = (6 + 21 + 3) * kb + k1;
-  if (A.in_lo) bytes += 3 * kb;
-  if (!A.first) bytes += kb;
-  if (A.valid) bytes += k1;
-  mbar_arrive_expect_tx(bar, bytes);
-#pragma unroll
-  for (int c = 0; c < 6; ++c) bulk_g2s(T.par[c], A.in_par + c * n + i0, kb, bar);
-  if (A.in_lo)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) bulk_g2s(T.lo[c], A.in_lo + c * n + i0, kb, bar);
-#pragma unroll
-  for (int c = 0; c < 21; ++c) bulk_g2s(T.cov[c], A.in_cov + c * n + i0, kb, bar);
-#pragma unroll
-  for (int c = 0; c < 3; ++c) bulk_g2s(T.hit[c], A.hit + c * n + i0, kb, bar);
-  if (!A.first) bulk_g2s(T.status, A.status + i0, kb, bar);
-  bulk_g2s(T.charge, A.charge + i0, k1, bar);
-  if (A.valid) bulk_g2s(T.valid, A.valid + i0, k1, bar);
-  return bytes;
-}
-
-__global__ void __launch_bounds__(kFitThreads) fit_layer_tma_kernel(const FitLayerArgs A) {
-  extern __shared__ __align__(128) unsigned char fit_smem[];
-  FitTile* tiles = reinterpret_cast<FitTile*>(fit_smem);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(fit_smem + 2 * sizeof(FitTile));
-  const int tid = threadIdx.x;
-  const int64_t n = A.n;
-  const int64_t n_tiles = (n + kFitThreads - 1) / kFitThreads;
-  int64_t tile = blockIdx.x;
-  if (tile >= n_tiles) return;
-  if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    mbar_init_fence();
-  }
-  __syncthreads();
-  if (tid == 0) issue_tile(A, tiles[0], &bar[0], tile * kFitThreads);
-  uint32_t use[2] = {0, 0};  // completed phases per buffer
-  for (int s = 0; tile < n_tiles; s ^= 1, tile += gridDim.x) {
-    const int64_t next = tile + gridDim.x;
-    if (tid == 0 && next < n_tiles) {
-      fence_proxy_async_smem();  // the other buffer was read by the generic proxy
-      issue_tile(A, tiles[s ^ 1], &bar[s ^ 1], next * kFitThreads);
-    }
-    const bool ok = mbar_wait_bounded(&bar[s], use[s] & 1u, kWaitLimit);
-    use[s]++;
-    if (__syncthreads_or(!ok)) {
-      // a copy did not complete: flag the tile's tracks, drain, leave
-      const int64_t i = tile * kFitThreads + tid;
-      if (i < n) A.status[i] = KF_ST_DEVICE_TIMEOUT;
-      if (next < n_tiles) mbar_wait_bounded(&bar[s ^ 1], use[s ^ 1] & 1u, kWaitLimit);
-      return;
-    }
-    const FitTile& T = tiles[s];
-    const int64_t i = tile * kFitThreads + tid;
-    if (i < n) {
-      const int32_t st = A.first ? 0 : T.status[tid];
-      float p[6], lo[3], C[21];
-#pragma unroll
-      for (int c = 0; c < 6; ++c) p[c] = T.par[c][tid];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) lo[c] = A.in_lo ? T.lo[c][tid] : 0.f;
-#pragma unroll
-      for (int c = 0; c < 21; ++c) C[c] = T.cov[c][tid];
-      const bool has_hit = A.valid ? T.valid[tid] != 0 : true;
-      fit_layer_track(A, i, st, p, lo, C, T.charge[tid], has_hit, T.hit[0][tid], T.hit[1][tid], T.hit[2][tid]);
-    }
-    __syncthreads();  // buffer s is free for the tile after next
-  }
-}
-
 template <bool UPD64>
-__global__ void __launch_bounds__(kFitThreads) fit_fused_kernel(const FitFusedArgs A) {
+__global__ void __launch_bounds__(kFitThreads, UPD64 ? 1 : kFitMinBlocks) fit_fused_kernel(const FitFusedArgs A) {
   const int64_t n = A.n;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -306,35 +215,6 @@ int fit_grid(kf_ctx* ctx, int64_t n) {
 
 cudaError_t launch_fit_layer(const FitLayerArgs& a, int grid, cudaStream_t st) {
   fit_layer_kernel<<<grid, kFitThreads, 0, st>>>(a);
-  return cudaGetLastError();
-}
-
-static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
-
-bool fit_tma_ok(const FitLayerArgs& a) {
-  return a.n % 16 == 0 && aligned16(a.in_par) && (!a.in_lo || aligned16(a.in_lo)) && aligned16(a.in_cov) &&
-         aligned16(a.hit) && aligned16(a.status) && aligned16(a.charge) && (!a.valid || aligned16(a.valid));
-}
-
-int fit_tma_grid(kf_ctx* ctx, int64_t n) {
-  static int blocks_per_sm = 0;
-  if (blocks_per_sm == 0) {
-    int b = 0;
-    if (cudaFuncSetAttribute(fit_layer_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kFitTmaSmem)) !=
-            cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fit_layer_tma_kernel, kFitThreads, kFitTmaSmem) !=
-            cudaSuccess ||
-        b < 1)
-      b = 1;
-    blocks_per_sm = b;
-  }
-  const int64_t tiles = (n + kFitThreads - 1) / kFitThreads;
-  const int64_t cap = int64_t(ctx->num_sms) * blocks_per_sm;
-  return int(tiles < cap ? (tiles > 0 ? tiles : 1) : cap);
-}
-
-cudaError_t launch_fit_layer_tma(const FitLayerArgs& a, int grid, cudaStream_t st) {
-  fit_layer_tma_kernel<<<grid, kFitThreads, kFitTmaSmem, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -128,10 +128,6 @@ struct FitF64Args {
 
 // kernel launchers (kf_fit.cu)
 cudaError_t launch_fit_layer(const FitLayerArgs& a, int grid, cudaStream_t st);
-// TMA-staged layer step: usable when fit_tma_ok(a) (aligned rows, n % 16 == 0)
-bool fit_tma_ok(const FitLayerArgs& a);
-int fit_tma_grid(kf_ctx* ctx, int64_t n);
-cudaError_t launch_fit_layer_tma(const FitLayerArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_fit_fused(const FitFusedArgs& a, int grid, cudaStream_t st, bool upd64 = false);
 cudaError_t launch_fit_f64(const FitF64Args& a, cudaStream_t st);
 int fit_grid(kf_ctx* ctx, int64_t n);

@@ -58,10 +58,9 @@ def test_fused_equals_graph_and_host_equals_device(cuda_ctx_factory, det):
 
 
 @pytest.mark.parametrize("n", [4096, 40000, 40016])
-def test_tma_staged_layer_kernel_equals_plain_kernel(cuda_ctx_factory, det, n):
-    """kf_fit takes the TMA-staged persistent kernel when rows are 16-byte
-    aligned (n % 16 == 0); kf_fit_noalloc always takes the plain one. Same
-    per-track arithmetic: identical bits, also for a partial last tile."""
+def test_graph_equals_noalloc_bitwise(cuda_ctx_factory, det, n):
+    """kf_fit (captured graph, scratch from the context) and kf_fit_noalloc
+    (static scratch, direct launches): identical bits, also for ragged n."""
     import torch
     from paper_1605_05508_gb300 import kf
     ctx = cuda_ctx_factory(det.radii)
@@ -80,7 +79,6 @@ def test_tma_staged_layer_kernel_equals_plain_kernel(cuda_ctx_factory, det, n):
         res.append(unpack(out, chi2, st))
     for k in ("par", "cov", "chi2", "status"):
         np.testing.assert_array_equal(res[0][k], res[1][k], err_msg=k)
-    assert not np.any(res[0]["status"] & kf.ST_DEVICE_TIMEOUT)
 
 
 def test_batch_invariance_bitwise(cuda_ctx_factory, det):
