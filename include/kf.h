@@ -238,6 +238,45 @@ int kf_build(kf_ctx *ctx, const kf_tracks *seeds, const int64_t *seed_off, const
              int32_t max_cands, kf_build_result *out, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Launch parameters and their autotuner.  They change speed only: every
+ * setting gives bitwise the same results.  (The paper tunes its CPU code by
+ * hand, Sec. 4; here the library measures on the caller's own batch.)
+ */
+typedef struct {
+    int32_t fit_block;        /* threads per block of the kf_fit / kf_fit_noalloc layer
+                                 kernel: 64 or 128 (default 128); 20 warps per SM either way */
+    int32_t build_hit_tile;   /* hits staged in shared memory per warp by the kf_build step
+                                 (bulk asynchronous copies of the window's bin rows):
+                                 0 = none, the scans read global memory (default), or 512 */
+    int32_t build_list_width; /* entries of a lane's child list in the kf_build step: 4 or 8
+                                 (default 8); 4 takes effect only when max_cands <= 4 */
+} kf_tuning;
+
+/* Current launch parameters of the context.  Errors: KF_EINVAL (null). */
+int kf_get_tuning(const kf_ctx *ctx, kf_tuning *out);
+
+/* Set the launch parameters for later calls.  A serving loop keeps those in
+ * effect at kf_serve_start.  Errors: KF_EINVAL (null, or a value outside the
+ * sets above; nothing is changed then). */
+int kf_set_tuning(kf_ctx *ctx, const kf_tuning *t);
+
+/* Autotuner of kf_fit: runs kf_fit on the caller's arguments once per
+ * fit_block value (one untimed call, then three timed with CUDA events on
+ * `stream`, which is synchronised), keeps the fastest in the context and
+ * writes the context's tuning to *chosen (may be NULL).  The outputs hold the
+ * result of the last call, identical for every value.  Errors: those of
+ * kf_fit. */
+int kf_autotune_fit(kf_ctx *ctx, const kf_tracks *seeds, const kf_track_hits *hits, kf_tracks *out,
+                    float *chi2, int32_t *status, void *stream, kf_tuning *chosen);
+
+/* Autotuner of kf_build: the same over build_hit_tile x build_list_width
+ * (list width 4 is tried only when max_cands <= 4).  Errors: those of
+ * kf_build. */
+int kf_autotune_build(kf_ctx *ctx, const kf_tracks *seeds, const int64_t *seed_off,
+                      const kf_layer_hit_bins *bins, int32_t max_cands, kf_build_result *out, void *stream,
+                      kf_tuning *chosen);
+
+/* ---------------------------------------------------------------------------
  * Serving: continuous batching of build requests (Sec. 3's per-event build,
  * run as a service).  Events of uneven size are admitted into resident slots
  * when a slot and device memory are free; every scheduler iteration issues

@@ -25,7 +25,9 @@
 #include "kf_build.cuh"
 #include "kf_internal.h"
 #include "kf_math.cuh"
+#include "kf_tma.cuh"
 
+#include <climits>
 #include <vector>
 
 namespace kfi {
@@ -35,10 +37,11 @@ __device__ __forceinline__ uint64_t make_key(int nhits, float chi2tot, int paren
          uint64_t(hit_plus1);
 }
 
-// insert (key, pos) into the ascending list L/P (kGroup entries, last dropped)
-__device__ __forceinline__ void list_insert(uint64_t (&L)[kGroup], int (&P)[kGroup], uint64_t key, int pos) {
+// insert (key, pos) into the ascending list L/P (LW entries, last dropped)
+template <int LW>
+__device__ __forceinline__ void list_insert(uint64_t (&L)[LW], int (&P)[LW], uint64_t key, int pos) {
 #pragma unroll
-  for (int t = 0; t < kGroup; ++t) {
+  for (int t = 0; t < LW; ++t) {
     if (key < L[t]) {
       const uint64_t tk = L[t];
       const int tp = P[t];
@@ -50,12 +53,51 @@ __device__ __forceinline__ void list_insert(uint64_t (&L)[kGroup], int (&P)[kGro
   }
 }
 
+// Hit staging, per warp.  The four seeds of a warp are consecutive in
+// (eta, phi) bin order, so their windows cluster: the warp takes the union of
+// its candidates' windows (eta rows emin..emax; in phi the hull of the
+// windows unwrapped around a reference bin, one or two bin ranges on the
+// circle), stages the bin offsets of that hull in shared memory with plain
+// loads and the hits of every (row, range) piece -- contiguous in the binned
+// hit array -- with one bulk asynchronous copy each (cp.async.bulk, completed
+// on the warp's mbarrier).  The chi2 scans then read shared memory only.  A
+// warp whose hull does not fit, or whose seeds belong to more than one event,
+// scans global memory.  Warps stage independently: no block-wide barrier.
+// TILE (hits staged per warp; 0: no staging, every scan reads the L2-resident
+// hits through L1) and LW (entries of a lane's child list, >= max_cands) are
+// launch parameters picked by the autotuner.
+constexpr int kWarps = kBuildThreads / 32;
+constexpr int kStageOffs = 384;  // bin offsets staged per warp
+constexpr int kStagePieces = 2 * KF_BIN_ETA;
+constexpr uint32_t kBuildWaitLimit = 1u << 22;  // bounded mbarrier polls
+
+__device__ __forceinline__ int wrap_phi(int d) {  // to [-KF_BIN_PHI/2, KF_BIN_PHI/2)
+  return ((d + KF_BIN_PHI / 2) & (KF_BIN_PHI - 1)) - KF_BIN_PHI / 2;
+}
+
+template <int TILE, int LW>
 __global__ void __launch_bounds__(kBuildThreads) build_step_kernel(const BuildStepArgs Args) {
+  extern __shared__ float4 s_hits_all[];
   __shared__ BuildSlot sD;
+  __shared__ int32_t s_off_all[TILE > 0 ? kWarps : 1][TILE > 0 ? kStageOffs : 1];
+  __shared__ int s_pob_all[TILE > 0 ? kWarps : 1][TILE > 0 ? kStagePieces : 1];  // per piece: offset base
+  __shared__ int s_phb_all[TILE > 0 ? kWarps : 1][TILE > 0 ? kStagePieces : 1];  // per piece: hit base
+  __shared__ int s_stage_all[kWarps];
+  __shared__ __align__(8) uint64_t s_bar_all[kWarps];
+  const int warp = threadIdx.x >> 5;
+  float4* const s_hits = s_hits_all + warp * TILE;
+  int32_t* const s_off = s_off_all[TILE > 0 ? warp : 0];
+  int* const s_pob = s_pob_all[TILE > 0 ? warp : 0];
+  int* const s_phb = s_phb_all[TILE > 0 ? warp : 0];
+  uint64_t* const s_bar = &s_bar_all[warp];
   if (threadIdx.x == 0) {
     int sl = 0;
     while (sl + 1 < Args.n_slots && int(blockIdx.x) >= Args.slots[sl + 1].block_begin) ++sl;
     sD = Args.slots[sl];
+  }
+  if (TILE > 0 && (threadIdx.x & 31) == 0) {
+    mbar_init(s_bar, 1);
+    mbar_init_fence();
   }
   __syncthreads();
   const BuildSlot& D = sD;
@@ -105,73 +147,177 @@ __global__ void __launch_bounds__(kBuildThreads) build_step_kernel(const BuildSt
     }
   }
 
+  // ---- hit window of this candidate: eta rows e0..e1, phi bins fa0..fa1
+  // and fb0..fb1 (second part when the window wraps around phi = +-pi)
+  const bool scan = active && !stopped;
+  float Si[6];
+  int e0 = 0, e1 = -1, fa0 = 0, fa1 = KF_BIN_PHI - 1, fb0 = 0, fb1 = -1;
+  if (scan) {
+    kf::inverse_S(C, Args.v0, Args.v1, Args.v2, Si);
+    const float X = p[0] + lo[0], Y = p[1] + lo[1], Z = p[2] + lo[2];
+    const float rr = sqrtf(X * X + Y * Y);
+    const float cph = X / rr, sph = Y / rr;
+    const float s00 = C[0] + Args.v0, s10 = C[1], s11 = C[2] + Args.v1, s22 = C[5] + Args.v2;
+    const float Stt = sph * sph * s00 - 2.f * sph * cph * s10 + cph * cph * s11;
+    const float Snn = cph * cph * s00 + 2.f * sph * cph * s10 + sph * sph * s11;
+    const float wt = sqrtf(Args.cut * fmaxf(Stt, 0.f));
+    const float wn = sqrtf(Args.cut * fmaxf(Snn, 0.f));
+    const float wz = sqrtf(Args.cut * fmaxf(s22, 0.f));
+    // phi bins: |dphi| <= atan(wt / (R - wn)), one bin of margin each side
+    const float rin = D.R - wn;
+    const float phic = atan2f(Y, X);
+    const float dphi = (rin > 0.5f * D.R && wt < rin) ? atanf(wt / rin) : 10.f;
+    if (dphi < 1.f && phic >= -kPi && phic <= kPi) {  // also false for NaN
+      const float scale = float(KF_BIN_PHI) / (2.0f * kPi);
+      const int f0 = __float2int_rd((phic - dphi + kPi) * scale) - 1;
+      const int f1 = __float2int_rd((phic + dphi + kPi) * scale) + 1;
+      if (f1 - f0 + 1 < KF_BIN_PHI) {
+        if (f0 < 0) {
+          fa0 = f0 + KF_BIN_PHI;
+          fb0 = 0;
+          fb1 = f1;
+        } else if (f1 >= KF_BIN_PHI) {
+          fa0 = f0;
+          fb0 = 0;
+          fb1 = f1 - KF_BIN_PHI;
+        } else {
+          fa0 = f0;
+          fa1 = f1;
+        }
+      }
+    }
+    // eta bins: z within Z +- wz and the hit radius within R +- wn
+    e0 = 0;
+    e1 = KF_BIN_ETA - 1;
+    const float rlo = D.R - wn, rhi = D.R + wn;
+    if (rlo > 0.f) {
+      const float zlo = Z - wz, zhi = Z + wz;
+      const float tmin = zlo >= 0.f ? zlo / rhi : zlo / rlo;
+      const float tmax = zhi >= 0.f ? zhi / rlo : zhi / rhi;
+      e0 = max(eta_bin(asinhf(tmin)) - 1, 0);
+      e1 = min(eta_bin(asinhf(tmax)) + 1, KF_BIN_ETA - 1);
+    }
+  }
+  const int32_t* boff = D.bin_off + int64_t(seg) * (KF_NBINS + 1);
+
+  // ---- warp union of the windows and staging (TILE > 0)
+  bool staged = false, timed_out = false;
+  int emin = 0, hs0a = 0, hs1a = KF_BIN_PHI - 1, hs1b = -1;
+  if constexpr (TILE > 0) {
+    // phi unwrapped around the bin of the warp's first seed; any reference is
+    // correct, a near one keeps the hull small
+    const int64_t j_first = j - (lane >> 3);
+    int f_ref = 0;
+    if (j_first < D.S) {
+      const int64_t s0 = j_first * kGroup;
+      const float ph = atan2f(D.in.par[S8 + s0], D.in.par[s0]);
+      if (ph >= -kPi && ph <= kPi) f_ref = phi_bin(ph);
+    }
+    int d0 = KF_BIN_PHI, d1 = -KF_BIN_PHI;
+    if (scan) {
+      d0 = wrap_phi(fa0 - f_ref);
+      d1 = fb1 >= fb0 ? d0 + (KF_BIN_PHI - fa0) + fb1  // wrapped: fa0..255 then 0..fb1
+                      : d0 + (fa1 - fa0);
+    }
+    emin = __reduce_min_sync(kFull, scan ? e0 : KF_BIN_ETA);
+    const int emax = __reduce_max_sync(kFull, scan ? e1 : -1);
+    const int umin = __reduce_min_sync(kFull, d0), umax = __reduce_max_sync(kFull, d1);
+    const int segmin = __reduce_min_sync(kFull, scan ? seg : INT_MAX);
+    const int segmax = __reduce_max_sync(kFull, scan ? seg : -1);
+    // the hull: phi bins hs0a..hs1a and 0..hs1b (empty if hs1b < 0)
+    if (umax - umin + 1 < KF_BIN_PHI) {
+      const int fh = (f_ref + umin + 2 * KF_BIN_PHI) & (KF_BIN_PHI - 1), W = umax - umin + 1;
+      hs0a = fh;
+      hs1a = min(fh + W - 1, KF_BIN_PHI - 1);
+      hs1b = fh + W - 1 - KF_BIN_PHI;
+    }
+    const int nrows = emax - emin + 1;
+    staged = nrows > 0 && segmin == segmax;
+    if (staged) {
+      const int lena = hs1a - hs0a + 2, lenb = hs1b + 2;  // offsets per piece (bins + end)
+      const int per_row = lena + (lenb >= 2 ? lenb : 0);
+      staged = nrows * per_row <= kStageOffs;
+      if (staged) {
+        // bin offsets of every piece, then the piece table and the copies
+        for (int q = 0; q < 2 * nrows; ++q) {
+          const int len = (q & 1) ? lenb : lena;
+          if (len < 2) continue;
+          const int32_t* src = boff + (emin + (q >> 1)) * KF_BIN_PHI + ((q & 1) ? 0 : hs0a);
+          const int ob = (q >> 1) * per_row + ((q & 1) ? lena : 0);
+          for (int t = lane; t < len; t += 32) s_off[ob + t] = src[t];
+        }
+        __syncwarp();
+        if (lane == 0) {
+          int nh_tot = 0;
+          for (int q = 0; q < 2 * nrows; ++q) {
+            const int len = (q & 1) ? lenb : lena;
+            const int ob = (q >> 1) * per_row + ((q & 1) ? lena : 0);
+            s_pob[q] = ob;
+            s_phb[q] = nh_tot;
+            if (len >= 2) nh_tot += s_off[ob + len - 1] - s_off[ob];
+          }
+          int st_flag = nh_tot <= TILE ? 1 : 0;
+          if (st_flag && nh_tot > 0) {
+            mbar_arrive_expect_tx(s_bar, uint32_t(nh_tot) * uint32_t(sizeof(float4)));
+            for (int q = 0; q < 2 * nrows; ++q) {
+              const int len = (q & 1) ? lenb : lena;
+              if (len < 2) continue;
+              const int u0 = s_off[s_pob[q]], cnt = s_off[s_pob[q] + len - 1] - u0;
+              if (cnt > 0)
+                bulk_g2s(s_hits + s_phb[q], D.hits + h0 + u0, uint32_t(cnt) * uint32_t(sizeof(float4)), s_bar);
+            }
+            st_flag = 2;  // copies in flight
+          }
+          s_stage_all[warp] = st_flag;
+        }
+        __syncwarp();
+        const int flag = s_stage_all[warp];
+        staged = flag != 0;
+        if (flag == 2 && !mbar_wait_bounded(s_bar, 0, kBuildWaitLimit)) {
+          // a copy did not complete: stop the warp's candidates with the error bit
+          st |= KF_ST_DEVICE_TIMEOUT;
+          stopped = true;
+        }
+      }
+    }
+    timed_out = __any_sync(kFull, stopped && (st & KF_ST_DEVICE_TIMEOUT));
+  }
+
   // ---- bookkeeping list of this parent's children (keys only)
-  uint64_t L[kGroup];
-  int P[kGroup];
+  uint64_t L[LW];
+  int P[LW];
 #pragma unroll
-  for (int t = 0; t < kGroup; ++t) {
+  for (int t = 0; t < LW; ++t) {
     L[t] = kNoKey;
     P[t] = -1;
   }
   if (active) {
     bool any = false;
     if (!stopped) {
-      float Si[6];
-      kf::inverse_S(C, Args.v0, Args.v1, Args.v2, Si);
-      const float X = p[0] + lo[0], Y = p[1] + lo[1], Z = p[2] + lo[2];
-      const float rr = sqrtf(X * X + Y * Y);
-      const float cph = X / rr, sph = Y / rr;
-      const float s00 = C[0] + Args.v0, s10 = C[1], s11 = C[2] + Args.v1, s22 = C[5] + Args.v2;
-      const float Stt = sph * sph * s00 - 2.f * sph * cph * s10 + cph * cph * s11;
-      const float Snn = cph * cph * s00 + 2.f * sph * cph * s10 + sph * sph * s11;
-      const float wt = sqrtf(Args.cut * fmaxf(Stt, 0.f));
-      const float wn = sqrtf(Args.cut * fmaxf(Snn, 0.f));
-      const float wz = sqrtf(Args.cut * fmaxf(s22, 0.f));
-      // phi bins: |dphi| <= atan(wt / (R - wn)), one bin of margin each side
-      int fa0 = 0, fa1 = KF_BIN_PHI - 1, fb0 = 0, fb1 = -1;
-      const float rin = D.R - wn;
-      const float phic = atan2f(Y, X);
-      const float dphi = (rin > 0.5f * D.R && wt < rin) ? atanf(wt / rin) : 10.f;
-      if (dphi < 1.f && phic >= -kPi && phic <= kPi) {  // also false for NaN
-        const float scale = float(KF_BIN_PHI) / (2.0f * kPi);
-        const int f0 = __float2int_rd((phic - dphi + kPi) * scale) - 1;
-        const int f1 = __float2int_rd((phic + dphi + kPi) * scale) + 1;
-        if (f1 - f0 + 1 < KF_BIN_PHI) {
-          if (f0 < 0) {
-            fa0 = f0 + KF_BIN_PHI;
-            fa1 = KF_BIN_PHI - 1;
-            fb0 = 0;
-            fb1 = f1;
-          } else if (f1 >= KF_BIN_PHI) {
-            fa0 = f0;
-            fa1 = KF_BIN_PHI - 1;
-            fb0 = 0;
-            fb1 = f1 - KF_BIN_PHI;
-          } else {
-            fa0 = f0;
-            fa1 = f1;
-          }
-        }
-      }
-      // eta bins: z within Z +- wz and the hit radius within R +- wn
-      int e0 = 0, e1 = KF_BIN_ETA - 1;
-      const float rlo = D.R - wn, rhi = D.R + wn;
-      if (rlo > 0.f) {
-        const float zlo = Z - wz, zhi = Z + wz;
-        const float tmin = zlo >= 0.f ? zlo / rhi : zlo / rlo;
-        const float tmax = zhi >= 0.f ? zhi / rlo : zhi / rhi;
-        e0 = max(eta_bin(asinhf(tmin)) - 1, 0);
-        e1 = min(eta_bin(asinhf(tmax)) + 1, KF_BIN_ETA - 1);
-      }
-      const int32_t* boff = D.bin_off + int64_t(seg) * (KF_NBINS + 1);
-      const float4* hs = D.hits + h0;
       for (int er = e0; er <= e1; ++er) {
         for (int part = 0; part < 2; ++part) {
           const int f0 = part == 0 ? fa0 : fb0, f1 = part == 0 ? fa1 : fb1;
           if (f1 < f0) continue;
-          const int u0 = boff[er * KF_BIN_PHI + f0], u1 = boff[er * KF_BIN_PHI + f1 + 1];
+          // the piece of the staged hull holding f0..f1 (always one of the
+          // two when staged; checked all the same)
+          const int pc = (f0 >= hs0a && f1 <= hs1a) ? 0 : 1;
+          const int ph0 = pc ? 0 : hs0a, ph1 = pc ? hs1b : hs1a;
+          const bool in_smem = TILE > 0 && staged && f0 >= ph0 && f1 <= ph1;
+          int u0, u1, ubias = 0;
+          const float4* hs = D.hits + h0;
+          if (in_smem) {
+            const int q = 2 * (er - emin) + pc;
+            const int32_t* off = s_off + (s_pob[q] - ph0);
+            u0 = off[f0];
+            u1 = off[f1 + 1];
+            hs = s_hits;
+            ubias = s_phb[q] - s_off[s_pob[q]];
+          } else {
+            u0 = boff[er * KF_BIN_PHI + f0];
+            u1 = boff[er * KF_BIN_PHI + f1 + 1];
+          }
           for (int u = u0; u < u1; ++u) {
-            const float4 m = hs[u];
+            const float4 m = hs[u + ubias];
             const float r0 = (m.x - p[0]) - lo[0], r1 = (m.y - p[1]) - lo[1], r2 = (m.z - p[2]) - lo[2];
             const float c2 = kf::chi2_of(r0, r1, r2, Si);
             if (c2 < Args.cut) {
@@ -188,13 +334,14 @@ __global__ void __launch_bounds__(kBuildThreads) build_step_kernel(const BuildSt
     // no compatible hit (or a stopped candidate): one child without a hit
     if (!any) list_insert(L, P, make_key(nh, chi2tot, k, 0), -1);
   }
+  if (TILE > 0 && timed_out && lane == 0) mbar_wait_bounded(s_bar, 0, kBuildWaitLimit);  // nothing in flight at exit
 
   // ---- clone engine: merge the group's lists into the best max_cands
   uint64_t my_key = kNoKey;
   int my_parent = 0, my_pos = -1, n_win = 0;
 #pragma unroll
-  for (int r = 0; r < kGroup; ++r) {
-    if (r < Args.max_cands) {  // uniform over the launch
+  for (int r = 0; r < LW; ++r) {
+    if (r < Args.max_cands) {  // uniform over the launch; max_cands <= LW
       uint64_t m = L[0];
 #pragma unroll
       for (int d = kGroup / 2; d >= 1; d >>= 1) {
@@ -207,12 +354,12 @@ __global__ void __launch_bounds__(kBuildThreads) build_step_kernel(const BuildSt
       const int wpos = __shfl_sync(kFull, P[0], gbase + wl);
       if (mine) {
 #pragma unroll
-        for (int t = 0; t < kGroup - 1; ++t) {
+        for (int t = 0; t < LW - 1; ++t) {
           L[t] = L[t + 1];
           P[t] = P[t + 1];
         }
-        L[kGroup - 1] = kNoKey;
-        P[kGroup - 1] = -1;
+        L[LW - 1] = kNoKey;
+        P[LW - 1] = -1;
       }
       if (m != kNoKey) {
         if (k == r) {
@@ -360,9 +507,21 @@ __global__ void build_final_kernel(const BuildFinalArgs A) {
   }
 }
 
-cudaError_t launch_build_step(const BuildStepArgs& a, int grid, cudaStream_t st) {
+cudaError_t launch_build_step(const BuildStepArgs& a, int grid, cudaStream_t st, int tile, int list) {
   if (grid <= 0) return cudaSuccess;
-  build_step_kernel<<<grid, kBuildThreads, 0, st>>>(a);
+  const bool narrow = list == 4 && a.max_cands <= 4;
+  const size_t smem = size_t(kWarps) * kBuildTile * sizeof(float4);
+  if (tile > 0) {
+    if (narrow)
+      build_step_kernel<kBuildTile, 4><<<grid, kBuildThreads, smem, st>>>(a);
+    else
+      build_step_kernel<kBuildTile, kGroup><<<grid, kBuildThreads, smem, st>>>(a);
+  } else {
+    if (narrow)
+      build_step_kernel<0, 4><<<grid, kBuildThreads, 0, st>>>(a);
+    else
+      build_step_kernel<0, kGroup><<<grid, kBuildThreads, 0, st>>>(a);
+  }
   return cudaGetLastError();
 }
 
@@ -486,8 +645,7 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
     a.v1 = v0;
     a.v2 = v2;
     a.cut = ctx->cfg.chi2_cut;
-    build_step_kernel<<<grid, kBuildThreads, 0, s>>>(a);
-    KF_CUDA_TRY(ctx, cudaGetLastError());
+    KF_CUDA_TRY(ctx, launch_build_step(a, grid, s, ctx->tune.build_hit_tile, ctx->tune.build_list_width));
   }
   BuildFinalArgs fa;
   fa.cand = (L % 2 == 0) ? bufA : bufB;

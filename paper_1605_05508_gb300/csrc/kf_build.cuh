@@ -13,6 +13,7 @@ namespace kfi {
 constexpr int kGroup = 8;           // lanes (candidate slots) per seed
 constexpr int kBuildThreads = 128;  // 16 seeds per block
 constexpr int kNewtonBuild = 12;
+constexpr int kBuildTile = 512;     // hits staged per warp when hit staging is on
 constexpr int kParN = 9;  // x y z px py pz + low parts of x y z
 constexpr uint64_t kNoKey = ~0ull;
 constexpr unsigned kFull = 0xffffffffu;
@@ -84,7 +85,9 @@ inline CandBuf cand_at(char* q, int64_t S) {
   return c;
 }
 
-cudaError_t launch_build_step(const BuildStepArgs& a, int grid, cudaStream_t st);
+// tile: 0 (scan global memory) or kBuildTile (stage the window hits per
+// warp); list: 4 (lane lists of 4 children, when max_cands <= 4) or 8
+cudaError_t launch_build_step(const BuildStepArgs& a, int grid, cudaStream_t st, int tile, int list);
 cudaError_t launch_build_init(const BuildInitArgs& a, cudaStream_t st);
 cudaError_t launch_build_final(const BuildFinalArgs& a, cudaStream_t st);
 

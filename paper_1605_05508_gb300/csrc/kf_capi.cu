@@ -159,11 +159,11 @@ int kf_fit(kf_ctx* ctx, const kf_tracks* seeds, const kf_track_hits* hits, kf_tr
   const float a_scale = float(kCLight * double(ctx->cfg.bz_tesla));
   const float v0 = ctx->cfg.sigma_xy_cm * ctx->cfg.sigma_xy_cm;
   const float v2 = ctx->cfg.sigma_z_cm * ctx->cfg.sigma_z_cm;
-  const int grid = fit_grid(ctx, n);
+  const int block = ctx->tune.fit_block;
   std::vector<uint64_t> key = {1,
                                uint64_t(n),
                                uint64_t(L),
-                               uint64_t(grid),
+                               uint64_t(block),
                                reinterpret_cast<uint64_t>(seeds->par),
                                reinterpret_cast<uint64_t>(seeds->par_lo),
                                reinterpret_cast<uint64_t>(seeds->cov),
@@ -204,7 +204,7 @@ int kf_fit(kf_ctx* ctx, const kf_tracks* seeds, const kf_track_hits* hits, kf_tr
       a.v2 = v2;
       a.first = l == 0;
       a.last = l == L - 1;
-      le = launch_fit_layer(a, grid, cs);
+      le = launch_fit_layer(a, block, cs);
     }
     cudaGraph_t graph = nullptr;
     cudaError_t ee = cudaStreamEndCapture(cs, &graph);
@@ -267,7 +267,7 @@ static int fit_fused_impl(kf_ctx* ctx, const kf_tracks* seeds, const kf_track_hi
   a.v0 = a.v1 = ctx->cfg.sigma_xy_cm * ctx->cfg.sigma_xy_cm;
   a.v2 = ctx->cfg.sigma_z_cm * ctx->cfg.sigma_z_cm;
   for (int l = 0; l < hits->n_layers; ++l) a.R[l] = ctx->radius[l];
-  KF_CUDA_TRY(ctx, launch_fit_fused(a, fit_grid(ctx, n), static_cast<cudaStream_t>(stream), upd64));
+  KF_CUDA_TRY(ctx, launch_fit_fused(a, static_cast<cudaStream_t>(stream), upd64));
   return KF_OK;
 }
 

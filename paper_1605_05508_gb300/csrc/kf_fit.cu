@@ -5,15 +5,14 @@
 // Track fitting is the branch-free part of Kalman-filter tracking (Cerati et
 // al., Sec. 2): with the hit set fixed, every track runs propagate + update
 // over the layers.  Forms:
-//   fit_layer_kernel  one layer step over the whole batch (persistent
-//                     grid-stride launch; kf_fit replays one per layer from a
-//                     captured CUDA graph);
+//   fit_layer_kernel  one layer step over the whole batch (kf_fit replays one
+//                     launch per layer from a captured CUDA graph);
 //   fit_fused_kernel  all layers in one launch, the track held in registers
 //                     (also the mixed-precision form);
 //   fit_f64_kernel    the plain FP64 form, launched per event and per layer.
-// Loads are plain coalesced row reads: 20 resident warps per SM hide their
-// latency, and staging the rows in shared memory with bulk copies (per block
-// or per warp) measured slower.
+// One track per thread, 20 resident warps per SM, plain coalesced row reads.
+// Staging the rows in shared memory (bulk copies per block or per warp, or
+// per-thread cp.async double buffering) measured no faster.
 #include "kf_internal.h"
 #include "kf_math.cuh"
 
@@ -21,6 +20,7 @@ namespace kfi {
 
 constexpr int kFitThreads = 128;
 constexpr int kFitMinBlocks = 5;  // 20 resident warps per SM: caps a thread at 96 registers
+constexpr int kFitWarpsPerSM = kFitThreads / 32 * kFitMinBlocks;
 constexpr int kNewtonF32 = 12;  // iteration cap of the safeguarded Newton solve
 constexpr int kNewtonF64 = 16;
 
@@ -112,23 +112,27 @@ __device__ __forceinline__ void fit_layer_track(const FitLayerArgs& A, int64_t i
   if (A.first || raised || A.last) A.status[i] = st;
 }
 
-__global__ void __launch_bounds__(kFitThreads, kFitMinBlocks) fit_layer_kernel(const FitLayerArgs A) {
+// One track per thread over a grid that covers the batch: blocks start as
+// others finish, so the warps of an SM drift out of phase and their load
+// bursts overlap other warps' arithmetic.  THREADS (64 or 128, picked by the
+// autotuner) keeps 20 warps per SM resident either way.
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, kFitWarpsPerSM * 32 / THREADS) fit_layer_kernel(const FitLayerArgs A) {
   const int64_t n = A.n;
-  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const int32_t st = A.first ? 0 : A.status[i];
-    float p[6], lo[3], C[21];
-    if (!(st & KF_ST_STOPPED)) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t st = A.first ? 0 : A.status[i];
+  float p[6], lo[3], C[21];
+  if (!(st & KF_ST_STOPPED)) {
 #pragma unroll
-      for (int c = 0; c < 6; ++c) p[c] = A.in_par[c * n + i];
+    for (int c = 0; c < 6; ++c) p[c] = A.in_par[c * n + i];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) lo[c] = A.in_lo ? A.in_lo[c * n + i] : 0.f;
+    for (int c = 0; c < 3; ++c) lo[c] = A.in_lo ? A.in_lo[c * n + i] : 0.f;
 #pragma unroll
-      for (int c = 0; c < 21; ++c) C[c] = A.in_cov[c * n + i];
-    }
-    const bool has_hit = A.valid ? A.valid[i] != 0 : true;
-    fit_layer_track(A, i, st, p, lo, C, A.charge[i], has_hit, A.hit[i], A.hit[n + i], A.hit[2 * n + i]);
+    for (int c = 0; c < 21; ++c) C[c] = A.in_cov[c * n + i];
   }
+  const bool has_hit = A.valid ? A.valid[i] != 0 : true;
+  fit_layer_track(A, i, st, p, lo, C, A.charge[i], has_hit, A.hit[i], A.hit[n + i], A.hit[2 * n + i]);
 }
 
 template <bool UPD64>
@@ -199,26 +203,22 @@ __global__ void __launch_bounds__(kFitThreads) fit_f64_kernel(const FitF64Args A
   if (A.first || raised || A.last) A.status[i] = st;
 }
 
-int fit_grid(kf_ctx* ctx, int64_t n) {
-  static int blocks_per_sm = 0;
-  if (blocks_per_sm == 0) {
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fit_layer_kernel, kFitThreads, 0) != cudaSuccess ||
-        b < 1)
-      b = 1;
-    blocks_per_sm = b;
-  }
-  const int64_t need = (n + kFitThreads - 1) / kFitThreads;
-  const int64_t cap = int64_t(ctx->num_sms) * blocks_per_sm;
-  return int(need < cap ? (need > 0 ? need : 1) : cap);
+int fit_grid(int block, int64_t n) {
+  const int64_t blocks = (n + block - 1) / block;
+  return int(blocks > 0 ? blocks : 1);
 }
 
-cudaError_t launch_fit_layer(const FitLayerArgs& a, int grid, cudaStream_t st) {
-  fit_layer_kernel<<<grid, kFitThreads, 0, st>>>(a);
+cudaError_t launch_fit_layer(const FitLayerArgs& a, int block, cudaStream_t st) {
+  if (block == 64)
+    fit_layer_kernel<64><<<fit_grid(64, a.n), 64, 0, st>>>(a);
+  else
+    fit_layer_kernel<128><<<fit_grid(128, a.n), 128, 0, st>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_fit_fused(const FitFusedArgs& a, int grid, cudaStream_t st, bool upd64) {
+cudaError_t launch_fit_fused(const FitFusedArgs& a, cudaStream_t st, bool upd64) {
+  const int64_t blocks = (a.n + kFitThreads - 1) / kFitThreads;
+  const int grid = int(blocks > 0 ? blocks : 1);
   if (upd64)
     fit_fused_kernel<true><<<grid, kFitThreads, 0, st>>>(a);
   else

@@ -50,6 +50,7 @@ struct kf_ctx {
   std::vector<kfi::GraphEntry> graphs;
   uint64_t use_clock = 0;
   kfi::Serve* serve = nullptr;
+  kf_tuning tune = {128, 0, 8};  // launch parameters (kf_set_tuning, kf_autotune_*)
 };
 
 namespace kfi {
@@ -127,9 +128,10 @@ struct FitF64Args {
 };
 
 // kernel launchers (kf_fit.cu)
-cudaError_t launch_fit_layer(const FitLayerArgs& a, int grid, cudaStream_t st);
-cudaError_t launch_fit_fused(const FitFusedArgs& a, int grid, cudaStream_t st, bool upd64 = false);
+// block: threads per block, 64 or 128 (kf_tuning.fit_block)
+cudaError_t launch_fit_layer(const FitLayerArgs& a, int block, cudaStream_t st);
+cudaError_t launch_fit_fused(const FitFusedArgs& a, cudaStream_t st, bool upd64 = false);
 cudaError_t launch_fit_f64(const FitF64Args& a, cudaStream_t st);
-int fit_grid(kf_ctx* ctx, int64_t n);
+int fit_grid(int block, int64_t n);
 
 }  // namespace kfi

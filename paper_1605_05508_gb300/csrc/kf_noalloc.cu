@@ -59,7 +59,6 @@ extern "C" int kf_fit_noalloc(kf_ctx* ctx, const kf_tracks* seeds, const kf_trac
   float* lo = out->par_lo ? out->par_lo : reinterpret_cast<float*>(scratch);
   int32_t* st = status ? status : reinterpret_cast<int32_t*>(scratch + 12 * kMaxTracks);
   const int L = hits->n_layers;
-  const int grid = kfi::fit_grid(ctx, n);
   const float v0 = ctx->cfg.sigma_xy_cm * ctx->cfg.sigma_xy_cm;
   const float v2 = ctx->cfg.sigma_z_cm * ctx->cfg.sigma_z_cm;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -84,7 +83,7 @@ extern "C" int kf_fit_noalloc(kf_ctx* ctx, const kf_tracks* seeds, const kf_trac
     a.v2 = v2;
     a.first = l == 0;
     a.last = l == L - 1;
-    KF_CUDA_TRY(ctx, kfi::launch_fit_layer(a, grid, s));
+    KF_CUDA_TRY(ctx, kfi::launch_fit_layer(a, ctx->tune.fit_block, s));
   }
   return KF_OK;
 }

@@ -191,6 +191,7 @@ struct Serve {
   std::vector<Request*> resident;  // resident or finishing
   std::unordered_map<uint64_t, std::unique_ptr<Request>> all;
   kf_serve_stats stats{};
+  kf_tuning tune{};  // launch parameters in effect at kf_serve_start
 };
 
 static void fail_all_locked(Serve* sv, int err) {
@@ -237,7 +238,7 @@ static cudaError_t prepare(Serve* sv, Request* r) {
   fa.v0 = fa.v1 = ctx->cfg.sigma_xy_cm * ctx->cfg.sigma_xy_cm;
   fa.v2 = ctx->cfg.sigma_z_cm * ctx->cfg.sigma_z_cm;
   for (int l = 0; l < L.ns; ++l) fa.R[l] = ctx->radius[l];
-  e = launch_fit_fused(fa, fit_grid(ctx, n), s);
+  e = launch_fit_fused(fa, s);
   if (e != cudaSuccess) return e;
   // hits into eta x phi bins, one segment per build layer
   BinArgs hb;
@@ -432,7 +433,8 @@ static void scheduler(Serve* sv) {
       a.v0 = a.v1 = sv->ctx->cfg.sigma_xy_cm * sv->ctx->cfg.sigma_xy_cm;
       a.v2 = sv->ctx->cfg.sigma_z_cm * sv->ctx->cfg.sigma_z_cm;
       a.cut = sv->ctx->cfg.chi2_cut;
-      if (e == cudaSuccess) e = launch_build_step(a, blocks, sv->stream);
+      if (e == cudaSuccess)
+        e = launch_build_step(a, blocks, sv->stream, sv->tune.build_hit_tile, sv->tune.build_list_width);
       for (Request* r : stepping) r->layer++;
       std::lock_guard<std::mutex> lk(sv->mu);
       sv->stats.step_launches++;
@@ -507,6 +509,7 @@ int kf_serve_start(kf_ctx* ctx, const kf_serve_config* cfg) {
   if (!sv) return KF_ENOMEM;
   sv->ctx = ctx;
   sv->cfg = *cfg;
+  sv->tune = ctx->tune;
   const size_t dbytes = cfg->device_arena_bytes ? cfg->device_arena_bytes : (size_t(1) << 30);
   const size_t hbytes = cfg->host_arena_bytes ? cfg->host_arena_bytes : (size_t(1) << 30);
   int rc = KF_OK;

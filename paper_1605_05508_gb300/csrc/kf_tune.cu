@@ -1,0 +1,116 @@
+// kf_tune.cu -- launch parameters of the context and their autotuner.
+//
+// Each tunable changes how the work is laid out on the GPU, never the
+// arithmetic of a track: the fit kernel's block size (64 or 128 threads, 20
+// resident warps per SM either way), the build step's hit staging (window
+// hits copied per warp into shared memory, or read through L1) and the
+// length of a lane's child list (4 suffices when at most 4 candidates are
+// kept).  The autotuner runs the caller's own batch once per setting and keeps
+// the fastest, so the choice follows the workload (batch size, hit density,
+// max_cands) rather than a fixed table.
+#include "kf_internal.h"
+
+#include <vector>
+
+namespace {
+
+bool valid_tuning(const kf_tuning& t) {
+  return (t.fit_block == 64 || t.fit_block == 128) && (t.build_hit_tile == 0 || t.build_hit_tile == 512) &&
+         (t.build_list_width == 4 || t.build_list_width == 8);
+}
+
+// Mean time of `reps` calls of fn after one untimed call; < 0 on failure
+// (the failing call's KF_* code is left in *rc).
+template <typename Fn>
+float time_calls(kf_ctx* ctx, cudaStream_t st, Fn&& fn, int reps, int* rc) {
+  *rc = fn();
+  if (*rc) return -1.f;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    *rc = kfi::cuda_fail(ctx, cudaGetLastError());
+    return -1.f;
+  }
+  float ms = -1.f;
+  cudaError_t ce = cudaEventRecord(e0, st);
+  for (int i = 0; i < reps && ce == cudaSuccess && !*rc; ++i) *rc = fn();
+  if (ce == cudaSuccess && !*rc) ce = cudaEventRecord(e1, st);
+  if (ce == cudaSuccess && !*rc) ce = cudaEventSynchronize(e1);
+  if (ce == cudaSuccess && !*rc) ce = cudaEventElapsedTime(&ms, e0, e1);
+  if (ce != cudaSuccess && !*rc) *rc = kfi::cuda_fail(ctx, ce);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return *rc ? -1.f : ms / float(reps);
+}
+
+// Try every setting in `cands` (applied with kf_set_tuning), keep the fastest.
+template <typename Fn>
+int autotune(kf_ctx* ctx, void* stream, const std::vector<kf_tuning>& cands, Fn&& fn, kf_tuning* chosen) {
+  const kf_tuning saved = ctx->tune;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  float best = -1.f;
+  kf_tuning best_t = saved;
+  for (const kf_tuning& t : cands) {
+    ctx->tune = t;
+    int rc = 0;
+    const float ms = time_calls(ctx, st, fn, 3, &rc);
+    if (rc) {
+      ctx->tune = saved;
+      return rc;
+    }
+    if (best < 0.f || ms < best) {
+      best = ms;
+      best_t = t;
+    }
+  }
+  // the outputs hold the last call's results: the same bits for every setting
+  ctx->tune = best_t;
+  if (chosen) *chosen = ctx->tune;
+  return KF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int kf_get_tuning(const kf_ctx* ctx, kf_tuning* out) {
+  if (!ctx || !out) return KF_EINVAL;
+  *out = ctx->tune;
+  return KF_OK;
+}
+
+int kf_set_tuning(kf_ctx* ctx, const kf_tuning* t) {
+  if (!ctx || !t || !valid_tuning(*t)) return KF_EINVAL;
+  ctx->tune = *t;
+  return KF_OK;
+}
+
+int kf_autotune_fit(kf_ctx* ctx, const kf_tracks* seeds, const kf_track_hits* hits, kf_tracks* out, float* chi2,
+                    int32_t* status, void* stream, kf_tuning* chosen) {
+  if (!ctx) return KF_EINVAL;
+  std::vector<kf_tuning> cands;
+  for (int b : {64, 128}) {
+    kf_tuning t = ctx->tune;
+    t.fit_block = b;
+    cands.push_back(t);
+  }
+  return autotune(ctx, stream, cands, [&] { return kf_fit(ctx, seeds, hits, out, chi2, status, stream); }, chosen);
+}
+
+int kf_autotune_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed_off, const kf_layer_hit_bins* bins,
+                      int32_t max_cands, kf_build_result* out, void* stream, kf_tuning* chosen) {
+  if (!ctx) return KF_EINVAL;
+  std::vector<kf_tuning> cands;
+  for (int tile : {0, 512})
+    for (int list : {8, 4}) {
+      if (list == 4 && max_cands > 4) continue;
+      kf_tuning t = ctx->tune;
+      t.build_hit_tile = tile;
+      t.build_list_width = list;
+      cands.push_back(t);
+    }
+  return autotune(ctx, stream, cands,
+                  [&] { return kf_build(ctx, seeds, seed_off, bins, max_cands, out, stream); }, chosen);
+}
+
+}  // extern "C"

@@ -89,6 +89,10 @@ class kf_serve_stats(C.Structure):
                 ("device_arena_bytes", C.c_size_t), ("device_arena_peak", C.c_size_t)]
 
 
+class kf_tuning(C.Structure):
+    _fields_ = [("fit_block", C.c_int32), ("build_hit_tile", C.c_int32), ("build_list_width", C.c_int32)]
+
+
 MAX_SLOTS = 32  # KF_MAX_SLOTS
 BIN_ETA, BIN_PHI, BIN_ETA_MAX = 64, 256, 1.5  # KF_BIN_ETA, KF_BIN_PHI, KF_BIN_ETA_MAX
 NBINS = BIN_ETA * BIN_PHI
@@ -124,6 +128,12 @@ def lib() -> C.CDLL:
         L.kf_serve_stats_get.argtypes = [vp, C.POINTER(kf_serve_stats)]
         L.kf_build.argtypes = [vp, C.POINTER(kf_tracks), vp, C.POINTER(kf_layer_hit_bins), i32,
                                C.POINTER(kf_build_result), vp]
+        L.kf_get_tuning.argtypes = [vp, C.POINTER(kf_tuning)]
+        L.kf_set_tuning.argtypes = [vp, C.POINTER(kf_tuning)]
+        L.kf_autotune_fit.argtypes = [vp, C.POINTER(kf_tracks), C.POINTER(kf_track_hits), C.POINTER(kf_tracks),
+                                      vp, vp, vp, C.POINTER(kf_tuning)]
+        L.kf_autotune_build.argtypes = [vp, C.POINTER(kf_tracks), vp, C.POINTER(kf_layer_hit_bins), i32,
+                                        C.POINTER(kf_build_result), vp, C.POINTER(kf_tuning)]
         _lib = L
     return _lib
 
@@ -328,6 +338,39 @@ def kf_build(ctx, seeds: Tracks, seed_off, bins: HitBins, max_cands: int, out: B
     s, b, o = seeds.abi(), bins.abi(), out.abi()
     _check(lib().kf_build(_h(ctx), C.byref(s), _ptr(seed_off), C.byref(b), int(max_cands), C.byref(o),
                           _stream(stream)), "kf_build", _h(ctx))
+
+
+# --------------------------------------------------------------------------- launch parameters
+
+
+def _tuning_dict(t: kf_tuning) -> dict:
+    return {f: getattr(t, f) for f, _ in kf_tuning._fields_}
+
+
+def kf_get_tuning(ctx) -> dict:
+    t = kf_tuning()
+    _check(lib().kf_get_tuning(_h(ctx), C.byref(t)), "kf_get_tuning", _h(ctx))
+    return _tuning_dict(t)
+
+
+def kf_set_tuning(ctx, fit_block: int, build_hit_tile: int, build_list_width: int):
+    t = kf_tuning(int(fit_block), int(build_hit_tile), int(build_list_width))
+    _check(lib().kf_set_tuning(_h(ctx), C.byref(t)), "kf_set_tuning", _h(ctx))
+
+
+def kf_autotune_fit(ctx, seeds: Tracks, hits: TrackHits, out: Tracks, chi2=None, status=None, stream=None) -> dict:
+    s, h, o, t = seeds.abi(), hits.abi(), out.abi(), kf_tuning()
+    _check(lib().kf_autotune_fit(_h(ctx), C.byref(s), C.byref(h), C.byref(o), _ptr(chi2), _ptr(status),
+                                 _stream(stream), C.byref(t)), "kf_autotune_fit", _h(ctx))
+    return _tuning_dict(t)
+
+
+def kf_autotune_build(ctx, seeds: Tracks, seed_off, bins: HitBins, max_cands: int, out: BuildResult,
+                      stream=None) -> dict:
+    s, b, o, t = seeds.abi(), bins.abi(), out.abi(), kf_tuning()
+    _check(lib().kf_autotune_build(_h(ctx), C.byref(s), _ptr(seed_off), C.byref(b), int(max_cands), C.byref(o),
+                                   _stream(stream), C.byref(t)), "kf_autotune_build", _h(ctx))
+    return _tuning_dict(t)
 
 
 # --------------------------------------------------------------------------- serving

@@ -31,9 +31,10 @@ def oracle_build(batch, max_cands, idx=None, cut=30.0):
     return b
 
 
-def gpu_build(ctx, batch, max_cands, want_cands=True):
-    """Seed fit (kf_fit over the seeding layers) -> kf_bin_hits -> kf_build.
-    Returns numpy arrays (hit_idx as [n, L])."""
+def gpu_build(ctx, batch, max_cands, want_cands=True, build_fn=None):
+    """Seed fit (kf_fit over the seeding layers) -> kf_bin_hits -> kf_build
+    (or build_fn with kf_build's arguments). Returns numpy arrays (hit_idx as
+    [n, L])."""
     import torch
     from paper_1605_05508_gb300 import kf
     n = batch.seeds.par.shape[1]
@@ -61,7 +62,7 @@ def gpu_build(ctx, batch, max_cands, want_cands=True):
         cand_hit_idx=torch.empty((Lb, n * N), **i32) if want_cands else None,
         cand_chi2_tot=torch.empty(n * N, device="cuda") if want_cands else None,
         cand_n_hits=torch.empty(n * N, **i32) if want_cands else None)
-    kf.kf_build(ctx, fo, seed_off, bins, N, out)
+    (build_fn or kf.kf_build)(ctx, fo, seed_off, bins, N, out)
     torch.cuda.synchronize()
     res = dict(par=out.best.par.double().cpu().numpy().T + np.pad(out.best.par_lo.double().cpu().numpy().T,
                                                                      ((0, 0), (0, 3))),

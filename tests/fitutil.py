@@ -46,6 +46,8 @@ def gpu_fit(ctx, seeds, hits_xyz, hits_valid, mode="graph", with_lo=True, sample
         kf.kf_fit(ctx, s, h, out, chi2, st)
     elif mode == "fused":
         kf.kf_fit_fused(ctx, s, h, out, chi2, st)
+    elif mode == "autotune":
+        kf.kf_autotune_fit(ctx, s, h, out, chi2, st)
     else:
         raise ValueError(mode)
     torch.cuda.synchronize()

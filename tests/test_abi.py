@@ -56,3 +56,9 @@ def test_strerror_and_argument_checks_need_no_gpu(libpath):
     cfg = kf.kf_config(3.8, 3, (ctypes.c_float * 3)(4.0, 8.0, 12.0), 0.01, 0.1, 30.0, 9)  # max_cands > 8
     assert lib.kf_create(ctypes.byref(h), ctypes.byref(cfg), 0, 0) == kf.KF_EINVAL
     assert lib.kf_fit(None, None, None, None, None, None, None) == kf.KF_EINVAL
+    # launch parameters: null context or output, and no GPU needed to reject them
+    t = kf.kf_tuning(128, 0, 8)
+    assert lib.kf_get_tuning(None, ctypes.byref(t)) == kf.KF_EINVAL
+    assert lib.kf_set_tuning(None, ctypes.byref(t)) == kf.KF_EINVAL
+    assert lib.kf_autotune_fit(None, None, None, None, None, None, None, None) == kf.KF_EINVAL
+    assert lib.kf_autotune_build(None, None, None, None, 6, None, None, None) == kf.KF_EINVAL

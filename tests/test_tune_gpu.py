@@ -1,0 +1,93 @@
+"""Launch parameters (kf_tuning) change speed, never results: every setting
+gives bitwise the same fit and build, including the build's per-warp hit
+staging (window bin rows copied into shared memory) on wrapped and dense
+windows; the autotuners keep a valid setting and leave identical outputs."""
+import numpy as np
+import pytest
+
+from paper_1605_05508_gb300 import synth as S
+from buildutil import gpu_build
+from fitutil import gpu_fit
+
+pytestmark = pytest.mark.gpu
+
+DEFAULT = {"fit_block": 128, "build_hit_tile": 0, "build_list_width": 8}
+BUILD_KEYS = ("par", "cov", "chi2", "nhits", "status", "hits", "n_cands", "cand_hits", "cand_chi2", "cand_nhits")
+
+
+def _same(a, b, keys):
+    for k in keys:
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+
+
+def test_tuning_defaults_and_validation(cuda_ctx_factory):
+    from paper_1605_05508_gb300 import kf
+    ctx = cuda_ctx_factory(S.barrel().radii)
+    assert kf.kf_get_tuning(ctx) == DEFAULT
+    for bad in [(96, 0, 8), (128, 256, 8), (128, 0, 6), (0, 0, 0)]:
+        with pytest.raises(kf.KfError):
+            kf.kf_set_tuning(ctx, *bad)
+    assert kf.kf_get_tuning(ctx) == DEFAULT
+    kf.kf_set_tuning(ctx, 64, 512, 4)
+    assert kf.kf_get_tuning(ctx) == {"fit_block": 64, "build_hit_tile": 512, "build_list_width": 4}
+
+
+@pytest.mark.parametrize("n", [7001, 64])
+def test_fit_block_sizes_bitwise(cuda_ctx_factory, n):
+    from paper_1605_05508_gb300 import kf
+    det = S.barrel()
+    ctx = cuda_ctx_factory(det.radii)
+    ev = S.make_fit_batch(91 + n, n, det, pt_range=(0.3, 10.0))
+    res = []
+    for b in (64, 128):
+        kf.kf_set_tuning(ctx, b, 0, 8)
+        res.append(gpu_fit(ctx, ev.seeds, ev.hits.xyz, ev.hits.valid, "graph"))
+    _same(res[0], res[1], ("par", "cov", "chi2", "status"))
+    # the autotuner keeps one of the two and gives the same bits
+    t = gpu_fit(ctx, ev.seeds, ev.hits.xyz, ev.hits.valid, "autotune")
+    _same(res[0], t, ("par", "cov", "chi2", "status"))
+    assert kf.kf_get_tuning(ctx)["fit_block"] in (64, 128)
+
+
+def _batches():
+    return {
+        "config3-like": S.make_build_batch(1611, 4, 1500),
+        "phi-wrap": S.make_build_batch(1612, 2, 300, phi_range=(np.pi - 0.06, np.pi + 0.06)),
+        # dense hits: many warps' hulls exceed the staging tile and fall back
+        "dense": S.make_build_batch(1613, 2, 1000, noise_factor=40),
+    }
+
+
+@pytest.mark.parametrize("max_cands", [6, 3, 1])
+def test_build_settings_bitwise(cuda_ctx_factory, max_cands):
+    from paper_1605_05508_gb300 import kf
+    det = S.barrel()
+    ctx = cuda_ctx_factory(det.radii, max_cands=8)
+    for name, batch in _batches().items():
+        ref = None
+        for tile in (0, 512):
+            for lw in (8, 4):
+                kf.kf_set_tuning(ctx, 128, tile, lw)
+                g = gpu_build(ctx, batch, max_cands)
+                if ref is None:
+                    ref = g
+                else:
+                    for k in BUILD_KEYS:
+                        np.testing.assert_array_equal(ref[k], g[k], err_msg=f"{name} tile={tile} list={lw} {k}")
+        assert np.mean(ref["nhits"]) > 5.0, name
+
+
+def test_build_autotune(cuda_ctx_factory):
+    from paper_1605_05508_gb300 import kf
+    det = S.barrel()
+    ctx = cuda_ctx_factory(det.radii, max_cands=8)
+    batch = S.make_build_batch(1614, 3, 1200)
+    ref = gpu_build(ctx, batch, 4)
+    chosen = {}
+
+    def tune(*args):
+        chosen.update(kf.kf_autotune_build(*args))
+    g = gpu_build(ctx, batch, 4, build_fn=tune)
+    _same(ref, g, BUILD_KEYS)
+    assert chosen["build_hit_tile"] in (0, 512) and chosen["build_list_width"] in (4, 8)
+    assert kf.kf_get_tuning(ctx) == chosen
