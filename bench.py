@@ -234,6 +234,8 @@ def run_ours(a):
     def step():
         kf.kf_fit(ctx, seeds, hits, out, chi2, status, stream)
 
+    # the library's autotuner picks the layer kernel's block size on this batch
+    tuning = kf.kf_autotune_fit(ctx, seeds, hits, out, chi2, status, stream)
     for _ in range(max(a.warmup, 3)):
         step()
     torch.cuda.synchronize()
@@ -267,7 +269,7 @@ def run_ours(a):
     achieved = bpt * n / launch_s / 1e9
     peak, peak_kind = measured_peaks()
     traffic = ncu_traffic(n)
-    roof = {"kernel": "fit_layer_kernel", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+    roof = {"kernel": f"fit_layer_kernel<{tuning['fit_block']}>", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
             "algorithmic_bytes_per_track_layer": bpt, "launch_us": launch_s * 1e6}
 
@@ -275,7 +277,8 @@ def run_ours(a):
             "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 (positions as float pairs)",
             "data": "synthetic (seeded generator, helix hits + Gaussian smear)",
-            "config": workload_config(a), "roofline": roof, "clocks": clk, "gpu_launches": a.steps * L}
+            "config": workload_config(a), "roofline": roof, "clocks": clk, "gpu_launches": a.steps * L,
+            "tuning": tuning}
 
     if not a.no_extras:
         line.update(extras(a, ctx, kf, torch, dev, det, ev, seeds, hits, out, chi2, status, stream, value,
@@ -289,7 +292,7 @@ def run_ours(a):
         line["precision"] = precision_leg(a, kf, torch, dev, stream, rank)
     if not a.no_serve:
         torch.cuda.empty_cache()
-        line["serving"] = serve_leg(a, kf, dev, rank)
+        line["serving"] = serve_leg(a, kf, dev, rank, line.get("build", {}).get("tuning"))
     ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -424,9 +427,23 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist):
             tot = float(tt.item())
         return tot, t
 
+    def sweep_and_tune(N):
+        # build time of every launch setting (for the record), then the
+        # library's autotuner keeps the fastest for the timed run
+        times = {}
+        for tile in (0, 512):
+            for lw in (8, 4):
+                if lw == 4 and N > 4:
+                    continue
+                kf.kf_set_tuning(ctx, 128, tile, lw)
+                times[f"tile{tile}_list{lw}"] = float(run(N, 5)[1][2])
+        return times, kf.kf_autotune_build(ctx, fo, seed_off, bins, N, out, stream)
+
     k = max(5, min(50, a.steps // 4))
+    sweep6, tune6 = sweep_and_tune(6)
     tot6, t6 = run(6, k)
     mean_hits = float(out.n_hits.float().mean())
+    sweep1, tune1 = sweep_and_tune(1)
     tot1, t1 = run(1, k)
     res = {"workload": f"combinatorial build: {E} events x {T} seeds, {int(3 * T)} noise + <= {T} track hits per "
                        f"layer, 64x256 eta-phi bins, chi2 < 30, N = 6, seed fit on layers 1-3, build on 4-10",
@@ -434,7 +451,9 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist):
            "events_per_s": world * E / (tot6 / 1e3), "seeds_per_s": world * n / (tot6 / 1e3),
            "phases_ms": {"seed_fit": float(t6[0]), "bin_hits": float(t6[1]), "build": float(t6[2])},
            "build_ms_per_layer": float(t6[2]) / Lb, "mean_hits_found": mean_hits, "max_cands": 6,
-           "best_hit_N1": {"ms_per_step": tot1, "value": world * n * Lb / (tot1 / 1e3), "build_ms": float(t1[2])},
+           "best_hit_N1": {"ms_per_step": tot1, "value": world * n * Lb / (tot1 / 1e3), "build_ms": float(t1[2]),
+                           "tuning": tune1, "build_ms_by_setting": sweep1},
+           "tuning": tune6, "build_ms_by_setting": sweep6,
            "gpu_launches_per_step": 3 + 1 + (3 + Lb + 1)}
     if rank == 0 and not a.no_extras:
         import oracle as O
@@ -510,7 +529,7 @@ def precision_leg(a, kf, torch, dev, stream, rank):
     return res
 
 
-def serve_leg(a, kf, dev, rank):
+def serve_leg(a, kf, dev, rank, tuning=None):
     """Continuous-batching service (kf_submit / kf_poll) on a Poisson stream of
     events with log-uniform 500-50 000 tracks (3x noise hits per layer), the
     build of the combinatorial-build leg (N = 6), admission by device memory."""
@@ -526,6 +545,8 @@ def serve_leg(a, kf, dev, rank):
                          layer_off=b.layer_off))
     det = S.barrel()
     ctx = kf.Context(det.radii, det.bz, det.sigma_xy, det.sigma_z, device=dev.index)
+    if tuning:  # the build leg's autotuned launch parameters (N = 6)
+        kf.kf_set_tuning(ctx, **tuning)
     kf.kf_serve_start(ctx, 3, 7, 6, max_slots=kf.MAX_SLOTS, max_queue=1 << 16, device_arena_bytes=16 << 30,
                       host_arena_bytes=3 << 30)
     M = a.serve_requests
