@@ -60,6 +60,23 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
+def max_over_ranks(x, dist, device=None):
+    """The largest value of x over the ranks (the slowest rank sets the
+    whole-job time); x itself on a single process."""
+    if not dist:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Weak scaling: every rank processes units_per_rank units in `seconds`
+    (the max over ranks), so the job's throughput is world * units / seconds."""
+    return world * units_per_rank / seconds
+
+
 def workload_config(a):
     return {"workload": f"batched FP32 fit: {a.events} events x {a.tracks} tracks, {a.layers} barrel layers "
                         f"r=4..{4 * a.layers} cm, Bz=3.8 T",
@@ -255,13 +272,9 @@ def run_ours(a):
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    t_ms = e0.elapsed_time(e1)
-    if dist:
-        tt = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
+    t_ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
     ms_per_step = t_ms / a.steps
-    value = world * n * L / (ms_per_step / 1e3)
+    value = whole_job_rate(n * L, world, ms_per_step / 1e3)
 
     # roofline of the per-layer kernel: the graph holds only the L layer launches
     launch_s = ms_per_step / 1e3 / L
@@ -335,10 +348,10 @@ def extras(a, ctx, kf, torch, dev, det, ev, seeds, hits, out, chi2, status, stre
     t0 = time.perf_counter()
     for _ in range(k_e2e):
         kf.kf_fit_host(ctx, hs, hh, ho, hc, hst, stream)
-    dt = (time.perf_counter() - t0) / k_e2e
+    dt = max_over_ranks((time.perf_counter() - t0) / k_e2e, dist, dev)
     h2d = n * (6 * 4 + 21 * 4 + 1) + L * n * (3 * 4 + 1)
     d2h = n * (6 * 4 + 3 * 4 + 21 * 4 + 4) + L * n * 4
-    res["e2e"] = {"value": world * n * L / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+    res["e2e"] = {"value": whole_job_rate(n * L, world, dt), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                   "ms_per_step": dt * 1e3, "api": "kf_fit_host (pinned host buffers)"}
 
     # plain per-event FP64 form on the same GPU
@@ -420,12 +433,7 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist):
             torch.cuda.synchronize()
             t += [evs[0].elapsed_time(evs[1]), evs[1].elapsed_time(evs[2]), evs[2].elapsed_time(evs[3])]
         t /= k
-        tot = float(t.sum())
-        if dist:
-            tt = torch.tensor([tot], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            tot = float(tt.item())
-        return tot, t
+        return max_over_ranks(float(t.sum()), dist, dev), t
 
     def sweep_and_tune(N):
         # build time of every launch setting (for the record), then the
