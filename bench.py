@@ -451,6 +451,40 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist):
     sweep6, tune6 = sweep_and_tune(6)
     tot6, t6 = run(6, k)
     mean_hits = float(out.n_hits.float().mean())
+    # build efficiency: best candidate with >= 80 % of its building-layer hits
+    # from its own track (truth of the generator)
+    hidx = out.hit_idx.cpu().numpy()
+    seed_first = np.searchsorted(batch.seed_event, np.arange(E + 1))
+    own = np.arange(n) - seed_first[batch.seed_event]
+    good = np.zeros(n, np.int64)
+    for b in range(Lb):
+        ok = hidx[b] >= 0
+        h = batch.layer_off[batch.seed_event * Lb + b] + hidx[b]
+        good[ok] += batch.layer_truth[h[ok]] == own[ok]
+    # re-fit of the built tracks over all 10 layers (kf_refit)
+    ro = kf.Tracks(torch.empty((6, n), device=dev), torch.empty((21, n), device=dev), s.charge,
+                   torch.empty((3, n), device=dev))
+    rchi2 = torch.empty((len(batch.seed_layers) + Lb, n), device=dev)
+    rst = torch.empty(n, **i32)
+
+    def refit():
+        kf.kf_refit(ctx, s, fh, seed_off, lh, out.hit_idx, ro, rchi2, rst, stream)
+    for _ in range(3):
+        refit()
+    torch.cuda.synchronize()
+    evs[0].record(stream)
+    for _ in range(k):
+        refit()
+    evs[1].record(stream)
+    torch.cuda.synchronize()
+    refit_ms = max_over_ranks(evs[0].elapsed_time(evs[1]) / k, dist, dev)
+    full = torch.from_numpy(good == Lb).to(dev) & (rst == 0)
+    rc = rchi2[:, full]
+    efficiency = {"best_candidate_ge_80pct_correct": float(np.mean(good >= 0.8 * Lb)),
+                  "all_hits_correct": float(np.mean(good == Lb)),
+                  "refit_ms": refit_ms, "refit_track_layers_per_s": whole_job_rate(n * rchi2.shape[0], world,
+                                                                                    refit_ms / 1e3),
+                  "refit_chi2_per_hit_all_correct": float(rc.mean()) if rc.numel() else None}
     sweep1, tune1 = sweep_and_tune(1)
     tot1, t1 = run(1, k)
     res = {"workload": f"combinatorial build: {E} events x {T} seeds, {int(3 * T)} noise + <= {T} track hits per "
@@ -461,7 +495,7 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist):
            "build_ms_per_layer": float(t6[2]) / Lb, "mean_hits_found": mean_hits, "max_cands": 6,
            "best_hit_N1": {"ms_per_step": tot1, "value": world * n * Lb / (tot1 / 1e3), "build_ms": float(t1[2]),
                            "tuning": tune1, "build_ms_by_setting": sweep1},
-           "tuning": tune6, "build_ms_by_setting": sweep6,
+           "tuning": tune6, "build_ms_by_setting": sweep6, "efficiency_and_refit": efficiency,
            "gpu_launches_per_step": 3 + 1 + (3 + Lb + 1)}
     if rank == 0 and not a.no_extras:
         import oracle as O

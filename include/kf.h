@@ -237,6 +237,26 @@ typedef struct {
 int kf_build(kf_ctx *ctx, const kf_tracks *seeds, const int64_t *seed_off, const kf_layer_hit_bins *bins,
              int32_t max_cands, kf_build_result *out, void *stream);
 
+/*
+ * Re-fit of built tracks: building (Sec. 3) followed by fitting (Sec. 2) over
+ * all layers with the hits the build chose.  For seed i of event e, layer
+ * l < seed_hits->n_layers uses seed_hits (the seeding-layer hits the build's
+ * seeds were fitted with); building layer b uses hit hit_idx[b][i] (an id
+ * within segment e * build_hits->n_layers + b of build_hits, -1 = no hit)
+ * at layer seed_hits->n_layers + b.  The fit starts from `seeds` (the states
+ * the build's seeds were fitted from) and runs as kf_fit over
+ * seed_hits->n_layers + build_hits->n_layers layers (configuration radii
+ * 0 ..; build_hits->first_layer must equal seed_hits->n_layers).
+ * seed_off: [n_events + 1] (device), as for kf_build; hit_idx: [build
+ * layers][n] (device), kf_build_result.hit_idx.  Outputs as kf_fit (chi2 has
+ * one row per layer, -1 where there is no hit).  The gathered hits (13 bytes
+ * per seed and layer) are context scratch.
+ * Errors: KF_EINVAL (sizes, layer counts, null pointers), KF_ENOMEM, KF_ECUDA.
+ */
+int kf_refit(kf_ctx *ctx, const kf_tracks *seeds, const kf_track_hits *seed_hits, const int64_t *seed_off,
+             const kf_layer_hits *build_hits, const int32_t *hit_idx, kf_tracks *out, float *chi2,
+             int32_t *status, void *stream);
+
 /* ---------------------------------------------------------------------------
  * Launch parameters and their autotuner.  They change speed only: every
  * setting gives bitwise the same results.  (The paper tunes its CPU code by

@@ -128,6 +128,8 @@ def lib() -> C.CDLL:
         L.kf_serve_stats_get.argtypes = [vp, C.POINTER(kf_serve_stats)]
         L.kf_build.argtypes = [vp, C.POINTER(kf_tracks), vp, C.POINTER(kf_layer_hit_bins), i32,
                                C.POINTER(kf_build_result), vp]
+        L.kf_refit.argtypes = [vp, C.POINTER(kf_tracks), C.POINTER(kf_track_hits), vp, C.POINTER(kf_layer_hits), vp,
+                               C.POINTER(kf_tracks), vp, vp, vp]
         L.kf_get_tuning.argtypes = [vp, C.POINTER(kf_tuning)]
         L.kf_set_tuning.argtypes = [vp, C.POINTER(kf_tuning)]
         L.kf_autotune_fit.argtypes = [vp, C.POINTER(kf_tracks), C.POINTER(kf_track_hits), C.POINTER(kf_tracks),
@@ -338,6 +340,14 @@ def kf_build(ctx, seeds: Tracks, seed_off, bins: HitBins, max_cands: int, out: B
     s, b, o = seeds.abi(), bins.abi(), out.abi()
     _check(lib().kf_build(_h(ctx), C.byref(s), _ptr(seed_off), C.byref(b), int(max_cands), C.byref(o),
                           _stream(stream)), "kf_build", _h(ctx))
+
+
+def kf_refit(ctx, seeds: Tracks, seed_hits: TrackHits, seed_off, build_hits: LayerHits, hit_idx, out: Tracks,
+             chi2=None, status=None, stream=None):
+    """Fit of built tracks over all layers with the hits kf_build chose."""
+    s, h, b, o = seeds.abi(), seed_hits.abi(), build_hits.abi(), out.abi()
+    _check(lib().kf_refit(_h(ctx), C.byref(s), C.byref(h), _ptr(seed_off), C.byref(b), _ptr(hit_idx), C.byref(o),
+                          _ptr(chi2), _ptr(status), _stream(stream)), "kf_refit", _h(ctx))
 
 
 # --------------------------------------------------------------------------- launch parameters
