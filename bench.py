@@ -602,6 +602,8 @@ def serve_leg(a, kf, dev, rank, tuning=None):
                     raise
                 time.sleep(50e-6)
 
+    refit_layers = [0]
+
     def run(gaps):
         """Submit M requests (cycling the pool) after the given gaps; a poller
         thread collects them in order. Returns (events/s, latencies ms)."""
@@ -611,7 +613,8 @@ def serve_leg(a, kf, dev, rank, tuning=None):
         def poller():
             for i in range(M):
                 ready.acquire()
-                r = kf.kf_poll(ctx, tickets[i], pool[i % len(pool)]["seed_par"].shape[1], 7, 120_000_000)
+                r = kf.kf_poll(ctx, tickets[i], pool[i % len(pool)]["seed_par"].shape[1], 7, 120_000_000,
+                               refit_layers=refit_layers[0])
                 lat[i] = r["latency_ms"]
         th = threading.Thread(target=poller)
         th.start()
@@ -644,6 +647,14 @@ def serve_leg(a, kf, dev, rank, tuning=None):
                      "p99_ms": float(np.percentile(lat, 99))})
     st = kf.kf_serve_stats_get(ctx)
     kf.kf_serve_stop(ctx)
+    # the same stream at saturation with the re-fit fused into each request
+    kf.kf_serve_start(ctx, 3, 7, 6, max_slots=kf.MAX_SLOTS, max_queue=1 << 16, device_arena_bytes=16 << 30,
+                      host_arena_bytes=3 << 30, refit=True)
+    refit_layers[0] = 10
+    for ev in pool[:4]:
+        kf.kf_poll(ctx, submit(ev), ev["seed_par"].shape[1], 7, 120_000_000, refit_layers=10)
+    sat_r, lat_r = run(np.zeros(M))
+    kf.kf_serve_stop(ctx)
     ctx.close()
     return {"workload": f"Poisson stream of events, tracks log-uniform 500-50000 (pool of {len(pool)} events, "
                         f"mean {int(sizes.mean())} tracks), 3x noise hits per layer, build N = 6 on layers 4-10 "
@@ -653,6 +664,10 @@ def serve_leg(a, kf, dev, rank, tuning=None):
                                                               "p99_ms": float(np.percentile(lat_sat, 99))},
             "poisson": runs, "serial_one_at_a_time_events_per_s": serial,
             "continuous_batching_speedup": sat / serial,
+            "with_refit": {"events_per_s": sat_r, "p50_ms": float(np.percentile(lat_r, 50)),
+                           "p99_ms": float(np.percentile(lat_r, 99)),
+                           "note": "build followed by the fit of every best candidate over all 10 layers, "
+                                   "in the same request"},
             "max_resident_events": st["max_resident"], "step_launches": st["step_launches"],
             "iterations": st["iterations"]}
 

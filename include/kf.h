@@ -313,6 +313,9 @@ typedef struct {
     int32_t max_cands;          /* 1 .. 8 */
     int32_t max_slots;          /* resident events, 1 .. KF_MAX_SLOTS */
     int32_t max_queue;          /* submitted, not yet admitted events (>= 1) */
+    int32_t refit;              /* 1: after the build, fit every seed's best candidate over all
+                                   n_seed_layers + n_build_layers layers with its hits (as
+                                   kf_refit) inside the same request; 0: build only */
     size_t device_arena_bytes;  /* device memory for resident events (0: 1 GiB) */
     size_t host_arena_bytes;    /* pinned host memory for queued inputs and results (0: 1 GiB) */
 } kf_serve_config;
@@ -339,6 +342,11 @@ typedef struct {
     int32_t *hit_idx;       /* [n_build_layers][n_seeds], -1 = none */
     double latency_ms;      /* written: kf_submit -> results on the host */
     double queued_ms;       /* written: kf_submit -> admitted */
+    /* re-fit results (kf_serve_config.refit = 1; L = n_seed_layers + n_build_layers) */
+    float *refit_par;       /* [6][n_seeds] state at the last layer (position hi parts) */
+    float *refit_cov;       /* [21][n_seeds] */
+    float *refit_chi2;      /* [L][n_seeds] chi2 increment per layer, -1 where no hit */
+    int32_t *refit_status;  /* [n_seeds] KF_ST_* bits of the re-fit */
 } kf_event_result;
 
 typedef struct {

@@ -132,6 +132,22 @@ struct FitF64Args {
 cudaError_t launch_fit_layer(const FitLayerArgs& a, int block, cudaStream_t st);
 cudaError_t launch_fit_fused(const FitFusedArgs& a, cudaStream_t st, bool upd64 = false);
 cudaError_t launch_fit_f64(const FitF64Args& a, cudaStream_t st);
+
+// Hits of all layers per seed for a re-fit (kf_refit.cu): seeding layers from
+// the seed hits, building layers by the build's hit ids.
+struct RefitGatherArgs {
+  const float* seed_xyz;      // [Ls][3][n]
+  const uint8_t* seed_valid;  // [Ls][n] or null (all valid)
+  const int64_t* seed_off;    // [E + 1]
+  const float* hit_xyz;       // [3][n_hits]
+  const int64_t* seg_off;     // [E * Lb + 1]
+  const int32_t* hit_idx;     // [Lb][n]
+  float* xyz;                 // [Ls + Lb][3][n]
+  uint8_t* valid;             // [Ls + Lb][n]
+  int64_t n, n_hits;
+  int Ls, Lb, E;
+};
+cudaError_t launch_refit_gather(const RefitGatherArgs& a, cudaStream_t st);
 int fit_grid(int block, int64_t n);
 
 }  // namespace kfi

@@ -10,19 +10,6 @@
 
 namespace kfi {
 
-struct RefitGatherArgs {
-  const float* seed_xyz;      // [Ls][3][n]
-  const uint8_t* seed_valid;  // [Ls][n] or null (all valid)
-  const int64_t* seed_off;    // [E + 1]
-  const float* hit_xyz;       // [3][n_hits]
-  const int64_t* seg_off;     // [E * Lb + 1]
-  const int32_t* hit_idx;     // [Lb][n]
-  float* xyz;                 // [Ls + Lb][3][n]
-  uint8_t* valid;             // [Ls + Lb][n]
-  int64_t n, n_hits;
-  int Ls, Lb, E;
-};
-
 // event of seed i: the e with seed_off[e] <= i < seed_off[e + 1]
 __device__ __forceinline__ int event_of(const int64_t* off, int E, int64_t i) {
   int lo = 0, hi = E - 1;
@@ -74,6 +61,13 @@ __global__ void refit_gather_kernel(const RefitGatherArgs A) {
   A.valid[int64_t(l) * n + i] = ok;
 }
 
+cudaError_t launch_refit_gather(const RefitGatherArgs& a, cudaStream_t st) {
+  const int64_t threads = int64_t(a.Ls + a.Lb) * a.n;
+  if (threads <= 0) return cudaSuccess;
+  refit_gather_kernel<<<int((threads + 255) / 256), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 }  // namespace kfi
 
 using namespace kfi;
@@ -109,9 +103,7 @@ extern "C" int kf_refit(kf_ctx* ctx, const kf_tracks* seeds, const kf_track_hits
   g.Ls = Ls;
   g.Lb = Lb;
   g.E = E;
-  const int64_t threads = int64_t(L) * n;
-  refit_gather_kernel<<<int((threads + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(g);
-  KF_CUDA_TRY(ctx, cudaGetLastError());
+  KF_CUDA_TRY(ctx, launch_refit_gather(g, static_cast<cudaStream_t>(stream)));
   kf_track_hits all;
   all.n_tracks = n;
   all.n_layers = L;

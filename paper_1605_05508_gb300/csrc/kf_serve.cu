@@ -91,18 +91,22 @@ enum ReqState { kQueued, kResident, kFinishing, kDone, kFailed };
 struct EventLayout {
   int64_t n, nh;
   int ns, Lb;
+  bool refit;
   // device offsets
   size_t d_par, d_cov, d_q, d_shits, d_sval, d_fpar, d_flo, d_fcov, d_fst, d_xyz, d_segoff, d_sseg, d_bhits, d_boff,
-      d_bid, d_perm, d_candA, d_candB, d_hp, d_hh, d_rpar, d_rcov, d_rchi, d_rnh, d_rst, d_rhit, d_total;
+      d_bid, d_perm, d_candA, d_candB, d_hp, d_hh, d_rpar, d_rcov, d_rchi, d_rnh, d_rst, d_rhit, d_qpar, d_qcov,
+      d_qchi, d_qst, d_gxyz, d_gval, d_total;
   // host input / output block offsets
   size_t h_par, h_cov, h_q, h_shits, h_sval, h_xyz, h_segoff, h_in_total;
-  size_t o_par, o_cov, o_chi, o_nh, o_st, o_hit, h_out_total;
+  size_t o_par, o_cov, o_chi, o_nh, o_st, o_hit, o_qpar, o_qcov, o_qchi, o_qst, h_out_total;
 
-  void make(int64_t n_, int64_t nh_, int ns_, int Lb_) {
+  void make(int64_t n_, int64_t nh_, int ns_, int Lb_, bool refit_) {
     n = n_;
     nh = nh_;
     ns = ns_;
     Lb = Lb_;
+    refit = refit_;
+    const size_t L = size_t(ns + Lb);
     size_t o = 0;
     auto take = [&](size_t b) {
       const size_t at = o;
@@ -135,6 +139,13 @@ struct EventLayout {
     d_rnh = take(n * 4);
     d_rst = take(n * 4);
     d_rhit = take(size_t(Lb) * n * 4);
+    // re-fit results follow the build results (one contiguous copy back)
+    d_qpar = take(refit ? 6 * n * 4 : 0);
+    d_qcov = take(refit ? 21 * n * 4 : 0);
+    d_qchi = take(refit ? L * n * 4 : 0);
+    d_qst = take(refit ? n * 4 : 0);
+    d_gxyz = take(refit ? L * 3 * n * 4 : 0);
+    d_gval = take(refit ? L * n : 0);
     d_total = o;
     o = 0;
     h_par = take(6 * n * 4);
@@ -152,6 +163,10 @@ struct EventLayout {
     o_nh = take(n * 4);
     o_st = take(n * 4);
     o_hit = take(size_t(Lb) * n * 4);
+    o_qpar = take(refit ? 6 * n * 4 : 0);
+    o_qcov = take(refit ? 21 * n * 4 : 0);
+    o_qchi = take(refit ? L * n * 4 : 0);
+    o_qst = take(refit ? n * 4 : 0);
     h_out_total = o;
   }
 };
@@ -325,7 +340,50 @@ static cudaError_t finish(Serve* sv, Request* r) {
   fa.out.status = reinterpret_cast<int32_t*>(d + L.d_rst);
   fa.out.hit_idx = reinterpret_cast<int32_t*>(d + L.d_rhit);
   cudaError_t e = launch_build_final(fa, s);
-  // results are contiguous on the device (rpar .. rhit) and in the output block
+  if (e == cudaSuccess && L.refit) {
+    // re-fit: every seed's hits over all layers, then one fused fit launch
+    // from the vertex seed (the same arithmetic as kf_refit / kf_fit)
+    RefitGatherArgs g;
+    g.seed_xyz = reinterpret_cast<const float*>(d + L.d_shits);
+    g.seed_valid = reinterpret_cast<const uint8_t*>(d + L.d_sval);
+    g.seed_off = reinterpret_cast<const int64_t*>(d + L.d_sseg);
+    g.hit_xyz = reinterpret_cast<const float*>(d + L.d_xyz);
+    g.seg_off = reinterpret_cast<const int64_t*>(d + L.d_segoff);
+    g.hit_idx = reinterpret_cast<const int32_t*>(d + L.d_rhit);
+    g.xyz = reinterpret_cast<float*>(d + L.d_gxyz);
+    g.valid = reinterpret_cast<uint8_t*>(d + L.d_gval);
+    g.n = n;
+    g.n_hits = L.nh;
+    g.Ls = L.ns;
+    g.Lb = L.Lb;
+    g.E = 1;
+    e = launch_refit_gather(g, s);
+    if (e == cudaSuccess) {
+      kf_ctx* ctx = sv->ctx;
+      FitFusedArgs q;
+      std::memset(&q, 0, sizeof q);
+      q.in_par = reinterpret_cast<const float*>(d + L.d_par);
+      q.in_lo = nullptr;
+      q.in_cov = reinterpret_cast<const float*>(d + L.d_cov);
+      q.charge = reinterpret_cast<const int8_t*>(d + L.d_q);
+      q.out_par = reinterpret_cast<float*>(d + L.d_qpar);
+      q.out_lo = nullptr;
+      q.out_cov = reinterpret_cast<float*>(d + L.d_qcov);
+      q.hits = g.xyz;
+      q.valid = g.valid;
+      q.chi2 = reinterpret_cast<float*>(d + L.d_qchi);
+      q.status = reinterpret_cast<int32_t*>(d + L.d_qst);
+      q.n = n;
+      q.n_layers = L.ns + L.Lb;
+      q.a_scale = float(kCLight * double(ctx->cfg.bz_tesla));
+      q.v0 = q.v1 = ctx->cfg.sigma_xy_cm * ctx->cfg.sigma_xy_cm;
+      q.v2 = ctx->cfg.sigma_z_cm * ctx->cfg.sigma_z_cm;
+      for (int l = 0; l < L.ns + L.Lb; ++l) q.R[l] = ctx->radius[l];
+      e = launch_fit_fused(q, s);
+    }
+  }
+  // results are contiguous on the device (rpar .. rhit, then the re-fit's)
+  // and in the output block
   if (e == cudaSuccess) e = cudaMemcpyAsync(o, d + L.d_rpar, L.h_out_total, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaEventRecord(r->done, s);
   return e;
@@ -502,7 +560,7 @@ int kf_serve_start(kf_ctx* ctx, const kf_serve_config* cfg) {
       cfg->n_seed_layers + cfg->n_build_layers > ctx->cfg.n_layers || cfg->n_seed_layers > kMaxLayers)
     return KF_EINVAL;
   if (cfg->max_cands < 1 || cfg->max_cands > kGroup || cfg->max_slots < 1 || cfg->max_slots > KF_MAX_SLOTS ||
-      cfg->max_queue < 1)
+      cfg->max_queue < 1 || (cfg->refit != 0 && cfg->refit != 1))
     return KF_EINVAL;
   KF_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   auto* sv = new (std::nothrow) Serve();
@@ -567,7 +625,7 @@ int kf_submit(kf_ctx* ctx, const kf_event* ev, uint64_t* ticket) {
   const int64_t nh = ev->layer_off[Lb];
   if (nh > 0 && !ev->layer_xyz) return KF_EINVAL;
   auto req = std::make_unique<Request>();
-  req->lay.make(n, nh, ns, Lb);
+  req->lay.make(n, nh, ns, Lb, sv->cfg.refit != 0);
   const EventLayout& L = req->lay;
   {
     std::lock_guard<std::mutex> lk(sv->mu);
@@ -648,6 +706,13 @@ int kf_poll(kf_ctx* ctx, uint64_t ticket, kf_event_result* out, int64_t timeout_
   if (out->n_hits) std::memcpy(out->n_hits, o + L.o_nh, n * 4);
   if (out->status) std::memcpy(out->status, o + L.o_st, n * 4);
   if (out->hit_idx) std::memcpy(out->hit_idx, o + L.o_hit, size_t(L.Lb) * n * 4);
+  if (L.refit) {
+    const size_t Lall = size_t(L.ns + L.Lb);
+    if (out->refit_par) std::memcpy(out->refit_par, o + L.o_qpar, 6 * n * 4);
+    if (out->refit_cov) std::memcpy(out->refit_cov, o + L.o_qcov, 21 * n * 4);
+    if (out->refit_chi2) std::memcpy(out->refit_chi2, o + L.o_qchi, Lall * n * 4);
+    if (out->refit_status) std::memcpy(out->refit_status, o + L.o_qst, n * 4);
+  }
   out->latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
   out->queued_ms = std::chrono::duration<double, std::milli>(r->t_admit - r->t_submit).count();
   release_locked(sv, r);

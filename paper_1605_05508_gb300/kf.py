@@ -66,8 +66,8 @@ class kf_build_result(C.Structure):
 
 class kf_serve_config(C.Structure):
     _fields_ = [("n_seed_layers", C.c_int32), ("n_build_layers", C.c_int32), ("max_cands", C.c_int32),
-                ("max_slots", C.c_int32), ("max_queue", C.c_int32), ("device_arena_bytes", C.c_size_t),
-                ("host_arena_bytes", C.c_size_t)]
+                ("max_slots", C.c_int32), ("max_queue", C.c_int32), ("refit", C.c_int32),
+                ("device_arena_bytes", C.c_size_t), ("host_arena_bytes", C.c_size_t)]
 
 
 class kf_event(C.Structure):
@@ -79,7 +79,8 @@ class kf_event(C.Structure):
 class kf_event_result(C.Structure):
     _fields_ = [("best_par", C.c_void_p), ("best_cov", C.c_void_p), ("chi2_tot", C.c_void_p),
                 ("n_hits", C.c_void_p), ("status", C.c_void_p), ("hit_idx", C.c_void_p),
-                ("latency_ms", C.c_double), ("queued_ms", C.c_double)]
+                ("latency_ms", C.c_double), ("queued_ms", C.c_double), ("refit_par", C.c_void_p),
+                ("refit_cov", C.c_void_p), ("refit_chi2", C.c_void_p), ("refit_status", C.c_void_p)]
 
 
 class kf_serve_stats(C.Structure):
@@ -387,9 +388,9 @@ def kf_autotune_build(ctx, seeds: Tracks, seed_off, bins: HitBins, max_cands: in
 
 
 def kf_serve_start(ctx, n_seed_layers=3, n_build_layers=7, max_cands=6, max_slots=MAX_SLOTS, max_queue=1024,
-                   device_arena_bytes=0, host_arena_bytes=0):
-    cfg = kf_serve_config(n_seed_layers, n_build_layers, max_cands, max_slots, max_queue, device_arena_bytes,
-                          host_arena_bytes)
+                   device_arena_bytes=0, host_arena_bytes=0, refit=False):
+    cfg = kf_serve_config(n_seed_layers, n_build_layers, max_cands, max_slots, max_queue, int(bool(refit)),
+                          device_arena_bytes, host_arena_bytes)
     _check(lib().kf_serve_start(_h(ctx), C.byref(cfg)), "kf_serve_start", _h(ctx))
 
 
@@ -417,15 +418,24 @@ def kf_submit(ctx, event: dict) -> int:
     return t.value
 
 
-def kf_poll(ctx, ticket: int, n_seeds: int, n_build_layers: int, timeout_us: int = -1, want_cov: bool = False):
-    """Returns a dict of numpy results, or raises KfError (KF_ETIMEDOUT if not done)."""
+def kf_poll(ctx, ticket: int, n_seeds: int, n_build_layers: int, timeout_us: int = -1, want_cov: bool = False,
+            refit_layers: int = 0):
+    """Returns a dict of numpy results, or raises KfError (KF_ETIMEDOUT if not done).
+    refit_layers > 0 (serving started with refit=True): also the re-fit's results
+    (refit_chi2 has refit_layers rows)."""
     import numpy as np
     out = dict(best_par=np.empty((6, n_seeds), np.float32),
                best_cov=np.empty((21, n_seeds), np.float32) if want_cov else None,
                chi2_tot=np.empty(n_seeds, np.float32), n_hits=np.empty(n_seeds, np.int32),
                status=np.empty(n_seeds, np.int32), hit_idx=np.empty((n_build_layers, n_seeds), np.int32))
+    if refit_layers:
+        out.update(refit_par=np.empty((6, n_seeds), np.float32),
+                   refit_cov=np.empty((21, n_seeds), np.float32) if want_cov else None,
+                   refit_chi2=np.empty((refit_layers, n_seeds), np.float32),
+                   refit_status=np.empty(n_seeds, np.int32))
     r = kf_event_result(*[_np_ptr(out[k]) for k in ("best_par", "best_cov", "chi2_tot", "n_hits", "status",
-                                                      "hit_idx")], 0.0, 0.0)
+                                                      "hit_idx")], 0.0, 0.0,
+                        *[_np_ptr(out.get(k)) for k in ("refit_par", "refit_cov", "refit_chi2", "refit_status")])
     _check(lib().kf_poll(_h(ctx), C.c_uint64(ticket), C.byref(r), int(timeout_us)), "kf_poll")
     out["latency_ms"], out["queued_ms"] = r.latency_ms, r.queued_ms
     return out

@@ -12,8 +12,9 @@ from fitutil import compare, oracle_fit, to_dev, unpack
 pytestmark = pytest.mark.gpu
 
 
-def pipeline(ctx, batch, max_cands):
-    """seed fit -> bin -> build -> refit through the binding."""
+def pipeline(ctx, batch, max_cands, raw=False):
+    """seed fit -> bin -> build -> refit through the binding (raw: the
+    re-fit's float32 outputs as returned, position hi parts only)."""
     import torch
     from paper_1605_05508_gb300 import kf
     n = batch.seeds.par.shape[1]
@@ -42,6 +43,9 @@ def pipeline(ctx, batch, max_cands):
     rst = torch.empty(n, **i32)
     kf.kf_refit(ctx, s, fh, seed_off, lh, out.hit_idx, ro, rchi2, rst)
     torch.cuda.synchronize()
+    if raw:
+        return out.hit_idx.cpu().numpy(), dict(par=ro.par.cpu().numpy(), chi2=rchi2.cpu().numpy(),
+                                               status=rst.cpu().numpy())
     return out.hit_idx.cpu().numpy(), unpack(ro, rchi2, rst)
 
 

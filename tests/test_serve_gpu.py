@@ -148,3 +148,26 @@ def test_concurrent_submitters_and_pollers(cuda_ctx_factory):
         t.join()
     kf.kf_serve_stop(ctx)
     assert not errors, errors
+
+
+def test_served_refit_equals_batch_refit(cuda_ctx_factory):
+    """refit = 1: each served request also fits its best candidates over all
+    10 layers; the result is bitwise that of kf_build + kf_refit on the
+    event alone."""
+    from paper_1605_05508_gb300 import kf
+    from test_refit_gpu import pipeline
+    det = S.barrel()
+    ctx = cuda_ctx_factory(det.radii)
+    sizes = [500, 1700, 90, 2600]
+    evs = [_event(300 + i, n) for i, n in enumerate(sizes)]
+    kf.kf_serve_start(ctx, 3, 7, 6, max_slots=32, device_arena_bytes=1 << 30, host_arena_bytes=1 << 29, refit=True)
+    tickets = [kf.kf_submit(ctx, ev) for _, ev in evs]
+    res = [kf.kf_poll(ctx, t, n, 7, 60_000_000, refit_layers=10) for t, n in zip(tickets, sizes)]
+    kf.kf_serve_stop(ctx)
+    for (b, _), r in zip(evs, res):
+        hit_idx, g = pipeline(ctx, b, 6, raw=True)
+        np.testing.assert_array_equal(hit_idx, r["hit_idx"])
+        np.testing.assert_array_equal(g["par"], r["refit_par"])
+        np.testing.assert_array_equal(g["chi2"], r["refit_chi2"])
+        np.testing.assert_array_equal(g["status"], r["refit_status"])
+        assert np.mean(r["refit_chi2"][r["refit_chi2"] >= 0]) < 4.0
