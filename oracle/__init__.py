@@ -65,9 +65,11 @@ def lib():
             L.orc_chi2.restype = C.c_double
             L.orc_update.argtypes = [d, d, d, d, d, d, d, d]
             L.orc_pd5.argtypes = [d, d]
-            L.orc_fit.argtypes = [i64, C.c_int, d, d, d, d, d, d, u8, d, d, d, i32, C.c_int]
+            L.orc_fit.argtypes = [i64, C.c_int, d, d, d, d, d, d, u8, d, d, d, i32, d, C.c_double, C.c_int]
+            L.orc_scattering_q.argtypes = [d, C.c_double, C.c_double, d]
+            L.orc_scattering_q.restype = None
             L.orc_build.argtypes = [i64, C.c_int, d, d, C.c_double, C.c_int, d, d, d, i32, d,
-                                    C.POINTER(C.c_int64), d, d, d, i32, i32, i32, i32, C.c_int]
+                                    C.POINTER(C.c_int64), d, d, d, i32, i32, i32, i32, d, C.c_double, C.c_int]
             L.orc_max_threads.restype = C.c_int
             _lib = L
     return _lib
@@ -156,12 +158,31 @@ def max_threads() -> int:
 
 # ---------------------------------------------------------------- batched fit / build
 
+PION_MASS = 0.13957  # GeV: default particle hypothesis of the scattering model
+
+
+def _material(x_x0, L):
+    if x_x0 is None:
+        return None
+    m = _f64(x_x0)
+    assert m.shape == (L,)
+    return m
+
+
+def scattering_q(x, x_x0: float, mass: float = PION_MASS) -> np.ndarray:
+    """[6, 6] process noise of multiple scattering at the crossing state x."""
+    Q = np.zeros(36)
+    lib().orc_scattering_q(_p(_f64(x)), float(x_x0), float(mass), _p(Q))
+    return Q.reshape(6, 6)
+
+
 def fit(seed_par, seed_cov_packed, charge, hit_xyz, hit_valid, radii, bz, sigma_xy, sigma_z,
-        n_threads: int = 0):
+        n_threads: int = 0, x_x0=None, mass: float = PION_MASS):
     """Fit every track over all layers.
 
     seed_par float [6, n]; seed_cov_packed float [21, n]; charge int [n];
-    hit_xyz float [L, 3, n]; hit_valid uint8 [L, n]. Inputs are upcast to FP64.
+    hit_xyz float [L, 3, n]; hit_valid uint8 [L, n]; x_x0 [L] layer thickness
+    in radiation lengths (None: no material). Inputs are upcast to FP64.
     Returns dict(par [n, 6], cov [n, 6, 6], chi2 [L, n] (-1: no update), status [n]).
     """
     seed_par = np.asarray(seed_par)
@@ -176,13 +197,16 @@ def fit(seed_par, seed_cov_packed, charge, hit_xyz, hit_valid, radii, bz, sigma_
     V = _f64([sigma_xy ** 2, sigma_xy ** 2, sigma_z ** 2])
     out_par, out_cov = np.zeros((n, 6)), np.zeros((n, 6, 6))
     c2, st = np.zeros((L, n)), np.zeros(n, dtype=np.int32)
+    mat = _material(x_x0, L)
     lib().orc_fit(n, L, _p(rad), _p(V), _p(sp), _p(sc), _p(ac), _p(hits), _p(val, C.c_uint8),
-                  _p(out_par), _p(out_cov), _p(c2), _p(st, C.c_int32), n_threads)
+                  _p(out_par), _p(out_cov), _p(c2), _p(st, C.c_int32), _p(mat) if mat is not None else None,
+                  float(mass), n_threads)
     return dict(par=out_par, cov=out_cov, chi2=c2, status=st)
 
 
 def build_tracks(seed_par, seed_cov, charge, seed_event, layer_xyz, layer_off, radii, bz,
-                 sigma_xy, sigma_z, chi2_cut=30.0, max_cands=6, n_threads: int = 0):
+                 sigma_xy, sigma_z, chi2_cut=30.0, max_cands=6, n_threads: int = 0, x_x0=None,
+                 mass: float = PION_MASS):
     """Combinatorial build over the given layers (clone engine, all-hits scan).
 
     seed_par float [n, 6] or [6, n] (see below); seed_cov [n, 6, 6] float64;
@@ -209,7 +233,8 @@ def build_tracks(seed_par, seed_cov, charge, seed_event, layer_xyz, layer_off, r
     rc = lib().orc_build(n, L, _p(rad), _p(V), float(chi2_cut), N, _p(sp), _p(sc), _p(ac),
                          _p(ev, C.c_int32), _p(hits), off.ctypes.data_as(C.POINTER(C.c_int64)),
                          _p(cp), _p(cc), _p(cchi), _p(cnh, C.c_int32), _p(chits, C.c_int32),
-                         _p(cst, C.c_int32), _p(ncand, C.c_int32), n_threads)
+                         _p(cst, C.c_int32), _p(ncand, C.c_int32),
+                         _p(_material(x_x0, L)) if x_x0 is not None else None, float(mass), n_threads)
     if rc != 0:
         raise ValueError("orc_build rejected its arguments")
     return dict(par=cp, cov=cc, chi2=cchi, nhits=cnh, hits=chits, status=cst, n_cands=ncand)

@@ -35,6 +35,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 C_LIGHT = 0.00299792458  # GeV / (T cm): pT[GeV] = C_LIGHT * B[T] * rho[cm]
+PION_MASS = 0.13957  # GeV: the particle hypothesis of the scattering model
 
 TRIL_I, TRIL_J = np.tril_indices(6)  # row-major packed lower triangle order
 
@@ -58,10 +59,29 @@ class Detector:
     bz: float = 3.8
     sigma_xy: float = 0.01
     sigma_z: float = 0.1
+    # thickness of each layer in radiation lengths at normal incidence (None:
+    # no material); the particles are simulated as pions
+    x_x0: tuple | None = None
+    mass: float = PION_MASS
 
     @property
     def n_layers(self) -> int:
         return len(self.radii)
+
+    @property
+    def has_material(self) -> bool:
+        return self.x_x0 is not None and any(x > 0 for x in self.x_x0)
+
+
+def highland_theta0(p, x_eff, mass=PION_MASS):
+    """RMS of the projected multiple-scattering angle of a unit-charge particle
+    of momentum p (GeV) after x_eff radiation lengths: the Highland formula
+    with the Lynch-Dahl logarithm, as in the Review of Particle Physics
+    (passage of particles through matter),
+      theta0 = 13.6 MeV / (beta c p) sqrt(x/X0) (1 + 0.038 ln(x / (X0 beta^2)))."""
+    p = np.asarray(p, dtype=np.float64)
+    beta2 = p * p / (p * p + mass * mass)
+    return 0.0136 / (np.sqrt(beta2) * p) * np.sqrt(x_eff) * (1.0 + 0.038 * np.log(x_eff / beta2))
 
 
 def barrel(n_layers: int = 10, spacing: float = 4.0, **kw) -> Detector:
@@ -175,10 +195,36 @@ def helix_crossing(vertex: np.ndarray, mom: np.ndarray, charge: np.ndarray,
     return out, reached
 
 
+def _kink(rng: np.random.Generator, state: np.ndarray, ok: np.ndarray, x_x0: float, mass: float) -> None:
+    """Multiple scattering in a thin layer at the crossing `state` [n, 6]
+    (in place, rows `ok`): the direction turns by two independent Gaussian
+    projected angles of RMS theta0 (Highland, path x_x0 / cos(incidence)) in
+    two planes containing it; |p| is unchanged."""
+    n = len(state)
+    pos, mom = state[:, :3], state[:, 3:]
+    p = np.linalg.norm(mom, axis=1)
+    d = mom / p[:, None]
+    r = np.hypot(pos[:, 0], pos[:, 1])
+    cos_inc = np.abs(pos[:, 0] * d[:, 0] + pos[:, 1] * d[:, 1]) / r
+    th0 = highland_theta0(p, x_x0 / np.maximum(cos_inc, 1e-6), mass)
+    u1 = np.stack([-d[:, 1], d[:, 0], np.zeros(n)], axis=1)  # z x d
+    u1 /= np.linalg.norm(u1, axis=1)[:, None]
+    u2 = np.cross(d, u1)
+    t1, t2 = rng.normal(0.0, 1.0, n) * th0, rng.normal(0.0, 1.0, n) * th0
+    nd = d + np.tan(t1)[:, None] * u1 + np.tan(t2)[:, None] * u2
+    nd /= np.linalg.norm(nd, axis=1)[:, None]
+    state[ok, 3:] = (nd * p[:, None])[ok]
+
+
 def simulate_hits(rng: np.random.Generator, parts: Particles, det: Detector,
                   keep_truth: bool = True) -> TrackHits:
     """Truth crossings on every layer plus the Gaussian hit smear.
+    With material (det.x_x0) the helix is followed layer by layer and the
+    direction is kinked by multiple scattering at every crossing; the truth
+    state of a layer is the crossing point with the momentum leaving it.
     `keep_truth=False` skips the [L, n, 6] float64 truth array (large batches)."""
+    if det.has_material:
+        return _simulate_hits_material(rng, parts, det, keep_truth)
     L, n = det.n_layers, parts.n
     xyz = np.zeros((L, 3, n), dtype=np.float32)
     valid = np.zeros((L, n), dtype=np.uint8)
@@ -195,6 +241,32 @@ def simulate_hits(rng: np.random.Generator, parts: Particles, det: Detector,
         h = np.where(ok[:, None], st[:, :3] + smear, 0.0)
         xyz[li] = h.T.astype(np.float32)
         valid[li] = ok
+    return TrackHits(xyz=xyz, valid=valid, truth=truth)
+
+
+def _simulate_hits_material(rng, parts, det, keep_truth):
+    L, n = det.n_layers, parts.n
+    xyz = np.zeros((L, 3, n), dtype=np.float32)
+    valid = np.zeros((L, n), dtype=np.uint8)
+    truth = np.full((L, n, 6), np.nan) if keep_truth else None
+    alive = np.ones(n, dtype=bool)
+    pos, mom = parts.vertex.copy(), parts.mom.copy()
+    for li, R in enumerate(det.radii):
+        st, ok = helix_crossing(pos, mom, parts.charge, det.bz, R)
+        ok &= alive
+        alive = ok
+        smear = np.stack([rng.normal(0.0, det.sigma_xy, n), rng.normal(0.0, det.sigma_xy, n),
+                          rng.normal(0.0, det.sigma_z, n)], axis=1)
+        h = np.where(ok[:, None], st[:, :3] + smear, 0.0)
+        xyz[li] = h.T.astype(np.float32)
+        valid[li] = ok
+        if det.x_x0[li] > 0:
+            st = np.where(ok[:, None], st, np.nan)
+            _kink(rng, st, ok, det.x_x0[li], det.mass)
+        if keep_truth:
+            truth[li][ok] = st[ok]
+        pos = np.where(ok[:, None], st[:, :3], pos)
+        mom = np.where(ok[:, None], st[:, 3:], mom)
     return TrackHits(xyz=xyz, valid=valid, truth=truth)
 
 
