@@ -303,6 +303,8 @@ def run_ours(a):
     if not a.no_extras:
         torch.cuda.empty_cache()
         line["precision"] = precision_leg(a, kf, torch, dev, stream, rank)
+        torch.cuda.empty_cache()
+        line["material"] = material_leg(a, kf, torch, dev, stream)
     if not a.no_serve:
         torch.cuda.empty_cache()
         line["serving"] = serve_leg(a, kf, dev, rank, line.get("build", {}).get("tuning"))
@@ -513,6 +515,55 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist):
                                "sample": f"first {m} seeds of event 0 x {Lb} layers, N = 6, all-hits chi2 scan "
                                          f"(the oracle bins nothing), {cores} OpenMP threads, {dtc:.2f} s wall"}
     ctx.close()
+    return res
+
+
+def material_leg(a, kf, torch, dev, stream):
+    """Multiple scattering as process noise: 1 M tracks (pT U[0.5, 2] GeV)
+    simulated with scattering kinks in 10 layers of 3 % X0 each, fitted with
+    the per-layer graph; cost of the process noise and the fit statistics."""
+    from paper_1605_05508_gb300 import synth as S
+    det = S.barrel(10, x_x0=(0.03,) * 10)
+    n = 1_000_000
+    ev = S.make_fit_batch(a.seed + 5, n, det, pt_range=(0.5, 2.0))
+    T = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    seeds = kf.Tracks(T(ev.seeds.par), T(ev.seeds.cov), T(ev.seeds.charge))
+    hits = kf.TrackHits(T(ev.hits.xyz), T(ev.hits.valid))
+    out = kf.Tracks(torch.empty((6, n), device=dev), torch.empty((21, n), device=dev), seeds.charge,
+                    torch.empty((3, n), device=dev))
+    chi2 = torch.empty((10, n), device=dev)
+    st = torch.empty(n, dtype=torch.int32, device=dev)
+    res = {"workload": "1000000 tracks, pT U[0.5, 2] GeV, 10 layers of 3 % X0 (pion hypothesis), "
+                       "hits simulated with scattering kinks"}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for name, x0 in (("with_process_noise", det.x_x0), ("without", None)):
+        ctx = kf.Context(det.radii, det.bz, det.sigma_xy, det.sigma_z, device=dev.index, x_x0=x0, mass=det.mass)
+        for _ in range(3):
+            kf.kf_fit(ctx, seeds, hits, out, chi2, st, stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        k = 20
+        for _ in range(k):
+            kf.kf_fit(ctx, seeds, hits, out, chi2, st, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / k
+        c = chi2[chi2 >= 0]
+        tr = torch.from_numpy(ev.hits.truth[-1]).to(dev)
+        r = torch.hypot(tr[:, 0], tr[:, 1])
+        par = out.par.double().T.clone()
+        par[:, :3] += out.par_lo.double().T
+        d = par - tr
+        cov = torch.from_numpy(S.unpack_cov(out.cov.double().cpu().numpy().T)).to(dev)
+        tvec = torch.stack([-tr[:, 1] / r, tr[:, 0] / r], dim=1)
+        rt = d[:, 0] * tvec[:, 0] + d[:, 1] * tvec[:, 1]
+        vt = (tvec[:, 0] ** 2 * cov[:, 0, 0] + 2 * tvec[:, 0] * tvec[:, 1] * cov[:, 0, 1] +
+              tvec[:, 1] ** 2 * cov[:, 1, 1])
+        pulls = [rt / vt.sqrt()] + [d[:, i] / cov[:, i, i].sqrt() for i in (2, 3, 4, 5)]
+        res[name] = {"ms_per_step": ms, "track_layer_steps_per_s": n * 10 / (ms / 1e3),
+                     "chi2_per_hit_mean": float(c.mean()),
+                     "pull_widths_t_z_px_py_pz": [float(p.std()) for p in pulls]}
+        ctx.close()
     return res
 
 

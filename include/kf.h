@@ -61,6 +61,15 @@ typedef struct {
     float sigma_z_cm;        /* longitudinal hit smear */
     float chi2_cut;          /* building: keep hits with chi2 increment < cut */
     int32_t max_cands;       /* building: candidates kept per seed, 1 .. 8 */
+    /* Material (multiple scattering as process noise, Sec. 2): thickness of
+     * each layer in radiation lengths at normal incidence, [n_layers] host,
+     * each in [0, 1), or NULL for no material; and the particle mass (GeV,
+     * >= 0) of the scattering model.  After every propagation to a layer
+     * with material the momentum covariance gains theta0^2 (p^2 I - p p^T),
+     * theta0 the Highland formula with the Lynch-Dahl logarithm (Review of
+     * Particle Physics) over x/X0 / cos(incidence). */
+    const float *x_x0;
+    float mass_gev;
 } kf_config;
 
 /* A batch of tracks, single precision (device pointers). */

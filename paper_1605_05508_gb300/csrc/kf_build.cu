@@ -144,6 +144,8 @@ __global__ void __launch_bounds__(kBuildThreads) build_step_kernel(const BuildSt
     if (r) {
       st |= r;
       stopped = true;
+    } else if (D.x_x0 > 0.f) {
+      kf::scatter(p, lo, C, D.x_x0, Args.mass);
     }
   }
 
@@ -631,6 +633,7 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
     d.layer = l;
     d.n_layers = L;
     d.R = ctx->radius[bins->first_layer + l];
+    d.x_x0 = ctx->x_x0[bins->first_layer + l];
     d.block_begin = 0;
   }
   BuildSlot* dtable = reinterpret_cast<BuildSlot*>(base + b_perm + b_evt + 2 * b_cand + b_hp + b_hh);
@@ -645,6 +648,7 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
     a.v1 = v0;
     a.v2 = v2;
     a.cut = ctx->cfg.chi2_cut;
+    a.mass = ctx->mass;
     KF_CUDA_TRY(ctx, launch_build_step(a, grid, s, ctx->tune.build_hit_tile, ctx->tune.build_list_width));
   }
   BuildFinalArgs fa;

@@ -42,6 +42,7 @@ struct BuildSlot {
   int64_t S;
   int layer, n_layers;
   float R;
+  float x_x0;  // this layer's thickness in radiation lengths (0: none)
   int block_begin;
 };
 
@@ -49,6 +50,7 @@ struct BuildStepArgs {
   const BuildSlot* slots;  // device table
   int n_slots, max_cands;
   float a_scale, v0, v1, v2, cut;
+  float mass;  // particle mass of the scattering model
 };
 
 struct BuildInitArgs {

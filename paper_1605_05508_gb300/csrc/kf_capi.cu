@@ -91,7 +91,9 @@ int kf_create(kf_ctx** out, const kf_config* cfg, int device, size_t mem_budget_
   for (int l = 0; l < cfg->n_layers; ++l) {
     if (!(cfg->radius_cm[l] > prev) || !std::isfinite(cfg->radius_cm[l])) return KF_EINVAL;
     prev = cfg->radius_cm[l];
+    if (cfg->x_x0 && !(cfg->x_x0[l] >= 0.f && cfg->x_x0[l] < 1.f)) return KF_EINVAL;
   }
+  if (!(cfg->mass_gev >= 0.f) || !std::isfinite(cfg->mass_gev)) return KF_EINVAL;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
     cudaGetLastError();
@@ -100,8 +102,13 @@ int kf_create(kf_ctx** out, const kf_config* cfg, int device, size_t mem_budget_
   kf_ctx* ctx = new (std::nothrow) kf_ctx();
   if (!ctx) return KF_ENOMEM;
   ctx->cfg = *cfg;
-  for (int l = 0; l < cfg->n_layers; ++l) ctx->radius[l] = cfg->radius_cm[l];
+  for (int l = 0; l < kMaxLayers; ++l) {
+    ctx->radius[l] = l < cfg->n_layers ? cfg->radius_cm[l] : 0.f;
+    ctx->x_x0[l] = (l < cfg->n_layers && cfg->x_x0) ? cfg->x_x0[l] : 0.f;
+  }
+  ctx->mass = cfg->mass_gev;
   ctx->cfg.radius_cm = ctx->radius;
+  ctx->cfg.x_x0 = ctx->x_x0;
   ctx->device = device;
   ctx->budget = mem_budget_bytes;
   cudaError_t e = cudaSetDevice(device);
@@ -199,6 +206,8 @@ int kf_fit(kf_ctx* ctx, const kf_tracks* seeds, const kf_track_hits* hits, kf_tr
       a.n = n;
       a.a_scale = a_scale;
       a.R = ctx->radius[l];
+      a.x_x0 = ctx->x_x0[l];
+      a.mass = ctx->mass;
       a.v0 = v0;
       a.v1 = v0;
       a.v2 = v2;
@@ -266,7 +275,11 @@ static int fit_fused_impl(kf_ctx* ctx, const kf_tracks* seeds, const kf_track_hi
   a.a_scale = float(kCLight * double(ctx->cfg.bz_tesla));
   a.v0 = a.v1 = ctx->cfg.sigma_xy_cm * ctx->cfg.sigma_xy_cm;
   a.v2 = ctx->cfg.sigma_z_cm * ctx->cfg.sigma_z_cm;
-  for (int l = 0; l < hits->n_layers; ++l) a.R[l] = ctx->radius[l];
+  for (int l = 0; l < hits->n_layers; ++l) {
+    a.R[l] = ctx->radius[l];
+    a.x_x0[l] = ctx->x_x0[l];
+  }
+  a.mass = ctx->mass;
   KF_CUDA_TRY(ctx, launch_fit_fused(a, static_cast<cudaStream_t>(stream), upd64));
   return KF_OK;
 }
@@ -311,6 +324,8 @@ int kf_fit_f64(kf_ctx* ctx, const kf_tracks_f64* seeds, const kf_track_hits* hit
       a.end = event_off[e + 1];
       a.a_scale = kCLight * bz;
       a.R = double(ctx->radius[l]);
+      a.x_x0 = double(ctx->x_x0[l]);
+      a.mass = double(ctx->mass);
       a.v0 = a.v1 = sxy * sxy;
       a.v2 = sz * sz;
       a.first = l == 0;

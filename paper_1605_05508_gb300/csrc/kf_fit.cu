@@ -66,11 +66,12 @@ __device__ __forceinline__ bool pd5(const T p[6], const T C[21]) {
 // bits raised; writes chi2 (-1 when no update).  UPD64: S^-1 and the
 // covariance downdate in FP64 (single-precision state only).
 template <typename T, int NEWTON, bool EXT, bool UPD64 = false>
-__device__ __forceinline__ int32_t track_step(T p[6], T lo[3], T C[21], T a, T R, bool has_hit,
+__device__ __forceinline__ int32_t track_step(T p[6], T lo[3], T C[21], T a, T R, T x_x0, T mass, bool has_hit,
                                               T m0, T m1, T m2, T v0, T v1, T v2, T& chi2) {
   chi2 = T(-1);
   const int st = kf::propagate<T, NEWTON, EXT>(p, lo, C, a, R);
   if (st) return st;
+  if (x_x0 > T(0)) kf::scatter(p, lo, C, x_x0, mass);
   if (!has_hit) return kf::ST_NO_HIT;
   T r0, r1, r2;
   kf::residual<T, EXT>(p, lo, m0, m1, m2, r0, r1, r2);
@@ -96,7 +97,8 @@ __device__ __forceinline__ void fit_layer_track(const FitLayerArgs& A, int64_t i
   const float a = A.a_scale * float(q);
   float chi2;
   const int32_t raised =
-      track_step<float, kNewtonF32, true>(p, lo, C, a, A.R, has_hit, m0, m1, m2, A.v0, A.v1, A.v2, chi2);
+      track_step<float, kNewtonF32, true>(p, lo, C, a, A.R, A.x_x0, A.mass, has_hit, m0, m1, m2, A.v0, A.v1, A.v2,
+                                          chi2);
   const bool stopped = (raised & KF_ST_STOPPED) != 0;
   if (!stopped || A.first) {
 #pragma unroll
@@ -154,8 +156,8 @@ __global__ void __launch_bounds__(kFitThreads, UPD64 ? 1 : kFitMinBlocks) fit_fu
       if (!(st & KF_ST_STOPPED)) {
         const float* h = A.hits + int64_t(l) * 3 * n;
         const bool has_hit = A.valid ? A.valid[int64_t(l) * n + i] != 0 : true;
-        st |= track_step<float, kNewtonF32, true, UPD64>(p, lo, C, a, A.R[l], has_hit, h[i], h[n + i],
-                                                         h[2 * n + i], A.v0, A.v1, A.v2, chi2);
+        st |= track_step<float, kNewtonF32, true, UPD64>(p, lo, C, a, A.R[l], A.x_x0[l], A.mass, has_hit, h[i],
+                                                         h[n + i], h[2 * n + i], A.v0, A.v1, A.v2, chi2);
       }
       if (A.chi2) A.chi2[int64_t(l) * n + i] = chi2;
     }
@@ -190,7 +192,7 @@ __global__ void __launch_bounds__(kFitThreads) fit_f64_kernel(const FitF64Args A
   const bool has_hit = A.valid ? A.valid[i] != 0 : true;
   double chi2;
   const int32_t raised = track_step<double, kNewtonF64, false>(
-      p, lo, C, a, A.R, has_hit, double(A.hit[i]), double(A.hit[n + i]), double(A.hit[2 * n + i]), A.v0,
+      p, lo, C, a, A.R, A.x_x0, A.mass, has_hit, double(A.hit[i]), double(A.hit[n + i]), double(A.hit[2 * n + i]), A.v0,
       A.v1, A.v2, chi2);
   const bool stopped = (raised & KF_ST_STOPPED) != 0;
   if (!stopped || A.first) {

@@ -37,6 +37,8 @@ struct Serve;  // serving loop state (kf_serve.cu)
 struct kf_ctx {
   kf_config cfg;
   float radius[kfi::kMaxLayers];
+  float x_x0[kfi::kMaxLayers];  // layer material (radiation lengths; 0: none)
+  float mass = 0.f;             // particle mass of the scattering model
   int device = 0;
   int num_sms = 0;
   size_t budget = 0;     // 0 = unbounded
@@ -86,6 +88,7 @@ struct FitLayerArgs {
   int64_t n;
   float a_scale;  // C_LIGHT * Bz
   float R, v0, v1, v2;
+  float x_x0, mass;  // this layer's thickness in radiation lengths (0: none); particle mass
   int first;  // 1: initialise status, always write the state
   int last;   // 1: run the positive-definite check
 };
@@ -106,7 +109,9 @@ struct FitFusedArgs {
   int n_layers;
   float a_scale;
   float v0, v1, v2;
-  float R[kMaxLayers];  // layer radii, by value
+  float mass;
+  float R[kMaxLayers];     // layer radii, by value
+  float x_x0[kMaxLayers];  // layer thickness in radiation lengths (0: none)
 };
 
 struct FitF64Args {
@@ -124,6 +129,7 @@ struct FitF64Args {
   int64_t end;
   double a_scale;
   double R, v0, v1, v2;
+  double x_x0, mass;
   int first, last;
 };
 

@@ -61,6 +61,8 @@ KF_HD double fma_t(double a, double b, double c) { return fma(a, b, c); }
 
 KF_HD float sqrt_t(float x) { return sqrtf(x); }
 KF_HD double sqrt_t(double x) { return sqrt(x); }
+KF_HD float log_t(float x) { return logf(x); }
+KF_HD double log_t(double x) { return log(x); }
 KF_HD float abs_t(float x) { return fabsf(x); }
 KF_HD double abs_t(double x) { return fabs(x); }
 
@@ -416,6 +418,35 @@ KF_HD typename Lanes<T>::I propagate_lanes(T p[6], T lo[3], T C[21], T a, T R, t
 template <typename T, int NEWTON, bool EXT>
 KF_HD int propagate(T p[6], T lo[3], T C[21], T a, T R) {
   return propagate_lanes<T, NEWTON, EXT>(p, lo, C, a, R, true);
+}
+
+// Multiple scattering in a thin layer at the crossing just reached (Sec. 2:
+// the KF folds the expected multiple scattering into the trajectory's
+// uncertainty).  The direction turns by two independent projected angles of
+// RMS theta0 in planes containing p, |p| unchanged: the momentum block gains
+// theta0^2 (p^2 I - p p^T).  theta0 is the Highland formula with the
+// Lynch-Dahl logarithm (Review of Particle Physics, passage of particles
+// through matter) for a unit charge of mass `mass`:
+//   theta0 = 0.0136 GeV / (beta p) sqrt(xe) (1 + 0.038 ln(xe / beta^2)),
+// over xe = x_x0 / cos(incidence) radiation lengths, the incidence cosine
+// being that of p with the cylinder normal (x, y, 0)/r; 1/(beta p)^2 = E^2/p^4.
+template <typename T>
+KF_HD void scatter(const T p[6], const T lo[3], T C[21], T x_x0, T mass) {
+  const T X = p[0] + lo[0], Y = p[1] + lo[1];
+  const T P[3] = {p[3], p[4], p[5]};
+  const T p2 = fma_t(P[0], P[0], fma_t(P[1], P[1], P[2] * P[2]));
+  const T cos_inc = abs_t(fma_t(X, P[0], Y * P[1])) / sqrt_t(fma_t(X, X, Y * Y) * p2);
+  const T xe = x_x0 / (cos_inc > T(1e-6) ? cos_inc : T(1e-6));
+  const T e2 = fma_t(mass, mass, p2);
+  const T lg = fma_t(T(0.038), log_t(xe * (e2 / p2)), T(1.0));
+  const T th2 = ((T(0.0136 * 0.0136) * xe) * (lg * lg)) * (e2 / (p2 * p2));
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      const T d = i == j ? fma_t(-P[i], P[j], p2) : -(P[i] * P[j]);
+      C[sym(3 + i, 3 + j)] = fma_t(th2, d, C[sym(3 + i, 3 + j)]);
+    }
 }
 
 // Residual r = m - H x with the position carried as hi + lo.

@@ -78,6 +78,8 @@ extern "C" int kf_fit_noalloc(kf_ctx* ctx, const kf_tracks* seeds, const kf_trac
     a.n = n;
     a.a_scale = float(kfi::kCLight * double(ctx->cfg.bz_tesla));
     a.R = ctx->radius[l];
+    a.x_x0 = ctx->x_x0[l];
+    a.mass = ctx->mass;
     a.v0 = v0;
     a.v1 = v0;
     a.v2 = v2;

@@ -252,7 +252,11 @@ static cudaError_t prepare(Serve* sv, Request* r) {
   fa.a_scale = float(kCLight * double(ctx->cfg.bz_tesla));
   fa.v0 = fa.v1 = ctx->cfg.sigma_xy_cm * ctx->cfg.sigma_xy_cm;
   fa.v2 = ctx->cfg.sigma_z_cm * ctx->cfg.sigma_z_cm;
-  for (int l = 0; l < L.ns; ++l) fa.R[l] = ctx->radius[l];
+  for (int l = 0; l < L.ns; ++l) {
+    fa.R[l] = ctx->radius[l];
+    fa.x_x0[l] = ctx->x_x0[l];
+  }
+  fa.mass = ctx->mass;
   e = launch_fit_fused(fa, s);
   if (e != cudaSuccess) return e;
   // hits into eta x phi bins, one segment per build layer
@@ -311,6 +315,7 @@ static BuildSlot slot_of(Serve* sv, Request* r) {
   b.layer = r->layer;
   b.n_layers = L.Lb;
   b.R = sv->ctx->radius[sv->cfg.n_seed_layers + r->layer];
+  b.x_x0 = sv->ctx->x_x0[sv->cfg.n_seed_layers + r->layer];
   b.block_begin = 0;
   return b;
 }
@@ -378,7 +383,11 @@ static cudaError_t finish(Serve* sv, Request* r) {
       q.a_scale = float(kCLight * double(ctx->cfg.bz_tesla));
       q.v0 = q.v1 = ctx->cfg.sigma_xy_cm * ctx->cfg.sigma_xy_cm;
       q.v2 = ctx->cfg.sigma_z_cm * ctx->cfg.sigma_z_cm;
-      for (int l = 0; l < L.ns + L.Lb; ++l) q.R[l] = ctx->radius[l];
+      for (int l = 0; l < L.ns + L.Lb; ++l) {
+        q.R[l] = ctx->radius[l];
+        q.x_x0[l] = ctx->x_x0[l];
+      }
+      q.mass = ctx->mass;
       e = launch_fit_fused(q, s);
     }
   }
@@ -491,6 +500,7 @@ static void scheduler(Serve* sv) {
       a.v0 = a.v1 = sv->ctx->cfg.sigma_xy_cm * sv->ctx->cfg.sigma_xy_cm;
       a.v2 = sv->ctx->cfg.sigma_z_cm * sv->ctx->cfg.sigma_z_cm;
       a.cut = sv->ctx->cfg.chi2_cut;
+      a.mass = sv->ctx->mass;
       if (e == cudaSuccess)
         e = launch_build_step(a, blocks, sv->stream, sv->tune.build_hit_tile, sv->tune.build_list_width);
       for (Request* r : stepping) r->layer++;

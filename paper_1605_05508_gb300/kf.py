@@ -32,7 +32,9 @@ class KfError(RuntimeError):
 class kf_config(C.Structure):
     _fields_ = [("bz_tesla", C.c_float), ("n_layers", C.c_int32), ("radius_cm", C.POINTER(C.c_float)),
                 ("sigma_xy_cm", C.c_float), ("sigma_z_cm", C.c_float), ("chi2_cut", C.c_float),
-                ("max_cands", C.c_int32)]
+                ("max_cands", C.c_int32), ("x_x0", C.POINTER(C.c_float)), ("mass_gev", C.c_float)]
+
+PION_MASS = 0.13957  # GeV: default particle hypothesis of the scattering model
 
 
 class kf_tracks(C.Structure):
@@ -203,10 +205,12 @@ class Context:
     """Owns a kf_ctx; `handle` is the opaque pointer."""
 
     def __init__(self, radii, bz=3.8, sigma_xy=0.01, sigma_z=0.1, chi2_cut=30.0, max_cands=6, device=0,
-                 mem_budget_bytes=0):
+                 mem_budget_bytes=0, x_x0=None, mass=PION_MASS):
+        """x_x0: per-layer thickness in radiation lengths (None: no material)."""
         self._radii = (C.c_float * len(radii))(*[float(r) for r in radii])
+        self._x_x0 = None if x_x0 is None else (C.c_float * len(radii))(*[float(x) for x in x_x0])
         self.cfg = kf_config(float(bz), len(radii), self._radii, float(sigma_xy), float(sigma_z), float(chi2_cut),
-                             int(max_cands))
+                             int(max_cands), self._x_x0, float(mass))
         self.handle = kf_create(self.cfg, device, mem_budget_bytes)
 
     def close(self):

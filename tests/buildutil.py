@@ -4,7 +4,7 @@ near-tie classification of differing chosen hits."""
 import numpy as np
 
 import oracle as O
-from fitutil import f32, to_dev
+from fitutil import f32, material, to_dev
 
 
 def oracle_seed_fit(batch, idx=None):
@@ -16,7 +16,7 @@ def oracle_seed_fit(batch, idx=None):
         sp, sc, q, xyz, val = sp[:, idx], sc[:, idx], q[idx], xyz[:, :, idx], val[:, idx]
     L = len(batch.seed_layers)
     return O.fit(sp, sc, q, xyz, val, [f32(r) for r in det.radii[:L]], f32(det.bz), f32(det.sigma_xy),
-                 f32(det.sigma_z))
+                 f32(det.sigma_z), **material(det, range(L)))
 
 
 def oracle_build(batch, max_cands, idx=None, cut=30.0):
@@ -26,7 +26,8 @@ def oracle_build(batch, max_cands, idx=None, cut=30.0):
     ev = batch.seed_event if idx is None else batch.seed_event[idx]
     radii = [f32(det.radii[l]) for l in batch.build_layers]
     b = O.build_tracks(r["par"], r["cov"], q, ev, batch.layer_xyz, batch.layer_off, radii, f32(det.bz),
-                       f32(det.sigma_xy), f32(det.sigma_z), chi2_cut=cut, max_cands=max_cands)
+                       f32(det.sigma_xy), f32(det.sigma_z), chi2_cut=cut, max_cands=max_cands,
+                       **material(det, batch.build_layers))
     b["seed_par"], b["seed_cov"] = r["par"], r["cov"]
     return b
 
@@ -93,7 +94,10 @@ def path_chi2(batch, seed_par, seed_cov, charge, event, hits_seq, cut=30.0):
         if st:
             out.append(None)
             continue
-        Cp = O.transport_cov(J, C)
+        Q = None
+        if det.has_material and det.x_x0[batch.build_layers[l]] > 0:
+            Q = O.scattering_q(xp, f32(det.x_x0[batch.build_layers[l]]), f32(det.mass))
+        Cp = O.transport_cov(J, C, Q)
         h = int(hits_seq[l])
         if h < 0:
             x, C = xp, Cp

@@ -76,7 +76,15 @@ def oracle_fit(seeds, hits_xyz, hits_valid, det, n_threads=0):
     and the float32-rounded field, smears and radii of kf_config."""
     L = hits_xyz.shape[0]
     return O.fit(seeds.par, seeds.cov, seeds.charge, hits_xyz, hits_valid, [f32(r) for r in det.radii[:L]],
-                 f32(det.bz), f32(det.sigma_xy), f32(det.sigma_z), n_threads=n_threads)
+                 f32(det.bz), f32(det.sigma_xy), f32(det.sigma_z), n_threads=n_threads, **material(det, range(L)))
+
+
+def material(det, layers):
+    """The oracle's material arguments for the given configuration layers
+    (float32-rounded, as the library receives them)."""
+    if not det.has_material:
+        return {}
+    return dict(x_x0=[f32(det.x_x0[l]) for l in layers], mass=f32(det.mass))
 
 
 def local_frame(par):

@@ -50,11 +50,15 @@ def test_strerror_and_argument_checks_need_no_gpu(libpath):
     # rejected before any CUDA call
     assert lib.kf_create(None, None, 0, 0) == kf.KF_EINVAL
     radii = (ctypes.c_float * 3)(4.0, 3.0, 8.0)  # not increasing
-    cfg = kf.kf_config(3.8, 3, radii, 0.01, 0.1, 30.0, 6)
+    cfg = kf.kf_config(3.8, 3, radii, 0.01, 0.1, 30.0, 6, None, 0.13957)
     h = ctypes.c_void_p()
     assert lib.kf_create(ctypes.byref(h), ctypes.byref(cfg), 0, 0) == kf.KF_EINVAL
-    cfg = kf.kf_config(3.8, 3, (ctypes.c_float * 3)(4.0, 8.0, 12.0), 0.01, 0.1, 30.0, 9)  # max_cands > 8
+    cfg = kf.kf_config(3.8, 3, (ctypes.c_float * 3)(4.0, 8.0, 12.0), 0.01, 0.1, 30.0, 9, None, 0.13957)  # max_cands > 8
     assert lib.kf_create(ctypes.byref(h), ctypes.byref(cfg), 0, 0) == kf.KF_EINVAL
+    good = (ctypes.c_float * 3)(4.0, 8.0, 12.0)
+    for x0, m in (((0.01, -0.1, 0.0), 0.14), ((0.01, 1.5, 0.0), 0.14), ((0.0, 0.0, 0.0), -1.0)):
+        cfg = kf.kf_config(3.8, 3, good, 0.01, 0.1, 30.0, 6, (ctypes.c_float * 3)(*x0), m)  # bad material
+        assert lib.kf_create(ctypes.byref(h), ctypes.byref(cfg), 0, 0) == kf.KF_EINVAL
     assert lib.kf_fit(None, None, None, None, None, None, None) == kf.KF_EINVAL
     # launch parameters: null context or output, and no GPU needed to reject them
     t = kf.kf_tuning(128, 0, 8)
