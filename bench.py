@@ -443,10 +443,11 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist):
         times = {}
         for tile in (0, 512):
             for lw in (8, 4):
-                if lw == 4 and N > 4:
-                    continue
-                kf.kf_set_tuning(ctx, 128, tile, lw)
-                times[f"tile{tile}_list{lw}"] = float(run(N, 5)[1][2])
+                for scan in (0, 1):
+                    if lw == 4 and N > 4:
+                        continue
+                    kf.kf_set_tuning(ctx, 128, tile, lw, scan)
+                    times[f"tile{tile}_list{lw}_{'coop' if scan else 'lane'}"] = float(run(N, 5)[1][2])
         return times, kf.kf_autotune_build(ctx, fo, seed_off, bins, N, out, stream)
 
     k = max(5, min(50, a.steps // 4))

@@ -279,6 +279,9 @@ typedef struct {
                                  0 = none, the scans read global memory (default), or 512 */
     int32_t build_list_width; /* entries of a lane's child list in the kf_build step: 4 or 8
                                  (default 8); 4 takes effect only when max_cands <= 4 */
+    int32_t build_scan;       /* chi2 scan of the kf_build step: 0 = each lane scans its own
+                                 candidate's window (default), 1 = the seed's 8 lanes scan each
+                                 parent's window together (balanced when few candidates) */
 } kf_tuning;
 
 /* Current launch parameters of the context.  Errors: KF_EINVAL (null). */
@@ -298,9 +301,9 @@ int kf_set_tuning(kf_ctx *ctx, const kf_tuning *t);
 int kf_autotune_fit(kf_ctx *ctx, const kf_tracks *seeds, const kf_track_hits *hits, kf_tracks *out,
                     float *chi2, int32_t *status, void *stream, kf_tuning *chosen);
 
-/* Autotuner of kf_build: the same over build_hit_tile x build_list_width
- * (list width 4 is tried only when max_cands <= 4).  Errors: those of
- * kf_build. */
+/* Autotuner of kf_build: the same over build_hit_tile x build_list_width x
+ * build_scan (list width 4 is tried only when max_cands <= 4).  Errors: those
+ * of kf_build. */
 int kf_autotune_build(kf_ctx *ctx, const kf_tracks *seeds, const int64_t *seed_off,
                       const kf_layer_hit_bins *bins, int32_t max_cands, kf_build_result *out, void *stream,
                       kf_tuning *chosen);

@@ -64,8 +64,9 @@ __device__ __forceinline__ void list_insert(uint64_t (&L)[LW], int (&P)[LW], uin
 // warp whose hull does not fit, or whose seeds belong to more than one event,
 // scans global memory.  Warps stage independently: no block-wide barrier.
 // TILE (hits staged per warp; 0: no staging, every scan reads the L2-resident
-// hits through L1) and LW (entries of a lane's child list, >= max_cands) are
-// launch parameters picked by the autotuner.
+// hits through L1), LW (entries of a lane's child list, >= max_cands) and
+// COOP (the seed's lanes scan each parent's window together, instead of each
+// lane its own candidate's) are launch parameters picked by the autotuner.
 constexpr int kWarps = kBuildThreads / 32;
 constexpr int kStageOffs = 384;  // bin offsets staged per warp
 constexpr int kStagePieces = 2 * KF_BIN_ETA;
@@ -75,7 +76,7 @@ __device__ __forceinline__ int wrap_phi(int d) {  // to [-KF_BIN_PHI/2, KF_BIN_P
   return ((d + KF_BIN_PHI / 2) & (KF_BIN_PHI - 1)) - KF_BIN_PHI / 2;
 }
 
-template <int TILE, int LW>
+template <int TILE, int LW, bool COOP>
 __global__ void __launch_bounds__(kBuildThreads) build_step_kernel(const BuildStepArgs Args) {
   extern __shared__ float4 s_hits_all[];
   __shared__ BuildSlot sD;
@@ -293,48 +294,125 @@ __global__ void __launch_bounds__(kBuildThreads) build_step_kernel(const BuildSt
     L[t] = kNoKey;
     P[t] = -1;
   }
-  if (active) {
-    bool any = false;
-    if (!stopped) {
-      for (int er = e0; er <= e1; ++er) {
-        for (int part = 0; part < 2; ++part) {
-          const int f0 = part == 0 ? fa0 : fb0, f1 = part == 0 ? fa1 : fb1;
-          if (f1 < f0) continue;
-          // the piece of the staged hull holding f0..f1 (always one of the
-          // two when staged; checked all the same)
-          const int pc = (f0 >= hs0a && f1 <= hs1a) ? 0 : 1;
-          const int ph0 = pc ? 0 : hs0a, ph1 = pc ? hs1b : hs1a;
-          const bool in_smem = TILE > 0 && staged && f0 >= ph0 && f1 <= ph1;
-          int u0, u1, ubias = 0;
-          const float4* hs = D.hits + h0;
-          if (in_smem) {
-            const int q = 2 * (er - emin) + pc;
-            const int32_t* off = s_off + (s_pob[q] - ph0);
-            u0 = off[f0];
-            u1 = off[f1 + 1];
-            hs = s_hits;
-            ubias = s_phb[q] - s_off[s_pob[q]];
-          } else {
-            u0 = boff[er * KF_BIN_PHI + f0];
-            u1 = boff[er * KF_BIN_PHI + f1 + 1];
-          }
-          for (int u = u0; u < u1; ++u) {
-            const float4 m = hs[u + ubias];
-            const float r0 = (m.x - p[0]) - lo[0], r1 = (m.y - p[1]) - lo[1], r2 = (m.z - p[2]) - lo[2];
-            const float c2 = kf::chi2_of(r0, r1, r2, Si);
-            if (c2 < Args.cut) {
-              const int id = __float_as_int(m.w);
-              if (id < KF_MAX_HITS_PER_SEGMENT) {
-                list_insert(L, P, make_key(nh + 1, chi2tot + c2, k, id + 1), u);
-                any = true;
+  if constexpr (!COOP) {
+    // each lane scans the window of its own candidate
+    if (active) {
+      bool any = false;
+      if (!stopped) {
+        for (int er = e0; er <= e1; ++er) {
+          for (int part = 0; part < 2; ++part) {
+            const int f0 = part == 0 ? fa0 : fb0, f1 = part == 0 ? fa1 : fb1;
+            if (f1 < f0) continue;
+            // the piece of the staged hull holding f0..f1 (always one of the
+            // two when staged; checked all the same)
+            const int pc = (f0 >= hs0a && f1 <= hs1a) ? 0 : 1;
+            const int ph0 = pc ? 0 : hs0a, ph1 = pc ? hs1b : hs1a;
+            const bool in_smem = TILE > 0 && staged && f0 >= ph0 && f1 <= ph1;
+            int u0, u1, ubias = 0;
+            const float4* hs = D.hits + h0;
+            if (in_smem) {
+              const int q = 2 * (er - emin) + pc;
+              const int32_t* off = s_off + (s_pob[q] - ph0);
+              u0 = off[f0];
+              u1 = off[f1 + 1];
+              hs = s_hits;
+              ubias = s_phb[q] - s_off[s_pob[q]];
+            } else {
+              u0 = boff[er * KF_BIN_PHI + f0];
+              u1 = boff[er * KF_BIN_PHI + f1 + 1];
+            }
+            for (int u = u0; u < u1; ++u) {
+              const float4 m = hs[u + ubias];
+              const float r0 = (m.x - p[0]) - lo[0], r1 = (m.y - p[1]) - lo[1], r2 = (m.z - p[2]) - lo[2];
+              const float c2 = kf::chi2_of(r0, r1, r2, Si);
+              if (c2 < Args.cut) {
+                const int id = __float_as_int(m.w);
+                if (id < KF_MAX_HITS_PER_SEGMENT) {
+                  list_insert(L, P, make_key(nh + 1, chi2tot + c2, k, id + 1), u);
+                  any = true;
+                }
               }
             }
           }
         }
       }
+      // no compatible hit (or a stopped candidate): one child without a hit
+      if (!any) list_insert(L, P, make_key(nh, chi2tot, k, 0), -1);
+    }
+  } else {
+    // The seed's lanes scan together: for each parent c in turn, its
+    // prediction, S^-1 and window are broadcast to the group and the 8 lanes
+    // take the window's hits with stride 8, each inserting the children it
+    // finds into its own list (the key carries the parent).  Any key of the
+    // seed's best max_cands is among the best max_cands of the lane holding it,
+    // so the merge below is unchanged; the keys are a total order, so the
+    // result does not depend on which lane scanned which hit.
+    const bool scan_me = active && !stopped;
+    if (!scan_me) {
+  #pragma unroll
+      for (int c = 0; c < 6; ++c) Si[c] = 0.f;
+    }
+    bool any_mine = false;  // a compatible hit was found for this lane's candidate
+  #pragma unroll 1
+    for (int c = 0; c < Args.max_cands; ++c) {
+      const int src = gbase + c;
+      const bool cs = __shfl_sync(kFull, int(scan_me), src) != 0;
+      const float q0 = __shfl_sync(kFull, p[0], src), q1 = __shfl_sync(kFull, p[1], src),
+                  q2 = __shfl_sync(kFull, p[2], src);
+      const float l0 = __shfl_sync(kFull, lo[0], src), l1 = __shfl_sync(kFull, lo[1], src),
+                  l2 = __shfl_sync(kFull, lo[2], src);
+      float cSi[6];
+  #pragma unroll
+      for (int t = 0; t < 6; ++t) cSi[t] = __shfl_sync(kFull, Si[t], src);
+      const int ce0 = __shfl_sync(kFull, e0, src), ce1 = __shfl_sync(kFull, e1, src);
+      const int cfa0 = __shfl_sync(kFull, fa0, src), cfa1 = __shfl_sync(kFull, fa1, src);
+      const int cfb0 = __shfl_sync(kFull, fb0, src), cfb1 = __shfl_sync(kFull, fb1, src);
+      const int cnh = __shfl_sync(kFull, nh, src);
+      const float cchi = __shfl_sync(kFull, chi2tot, src);
+      bool found = false;
+      if (cs) {
+        for (int er = ce0; er <= ce1; ++er) {
+          for (int part = 0; part < 2; ++part) {
+            const int f0 = part == 0 ? cfa0 : cfb0, f1 = part == 0 ? cfa1 : cfb1;
+            if (f1 < f0) continue;
+            // the piece of the staged hull holding f0..f1 (always one of the
+            // two when staged; checked all the same)
+            const int pc = (f0 >= hs0a && f1 <= hs1a) ? 0 : 1;
+            const int ph0 = pc ? 0 : hs0a, ph1 = pc ? hs1b : hs1a;
+            const bool in_smem = TILE > 0 && staged && f0 >= ph0 && f1 <= ph1;
+            int u0, u1, ubias = 0;
+            const float4* hs = D.hits + h0;
+            if (in_smem) {
+              const int q = 2 * (er - emin) + pc;
+              const int32_t* off = s_off + (s_pob[q] - ph0);
+              u0 = off[f0];
+              u1 = off[f1 + 1];
+              hs = s_hits;
+              ubias = s_phb[q] - s_off[s_pob[q]];
+            } else {
+              u0 = boff[er * KF_BIN_PHI + f0];
+              u1 = boff[er * KF_BIN_PHI + f1 + 1];
+            }
+            for (int u = u0 + k; u < u1; u += kGroup) {
+              const float4 m = hs[u + ubias];
+              const float r0 = (m.x - q0) - l0, r1 = (m.y - q1) - l1, r2 = (m.z - q2) - l2;
+              const float c2 = kf::chi2_of(r0, r1, r2, cSi);
+              if (c2 < Args.cut) {
+                const int id = __float_as_int(m.w);
+                if (id < KF_MAX_HITS_PER_SEGMENT) {
+                  list_insert(L, P, make_key(cnh + 1, cchi + c2, c, id + 1), u);
+                  found = true;
+                }
+              }
+            }
+          }
+        }
+      }
+      const unsigned fb = (__ballot_sync(kFull, found) >> gbase) & 0xffu;
+      if (k == c) any_mine = fb != 0;
     }
     // no compatible hit (or a stopped candidate): one child without a hit
-    if (!any) list_insert(L, P, make_key(nh, chi2tot, k, 0), -1);
+    if (active && !any_mine) list_insert(L, P, make_key(nh, chi2tot, k, 0), -1);
   }
   if (TILE > 0 && timed_out && lane == 0) mbar_wait_bounded(s_bar, 0, kBuildWaitLimit);  // nothing in flight at exit
 
@@ -366,7 +444,7 @@ __global__ void __launch_bounds__(kBuildThreads) build_step_kernel(const BuildSt
       if (m != kNoKey) {
         if (k == r) {
           my_key = m;
-          my_parent = wl;
+          my_parent = int((m >> 21) & 7u);
           my_pos = wpos;
         }
         ++n_win;
@@ -509,20 +587,28 @@ __global__ void build_final_kernel(const BuildFinalArgs A) {
   }
 }
 
-cudaError_t launch_build_step(const BuildStepArgs& a, int grid, cudaStream_t st, int tile, int list) {
+template <int TILE, int LW>
+static void launch_step_scan(const BuildStepArgs& a, int grid, cudaStream_t st, bool coop) {
+  const size_t smem = size_t(kWarps) * TILE * sizeof(float4);
+  if (coop)
+    build_step_kernel<TILE, LW, true><<<grid, kBuildThreads, smem, st>>>(a);
+  else
+    build_step_kernel<TILE, LW, false><<<grid, kBuildThreads, smem, st>>>(a);
+}
+
+cudaError_t launch_build_step(const BuildStepArgs& a, int grid, cudaStream_t st, int tile, int list, int scan) {
   if (grid <= 0) return cudaSuccess;
-  const bool narrow = list == 4 && a.max_cands <= 4;
-  const size_t smem = size_t(kWarps) * kBuildTile * sizeof(float4);
+  const bool narrow = list == 4 && a.max_cands <= 4, coop = scan != 0;
   if (tile > 0) {
     if (narrow)
-      build_step_kernel<kBuildTile, 4><<<grid, kBuildThreads, smem, st>>>(a);
+      launch_step_scan<kBuildTile, 4>(a, grid, st, coop);
     else
-      build_step_kernel<kBuildTile, kGroup><<<grid, kBuildThreads, smem, st>>>(a);
+      launch_step_scan<kBuildTile, kGroup>(a, grid, st, coop);
   } else {
     if (narrow)
-      build_step_kernel<0, 4><<<grid, kBuildThreads, 0, st>>>(a);
+      launch_step_scan<0, 4>(a, grid, st, coop);
     else
-      build_step_kernel<0, kGroup><<<grid, kBuildThreads, 0, st>>>(a);
+      launch_step_scan<0, kGroup>(a, grid, st, coop);
   }
   return cudaGetLastError();
 }
@@ -649,7 +735,8 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
     a.v2 = v2;
     a.cut = ctx->cfg.chi2_cut;
     a.mass = ctx->mass;
-    KF_CUDA_TRY(ctx, launch_build_step(a, grid, s, ctx->tune.build_hit_tile, ctx->tune.build_list_width));
+    KF_CUDA_TRY(ctx, launch_build_step(a, grid, s, ctx->tune.build_hit_tile, ctx->tune.build_list_width,
+                                       ctx->tune.build_scan));
   }
   BuildFinalArgs fa;
   fa.cand = (L % 2 == 0) ? bufA : bufB;

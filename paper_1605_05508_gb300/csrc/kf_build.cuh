@@ -88,8 +88,10 @@ inline CandBuf cand_at(char* q, int64_t S) {
 }
 
 // tile: 0 (scan global memory) or kBuildTile (stage the window hits per
-// warp); list: 4 (lane lists of 4 children, when max_cands <= 4) or 8
-cudaError_t launch_build_step(const BuildStepArgs& a, int grid, cudaStream_t st, int tile, int list);
+// warp); list: 4 (lane lists of 4 children, when max_cands <= 4) or 8;
+// scan: 0 (each lane scans its own candidate's window) or 1 (the seed's
+// lanes scan each parent's window together)
+cudaError_t launch_build_step(const BuildStepArgs& a, int grid, cudaStream_t st, int tile, int list, int scan);
 cudaError_t launch_build_init(const BuildInitArgs& a, cudaStream_t st);
 cudaError_t launch_build_final(const BuildFinalArgs& a, cudaStream_t st);
 

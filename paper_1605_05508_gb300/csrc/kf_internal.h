@@ -52,7 +52,7 @@ struct kf_ctx {
   std::vector<kfi::GraphEntry> graphs;
   uint64_t use_clock = 0;
   kfi::Serve* serve = nullptr;
-  kf_tuning tune = {128, 0, 8};  // launch parameters (kf_set_tuning, kf_autotune_*)
+  kf_tuning tune = {128, 0, 8, 0};  // launch parameters (kf_set_tuning, kf_autotune_*)
 };
 
 namespace kfi {

@@ -502,7 +502,8 @@ static void scheduler(Serve* sv) {
       a.cut = sv->ctx->cfg.chi2_cut;
       a.mass = sv->ctx->mass;
       if (e == cudaSuccess)
-        e = launch_build_step(a, blocks, sv->stream, sv->tune.build_hit_tile, sv->tune.build_list_width);
+        e = launch_build_step(a, blocks, sv->stream, sv->tune.build_hit_tile, sv->tune.build_list_width,
+                              sv->tune.build_scan);
       for (Request* r : stepping) r->layer++;
       std::lock_guard<std::mutex> lk(sv->mu);
       sv->stats.step_launches++;

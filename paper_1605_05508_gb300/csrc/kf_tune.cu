@@ -3,9 +3,10 @@
 // Each tunable changes how the work is laid out on the GPU, never the
 // arithmetic of a track: the fit kernel's block size (64 or 128 threads, 20
 // resident warps per SM either way), the build step's hit staging (window
-// hits copied per warp into shared memory, or read through L1) and the
-// length of a lane's child list (4 suffices when at most 4 candidates are
-// kept).  The autotuner runs the caller's own batch once per setting and keeps
+// hits copied per warp into shared memory, or read through L1), the length
+// of a lane's child list (4 suffices when at most 4 candidates are kept) and
+// the chi2 scan scheme (each lane its own candidate's window, or the seed's
+// lanes over each parent's window in turn).  The autotuner runs the caller's own batch once per setting and keeps
 // the fastest, so the choice follows the workload (batch size, hit density,
 // max_cands) rather than a fixed table.
 #include "kf_internal.h"
@@ -16,7 +17,7 @@ namespace {
 
 bool valid_tuning(const kf_tuning& t) {
   return (t.fit_block == 64 || t.fit_block == 128) && (t.build_hit_tile == 0 || t.build_hit_tile == 512) &&
-         (t.build_list_width == 4 || t.build_list_width == 8);
+         (t.build_list_width == 4 || t.build_list_width == 8) && (t.build_scan == 0 || t.build_scan == 1);
 }
 
 // Mean time of `reps` calls of fn after one untimed call; < 0 on failure
@@ -102,13 +103,15 @@ int kf_autotune_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed_o
   if (!ctx) return KF_EINVAL;
   std::vector<kf_tuning> cands;
   for (int tile : {0, 512})
-    for (int list : {8, 4}) {
-      if (list == 4 && max_cands > 4) continue;
-      kf_tuning t = ctx->tune;
-      t.build_hit_tile = tile;
-      t.build_list_width = list;
-      cands.push_back(t);
-    }
+    for (int list : {8, 4})
+      for (int scan : {0, 1}) {
+        if (list == 4 && max_cands > 4) continue;
+        kf_tuning t = ctx->tune;
+        t.build_hit_tile = tile;
+        t.build_list_width = list;
+        t.build_scan = scan;
+        cands.push_back(t);
+      }
   return autotune(ctx, stream, cands,
                   [&] { return kf_build(ctx, seeds, seed_off, bins, max_cands, out, stream); }, chosen);
 }

@@ -93,7 +93,8 @@ class kf_serve_stats(C.Structure):
 
 
 class kf_tuning(C.Structure):
-    _fields_ = [("fit_block", C.c_int32), ("build_hit_tile", C.c_int32), ("build_list_width", C.c_int32)]
+    _fields_ = [("fit_block", C.c_int32), ("build_hit_tile", C.c_int32), ("build_list_width", C.c_int32),
+                ("build_scan", C.c_int32)]
 
 
 MAX_SLOTS = 32  # KF_MAX_SLOTS
@@ -368,8 +369,8 @@ def kf_get_tuning(ctx) -> dict:
     return _tuning_dict(t)
 
 
-def kf_set_tuning(ctx, fit_block: int, build_hit_tile: int, build_list_width: int):
-    t = kf_tuning(int(fit_block), int(build_hit_tile), int(build_list_width))
+def kf_set_tuning(ctx, fit_block: int, build_hit_tile: int, build_list_width: int, build_scan: int = 0):
+    t = kf_tuning(int(fit_block), int(build_hit_tile), int(build_list_width), int(build_scan))
     _check(lib().kf_set_tuning(_h(ctx), C.byref(t)), "kf_set_tuning", _h(ctx))
 
 

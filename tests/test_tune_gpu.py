@@ -11,7 +11,7 @@ from fitutil import gpu_fit
 
 pytestmark = pytest.mark.gpu
 
-DEFAULT = {"fit_block": 128, "build_hit_tile": 0, "build_list_width": 8}
+DEFAULT = {"fit_block": 128, "build_hit_tile": 0, "build_list_width": 8, "build_scan": 0}
 BUILD_KEYS = ("par", "cov", "chi2", "nhits", "status", "hits", "n_cands", "cand_hits", "cand_chi2", "cand_nhits")
 
 
@@ -24,12 +24,12 @@ def test_tuning_defaults_and_validation(cuda_ctx_factory):
     from paper_1605_05508_gb300 import kf
     ctx = cuda_ctx_factory(S.barrel().radii)
     assert kf.kf_get_tuning(ctx) == DEFAULT
-    for bad in [(96, 0, 8), (128, 256, 8), (128, 0, 6), (0, 0, 0)]:
+    for bad in [(96, 0, 8, 0), (128, 256, 8, 0), (128, 0, 6, 0), (0, 0, 0, 0), (128, 0, 8, 2)]:
         with pytest.raises(kf.KfError):
             kf.kf_set_tuning(ctx, *bad)
     assert kf.kf_get_tuning(ctx) == DEFAULT
-    kf.kf_set_tuning(ctx, 64, 512, 4)
-    assert kf.kf_get_tuning(ctx) == {"fit_block": 64, "build_hit_tile": 512, "build_list_width": 4}
+    kf.kf_set_tuning(ctx, 64, 512, 4, 1)
+    assert kf.kf_get_tuning(ctx) == {"fit_block": 64, "build_hit_tile": 512, "build_list_width": 4, "build_scan": 1}
 
 
 @pytest.mark.parametrize("n", [7001, 64])
@@ -67,13 +67,15 @@ def test_build_settings_bitwise(cuda_ctx_factory, max_cands):
         ref = None
         for tile in (0, 512):
             for lw in (8, 4):
-                kf.kf_set_tuning(ctx, 128, tile, lw)
-                g = gpu_build(ctx, batch, max_cands)
-                if ref is None:
-                    ref = g
-                else:
-                    for k in BUILD_KEYS:
-                        np.testing.assert_array_equal(ref[k], g[k], err_msg=f"{name} tile={tile} list={lw} {k}")
+                for scan in (0, 1):
+                    kf.kf_set_tuning(ctx, 128, tile, lw, scan)
+                    g = gpu_build(ctx, batch, max_cands)
+                    if ref is None:
+                        ref = g
+                    else:
+                        for k in BUILD_KEYS:
+                            np.testing.assert_array_equal(ref[k], g[k],
+                                                          err_msg=f"{name} tile={tile} list={lw} scan={scan} {k}")
         assert np.mean(ref["nhits"]) > 5.0, name
 
 
@@ -90,4 +92,5 @@ def test_build_autotune(cuda_ctx_factory):
     g = gpu_build(ctx, batch, 4, build_fn=tune)
     _same(ref, g, BUILD_KEYS)
     assert chosen["build_hit_tile"] in (0, 512) and chosen["build_list_width"] in (4, 8)
+    assert chosen["build_scan"] in (0, 1)
     assert kf.kf_get_tuning(ctx) == chosen
