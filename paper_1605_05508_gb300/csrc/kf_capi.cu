@@ -138,6 +138,12 @@ void kf_destroy(kf_ctx* ctx) {
   scratch_free(ctx, ctx->s_host_out);
   scratch_free(ctx, ctx->s_bin_id);
   scratch_free(ctx, ctx->s_build);
+  scratch_free(ctx, ctx->s_refit);
+  for (int k = 0; k < kHostStreams; ++k) {
+    if (ctx->host_streams[k]) cudaStreamDestroy(ctx->host_streams[k]);
+    if (ctx->host_done[k]) cudaEventDestroy(ctx->host_done[k]);
+  }
+  if (ctx->host_start) cudaEventDestroy(ctx->host_start);
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   delete ctx;
 }
@@ -344,45 +350,75 @@ int kf_fit_host(kf_ctx* ctx, const kf_tracks* seeds, const kf_track_hits* hits, 
   if (n == 0) return KF_OK;
   KF_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   const int L = hits->n_layers;
-  // device staging: inputs [par 6n, lo 3n, cov 21n, hits 3Ln] floats + charge n + valid Ln bytes;
-  // outputs [par 6n, lo 3n, cov 21n, chi2 Ln] floats + status n int32
+  // The batch is cut into chunks of C tracks; chunk j runs on internal stream
+  // j % S with its own device staging slot: strided 2-D copies of its columns
+  // in, its kf_fit, 2-D copies out.  Copies in, copies out and the fit of
+  // different chunks overlap; a track's result does not depend on its batch.
+  const int64_t C = std::max<int64_t>(kHostChunkMin, ((n + kHostChunks - 1) / kHostChunks + 255) / 256 * 256);
+  const int64_t n_chunks = (n + C - 1) / C;
+  const int S = int(std::min<int64_t>(kHostStreams, n_chunks));
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
-  const size_t b_par = al(6 * n * 4), b_lo = al(3 * n * 4), b_cov = al(21 * n * 4), b_hit = al(size_t(3) * L * n * 4),
-               b_q = al(n), b_val = al(size_t(L) * n), b_chi = al(size_t(L) * n * 4), b_st = al(n * 4);
+  const size_t b_par = al(6 * C * 4), b_lo = al(3 * C * 4), b_cov = al(21 * C * 4), b_hit = al(size_t(3) * L * C * 4),
+               b_q = al(C), b_val = al(size_t(L) * C), b_chi = al(size_t(L) * C * 4), b_st = al(C * 4);
   const size_t in_bytes = b_par + b_lo + b_cov + b_hit + b_q + b_val;
   const size_t out_bytes = b_par + b_lo + b_cov + b_chi + b_st;
-  rc = scratch_reserve(ctx, ctx->s_host_in, in_bytes);
+  rc = scratch_reserve(ctx, ctx->s_host_in, in_bytes * S);
   if (rc) return rc;
-  rc = scratch_reserve(ctx, ctx->s_host_out, out_bytes);
+  rc = scratch_reserve(ctx, ctx->s_host_out, out_bytes * S);
   if (rc) return rc;
-  char* di = static_cast<char*>(ctx->s_host_in.ptr);
-  char* dout = static_cast<char*>(ctx->s_host_out.ptr);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  kf_tracks ds{n, reinterpret_cast<float*>(di), seeds->par_lo ? reinterpret_cast<float*>(di + b_par) : nullptr,
-               reinterpret_cast<float*>(di + b_par + b_lo), reinterpret_cast<int8_t*>(di + b_par + b_lo + b_cov + b_hit)};
-  float* dhit = reinterpret_cast<float*>(di + b_par + b_lo + b_cov);
-  uint8_t* dval = hits->valid ? reinterpret_cast<uint8_t*>(di + b_par + b_lo + b_cov + b_hit + b_q) : nullptr;
-  kf_tracks dout_t{n, reinterpret_cast<float*>(dout), reinterpret_cast<float*>(dout + b_par),
-                   reinterpret_cast<float*>(dout + b_par + b_lo), ds.charge};
-  float* dchi = reinterpret_cast<float*>(dout + b_par + b_lo + b_cov);
-  int32_t* dst = reinterpret_cast<int32_t*>(dout + b_par + b_lo + b_cov + b_chi);
-  KF_CUDA_TRY(ctx, cudaMemcpyAsync(ds.par, seeds->par, 6 * n * 4, cudaMemcpyHostToDevice, s));
-  if (seeds->par_lo) KF_CUDA_TRY(ctx, cudaMemcpyAsync(ds.par_lo, seeds->par_lo, 3 * n * 4, cudaMemcpyHostToDevice, s));
-  KF_CUDA_TRY(ctx, cudaMemcpyAsync(ds.cov, seeds->cov, 21 * n * 4, cudaMemcpyHostToDevice, s));
-  KF_CUDA_TRY(ctx, cudaMemcpyAsync(ds.charge, seeds->charge, n, cudaMemcpyHostToDevice, s));
-  KF_CUDA_TRY(ctx, cudaMemcpyAsync(dhit, hits->xyz, size_t(3) * L * n * 4, cudaMemcpyHostToDevice, s));
-  if (dval) KF_CUDA_TRY(ctx, cudaMemcpyAsync(dval, hits->valid, size_t(L) * n, cudaMemcpyHostToDevice, s));
-  kf_track_hits dh{n, L, dhit, dval};
-  rc = kf_fit(ctx, &ds, &dh, &dout_t, dchi, dst, stream);
-  if (rc) return rc;
-  KF_CUDA_TRY(ctx, cudaMemcpyAsync(out->par, dout_t.par, 6 * n * 4, cudaMemcpyDeviceToHost, s));
-  if (out->par_lo) KF_CUDA_TRY(ctx, cudaMemcpyAsync(out->par_lo, dout_t.par_lo, 3 * n * 4, cudaMemcpyDeviceToHost, s));
-  KF_CUDA_TRY(ctx, cudaMemcpyAsync(out->cov, dout_t.cov, 21 * n * 4, cudaMemcpyDeviceToHost, s));
-  if (out->charge && out->charge != seeds->charge)
-    KF_CUDA_TRY(ctx, cudaMemcpyAsync(out->charge, ds.charge, n, cudaMemcpyDeviceToHost, s));
-  if (chi2) KF_CUDA_TRY(ctx, cudaMemcpyAsync(chi2, dchi, size_t(L) * n * 4, cudaMemcpyDeviceToHost, s));
-  if (status) KF_CUDA_TRY(ctx, cudaMemcpyAsync(status, dst, n * 4, cudaMemcpyDeviceToHost, s));
-  KF_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  for (int k = 0; k < kHostStreams; ++k) {
+    if (!ctx->host_streams[k]) KF_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->host_streams[k], cudaStreamNonBlocking));
+    if (!ctx->host_done[k]) KF_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->host_done[k], cudaEventDisableTiming));
+  }
+  if (!ctx->host_start) KF_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->host_start, cudaEventDisableTiming));
+  cudaStream_t user = static_cast<cudaStream_t>(stream);
+  KF_CUDA_TRY(ctx, cudaEventRecord(ctx->host_start, user));
+  for (int k = 0; k < S; ++k) KF_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->host_streams[k], ctx->host_start, 0));
+  const size_t hp = size_t(n) * 4;  // host row pitch of a float component
+  for (int64_t j = 0; j < n_chunks; ++j) {
+    const int k = int(j % S);
+    cudaStream_t s = ctx->host_streams[k];
+    const int64_t j0 = j * C, c = std::min(C, n - j0);
+    const size_t w = size_t(c) * 4;  // device row pitch of this chunk
+    char* di = static_cast<char*>(ctx->s_host_in.ptr) + in_bytes * k;
+    char* dout = static_cast<char*>(ctx->s_host_out.ptr) + out_bytes * k;
+    kf_tracks ds{c, reinterpret_cast<float*>(di), seeds->par_lo ? reinterpret_cast<float*>(di + b_par) : nullptr,
+                 reinterpret_cast<float*>(di + b_par + b_lo),
+                 reinterpret_cast<int8_t*>(di + b_par + b_lo + b_cov + b_hit)};
+    float* dhit = reinterpret_cast<float*>(di + b_par + b_lo + b_cov);
+    uint8_t* dval = hits->valid ? reinterpret_cast<uint8_t*>(di + b_par + b_lo + b_cov + b_hit + b_q) : nullptr;
+    kf_tracks dt{c, reinterpret_cast<float*>(dout), reinterpret_cast<float*>(dout + b_par),
+                 reinterpret_cast<float*>(dout + b_par + b_lo), ds.charge};
+    float* dchi = reinterpret_cast<float*>(dout + b_par + b_lo + b_cov);
+    int32_t* dst = reinterpret_cast<int32_t*>(dout + b_par + b_lo + b_cov + b_chi);
+    auto h2d = [&](void* d, const void* h, size_t width, size_t rows, size_t hpitch) {
+      return cudaMemcpy2DAsync(d, width, h, hpitch, width, rows, cudaMemcpyHostToDevice, s);
+    };
+    auto d2h = [&](void* h, const void* d, size_t width, size_t rows, size_t hpitch) {
+      return cudaMemcpy2DAsync(h, hpitch, d, width, width, rows, cudaMemcpyDeviceToHost, s);
+    };
+    KF_CUDA_TRY(ctx, h2d(ds.par, seeds->par + j0, w, 6, hp));
+    if (seeds->par_lo) KF_CUDA_TRY(ctx, h2d(ds.par_lo, seeds->par_lo + j0, w, 3, hp));
+    KF_CUDA_TRY(ctx, h2d(ds.cov, seeds->cov + j0, w, 21, hp));
+    KF_CUDA_TRY(ctx, cudaMemcpyAsync(ds.charge, seeds->charge + j0, size_t(c), cudaMemcpyHostToDevice, s));
+    KF_CUDA_TRY(ctx, h2d(dhit, hits->xyz + j0, w, size_t(3) * L, hp));
+    if (dval) KF_CUDA_TRY(ctx, h2d(dval, hits->valid + j0, size_t(c), size_t(L), size_t(n)));
+    kf_track_hits dh{c, L, dhit, dval};
+    rc = kf_fit(ctx, &ds, &dh, &dt, dchi, dst, s);
+    if (rc) return rc;
+    KF_CUDA_TRY(ctx, d2h(out->par + j0, dt.par, w, 6, hp));
+    if (out->par_lo) KF_CUDA_TRY(ctx, d2h(out->par_lo + j0, dt.par_lo, w, 3, hp));
+    KF_CUDA_TRY(ctx, d2h(out->cov + j0, dt.cov, w, 21, hp));
+    if (out->charge && out->charge != seeds->charge)
+      KF_CUDA_TRY(ctx, cudaMemcpyAsync(out->charge + j0, ds.charge, size_t(c), cudaMemcpyDeviceToHost, s));
+    if (chi2) KF_CUDA_TRY(ctx, d2h(chi2 + j0, dchi, w, size_t(L), hp));
+    if (status) KF_CUDA_TRY(ctx, cudaMemcpyAsync(status + j0, dst, w, cudaMemcpyDeviceToHost, s));
+  }
+  for (int k = 0; k < S; ++k) {
+    KF_CUDA_TRY(ctx, cudaEventRecord(ctx->host_done[k], ctx->host_streams[k]));
+    KF_CUDA_TRY(ctx, cudaStreamWaitEvent(user, ctx->host_done[k], 0));
+  }
+  KF_CUDA_TRY(ctx, cudaStreamSynchronize(user));
   return KF_OK;
 }
 

@@ -15,6 +15,11 @@
 namespace kfi {
 
 constexpr int kMaxLayers = 64;
+// kf_fit_host pipeline: chunks (at most kHostChunks, at least kHostChunkMin
+// tracks each) over kHostStreams internal streams
+constexpr int kHostStreams = 3;
+constexpr int kHostChunks = 16;
+constexpr int64_t kHostChunkMin = 65536;
 constexpr double kCLight = 0.00299792458;  // GeV / (T cm)
 
 // A device allocation owned by the context, grown on demand.
@@ -52,6 +57,9 @@ struct kf_ctx {
   std::vector<kfi::GraphEntry> graphs;
   uint64_t use_clock = 0;
   kfi::Serve* serve = nullptr;
+  cudaStream_t host_streams[kfi::kHostStreams] = {};  // kf_fit_host pipeline
+  cudaEvent_t host_done[kfi::kHostStreams] = {};
+  cudaEvent_t host_start = nullptr;
   kf_tuning tune = {128, 0, 8, 0};  // launch parameters (kf_set_tuning, kf_autotune_*)
 };
 
