@@ -273,7 +273,7 @@ int kf_refit(kf_ctx *ctx, const kf_tracks *seeds, const kf_track_hits *seed_hits
  */
 typedef struct {
     int32_t fit_block;        /* threads per block of the kf_fit / kf_fit_noalloc layer
-                                 kernel: 64 or 128 (default 128); 20 warps per SM either way */
+                                 kernel: 64 or 128 (default 128); 24 warps per SM either way */
     int32_t build_hit_tile;   /* hits staged in shared memory per warp by the kf_build step
                                  (bulk asynchronous copies of the window's bin rows):
                                  0 = none, the scans read global memory (default), or 512 */

@@ -10,7 +10,7 @@
 //   fit_fused_kernel  all layers in one launch, the track held in registers
 //                     (also the mixed-precision form);
 //   fit_f64_kernel    the plain FP64 form, launched per event and per layer.
-// One track per thread, 20 resident warps per SM, plain coalesced row reads.
+// One track per thread, 24 resident warps per SM, plain coalesced row reads.
 // Staging the rows in shared memory (bulk copies per block or per warp, or
 // per-thread cp.async double buffering) measured no faster.
 #include "kf_internal.h"
@@ -19,8 +19,13 @@
 namespace kfi {
 
 constexpr int kFitThreads = 128;
-constexpr int kFitMinBlocks = 5;  // 20 resident warps per SM: caps a thread at 96 registers
-constexpr int kFitWarpsPerSM = kFitThreads / 32 * kFitMinBlocks;
+constexpr int kFitMinBlocks = 5;  // fused fit: 20 resident warps per SM (96 registers)
+// The layer kernel moves 261 B per track: at 20 resident warps per SM the
+// loads a warp issues at the start of its tracks do not keep enough bytes in
+// flight to reach the HBM rate (a pure copy with this access pattern takes
+// 181 us per 4M tracks at 20 warps, 150 us at full occupancy).  24 warps
+// (80 registers, no spills) measured best; 32 warps spill.
+constexpr int kFitWarpsPerSM = 24;
 constexpr int kNewtonF32 = 12;  // iteration cap of the safeguarded Newton solve
 constexpr int kNewtonF64 = 16;
 
@@ -117,7 +122,7 @@ __device__ __forceinline__ void fit_layer_track(const FitLayerArgs& A, int64_t i
 // One track per thread over a grid that covers the batch: blocks start as
 // others finish, so the warps of an SM drift out of phase and their load
 // bursts overlap other warps' arithmetic.  THREADS (64 or 128, picked by the
-// autotuner) keeps 20 warps per SM resident either way.
+// autotuner) keeps kFitWarpsPerSM warps per SM resident either way.
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS, kFitWarpsPerSM * 32 / THREADS) fit_layer_kernel(const FitLayerArgs A) {
   const int64_t n = A.n;

@@ -1,7 +1,7 @@
 // kf_tune.cu -- launch parameters of the context and their autotuner.
 //
 // Each tunable changes how the work is laid out on the GPU, never the
-// arithmetic of a track: the fit kernel's block size (64 or 128 threads, 20
+// arithmetic of a track: the fit kernel's block size (64 or 128 threads, 24
 // resident warps per SM either way), the build step's hit staging (window
 // hits copied per warp into shared memory, or read through L1), the length
 // of a lane's child list (4 suffices when at most 4 candidates are kept) and
