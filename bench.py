@@ -178,6 +178,16 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def line_clock_mhz(dev):
+    """Maximum SM clock (MHz) as nvidia-smi reports it; 2070 if unavailable."""
+    try:
+        out = subprocess.run(["nvidia-smi", f"--id={dev.index}", "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=20).stdout
+        return float(out.strip().splitlines()[0])
+    except Exception:
+        return 2070.0
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -193,11 +203,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(n_tracks):
-    """DRAM bytes per fit-layer launch from the committed ncu summary, scaled to
-    n_tracks (traffic grows in proportion to the tracks of a launch); None if
+def profile_value(name, key):
+    """A figure from a committed ncu summary (profiles/<name>), or None when
     absent or taken on a different kernel source."""
-    p = os.path.join(ROOT, "profiles", "fit_layer_kernel.traffic.txt")
+    p = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(p):
         return None
     kv = {}
@@ -207,7 +216,15 @@ def ncu_traffic(n_tracks):
             kv[k.strip()] = v.strip()
     if kv.get("source_hash") != kernel_source_hash():
         return None
-    return float(kv["dram_bytes_per_track"]) * n_tracks
+    return float(kv[key])
+
+
+def ncu_traffic(n_tracks):
+    """DRAM bytes per fit-layer launch from the committed ncu summary, scaled to
+    n_tracks (traffic grows in proportion to the tracks of a launch); None if
+    absent or taken on a different kernel source."""
+    b = profile_value("fit_layer_kernel.traffic.txt", "dram_bytes_per_track")
+    return None if b is None else b * n_tracks
 
 
 def fit_bytes_per_track_layer(L, seeds_have_lo, have_valid, have_chi2):
@@ -336,6 +353,18 @@ def extras(a, ctx, kf, torch, dev, det, ev, seeds, hits, out, chi2, status, stre
     ms_f = timed(lambda: kf.kf_fit_fused(ctx, seeds, hits, out, chi2, status, stream), max(3, a.steps // 4))
     res["fused"] = {"value": n * L / (ms_f / 1e3), "unit": UNIT, "ms_per_step": ms_f,
                     "note": "one launch, track kept in registers across layers"}
+    # issue roofline of the fused form: warp instructions per track-layer from
+    # the committed ncu summary, against 4 issues per SM per cycle
+    ipt = profile_value("fit_fused_kernel.instructions.txt", "warp_instructions_per_track_layer")
+    if ipt:
+        props = torch.cuda.get_device_properties(dev)
+        clk = float(line_clock_mhz(dev)) * 1e6
+        peak = 4.0 * props.multi_processor_count * clk
+        ach = ipt * n * L / (ms_f / 1e3)
+        res["fused"]["roofline"] = {"kernel": "fit_fused_kernel<0>", "bound": "alu", "achieved": ach, "peak": peak,
+                                    "unit": "warp instructions/s", "frac": ach / peak,
+                                    "warp_instructions_per_track_layer": ipt,
+                                    "peak_kind": "4 issues per SM per cycle x SMs x max SM clock"}
 
     # end to end through the public C ABI with pinned host buffers
     pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
