@@ -2,45 +2,65 @@
 // projective eta x phi bins per layer (Cerati et al., Sec. 3: hits sorted in
 // phi within eta bins, phi bins for fast look-up of compatible hits).
 //
-// A counting sort with one thread block per segment (one event on one
-// layer): a shared-memory histogram of the 64 x 256 bins, a block-wide
-// exclusive scan, a scatter through shared-memory cursors, and a final
-// insertion sort by id inside each bin so that the output is deterministic.
+// A counting sort of every segment (one event on one layer) into the 64 x 256
+// bins, with a final insertion sort by id inside each bin so that the output
+// is deterministic.
 #include "kf_bin.cuh"
 #include "kf_internal.h"
 
+#include <algorithm>
+
 namespace kfi {
 
-constexpr int kBinThreads = 1024;
-constexpr int kPerThread = KF_NBINS / kBinThreads;  // 16 consecutive bins per thread
-static_assert(KF_NBINS % kBinThreads == 0, "bins per thread");
+// A counting sort over all points of all segments at once, in four fully
+// parallel passes: (1) every point adds one to its segment's count of its
+// bin (global atomics into bin_off), (2) one block per segment turns the
+// counts into exclusive offsets (bin_off) and scatter cursors, (3) every
+// point takes the next slot of its bin, (4) one thread per (segment, bin)
+// sorts the bin's slots by id, so the output does not depend on the order
+// in which (3) took them.  A segment of any size spreads over the whole GPU.
+constexpr int kScanThreads = 1024;
+constexpr int kPerThread = KF_NBINS / kScanThreads;  // 16 consecutive bins per thread
+static_assert(KF_NBINS % kScanThreads == 0, "bins per thread");
+constexpr int kPointThreads = 256;
 
-__global__ void __launch_bounds__(kBinThreads) bin_points_kernel(const BinArgs A) {
-  extern __shared__ int smem[];
-  int* cnt = smem;               // [KF_NBINS] counts, then cursors
-  int* warp_tot = smem + KF_NBINS;  // [32]
-  const int seg = blockIdx.x;
-  // offsets are clamped to the point arrays, so malformed ones cannot index past them
-  int64_t p0 = A.seg_off[seg], p1 = A.seg_off[seg + 1];
-  p0 = p0 < 0 ? 0 : (p0 > A.stride ? A.stride : p0);
-  p1 = p1 < p0 ? p0 : (p1 > A.stride ? A.stride : p1);
-  const int n = int(p1 - p0);
-  const int tid = threadIdx.x;
-  for (int b = tid; b < KF_NBINS; b += kBinThreads) cnt[b] = 0;
-  __syncthreads();
-  for (int i = tid; i < n; i += kBinThreads) {
-    const int64_t g = p0 + i;
-    const int b = bin_of(A.xyz[g], A.xyz[A.stride + g], A.xyz[2 * A.stride + g]);
-    atomicAdd(&cnt[b], 1);
+// the segment s with seg_off[s] <= g < seg_off[s + 1], or -1
+__device__ __forceinline__ int segment_of(const int64_t* off, int nseg, int64_t g) {
+  if (g < off[0] || g >= off[nseg]) return -1;
+  int lo = 0, hi = nseg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= g)
+      lo = mid;
+    else
+      hi = mid - 1;
   }
-  __syncthreads();
+  return g < off[lo + 1] ? lo : -1;
+}
+
+__global__ void __launch_bounds__(kPointThreads) bin_count_kernel(const BinArgs A, int nseg) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < A.stride; g += stride) {
+    const int s = segment_of(A.seg_off, nseg, g);
+    if (s < 0) continue;
+    const int b = bin_of(A.xyz[g], A.xyz[A.stride + g], A.xyz[2 * A.stride + g]);
+    atomicAdd(&A.bin_off[int64_t(s) * (KF_NBINS + 1) + b], 1);
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) bin_scan_kernel(const BinArgs A) {
+  __shared__ int warp_tot[32];
+  const int seg = blockIdx.x;
+  int32_t* off = A.bin_off + int64_t(seg) * (KF_NBINS + 1);
+  int32_t* cur = A.cursor + int64_t(seg) * KF_NBINS;
+  const int tid = threadIdx.x;
   // exclusive scan: each thread owns kPerThread consecutive bins
   int local[kPerThread];
   int run = 0;
 #pragma unroll
   for (int t = 0; t < kPerThread; ++t) {
     local[t] = run;
-    run += cnt[tid * kPerThread + t];
+    run += off[tid * kPerThread + t];
   }
   const int lane = tid & 31, warp = tid >> 5;
   int incl = run;
@@ -62,55 +82,67 @@ __global__ void __launch_bounds__(kBinThreads) bin_points_kernel(const BinArgs A
   }
   __syncthreads();
   const int base = (incl - run) + (warp > 0 ? warp_tot[warp - 1] : 0);
-  int32_t* off = A.bin_off ? A.bin_off + int64_t(seg) * (KF_NBINS + 1) : nullptr;
+  __syncthreads();  // every count is read before it is overwritten
 #pragma unroll
   for (int t = 0; t < kPerThread; ++t) {
     const int b = tid * kPerThread + t;
-    cnt[b] = base + local[t];
-    if (off) off[b] = base + local[t];
+    off[b] = base + local[t];
+    cur[b] = base + local[t];
   }
-  if (off && tid == 0) off[KF_NBINS] = n;
-  __syncthreads();
-  // scatter through the cursors (order inside a bin fixed below)
-  for (int i = tid; i < n; i += kBinThreads) {
-    const int64_t g = p0 + i;
+  if (tid == kScanThreads - 1) off[KF_NBINS] = base + run;
+}
+
+__global__ void __launch_bounds__(kPointThreads) bin_scatter_kernel(const BinArgs A, int nseg) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < A.stride; g += stride) {
+    const int s = segment_of(A.seg_off, nseg, g);
+    if (s < 0) continue;
     const float x = A.xyz[g], y = A.xyz[A.stride + g], z = A.xyz[2 * A.stride + g];
     const int b = bin_of(x, y, z);
-    const int pos = atomicAdd(&cnt[b], 1);
-    A.out_id[p0 + pos] = i;
-    if (A.out_pts) A.out_pts[p0 + pos] = make_float4(x, y, z, __int_as_float(i));
-    if (A.out_seg) A.out_seg[p0 + pos] = seg;
+    const int64_t p0 = A.seg_off[s];
+    const int i = int(g - p0);
+    const int64_t q = p0 + atomicAdd(&A.cursor[int64_t(s) * KF_NBINS + b], 1);
+    if (q >= A.stride) continue;  // only for malformed offsets
+    A.out_id[q] = i;
+    if (A.out_pts) A.out_pts[q] = make_float4(x, y, z, __int_as_float(i));
+    if (A.out_seg) A.out_seg[q] = s;
   }
-  __syncthreads();
-  // deterministic order: insertion sort by id inside each bin (cnt[b] is now
-  // the end of bin b, its start is the end of bin b - 1)
-  for (int b = tid; b < KF_NBINS; b += kBinThreads) {
-    const int beg = b == 0 ? 0 : cnt[b - 1], end = cnt[b];
-    for (int u = beg + 1; u < end; ++u) {
-      const int id = A.out_id[p0 + u];
-      const float4 pt = A.out_pts ? A.out_pts[p0 + u] : make_float4(0.f, 0.f, 0.f, 0.f);
-      int v = u - 1;
-      while (v >= beg && A.out_id[p0 + v] > id) {
-        A.out_id[p0 + v + 1] = A.out_id[p0 + v];
-        if (A.out_pts) A.out_pts[p0 + v + 1] = A.out_pts[p0 + v];
-        --v;
-      }
-      A.out_id[p0 + v + 1] = id;
-      if (A.out_pts) A.out_pts[p0 + v + 1] = pt;
+}
+
+// deterministic order: insertion sort by id inside each bin
+__global__ void __launch_bounds__(kPointThreads) bin_sort_kernel(const BinArgs A, int nseg) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= int64_t(nseg) * KF_NBINS) return;
+  const int s = int(t / KF_NBINS), b = int(t % KF_NBINS);
+  const int32_t* off = A.bin_off + int64_t(s) * (KF_NBINS + 1);
+  const int64_t p0 = A.seg_off[s];
+  int64_t beg = p0 + off[b], end = p0 + off[b + 1];
+  if (end > A.stride) end = A.stride;
+  for (int64_t u = beg + 1; u < end; ++u) {
+    const int id = A.out_id[u];
+    const float4 pt = A.out_pts ? A.out_pts[u] : make_float4(0.f, 0.f, 0.f, 0.f);
+    int64_t v = u - 1;
+    while (v >= beg && A.out_id[v] > id) {
+      A.out_id[v + 1] = A.out_id[v];
+      if (A.out_pts) A.out_pts[v + 1] = A.out_pts[v];
+      --v;
     }
+    A.out_id[v + 1] = id;
+    if (A.out_pts) A.out_pts[v + 1] = pt;
   }
 }
 
 cudaError_t launch_bin_points(const BinArgs& a, int n_segments, cudaStream_t st) {
   if (n_segments <= 0) return cudaSuccess;
-  const int smem = (KF_NBINS + 32) * int(sizeof(int));
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(bin_points_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  bin_points_kernel<<<n_segments, kBinThreads, smem, st>>>(a);
+  cudaError_t e = cudaMemsetAsync(a.bin_off, 0, size_t(n_segments) * (KF_NBINS + 1) * sizeof(int32_t), st);
+  if (e != cudaSuccess) return e;
+  const int64_t pts = a.stride > 0 ? a.stride : 1;
+  const int pgrid = int(std::min<int64_t>((pts + kPointThreads - 1) / kPointThreads, int64_t(1) << 20));
+  bin_count_kernel<<<pgrid, kPointThreads, 0, st>>>(a, n_segments);
+  bin_scan_kernel<<<n_segments, kScanThreads, 0, st>>>(a);
+  bin_scatter_kernel<<<pgrid, kPointThreads, 0, st>>>(a, n_segments);
+  const int64_t bins = int64_t(n_segments) * KF_NBINS;
+  bin_sort_kernel<<<int((bins + kPointThreads - 1) / kPointThreads), kPointThreads, 0, st>>>(a, n_segments);
   return cudaGetLastError();
 }
 
@@ -132,7 +164,8 @@ extern "C" int kf_bin_hits(kf_ctx* ctx, const kf_layer_hits* in, kf_layer_hit_bi
   const int nseg = in->n_events * in->n_layers;
   if (nseg == 0) return KF_OK;
   KF_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-  int rc = scratch_reserve(ctx, ctx->s_bin_id, size_t(in->n_hits > 0 ? in->n_hits : 1) * sizeof(int32_t));
+  const size_t id_bytes = (size_t(in->n_hits > 0 ? in->n_hits : 1) * sizeof(int32_t) + 255) & ~size_t(255);
+  int rc = scratch_reserve(ctx, ctx->s_bin_id, id_bytes + size_t(nseg) * KF_NBINS * sizeof(int32_t));
   if (rc) return rc;
   BinArgs a;
   a.xyz = in->xyz;
@@ -142,6 +175,7 @@ extern "C" int kf_bin_hits(kf_ctx* ctx, const kf_layer_hits* in, kf_layer_hit_bi
   a.out_pts = reinterpret_cast<float4*>(out->hits);
   a.out_id = static_cast<int32_t*>(ctx->s_bin_id.ptr);
   a.out_seg = nullptr;
+  a.cursor = reinterpret_cast<int32_t*>(static_cast<char*>(ctx->s_bin_id.ptr) + id_bytes);
   KF_CUDA_TRY(ctx, launch_bin_points(a, nseg, static_cast<cudaStream_t>(stream)));
   return KF_OK;
 }

@@ -33,12 +33,16 @@ struct BinArgs {
   const float* xyz;        // [3][stride]
   int64_t stride;
   const int64_t* seg_off;  // [n_seg + 1]
-  int32_t* bin_off;        // [n_seg][KF_NBINS + 1] or null
+  int32_t* bin_off;        // [n_seg][KF_NBINS + 1] required: bin starts within the segment, then the count
   float4* out_pts;         // [total] or null
   int32_t* out_id;         // [total] required: id within the segment, bin order
   int32_t* out_seg;        // [total] or null
+  int32_t* cursor;         // [n_seg][KF_NBINS] scratch
 };
 
+// Sort the points of every segment into bins (several launches on `st`);
+// stride is the number of points (the segments cover [seg_off[0],
+// seg_off[n_segments])).
 cudaError_t launch_bin_points(const BinArgs& a, int n_segments, cudaStream_t st);
 
 }  // namespace kfi

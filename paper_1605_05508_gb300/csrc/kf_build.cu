@@ -659,7 +659,9 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
   const size_t b_cand = cand_bytes(S);
   const size_t b_hp = al256(size_t(L) * S8), b_hh = al256(size_t(L) * S8 * 4);
   const size_t b_tab = al256(sizeof(BuildSlot) * size_t(L));
-  const size_t total = b_perm + b_evt + 2 * b_cand + b_hp + b_hh + b_tab;
+  const int64_t E = bins->n_events;
+  const size_t b_sbin = al256(size_t(E) * (KF_NBINS + 1) * 4), b_scur = al256(size_t(E) * KF_NBINS * 4);
+  const size_t total = b_perm + b_evt + 2 * b_cand + b_hp + b_hh + b_tab + b_sbin + b_scur;
   int rc = scratch_reserve(ctx, ctx->s_build, total);
   if (rc) return rc;
   char* base = static_cast<char*>(ctx->s_build.ptr);
@@ -676,10 +678,11 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
   ba.xyz = seeds->par;
   ba.stride = S;
   ba.seg_off = seed_off;
-  ba.bin_off = nullptr;
+  ba.bin_off = reinterpret_cast<int32_t*>(base + b_perm + b_evt + 2 * b_cand + b_hp + b_hh + b_tab);
   ba.out_pts = nullptr;
   ba.out_id = perm;
   ba.out_seg = evt;
+  ba.cursor = reinterpret_cast<int32_t*>(base + b_perm + b_evt + 2 * b_cand + b_hp + b_hh + b_tab + b_sbin);
   KF_CUDA_TRY(ctx, launch_bin_points(ba, bins->n_events, s));
   // perm holds ids within each event: make them global seed indices
   // (the seeds of event e start at seed_off[e])

@@ -95,7 +95,7 @@ struct EventLayout {
   // device offsets
   size_t d_par, d_cov, d_q, d_shits, d_sval, d_fpar, d_flo, d_fcov, d_fst, d_xyz, d_segoff, d_sseg, d_bhits, d_boff,
       d_bid, d_perm, d_candA, d_candB, d_hp, d_hh, d_rpar, d_rcov, d_rchi, d_rnh, d_rst, d_rhit, d_qpar, d_qcov,
-      d_qchi, d_qst, d_gxyz, d_gval, d_total;
+      d_qchi, d_qst, d_gxyz, d_gval, d_bcur, d_sboff, d_total;
   // host input / output block offsets
   size_t h_par, h_cov, h_q, h_shits, h_sval, h_xyz, h_segoff, h_in_total;
   size_t o_par, o_cov, o_chi, o_nh, o_st, o_hit, o_qpar, o_qcov, o_qchi, o_qst, h_out_total;
@@ -146,6 +146,8 @@ struct EventLayout {
     d_qst = take(refit ? n * 4 : 0);
     d_gxyz = take(refit ? L * 3 * n * 4 : 0);
     d_gval = take(refit ? L * n : 0);
+    d_bcur = take(size_t(Lb) * KF_NBINS * 4);     // binning cursors (hits, then seeds)
+    d_sboff = take(size_t(KF_NBINS + 1) * 4);  // seed bin offsets
     d_total = o;
     o = 0;
     h_par = take(6 * n * 4);
@@ -268,6 +270,7 @@ static cudaError_t prepare(Serve* sv, Request* r) {
   hb.out_pts = reinterpret_cast<float4*>(d + L.d_bhits);
   hb.out_id = reinterpret_cast<int32_t*>(d + L.d_bid);
   hb.out_seg = nullptr;
+  hb.cursor = reinterpret_cast<int32_t*>(d + L.d_bcur);
   e = launch_bin_points(hb, L.Lb, s);
   if (e != cudaSuccess) return e;
   // seeds in (eta, phi) order: one segment [0, n)
@@ -278,10 +281,11 @@ static cudaError_t prepare(Serve* sv, Request* r) {
   sb.xyz = reinterpret_cast<const float*>(d + L.d_fpar);
   sb.stride = n;
   sb.seg_off = reinterpret_cast<const int64_t*>(d + L.d_sseg);
-  sb.bin_off = nullptr;
+  sb.bin_off = reinterpret_cast<int32_t*>(d + L.d_sboff);
   sb.out_pts = nullptr;
   sb.out_id = reinterpret_cast<int32_t*>(d + L.d_perm);
   sb.out_seg = nullptr;
+  sb.cursor = reinterpret_cast<int32_t*>(d + L.d_bcur);
   e = launch_bin_points(sb, 1, s);
   if (e != cudaSuccess) return e;
   BuildInitArgs ia;
