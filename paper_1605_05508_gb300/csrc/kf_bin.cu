@@ -48,19 +48,27 @@ __global__ void __launch_bounds__(kPointThreads) bin_count_kernel(const BinArgs 
   }
 }
 
+// padded shared-memory index of bin b: a thread's 16 consecutive bins and a
+// warp's 32 threads fall in distinct banks
+__device__ __forceinline__ int pad_idx(int b) { return b + (b >> 5); }
+constexpr int kScanSmem = (KF_NBINS + KF_NBINS / 32) * int(sizeof(int));
+
 __global__ void __launch_bounds__(kScanThreads) bin_scan_kernel(const BinArgs A) {
+  extern __shared__ int cnt[];  // counts, then offsets (padded layout)
   __shared__ int warp_tot[32];
   const int seg = blockIdx.x;
   int32_t* off = A.bin_off + int64_t(seg) * (KF_NBINS + 1);
   int32_t* cur = A.cursor + int64_t(seg) * KF_NBINS;
   const int tid = threadIdx.x;
+  for (int b = tid; b < KF_NBINS; b += kScanThreads) cnt[pad_idx(b)] = off[b];  // coalesced
+  __syncthreads();
   // exclusive scan: each thread owns kPerThread consecutive bins
   int local[kPerThread];
   int run = 0;
 #pragma unroll
   for (int t = 0; t < kPerThread; ++t) {
     local[t] = run;
-    run += off[tid * kPerThread + t];
+    run += cnt[pad_idx(tid * kPerThread + t)];
   }
   const int lane = tid & 31, warp = tid >> 5;
   int incl = run;
@@ -82,14 +90,15 @@ __global__ void __launch_bounds__(kScanThreads) bin_scan_kernel(const BinArgs A)
   }
   __syncthreads();
   const int base = (incl - run) + (warp > 0 ? warp_tot[warp - 1] : 0);
-  __syncthreads();  // every count is read before it is overwritten
 #pragma unroll
-  for (int t = 0; t < kPerThread; ++t) {
-    const int b = tid * kPerThread + t;
-    off[b] = base + local[t];
-    cur[b] = base + local[t];
-  }
+  for (int t = 0; t < kPerThread; ++t) cnt[pad_idx(tid * kPerThread + t)] = base + local[t];
   if (tid == kScanThreads - 1) off[KF_NBINS] = base + run;
+  __syncthreads();
+  for (int b = tid; b < KF_NBINS; b += kScanThreads) {  // coalesced
+    const int o = cnt[pad_idx(b)];
+    off[b] = o;
+    cur[b] = o;
+  }
 }
 
 __global__ void __launch_bounds__(kPointThreads) bin_scatter_kernel(const BinArgs A, int nseg) {
@@ -139,7 +148,13 @@ cudaError_t launch_bin_points(const BinArgs& a, int n_segments, cudaStream_t st)
   const int64_t pts = a.stride > 0 ? a.stride : 1;
   const int pgrid = int(std::min<int64_t>((pts + kPointThreads - 1) / kPointThreads, int64_t(1) << 20));
   bin_count_kernel<<<pgrid, kPointThreads, 0, st>>>(a, n_segments);
-  bin_scan_kernel<<<n_segments, kScanThreads, 0, st>>>(a);
+  static bool attr = false;
+  if (!attr) {
+    e = cudaFuncSetAttribute(bin_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kScanSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  bin_scan_kernel<<<n_segments, kScanThreads, kScanSmem, st>>>(a);
   bin_scatter_kernel<<<pgrid, kPointThreads, 0, st>>>(a, n_segments);
   const int64_t bins = int64_t(n_segments) * KF_NBINS;
   bin_sort_kernel<<<int((bins + kPointThreads - 1) / kPointThreads), kPointThreads, 0, st>>>(a, n_segments);

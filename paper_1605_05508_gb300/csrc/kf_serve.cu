@@ -85,7 +85,100 @@ class Arena {
   size_t size_ = 0, used_ = 0, peak_ = 0;
 };
 
-enum ReqState { kQueued, kResident, kFinishing, kDone, kFailed };
+// Host threads that share the large copies of kf_submit: staging an event in
+// pinned memory is a few MB, and one thread copies at ~15 GB/s, far below
+// what the host memory delivers; the submitting thread takes chunks too and
+// returns when all of its event's chunks are done.
+class CopyPool {
+ public:
+  struct Piece {
+    void* dst;
+    const void* src;
+    size_t bytes;
+  };
+  void start(int n_threads) {
+    for (int i = 0; i < n_threads; ++i) threads_.emplace_back([this] { worker(); });
+  }
+  void stop() {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      stop_ = true;
+    }
+    cv_.notify_all();
+    for (auto& t : threads_) t.join();
+    threads_.clear();
+  }
+  void copy(const Piece* pieces, int n_pieces) {
+    Job job;
+    std::vector<Chunk> chunks;
+    for (int p = 0; p < n_pieces; ++p)
+      for (size_t o = 0; o < pieces[p].bytes; o += kChunk) {
+        const size_t b = std::min(kChunk, pieces[p].bytes - o);
+        chunks.push_back({static_cast<char*>(pieces[p].dst) + o, static_cast<const char*>(pieces[p].src) + o, b, &job});
+      }
+    if (chunks.size() <= 1 || threads_.empty()) {
+      for (const Chunk& c : chunks) std::memcpy(c.dst, c.src, c.bytes);
+      return;
+    }
+    job.left = int(chunks.size());
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      for (const Chunk& c : chunks) q_.push_back(c);
+    }
+    cv_.notify_all();
+    while (true) {  // help until the queue is empty, then wait for this job
+      Chunk c;
+      {
+        std::lock_guard<std::mutex> lk(mu_);
+        if (q_.empty()) break;
+        c = q_.front();
+        q_.pop_front();
+      }
+      run(c);
+    }
+    std::unique_lock<std::mutex> lk(job.m);
+    job.cv.wait(lk, [&] { return job.left == 0; });
+  }
+
+ private:
+  static constexpr size_t kChunk = size_t(1) << 20;
+  struct Job {
+    std::mutex m;
+    std::condition_variable cv;
+    int left = 0;
+  };
+  struct Chunk {
+    char* dst;
+    const char* src;
+    size_t bytes;
+    Job* job;
+  };
+  static void run(const Chunk& c) {
+    std::memcpy(c.dst, c.src, c.bytes);
+    std::lock_guard<std::mutex> lk(c.job->m);
+    if (--c.job->left == 0) c.job->cv.notify_all();
+  }
+  void worker() {
+    while (true) {
+      Chunk c;
+      {
+        std::unique_lock<std::mutex> lk(mu_);
+        cv_.wait(lk, [&] { return stop_ || !q_.empty(); });
+        if (q_.empty()) return;  // stopping
+        c = q_.front();
+        q_.pop_front();
+      }
+      run(c);
+    }
+  }
+  std::mutex mu_;
+  std::condition_variable cv_;
+  std::deque<Chunk> q_;
+  std::vector<std::thread> threads_;
+  bool stop_ = false;
+};
+
+enum ReqState { kQueued, kPreparing, kResident, kFinishing, kDone, kFailed };
 
 // Byte layout of one event inside the device arena and the host arena.
 struct EventLayout {
@@ -180,7 +273,8 @@ struct Request {
   int layer = 0;  // next build layer
   size_t d_off = 0, h_in_off = 0, h_out_off = 0;
   bool has_d = false, has_in = false, has_out = false;
-  cudaEvent_t done = nullptr;
+  cudaEvent_t done = nullptr;      // results on the host
+  cudaEvent_t prepped = nullptr;   // preparation finished (prep stream)
   Clock::time_point t_submit, t_admit, t_done;
 };
 
@@ -196,7 +290,8 @@ struct Serve {
   std::thread thread;
   bool stop = false;
   int cuda_error = 0;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;       // build steps, final selection, results
+  cudaStream_t prep_stream = nullptr;  // preparation of admitted events (overlaps the steps)
   char* dmem = nullptr;
   char* hmem = nullptr;
   Arena darena, harena;
@@ -209,6 +304,7 @@ struct Serve {
   std::unordered_map<uint64_t, std::unique_ptr<Request>> all;
   kf_serve_stats stats{};
   kf_tuning tune{};  // launch parameters in effect at kf_serve_start
+  CopyPool copier;   // kf_submit's staging copies
 };
 
 static void fail_all_locked(Serve* sv, int err) {
@@ -218,13 +314,14 @@ static void fail_all_locked(Serve* sv, int err) {
   sv->done_cv.notify_all();
 }
 
-// Enqueue the preparation of an admitted event on the serve stream.
+// Enqueue the preparation of an admitted event on the preparation stream;
+// the event joins the build steps once r->prepped has completed.
 static cudaError_t prepare(Serve* sv, Request* r) {
   kf_ctx* ctx = sv->ctx;
   const EventLayout& L = r->lay;
   char* d = sv->dmem + r->d_off;
   char* h = sv->hmem + r->h_in_off;
-  cudaStream_t s = sv->stream;
+  cudaStream_t s = sv->prep_stream;
   const int64_t n = L.n;
   // the host input block mirrors the first device pieces (par .. sval); the
   // raw hits and their offsets follow in the host block and go to their own
@@ -296,7 +393,9 @@ static cudaError_t prepare(Serve* sv, Request* r) {
   ia.seed_perm = reinterpret_cast<const int32_t*>(d + L.d_perm);
   ia.n = n;
   ia.S = n;
-  return launch_build_init(ia, s);
+  e = launch_build_init(ia, s);
+  if (e != cudaSuccess) return e;
+  return cudaEventRecord(r->prepped, s);
 }
 
 static BuildSlot slot_of(Serve* sv, Request* r) {
@@ -437,6 +536,17 @@ static void scheduler(Serve* sv) {
         }
         ++it;
       }
+      // prepared events join the build steps (layer 0)
+      for (Request* r : sv->resident) {
+        if (r->state != kPreparing) continue;
+        const cudaError_t q = cudaEventQuery(r->prepped);
+        if (q == cudaSuccess) {
+          r->state = kResident;
+          r->layer = 0;
+        } else if (q != cudaErrorNotReady) {
+          fail_all_locked(sv, int(q));
+        }
+      }
       if (sv->cuda_error) {
         sv->resident.clear();
         sv->queue.clear();
@@ -449,7 +559,7 @@ static void scheduler(Serve* sv) {
         sv->queue.pop_front();
         r->d_off = off;
         r->has_d = true;
-        r->state = kResident;
+        r->state = kPreparing;
         r->layer = 0;
         r->t_admit = Clock::now();
         sv->stats.admitted++;
@@ -458,8 +568,8 @@ static void scheduler(Serve* sv) {
       }
       bool active = false;
       for (Request* r : sv->resident) active |= r->state == kResident;
-      bool finishing = false;
-      for (Request* r : sv->resident) finishing |= r->state == kFinishing;
+      bool finishing = false;  // (or preparing): the GPU will make progress without the host
+      for (Request* r : sv->resident) finishing |= r->state == kFinishing || r->state == kPreparing;
       if (!active && admitted.empty()) {
         if (sv->stop && sv->queue.empty() && !finishing) break;
         if (finishing)
@@ -550,10 +660,14 @@ void kf_serve_shutdown_internal(kf_ctx* ctx) {
   }
   sv->cv.notify_all();
   if (sv->thread.joinable()) sv->thread.join();
+  sv->copier.stop();
   cudaSetDevice(ctx->device);
   if (sv->stream) cudaStreamSynchronize(sv->stream);
-  for (auto& kv : sv->all)
+  if (sv->prep_stream) cudaStreamSynchronize(sv->prep_stream);
+  for (auto& kv : sv->all) {
     if (kv.second->done) cudaEventDestroy(kv.second->done);
+    if (kv.second->prepped) cudaEventDestroy(kv.second->prepped);
+  }
   for (int i = 0; i < kRing; ++i)
     if (sv->iter_ev[i]) cudaEventDestroy(sv->iter_ev[i]);
   if (sv->dmem) cudaFree(sv->dmem);
@@ -561,6 +675,7 @@ void kf_serve_shutdown_internal(kf_ctx* ctx) {
   if (sv->hmem) cudaFreeHost(sv->hmem);
   if (sv->h_table) cudaFreeHost(sv->h_table);
   if (sv->stream) cudaStreamDestroy(sv->stream);
+  if (sv->prep_stream) cudaStreamDestroy(sv->prep_stream);
   ctx->allocated -= sv->darena.size();
   delete sv;
   ctx->serve = nullptr;
@@ -595,6 +710,7 @@ int kf_serve_start(kf_ctx* ctx, const kf_serve_config* cfg) {
                            cudaHostAllocDefault) != cudaSuccess)
     rc = KF_ENOMEM;
   if (!rc && cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking) != cudaSuccess) rc = KF_ECUDA;
+  if (!rc && cudaStreamCreateWithFlags(&sv->prep_stream, cudaStreamNonBlocking) != cudaSuccess) rc = KF_ECUDA;
   for (int i = 0; i < kRing && !rc; ++i)
     if (cudaEventCreateWithFlags(&sv->iter_ev[i], cudaEventDisableTiming) != cudaSuccess) rc = KF_ECUDA;
   if (rc) {
@@ -604,6 +720,7 @@ int kf_serve_start(kf_ctx* ctx, const kf_serve_config* cfg) {
     if (sv->hmem) cudaFreeHost(sv->hmem);
     if (sv->h_table) cudaFreeHost(sv->h_table);
     if (sv->stream) cudaStreamDestroy(sv->stream);
+    if (sv->prep_stream) cudaStreamDestroy(sv->prep_stream);
     for (int i = 0; i < kRing; ++i)
       if (sv->iter_ev[i]) cudaEventDestroy(sv->iter_ev[i]);
     delete sv;
@@ -614,6 +731,8 @@ int kf_serve_start(kf_ctx* ctx, const kf_serve_config* cfg) {
   sv->stats.device_arena_bytes = dbytes;
   ctx->allocated += dbytes;
   ctx->serve = sv;
+  const int hw = int(std::thread::hardware_concurrency());
+  sv->copier.start(std::max(1, std::min(6, hw / 2 - 1)));
   sv->thread = std::thread(scheduler, sv);
   return KF_OK;
 }
@@ -656,21 +775,27 @@ int kf_submit(kf_ctx* ctx, const kf_event* ev, uint64_t* ticket) {
   }
   // stage the event in its pinned input block (layout mirrors the device block)
   char* h = sv->hmem + req->h_in_off;
-  std::memcpy(h + L.h_par, ev->seed_par, 6 * n * 4);
-  std::memcpy(h + L.h_cov, ev->seed_cov, 21 * n * 4);
-  std::memcpy(h + L.h_q, ev->seed_charge, n);
-  std::memcpy(h + L.h_shits, ev->seed_hits, size_t(ns) * 3 * n * 4);
+  CopyPool::Piece pieces[7];
+  int np = 0;
+  pieces[np++] = {h + L.h_par, ev->seed_par, size_t(6) * n * 4};
+  pieces[np++] = {h + L.h_cov, ev->seed_cov, size_t(21) * n * 4};
+  pieces[np++] = {h + L.h_q, ev->seed_charge, size_t(n)};
+  pieces[np++] = {h + L.h_shits, ev->seed_hits, size_t(ns) * 3 * n * 4};
   if (ev->seed_valid)
-    std::memcpy(h + L.h_sval, ev->seed_valid, size_t(ns) * n);
+    pieces[np++] = {h + L.h_sval, ev->seed_valid, size_t(ns) * n};
   else
     std::memset(h + L.h_sval, 1, size_t(ns) * n);
-  if (nh > 0) std::memcpy(h + L.h_xyz, ev->layer_xyz, size_t(3) * nh * 4);
-  std::memcpy(h + L.h_segoff, ev->layer_off, size_t(Lb + 1) * 8);
+  if (nh > 0) pieces[np++] = {h + L.h_xyz, ev->layer_xyz, size_t(3) * nh * 4};
+  pieces[np++] = {h + L.h_segoff, ev->layer_off, size_t(Lb + 1) * 8};
+  sv->copier.copy(pieces, np);
   const int64_t sseg[2] = {0, n};  // seed segment, right after the layer offsets (padding room)
   std::memcpy(h + L.h_segoff + size_t(Lb + 1) * 8, sseg, sizeof sseg);
   cudaSetDevice(ctx->device);
-  if (cudaEventCreateWithFlags(&req->done, cudaEventDisableTiming) != cudaSuccess) {
+  if (cudaEventCreateWithFlags(&req->done, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&req->prepped, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
+    if (req->done) cudaEventDestroy(req->done);
+    if (req->prepped) cudaEventDestroy(req->prepped);
     std::lock_guard<std::mutex> lk(sv->mu);
     release_locked(sv, req.get());
     sv->harena.release(req->h_out_off, L.h_out_total);
@@ -709,6 +834,7 @@ int kf_poll(kf_ctx* ctx, uint64_t ticket, kf_event_result* out, int64_t timeout_
     if (r->has_out) sv->harena.release(r->h_out_off, r->lay.h_out_total);
     r->has_out = false;
     if (r->done) cudaEventDestroy(r->done);
+    if (r->prepped) cudaEventDestroy(r->prepped);
     sv->all.erase(it);
     return KF_ECUDA;
   }
@@ -734,6 +860,7 @@ int kf_poll(kf_ctx* ctx, uint64_t ticket, kf_event_result* out, int64_t timeout_
   sv->harena.release(r->h_out_off, L.h_out_total);
   r->has_out = false;
   if (r->done) cudaEventDestroy(r->done);
+  if (r->prepped) cudaEventDestroy(r->prepped);
   sv->all.erase(it);
   return KF_OK;
 }
@@ -750,6 +877,7 @@ int kf_cancel(kf_ctx* ctx, uint64_t ticket) {
   release_locked(sv, r);
   if (r->has_out) sv->harena.release(r->h_out_off, r->lay.h_out_total);
   if (r->done) cudaEventDestroy(r->done);
+  if (r->prepped) cudaEventDestroy(r->prepped);
   sv->stats.cancelled++;
   sv->all.erase(it);
   return KF_OK;
