@@ -282,6 +282,11 @@ typedef struct {
     int32_t build_scan;       /* chi2 scan of the kf_build step: 0 = each lane scans its own
                                  candidate's window (default), 1 = the seed's 8 lanes scan each
                                  parent's window together (balanced when few candidates) */
+    int32_t fit_chunk;        /* kf_fit: 0 = each layer step is one launch over the whole batch
+                                 (default); 262144, 524288 or 1048576 = the batch is fitted in
+                                 chunks of that many tracks, all layers of a chunk before the
+                                 next, so the chunk's state stays in the L2 cache between its
+                                 layer launches */
 } kf_tuning;
 
 /* Current launch parameters of the context.  Errors: KF_EINVAL (null). */
@@ -293,7 +298,7 @@ int kf_get_tuning(const kf_ctx *ctx, kf_tuning *out);
 int kf_set_tuning(kf_ctx *ctx, const kf_tuning *t);
 
 /* Autotuner of kf_fit: runs kf_fit on the caller's arguments once per
- * fit_block value (one untimed call, then three timed with CUDA events on
+ * (fit_block, fit_chunk) value (one untimed call, then three timed with CUDA events on
  * `stream`, which is synchronised), keeps the fastest in the context and
  * writes the context's tuning to *chosen (may be NULL).  The outputs hold the
  * result of the last call, identical for every value.  Errors: those of

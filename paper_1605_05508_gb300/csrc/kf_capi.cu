@@ -173,10 +173,14 @@ int kf_fit(kf_ctx* ctx, const kf_tracks* seeds, const kf_track_hits* hits, kf_tr
   const float v0 = ctx->cfg.sigma_xy_cm * ctx->cfg.sigma_xy_cm;
   const float v2 = ctx->cfg.sigma_z_cm * ctx->cfg.sigma_z_cm;
   const int block = ctx->tune.fit_block;
+  // tracks per L2 block: every layer of a chunk runs before the next chunk,
+  // so the chunk's state stays in L2 between its layer launches
+  const int64_t chunk = ctx->tune.fit_chunk > 0 ? std::min<int64_t>(ctx->tune.fit_chunk, n) : n;
   std::vector<uint64_t> key = {1,
                                uint64_t(n),
                                uint64_t(L),
                                uint64_t(block),
+                               uint64_t(chunk),
                                reinterpret_cast<uint64_t>(seeds->par),
                                reinterpret_cast<uint64_t>(seeds->par_lo),
                                reinterpret_cast<uint64_t>(seeds->cov),
@@ -196,8 +200,11 @@ int kf_fit(kf_ctx* ctx, const kf_tracks* seeds, const kf_track_hits* hits, kf_tr
     cudaStream_t cs = ctx->capture_stream;
     KF_CUDA_TRY(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     cudaError_t le = cudaSuccess;
+    for (int64_t c0 = 0; c0 < n && le == cudaSuccess; c0 += chunk)
     for (int l = 0; l < L && le == cudaSuccess; ++l) {
       FitLayerArgs a;
+      a.begin = c0;
+      a.count = std::min(chunk, n - c0);
       a.in_par = l == 0 ? seeds->par : out->par;
       a.in_lo = l == 0 ? seeds->par_lo : lo;
       a.in_cov = l == 0 ? seeds->cov : out->cov;

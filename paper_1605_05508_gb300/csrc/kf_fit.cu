@@ -126,8 +126,8 @@ __device__ __forceinline__ void fit_layer_track(const FitLayerArgs& A, int64_t i
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS, kFitWarpsPerSM * 32 / THREADS) fit_layer_kernel(const FitLayerArgs A) {
   const int64_t n = A.n;
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const int64_t i = A.begin + int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= A.begin + A.count) return;
   const int32_t st = A.first ? 0 : A.status[i];
   float p[6], lo[3], C[21];
   if (!(st & KF_ST_STOPPED)) {
@@ -217,9 +217,9 @@ int fit_grid(int block, int64_t n) {
 
 cudaError_t launch_fit_layer(const FitLayerArgs& a, int block, cudaStream_t st) {
   if (block == 64)
-    fit_layer_kernel<64><<<fit_grid(64, a.n), 64, 0, st>>>(a);
+    fit_layer_kernel<64><<<fit_grid(64, a.count), 64, 0, st>>>(a);
   else
-    fit_layer_kernel<128><<<fit_grid(128, a.n), 128, 0, st>>>(a);
+    fit_layer_kernel<128><<<fit_grid(128, a.count), 128, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -60,7 +60,7 @@ struct kf_ctx {
   cudaStream_t host_streams[kfi::kHostStreams] = {};  // kf_fit_host pipeline
   cudaEvent_t host_done[kfi::kHostStreams] = {};
   cudaEvent_t host_start = nullptr;
-  kf_tuning tune = {128, 0, 8, 0};  // launch parameters (kf_set_tuning, kf_autotune_*)
+  kf_tuning tune = {128, 0, 8, 0, 0};  // launch parameters (kf_set_tuning, kf_autotune_*)
 };
 
 namespace kfi {
@@ -93,7 +93,8 @@ struct FitLayerArgs {
   const uint8_t* valid;  // [n] of this layer or null
   float* chi2;           // [n] of this layer or null
   int32_t* status;       // [n], required
-  int64_t n;
+  int64_t n;             // tracks of the batch (the row stride)
+  int64_t begin, count;  // this launch: tracks [begin, begin + count)
   float a_scale;  // C_LIGHT * Bz
   float R, v0, v1, v2;
   float x_x0, mass;  // this layer's thickness in radiation lengths (0: none); particle mass

@@ -76,6 +76,8 @@ extern "C" int kf_fit_noalloc(kf_ctx* ctx, const kf_tracks* seeds, const kf_trac
     a.chi2 = chi2 ? chi2 + int64_t(l) * n : nullptr;
     a.status = st;
     a.n = n;
+    a.begin = 0;
+    a.count = n;
     a.a_scale = float(kfi::kCLight * double(ctx->cfg.bz_tesla));
     a.R = ctx->radius[l];
     a.x_x0 = ctx->x_x0[l];

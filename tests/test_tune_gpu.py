@@ -11,7 +11,7 @@ from fitutil import gpu_fit
 
 pytestmark = pytest.mark.gpu
 
-DEFAULT = {"fit_block": 128, "build_hit_tile": 0, "build_list_width": 8, "build_scan": 0}
+DEFAULT = {"fit_block": 128, "build_hit_tile": 0, "build_list_width": 8, "build_scan": 0, "fit_chunk": 0}
 BUILD_KEYS = ("par", "cov", "chi2", "nhits", "status", "hits", "n_cands", "cand_hits", "cand_chi2", "cand_nhits")
 
 
@@ -24,12 +24,13 @@ def test_tuning_defaults_and_validation(cuda_ctx_factory):
     from paper_1605_05508_gb300 import kf
     ctx = cuda_ctx_factory(S.barrel().radii)
     assert kf.kf_get_tuning(ctx) == DEFAULT
-    for bad in [(96, 0, 8, 0), (128, 256, 8, 0), (128, 0, 6, 0), (0, 0, 0, 0), (128, 0, 8, 2)]:
+    for bad in [(96, 0, 8, 0), (128, 256, 8, 0), (128, 0, 6, 0), (0, 0, 0, 0), (128, 0, 8, 2), (128, 0, 8, 0, 1000)]:
         with pytest.raises(kf.KfError):
             kf.kf_set_tuning(ctx, *bad)
     assert kf.kf_get_tuning(ctx) == DEFAULT
-    kf.kf_set_tuning(ctx, 64, 512, 4, 1)
-    assert kf.kf_get_tuning(ctx) == {"fit_block": 64, "build_hit_tile": 512, "build_list_width": 4, "build_scan": 1}
+    kf.kf_set_tuning(ctx, 64, 512, 4, 1, 524288)
+    assert kf.kf_get_tuning(ctx) == {"fit_block": 64, "build_hit_tile": 512, "build_list_width": 4, "build_scan": 1,
+                                     "fit_chunk": 524288}
 
 
 @pytest.mark.parametrize("n", [7001, 64])
@@ -47,6 +48,20 @@ def test_fit_block_sizes_bitwise(cuda_ctx_factory, n):
     t = gpu_fit(ctx, ev.seeds, ev.hits.xyz, ev.hits.valid, "autotune")
     _same(res[0], t, ("par", "cov", "chi2", "status"))
     assert kf.kf_get_tuning(ctx)["fit_block"] in (64, 128)
+
+
+def test_fit_l2_chunks_bitwise(cuda_ctx_factory):
+    """fit_chunk: all layers of a chunk of tracks before the next chunk (three
+    chunks of 262 144 tracks, the last one ragged): the same bits."""
+    from paper_1605_05508_gb300 import kf
+    det = S.barrel()
+    ctx = cuda_ctx_factory(det.radii)
+    ev = S.make_fit_batch(95, 600_001, det, keep_truth=False)
+    res = []
+    for chunk in (0, 262144):
+        kf.kf_set_tuning(ctx, 64, 0, 8, 0, chunk)
+        res.append(gpu_fit(ctx, ev.seeds, ev.hits.xyz, ev.hits.valid, "graph"))
+    _same(res[0], res[1], ("par", "cov", "chi2", "status"))
 
 
 def _batches():
