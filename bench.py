@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--tracks", type=int, default=20000)
     ap.add_argument("--layers", type=int, default=10)
     ap.add_argument("--seed", type=int, default=1606)
+    ap.add_argument("--fit-tuning", default=None, metavar="BLOCK,CHUNK",
+                    help="fixed fit launch parameters (threads per block, tracks per L2 chunk; 0 = whole batch) "
+                         "instead of the autotuner's")
     ap.add_argument("--no-extras", action="store_true", help="headline only (no e2e/f64/fused/cpu legs)")
     ap.add_argument("--no-build", action="store_true", help="skip the combinatorial-build leg")
     ap.add_argument("--build-events", type=int, default=50)
@@ -268,8 +271,14 @@ def run_ours(a):
     def step():
         kf.kf_fit(ctx, seeds, hits, out, chi2, status, stream)
 
-    # the library's autotuner picks the layer kernel's block size on this batch
-    tuning = kf.kf_autotune_fit(ctx, seeds, hits, out, chi2, status, stream)
+    # the library's autotuner picks the layer kernel's block size and L2 chunk on this batch
+    if a.fit_tuning:
+        block, chunk = (int(v) for v in a.fit_tuning.split(","))
+        kf.kf_set_tuning(ctx, block, 0, 8, 0, chunk)
+        tuning = kf.kf_get_tuning(ctx)
+    else:
+        tuning = kf.kf_autotune_fit(ctx, seeds, hits, out, chi2, status, stream)
+    chunks = -(-n // tuning["fit_chunk"]) if 0 < tuning["fit_chunk"] < n else 1
     for _ in range(max(a.warmup, 3)):
         step()
     torch.cuda.synchronize()
@@ -293,21 +302,21 @@ def run_ours(a):
     ms_per_step = t_ms / a.steps
     value = whole_job_rate(n * L, world, ms_per_step / 1e3)
 
-    # roofline of the per-layer kernel: the graph holds only the L layer launches
-    launch_s = ms_per_step / 1e3 / L
+    # roofline of the per-layer kernel: the graph holds only the L x chunks layer launches
+    launch_s = ms_per_step / 1e3 / (L * chunks)
     bpt = fit_bytes_per_track_layer(L, False, True, True)
-    achieved = bpt * n / launch_s / 1e9
+    achieved = bpt * n / chunks / launch_s / 1e9
     peak, peak_kind = measured_peaks()
     traffic = ncu_traffic(n)
     roof = {"kernel": f"fit_layer_kernel<{tuning['fit_block']}>", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+            "frac": achieved / peak, "traffic": traffic if chunks == 1 else None, "peak_kind": peak_kind,
             "algorithmic_bytes_per_track_layer": bpt, "launch_us": launch_s * 1e6}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 (positions as float pairs)",
             "data": "synthetic (seeded generator, helix hits + Gaussian smear)",
-            "config": workload_config(a), "roofline": roof, "clocks": clk, "gpu_launches": a.steps * L,
+            "config": workload_config(a), "roofline": roof, "clocks": clk, "gpu_launches": a.steps * L * chunks,
             "tuning": tuning}
 
     if not a.no_extras:
