@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-build", action="store_true", help="skip the combinatorial-build leg")
     ap.add_argument("--build-events", type=int, default=50)
     ap.add_argument("--build-seeds", type=int, default=5000)
+    ap.add_argument("--build-tuning", default=None, metavar="TILE,LIST,SCAN",
+                    help="fixed launch parameters of the N = 6 build (hit tile, child-list width, scan scheme) "
+                         "instead of the sweep and the autotuner's choice")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--serve-pool", type=int, default=24, help="distinct events in the serving pool")
     ap.add_argument("--serve-requests", type=int, default=240, help="requests per serving run")
@@ -199,16 +202,20 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+FIT_SOURCES = ("kf_fit.cu", "kf_math.cuh")
+BUILD_SOURCES = ("kf_build.cu", "kf_build.cuh", "kf_math.cuh")
+
+
+def kernel_source_hash(files=FIT_SOURCES):
     h = hashlib.sha256()
-    for f in ("kf_fit.cu", "kf_math.cuh"):
+    for f in files:
         h.update(open(os.path.join(ROOT, "paper_1605_05508_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def profile_value(name, key):
+def profile_value(name, key, files=FIT_SOURCES):
     """A figure from a committed ncu summary (profiles/<name>), or None when
-    absent or taken on a different kernel source."""
+    absent or taken on a different kernel source (`files`, hashed)."""
     p = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(p):
         return None
@@ -217,7 +224,7 @@ def profile_value(name, key):
         if ":" in ln and not ln.lstrip().startswith("#"):
             k, v = ln.split(":", 1)
             kv[k.strip()] = v.strip()
-    if kv.get("source_hash") != kernel_source_hash():
+    if kv.get("source_hash") != kernel_source_hash(files):
         return None
     return float(kv[key])
 
@@ -481,15 +488,19 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist):
         times = {}
         for tile in (0, 512):
             for lw in (8, 4):
-                for scan in (0, 1):
-                    if lw == 4 and N > 4:
+                for scan in (0, 1, 2):
+                    if (lw == 4 and N > 4) or (scan == 2 and tile > 0):
                         continue
                     kf.kf_set_tuning(ctx, 128, tile, lw, scan)
-                    times[f"tile{tile}_list{lw}_{'coop' if scan else 'lane'}"] = float(run(N, 5)[1][2])
+                    times[f"tile{tile}_list{lw}_{('lane', 'coop', 'packed')[scan]}"] = float(run(N, 5)[1][2])
         return times, kf.kf_autotune_build(ctx, fo, seed_off, bins, N, out, stream)
 
     k = max(5, min(50, a.steps // 4))
-    sweep6, tune6 = sweep_and_tune(6)
+    if a.build_tuning:
+        kf.kf_set_tuning(ctx, 128, *(int(v) for v in a.build_tuning.split(",")))
+        sweep6, tune6 = None, kf.kf_get_tuning(ctx)
+    else:
+        sweep6, tune6 = sweep_and_tune(6)
     tot6, t6 = run(6, k)
     mean_hits = float(out.n_hits.float().mean())
     # build efficiency: best candidate with >= 80 % of its building-layer hits
@@ -538,6 +549,23 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist):
                            "tuning": tune1, "build_ms_by_setting": sweep1},
            "tuning": tune6, "build_ms_by_setting": sweep6, "efficiency_and_refit": efficiency,
            "gpu_launches_per_step": 3 + 1 + (3 + Lb + 1)}
+    # issue roofline of the build steps: warp instructions of the Lb step
+    # launches of one build (committed ncu summary, same setting) over the whole
+    # build phase's time (which also holds seed ordering, init and final
+    # selection: a lower bound on the step kernels' rate)
+    prof = "build_step_kernel.instructions.txt"
+    wi = profile_value(prof, "warp_instructions_per_build", BUILD_SOURCES)
+    setting = profile_value(prof, "setting_code", BUILD_SOURCES)
+    code = tune6["build_hit_tile"] * 100 + tune6["build_list_width"] * 10 + tune6["build_scan"]
+    if wi and setting == code and E == profile_value(prof, "events", BUILD_SOURCES):
+        props = torch.cuda.get_device_properties(dev)
+        peak = 4.0 * props.multi_processor_count * float(line_clock_mhz(dev)) * 1e6
+        ach = wi / (float(t6[2]) / 1e3)
+        res["roofline"] = {"kernel": "build_step_kernel", "bound": "alu", "achieved": ach, "peak": peak,
+                           "unit": "warp instructions/s", "frac": ach / peak, "warp_instructions_per_build": wi,
+                           "active_lanes_per_warp_instruction": profile_value(prof, "active_lanes_per_warp_instruction",
+                                                                              BUILD_SOURCES),
+                           "peak_kind": "4 issues per SM per cycle x SMs x max SM clock"}
     if rank == 0 and not a.no_extras:
         import oracle as O
         cores = os.cpu_count() or 1

@@ -279,9 +279,12 @@ typedef struct {
                                  0 = none, the scans read global memory (default), or 512 */
     int32_t build_list_width; /* entries of a lane's child list in the kf_build step: 4 or 8
                                  (default 8); 4 takes effect only when max_cands <= 4 */
-    int32_t build_scan;       /* chi2 scan of the kf_build step: 0 = each lane scans its own
-                                 candidate's window (default), 1 = the seed's 8 lanes scan each
-                                 parent's window together (balanced when few candidates) */
+    int32_t build_scan;       /* thread layout of the kf_build step: 0 = 8 lanes per seed, each
+                                 scanning its own candidate's window (default), 1 = 8 lanes per
+                                 seed scanning each parent's window together (balanced when few
+                                 candidates), 2 = the live candidates packed onto consecutive
+                                 threads for the propagation and scan, and the kept children
+                                 for the update (requires build_hit_tile 0) */
     int32_t fit_chunk;        /* kf_fit: 0 = each layer step is one launch over the whole batch
                                  (default); 262144, 524288 or 1048576 = the batch is fitted in
                                  chunks of that many tracks, all layers of a chunk before the
@@ -307,8 +310,8 @@ int kf_autotune_fit(kf_ctx *ctx, const kf_tracks *seeds, const kf_track_hits *hi
                     float *chi2, int32_t *status, void *stream, kf_tuning *chosen);
 
 /* Autotuner of kf_build: the same over build_hit_tile x build_list_width x
- * build_scan (list width 4 is tried only when max_cands <= 4).  Errors: those
- * of kf_build. */
+ * build_scan (list width 4 is tried only when max_cands <= 4, layout 2 only
+ * without hit staging).  Errors: those of kf_build. */
 int kf_autotune_build(kf_ctx *ctx, const kf_tracks *seeds, const int64_t *seed_off,
                       const kf_layer_hit_bins *bins, int32_t max_cands, kf_build_result *out, void *stream,
                       kf_tuning *chosen);

@@ -76,6 +76,99 @@ __device__ __forceinline__ int wrap_phi(int d) {  // to [-KF_BIN_PHI/2, KF_BIN_P
   return ((d + KF_BIN_PHI / 2) & (KF_BIN_PHI - 1)) - KF_BIN_PHI / 2;
 }
 
+// Window of a predicted candidate: S^-1 = (C_pos + V)^-1, and the eta rows
+// e0..e1 and phi bins fa0..fa1, fb0..fb1 (second part when the window wraps
+// around phi = +-pi) that can hold a hit with chi2 < cut at radius R.
+__device__ __forceinline__ void hit_window(const float p[6], const float lo[3], const float C[21], float R,
+                                           const BuildStepArgs& Args, float Si[6], int& e0, int& e1, int& fa0,
+                                           int& fa1, int& fb0, int& fb1) {
+  kf::inverse_S(C, Args.v0, Args.v1, Args.v2, Si);
+  const float X = p[0] + lo[0], Y = p[1] + lo[1], Z = p[2] + lo[2];
+  const float rr = sqrtf(X * X + Y * Y);
+  const float cph = X / rr, sph = Y / rr;
+  const float s00 = C[0] + Args.v0, s10 = C[1], s11 = C[2] + Args.v1, s22 = C[5] + Args.v2;
+  const float Stt = sph * sph * s00 - 2.f * sph * cph * s10 + cph * cph * s11;
+  const float Snn = cph * cph * s00 + 2.f * sph * cph * s10 + sph * sph * s11;
+  const float wt = sqrtf(Args.cut * fmaxf(Stt, 0.f));
+  const float wn = sqrtf(Args.cut * fmaxf(Snn, 0.f));
+  const float wz = sqrtf(Args.cut * fmaxf(s22, 0.f));
+  // phi bins: |dphi| <= atan(wt / (R - wn)), one bin of margin each side
+  const float rin = R - wn;
+  const float phic = atan2f(Y, X);
+  const float dphi = (rin > 0.5f * R && wt < rin) ? atanf(wt / rin) : 10.f;
+  if (dphi < 1.f && phic >= -kPi && phic <= kPi) {  // also false for NaN
+    const float scale = float(KF_BIN_PHI) / (2.0f * kPi);
+    const int f0 = __float2int_rd((phic - dphi + kPi) * scale) - 1;
+    const int f1 = __float2int_rd((phic + dphi + kPi) * scale) + 1;
+    if (f1 - f0 + 1 < KF_BIN_PHI) {
+      if (f0 < 0) {
+        fa0 = f0 + KF_BIN_PHI;
+        fb0 = 0;
+        fb1 = f1;
+      } else if (f1 >= KF_BIN_PHI) {
+        fa0 = f0;
+        fb0 = 0;
+        fb1 = f1 - KF_BIN_PHI;
+      } else {
+        fa0 = f0;
+        fa1 = f1;
+      }
+    }
+  }
+  // eta bins: z within Z +- wz and the hit radius within R +- wn
+  e0 = 0;
+  e1 = KF_BIN_ETA - 1;
+  const float rlo = R - wn, rhi = R + wn;
+  if (rlo > 0.f) {
+    const float zlo = Z - wz, zhi = Z + wz;
+    const float tmin = zlo >= 0.f ? zlo / rhi : zlo / rlo;
+    const float tmax = zhi >= 0.f ? zhi / rlo : zhi / rhi;
+    e0 = max(eta_bin(asinhf(tmin)) - 1, 0);
+    e1 = min(eta_bin(asinhf(tmax)) + 1, KF_BIN_ETA - 1);
+  }
+}
+
+// Clone engine, one seed per 8-lane group: the lanes' sorted child lists
+// (L, P) are merged by shuffles into the seed's best max_cands keys.  Lane k
+// receives the k-th best (key, parent rank, hit position); every lane gets
+// the number of children kept.
+template <int LW>
+__device__ __forceinline__ void merge_group(uint64_t (&L)[LW], int (&P)[LW], int max_cands, int k, int gbase,
+                                            uint64_t& my_key, int& my_parent, int& my_pos, int& n_win) {
+#pragma unroll
+  for (int r = 0; r < LW; ++r) {
+    if (r < max_cands) {  // uniform over the launch; max_cands <= LW
+      uint64_t m = L[0];
+#pragma unroll
+      for (int d = kGroup / 2; d >= 1; d >>= 1) {
+        const uint64_t o = __shfl_xor_sync(kFull, m, d);
+        m = o < m ? o : m;
+      }
+      const bool mine = (L[0] == m) && (m != kNoKey);
+      const unsigned bal = (__ballot_sync(kFull, mine) >> gbase) & 0xffu;
+      const int wl = bal ? __ffs(bal) - 1 : 0;
+      const int wpos = __shfl_sync(kFull, P[0], gbase + wl);
+      if (mine) {
+#pragma unroll
+        for (int t = 0; t < LW - 1; ++t) {
+          L[t] = L[t + 1];
+          P[t] = P[t + 1];
+        }
+        L[LW - 1] = kNoKey;
+        P[LW - 1] = -1;
+      }
+      if (m != kNoKey) {
+        if (k == r) {
+          my_key = m;
+          my_parent = int((m >> 21) & 7u);
+          my_pos = wpos;
+        }
+        ++n_win;
+      }
+    }
+  }
+}
+
 // Five blocks of 128 threads per SM (20 warps, at most 96 registers): more
 // resident warps hide the dependent loads of the window scans better than
 // the spills they cost (measured: 3.43 vs 3.78 ms per 7-layer build at N = 6).
@@ -158,52 +251,7 @@ __global__ void __launch_bounds__(kBuildThreads, 5) build_step_kernel(const Buil
   const bool scan = active && !stopped;
   float Si[6];
   int e0 = 0, e1 = -1, fa0 = 0, fa1 = KF_BIN_PHI - 1, fb0 = 0, fb1 = -1;
-  if (scan) {
-    kf::inverse_S(C, Args.v0, Args.v1, Args.v2, Si);
-    const float X = p[0] + lo[0], Y = p[1] + lo[1], Z = p[2] + lo[2];
-    const float rr = sqrtf(X * X + Y * Y);
-    const float cph = X / rr, sph = Y / rr;
-    const float s00 = C[0] + Args.v0, s10 = C[1], s11 = C[2] + Args.v1, s22 = C[5] + Args.v2;
-    const float Stt = sph * sph * s00 - 2.f * sph * cph * s10 + cph * cph * s11;
-    const float Snn = cph * cph * s00 + 2.f * sph * cph * s10 + sph * sph * s11;
-    const float wt = sqrtf(Args.cut * fmaxf(Stt, 0.f));
-    const float wn = sqrtf(Args.cut * fmaxf(Snn, 0.f));
-    const float wz = sqrtf(Args.cut * fmaxf(s22, 0.f));
-    // phi bins: |dphi| <= atan(wt / (R - wn)), one bin of margin each side
-    const float rin = D.R - wn;
-    const float phic = atan2f(Y, X);
-    const float dphi = (rin > 0.5f * D.R && wt < rin) ? atanf(wt / rin) : 10.f;
-    if (dphi < 1.f && phic >= -kPi && phic <= kPi) {  // also false for NaN
-      const float scale = float(KF_BIN_PHI) / (2.0f * kPi);
-      const int f0 = __float2int_rd((phic - dphi + kPi) * scale) - 1;
-      const int f1 = __float2int_rd((phic + dphi + kPi) * scale) + 1;
-      if (f1 - f0 + 1 < KF_BIN_PHI) {
-        if (f0 < 0) {
-          fa0 = f0 + KF_BIN_PHI;
-          fb0 = 0;
-          fb1 = f1;
-        } else if (f1 >= KF_BIN_PHI) {
-          fa0 = f0;
-          fb0 = 0;
-          fb1 = f1 - KF_BIN_PHI;
-        } else {
-          fa0 = f0;
-          fa1 = f1;
-        }
-      }
-    }
-    // eta bins: z within Z +- wz and the hit radius within R +- wn
-    e0 = 0;
-    e1 = KF_BIN_ETA - 1;
-    const float rlo = D.R - wn, rhi = D.R + wn;
-    if (rlo > 0.f) {
-      const float zlo = Z - wz, zhi = Z + wz;
-      const float tmin = zlo >= 0.f ? zlo / rhi : zlo / rlo;
-      const float tmax = zhi >= 0.f ? zhi / rlo : zhi / rhi;
-      e0 = max(eta_bin(asinhf(tmin)) - 1, 0);
-      e1 = min(eta_bin(asinhf(tmax)) + 1, KF_BIN_ETA - 1);
-    }
-  }
+  if (scan) hit_window(p, lo, C, D.R, Args, Si, e0, e1, fa0, fa1, fb0, fb1);
   const int32_t* boff = D.bin_off + int64_t(seg) * (KF_NBINS + 1);
 
   // ---- warp union of the windows and staging (TILE > 0)
@@ -422,38 +470,7 @@ __global__ void __launch_bounds__(kBuildThreads, 5) build_step_kernel(const Buil
   // ---- clone engine: merge the group's lists into the best max_cands
   uint64_t my_key = kNoKey;
   int my_parent = 0, my_pos = -1, n_win = 0;
-#pragma unroll
-  for (int r = 0; r < LW; ++r) {
-    if (r < Args.max_cands) {  // uniform over the launch; max_cands <= LW
-      uint64_t m = L[0];
-#pragma unroll
-      for (int d = kGroup / 2; d >= 1; d >>= 1) {
-        const uint64_t o = __shfl_xor_sync(kFull, m, d);
-        m = o < m ? o : m;
-      }
-      const bool mine = (L[0] == m) && (m != kNoKey);
-      const unsigned bal = (__ballot_sync(kFull, mine) >> gbase) & 0xffu;
-      const int wl = bal ? __ffs(bal) - 1 : 0;
-      const int wpos = __shfl_sync(kFull, P[0], gbase + wl);
-      if (mine) {
-#pragma unroll
-        for (int t = 0; t < LW - 1; ++t) {
-          L[t] = L[t + 1];
-          P[t] = P[t + 1];
-        }
-        L[LW - 1] = kNoKey;
-        P[LW - 1] = -1;
-      }
-      if (m != kNoKey) {
-        if (k == r) {
-          my_key = m;
-          my_parent = int((m >> 21) & 7u);
-          my_pos = wpos;
-        }
-        ++n_win;
-      }
-    }
-  }
+  merge_group(L, P, Args.max_cands, k, gbase, my_key, my_parent, my_pos, n_win);
 
   // ---- materialise the winners: pull the parent's predicted state
   const int src = gbase + my_parent;
@@ -493,6 +510,240 @@ __global__ void __launch_bounds__(kBuildThreads, 5) build_step_kernel(const Buil
     D.hist_hit[slot] = hit_plus1 - 1;
   }
   if (seed_ok && k == 0) D.out.ncand[j] = int8_t(n_win);
+}
+
+// ---- candidate-packed step (scan scheme 2)
+//
+// The same computation as build_step_kernel, with threads assigned to live
+// candidates instead of fixed 8-lane seed groups.  A block serves the same 16
+// seeds (same grid and slot table), in three phases separated by block
+// barriers:
+//   1. the block's live parents are packed onto its first threads; each
+//      propagates its candidate, derives its window, scans it (global memory)
+//      and leaves its prediction and sorted child list in shared memory --
+//      warps past the last parent skip the phase;
+//   2. the 8 lanes of seed s load the lists of its parents and merge them as
+//      in the grouped step (merge_group);
+//   3. the kept children are packed the same way; each is updated with its
+//      hit from its parent's prediction in shared memory and stored.
+// In the early building layers a seed holds one or two candidates, so the
+// grouped layout leaves most lanes of a warp idle through the propagation
+// and the update; packed, those phases take as many warps as there are
+// candidates (rounded up to 32).  Every candidate and child goes through the
+// same functions as in the grouped step, so the results are bitwise equal.
+constexpr int kSeedsPerBlock = kBuildThreads / kGroup;  // 16
+constexpr int kStateWords = kParN + 21;                 // x y z px py pz, lo x y z, covariance
+constexpr int kStoppedBit = 1 << 30;                    // parent stopped (status word in shared memory)
+
+// Exclusive scan of one count per seed (lanes 0..15 of warp 0; all 32 lanes
+// call): start[0] = 0, start[s + 1] = start[s] + count of seed s.
+__device__ __forceinline__ void seed_scan(int count, int* start) {
+  const int lane = threadIdx.x & 31;
+  int x = lane < kSeedsPerBlock ? count : 0;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int y = __shfl_up_sync(kFull, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane < kSeedsPerBlock) start[lane + 1] = x;
+  if (lane == 0) start[0] = 0;
+}
+
+// The seed whose packed items hold position t: start[s] <= t < start[s + 1]
+// (requires t < start[kSeedsPerBlock]).
+__device__ __forceinline__ int packed_owner(const int* start, int t) {
+  int s = 0;
+#pragma unroll
+  for (int b = kSeedsPerBlock / 2; b >= 1; b >>= 1)
+    if (start[s + b] <= t) s += b;
+  return s;
+}
+
+template <int LW>
+__global__ void __launch_bounds__(kBuildThreads, 5) build_step_packed_kernel(const BuildStepArgs Args) {
+  __shared__ BuildSlot sD;
+  __shared__ float s_state[kStateWords][kBuildThreads];  // parent predictions
+  __shared__ uint64_t s_key[LW][kBuildThreads];          // parent child lists
+  __shared__ int s_pos[LW][kBuildThreads];
+  __shared__ int s_pst[kBuildThreads];        // parent status | kStoppedBit
+  __shared__ uint64_t s_ckey[kBuildThreads];  // kept child of rank r of seed s at s * kGroup + r
+  __shared__ int s_cpos[kBuildThreads];
+  __shared__ int s_nwin[kSeedsPerBlock];
+  __shared__ int s_pstart[kSeedsPerBlock + 1], s_cstart[kSeedsPerBlock + 1];
+  const int t = threadIdx.x;
+  if (t == 0) {
+    int sl = 0;
+    while (sl + 1 < Args.n_slots && int(blockIdx.x) >= Args.slots[sl + 1].block_begin) ++sl;
+    sD = Args.slots[sl];
+  }
+  __syncthreads();
+  const BuildSlot& D = sD;
+  const int64_t S8 = D.S * kGroup;
+  const int64_t j0 = int64_t(blockIdx.x - D.block_begin) * kSeedsPerBlock;
+  if (t < 32) {
+    const bool ok = t < kSeedsPerBlock && j0 + t < D.S;
+    seed_scan(ok ? int(D.in.ncand[j0 + t]) : 0, s_pstart);
+  }
+  __syncthreads();
+
+  // ---- 1. parents: propagate, window, scan
+  if (t < s_pstart[kSeedsPerBlock]) {
+    const int sd = packed_owner(s_pstart, t);
+    const int k = t - s_pstart[sd];
+    const int64_t j = j0 + sd;
+    const int64_t slot = j * kGroup + k;
+    float p[6], lo[3], C[21];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) p[c] = D.in.par[c * S8 + slot];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) lo[c] = D.in.par[(6 + c) * S8 + slot];
+#pragma unroll
+    for (int c = 0; c < 21; ++c) C[c] = D.in.cov[c * S8 + slot];
+    const float chi2tot = D.in.chi2[slot];
+    const int32_t meta = D.in.meta[slot];
+    const int nh = meta & 0xff;
+    int32_t st = meta >> 8;
+    const int e = D.seed_evt ? D.seed_evt[j] : 0;
+    const float a = Args.a_scale * float(D.charge[D.seed_perm[j]]);
+    const int seg = e * D.n_layers + D.layer;
+    bool stopped = (st & KF_ST_STOPPED) != 0;
+    if (!stopped) {
+      const int r = kf::propagate<float, kNewtonBuild, true>(p, lo, C, a, D.R);
+      if (r) {
+        st |= r;
+        stopped = true;
+      } else if (D.x_x0 > 0.f) {
+        kf::scatter(p, lo, C, D.x_x0, Args.mass);
+      }
+    }
+    uint64_t L[LW];
+    int P[LW];
+#pragma unroll
+    for (int q = 0; q < LW; ++q) {
+      L[q] = kNoKey;
+      P[q] = -1;
+    }
+    bool any = false;
+    if (!stopped) {
+      float Si[6];
+      int e0 = 0, e1 = -1, fa0 = 0, fa1 = KF_BIN_PHI - 1, fb0 = 0, fb1 = -1;
+      hit_window(p, lo, C, D.R, Args, Si, e0, e1, fa0, fa1, fb0, fb1);
+      const int32_t* boff = D.bin_off + int64_t(seg) * (KF_NBINS + 1);
+      const float4* hs = D.hits + D.seg_off[seg];
+      for (int er = e0; er <= e1; ++er) {
+        for (int part = 0; part < 2; ++part) {
+          const int f0 = part == 0 ? fa0 : fb0, f1 = part == 0 ? fa1 : fb1;
+          if (f1 < f0) continue;
+          const int u0 = boff[er * KF_BIN_PHI + f0], u1 = boff[er * KF_BIN_PHI + f1 + 1];
+          for (int u = u0; u < u1; ++u) {
+            const float4 m = hs[u];
+            const float r0 = (m.x - p[0]) - lo[0], r1 = (m.y - p[1]) - lo[1], r2 = (m.z - p[2]) - lo[2];
+            const float c2 = kf::chi2_of(r0, r1, r2, Si);
+            if (c2 < Args.cut) {
+              const int id = __float_as_int(m.w);
+              if (id < KF_MAX_HITS_PER_SEGMENT) {
+                list_insert(L, P, make_key(nh + 1, chi2tot + c2, k, id + 1), u);
+                any = true;
+              }
+            }
+          }
+        }
+      }
+    }
+    // no compatible hit (or a stopped candidate): one child without a hit
+    if (!any) list_insert(L, P, make_key(nh, chi2tot, k, 0), -1);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) s_state[c][t] = p[c];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) s_state[6 + c][t] = lo[c];
+#pragma unroll
+    for (int c = 0; c < 21; ++c) s_state[kParN + c][t] = C[c];
+#pragma unroll
+    for (int q = 0; q < LW; ++q) {
+      s_key[q][t] = L[q];
+      s_pos[q][t] = P[q];
+    }
+    s_pst[t] = st | (stopped ? kStoppedBit : 0);
+  }
+  __syncthreads();
+
+  // ---- 2. clone engine: lane k of seed sd holds the list of its parent k
+  {
+    const int sd = t / kGroup, k = t & (kGroup - 1), gbase = (t & 31) & ~(kGroup - 1);
+    const int64_t j = j0 + sd;
+    const bool seed_ok = j < D.S;
+    uint64_t L[LW];
+    int P[LW];
+    const int pi = s_pstart[sd] + k;
+    if (pi < s_pstart[sd + 1]) {
+#pragma unroll
+      for (int q = 0; q < LW; ++q) {
+        L[q] = s_key[q][pi];
+        P[q] = s_pos[q][pi];
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < LW; ++q) {
+        L[q] = kNoKey;
+        P[q] = -1;
+      }
+    }
+    uint64_t my_key = kNoKey;
+    int my_parent = 0, my_pos = -1, n_win = 0;
+    merge_group(L, P, Args.max_cands, k, gbase, my_key, my_parent, my_pos, n_win);
+    s_ckey[t] = my_key;
+    s_cpos[t] = my_pos;
+    if (k == 0) s_nwin[sd] = seed_ok ? n_win : 0;
+    if (seed_ok && k < n_win) {
+      D.hist_parent[j * kGroup + k] = int8_t(my_parent);
+      D.hist_hit[j * kGroup + k] = int(my_key & 0x1fffffu) - 1;
+    }
+    if (seed_ok && k == 0) D.out.ncand[j] = int8_t(n_win);
+  }
+  __syncthreads();
+  if (t < 32) seed_scan(t < kSeedsPerBlock ? s_nwin[t] : 0, s_cstart);
+  __syncthreads();
+
+  // ---- 3. children: the parent's prediction updated with the child's hit
+  if (t < s_cstart[kSeedsPerBlock]) {
+    const int sd = packed_owner(s_cstart, t);
+    const int r = t - s_cstart[sd];
+    const int64_t j = j0 + sd;
+    const int64_t slot = j * kGroup + r;
+    const uint64_t key = s_ckey[sd * kGroup + r];
+    const int pi = s_pstart[sd] + int((key >> 21) & 7u);
+    float q[6], ql[3], qC[21];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) q[c] = s_state[c][pi];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) ql[c] = s_state[6 + c][pi];
+#pragma unroll
+    for (int c = 0; c < 21; ++c) qC[c] = s_state[kParN + c][pi];
+    const int pw = s_pst[pi];
+    const int nh_new = 255 - int(key >> 56);
+    const float chi2_new = __uint_as_float(uint32_t(key >> 24));
+    const int hit_plus1 = int(key & 0x1fffffu);
+    int32_t st_new = pw & ~kStoppedBit;
+    if (hit_plus1 > 0) {
+      const int e = D.seed_evt ? D.seed_evt[j] : 0;
+      const float4 m = D.hits[D.seg_off[e * D.n_layers + D.layer] + s_cpos[sd * kGroup + r]];
+      float Si[6];
+      kf::inverse_S(qC, Args.v0, Args.v1, Args.v2, Si);
+      float r0, r1, r2;
+      kf::residual<float, true>(q, ql, m.x, m.y, m.z, r0, r1, r2);
+      kf::kalman_update<float, true>(q, ql, qC, Si, r0, r1, r2, Args.v0, Args.v1, Args.v2);
+    } else if (!(pw & kStoppedBit)) {
+      st_new |= KF_ST_NO_HIT;
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) D.out.par[c * S8 + slot] = q[c];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) D.out.par[(6 + c) * S8 + slot] = ql[c];
+#pragma unroll
+    for (int c = 0; c < 21; ++c) D.out.cov[c * S8 + slot] = qC[c];
+    D.out.chi2[slot] = chi2_new;
+    D.out.meta[slot] = nh_new | (st_new << 8);
+  }
 }
 
 __global__ void build_init_kernel(const BuildInitArgs A) {
@@ -601,7 +852,14 @@ static void launch_step_scan(const BuildStepArgs& a, int grid, cudaStream_t st, 
 
 cudaError_t launch_build_step(const BuildStepArgs& a, int grid, cudaStream_t st, int tile, int list, int scan) {
   if (grid <= 0) return cudaSuccess;
-  const bool narrow = list == 4 && a.max_cands <= 4, coop = scan != 0;
+  const bool narrow = list == 4 && a.max_cands <= 4, coop = scan == 1;
+  if (scan == 2) {  // candidate-packed (no hit staging)
+    if (narrow)
+      build_step_packed_kernel<4><<<grid, kBuildThreads, 0, st>>>(a);
+    else
+      build_step_packed_kernel<kGroup><<<grid, kBuildThreads, 0, st>>>(a);
+    return cudaGetLastError();
+  }
   if (tile > 0) {
     if (narrow)
       launch_step_scan<kBuildTile, 4>(a, grid, st, coop);

@@ -124,3 +124,20 @@ def compare(g, r, radius_scale, chi2_frac=CHI2_TOL_FRAC, label=""):
     assert stats["cov_max"] <= COV_TOL, (label, stats)
     assert over <= max(0, int(chi2_frac * cer.size)) and stats["chi2_max"] <= CHI2_TOL_MAX, (label, stats)
     return stats
+
+
+def helix_crossings():
+    """Rows of tests/golden/helix_crossings.txt (closed-form first crossings):
+    dict of arrays q, x0 [n,6], R, status, s, x1 [n,6], cos; and bz."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "helix_crossings.txt")
+    bz = None
+    rows = []
+    for line in open(path):
+        if line.startswith("# bz_tesla"):
+            bz = float(line.split()[2])
+        elif line.strip() and not line.startswith("#"):
+            rows.append([float(v) for v in line.split()])
+    a = np.array(rows)
+    return dict(bz=bz, q=a[:, 0].astype(np.int8), x0=a[:, 1:7], R=a[:, 7], status=a[:, 8].astype(np.int32),
+                s=a[:, 9], x1=a[:, 10:16], cos=a[:, 16])

@@ -62,3 +62,53 @@ def test_layer_without_hits_single_track_and_block_edges(cuda_ctx_factory):
             r = oracle_fit(ev.seeds, ev.hits.xyz, valid, det)
             compare(g, r, det.radii[-1], chi2_frac=1.0 / (10 * n), label=f"n={n} {mode}")
             assert np.all(g["chi2"][5] == -1.0) and np.all(g["status"] & 16)
+
+
+@pytest.mark.parametrize("mode", ["graph", "fused"])
+def test_propagation_equals_closed_form_golden(cuda_ctx_factory, mode):
+    """The kernels' propagate-to-radius against the closed-form crossings of
+    tests/golden/helix_crossings.txt (circle-circle intersection at 40 digits;
+    no hit on the layer, so the fit only propagates): the stated 1e-4 of scale,
+    and the FP32 floor of one step, 1e-6 of scale (R for positions, |p| for
+    momenta); a layer out of reach leaves the state untouched with NOT_REACHED
+    (and no NO_HIT: the stop comes first)."""
+    import torch
+    from paper_1605_05508_gb300 import kf
+    from fitutil import helix_crossings, to_dev
+    g = helix_crossings()
+    worst = 0.0
+    for R in np.unique(g["R"]):
+        rows = np.nonzero(g["R"] == R)[0]
+        n = len(rows)
+        ctx = cuda_ctx_factory([R], bz=g["bz"])
+        x0 = g["x0"][rows].astype(np.float32)
+        assert np.array_equal(x0.astype(np.float64), g["x0"][rows])  # inputs are float32 values
+        cov = np.zeros((21, n), np.float32)
+        p = np.linalg.norm(g["x0"][rows][:, 3:], axis=1)
+        for i, d in enumerate([1e-4, 1e-4, 1e-2]):
+            cov[i * (i + 1) // 2 + i] = d
+        for i in range(3, 6):
+            cov[i * (i + 1) // 2 + i] = (0.01 * p) ** 2
+        s = kf.Tracks(to_dev(x0.T), to_dev(cov), to_dev(g["q"][rows]))
+        out = kf.Tracks(torch.empty((6, n), device="cuda"), torch.empty((21, n), device="cuda"), s.charge,
+                        torch.empty((3, n), device="cuda"))
+        h = kf.TrackHits(torch.zeros((1, 3, n), device="cuda"), torch.zeros((1, n), dtype=torch.uint8, device="cuda"))
+        st = torch.empty(n, dtype=torch.int32, device="cuda")
+        (kf.kf_fit if mode == "graph" else kf.kf_fit_fused)(ctx, s, h, out, None, st)
+        torch.cuda.synchronize()
+        par = out.par.double().cpu().numpy().T
+        par[:, :3] += out.par_lo.double().cpu().numpy().T
+        st = st.cpu().numpy()
+        far = g["status"][rows] == 1
+        # reached: only NO_HIT (the layer has no hit); out of reach: NOT_REACHED
+        # stops the track before the hit is looked at
+        np.testing.assert_array_equal(st[~far], 16, err_msg=f"R={R} status of reached tracks")
+        np.testing.assert_array_equal(st[far] & (7 | 16), 1, err_msg=f"R={R} status of tracks out of reach")
+        np.testing.assert_array_equal(par[far], g["x0"][rows][far])
+        ok = ~far
+        epos = np.abs(par[ok, :3] - g["x1"][rows][ok, :3]).max(initial=0) / R
+        emom = (np.abs(par[ok, 3:] - g["x1"][rows][ok, 3:]) / p[ok, None]).max(initial=0)
+        worst = max(worst, epos, emom)
+        assert epos <= 1e-4 and emom <= 1e-4, (R, epos, emom)
+    print(f"{mode}: max error against the closed form {worst:.2e} of scale")
+    assert worst <= 1e-6, worst

@@ -165,3 +165,23 @@ def test_jacobian_matches_finite_differences(seed):
     # structure: column z0 is e_z, row pz is e_pz
     np.testing.assert_array_equal(J[:, 2], [0, 0, 1, 0, 0, 0])
     np.testing.assert_array_equal(J[5], [0, 0, 0, 0, 0, 1])
+
+
+def test_crossings_equal_closed_form_golden():
+    """The oracle's propagate-to-radius against the closed-form crossings of
+    tests/golden/helix_crossings.txt (circle-circle intersection at 40 digits,
+    written by tests/golden/make_helix_crossings.py without the oracle)."""
+    from fitutil import helix_crossings
+    g = helix_crossings()
+    assert len(g["R"]) >= 150 and np.any(g["status"] == 1) and np.any(g["status"] == 0)
+    for i in range(len(g["R"])):
+        a = float(g["q"][i]) * C_LIGHT * g["bz"]
+        x1, _, s, st = O.propagate(g["x0"][i], a, g["R"][i])
+        if g["status"][i] == 1:
+            assert st & 1, i
+            continue
+        assert st == 0, (i, st)
+        p = np.linalg.norm(g["x0"][i][3:])
+        assert abs(s - g["s"][i]) < 1e-10, (i, s, g["s"][i])
+        assert np.max(np.abs(x1[:3] - g["x1"][i][:3])) < 1e-10, i
+        assert np.max(np.abs(x1[3:] - g["x1"][i][3:])) < 1e-12 * p, i

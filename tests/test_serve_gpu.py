@@ -28,11 +28,15 @@ def _poll_all(kf, ctx, tickets, sizes, timeout_us=60_000_000):
 SIZES = [700, 3100, 150, 5000, 1200, 60, 2300, 900]
 
 
-def test_alone_equals_mix_equals_batch_build(cuda_ctx_factory):
+@pytest.mark.parametrize("layout", [0, 2])
+def test_alone_equals_mix_equals_batch_build(cuda_ctx_factory, layout):
+    """layout: the build step's thread layout in the serving loop (grouped, or
+    candidate-packed); the batch comparison runs the grouped layout."""
     from paper_1605_05508_gb300 import kf
     det = S.barrel()
     ctx = cuda_ctx_factory(det.radii)
     evs = [_event(100 + i, n) for i, n in enumerate(SIZES)]
+    kf.kf_set_tuning(ctx, 128, 0, 8, layout)
     kf.kf_serve_start(ctx, 3, 7, 6, max_slots=32, device_arena_bytes=1 << 30, host_arena_bytes=1 << 29)
     alone = []
     for (b, ev), n in zip(evs, SIZES):
@@ -48,6 +52,7 @@ def test_alone_equals_mix_equals_batch_build(cuda_ctx_factory):
         for k in ("best_par", "chi2_tot", "n_hits", "status", "hit_idx"):
             np.testing.assert_array_equal(a[k], m[k], err_msg=k)
     # the batch API on the same events gives the same bits
+    kf.kf_set_tuning(ctx, 128, 0, 8, 0)
     for (b, _), a in zip(evs, alone):
         g = gpu_build(ctx, b, 6, want_cands=False)
         np.testing.assert_array_equal(g["hits"].T, a["hit_idx"])
