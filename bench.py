@@ -488,11 +488,12 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist):
         times = {}
         for tile in (0, 512):
             for lw in (8, 4):
-                for scan in (0, 1, 2):
-                    if (lw == 4 and N > 4) or (scan == 2 and tile > 0):
+                for scan in (0, 1, 2, 3):
+                    if (lw == 4 and N > 4) or (scan >= 2 and tile > 0):
                         continue
                     kf.kf_set_tuning(ctx, 128, tile, lw, scan)
-                    times[f"tile{tile}_list{lw}_{('lane', 'coop', 'packed')[scan]}"] = float(run(N, 5)[1][2])
+                    name = ("lane", "coop", "packed128", "packed64")[scan]
+                    times[f"tile{tile}_list{lw}_{name}"] = float(run(N, 5)[1][2])
         return times, kf.kf_autotune_build(ctx, fo, seed_off, bins, N, out, stream)
 
     k = max(5, min(50, a.steps // 4))

@@ -284,7 +284,8 @@ typedef struct {
                                  seed scanning each parent's window together (balanced when few
                                  candidates), 2 = the live candidates packed onto consecutive
                                  threads for the propagation and scan, and the kept children
-                                 for the update (requires build_hit_tile 0) */
+                                 for the update, 128 seeds per block; 3 = the same with 64
+                                 seeds per block (2 and 3 require build_hit_tile 0) */
     int32_t fit_chunk;        /* kf_fit: 0 = each layer step is one launch over the whole batch
                                  (default); 262144, 524288 or 1048576 = the batch is fitted in
                                  chunks of that many tracks, all layers of a chunk before the
@@ -310,8 +311,8 @@ int kf_autotune_fit(kf_ctx *ctx, const kf_tracks *seeds, const kf_track_hits *hi
                     float *chi2, int32_t *status, void *stream, kf_tuning *chosen);
 
 /* Autotuner of kf_build: the same over build_hit_tile x build_list_width x
- * build_scan (list width 4 is tried only when max_cands <= 4, layout 2 only
- * without hit staging).  Errors: those of kf_build. */
+ * build_scan (list width 4 is tried only when max_cands <= 4, layouts 2 and 3
+ * only without hit staging).  Errors: those of kf_build. */
 int kf_autotune_build(kf_ctx *ctx, const kf_tracks *seeds, const int64_t *seed_off,
                       const kf_layer_hit_bins *bins, int32_t max_cands, kf_build_result *out, void *stream,
                       kf_tuning *chosen);

@@ -515,61 +515,76 @@ __global__ void __launch_bounds__(kBuildThreads, 5) build_step_kernel(const Buil
 // ---- candidate-packed step (scan scheme 2)
 //
 // The same computation as build_step_kernel, with threads assigned to live
-// candidates instead of fixed 8-lane seed groups.  A block serves the same 16
-// seeds (same grid and slot table), in three phases separated by block
+// candidates instead of fixed 8-lane seed groups.  A block serves 128 seeds
+// (kPackSeeds; scheme 3: 64) in rounds; a round takes the next seeds whose
+// parents fit the block's threads and runs three phases separated by block
 // barriers:
-//   1. the block's live parents are packed onto its first threads; each
-//      propagates its candidate, derives its window, scans it (global memory)
-//      and leaves its prediction and sorted child list in shared memory --
-//      warps past the last parent skip the phase;
-//   2. the 8 lanes of seed s load the lists of its parents and merge them as
-//      in the grouped step (merge_group);
-//   3. the kept children are packed the same way; each is updated with its
-//      hit from its parent's prediction in shared memory and stored.
-// In the early building layers a seed holds one or two candidates, so the
-// grouped layout leaves most lanes of a warp idle through the propagation
-// and the update; packed, those phases take as many warps as there are
-// candidates (rounded up to 32).  Every candidate and child goes through the
-// same functions as in the grouped step, so the results are bitwise equal.
-constexpr int kSeedsPerBlock = kBuildThreads / kGroup;  // 16
-constexpr int kStateWords = kParN + 21;                 // x y z px py pz, lo x y z, covariance
-constexpr int kStoppedBit = 1 << 30;                    // parent stopped (status word in shared memory)
+//   1. the round's parents, packed onto consecutive threads, each propagate
+//      their candidate, derive the window, scan it (global memory) and leave
+//      the prediction and the sorted child list in shared memory;
+//   2. one thread per seed merges its parents' lists into the best max_cands
+//      keys -- the same selection as merge_group: the keys are a total order;
+//   3. the kept children, packed the same way, are each updated with their hit
+//      from the parent's prediction in shared memory and stored.
+// In the early building layers a seed holds one or two candidates, where the
+// grouped layout leaves most lanes of a warp idle through the propagation,
+// the scan and the update; packed, every phase keeps the warps full.  Each
+// candidate and child goes through the same functions as in the grouped
+// step, so the results are bitwise equal.
+constexpr int kStateWords = kParN + 21;  // x y z px py pz, lo x y z, covariance
+constexpr int kStoppedBit = 1 << 30;     // parent stopped (status word in shared memory)
 
-// Exclusive scan of one count per seed (lanes 0..15 of warp 0; all 32 lanes
-// call): start[0] = 0, start[s + 1] = start[s] + count of seed s.
-__device__ __forceinline__ void seed_scan(int count, int* start) {
-  const int lane = threadIdx.x & 31;
-  int x = lane < kSeedsPerBlock ? count : 0;
+// Exclusive scan over the block's threads: start[0] = 0, start[t + 1] =
+// start[t] + v of thread t.  All threads call; ends with a barrier.
+template <int NT>
+__device__ __forceinline__ void block_scan(int v, int* start, int* warp_sum) {
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  int x = v;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
     const int y = __shfl_up_sync(kFull, x, d);
     if (lane >= d) x += y;
   }
-  if (lane < kSeedsPerBlock) start[lane + 1] = x;
-  if (lane == 0) start[0] = 0;
-}
-
-// The seed whose packed items hold position t: start[s] <= t < start[s + 1]
-// (requires t < start[kSeedsPerBlock]).
-__device__ __forceinline__ int packed_owner(const int* start, int t) {
-  int s = 0;
+  if (lane == 31) warp_sum[w] = x;
+  __syncthreads();
 #pragma unroll
-  for (int b = kSeedsPerBlock / 2; b >= 1; b >>= 1)
-    if (start[s + b] <= t) s += b;
-  return s;
+  for (int q = 0; q < NT / 32; ++q)
+    if (q < w) x += warp_sum[q];
+  start[t + 1] = x;
+  if (t == 0) start[0] = 0;
+  __syncthreads();
 }
 
-template <int LW>
-__global__ void __launch_bounds__(kBuildThreads, 5) build_step_packed_kernel(const BuildStepArgs Args) {
+// The largest s in [lo, hi] with start[s] <= v.
+__device__ __forceinline__ int packed_owner(const int* start, int lo, int hi, int v) {
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (start[mid] <= v)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// NT threads per block, one seed per thread: 128 (5 blocks per SM) or 64 (10
+// blocks per SM: a block barrier holds two warps, not four); 20 warps per SM
+// either way, at most 96 registers.
+template <int LW, int NT>
+__global__ void __launch_bounds__(NT, 5 * kBuildThreads / NT) build_step_packed_kernel(const BuildStepArgs Args) {
   __shared__ BuildSlot sD;
-  __shared__ float s_state[kStateWords][kBuildThreads];  // parent predictions
-  __shared__ uint64_t s_key[LW][kBuildThreads];          // parent child lists
-  __shared__ int s_pos[LW][kBuildThreads];
-  __shared__ int s_pst[kBuildThreads];        // parent status | kStoppedBit
-  __shared__ uint64_t s_ckey[kBuildThreads];  // kept child of rank r of seed s at s * kGroup + r
-  __shared__ int s_cpos[kBuildThreads];
-  __shared__ int s_nwin[kSeedsPerBlock];
-  __shared__ int s_pstart[kSeedsPerBlock + 1], s_cstart[kSeedsPerBlock + 1];
+  __shared__ float s_state[kStateWords][NT];  // the round's parent predictions
+  __shared__ uint64_t s_key[LW][NT];          // and their sorted child lists
+  __shared__ int s_pos[LW][NT];
+  __shared__ int s_pst[NT];         // parent status | kStoppedBit
+  __shared__ uint64_t s_ckey[NT][LW];  // kept children of the round's seeds, by rank
+  __shared__ int s_cpos[NT][LW];
+  __shared__ int s_pstart[NT + 1];  // parents of the block's seeds (exclusive scan)
+  __shared__ int s_cstart[NT + 1];  // kept children of the round's seeds (exclusive scan)
+  __shared__ int s_wsum[NT / 32];
+  __shared__ float s_a[NT];      // per seed: a = c Bz q
+  __shared__ int s_seg[NT];      // per seed: hit segment (event, layer)
+  __shared__ int64_t s_h0[NT];   // per seed: first hit of the segment
   const int t = threadIdx.x;
   if (t == 0) {
     int sl = 0;
@@ -579,64 +594,94 @@ __global__ void __launch_bounds__(kBuildThreads, 5) build_step_packed_kernel(con
   __syncthreads();
   const BuildSlot& D = sD;
   const int64_t S8 = D.S * kGroup;
-  const int64_t j0 = int64_t(blockIdx.x - D.block_begin) * kSeedsPerBlock;
-  if (t < 32) {
-    const bool ok = t < kSeedsPerBlock && j0 + t < D.S;
-    seed_scan(ok ? int(D.in.ncand[j0 + t]) : 0, s_pstart);
+  const int64_t j0 = int64_t(blockIdx.x - D.block_begin) * NT;
+  const int ns = int(D.S - j0 < NT ? D.S - j0 : NT);
+  if (t < ns) {  // per-seed constants, read once (visible after the scan's barriers)
+    const int64_t j = j0 + t;
+    const int seg = (D.seed_evt ? D.seed_evt[j] : 0) * D.n_layers + D.layer;
+    s_seg[t] = seg;
+    s_h0[t] = D.seg_off[seg];
+    s_a[t] = Args.a_scale * float(D.charge[D.seed_perm[j]]);
   }
-  __syncthreads();
+  block_scan<NT>(t < ns ? int(D.in.ncand[j0 + t]) : 0, s_pstart, s_wsum);
 
-  // ---- 1. parents: propagate, window, scan
-  if (t < s_pstart[kSeedsPerBlock]) {
-    const int sd = packed_owner(s_pstart, t);
-    const int k = t - s_pstart[sd];
-    const int64_t j = j0 + sd;
-    const int64_t slot = j * kGroup + k;
-    float p[6], lo[3], C[21];
+  for (int sa = 0; sa < ns;) {  // uniform over the block
+    // the round: seeds [sa, sb), parents s_pstart[sa] .. s_pstart[sb] - 1
+    const int base = s_pstart[sa];
+    const int sb = packed_owner(s_pstart, sa + 1, ns, base + NT);
+    const int npar = s_pstart[sb] - base;
+
+    // ---- 1. parents: propagate, window, scan
+    if (t < npar) {
+      const int sd = packed_owner(s_pstart, sa, sb - 1, base + t);
+      const int k = base + t - s_pstart[sd];
+      const int64_t j = j0 + sd;
+      const int64_t slot = j * kGroup + k;
+      float p[6], lo[3], C[21];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) p[c] = D.in.par[c * S8 + slot];
+      for (int c = 0; c < 6; ++c) p[c] = D.in.par[c * S8 + slot];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) lo[c] = D.in.par[(6 + c) * S8 + slot];
+      for (int c = 0; c < 3; ++c) lo[c] = D.in.par[(6 + c) * S8 + slot];
 #pragma unroll
-    for (int c = 0; c < 21; ++c) C[c] = D.in.cov[c * S8 + slot];
-    const float chi2tot = D.in.chi2[slot];
-    const int32_t meta = D.in.meta[slot];
-    const int nh = meta & 0xff;
-    int32_t st = meta >> 8;
-    const int e = D.seed_evt ? D.seed_evt[j] : 0;
-    const float a = Args.a_scale * float(D.charge[D.seed_perm[j]]);
-    const int seg = e * D.n_layers + D.layer;
-    bool stopped = (st & KF_ST_STOPPED) != 0;
-    if (!stopped) {
-      const int r = kf::propagate<float, kNewtonBuild, true>(p, lo, C, a, D.R);
-      if (r) {
-        st |= r;
-        stopped = true;
-      } else if (D.x_x0 > 0.f) {
-        kf::scatter(p, lo, C, D.x_x0, Args.mass);
+      for (int c = 0; c < 21; ++c) C[c] = D.in.cov[c * S8 + slot];
+      const float chi2tot = D.in.chi2[slot];
+      const int32_t meta = D.in.meta[slot];
+      const int nh = meta & 0xff;
+      int32_t st = meta >> 8;
+      bool stopped = (st & KF_ST_STOPPED) != 0;
+      if (!stopped) {
+        const int r = kf::propagate<float, kNewtonBuild, true>(p, lo, C, s_a[sd], D.R);
+        if (r) {
+          st |= r;
+          stopped = true;
+        } else if (D.x_x0 > 0.f) {
+          kf::scatter(p, lo, C, D.x_x0, Args.mass);
+        }
       }
-    }
-    uint64_t L[LW];
-    int P[LW];
+      uint64_t L[LW];
+      int P[LW];
 #pragma unroll
-    for (int q = 0; q < LW; ++q) {
-      L[q] = kNoKey;
-      P[q] = -1;
-    }
-    bool any = false;
-    if (!stopped) {
-      float Si[6];
-      int e0 = 0, e1 = -1, fa0 = 0, fa1 = KF_BIN_PHI - 1, fb0 = 0, fb1 = -1;
-      hit_window(p, lo, C, D.R, Args, Si, e0, e1, fa0, fa1, fb0, fb1);
-      const int32_t* boff = D.bin_off + int64_t(seg) * (KF_NBINS + 1);
-      const float4* hs = D.hits + D.seg_off[seg];
-      for (int er = e0; er <= e1; ++er) {
-        for (int part = 0; part < 2; ++part) {
-          const int f0 = part == 0 ? fa0 : fb0, f1 = part == 0 ? fa1 : fb1;
-          if (f1 < f0) continue;
-          const int u0 = boff[er * KF_BIN_PHI + f0], u1 = boff[er * KF_BIN_PHI + f1 + 1];
-          for (int u = u0; u < u1; ++u) {
-            const float4 m = hs[u];
+      for (int q = 0; q < LW; ++q) {
+        L[q] = kNoKey;
+        P[q] = -1;
+      }
+      bool any = false;
+      if (!stopped) {
+        float Si[6];
+        int e0 = 0, e1 = -1, fa0 = 0, fa1 = KF_BIN_PHI - 1, fb0 = 0, fb1 = -1;
+        hit_window(p, lo, C, D.R, Args, Si, e0, e1, fa0, fa1, fb0, fb1);
+        const int32_t* boff = D.bin_off + int64_t(s_seg[sd]) * (KF_NBINS + 1);
+        const float4* hs = D.hits + s_h0[sd];
+        // rows e0..e1, each the hits of bins fa0..fa1 then fb0..fb1: the next
+        // row's bin offsets and the next hit are loaded one step ahead
+        const bool two = fb1 >= fb0;
+        int na0 = 0, na1 = 0, nb0 = 0, nb1 = 0;
+        if (e0 <= e1) {
+          const int32_t* q = boff + e0 * KF_BIN_PHI;
+          na0 = q[fa0];
+          na1 = q[fa1 + 1];
+          if (two) {
+            nb0 = q[fb0];
+            nb1 = q[fb1 + 1];
+          }
+        }
+        for (int er = e0; er <= e1; ++er) {
+          const int a0 = na0, na = na1 - na0, b0 = nb0, n = na + (nb1 - nb0);
+          if (er < e1) {
+            const int32_t* q = boff + (er + 1) * KF_BIN_PHI;
+            na0 = q[fa0];
+            na1 = q[fa1 + 1];
+            if (two) {
+              nb0 = q[fb0];
+              nb1 = q[fb1 + 1];
+            }
+          }
+          float4 mn = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (n > 0) mn = hs[na > 0 ? a0 : b0];
+          for (int v = 0; v < n; ++v) {
+            const int u = v < na ? a0 + v : b0 + (v - na);
+            const float4 m = mn;
+            if (v + 1 < n) mn = hs[v + 1 < na ? a0 + v + 1 : b0 + (v + 1 - na)];
             const float r0 = (m.x - p[0]) - lo[0], r1 = (m.y - p[1]) - lo[1], r2 = (m.z - p[2]) - lo[2];
             const float c2 = kf::chi2_of(r0, r1, r2, Si);
             if (c2 < Args.cut) {
@@ -649,100 +694,100 @@ __global__ void __launch_bounds__(kBuildThreads, 5) build_step_packed_kernel(con
           }
         }
       }
-    }
-    // no compatible hit (or a stopped candidate): one child without a hit
-    if (!any) list_insert(L, P, make_key(nh, chi2tot, k, 0), -1);
+      // no compatible hit (or a stopped candidate): one child without a hit
+      if (!any) list_insert(L, P, make_key(nh, chi2tot, k, 0), -1);
 #pragma unroll
-    for (int c = 0; c < 6; ++c) s_state[c][t] = p[c];
+      for (int c = 0; c < 6; ++c) s_state[c][t] = p[c];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) s_state[6 + c][t] = lo[c];
+      for (int c = 0; c < 3; ++c) s_state[6 + c][t] = lo[c];
 #pragma unroll
-    for (int c = 0; c < 21; ++c) s_state[kParN + c][t] = C[c];
-#pragma unroll
-    for (int q = 0; q < LW; ++q) {
-      s_key[q][t] = L[q];
-      s_pos[q][t] = P[q];
-    }
-    s_pst[t] = st | (stopped ? kStoppedBit : 0);
-  }
-  __syncthreads();
-
-  // ---- 2. clone engine: lane k of seed sd holds the list of its parent k
-  {
-    const int sd = t / kGroup, k = t & (kGroup - 1), gbase = (t & 31) & ~(kGroup - 1);
-    const int64_t j = j0 + sd;
-    const bool seed_ok = j < D.S;
-    uint64_t L[LW];
-    int P[LW];
-    const int pi = s_pstart[sd] + k;
-    if (pi < s_pstart[sd + 1]) {
+      for (int c = 0; c < 21; ++c) s_state[kParN + c][t] = C[c];
 #pragma unroll
       for (int q = 0; q < LW; ++q) {
-        L[q] = s_key[q][pi];
-        P[q] = s_pos[q][pi];
+        s_key[q][t] = L[q];
+        s_pos[q][t] = P[q];
       }
-    } else {
-#pragma unroll
-      for (int q = 0; q < LW; ++q) {
-        L[q] = kNoKey;
-        P[q] = -1;
-      }
+      s_pst[t] = st | (stopped ? kStoppedBit : 0);
     }
-    uint64_t my_key = kNoKey;
-    int my_parent = 0, my_pos = -1, n_win = 0;
-    merge_group(L, P, Args.max_cands, k, gbase, my_key, my_parent, my_pos, n_win);
-    s_ckey[t] = my_key;
-    s_cpos[t] = my_pos;
-    if (k == 0) s_nwin[sd] = seed_ok ? n_win : 0;
-    if (seed_ok && k < n_win) {
-      D.hist_parent[j * kGroup + k] = int8_t(my_parent);
-      D.hist_hit[j * kGroup + k] = int(my_key & 0x1fffffu) - 1;
-    }
-    if (seed_ok && k == 0) D.out.ncand[j] = int8_t(n_win);
-  }
-  __syncthreads();
-  if (t < 32) seed_scan(t < kSeedsPerBlock ? s_nwin[t] : 0, s_cstart);
-  __syncthreads();
+    __syncthreads();
 
-  // ---- 3. children: the parent's prediction updated with the child's hit
-  if (t < s_cstart[kSeedsPerBlock]) {
-    const int sd = packed_owner(s_cstart, t);
-    const int r = t - s_cstart[sd];
-    const int64_t j = j0 + sd;
-    const int64_t slot = j * kGroup + r;
-    const uint64_t key = s_ckey[sd * kGroup + r];
-    const int pi = s_pstart[sd] + int((key >> 21) & 7u);
-    float q[6], ql[3], qC[21];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) q[c] = s_state[c][pi];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) ql[c] = s_state[6 + c][pi];
-#pragma unroll
-    for (int c = 0; c < 21; ++c) qC[c] = s_state[kParN + c][pi];
-    const int pw = s_pst[pi];
-    const int nh_new = 255 - int(key >> 56);
-    const float chi2_new = __uint_as_float(uint32_t(key >> 24));
-    const int hit_plus1 = int(key & 0x1fffffu);
-    int32_t st_new = pw & ~kStoppedBit;
-    if (hit_plus1 > 0) {
-      const int e = D.seed_evt ? D.seed_evt[j] : 0;
-      const float4 m = D.hits[D.seg_off[e * D.n_layers + D.layer] + s_cpos[sd * kGroup + r]];
-      float Si[6];
-      kf::inverse_S(qC, Args.v0, Args.v1, Args.v2, Si);
-      float r0, r1, r2;
-      kf::residual<float, true>(q, ql, m.x, m.y, m.z, r0, r1, r2);
-      kf::kalman_update<float, true>(q, ql, qC, Si, r0, r1, r2, Args.v0, Args.v1, Args.v2);
-    } else if (!(pw & kStoppedBit)) {
-      st_new |= KF_ST_NO_HIT;
+    // ---- 2. clone engine: one thread per seed of the round merges the
+    // sorted lists of its parents (heads packed 4 bits per parent)
+    int n_win = 0;
+    const int nr = sb - sa;
+    if (t < nr) {
+      const int sd = sa + t;
+      const int64_t j = j0 + sd;
+      const int p0 = s_pstart[sd] - base, nc = s_pstart[sd + 1] - s_pstart[sd];
+      uint32_t heads = 0;
+      for (int r = 0; r < Args.max_cands; ++r) {
+        uint64_t best = kNoKey;
+        int bk = 0;
+        for (int k = 0; k < nc; ++k) {
+          const int h = int((heads >> (4 * k)) & 15u);
+          if (h < LW) {
+            const uint64_t key = s_key[h][p0 + k];
+            if (key < best) {
+              best = key;
+              bk = k;
+            }
+          }
+        }
+        if (best == kNoKey) break;
+        const int bh = int((heads >> (4 * bk)) & 15u);
+        s_ckey[t][r] = best;
+        s_cpos[t][r] = s_pos[bh][p0 + bk];
+        heads += 1u << (4 * bk);
+        D.hist_parent[j * kGroup + r] = int8_t((best >> 21) & 7u);
+        D.hist_hit[j * kGroup + r] = int(best & 0x1fffffu) - 1;
+        ++n_win;
+      }
+      D.out.ncand[j] = int8_t(n_win);
     }
+    block_scan<NT>(n_win, s_cstart, s_wsum);
+
+    // ---- 3. children: the parent's prediction updated with the child's hit
+    const int nch = s_cstart[nr];
+    for (int c = t; c < nch; c += NT) {
+      const int sl = packed_owner(s_cstart, 0, nr - 1, c);
+      const int r = c - s_cstart[sl];
+      const int64_t j = j0 + sa + sl;
+      const int64_t slot = j * kGroup + r;
+      const uint64_t key = s_ckey[sl][r];
+      const int pi = s_pstart[sa + sl] - base + int((key >> 21) & 7u);
+      float q[6], ql[3], qC[21];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) D.out.par[c * S8 + slot] = q[c];
+      for (int w = 0; w < 6; ++w) q[w] = s_state[w][pi];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) D.out.par[(6 + c) * S8 + slot] = ql[c];
+      for (int w = 0; w < 3; ++w) ql[w] = s_state[6 + w][pi];
 #pragma unroll
-    for (int c = 0; c < 21; ++c) D.out.cov[c * S8 + slot] = qC[c];
-    D.out.chi2[slot] = chi2_new;
-    D.out.meta[slot] = nh_new | (st_new << 8);
+      for (int w = 0; w < 21; ++w) qC[w] = s_state[kParN + w][pi];
+      const int pw = s_pst[pi];
+      const int nh_new = 255 - int(key >> 56);
+      const float chi2_new = __uint_as_float(uint32_t(key >> 24));
+      const int hit_plus1 = int(key & 0x1fffffu);
+      int32_t st_new = pw & ~kStoppedBit;
+      if (hit_plus1 > 0) {
+        const float4 m = D.hits[s_h0[sa + sl] + s_cpos[sl][r]];
+        float Si[6];
+        kf::inverse_S(qC, Args.v0, Args.v1, Args.v2, Si);
+        float r0, r1, r2;
+        kf::residual<float, true>(q, ql, m.x, m.y, m.z, r0, r1, r2);
+        kf::kalman_update<float, true>(q, ql, qC, Si, r0, r1, r2, Args.v0, Args.v1, Args.v2);
+      } else if (!(pw & kStoppedBit)) {
+        st_new |= KF_ST_NO_HIT;
+      }
+#pragma unroll
+      for (int w = 0; w < 6; ++w) D.out.par[w * S8 + slot] = q[w];
+#pragma unroll
+      for (int w = 0; w < 3; ++w) D.out.par[(6 + w) * S8 + slot] = ql[w];
+#pragma unroll
+      for (int w = 0; w < 21; ++w) D.out.cov[w * S8 + slot] = qC[w];
+      D.out.chi2[slot] = chi2_new;
+      D.out.meta[slot] = nh_new | (st_new << 8);
+    }
+    __syncthreads();  // the next round reuses the shared tables
+    sa = sb;
   }
 }
 
@@ -853,11 +898,15 @@ static void launch_step_scan(const BuildStepArgs& a, int grid, cudaStream_t st, 
 cudaError_t launch_build_step(const BuildStepArgs& a, int grid, cudaStream_t st, int tile, int list, int scan) {
   if (grid <= 0) return cudaSuccess;
   const bool narrow = list == 4 && a.max_cands <= 4, coop = scan == 1;
-  if (scan == 2) {  // candidate-packed (no hit staging)
-    if (narrow)
-      build_step_packed_kernel<4><<<grid, kBuildThreads, 0, st>>>(a);
+  if (scan >= 2) {  // candidate-packed (no hit staging)
+    if (scan == 2 && narrow)
+      build_step_packed_kernel<4, kPackSeeds><<<grid, kPackSeeds, 0, st>>>(a);
+    else if (scan == 2)
+      build_step_packed_kernel<kGroup, kPackSeeds><<<grid, kPackSeeds, 0, st>>>(a);
+    else if (narrow)
+      build_step_packed_kernel<4, kPackSeeds / 2><<<grid, kPackSeeds / 2, 0, st>>>(a);
     else
-      build_step_packed_kernel<kGroup><<<grid, kBuildThreads, 0, st>>>(a);
+      build_step_packed_kernel<kGroup, kPackSeeds / 2><<<grid, kPackSeeds / 2, 0, st>>>(a);
     return cudaGetLastError();
   }
   if (tile > 0) {
@@ -963,7 +1012,7 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
   }
   const float v0 = ctx->cfg.sigma_xy_cm * ctx->cfg.sigma_xy_cm;
   const float v2 = ctx->cfg.sigma_z_cm * ctx->cfg.sigma_z_cm;
-  const int grid = int((S8 + kBuildThreads - 1) / kBuildThreads);
+  const int grid = build_step_blocks(S, ctx->tune.build_scan);
   // one slot (the whole batch) per layer launch; the table goes to device
   // scratch in one copy (the host array is consumed before the call returns)
   std::vector<BuildSlot> table(L);

@@ -14,6 +14,7 @@ constexpr int kGroup = 8;           // lanes (candidate slots) per seed
 constexpr int kBuildThreads = 128;  // 16 seeds per block
 constexpr int kNewtonBuild = 12;
 constexpr int kBuildTile = 512;     // hits staged per warp when hit staging is on
+constexpr int kPackSeeds = 128;     // seeds per block of the candidate-packed step (scan scheme 2)
 constexpr int kParN = 9;  // x y z px py pz + low parts of x y z
 constexpr uint64_t kNoKey = ~0ull;
 constexpr unsigned kFull = 0xffffffffu;
@@ -89,9 +90,17 @@ inline CandBuf cand_at(char* q, int64_t S) {
 
 // tile: 0 (scan global memory) or kBuildTile (stage the window hits per
 // warp); list: 4 (lane lists of 4 children, when max_cands <= 4) or 8;
-// scan: 0 (each lane scans its own candidate's window) or 1 (the seed's
-// lanes scan each parent's window together)
+// scan: 0 (each lane scans its own candidate's window), 1 (the seed's
+// lanes scan each parent's window together), 2 or 3 (candidate-packed, 128 or
+// 64 seeds per block: grid of build_step_blocks(S, scan); tile is ignored)
 cudaError_t launch_build_step(const BuildStepArgs& a, int grid, cudaStream_t st, int tile, int list, int scan);
+// Blocks of the build step for S seeds: 8 lanes per seed, 16 seeds per block,
+// or one seed per thread in the candidate-packed layouts (scan 2: kPackSeeds
+// per block, scan 3: half as many).
+inline int build_step_blocks(int64_t S, int scan) {
+  const int per_block = scan == 2 ? kPackSeeds : scan == 3 ? kPackSeeds / 2 : kBuildThreads / kGroup;
+  return int((S + per_block - 1) / per_block);
+}
 cudaError_t launch_build_init(const BuildInitArgs& a, cudaStream_t st);
 cudaError_t launch_build_final(const BuildFinalArgs& a, cudaStream_t st);
 

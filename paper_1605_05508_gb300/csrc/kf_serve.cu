@@ -602,7 +602,7 @@ static void scheduler(Serve* sv) {
       for (size_t i = 0; i < stepping.size(); ++i) {
         ht[i] = slot_of(sv, stepping[i]);
         ht[i].block_begin = blocks;
-        blocks += int((ht[i].S * kGroup + kBuildThreads - 1) / kBuildThreads);
+        blocks += build_step_blocks(ht[i].S, sv->tune.build_scan);
       }
       BuildSlot* dt = sv->d_table + size_t(ring) * KF_MAX_SLOTS;
       e = cudaMemcpyAsync(dt, ht, sizeof(BuildSlot) * stepping.size(), cudaMemcpyHostToDevice, sv->stream);
