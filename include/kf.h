@@ -339,6 +339,12 @@ typedef struct {
                                    kf_refit) inside the same request; 0: build only */
     size_t device_arena_bytes;  /* device memory for resident events (0: 1 GiB) */
     size_t host_arena_bytes;    /* pinned host memory for queued inputs and results (0: 1 GiB) */
+    int64_t pack_min_seeds;     /* with a candidate-packed build_scan (2, 3) in the context's
+                                   tuning: a step launch uses it only when the resident events
+                                   being stepped hold at least this many seeds, else the grouped
+                                   per-lane layout (same results; the packed blocks of a small
+                                   step would not fill the GPU).  0: automatic (SMs x 640),
+                                   1: always packed.  >= 0 */
 } kf_serve_config;
 
 /* One event (host memory; copied by kf_submit, reusable when it returns). */

@@ -173,7 +173,7 @@ __device__ __forceinline__ void merge_group(uint64_t (&L)[LW], int (&P)[LW], int
 // resident warps hide the dependent loads of the window scans better than
 // the spills they cost (measured: 3.43 vs 3.78 ms per 7-layer build at N = 6).
 template <int TILE, int LW, bool COOP>
-__global__ void __launch_bounds__(kBuildThreads, 5) build_step_kernel(const BuildStepArgs Args) {
+__global__ void __launch_bounds__(kBuildThreads, kBuildBlocksPerSM) build_step_kernel(const BuildStepArgs Args) {
   extern __shared__ float4 s_hits_all[];
   __shared__ BuildSlot sD;
   __shared__ int32_t s_off_all[TILE > 0 ? kWarps : 1][TILE > 0 ? kStageOffs : 1];
@@ -571,7 +571,7 @@ __device__ __forceinline__ int packed_owner(const int* start, int lo, int hi, in
 // blocks per SM: a block barrier holds two warps, not four); 20 warps per SM
 // either way, at most 96 registers.
 template <int LW, int NT>
-__global__ void __launch_bounds__(NT, 5 * kBuildThreads / NT) build_step_packed_kernel(const BuildStepArgs Args) {
+__global__ void __launch_bounds__(NT, kBuildBlocksPerSM * kBuildThreads / NT) build_step_packed_kernel(const BuildStepArgs Args) {
   __shared__ BuildSlot sD;
   __shared__ float s_state[kStateWords][NT];  // the round's parent predictions
   __shared__ uint64_t s_key[LW][NT];          // and their sorted child lists

@@ -12,6 +12,7 @@ namespace kfi {
 
 constexpr int kGroup = 8;           // lanes (candidate slots) per seed
 constexpr int kBuildThreads = 128;  // 16 seeds per block
+constexpr int kBuildBlocksPerSM = 5;  // resident blocks of kBuildThreads (96 registers a thread)
 constexpr int kNewtonBuild = 12;
 constexpr int kBuildTile = 512;     // hits staged per warp when hit staging is on
 constexpr int kPackSeeds = 128;     // seeds per block of the candidate-packed step (scan scheme 2)

@@ -598,11 +598,24 @@ static void scheduler(Serve* sv) {
     }
     if (e == cudaSuccess && !stepping.empty()) {
       BuildSlot* ht = sv->h_table + size_t(ring) * KF_MAX_SLOTS;
-      int blocks = 0;
+      int64_t seeds = 0;
       for (size_t i = 0; i < stepping.size(); ++i) {
         ht[i] = slot_of(sv, stepping[i]);
+        seeds += ht[i].S;
+      }
+      // A packed step whose blocks do not fill the GPU once (by default fewer
+      // seeds than SMs x resident blocks x 128) runs its rounds on too few
+      // SMs: the grouped layout, with 8 lanes per seed and 8x the blocks,
+      // ends such a small step sooner (the same bits either way).
+      int scan = sv->tune.build_scan;
+      const int64_t pack_min = sv->cfg.pack_min_seeds > 0
+                                   ? sv->cfg.pack_min_seeds
+                                   : int64_t(sv->ctx->num_sms) * kBuildBlocksPerSM * kBuildThreads;
+      if (scan >= 2 && seeds < pack_min) scan = 0;
+      int blocks = 0;
+      for (size_t i = 0; i < stepping.size(); ++i) {
         ht[i].block_begin = blocks;
-        blocks += build_step_blocks(ht[i].S, sv->tune.build_scan);
+        blocks += build_step_blocks(ht[i].S, scan);
       }
       BuildSlot* dt = sv->d_table + size_t(ring) * KF_MAX_SLOTS;
       e = cudaMemcpyAsync(dt, ht, sizeof(BuildSlot) * stepping.size(), cudaMemcpyHostToDevice, sv->stream);
@@ -616,8 +629,7 @@ static void scheduler(Serve* sv) {
       a.cut = sv->ctx->cfg.chi2_cut;
       a.mass = sv->ctx->mass;
       if (e == cudaSuccess)
-        e = launch_build_step(a, blocks, sv->stream, sv->tune.build_hit_tile, sv->tune.build_list_width,
-                              sv->tune.build_scan);
+        e = launch_build_step(a, blocks, sv->stream, sv->tune.build_hit_tile, sv->tune.build_list_width, scan);
       for (Request* r : stepping) r->layer++;
       std::lock_guard<std::mutex> lk(sv->mu);
       sv->stats.step_launches++;
@@ -690,7 +702,7 @@ int kf_serve_start(kf_ctx* ctx, const kf_serve_config* cfg) {
       cfg->n_seed_layers + cfg->n_build_layers > ctx->cfg.n_layers || cfg->n_seed_layers > kMaxLayers)
     return KF_EINVAL;
   if (cfg->max_cands < 1 || cfg->max_cands > kGroup || cfg->max_slots < 1 || cfg->max_slots > KF_MAX_SLOTS ||
-      cfg->max_queue < 1 || (cfg->refit != 0 && cfg->refit != 1))
+      cfg->max_queue < 1 || (cfg->refit != 0 && cfg->refit != 1) || cfg->pack_min_seeds < 0)
     return KF_EINVAL;
   KF_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   auto* sv = new (std::nothrow) Serve();

@@ -69,7 +69,8 @@ class kf_build_result(C.Structure):
 class kf_serve_config(C.Structure):
     _fields_ = [("n_seed_layers", C.c_int32), ("n_build_layers", C.c_int32), ("max_cands", C.c_int32),
                 ("max_slots", C.c_int32), ("max_queue", C.c_int32), ("refit", C.c_int32),
-                ("device_arena_bytes", C.c_size_t), ("host_arena_bytes", C.c_size_t)]
+                ("device_arena_bytes", C.c_size_t), ("host_arena_bytes", C.c_size_t),
+                ("pack_min_seeds", C.c_int64)]
 
 
 class kf_event(C.Structure):
@@ -394,9 +395,9 @@ def kf_autotune_build(ctx, seeds: Tracks, seed_off, bins: HitBins, max_cands: in
 
 
 def kf_serve_start(ctx, n_seed_layers=3, n_build_layers=7, max_cands=6, max_slots=MAX_SLOTS, max_queue=1024,
-                   device_arena_bytes=0, host_arena_bytes=0, refit=False):
+                   device_arena_bytes=0, host_arena_bytes=0, refit=False, pack_min_seeds=0):
     cfg = kf_serve_config(n_seed_layers, n_build_layers, max_cands, max_slots, max_queue, int(bool(refit)),
-                          device_arena_bytes, host_arena_bytes)
+                          device_arena_bytes, host_arena_bytes, int(pack_min_seeds))
     _check(lib().kf_serve_start(_h(ctx), C.byref(cfg)), "kf_serve_start", _h(ctx))
 
 

@@ -37,7 +37,9 @@ def test_alone_equals_mix_equals_batch_build(cuda_ctx_factory, layout):
     ctx = cuda_ctx_factory(det.radii)
     evs = [_event(100 + i, n) for i, n in enumerate(SIZES)]
     kf.kf_set_tuning(ctx, 128, 0, 8, layout)
-    kf.kf_serve_start(ctx, 3, 7, 6, max_slots=32, device_arena_bytes=1 << 30, host_arena_bytes=1 << 29)
+    # pack_min_seeds=1: every step launch takes the configured layout, however few seeds
+    kf.kf_serve_start(ctx, 3, 7, 6, max_slots=32, device_arena_bytes=1 << 30, host_arena_bytes=1 << 29,
+                      pack_min_seeds=1)
     alone = []
     for (b, ev), n in zip(evs, SIZES):
         t = kf.kf_submit(ctx, ev)
@@ -124,6 +126,9 @@ def test_oversized_event_cancel_timeout_and_bad_arguments(cuda_ctx_factory):
     st = kf.kf_serve_stats_get(ctx)
     kf.kf_serve_stop(ctx)
     assert st["max_resident"] == 1
+    with pytest.raises(kf.KfError) as e:
+        kf.kf_serve_start(ctx, 3, 7, 6, pack_min_seeds=-1)
+    assert e.value.code == kf.KF_EINVAL
 
 
 def test_concurrent_submitters_and_pollers(cuda_ctx_factory):
