@@ -116,12 +116,23 @@ def test_build_phi_wraparound_and_eta_edges(cuda_ctx_factory):
 
 def test_build_config3_full_size_sampled(cuda_ctx_factory):
     """50 events x 5000 seeds, 15000 noise + 5000 track hits per layer, N = 6,
-    building on layers 4-10; a sample of seeds is checked against the
-    oracle's all-hits build."""
+    building on layers 4-10, in the launch setting the benchmark times (the
+    autotuner's choice on this batch): the same bits as the grouped per-lane
+    layout, and a sample of seeds checked against the oracle's all-hits build."""
+    from paper_1605_05508_gb300 import kf
     det = S.barrel()
     ctx = cuda_ctx_factory(det.radii)
     batch = S.make_build_batch(1608, 50, 5000)
-    g = gpu_build(ctx, batch, 6, want_cands=False)
+    chosen = {}
+
+    def tune(*args):
+        chosen.update(kf.kf_autotune_build(*args))
+    g = gpu_build(ctx, batch, 6, want_cands=False, build_fn=tune)
+    print("autotuned build setting:", chosen)
+    kf.kf_set_tuning(ctx, 128, 0, 8, 0)
+    g0 = gpu_build(ctx, batch, 6, want_cands=False)
+    for k in ("par", "chi2", "nhits", "status", "hits"):
+        np.testing.assert_array_equal(g[k], g0[k], err_msg=k)
     rng = np.random.default_rng(1)
     idx = np.sort(rng.choice(50 * 5000, 240, replace=False))
     r = oracle_build(batch, 6, idx=idx)

@@ -175,13 +175,14 @@ def test_empty_and_invalid_arguments(cuda_ctx_factory, det):
 
 def test_full_size_config2_sampled(cuda_ctx_factory, det):
     """200 events x 20000 tracks in one batch, in the benchmark's launch
-    configuration; a random sample of tracks is checked against the oracle."""
+    configuration (the autotuner's block size and L2 chunk on this batch); a
+    random sample of tracks is checked against the oracle."""
     ctx = cuda_ctx_factory(det.radii)
     n = 200 * 20000
     ev = S.make_fit_batch(1606, n, keep_truth=False)
     rng = np.random.default_rng(0)
     idx = np.sort(rng.choice(n, 3000, replace=False))
-    g = gpu_fit(ctx, ev.seeds, ev.hits.xyz, ev.hits.valid, "graph", sample=idx)
+    g = gpu_fit(ctx, ev.seeds, ev.hits.xyz, ev.hits.valid, "autotune", sample=idx)
     sub = S.Seeds(ev.seeds.par[:, idx], ev.seeds.cov[:, idx], ev.seeds.charge[idx])
     r = oracle_fit(sub, ev.hits.xyz[:, :, idx], ev.hits.valid[:, idx], det)
     compare(g, r, det.radii[-1], chi2_frac=1e-3, label="config2 sample")
