@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(kBuildThreads, kBuildBlocksPerSM) build_step_k
   const bool seed_ok = j < D.S;
   const int nc = seed_ok ? D.in.ncand[j] : 0;
   const bool active = k < nc;
-  const int64_t slot = j * kGroup + k;
+  const int64_t slot = cand_slot(j, k, D.S);
 
   float p[6], lo[3], C[21];
   float chi2tot = 0.f;
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(kBuildThreads, kBuildBlocksPerSM) build_step_k
     const int64_t j_first = j - (lane >> 3);
     int f_ref = 0;
     if (j_first < D.S) {
-      const int64_t s0 = j_first * kGroup;
+      const int64_t s0 = cand_slot(j_first, 0, D.S);
       const float ph = atan2f(D.in.par[S8 + s0], D.in.par[s0]);
       if (ph >= -kPi && ph <= kPi) f_ref = phi_bin(ph);
     }
@@ -616,7 +616,7 @@ __global__ void __launch_bounds__(NT, kBuildBlocksPerSM * kBuildThreads / NT) bu
       const int sd = packed_owner(s_pstart, sa, sb - 1, base + t);
       const int k = base + t - s_pstart[sd];
       const int64_t j = j0 + sd;
-      const int64_t slot = j * kGroup + k;
+      const int64_t slot = cand_slot(j, k, D.S);
       float p[6], lo[3], C[21];
 #pragma unroll
       for (int c = 0; c < 6; ++c) p[c] = D.in.par[c * S8 + slot];
@@ -738,8 +738,8 @@ __global__ void __launch_bounds__(NT, kBuildBlocksPerSM * kBuildThreads / NT) bu
         s_ckey[t][r] = best;
         s_cpos[t][r] = s_pos[bh][p0 + bk];
         heads += 1u << (4 * bk);
-        D.hist_parent[j * kGroup + r] = int8_t((best >> 21) & 7u);
-        D.hist_hit[j * kGroup + r] = int(best & 0x1fffffu) - 1;
+        D.hist_parent[cand_slot(j, r, D.S)] = int8_t((best >> 21) & 7u);
+        D.hist_hit[cand_slot(j, r, D.S)] = int(best & 0x1fffffu) - 1;
         ++n_win;
       }
       D.out.ncand[j] = int8_t(n_win);
@@ -752,7 +752,7 @@ __global__ void __launch_bounds__(NT, kBuildBlocksPerSM * kBuildThreads / NT) bu
       const int sl = packed_owner(s_cstart, 0, nr - 1, c);
       const int r = c - s_cstart[sl];
       const int64_t j = j0 + sa + sl;
-      const int64_t slot = j * kGroup + r;
+      const int64_t slot = cand_slot(j, r, D.S);
       const uint64_t key = s_ckey[sl][r];
       const int pi = s_pstart[sa + sl] - base + int((key >> 21) & 7u);
       float q[6], ql[3], qC[21];
@@ -795,7 +795,7 @@ __global__ void build_init_kernel(const BuildInitArgs A) {
   const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j >= A.S) return;
   const int64_t s = A.seed_perm[j];
-  const int64_t S8 = A.S * kGroup, slot = j * kGroup;
+  const int64_t S8 = A.S * kGroup, slot = cand_slot(j, 0, A.S);
   for (int c = 0; c < 6; ++c) A.out.par[c * S8 + slot] = A.par[c * A.n + s];
   for (int c = 0; c < 3; ++c) A.out.par[(6 + c) * S8 + slot] = A.lo ? A.lo[c * A.n + s] : 0.f;
   for (int c = 0; c < 21; ++c) A.out.cov[c * S8 + slot] = A.cov[c * A.n + s];
@@ -839,7 +839,7 @@ __global__ void build_final_kernel(const BuildFinalArgs A) {
   const kf_build_result& o = A.out;
   // best candidate: rank 0
   {
-    const int64_t slot = j * kGroup;
+    const int64_t slot = cand_slot(j, 0, A.S);
     float p[6], C[21];
     for (int c = 0; c < 6; ++c) p[c] = A.cand.par[c * S8 + slot];
     for (int c = 0; c < 21; ++c) C[c] = A.cand.cov[c * S8 + slot];
@@ -859,7 +859,7 @@ __global__ void build_final_kernel(const BuildFinalArgs A) {
     if (o.hit_idx) {
       int kk = 0;
       for (int l = A.n_layers - 1; l >= 0; --l) {
-        const int64_t sl = int64_t(l) * S8 + j * kGroup + kk;
+        const int64_t sl = int64_t(l) * S8 + cand_slot(j, kk, A.S);
         o.hit_idx[int64_t(l) * A.S + seed] = A.hist_hit[sl];
         kk = A.hist_parent[sl];
       }
@@ -868,7 +868,7 @@ __global__ void build_final_kernel(const BuildFinalArgs A) {
   if (o.n_cands) o.n_cands[seed] = nc;
   for (int c = 0; c < A.max_cands; ++c) {
     const int64_t oc = seed * A.max_cands + c;
-    const int64_t slot = j * kGroup + c;
+    const int64_t slot = cand_slot(j, c, A.S);
     if (o.cand_chi2_tot) o.cand_chi2_tot[oc] = c < nc ? A.cand.chi2[slot] : 0.f;
     if (o.cand_n_hits) o.cand_n_hits[oc] = c < nc ? (A.cand.meta[slot] & 0xff) : 0;
     if (o.cand_hit_idx) {
@@ -876,7 +876,7 @@ __global__ void build_final_kernel(const BuildFinalArgs A) {
       for (int l = A.n_layers - 1; l >= 0; --l) {
         int32_t h = -1;
         if (c < nc) {
-          const int64_t sl = int64_t(l) * S8 + j * kGroup + kk;
+          const int64_t sl = int64_t(l) * S8 + cand_slot(j, kk, A.S);
           h = A.hist_hit[sl];
           kk = A.hist_parent[sl];
         }

@@ -20,8 +20,13 @@ constexpr int kParN = 9;  // x y z px py pz + low parts of x y z
 constexpr uint64_t kNoKey = ~0ull;
 constexpr unsigned kFull = 0xffffffffu;
 
+// Candidate k (0 .. kGroup-1, by rank) of seed j among S seeds: rank-major,
+// so the candidates of one rank are contiguous over the seeds (the first
+// layers, with one or two candidates a seed, read and write whole sectors).
+__host__ __device__ __forceinline__ int64_t cand_slot(int64_t j, int k, int64_t S) { return int64_t(k) * S + j; }
+
 struct CandBuf {
-  float* par;      // [9][S8]
+  float* par;      // [9][S8], S8 = kGroup * S, slot cand_slot(j, k, S)
   float* cov;      // [21][S8]
   float* chi2;     // [S8] chi2_tot
   int32_t* meta;   // [S8] nHits | status << 8
@@ -33,7 +38,7 @@ struct CandBuf {
 // different layers.  Blocks [block_begin, next slot's block_begin) serve it.
 struct BuildSlot {
   CandBuf in, out;
-  int8_t* hist_parent;       // [S8] of this layer
+  int8_t* hist_parent;       // [S8] of this layer (slot cand_slot(j, k, S))
   int32_t* hist_hit;         // [S8] of this layer
   const int32_t* seed_evt;   // [S] sorted position -> event, or null (event 0)
   const int32_t* seed_perm;  // [S] sorted position -> seed index
