@@ -58,12 +58,13 @@ def test_fused_equals_graph_and_host_equals_device(cuda_ctx_factory, det):
 
 
 def test_host_pipeline_chunks_equal_device_fit(cuda_ctx_factory, det):
-    """kf_fit_host on a batch of several chunks (65 536 tracks each, three
-    streams, a ragged last chunk): the same bits as kf_fit on the device."""
+    """kf_fit_host on a batch of seven chunks (65 536 tracks each, a ragged
+    last one) on three streams, each reusing its staging slot: the same bits
+    as kf_fit on the device; a separate charge output is the input's copy."""
     import torch
     from paper_1605_05508_gb300 import kf
     ctx = cuda_ctx_factory(det.radii)
-    n = 200_003
+    n = 400_003
     ev = S.make_fit_batch(4242, n, keep_truth=False)
     valid = ev.hits.valid.copy()
     valid[4, ::11] = 0
@@ -71,8 +72,8 @@ def test_host_pipeline_chunks_equal_device_fit(cuda_ctx_factory, det):
     L = det.n_layers
     pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
     s = kf.Tracks(pin(ev.seeds.par), pin(ev.seeds.cov), pin(ev.seeds.charge))
-    out = kf.Tracks(torch.empty((6, n)).pin_memory(), torch.empty((21, n)).pin_memory(), s.charge,
-                    torch.empty((3, n)).pin_memory())
+    out = kf.Tracks(torch.empty((6, n)).pin_memory(), torch.empty((21, n)).pin_memory(),
+                    torch.zeros(n, dtype=torch.int8).pin_memory(), torch.empty((3, n)).pin_memory())
     chi2 = torch.empty((L, n)).pin_memory()
     st = torch.empty(n, dtype=torch.int32).pin_memory()
     for _ in range(2):  # the second call replays the cached per-chunk graphs
@@ -80,6 +81,7 @@ def test_host_pipeline_chunks_equal_device_fit(cuda_ctx_factory, det):
         c = unpack(out, chi2, st)
         for k in ("par", "cov", "chi2", "status"):
             np.testing.assert_array_equal(a[k], c[k], err_msg=k)
+        np.testing.assert_array_equal(out.charge.numpy(), ev.seeds.charge)
 
 
 @pytest.mark.parametrize("n", [4096, 40000, 40016])
