@@ -148,12 +148,9 @@ cudaError_t launch_bin_points(const BinArgs& a, int n_segments, cudaStream_t st)
   const int64_t pts = a.stride > 0 ? a.stride : 1;
   const int pgrid = int(std::min<int64_t>((pts + kPointThreads - 1) / kPointThreads, int64_t(1) << 20));
   bin_count_kernel<<<pgrid, kPointThreads, 0, st>>>(a, n_segments);
-  static bool attr = false;
-  if (!attr) {
-    e = cudaFuncSetAttribute(bin_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kScanSmem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  // per device and cheap: set on every call (no process-wide flag, no race)
+  e = cudaFuncSetAttribute(bin_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kScanSmem);
+  if (e != cudaSuccess) return e;
   bin_scan_kernel<<<n_segments, kScanThreads, kScanSmem, st>>>(a);
   bin_scatter_kernel<<<pgrid, kPointThreads, 0, st>>>(a, n_segments);
   const int64_t bins = int64_t(n_segments) * KF_NBINS;
