@@ -199,8 +199,9 @@ typedef struct {
 } kf_layer_hit_bins;
 
 /* Sort every segment's hits into the eta x phi bins (Sec. 3: hits sorted in
- * phi within eta bins per layer, phi bins for fast look-up): a counting sort,
- * one thread block per segment.  `out->hits` and `out->bin_off` are
+ * phi within eta bins per layer, phi bins for fast look-up): a counting sort
+ * over all segments at once (count, per-segment scan, scatter, then an id
+ * sort inside each bin, so the order is deterministic).  `out->hits` and `out->bin_off` are
  * caller-allocated with the sizes above; the other fields of `out` are set
  * from `in`.  Segments must hold at most KF_MAX_HITS_PER_SEGMENT hits (not
  * checked here: seg_off is device memory; kf_build ignores hits beyond it).
