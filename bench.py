@@ -427,6 +427,60 @@ def extras(a, ctx, kf, torch, dev, det, ev, seeds, hits, out, chi2, status, stre
         res["cpu_baseline"] = {"value": m * L / dtc, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": f"first {m} tracks ({m // a.tracks} events) x {L} layers, FP64 oracle, "
                                          f"{cores} OpenMP threads, {dtc:.2f} s wall"}
+    res["single_event"] = single_event_leg(a, kf, torch, dev, det, stream, rank)
+    return res
+
+
+def single_event_leg(a, kf, torch, dev, det, stream, rank):
+    """The plain FP64 configuration: one event of 1 000 tracks (seed 1605),
+    fitted over the 10 layers by the FP32 per-layer graph, the plain FP64
+    form and the oracle (one thread, and all host cores); medians of 20 GPU
+    fits (CUDA events) and of 5 oracle runs."""
+    from paper_1605_05508_gb300 import synth as S
+    n, L = 1000, det.n_layers
+    ev = S.make_fit_batch(1605, n, det, keep_truth=False)
+    T = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    ctx = kf.Context(det.radii, det.bz, det.sigma_xy, det.sigma_z, device=dev.index)
+    s32 = kf.Tracks(T(ev.seeds.par), T(ev.seeds.cov), T(ev.seeds.charge))
+    h = kf.TrackHits(T(ev.hits.xyz), T(ev.hits.valid))
+    o32 = kf.Tracks(torch.empty((6, n), device=dev), torch.empty((21, n), device=dev), s32.charge,
+                    torch.empty((3, n), device=dev))
+    c32 = torch.empty((L, n), device=dev)
+    st = torch.empty(n, dtype=torch.int32, device=dev)
+    s64 = kf.Tracks(s32.par.double(), s32.cov.double(), s32.charge)
+    o64 = kf.Tracks(torch.empty((6, n), dtype=torch.float64, device=dev),
+                    torch.empty((21, n), dtype=torch.float64, device=dev), s32.charge)
+    c64 = torch.empty((L, n), dtype=torch.float64, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def med(fn, k=20):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(k):
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+    us32 = med(lambda: kf.kf_fit(ctx, s32, h, o32, c32, st, stream)) * 1e3
+    us64 = med(lambda: kf.kf_fit_f64(ctx, s64, h, o64, [0, n], c64, st, stream)) * 1e3
+    ctx.close()
+    res = {"workload": "1 event x 1000 tracks, 10 layers (seed 1605)", "unit": "us per event",
+           "fp32_graph_us": us32, "plain_f64_us": us64, "fp32_over_f64_speedup": us64 / us32}
+    if rank == 0:
+        import oracle as O
+        cores = os.cpu_count() or 1
+        for name, thr in (("oracle_1_thread_us", 1), ("oracle_all_cores_us", cores)):
+            ts = []
+            for _ in range(5):
+                t0 = time.perf_counter()
+                O.fit(ev.seeds.par, ev.seeds.cov, ev.seeds.charge, ev.hits.xyz, ev.hits.valid, det.radii, det.bz,
+                      det.sigma_xy, det.sigma_z, n_threads=thr)
+                ts.append(time.perf_counter() - t0)
+            res[name] = float(np.median(ts)) * 1e6
+        res["oracle_cores"] = cores
     return res
 
 
