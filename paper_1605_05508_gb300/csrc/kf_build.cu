@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(kBuildThreads, kBuildBlocksPerSM) build_step_k
   const bool seed_ok = j < D.S;
   const int nc = seed_ok ? D.in.ncand[j] : 0;
   const bool active = k < nc;
-  const int64_t slot = cand_slot(j, k, D.S);
+  const int64_t slot = cand_slot(j, k, D.S, D.in_rm), oslot = cand_slot(j, k, D.S, D.out_rm);
 
   float p[6], lo[3], C[21];
   float chi2tot = 0.f;
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(kBuildThreads, kBuildBlocksPerSM) build_step_k
     const int64_t j_first = j - (lane >> 3);
     int f_ref = 0;
     if (j_first < D.S) {
-      const int64_t s0 = cand_slot(j_first, 0, D.S);
+      const int64_t s0 = cand_slot(j_first, 0, D.S, D.in_rm);
       const float ph = atan2f(D.in.par[S8 + s0], D.in.par[s0]);
       if (ph >= -kPi && ph <= kPi) f_ref = phi_bin(ph);
     }
@@ -499,15 +499,15 @@ __global__ void __launch_bounds__(kBuildThreads, kBuildBlocksPerSM) build_step_k
       st_new |= KF_ST_NO_HIT;
     }
 #pragma unroll
-    for (int c = 0; c < 6; ++c) D.out.par[c * S8 + slot] = q[c];
+    for (int c = 0; c < 6; ++c) D.out.par[c * S8 + oslot] = q[c];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) D.out.par[(6 + c) * S8 + slot] = ql[c];
+    for (int c = 0; c < 3; ++c) D.out.par[(6 + c) * S8 + oslot] = ql[c];
 #pragma unroll
-    for (int c = 0; c < 21; ++c) D.out.cov[c * S8 + slot] = qC[c];
-    D.out.chi2[slot] = chi2_new;
-    D.out.meta[slot] = nh_new | (st_new << 8);
-    D.hist_parent[slot] = int8_t(my_parent);
-    D.hist_hit[slot] = hit_plus1 - 1;
+    for (int c = 0; c < 21; ++c) D.out.cov[c * S8 + oslot] = qC[c];
+    D.out.chi2[oslot] = chi2_new;
+    D.out.meta[oslot] = nh_new | (st_new << 8);
+    D.hist_parent[oslot] = int8_t(my_parent);
+    D.hist_hit[oslot] = hit_plus1 - 1;
   }
   if (seed_ok && k == 0) D.out.ncand[j] = int8_t(n_win);
 }
@@ -616,7 +616,7 @@ __global__ void __launch_bounds__(NT, kBuildBlocksPerSM * kBuildThreads / NT) bu
       const int sd = packed_owner(s_pstart, sa, sb - 1, base + t);
       const int k = base + t - s_pstart[sd];
       const int64_t j = j0 + sd;
-      const int64_t slot = cand_slot(j, k, D.S);
+      const int64_t slot = cand_slot(j, k, D.S, D.in_rm);
       float p[6], lo[3], C[21];
 #pragma unroll
       for (int c = 0; c < 6; ++c) p[c] = D.in.par[c * S8 + slot];
@@ -738,8 +738,8 @@ __global__ void __launch_bounds__(NT, kBuildBlocksPerSM * kBuildThreads / NT) bu
         s_ckey[t][r] = best;
         s_cpos[t][r] = s_pos[bh][p0 + bk];
         heads += 1u << (4 * bk);
-        D.hist_parent[cand_slot(j, r, D.S)] = int8_t((best >> 21) & 7u);
-        D.hist_hit[cand_slot(j, r, D.S)] = int(best & 0x1fffffu) - 1;
+        D.hist_parent[cand_slot(j, r, D.S, D.out_rm)] = int8_t((best >> 21) & 7u);
+        D.hist_hit[cand_slot(j, r, D.S, D.out_rm)] = int(best & 0x1fffffu) - 1;
         ++n_win;
       }
       D.out.ncand[j] = int8_t(n_win);
@@ -752,7 +752,7 @@ __global__ void __launch_bounds__(NT, kBuildBlocksPerSM * kBuildThreads / NT) bu
       const int sl = packed_owner(s_cstart, 0, nr - 1, c);
       const int r = c - s_cstart[sl];
       const int64_t j = j0 + sa + sl;
-      const int64_t slot = cand_slot(j, r, D.S);
+      const int64_t slot = cand_slot(j, r, D.S, D.out_rm);
       const uint64_t key = s_ckey[sl][r];
       const int pi = s_pstart[sa + sl] - base + int((key >> 21) & 7u);
       float q[6], ql[3], qC[21];
@@ -795,7 +795,7 @@ __global__ void build_init_kernel(const BuildInitArgs A) {
   const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j >= A.S) return;
   const int64_t s = A.seed_perm[j];
-  const int64_t S8 = A.S * kGroup, slot = cand_slot(j, 0, A.S);
+  const int64_t S8 = A.S * kGroup, slot = cand_slot(j, 0, A.S, true);  // buffer 0: rank-major
   for (int c = 0; c < 6; ++c) A.out.par[c * S8 + slot] = A.par[c * A.n + s];
   for (int c = 0; c < 3; ++c) A.out.par[(6 + c) * S8 + slot] = A.lo ? A.lo[c * A.n + s] : 0.f;
   for (int c = 0; c < 21; ++c) A.out.cov[c * S8 + slot] = A.cov[c * A.n + s];
@@ -835,11 +835,12 @@ __global__ void build_final_kernel(const BuildFinalArgs A) {
   if (j >= A.S) return;
   const int64_t seed = A.seed_perm[j];
   const int64_t S8 = A.S * kGroup;
+  const bool last_rm = A.n_layers < A.rm_buffers;  // layout of buffer n_layers
   const int nc = A.cand.ncand[j];
   const kf_build_result& o = A.out;
   // best candidate: rank 0
   {
-    const int64_t slot = cand_slot(j, 0, A.S);
+    const int64_t slot = cand_slot(j, 0, A.S, last_rm);
     float p[6], C[21];
     for (int c = 0; c < 6; ++c) p[c] = A.cand.par[c * S8 + slot];
     for (int c = 0; c < 21; ++c) C[c] = A.cand.cov[c * S8 + slot];
@@ -859,7 +860,7 @@ __global__ void build_final_kernel(const BuildFinalArgs A) {
     if (o.hit_idx) {
       int kk = 0;
       for (int l = A.n_layers - 1; l >= 0; --l) {
-        const int64_t sl = int64_t(l) * S8 + cand_slot(j, kk, A.S);
+        const int64_t sl = int64_t(l) * S8 + cand_slot(j, kk, A.S, l + 1 < A.rm_buffers);
         o.hit_idx[int64_t(l) * A.S + seed] = A.hist_hit[sl];
         kk = A.hist_parent[sl];
       }
@@ -868,7 +869,7 @@ __global__ void build_final_kernel(const BuildFinalArgs A) {
   if (o.n_cands) o.n_cands[seed] = nc;
   for (int c = 0; c < A.max_cands; ++c) {
     const int64_t oc = seed * A.max_cands + c;
-    const int64_t slot = cand_slot(j, c, A.S);
+    const int64_t slot = cand_slot(j, c, A.S, last_rm);
     if (o.cand_chi2_tot) o.cand_chi2_tot[oc] = c < nc ? A.cand.chi2[slot] : 0.f;
     if (o.cand_n_hits) o.cand_n_hits[oc] = c < nc ? (A.cand.meta[slot] & 0xff) : 0;
     if (o.cand_hit_idx) {
@@ -876,7 +877,7 @@ __global__ void build_final_kernel(const BuildFinalArgs A) {
       for (int l = A.n_layers - 1; l >= 0; --l) {
         int32_t h = -1;
         if (c < nc) {
-          const int64_t sl = int64_t(l) * S8 + cand_slot(j, kk, A.S);
+          const int64_t sl = int64_t(l) * S8 + cand_slot(j, kk, A.S, l + 1 < A.rm_buffers);
           h = A.hist_hit[sl];
           kk = A.hist_parent[sl];
         }
@@ -1015,6 +1016,7 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
   const int grid = build_step_blocks(S, ctx->tune.build_scan);
   // one slot (the whole batch) per layer launch; the table goes to device
   // scratch in one copy (the host array is consumed before the call returns)
+  const int rm_buffers = rank_major_buffers(max_cands, L);
   std::vector<BuildSlot> table(L);
   for (int l = 0; l < L; ++l) {
     BuildSlot& d = table[l];
@@ -1033,6 +1035,8 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
     d.n_layers = L;
     d.R = ctx->radius[bins->first_layer + l];
     d.x_x0 = ctx->x_x0[bins->first_layer + l];
+    d.in_rm = l < rm_buffers;
+    d.out_rm = l + 1 < rm_buffers;
     d.block_begin = 0;
   }
   BuildSlot* dtable = reinterpret_cast<BuildSlot*>(base + b_perm + b_evt + 2 * b_cand + b_hp + b_hh);
@@ -1059,6 +1063,7 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
   fa.S = S;
   fa.n_layers = L;
   fa.max_cands = max_cands;
+  fa.rm_buffers = rm_buffers;
   fa.out = *out;
   build_final_kernel<<<int((S + 127) / 128), 128, 0, s>>>(fa);
   KF_CUDA_TRY(ctx, cudaGetLastError());

@@ -20,13 +20,22 @@ constexpr int kParN = 9;  // x y z px py pz + low parts of x y z
 constexpr uint64_t kNoKey = ~0ull;
 constexpr unsigned kFull = 0xffffffffu;
 
-// Candidate k (0 .. kGroup-1, by rank) of seed j among S seeds: rank-major,
-// so the candidates of one rank are contiguous over the seeds (the first
-// layers, with one or two candidates a seed, read and write whole sectors).
-__host__ __device__ __forceinline__ int64_t cand_slot(int64_t j, int k, int64_t S) { return int64_t(k) * S + j; }
+// Candidate k (0 .. kGroup-1, by rank) of seed j among S seeds.  Rank-major
+// (k S + j: the candidates of one rank contiguous over the seeds) suits a
+// buffer with one or two candidates a seed, whose loads and stores then fill
+// whole 32-byte sectors; seed-major (kGroup j + k: a seed's candidates in one
+// sector) suits a buffer with five or six.
+__host__ __device__ __forceinline__ int64_t cand_slot(int64_t j, int k, int64_t S, bool rank_major) {
+  return rank_major ? int64_t(k) * S + j : j * kGroup + k;
+}
+// Buffer b of a build holds the candidates after b building layers (b = 0:
+// the seeds).  Buffers b < rank_major_buffers(...) are rank-major, the rest
+// seed-major: with max_cands <= 2 every buffer, otherwise the seeds and the
+// first layer's children (one to three candidates a seed).
+inline int rank_major_buffers(int max_cands, int n_layers) { return max_cands <= 2 ? n_layers + 1 : 2; }
 
 struct CandBuf {
-  float* par;      // [9][S8], S8 = kGroup * S, slot cand_slot(j, k, S)
+  float* par;      // [9][S8], S8 = kGroup * S, slot cand_slot(j, k, S, layout)
   float* cov;      // [21][S8]
   float* chi2;     // [S8] chi2_tot
   int32_t* meta;   // [S8] nHits | status << 8
@@ -38,7 +47,7 @@ struct CandBuf {
 // different layers.  Blocks [block_begin, next slot's block_begin) serve it.
 struct BuildSlot {
   CandBuf in, out;
-  int8_t* hist_parent;       // [S8] of this layer (slot cand_slot(j, k, S))
+  int8_t* hist_parent;       // [S8] of this layer (slots in the layout of `out`)
   int32_t* hist_hit;         // [S8] of this layer
   const int32_t* seed_evt;   // [S] sorted position -> event, or null (event 0)
   const int32_t* seed_perm;  // [S] sorted position -> seed index
@@ -50,6 +59,7 @@ struct BuildSlot {
   int layer, n_layers;
   float R;
   float x_x0;  // this layer's thickness in radiation lengths (0: none)
+  int in_rm, out_rm;  // 1: `in` / `out` (and the history) are rank-major (cand_slot)
   int block_begin;
 };
 
@@ -77,6 +87,7 @@ struct BuildFinalArgs {
   const int32_t* seed_perm;
   int64_t S;
   int n_layers, max_cands;
+  int rm_buffers;  // rank_major_buffers(max_cands, n_layers)
   kf_build_result out;
 };
 

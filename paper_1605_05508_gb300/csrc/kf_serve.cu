@@ -419,6 +419,9 @@ static BuildSlot slot_of(Serve* sv, Request* r) {
   b.n_layers = L.Lb;
   b.R = sv->ctx->radius[sv->cfg.n_seed_layers + r->layer];
   b.x_x0 = sv->ctx->x_x0[sv->cfg.n_seed_layers + r->layer];
+  const int rm = rank_major_buffers(sv->cfg.max_cands, L.Lb);
+  b.in_rm = r->layer < rm;
+  b.out_rm = r->layer + 1 < rm;
   b.block_begin = 0;
   return b;
 }
@@ -439,6 +442,7 @@ static cudaError_t finish(Serve* sv, Request* r) {
   fa.S = n;
   fa.n_layers = L.Lb;
   fa.max_cands = sv->cfg.max_cands;
+  fa.rm_buffers = rank_major_buffers(sv->cfg.max_cands, L.Lb);
   fa.out.best.n = n;
   fa.out.best.par = reinterpret_cast<float*>(d + L.d_rpar);
   fa.out.best.par_lo = nullptr;
