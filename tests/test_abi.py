@@ -66,3 +66,31 @@ def test_strerror_and_argument_checks_need_no_gpu(libpath):
     assert lib.kf_set_tuning(None, ctypes.byref(t)) == kf.KF_EINVAL
     assert lib.kf_autotune_fit(None, None, None, None, None, None, None, None) == kf.KF_EINVAL
     assert lib.kf_autotune_build(None, None, None, None, 6, None, None, None) == kf.KF_EINVAL
+
+
+def test_binding_constants_match_the_header():
+    """Every numeric #define of include/kf.h that the binding mirrors has the
+    same value there (error codes, status bits, bin grid, size limits)."""
+    import re
+    from paper_1605_05508_gb300 import kf
+    hdr = open(os.path.join(ROOT, "include", "kf.h")).read()
+    defs = {}
+    for name, expr in re.findall(r"^#define (KF_\w+)\s+(.+?)\s*(?:/\*.*)?$", hdr, flags=re.M):
+        e = expr.strip().rstrip("f")
+        for k, v in sorted(defs.items(), key=lambda kv: -len(kv[0])):
+            e = e.replace(k, repr(v))
+        try:
+            defs[name] = eval(e, {"__builtins__": {}})
+        except Exception:
+            pass
+    mirror = {"KF_OK": kf.KF_OK, "KF_EINVAL": kf.KF_EINVAL, "KF_ENOMEM": kf.KF_ENOMEM, "KF_EAGAIN": kf.KF_EAGAIN,
+              "KF_ETIMEDOUT": kf.KF_ETIMEDOUT, "KF_ECUDA": kf.KF_ECUDA, "KF_ENOTSUP": kf.KF_ENOTSUP,
+              "KF_ST_NOT_REACHED": kf.ST_NOT_REACHED, "KF_ST_NEWTON_FAIL": kf.ST_NEWTON_FAIL,
+              "KF_ST_TANGENT": kf.ST_TANGENT, "KF_ST_NOT_PD": kf.ST_NOT_PD, "KF_ST_NO_HIT": kf.ST_NO_HIT,
+              "KF_ST_DEVICE_TIMEOUT": kf.ST_DEVICE_TIMEOUT, "KF_ST_STOPPED": kf.ST_STOPPED,
+              "KF_BIN_ETA": kf.BIN_ETA, "KF_BIN_PHI": kf.BIN_PHI, "KF_BIN_ETA_MAX": kf.BIN_ETA_MAX,
+              "KF_NBINS": kf.NBINS, "KF_MAX_HITS_PER_SEGMENT": kf.MAX_HITS_PER_SEGMENT,
+              "KF_MAX_SLOTS": kf.MAX_SLOTS, "KF_NOALLOC_MAX_TRACKS": kf.NOALLOC_MAX_TRACKS}
+    for name, value in mirror.items():
+        assert name in defs, name
+        assert defs[name] == value, (name, defs[name], value)

@@ -173,3 +173,38 @@ def test_build_edge_cases(cuda_ctx_factory):
     kf.kf_build(ctx, z, to_dev(np.zeros(1, np.int64)), g["bins"], 6, out)
     with pytest.raises(kf.KfError):
         kf.kf_build(ctx, z, to_dev(np.zeros(1, np.int64)), g["bins"], 9, out)  # max_cands > 8
+
+
+def test_build_segment_beyond_the_hit_id_limit(cuda_ctx_factory):
+    """A segment (event, layer) with more hits than a hit id can number
+    (KF_MAX_HITS_PER_SEGMENT + 1000, uniform noise on the first building
+    layer): binning and building run, the hits past the limit are ignored --
+    the result equals that of the same event with those hits removed, for the
+    grouped and the candidate-packed layouts."""
+    from paper_1605_05508_gb300 import kf
+    det = S.barrel()
+    ctx = cuda_ctx_factory(det.radii)
+    base = S.make_build_batch(1777, 1, 300)
+    rng = np.random.default_rng(1778)
+    lim = kf.MAX_HITS_PER_SEGMENT
+    n0 = int(base.layer_off[1] - base.layer_off[0])
+    extra = lim + 1000 - n0
+    R = det.radii[base.build_layers[0]]
+    phi = rng.uniform(0.0, 2.0 * np.pi, extra)
+    ex = np.stack([R * np.cos(phi), R * np.sin(phi), rng.uniform(-20.0, 20.0, extra)]).astype(np.float32)
+
+    def with_extra(k):
+        b = S.make_build_batch(1777, 1, 300)
+        b.layer_xyz = np.ascontiguousarray(np.concatenate([b.layer_xyz[:, :n0], ex[:, :k], b.layer_xyz[:, n0:]], 1))
+        b.layer_off = b.layer_off.copy()
+        b.layer_off[1:] += k
+        return b
+    full, cut = with_extra(extra), with_extra(extra - 1000)
+    assert full.layer_off[1] - full.layer_off[0] == lim + 1000 and cut.layer_off[1] - cut.layer_off[0] == lim
+    for layout in (0, 2):
+        kf.kf_set_tuning(ctx, 128, 0, 8, layout)
+        g, h = gpu_build(ctx, full, 6, want_cands=False), gpu_build(ctx, cut, 6, want_cands=False)
+        for k in ("par", "chi2", "nhits", "status", "hits"):
+            np.testing.assert_array_equal(g[k], h[k], err_msg=f"layout {layout} {k}")
+        assert np.all(g["hits"][:, 0] < lim) and np.mean(g["nhits"]) > 5.0
+    kf.kf_set_tuning(ctx, 128, 0, 8, 0)
