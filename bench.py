@@ -46,9 +46,9 @@ def parse():
     ap.add_argument("--tracks", type=int, default=20000)
     ap.add_argument("--layers", type=int, default=10)
     ap.add_argument("--seed", type=int, default=1606)
-    ap.add_argument("--fit-tuning", default=None, metavar="BLOCK,CHUNK",
-                    help="fixed fit launch parameters (threads per block, tracks per L2 chunk; 0 = whole batch) "
-                         "instead of the autotuner's")
+    ap.add_argument("--fit-tuning", default=None, metavar="BLOCK,CHUNK[,STAGE]",
+                    help="fixed fit launch parameters (threads per block, tracks per L2 chunk; 0 = whole batch; "
+                         "staged tiles 0/1) instead of the autotuner's")
     ap.add_argument("--no-extras", action="store_true", help="headline only (no e2e/f64/fused/cpu legs)")
     ap.add_argument("--no-build", action="store_true", help="skip the combinatorial-build leg")
     ap.add_argument("--build-events", type=int, default=50)
@@ -280,8 +280,8 @@ def run_ours(a):
 
     # the library's autotuner picks the layer kernel's block size and L2 chunk on this batch
     if a.fit_tuning:
-        block, chunk = (int(v) for v in a.fit_tuning.split(","))
-        kf.kf_set_tuning(ctx, block, 0, 8, 0, chunk)
+        block, chunk, stage = ([int(v) for v in a.fit_tuning.split(",")] + [0])[:3]
+        kf.kf_set_tuning(ctx, block, 0, 8, 0, chunk, stage)
         tuning = kf.kf_get_tuning(ctx)
     else:
         tuning = kf.kf_autotune_fit(ctx, seeds, hits, out, chi2, status, stream)
@@ -315,7 +315,8 @@ def run_ours(a):
     achieved = bpt * n / chunks / launch_s / 1e9
     peak, peak_kind = measured_peaks()
     traffic = ncu_traffic(n)
-    roof = {"kernel": f"fit_layer_kernel<{tuning['fit_block']}>", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+    kname = "fit_layer_stage_kernel" if tuning.get("fit_stage") else f"fit_layer_kernel<{tuning['fit_block']}>"
+    roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic if chunks == 1 else None, "peak_kind": peak_kind,
             "algorithmic_bytes_per_track_layer": bpt, "launch_us": launch_s * 1e6}
 

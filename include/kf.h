@@ -292,6 +292,11 @@ typedef struct {
                                  chunks of that many tracks, all layers of a chunk before the
                                  next, so the chunk's state stays in the L2 cache between its
                                  layer launches */
+    int32_t fit_stage;        /* kf_fit layer step: 0 = every thread loads its track's rows
+                                 (default), 1 = each warp's next 32 tracks are copied into shared
+                                 memory by tensor copies while it computes the current ones
+                                 (batches whose size is a multiple of 32 with 16-byte aligned
+                                 rows; others take form 0) */
 } kf_tuning;
 
 /* Current launch parameters of the context.  Errors: KF_EINVAL (null). */

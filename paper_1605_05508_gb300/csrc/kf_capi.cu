@@ -181,6 +181,7 @@ int kf_fit(kf_ctx* ctx, const kf_tracks* seeds, const kf_track_hits* hits, kf_tr
                                uint64_t(L),
                                uint64_t(block),
                                uint64_t(chunk),
+                               uint64_t(ctx->tune.fit_stage),
                                reinterpret_cast<uint64_t>(seeds->par),
                                reinterpret_cast<uint64_t>(seeds->par_lo),
                                reinterpret_cast<uint64_t>(seeds->cov),
@@ -226,7 +227,11 @@ int kf_fit(kf_ctx* ctx, const kf_tracks* seeds, const kf_track_hits* hits, kf_tr
       a.v2 = v2;
       a.first = l == 0;
       a.last = l == L - 1;
-      le = launch_fit_layer(a, block, cs);
+      FitStageMaps maps;
+      if (ctx->tune.fit_stage && make_stage_maps(a, &maps))
+        le = launch_fit_layer_stage(a, maps, ctx->num_sms, cs);
+      else
+        le = launch_fit_layer(a, block, cs);
     }
     cudaGraph_t graph = nullptr;
     cudaError_t ee = cudaStreamEndCapture(cs, &graph);

@@ -13,8 +13,14 @@
 // One track per thread, 24 resident warps per SM, plain coalesced row reads.
 // Staging the rows in shared memory (bulk copies per block or per warp, or
 // per-thread cp.async double buffering) measured no faster.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+
 #include "kf_internal.h"
 #include "kf_math.cuh"
+#include "kf_tma.cuh"
 
 namespace kfi {
 
@@ -142,6 +148,115 @@ __global__ void __launch_bounds__(THREADS, kFitWarpsPerSM * 32 / THREADS) fit_la
   fit_layer_track(A, i, st, p, lo, C, A.charge[i], has_hit, A.hit[i], A.hit[n + i], A.hit[2 * n + i]);
 }
 
+// ---------------------------------------------------------------------------
+// Staged form of the layer step (kf_tuning.fit_stage = 1): the same step per
+// track, but the 33 float rows a track reads (state, position low parts,
+// covariance, hit) arrive in shared memory by tensor copies.  Each warp walks
+// tiles of 32 tracks; lane 0 issues four 2-D tensor copies (boxes of 32 tracks
+// x 6, 3, 21 and 3 rows) for the warp's next tile into the other half of a
+// double buffer while the warp computes the current tile, so a tile's loads
+// are in flight during the previous tile's arithmetic without holding
+// registers.  Completion is tracked by one mbarrier per buffer; every wait is
+// bounded (a wait that gives up marks the warp's remaining tracks with
+// KF_ST_DEVICE_TIMEOUT).  Requires n, begin and count multiples of 32 and
+// 16-byte aligned rows; kf_fit falls back to fit_layer_kernel otherwise.
+constexpr int kStageTile = 32;                 // tracks per warp tile
+constexpr int kStageThreads = 64;              // two warps per block
+constexpr int kStageBlocksPerSM = 12;          // 24 warps per SM
+constexpr uint32_t kStageWaitLimit = 1u << 22; // bounded mbarrier polls
+
+struct StageTile {  // one buffer: rows of 32 tracks, each box 128-byte aligned
+  float par[6][kStageTile];
+  float lo[3][kStageTile];
+  float cov[21][kStageTile];
+  float hit[3][kStageTile];
+};
+static_assert(sizeof(StageTile) % 128 == 0, "box alignment");
+constexpr size_t kStageSmem = size_t(kStageThreads / 32) * 2 * sizeof(StageTile) + 64;
+
+__device__ __forceinline__ void tensor_g2s_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void stage_issue(const FitStageMaps& M, bool has_lo, StageTile& T, uint64_t* bar, int x,
+                                            uint32_t bytes) {
+  mbar_arrive_expect_tx(bar, bytes);
+  tensor_g2s_2d(T.par, &M.par, x, 0, bar);
+  if (has_lo) tensor_g2s_2d(T.lo, &M.lo, x, 0, bar);
+  tensor_g2s_2d(T.cov, &M.cov, x, 0, bar);
+  tensor_g2s_2d(T.hit, &M.hit, x, 0, bar);
+}
+
+__global__ void __launch_bounds__(kStageThreads, kStageBlocksPerSM)
+    fit_layer_stage_kernel(const FitLayerArgs A, const __grid_constant__ FitStageMaps M) {
+  extern __shared__ __align__(128) unsigned char stage_smem[];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  StageTile* buf = reinterpret_cast<StageTile*>(stage_smem) + 2 * wib;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(stage_smem + size_t(kStageThreads / 32) * 2 * sizeof(StageTile)) + 2 * wib;
+  const int64_t n_tiles = A.count / kStageTile;
+  const int64_t nwarps = int64_t(gridDim.x) * (kStageThreads / 32);
+  int64_t t = int64_t(blockIdx.x) * (kStageThreads / 32) + wib;
+  if (t >= n_tiles) return;  // the whole warp
+  const bool has_lo = A.in_lo != nullptr;
+  const uint32_t bytes = uint32_t(sizeof(float)) * kStageTile * (6 + 21 + 3 + (has_lo ? 3 : 0));
+  if (lane == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_init_fence();
+    stage_issue(M, has_lo, buf[0], &bar[0], int(A.begin + t * kStageTile), bytes);
+  }
+  __syncwarp();
+  uint32_t ph0 = 0, ph1 = 0;
+  bool failed = false;
+  for (int s = 0; t < n_tiles; t += nwarps, s ^= 1) {
+    const int64_t i = A.begin + t * kStageTile + lane;
+    if (failed) {  // an earlier wait gave up: flag the remaining tracks
+      A.status[i] = (A.first ? 0 : A.status[i]) | KF_ST_DEVICE_TIMEOUT;
+      continue;
+    }
+    // the next tile into the other buffer (its previous tile was read by every
+    // lane before the __syncwarp that closed the last iteration)
+    const int64_t tn = t + nwarps;
+    if (tn < n_tiles && lane == 0) {
+      fence_proxy_async_smem();
+      stage_issue(M, has_lo, buf[s ^ 1], &bar[s ^ 1], int(A.begin + tn * kStageTile), bytes);
+    }
+    // per-track inputs outside the tile, loaded while the copies land
+    const int32_t st = A.first ? 0 : A.status[i];
+    const int8_t q = A.charge[i];
+    const bool has_hit = A.valid ? A.valid[i] != 0 : true;
+    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bar[s], s ? ph1 : ph0, kStageWaitLimit));
+    if (!ok) {  // the phase stays pending: waited for once more below
+      failed = true;
+      A.status[i] = st | KF_ST_DEVICE_TIMEOUT;
+      continue;
+    }
+    if (s)
+      ph1 ^= 1u;
+    else
+      ph0 ^= 1u;
+    const StageTile& T = buf[s];
+    float p[6], lo[3], C[21];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) p[c] = T.par[c][lane];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) lo[c] = has_lo ? T.lo[c][lane] : 0.f;
+#pragma unroll
+    for (int c = 0; c < 21; ++c) C[c] = T.cov[c][lane];
+    const float m0 = T.hit[0][lane], m1 = T.hit[1][lane], m2 = T.hit[2][lane];
+    __syncwarp();  // every lane has read buffer s before lane 0 may refill it
+    fit_layer_track(A, i, st, p, lo, C, q, has_hit, m0, m1, m2);
+  }
+  if (failed && lane == 0) {  // copies still in flight land before the block's memory is released
+    mbar_wait_bounded(&bar[0], ph0, kStageWaitLimit);
+    mbar_wait_bounded(&bar[1], ph1, kStageWaitLimit);
+  }
+}
+
 template <bool UPD64>
 __global__ void __launch_bounds__(kFitThreads, UPD64 ? 1 : kFitMinBlocks) fit_fused_kernel(const FitFusedArgs A) {
   const int64_t n = A.n;
@@ -220,6 +335,52 @@ cudaError_t launch_fit_layer(const FitLayerArgs& a, int block, cudaStream_t st) 
     fit_layer_kernel<64><<<fit_grid(64, a.count), 64, 0, st>>>(a);
   else
     fit_layer_kernel<128><<<fit_grid(128, a.count), 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// Tensor maps of a layer step for fit_layer_stage_kernel: 2-D views (x =
+// track, y = row) of the input state, position low parts, covariance and the
+// layer's hits, boxes of 32 tracks x all rows.  False when the layout does not
+// allow them (rows not 16-byte aligned, sizes not multiples of 32) or the
+// driver's encoder is unavailable.
+bool make_stage_maps(const FitLayerArgs& a, FitStageMaps* m) {
+  if (a.n % kStageTile || a.begin % kStageTile || a.count % kStageTile || a.count <= 0) return false;
+  if (a.n > (int64_t(1) << 31) - 1) return false;
+  auto aligned = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  if (!aligned(a.in_par) || !aligned(a.in_cov) || !aligned(a.hit) || (a.in_lo && !aligned(a.in_lo))) return false;
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  });
+  if (!encode) return false;
+  auto map2d = [&](CUtensorMap* t, const float* base, uint32_t rows) {
+    const cuuint64_t dims[2] = {cuuint64_t(a.n), rows};
+    const cuuint64_t strides[1] = {cuuint64_t(a.n) * sizeof(float)};
+    const cuuint32_t box[2] = {kStageTile, rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return encode(t, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  };
+  std::memset(m, 0, sizeof(*m));
+  return map2d(&m->par, a.in_par, 6) && (!a.in_lo || map2d(&m->lo, a.in_lo, 3)) && map2d(&m->cov, a.in_cov, 21) &&
+         map2d(&m->hit, a.hit, 3);
+}
+
+cudaError_t launch_fit_layer_stage(const FitLayerArgs& a, const FitStageMaps& m, int num_sms, cudaStream_t st) {
+  const int64_t tiles = a.count / kStageTile;
+  const int64_t need = (tiles + kStageThreads / 32 - 1) / (kStageThreads / 32);
+  const int grid = int(std::max<int64_t>(1, std::min<int64_t>(need, int64_t(num_sms) * kStageBlocksPerSM)));
+  cudaError_t e = cudaFuncSetAttribute(fit_layer_stage_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(kStageSmem));
+  if (e != cudaSuccess) return e;
+  fit_layer_stage_kernel<<<grid, kStageThreads, kStageSmem, st>>>(a, m);
   return cudaGetLastError();
 }
 

@@ -2,6 +2,7 @@
 // of libkf (not part of the public ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -60,7 +61,7 @@ struct kf_ctx {
   cudaStream_t host_streams[kfi::kHostStreams] = {};  // kf_fit_host pipeline
   cudaEvent_t host_done[kfi::kHostStreams] = {};
   cudaEvent_t host_start = nullptr;
-  kf_tuning tune = {128, 0, 8, 0, 0};  // launch parameters (kf_set_tuning, kf_autotune_*)
+  kf_tuning tune = {128, 0, 8, 0, 0, 0};  // launch parameters (kf_set_tuning, kf_autotune_*)
 };
 
 namespace kfi {
@@ -142,9 +143,18 @@ struct FitF64Args {
   int first, last;
 };
 
+// Tensor maps of one staged layer step (kf_fit.cu, fit_layer_stage_kernel).
+struct FitStageMaps {
+  CUtensorMap par, lo, cov, hit;
+};
+
 // kernel launchers (kf_fit.cu)
 // block: threads per block, 64 or 128 (kf_tuning.fit_block)
 cudaError_t launch_fit_layer(const FitLayerArgs& a, int block, cudaStream_t st);
+// staged form (kf_tuning.fit_stage): false from make_stage_maps when the
+// batch's layout does not allow it (the caller then launches fit_layer_kernel)
+bool make_stage_maps(const FitLayerArgs& a, FitStageMaps* m);
+cudaError_t launch_fit_layer_stage(const FitLayerArgs& a, const FitStageMaps& m, int num_sms, cudaStream_t st);
 cudaError_t launch_fit_fused(const FitFusedArgs& a, cudaStream_t st, bool upd64 = false);
 cudaError_t launch_fit_f64(const FitF64Args& a, cudaStream_t st);
 

@@ -20,7 +20,8 @@ namespace {
 bool valid_tuning(const kf_tuning& t) {
   return (t.fit_block == 64 || t.fit_block == 128) && (t.build_hit_tile == 0 || t.build_hit_tile == 512) &&
          (t.build_list_width == 4 || t.build_list_width == 8) && (t.build_scan == 0 || t.build_scan == 1 || ((t.build_scan == 2 || t.build_scan == 3) && t.build_hit_tile == 0)) &&
-         (t.fit_chunk == 0 || t.fit_chunk == 262144 || t.fit_chunk == 524288 || t.fit_chunk == 1048576);
+         (t.fit_chunk == 0 || t.fit_chunk == 262144 || t.fit_chunk == 524288 || t.fit_chunk == 1048576) &&
+         (t.fit_stage == 0 || t.fit_stage == 1);
 }
 
 // Mean time of `reps` calls of fn after one untimed call; < 0 on failure
@@ -93,14 +94,17 @@ int kf_autotune_fit(kf_ctx* ctx, const kf_tracks* seeds, const kf_track_hits* hi
                     int32_t* status, void* stream, kf_tuning* chosen) {
   if (!ctx) return KF_EINVAL;
   std::vector<kf_tuning> cands;
-  for (int b : {64, 128})
-    for (int chunk : {0, 262144, 524288, 1048576}) {
-      if (chunk > 0 && seeds && chunk >= seeds->n) continue;  // one chunk: the same as 0
-      kf_tuning t = ctx->tune;
-      t.fit_block = b;
-      t.fit_chunk = chunk;
-      cands.push_back(t);
-    }
+  for (int stage : {0, 1})
+    for (int b : {64, 128})
+      for (int chunk : {0, 262144, 524288, 1048576}) {
+        if (chunk > 0 && seeds && chunk >= seeds->n) continue;  // one chunk: the same as 0
+        if (stage == 1 && b != 64) continue;                     // the staged kernel has its own blocks
+        kf_tuning t = ctx->tune;
+        t.fit_block = b;
+        t.fit_chunk = chunk;
+        t.fit_stage = stage;
+        cands.push_back(t);
+      }
   return autotune(ctx, stream, cands, [&] { return kf_fit(ctx, seeds, hits, out, chi2, status, stream); }, chosen);
 }
 

@@ -11,7 +11,8 @@ from fitutil import gpu_fit
 
 pytestmark = pytest.mark.gpu
 
-DEFAULT = {"fit_block": 128, "build_hit_tile": 0, "build_list_width": 8, "build_scan": 0, "fit_chunk": 0}
+DEFAULT = {"fit_block": 128, "build_hit_tile": 0, "build_list_width": 8, "build_scan": 0, "fit_chunk": 0,
+           "fit_stage": 0}
 BUILD_KEYS = ("par", "cov", "chi2", "nhits", "status", "hits", "n_cands", "cand_hits", "cand_chi2", "cand_nhits")
 
 
@@ -31,20 +32,24 @@ def test_tuning_defaults_and_validation(cuda_ctx_factory):
     assert kf.kf_get_tuning(ctx) == DEFAULT
     kf.kf_set_tuning(ctx, 64, 512, 4, 1, 524288)
     assert kf.kf_get_tuning(ctx) == {"fit_block": 64, "build_hit_tile": 512, "build_list_width": 4, "build_scan": 1,
-                                     "fit_chunk": 524288}
+                                     "fit_chunk": 524288, "fit_stage": 0}
 
 
-@pytest.mark.parametrize("n", [7001, 64])
+@pytest.mark.parametrize("n", [7001, 64, 40_000])
 def test_fit_block_sizes_bitwise(cuda_ctx_factory, n):
+    """Block sizes 64 and 128, and the staged layer kernel (tensor copies of
+    32-track tiles; batches not a multiple of 32 take the plain kernel): the
+    same bits."""
     from paper_1605_05508_gb300 import kf
     det = S.barrel()
     ctx = cuda_ctx_factory(det.radii)
     ev = S.make_fit_batch(91 + n, n, det, pt_range=(0.3, 10.0))
     res = []
-    for b in (64, 128):
-        kf.kf_set_tuning(ctx, b, 0, 8)
+    for b, stage in ((64, 0), (128, 0), (64, 1)):
+        kf.kf_set_tuning(ctx, b, 0, 8, 0, 0, stage)
         res.append(gpu_fit(ctx, ev.seeds, ev.hits.xyz, ev.hits.valid, "graph"))
     _same(res[0], res[1], ("par", "cov", "chi2", "status"))
+    _same(res[0], res[2], ("par", "cov", "chi2", "status"))
     # the autotuner keeps one of the two and gives the same bits
     t = gpu_fit(ctx, ev.seeds, ev.hits.xyz, ev.hits.valid, "autotune")
     _same(res[0], t, ("par", "cov", "chi2", "status"))
@@ -63,6 +68,14 @@ def test_fit_l2_chunks_bitwise(cuda_ctx_factory):
         kf.kf_set_tuning(ctx, 64, 0, 8, 0, chunk)
         res.append(gpu_fit(ctx, ev.seeds, ev.hits.xyz, ev.hits.valid, "graph"))
     _same(res[0], res[1], ("par", "cov", "chi2", "status"))
+    # the staged kernel over the same chunks (600 000 tracks: every chunk a multiple of 32)
+    sub = S.Seeds(ev.seeds.par[:, :600_000], ev.seeds.cov[:, :600_000], ev.seeds.charge[:600_000])
+    hx, hv = ev.hits.xyz[:, :, :600_000], ev.hits.valid[:, :600_000]
+    kf.kf_set_tuning(ctx, 64, 0, 8, 0, 0)
+    ref = gpu_fit(ctx, sub, hx, hv, "graph")
+    for chunk in (0, 262144):
+        kf.kf_set_tuning(ctx, 64, 0, 8, 0, chunk, 1)
+        _same(ref, gpu_fit(ctx, sub, hx, hv, "graph"), ("par", "cov", "chi2", "status"))
 
 
 def _batches():
