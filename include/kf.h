@@ -308,11 +308,11 @@ int kf_get_tuning(const kf_ctx *ctx, kf_tuning *out);
 int kf_set_tuning(kf_ctx *ctx, const kf_tuning *t);
 
 /* Autotuner of kf_fit: runs kf_fit on the caller's arguments once per
- * (fit_block, fit_chunk) value (one untimed call, then three timed with CUDA events on
- * `stream`, which is synchronised), keeps the fastest in the context and
- * writes the context's tuning to *chosen (may be NULL).  The outputs hold the
- * result of the last call, identical for every value.  Errors: those of
- * kf_fit. */
+ * (fit_stage, fit_block, fit_chunk) value (one untimed call, then three timed with CUDA
+ * events on `stream`, which is synchronised), keeps the fastest in the context (a
+ * setting must beat the best so far by 2 % to replace it; the simplest come first)
+ * and writes the context's tuning to *chosen (may be NULL).  The outputs hold the
+ * result of the last call, identical for every value.  Errors: those of kf_fit. */
 int kf_autotune_fit(kf_ctx *ctx, const kf_tracks *seeds, const kf_track_hits *hits, kf_tracks *out,
                     float *chi2, int32_t *status, void *stream, kf_tuning *chosen);
 

@@ -48,7 +48,11 @@ float time_calls(kf_ctx* ctx, cudaStream_t st, Fn&& fn, int reps, int* rc) {
   return *rc ? -1.f : ms / float(reps);
 }
 
-// Try every setting in `cands` (applied with kf_set_tuning), keep the fastest.
+// Try every setting in `cands` (applied with kf_set_tuning), keep the fastest:
+// a setting replaces the best so far only when it is kMargin faster, so among
+// settings that time alike (within the noise of three calls) the first one --
+// the candidates are listed simplest first -- is kept, and repeated runs agree.
+constexpr float kMargin = 0.02f;
 template <typename Fn>
 int autotune(kf_ctx* ctx, void* stream, const std::vector<kf_tuning>& cands, Fn&& fn, kf_tuning* chosen) {
   const kf_tuning saved = ctx->tune;
@@ -63,7 +67,7 @@ int autotune(kf_ctx* ctx, void* stream, const std::vector<kf_tuning>& cands, Fn&
       ctx->tune = saved;
       return rc;
     }
-    if (best < 0.f || ms < best) {
+    if (best < 0.f || ms < best * (1.f - kMargin)) {
       best = ms;
       best_t = t;
     }
