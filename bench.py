@@ -317,7 +317,8 @@ def run_ours(a):
     traffic = ncu_traffic(n)
     kname = "fit_layer_stage_kernel" if tuning.get("fit_stage") else f"fit_layer_kernel<{tuning['fit_block']}>"
     roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": traffic if chunks == 1 else None, "peak_kind": peak_kind,
+            "frac": achieved / peak, "traffic": traffic if chunks == 1 and not tuning.get("fit_stage") else None,
+            "peak_kind": peak_kind,
             "algorithmic_bytes_per_track_layer": bpt, "launch_us": launch_s * 1e6}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
