@@ -94,3 +94,35 @@ def test_binding_constants_match_the_header():
     for name, value in mirror.items():
         assert name in defs, name
         assert defs[name] == value, (name, defs[name], value)
+
+
+def test_binding_structures_match_the_header(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets the
+    C compiler gives the header's struct of the same name (a plain C program
+    built from include/kf.h prints them)."""
+    import shutil
+    from paper_1605_05508_gb300 import kf
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    structs = [getattr(kf, n) for n in ("kf_config", "kf_tracks", "kf_tracks_f64", "kf_track_hits", "kf_layer_hits",
+                                        "kf_layer_hit_bins", "kf_build_result", "kf_serve_config", "kf_event",
+                                        "kf_event_result", "kf_serve_stats", "kf_tuning")]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "kf.h"', "int main(void) {"]
+    for st in structs:
+        lines.append(f'  printf("{st.__name__} size %zu\\n", sizeof({st.__name__}));')
+        for f, *_ in st._fields_:
+            lines.append(f'  printf("{st.__name__} {f} %zu\\n", offsetof({st.__name__}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        name, field, value = ln.split()
+        got[(name, field)] = int(value)
+    for st in structs:
+        assert got[(st.__name__, "size")] == ctypes.sizeof(st), st.__name__
+        for f, *_ in st._fields_:
+            assert got[(st.__name__, f)] == getattr(st, f).offset, (st.__name__, f)
