@@ -67,7 +67,8 @@ struct BuildStepArgs {
   const BuildSlot* slots;  // device table
   int n_slots, max_cands;
   float a_scale, v0, v1, v2, cut;
-  float mass;  // particle mass of the scattering model
+  float mass;            // particle mass of the scattering model
+  int pack_seeds;        // candidate-packed layouts: seeds per block (<= the block's threads; 0: as many)
 };
 
 struct BuildInitArgs {

@@ -632,6 +632,7 @@ static void scheduler(Serve* sv) {
       a.v2 = sv->ctx->cfg.sigma_z_cm * sv->ctx->cfg.sigma_z_cm;
       a.cut = sv->ctx->cfg.chi2_cut;
       a.mass = sv->ctx->mass;
+      a.pack_seeds = 0;  // each event's blocks by build_step_blocks
       if (e == cudaSuccess)
         e = launch_build_step(a, blocks, sv->stream, sv->tune.build_hit_tile, sv->tune.build_list_width, scan);
       for (Request* r : stepping) r->layer++;
