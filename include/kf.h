@@ -348,8 +348,8 @@ typedef struct {
     int64_t pack_min_seeds;     /* with a candidate-packed build_scan (2, 3) in the context's
                                    tuning: a step launch uses it only when the resident events
                                    being stepped hold at least this many seeds, else the grouped
-                                   per-lane layout (same results; the packed blocks of a small
-                                   step would not fill the GPU).  0: automatic (SMs x 640),
+                                   per-lane layout (same results; a small packed step puts too
+                                   few parents on a block).  0: automatic (SMs x 400),
                                    1: always packed.  >= 0 */
 } kf_serve_config;
 

@@ -1014,22 +1014,9 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
   }
   const float v0 = ctx->cfg.sigma_xy_cm * ctx->cfg.sigma_xy_cm;
   const float v2 = ctx->cfg.sigma_z_cm * ctx->cfg.sigma_z_cm;
-  int grid = build_step_blocks(S, ctx->tune.build_scan);
-  // Candidate-packed layouts with more than two candidates a seed: the seeds
-  // are spread so that the grid is a whole number of waves of resident
-  // blocks (a block's several rounds take about equal time, so a last partial
-  // wave would leave most SMs idle at the end of every layer step).  With one
-  // or two candidates a block's single round is short and a full block of
-  // seeds keeps its threads busier (measured: N = 6 2.49 against 2.58 ms,
-  // N = 1 0.73 against 0.66 ms spread).
-  int pack_seeds = 0;
-  if (ctx->tune.build_scan >= 2 && max_cands > 2 && ctx->num_sms > 0) {
-    const int per_block = ctx->tune.build_scan == 2 ? kPackSeeds : kPackSeeds / 2;
-    const int64_t wave = int64_t(ctx->num_sms) * kBuildBlocksPerSM * (kPackSeeds / per_block);
-    const int64_t waves = (grid + wave - 1) / wave;
-    pack_seeds = int((S + waves * wave - 1) / (waves * wave));
-    grid = int((S + pack_seeds - 1) / pack_seeds);
-  }
+  // candidate-packed steps: seeds spread over whole waves of blocks (build_pack_seeds)
+  const int pack_seeds = build_pack_seeds(S, ctx->tune.build_scan, max_cands, ctx->num_sms);
+  const int grid = pack_seeds > 0 ? int((S + pack_seeds - 1) / pack_seeds) : build_step_blocks(S, ctx->tune.build_scan);
   // one slot (the whole batch) per layer launch; the table goes to device
   // scratch in one copy (the host array is consumed before the call returns)
   const int rm_buffers = rank_major_buffers(max_cands, L);

@@ -119,6 +119,20 @@ inline int build_step_blocks(int64_t S, int scan) {
   const int per_block = scan == 2 ? kPackSeeds : scan == 3 ? kPackSeeds / 2 : kBuildThreads / kGroup;
   return int((S + per_block - 1) / per_block);
 }
+
+// Candidate-packed steps that keep more than two candidates a seed: seeds per
+// block so that `seeds` spread over a whole number of waves of resident blocks
+// (a block's several rounds take about equal time, so a last partial wave
+// would leave most SMs idle at the end of the step); 0 otherwise (one or two
+// candidates: a block's single round is short and a full block of seeds keeps
+// its threads busier).
+inline int build_pack_seeds(int64_t seeds, int scan, int max_cands, int num_sms) {
+  if (scan < 2 || max_cands <= 2 || num_sms <= 0 || seeds <= 0) return 0;
+  const int per_block = scan == 2 ? kPackSeeds : kPackSeeds / 2;
+  const int64_t wave = int64_t(num_sms) * kBuildBlocksPerSM * (kPackSeeds / per_block);
+  const int64_t waves = ((seeds + per_block - 1) / per_block + wave - 1) / wave;
+  return int((seeds + waves * wave - 1) / (waves * wave));
+}
 cudaError_t launch_build_init(const BuildInitArgs& a, cudaStream_t st);
 cudaError_t launch_build_final(const BuildFinalArgs& a, cudaStream_t st);
 

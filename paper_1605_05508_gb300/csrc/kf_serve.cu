@@ -607,19 +607,21 @@ static void scheduler(Serve* sv) {
         ht[i] = slot_of(sv, stepping[i]);
         seeds += ht[i].S;
       }
-      // A packed step whose blocks do not fill the GPU once (by default fewer
-      // seeds than SMs x resident blocks x 128) runs its rounds on too few
-      // SMs: the grouped layout, with 8 lanes per seed and 8x the blocks,
-      // ends such a small step sooner (the same bits either way).
+      // A packed step spreads its seeds over one wave of resident blocks at
+      // least; with fewer than about 80 seeds a block (by default: SMs x
+      // resident blocks x 80 seeds) a block's rounds hold too few parents and
+      // the grouped layout, 8 lanes per seed, ends such a small step sooner
+      // (the same bits either way).
       int scan = sv->tune.build_scan;
       const int64_t pack_min = sv->cfg.pack_min_seeds > 0
                                    ? sv->cfg.pack_min_seeds
-                                   : int64_t(sv->ctx->num_sms) * kBuildBlocksPerSM * kBuildThreads;
+                                   : int64_t(sv->ctx->num_sms) * kBuildBlocksPerSM * 80;
       if (scan >= 2 && seeds < pack_min) scan = 0;
+      const int pack_seeds = build_pack_seeds(seeds, scan, sv->cfg.max_cands, sv->ctx->num_sms);
       int blocks = 0;
       for (size_t i = 0; i < stepping.size(); ++i) {
         ht[i].block_begin = blocks;
-        blocks += build_step_blocks(ht[i].S, scan);
+        blocks += pack_seeds > 0 ? int((ht[i].S + pack_seeds - 1) / pack_seeds) : build_step_blocks(ht[i].S, scan);
       }
       BuildSlot* dt = sv->d_table + size_t(ring) * KF_MAX_SLOTS;
       e = cudaMemcpyAsync(dt, ht, sizeof(BuildSlot) * stepping.size(), cudaMemcpyHostToDevice, sv->stream);
@@ -632,7 +634,7 @@ static void scheduler(Serve* sv) {
       a.v2 = sv->ctx->cfg.sigma_z_cm * sv->ctx->cfg.sigma_z_cm;
       a.cut = sv->ctx->cfg.chi2_cut;
       a.mass = sv->ctx->mass;
-      a.pack_seeds = 0;  // each event's blocks by build_step_blocks
+      a.pack_seeds = pack_seeds;
       if (e == cudaSuccess)
         e = launch_build_step(a, blocks, sv->stream, sv->tune.build_hit_tile, sv->tune.build_list_width, scan);
       for (Request* r : stepping) r->layer++;
