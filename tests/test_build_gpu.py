@@ -208,3 +208,23 @@ def test_build_segment_beyond_the_hit_id_limit(cuda_ctx_factory):
             np.testing.assert_array_equal(g[k], h[k], err_msg=f"layout {layout} {k}")
         assert np.all(g["hits"][:, 0] < lim) and np.mean(g["nhits"]) > 5.0
     kf.kf_set_tuning(ctx, 128, 0, 8, 0)
+
+
+@pytest.mark.parametrize("n_seeds", [1, 3, 129])
+def test_build_tiny_batches_every_layout(cuda_ctx_factory, n_seeds):
+    """A batch of 1, 3 or 129 seeds (fewer than a block of any layout, and one
+    past a packed block): every thread layout gives the oracle-checked bits of
+    the grouped per-lane one."""
+    from paper_1605_05508_gb300 import kf
+    det = S.barrel()
+    ctx = cuda_ctx_factory(det.radii)
+    batch = S.make_build_batch(1900 + n_seeds, 1, n_seeds)
+    kf.kf_set_tuning(ctx, 128, 0, 8, 0)
+    ref = gpu_build(ctx, batch, 6, want_cands=False)
+    _check_build(batch, ref, oracle_build(batch, 6), label=f"{n_seeds} seeds")
+    for scan in (1, 2, 3):
+        kf.kf_set_tuning(ctx, 128, 0, 8, scan)
+        g = gpu_build(ctx, batch, 6, want_cands=False)
+        for k in ("par", "chi2", "nhits", "status", "hits"):
+            np.testing.assert_array_equal(g[k], ref[k], err_msg=f"layout {scan} {k}")
+    kf.kf_set_tuning(ctx, 128, 0, 8, 0)
