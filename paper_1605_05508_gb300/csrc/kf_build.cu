@@ -92,14 +92,21 @@ __device__ __forceinline__ void hit_window(const float p[6], const float lo[3], 
   const float wt = sqrtf(Args.cut * fmaxf(Stt, 0.f));
   const float wn = sqrtf(Args.cut * fmaxf(Snn, 0.f));
   const float wz = sqrtf(Args.cut * fmaxf(s22, 0.f));
-  // phi bins: |dphi| <= atan(wt / (R - wn)), one bin of margin each side
-  const float rin = R - wn;
+  // A hit with chi2 < cut lies within wt of the prediction along the tangent,
+  // wn along the normal and wz in z (chi2 >= (u.r)^2 / u^T S u for any unit
+  // u), so its distance from the axis is between R - wn and
+  // sqrt((R + wn)^2 + wt^2) and its phi within atan(wt / (R - wn)) of the
+  // prediction's.  The bounds are widened by 0.1 % plus a small absolute
+  // term -- far above the float rounding of the window, of the chi2 and of
+  // the hits' own bins -- and cover exactly the bins they reach.
+  constexpr float kWiden = 1.001f;
+  const float rin = R - wn * kWiden;
   const float phic = atan2f(Y, X);
-  const float dphi = (rin > 0.5f * R && wt < rin) ? atanf(wt / rin) : 10.f;
+  const float dphi = (rin > 0.5f * R && wt * kWiden < rin) ? atanf(wt * kWiden / rin) * kWiden + 1e-6f : 10.f;
   if (dphi < 1.f && phic >= -kPi && phic <= kPi) {  // also false for NaN
     const float scale = float(KF_BIN_PHI) / (2.0f * kPi);
-    const int f0 = __float2int_rd((phic - dphi + kPi) * scale) - 1;
-    const int f1 = __float2int_rd((phic + dphi + kPi) * scale) + 1;
+    const int f0 = __float2int_rd((phic - dphi + kPi) * scale);
+    const int f1 = __float2int_rd((phic + dphi + kPi) * scale);
     if (f1 - f0 + 1 < KF_BIN_PHI) {
       if (f0 < 0) {
         fa0 = f0 + KF_BIN_PHI;
@@ -115,16 +122,17 @@ __device__ __forceinline__ void hit_window(const float p[6], const float lo[3], 
       }
     }
   }
-  // eta bins: z within Z +- wz and the hit radius within R +- wn
+  // eta bins: z within Z +- wz over the hit radii above
   e0 = 0;
   e1 = KF_BIN_ETA - 1;
-  const float rlo = R - wn, rhi = R + wn;
+  const float rlo = R - wn * kWiden - 1e-5f;
+  const float rhi = sqrtf((R + wn) * (R + wn) + wt * wt) * kWiden + 1e-5f;
   if (rlo > 0.f) {
-    const float zlo = Z - wz, zhi = Z + wz;
+    const float zlo = Z - wz * kWiden - 1e-5f, zhi = Z + wz * kWiden + 1e-5f;
     const float tmin = zlo >= 0.f ? zlo / rhi : zlo / rlo;
     const float tmax = zhi >= 0.f ? zhi / rlo : zhi / rhi;
-    e0 = max(eta_bin(asinhf(tmin)) - 1, 0);
-    e1 = min(eta_bin(asinhf(tmax)) + 1, KF_BIN_ETA - 1);
+    e0 = eta_bin(asinhf(tmin));
+    e1 = eta_bin(asinhf(tmax));
   }
 }
 
