@@ -4,7 +4,7 @@ bins): equal results also show that the chi2 window never drops a hit."""
 import numpy as np
 import pytest
 
-from buildutil import classify, gpu_build, oracle_build
+from buildutil import classify, gpu_build, oracle_build, oracle_seed_fit
 from fitutil import to_dev
 from paper_1605_05508_gb300 import synth as S
 
@@ -228,3 +228,49 @@ def test_build_tiny_batches_every_layout(cuda_ctx_factory, n_seeds):
         for k in ("par", "chi2", "nhits", "status", "hits"):
             np.testing.assert_array_equal(g[k], ref[k], err_msg=f"layout {scan} {k}")
     kf.kf_set_tuning(ctx, 128, 0, 8, 0)
+
+
+@pytest.mark.parametrize("tile,layout", [(0, 0), (512, 0), (0, 2)])
+def test_window_holds_hits_on_the_chi2_boundary(cuda_ctx_factory, tile, layout):
+    """Hits placed where each seed's chi2 = 0.99 cut ellipse touches the edges
+    of its window (r = sqrt(0.99 cut / u^T S u) S u for u = +-t, +-n, +-z at
+    the oracle's prediction on the first building layer) are all found: with
+    one building layer and 8 kept candidates, every one of them heads a kept
+    candidate, on the GPU (grouped, grouped with staged hits, packed) as in
+    the oracle."""
+    import oracle as O
+    from paper_1605_05508_gb300 import kf
+    from fitutil import f32
+    det = S.barrel()
+    ctx = cuda_ctx_factory(det.radii, max_cands=8)
+    batch = S.make_build_batch(2024, 1, 60, noise_factor=0.0)
+    l4 = batch.build_layers[0]
+    n0 = int(batch.layer_off[1] - batch.layer_off[0])
+    fit = oracle_seed_fit(batch)
+    R = f32(det.radii[l4])
+    V = np.diag([f32(det.sigma_xy) ** 2, f32(det.sigma_xy) ** 2, f32(det.sigma_z) ** 2])
+    extra, owner = [], []
+    for s in range(batch.seeds.par.shape[1]):
+        a = float(batch.seeds.charge[s]) * 0.00299792458 * f32(det.bz)
+        x1, J, _, st = O.propagate(fit["par"][s], a, R)
+        if st:
+            continue
+        Sm = O.transport_cov(J, fit["cov"][s])[:3, :3] + V
+        rr = np.hypot(x1[0], x1[1])
+        t, nn = np.array([-x1[1], x1[0], 0.0]) / rr, np.array([x1[0], x1[1], 0.0]) / rr
+        for u in (t, -t, nn, -nn, np.array([0.0, 0.0, 1.0]), np.array([0.0, 0.0, -1.0])):
+            extra.append(x1[:3] + np.sqrt(0.99 * 30.0 / (u @ Sm @ u)) * (Sm @ u))
+            owner.append(s)
+    owner = np.array(owner)
+    assert len(owner) >= 6 * 50
+    batch.build_layers = (l4,)
+    batch.layer_xyz = np.ascontiguousarray(np.concatenate([batch.layer_xyz[:, :n0], np.array(extra, np.float32).T], 1))
+    batch.layer_off = np.array([0, batch.layer_xyz.shape[1]], np.int64)
+    kf.kf_set_tuning(ctx, 128, tile, 8, layout)
+    g = gpu_build(ctx, batch, 8)
+    kf.kf_set_tuning(ctx, 128, 0, 8, 0)
+    r = oracle_build(batch, 8)
+    for res, name in ((g, "gpu"), (r, "oracle")):
+        cand_hits = res["cand_hits"][:, :, 0] if name == "gpu" else res["hits"][:, :, 0]
+        for k, s in enumerate(owner):
+            assert n0 + k in set(cand_hits[s].tolist()), (name, s, k)
