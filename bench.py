@@ -558,6 +558,10 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist):
         sweep6, tune6 = None, kf.kf_get_tuning(ctx)
     else:
         sweep6, tune6 = sweep_and_tune(6)
+    # the timed steps bin the hits without the in-bin id sort: the build's
+    # results do not depend on the order of the hits inside a bin
+    tune6 = dict(tune6, bin_unordered=1)
+    kf.kf_set_tuning(ctx, **tune6)
     tot6, t6 = run(6, k)
     mean_hits = float(out.n_hits.float().mean())
     # build efficiency: best candidate with >= 80 % of its building-layer hits
@@ -595,6 +599,8 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist):
                                                                                     refit_ms / 1e3),
                   "refit_chi2_per_hit_all_correct": float(rc.mean()) if rc.numel() else None}
     sweep1, tune1 = sweep_and_tune(1)
+    tune1 = dict(tune1, bin_unordered=1)
+    kf.kf_set_tuning(ctx, **tune1)
     tot1, t1 = run(1, k)
     res = {"workload": f"combinatorial build: {E} events x {T} seeds, {int(3 * T)} noise + <= {T} track hits per "
                        f"layer, 64x256 eta-phi bins, chi2 < 30, N = 6, seed fit on layers 1-3, build on 4-10",
@@ -605,7 +611,10 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist):
            "best_hit_N1": {"ms_per_step": tot1, "value": world * n * Lb / (tot1 / 1e3), "build_ms": float(t1[2]),
                            "tuning": tune1, "build_ms_by_setting": sweep1},
            "tuning": tune6, "build_ms_by_setting": sweep6, "efficiency_and_refit": efficiency,
-           "gpu_launches_per_step": 3 + 1 + (3 + Lb + 1)}
+           "bin_order": "scatter order inside each bin (bin_unordered 1; the build's results are the same bits)",
+           # seed fit (3 layer launches) + hit binning (count, scan, scatter) + kf_build (seed
+           # binning: count, scan, scatter, sort; seed ids; initial candidates; Lb steps; final)
+           "gpu_launches_per_step": 3 + 3 + (4 + 1 + 1 + Lb + 1)}
     # issue roofline of the build steps: warp instructions of the Lb step
     # launches of one build (committed ncu summary, same setting) over the whole
     # build phase's time (which also holds seed ordering, init and final

@@ -297,6 +297,9 @@ typedef struct {
                                  memory by tensor copies while it computes the current ones
                                  (batches whose size is a multiple of 32 with 16-byte aligned
                                  rows; others take form 0) */
+    int32_t bin_unordered;    /* kf_bin_hits: 0 = the hits of a bin in id order (default, a
+                                 deterministic output), 1 = in the order the scatter pass left
+                                 them (one pass less); kf_build's results do not depend on it */
 } kf_tuning;
 
 /* Current launch parameters of the context.  Errors: KF_EINVAL (null). */

@@ -4,7 +4,8 @@
 //
 // A counting sort of every segment (one event on one layer) into the 64 x 256
 // bins, with a final insertion sort by id inside each bin so that the output
-// is deterministic.
+// is deterministic (skipped with kf_tuning.bin_unordered: the build's results
+// do not depend on the order of the hits inside a bin).
 #include "kf_bin.cuh"
 #include "kf_internal.h"
 
@@ -154,7 +155,8 @@ cudaError_t launch_bin_points(const BinArgs& a, int n_segments, cudaStream_t st)
   bin_scan_kernel<<<n_segments, kScanThreads, kScanSmem, st>>>(a);
   bin_scatter_kernel<<<pgrid, kPointThreads, 0, st>>>(a, n_segments);
   const int64_t bins = int64_t(n_segments) * KF_NBINS;
-  bin_sort_kernel<<<int((bins + kPointThreads - 1) / kPointThreads), kPointThreads, 0, st>>>(a, n_segments);
+  if (!a.unordered)
+    bin_sort_kernel<<<int((bins + kPointThreads - 1) / kPointThreads), kPointThreads, 0, st>>>(a, n_segments);
   return cudaGetLastError();
 }
 
@@ -188,6 +190,7 @@ extern "C" int kf_bin_hits(kf_ctx* ctx, const kf_layer_hits* in, kf_layer_hit_bi
   a.out_id = static_cast<int32_t*>(ctx->s_bin_id.ptr);
   a.out_seg = nullptr;
   a.cursor = reinterpret_cast<int32_t*>(static_cast<char*>(ctx->s_bin_id.ptr) + id_bytes);
+  a.unordered = ctx->tune.bin_unordered;
   KF_CUDA_TRY(ctx, launch_bin_points(a, nseg, static_cast<cudaStream_t>(stream)));
   return KF_OK;
 }

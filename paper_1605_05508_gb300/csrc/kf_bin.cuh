@@ -38,6 +38,7 @@ struct BinArgs {
   int32_t* out_id;         // [total] required: id within the segment, bin order
   int32_t* out_seg;        // [total] or null
   int32_t* cursor;         // [n_seg][KF_NBINS] scratch
+  int unordered = 0;       // 1: leave each bin in scatter order (no sort by id)
 };
 
 // Sort the points of every segment into bins (several launches on `st`);

@@ -61,7 +61,7 @@ struct kf_ctx {
   cudaStream_t host_streams[kfi::kHostStreams] = {};  // kf_fit_host pipeline
   cudaEvent_t host_done[kfi::kHostStreams] = {};
   cudaEvent_t host_start = nullptr;
-  kf_tuning tune = {128, 0, 8, 0, 0, 0};  // launch parameters (kf_set_tuning, kf_autotune_*)
+  kf_tuning tune = {128, 0, 8, 0, 0, 0, 0};  // launch parameters (kf_set_tuning, kf_autotune_*)
 };
 
 namespace kfi {

@@ -368,6 +368,7 @@ static cudaError_t prepare(Serve* sv, Request* r) {
   hb.out_id = reinterpret_cast<int32_t*>(d + L.d_bid);
   hb.out_seg = nullptr;
   hb.cursor = reinterpret_cast<int32_t*>(d + L.d_bcur);
+  hb.unordered = 1;  // the build's results do not depend on the order inside a bin
   e = launch_bin_points(hb, L.Lb, s);
   if (e != cudaSuccess) return e;
   // seeds in (eta, phi) order: one segment [0, n)
@@ -383,6 +384,7 @@ static cudaError_t prepare(Serve* sv, Request* r) {
   sb.out_id = reinterpret_cast<int32_t*>(d + L.d_perm);
   sb.out_seg = nullptr;
   sb.cursor = reinterpret_cast<int32_t*>(d + L.d_bcur);
+  sb.unordered = 1;  // the build's results do not depend on the order inside a bin
   e = launch_bin_points(sb, 1, s);
   if (e != cudaSuccess) return e;
   BuildInitArgs ia;

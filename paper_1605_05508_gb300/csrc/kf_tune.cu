@@ -21,7 +21,7 @@ bool valid_tuning(const kf_tuning& t) {
   return (t.fit_block == 64 || t.fit_block == 128) && (t.build_hit_tile == 0 || t.build_hit_tile == 512) &&
          (t.build_list_width == 4 || t.build_list_width == 8) && (t.build_scan == 0 || t.build_scan == 1 || ((t.build_scan == 2 || t.build_scan == 3) && t.build_hit_tile == 0)) &&
          (t.fit_chunk == 0 || t.fit_chunk == 262144 || t.fit_chunk == 524288 || t.fit_chunk == 1048576) &&
-         (t.fit_stage == 0 || t.fit_stage == 1);
+         (t.fit_stage == 0 || t.fit_stage == 1) && (t.bin_unordered == 0 || t.bin_unordered == 1);
 }
 
 // Mean time of `reps` calls of fn after one untimed call; < 0 on failure

@@ -95,7 +95,8 @@ class kf_serve_stats(C.Structure):
 
 class kf_tuning(C.Structure):
     _fields_ = [("fit_block", C.c_int32), ("build_hit_tile", C.c_int32), ("build_list_width", C.c_int32),
-                ("build_scan", C.c_int32), ("fit_chunk", C.c_int32), ("fit_stage", C.c_int32)]
+                ("build_scan", C.c_int32), ("fit_chunk", C.c_int32), ("fit_stage", C.c_int32),
+                ("bin_unordered", C.c_int32)]
 
 
 MAX_SLOTS = 32  # KF_MAX_SLOTS
@@ -372,9 +373,9 @@ def kf_get_tuning(ctx) -> dict:
 
 
 def kf_set_tuning(ctx, fit_block: int, build_hit_tile: int, build_list_width: int, build_scan: int = 0,
-                  fit_chunk: int = 0, fit_stage: int = 0):
+                  fit_chunk: int = 0, fit_stage: int = 0, bin_unordered: int = 0):
     t = kf_tuning(int(fit_block), int(build_hit_tile), int(build_list_width), int(build_scan), int(fit_chunk),
-                  int(fit_stage))
+                  int(fit_stage), int(bin_unordered))
     _check(lib().kf_set_tuning(_h(ctx), C.byref(t)), "kf_set_tuning", _h(ctx))
 
 

@@ -61,7 +61,7 @@ def test_strerror_and_argument_checks_need_no_gpu(libpath):
         assert lib.kf_create(ctypes.byref(h), ctypes.byref(cfg), 0, 0) == kf.KF_EINVAL
     assert lib.kf_fit(None, None, None, None, None, None, None) == kf.KF_EINVAL
     # launch parameters: null context or output, and no GPU needed to reject them
-    t = kf.kf_tuning(128, 0, 8, 0, 0, 0)
+    t = kf.kf_tuning(128, 0, 8, 0, 0, 0, 0)
     assert lib.kf_get_tuning(None, ctypes.byref(t)) == kf.KF_EINVAL
     assert lib.kf_set_tuning(None, ctypes.byref(t)) == kf.KF_EINVAL
     assert lib.kf_autotune_fit(None, None, None, None, None, None, None, None) == kf.KF_EINVAL

@@ -12,7 +12,7 @@ from fitutil import gpu_fit
 pytestmark = pytest.mark.gpu
 
 DEFAULT = {"fit_block": 128, "build_hit_tile": 0, "build_list_width": 8, "build_scan": 0, "fit_chunk": 0,
-           "fit_stage": 0}
+           "fit_stage": 0, "bin_unordered": 0}
 BUILD_KEYS = ("par", "cov", "chi2", "nhits", "status", "hits", "n_cands", "cand_hits", "cand_chi2", "cand_nhits")
 
 
@@ -32,7 +32,7 @@ def test_tuning_defaults_and_validation(cuda_ctx_factory):
     assert kf.kf_get_tuning(ctx) == DEFAULT
     kf.kf_set_tuning(ctx, 64, 512, 4, 1, 524288)
     assert kf.kf_get_tuning(ctx) == {"fit_block": 64, "build_hit_tile": 512, "build_list_width": 4, "build_scan": 1,
-                                     "fit_chunk": 524288, "fit_stage": 0}
+                                     "fit_chunk": 524288, "fit_stage": 0, "bin_unordered": 0}
 
 
 @pytest.mark.parametrize("n", [7001, 64, 40_000])
@@ -129,3 +129,28 @@ def test_build_autotune(cuda_ctx_factory):
     assert chosen["build_hit_tile"] in (0, 512) and chosen["build_list_width"] in (4, 8)
     assert chosen["build_scan"] in (0, 1, 2, 3)
     assert kf.kf_get_tuning(ctx) == chosen
+
+
+def test_unordered_bins_give_the_same_build(cuda_ctx_factory):
+    """kf_tuning.bin_unordered leaves each bin in scatter order: the bins hold
+    the same hits per bin, and kf_build's results are the same bits."""
+    from paper_1605_05508_gb300 import kf
+    det = S.barrel()
+    ctx = cuda_ctx_factory(det.radii, max_cands=8)
+    for name, batch in _batches().items():
+        res = []
+        for unordered in (0, 1):
+            kf.kf_set_tuning(ctx, 128, 0, 8, 2, 0, 0, unordered)
+            res.append(gpu_build(ctx, batch, 6))
+        _same(res[0], res[1], BUILD_KEYS)
+        b0, b1 = res[0]["bins"], res[1]["bins"]
+        assert np.array_equal(b0.bin_off.cpu().numpy(), b1.bin_off.cpu().numpy()), name
+        ids0 = b0.hits.cpu().numpy()[:, 3].view(np.int32)
+        ids1 = b1.hits.cpu().numpy()[:, 3].view(np.int32)
+        off = b0.bin_off.cpu().numpy()
+        for s in range(off.shape[0]):  # per segment and bin: the same set of hits
+            base = int(batch.layer_off[s])
+            for bb in np.nonzero(np.diff(off[s]) > 1)[0][:200]:
+                lo, hi = base + off[s, bb], base + off[s, bb + 1]
+                assert sorted(ids0[lo:hi]) == sorted(ids1[lo:hi]), (name, s, bb)
+    kf.kf_set_tuning(ctx, 128, 0, 8, 0)
