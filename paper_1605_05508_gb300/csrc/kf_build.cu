@@ -594,10 +594,19 @@ __global__ void __launch_bounds__(NT, kBuildBlocksPerSM * kBuildThreads / NT) bu
   __shared__ int s_seg[NT];      // per seed: hit segment (event, layer)
   __shared__ int64_t s_h0[NT];   // per seed: first hit of the segment
   const int t = threadIdx.x;
+  // one layer step, or (Args.layers > 1) every layer of the batch in turn for
+  // the block's seeds: a seed's candidates are read and written by its block
+  // only, so the block needs no other block between its layers
+  const int n_steps = Args.layers > 1 ? Args.layers : 1;
+  for (int li = 0; li < n_steps; ++li) {
   if (t == 0) {
-    int sl = 0;
-    while (sl + 1 < Args.n_slots && int(blockIdx.x) >= Args.slots[sl + 1].block_begin) ++sl;
-    sD = Args.slots[sl];
+    if (Args.layers > 1) {
+      sD = Args.slots[li];
+    } else {
+      int sl = 0;
+      while (sl + 1 < Args.n_slots && int(blockIdx.x) >= Args.slots[sl + 1].block_begin) ++sl;
+      sD = Args.slots[sl];
+    }
   }
   __syncthreads();
   const BuildSlot& D = sD;
@@ -797,6 +806,8 @@ __global__ void __launch_bounds__(NT, kBuildBlocksPerSM * kBuildThreads / NT) bu
     }
     __syncthreads();  // the next round reuses the shared tables
     sa = sb;
+  }
+  __syncthreads();  // the next layer rewrites sD and the per-seed tables
   }
 }
 
@@ -1052,10 +1063,20 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
   }
   BuildSlot* dtable = reinterpret_cast<BuildSlot*>(base + b_perm + b_evt + 2 * b_cand + b_hp + b_hh);
   KF_CUDA_TRY(ctx, cudaMemcpyAsync(dtable, table.data(), sizeof(BuildSlot) * L, cudaMemcpyHostToDevice, s));
-  for (int l = 0; l < L; ++l) {
+  // Candidate-packed layouts take every block's seeds through consecutive
+  // layers in one launch -- but only over buffers of one layout: where the
+  // layout switches from rank-major to seed-major, a slot of one seed in one
+  // layout is a slot of another seed in the other, so a block writing the
+  // next buffer could overwrite what a block still on the previous layer
+  // reads in the same memory.  Layers up to the switch run one launch each.
+  // The grouped layouts launch once per layer.
+  const int first_fused = ctx->tune.build_scan >= 2 ? (rm_buffers > L ? 0 : std::min(L, rm_buffers)) : L;
+  for (int l = 0; l < (first_fused < L ? first_fused + 1 : L); ++l) {
+    const bool fused = l == first_fused;
     BuildStepArgs a;
     a.slots = dtable + l;
     a.n_slots = 1;
+    a.layers = fused ? L - l : 0;
     a.max_cands = max_cands;
     a.a_scale = float(kCLight * double(ctx->cfg.bz_tesla));
     a.v0 = v0;

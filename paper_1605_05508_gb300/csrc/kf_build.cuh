@@ -69,6 +69,8 @@ struct BuildStepArgs {
   float a_scale, v0, v1, v2, cut;
   float mass;            // particle mass of the scattering model
   int pack_seeds;        // candidate-packed layouts: seeds per block (<= the block's threads; 0: as many)
+  int layers;            // candidate-packed layouts: > 1 = `slots` are that many consecutive layers of
+                         // one batch and each block takes its seeds through all of them
 };
 
 struct BuildInitArgs {

@@ -637,6 +637,7 @@ static void scheduler(Serve* sv) {
       a.cut = sv->ctx->cfg.chi2_cut;
       a.mass = sv->ctx->mass;
       a.pack_seeds = pack_seeds;
+      a.layers = 0;  // events at different layers: one step each
       if (e == cudaSuccess)
         e = launch_build_step(a, blocks, sv->stream, sv->tune.build_hit_tile, sv->tune.build_list_width, scan);
       for (Request* r : stepping) r->layer++;

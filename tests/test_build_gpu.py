@@ -274,3 +274,33 @@ def test_window_holds_hits_on_the_chi2_boundary(cuda_ctx_factory, tile, layout):
         cand_hits = res["cand_hits"][:, :, 0] if name == "gpu" else res["hits"][:, :, 0]
         for k, s in enumerate(owner):
             assert n0 + k in set(cand_hits[s].tolist()), (name, s, k)
+
+
+def test_packed_layers_in_one_launch_match_with_skewed_blocks(cuda_ctx_factory):
+    """The packed layouts take each block's seeds through several layers in one
+    launch: with a dense first building layer (500 000 extra hits) blocks run
+    far apart in time, and the results stay the grouped layout's bits (a
+    block writing one layout's buffer while another still reads the other
+    layout's would show here)."""
+    from paper_1605_05508_gb300 import kf
+    det = S.barrel()
+    ctx = cuda_ctx_factory(det.radii)
+    b = S.make_build_batch(1779, 1, 300)
+    rng = np.random.default_rng(1780)
+    n0 = int(b.layer_off[1] - b.layer_off[0])
+    k = 500_000
+    R = det.radii[b.build_layers[0]]
+    phi = rng.uniform(0.0, 2.0 * np.pi, k)
+    ex = np.stack([R * np.cos(phi), R * np.sin(phi), rng.uniform(-20.0, 20.0, k)]).astype(np.float32)
+    b.layer_xyz = np.ascontiguousarray(np.concatenate([b.layer_xyz[:, :n0], ex, b.layer_xyz[:, n0:]], 1))
+    b.layer_off = b.layer_off.copy()
+    b.layer_off[1:] += k
+    res = {}
+    for layout in (0, 2, 3, 2):
+        kf.kf_set_tuning(ctx, 128, 0, 8, layout)
+        g = gpu_build(ctx, b, 6, want_cands=False)
+        if 0 in res:
+            for key in ("par", "chi2", "nhits", "status", "hits"):
+                np.testing.assert_array_equal(g[key], res[0][key], err_msg=f"layout {layout} {key}")
+        res[layout] = g
+    kf.kf_set_tuning(ctx, 128, 0, 8, 0)
