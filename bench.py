@@ -229,11 +229,12 @@ def profile_value(name, key, files=FIT_SOURCES):
     return float(kv[key])
 
 
-def ncu_traffic(n_tracks):
-    """DRAM bytes per fit-layer launch from the committed ncu summary, scaled to
-    n_tracks (traffic grows in proportion to the tracks of a launch); None if
-    absent or taken on a different kernel source."""
-    b = profile_value("fit_layer_kernel.traffic.txt", "dram_bytes_per_track")
+def ncu_traffic(n_tracks, staged=False):
+    """DRAM bytes per fit-layer launch (the plain-load or the staged kernel) from
+    the committed ncu summary, scaled to n_tracks (traffic grows in proportion to
+    the tracks of a launch); None if absent or taken on a different kernel source."""
+    name = "fit_layer_stage_kernel" if staged else "fit_layer_kernel"
+    b = profile_value(f"{name}.traffic.txt", "dram_bytes_per_track")
     return None if b is None else b * n_tracks
 
 
@@ -314,10 +315,10 @@ def run_ours(a):
     bpt = fit_bytes_per_track_layer(L, False, True, True)
     achieved = bpt * n / chunks / launch_s / 1e9
     peak, peak_kind = measured_peaks()
-    traffic = ncu_traffic(n)
+    traffic = ncu_traffic(n, bool(tuning.get("fit_stage")))
     kname = "fit_layer_stage_kernel" if tuning.get("fit_stage") else f"fit_layer_kernel<{tuning['fit_block']}>"
     roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": traffic if chunks == 1 and not tuning.get("fit_stage") else None,
+            "frac": achieved / peak, "traffic": traffic if chunks == 1 else None,
             "peak_kind": peak_kind,
             "algorithmic_bytes_per_track_layer": bpt, "launch_us": launch_s * 1e6}
 

@@ -23,7 +23,8 @@
 // sin(th)/a = (s/p) sinc(h) cos(h) and (1 - cos th)/a = (s/p) h sinc(h)^2
 // with h = th/2: no 1/a and no 1 - cos cancellation.
 // The path length s to radius R solves g(s) = x(s)^2 + y(s)^2 - R^2 = 0 by
-// Newton iterations from the straight-line guess.  The transport Jacobian is
+// Newton iterations from a guess that keeps the curvature terms to second
+// order (below).  The transport Jacobian is
 // the surface one, J = dF/dx0|_s - (dF/ds)(dg/dx0|_s)/(dg/ds).
 //
 // Compiles for the host too, so that the same source can be exercised off
@@ -234,12 +235,28 @@ KF_HD typename Lanes<T>::I propagate_lanes(T p[6], T lo[3], T C[21], T a, T R, t
     g0h = s2;
     g0l = ((e1 + e2) + ((b1 + b2) - b3)) + T(2.0f) * fma_t(x, xl, y * yl);
   }
-  // straight-line first guess in the transverse plane
+  // First guess from the transverse path t = s pT / p.  With u = pT/|pT|,
+  // n = (uy, -ux) and kappa = a / pT the transverse displacement is
+  // u sin(kappa t)/kappa + n (1 - cos(kappa t))/kappa, so
+  //   g(t) = G0 + 2 b t + A t^2 - (kappa^2 t^3 / 12)(4 b + t) + O(kappa^3),
+  // b = r0.u, A = 1 + kappa r0.n.  The quadratic's root, then one Newton
+  // step on the polynomial for the cubic and quartic terms (its slope at the
+  // root is 2 sqrt(disc)); the straight line (A = 1) where A is small, and no
+  // polynomial step near a tangent crossing.  The guess is a few microns off
+  // where the straight line is up to a millimetre off, so one Newton step
+  // below usually meets the tolerance.
   const T tx = px * ipt, ty = py * ipt;
   const T b = fma_t(x, tx, y * ty);
-  T disc = fma_t(b, b, -(g0h + g0l));
+  const T kap = a * ipt;
+  T A = fma_t(kap, fma_t(x, ty, -(y * tx)), T(1.0f));
+  A = sel(A > T(0.5f), A, T(1.0f));
+  T disc = fma_t(b, b, -(A * (g0h + g0l)));
   disc = sel(disc > T(0.0f), disc, T(0.0f));
-  T s = ((sqrt_t(disc) - b) * pmag) * ipt;
+  const T sq = sqrt_t(disc);
+  T t = (sq - b) * rcp_t(A);
+  const T corr = (((kap * kap) * ((t * t) * t)) * fma_t(T(4.0f), b, t)) * (T(1.0f / 24.0f) * rcp_t(sq));
+  t = sel(sq > fma_t(T(1e-3f), abs_t(b), T(1e-6f)), t + corr, t);
+  T s = (t * pmag) * ipt;
   // Safeguarded Newton on g(s) = |r0 + d(s)|^2 - R^2 = G0 + 2 r0.d + |d|^2,
   // the large terms summed error-free when the position is a float pair.
   // [lo, hi] brackets the first crossing: g < 0 on the way out below it; a
