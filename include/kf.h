@@ -235,8 +235,8 @@ typedef struct {
  * asc, hit id asc) and only the best max_cands are copied and updated.
  * max_cands = 1 is the best-hit approach.  The window is the set of bins
  * that a hit with chi2 < cut can fall in (chi2 >= (u.r)^2 / (u^T S u) for
- * every direction u), widened by one bin, so binning never changes the
- * result.  Seeds are processed in (eta, phi) bin order within each event.
+ * every direction u), each bound widened by 0.1 % plus 1e-6 rad / 1e-5 cm
+ * against rounding, so binning never changes the result.  Seeds are processed in (eta, phi) bin order within each event.
  *
  * seeds: [n_seeds] starting states at or inside the first build layer (the
  * seeds' charge is read); seeds of event e are seed_off[e] .. seed_off[e+1]

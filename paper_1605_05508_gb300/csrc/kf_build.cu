@@ -1,14 +1,15 @@
 // kf_build.cu -- combinatorial track building with the clone engine
 // (Cerati et al., Sec. 3).
 //
-// One launch per building layer.  An 8-lane group of a warp owns one seed;
-// lane k holds the seed's candidate of rank k (up to max_cands <= 8).  Per
-// layer each live lane
+// Grouped layouts: one launch per building layer.  An 8-lane group of a warp
+// owns one seed; lane k holds the seed's candidate of rank k (up to
+// max_cands <= 8).  Per layer each live lane
 //   1. propagates its candidate to the layer radius (kf::propagate),
 //   2. derives the hit window: chi2 >= (u.r)^2 / (u^T S u) for every unit u,
 //      so a hit with chi2 < cut lies within sqrt(cut u^T S u) of the
-//      prediction along the tangent, the normal and z; those bounds are
-//      mapped to eta x phi bins and widened by one bin,
+//      prediction along the tangent, the normal and z; those bounds, each
+//      widened by 0.1 % plus 1e-6 rad / 1e-5 cm against rounding, are mapped
+//      to eta x phi bins,
 //   3. computes the chi2 increment of every hit in the window and keeps its
 //      best children in a sorted register list (the bookkeeping list of the
 //      clone engine: parent, hit, chi2_tot, nHits -- no state is copied),
@@ -21,6 +22,9 @@
 //      propagation).
 // The hit history is kept as per-layer back-pointers (parent rank, hit id)
 // and resolved once at the end, instead of copying index arrays per child.
+// The candidate-packed step (below) computes the same per candidate with
+// threads assigned to live candidates, and takes a block's seeds through
+// several layers in one launch where the candidate buffers allow it.
 #include "kf_bin.cuh"
 #include "kf_build.cuh"
 #include "kf_internal.h"
