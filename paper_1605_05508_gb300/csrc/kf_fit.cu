@@ -5,14 +5,20 @@
 // Track fitting is the branch-free part of Kalman-filter tracking (Cerati et
 // al., Sec. 2): with the hit set fixed, every track runs propagate + update
 // over the layers.  Forms:
-//   fit_layer_kernel  one layer step over the whole batch (kf_fit replays one
-//                     launch per layer from a captured CUDA graph);
-//   fit_fused_kernel  all layers in one launch, the track held in registers
-//                     (also the mixed-precision form);
-//   fit_f64_kernel    the plain FP64 form, launched per event and per layer.
-// One track per thread, 24 resident warps per SM, plain coalesced row reads.
-// Staging the rows in shared memory (bulk copies per block or per warp, or
-// per-thread cp.async double buffering) measured no faster.
+//   fit_layer_kernel        one layer step over the whole batch (kf_fit
+//                           replays one launch per layer from a captured CUDA
+//                           graph), plain coalesced row reads;
+//   fit_layer_stage_kernel  the same step with each warp's next 32 tracks
+//                           copied into shared memory by 2-D tensor copies
+//                           while it computes the current ones (an autotuned
+//                           alternative, bitwise equal);
+//   fit_fused_kernel        all layers in one launch, the track held in
+//                           registers (also the mixed-precision form);
+//   fit_f64_kernel          the plain FP64 form, launched per event and per
+//                           layer.
+// One track per thread, 24 resident warps per SM in the layer step.  Other
+// stagings of the rows (bulk copies per block or per 32 tracks, per-thread
+// cp.async double buffering) measured slower than plain reads.
 #include <cudaTypedefs.h>
 
 #include <algorithm>
