@@ -567,14 +567,18 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist):
     mean_hits = float(out.n_hits.float().mean())
     # build efficiency: best candidate with >= 80 % of its building-layer hits
     # from its own track (truth of the generator)
-    hidx = out.hit_idx.cpu().numpy()
     seed_first = np.searchsorted(batch.seed_event, np.arange(E + 1))
     own = np.arange(n) - seed_first[batch.seed_event]
-    good = np.zeros(n, np.int64)
-    for b in range(Lb):
-        ok = hidx[b] >= 0
-        h = batch.layer_off[batch.seed_event * Lb + b] + hidx[b]
-        good[ok] += batch.layer_truth[h[ok]] == own[ok]
+
+    def correct_hits():
+        hidx = out.hit_idx.cpu().numpy()
+        good = np.zeros(n, np.int64)
+        for b in range(Lb):
+            ok = hidx[b] >= 0
+            h = batch.layer_off[batch.seed_event * Lb + b] + hidx[b]
+            good[ok] += batch.layer_truth[h[ok]] == own[ok]
+        return good
+    good = correct_hits()
     # re-fit of the built tracks over all 10 layers (kf_refit)
     ro = kf.Tracks(torch.empty((6, n), device=dev), torch.empty((21, n), device=dev), s.charge,
                    torch.empty((3, n), device=dev))
@@ -603,6 +607,20 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist):
     tune1 = dict(tune1, bin_unordered=1)
     kf.kf_set_tuning(ctx, **tune1)
     tot1, t1 = run(1, k)
+    # best-hit against the clone engine: build time and efficiency for each
+    # number of candidates kept per seed, each with the autotuner's setting
+    curve = []
+    for N in (1, 2, 3, 4, 6, 8):
+        tn = dict(kf.kf_autotune_build(ctx, fo, seed_off, bins, N, out, stream), bin_unordered=1)
+        kf.kf_set_tuning(ctx, **tn)
+        _, tN = run(N, k)
+        gN = correct_hits()
+        curve.append({"max_cands": N, "build_ms": float(tN[2]),
+                      "best_candidate_ge_80pct_correct": float(np.mean(gN >= 0.8 * Lb)),
+                      "all_hits_correct": float(np.mean(gN == Lb)),
+                      "mean_hits_found": float(out.n_hits.float().mean()),
+                      "setting": f"tile{tn['build_hit_tile']}_list{tn['build_list_width']}_"
+                                 f"{('lane', 'coop', 'packed128', 'packed64')[tn['build_scan']]}"})
     res = {"workload": f"combinatorial build: {E} events x {T} seeds, {int(3 * T)} noise + <= {T} track hits per "
                        f"layer, 64x256 eta-phi bins, chi2 < 30, N = 6, seed fit on layers 1-3, build on 4-10",
            "value": world * n * Lb / (tot6 / 1e3), "unit": "seed-layer steps/s", "ms_per_step": tot6,
@@ -612,6 +630,7 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist):
            "best_hit_N1": {"ms_per_step": tot1, "value": world * n * Lb / (tot1 / 1e3), "build_ms": float(t1[2]),
                            "tuning": tune1, "build_ms_by_setting": sweep1},
            "tuning": tune6, "build_ms_by_setting": sweep6, "efficiency_and_refit": efficiency,
+           "clone_engine_curve": curve,
            "bin_order": "scatter order inside each bin (bin_unordered 1; the build's results are the same bits)",
            # seed fit (3 layer launches) + hit binning (count, scan, scatter) + kf_build (seed
            # binning: count, scan, scatter, sort; seed ids; initial candidates; Lb steps; final)
