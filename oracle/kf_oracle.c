@@ -32,7 +32,9 @@
  *   orc_fit                 pinned: noise-free fit recovers truth, chi2 = 0.
  *   orc_build               pinned: exhaustive enumeration on tiny inputs.
  *   orc_scattering_q        pinned: symmetric, rank 2 with p in its null space,
- *                           trace 2 p^2 theta0^2; fits of tracks simulated
+ *                           trace 2 p^2 theta0^2 with theta0 from a golden table
+ *                           of the Highland formula (40-digit mpmath, written
+ *                           without this file or the generator); fits of tracks simulated
  *                           with scattering kinks have chi2 mean 3 and unit
  *                           pulls in every eta range (the incidence factor).
  */

@@ -3,12 +3,17 @@ multiple scattering into the trajectory's uncertainty) in the oracle.
 
 Pins: the layer's process noise is symmetric, of rank 2 with the momentum in
 its null space (the direction turns, |p| does not change), zero outside the
-momentum block, and its trace is 2 p^2 theta0^2 with the generator's theta0;
+momentum block, and its trace is 2 p^2 theta0^2 with theta0 from a golden
+table (tests/golden/highland_theta0.txt: the Highland formula with the
+Lynch-Dahl logarithm evaluated at 40 digits by a script that imports neither
+the oracle nor the generator), which pins the generator's theta0 too;
 fits of tracks simulated with scattering kinks (the generator turns the
 direction by Gaussian projected angles at every crossing) have chi2 mean 3
 per hit and unit pulls -- in the central and in the forward eta range, which
 pins the path-length (incidence) factor -- while the same fits without the
 process noise do not; zero material reduces to the plain fit exactly."""
+import os
+
 import numpy as np
 import pytest
 
@@ -39,6 +44,38 @@ def test_process_noise_structure():
     # thicker layer, more scattering; zero thickness, none
     x = np.array([30.0, 0.0, 1.0, 1.0, 0.1, 0.2])
     assert np.trace(O.scattering_q(x, 0.05)) > np.trace(O.scattering_q(x, 0.01)) > 0
+
+
+def _highland_rows():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "highland_theta0.txt")
+    rows = []
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            f = line.split()
+            rows.append((f[0], float(f[1]), float(f[2]), float(f[3]), float(f[4]), float(f[5])))
+    return rows
+
+
+def test_theta0_matches_the_golden_highland_table():
+    """Every row of the golden table: a state on a cylinder whose momentum makes
+    angle psi with the layer normal (turned about the normal by a row-dependent
+    azimuth, placed at a row-dependent phi); the oracle's Q has trace
+    2 p^2 theta0^2, and the generator's theta0 over the oblique path agrees."""
+    rows = _highland_rows()
+    assert len(rows) >= 200
+    for i, (name, p, m, t, psi_deg, th_ref) in enumerate(rows):
+        psi, alpha, phi = np.radians(psi_deg), 0.7 * i, 0.37 * i
+        nrm = np.array([np.cos(phi), np.sin(phi), 0.0])
+        ez = np.array([0.0, 0.0, 1.0])
+        tan = np.cross(ez, nrm)
+        u = np.cos(psi) * nrm + np.sin(psi) * (np.cos(alpha) * tan + np.sin(alpha) * ez)
+        R = 4.0 + 3.0 * (i % 13)
+        x = np.concatenate([R * nrm + np.array([0.0, 0.0, 5.0 - (i % 7)]), p * u])
+        Q = O.scattering_q(x, t, m)
+        th_orc = np.sqrt(np.trace(Q) / (2.0 * p * p))
+        assert th_orc == pytest.approx(th_ref, rel=1e-12), (name, p, m, t, psi_deg)
+        th_gen = S.highland_theta0(p, t / np.cos(psi), m)
+        assert float(th_gen) == pytest.approx(th_ref, rel=1e-12), (name, p, m, t, psi_deg)
 
 
 def _fit(ev, det, with_q=True):
