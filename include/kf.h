@@ -46,8 +46,11 @@ extern "C" {
                                tangent (dg/ds ~ 0); stops */
 #define KF_ST_NOT_PD 8      /* final covariance failed the positive-definite check */
 #define KF_ST_NO_HIT 16     /* at least one layer had no hit (propagated only) */
-#define KF_ST_DEVICE_TIMEOUT 64 /* a bounded wait for staged input gave up (never expected):
-                                 the track's results of that call are not valid */
+#define KF_ST_DEVICE_TIMEOUT 64 /* a bounded wait for staged input gave up (never expected).
+                                 If any track of a call carries it, treat every result of
+                                 that call as invalid: a block whose final drain wait also
+                                 gave up may have exited with a copy still in flight into
+                                 shared memory that a later block then uses */
 #define KF_ST_STOPPED (KF_ST_NOT_REACHED | KF_ST_NEWTON_FAIL | KF_ST_TANGENT | KF_ST_DEVICE_TIMEOUT)
 
 typedef struct kf_ctx kf_ctx;
@@ -440,7 +443,8 @@ int kf_serve_stop(kf_ctx *ctx);
  *  - the layer steps are issued as plain kernel launches on `stream`.
  * The first call on a device looks up the array's device address (with the
  * context's device current) and caches it; make that first call before any
- * stream capture begins.  Every call shares the one array and leaves its
+ * stream capture begins.  The cached address does not survive a
+ * cudaDeviceReset (which also invalidates every kf_ctx).  Every call shares the one array and leaves its
  * contents behind; each call's first layer launch rewrites what the later
  * launches read, so no clearing is needed.  Calls that overlap on the GPU
  * (other streams, other host threads) race on the array: serialise them.

@@ -49,7 +49,7 @@ static bool tracks_ok(const kf_tracks* t, bool need_lo) {
 
 // Validate a fit request against the configuration.
 // An empty batch (n = 0) is valid with any pointers.
-static int check_fit(kf_ctx* ctx, const kf_tracks* seeds, const kf_track_hits* hits,
+int check_fit(kf_ctx* ctx, const kf_tracks* seeds, const kf_track_hits* hits,
                      const kf_tracks* out) {
   if (!ctx || !seeds || !hits || !out) return KF_EINVAL;
   if (seeds->n < 0 || out->n != seeds->n || hits->n_tracks != seeds->n) return KF_EINVAL;

@@ -257,7 +257,12 @@ __global__ void __launch_bounds__(kStageThreads, kStageBlocksPerSM)
     __syncwarp();  // every lane has read buffer s before lane 0 may refill it
     fit_layer_track(A, i, st, p, lo, C, q, has_hit, m0, m1, m2);
   }
-  if (failed && lane == 0) {  // copies still in flight land before the block's memory is released
+  // Copies still in flight land before the block's memory is released.  Should
+  // this bounded wait give up too, the block exits with a copy in flight into
+  // shared memory that a later block on the SM may already use: the damage is
+  // not confined to this warp's tracks, which is why a KF_ST_DEVICE_TIMEOUT on
+  // any track invalidates every result of the call (documented in kf.h).
+  if (failed && lane == 0) {
     mbar_wait_bounded(&bar[0], ph0, kStageWaitLimit);
     mbar_wait_bounded(&bar[1], ph1, kStageWaitLimit);
   }

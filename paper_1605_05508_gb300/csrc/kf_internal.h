@@ -81,6 +81,10 @@ inline int cuda_fail(kf_ctx* ctx, cudaError_t e) {
 // Grow a scratch buffer to at least `bytes` (under the context budget).
 int scratch_reserve(kf_ctx* ctx, Scratch& s, size_t bytes);
 
+// Argument check shared by the kf_fit family (kf_capi.cu): KF_OK or KF_EINVAL.
+// An empty batch (n = 0) is valid with any pointers.
+int check_fit(kf_ctx* ctx, const kf_tracks* seeds, const kf_track_hits* hits, const kf_tracks* out);
+
 // Arguments of one fit layer step (single precision).
 struct FitLayerArgs {
   const float* in_par;

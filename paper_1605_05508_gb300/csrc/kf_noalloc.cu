@@ -25,7 +25,9 @@ void* g_scratch_addr[kMaxDevices] = {};
 // Device address of g_fit_scratch on the context's device.  Host code must
 // not use the symbol itself (on the host it names a stand-in, not device
 // memory); the address is looked up once per device, with that device
-// current, and cached.
+// current, and cached for the life of the process.  A cudaDeviceReset (or any
+// teardown of the device's primary context) reloads the module and may move
+// the array, so the cache does not survive one; neither does any kf_ctx.
 int scratch_address(kf_ctx* ctx, unsigned char** out) {
   if (ctx->device < 0 || ctx->device >= kMaxDevices) return KF_ENOTSUP;
   std::lock_guard<std::mutex> lock(g_mu);
@@ -43,13 +45,11 @@ int scratch_address(kf_ctx* ctx, unsigned char** out) {
 
 extern "C" int kf_fit_noalloc(kf_ctx* ctx, const kf_tracks* seeds, const kf_track_hits* hits, kf_tracks* out,
                               float* chi2, int32_t* status, void* stream) {
-  if (!ctx || !seeds || !hits || !out) return KF_EINVAL;
+  const int rc0 = kfi::check_fit(ctx, seeds, hits, out);  // the checks of kf_fit
+  if (rc0) return rc0;
   const int64_t n = seeds->n;
-  if (n < 0 || out->n != n || hits->n_tracks != n) return KF_EINVAL;
   if (n > kMaxTracks) return KF_EINVAL;  // beyond the static scratch: split the batch
-  if (hits->n_layers < 1 || hits->n_layers > ctx->cfg.n_layers) return KF_EINVAL;
   if (n == 0) return KF_OK;
-  if (!seeds->par || !seeds->cov || !seeds->charge || !out->par || !out->cov || !hits->xyz) return KF_EINVAL;
   KF_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   unsigned char* scratch = nullptr;
   const int rc = scratch_address(ctx, &scratch);

@@ -7,8 +7,11 @@ with the stated tolerances:
               surface propagation the covariance is rank 5 with n exactly in its
               null space, so the n row is measured against the t scale
   chi2        |d| <= 1e-3 absolute; FP32 leaves a floor near 4e-4 sqrt(chi2)
-              (momentum and path-length roundings at ~2e-7 cm), so at most a
-              1e-4 fraction of increments may exceed it, none beyond 3e-3
+              at r = 40 cm (momentum-direction and path-length roundings at
+              ~2e-7 cm), so at most CHI2_TOL_FRAC = 0.1 % of the increments
+              (rounded up to a whole increment) may exceed it, and none 3e-3.
+              This one rule holds for every comparison on layers up to 40 cm
+              (the benchmark geometry); no test may loosen it.
   status      bits identical."""
 import numpy as np
 
@@ -17,8 +20,13 @@ import oracle as O
 PAR_TOL = 1e-4
 COV_TOL = 1e-3
 CHI2_TOL = 1e-3
-CHI2_TOL_FRAC = 1e-4
+CHI2_TOL_FRAC = 1e-3
 CHI2_TOL_MAX = 3e-3
+
+
+def chi2_allowed_over(n_increments):
+    """Increments allowed above CHI2_TOL among n: CHI2_TOL_FRAC of them, rounded up."""
+    return int(np.ceil(CHI2_TOL_FRAC * n_increments))
 
 
 def to_dev(a, dtype=None):
@@ -107,7 +115,7 @@ def cov_error(g_cov, r_cov, r_par):
     return np.abs(gl - rl) / (sd[:, :, None] * sd[:, None, :] + 1e-300)
 
 
-def compare(g, r, radius_scale, chi2_frac=CHI2_TOL_FRAC, label=""):
+def compare(g, r, radius_scale, label=""):
     """Assert parity; returns a dict of the observed errors."""
     np.testing.assert_array_equal(g["status"], r["status"], err_msg=f"{label} status bits")
     pscale = np.concatenate([np.full((len(r["par"]), 3), radius_scale),
@@ -122,7 +130,7 @@ def compare(g, r, radius_scale, chi2_frac=CHI2_TOL_FRAC, label=""):
                  chi2_max=float(cer.max(initial=0)), chi2_over=over, n_chi2=int(both.sum()))
     assert stats["par_max"] <= PAR_TOL, (label, stats)
     assert stats["cov_max"] <= COV_TOL, (label, stats)
-    assert over <= max(0, int(chi2_frac * cer.size)) and stats["chi2_max"] <= CHI2_TOL_MAX, (label, stats)
+    assert over <= chi2_allowed_over(cer.size) and stats["chi2_max"] <= CHI2_TOL_MAX, (label, stats)
     return stats
 
 

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from buildutil import classify, gpu_build, oracle_build, oracle_seed_fit
-from fitutil import to_dev
+from fitutil import COV_TOL, PAR_TOL, cov_error, to_dev
 from paper_1605_05508_gb300 import synth as S
 
 pytestmark = pytest.mark.gpu
@@ -61,20 +61,34 @@ def test_bin_hits_is_a_deterministic_counting_sort(cuda_ctx_factory):
     assert torch.equal(again.hits, bins.hits) and torch.equal(again.bin_off, bins.bin_off)
 
 
+def _check_agreeing(g, r, idx, label=""):
+    """On the seeds (GPU rows idx, oracle rows 0..) whose best path equals the
+    oracle's: hit count, status bits, chi2_tot (1e-3 per hit), parameters
+    (1e-4 of scale) and the covariance (1e-3 sqrt(C_ii C_jj), local frame)
+    of the best candidate agree.  Returns the agreement mask."""
+    agree = np.array([np.array_equal(g["hits"][i], r["hits"][t, 0]) for t, i in enumerate(idx)])
+    gi = idx[agree]
+    assert np.array_equal(g["nhits"][gi], r["nhits"][agree, 0]), label
+    assert np.array_equal(g["status"][gi], r["status"][agree, 0]), label
+    assert np.all(np.abs(g["chi2"][gi] - r["chi2"][agree, 0]) <= 1e-3 * np.maximum(1, r["nhits"][agree, 0])), label
+    pscale = np.concatenate([np.full((agree.sum(), 3), 40.0),
+                             np.repeat(np.linalg.norm(r["par"][agree, 0, 3:], axis=1)[:, None], 3, axis=1)], axis=1)
+    perr = np.abs(g["par"][gi] - r["par"][agree, 0]) / pscale
+    cerr = cov_error(g["cov"][gi], r["cov"][agree, 0], r["par"][agree, 0])
+    print(f"{label}: best-candidate parameters {perr.max(initial=0):.2e} of scale, covariance "
+          f"{cerr.max(initial=0):.2e} (local frame) on {agree.sum()} agreeing paths")
+    assert perr.max(initial=0) <= PAR_TOL, label
+    assert cerr.max(initial=0) <= COV_TOL, label
+    return agree
+
+
 def _check_build(batch, g, r, max_bad=0, tie_frac=0.01, label=""):
     same, ties, bad = classify(batch, g, r)
     n = len(r["n_cands"])
     print(f"{label}: {same}/{n} identical best paths, {len(ties)} near ties, {len(bad)} other")
     assert len(bad) <= max_bad, bad[:5]
     assert len(ties) <= max(2, tie_frac * n), ties[:5]
-    agree = np.array([np.array_equal(g["hits"][i], r["hits"][i, 0]) for i in range(n)])
-    # on identical paths: hit count, chi2_tot and the state agree
-    assert np.array_equal(g["nhits"][agree], r["nhits"][agree, 0])
-    assert np.all(np.abs(g["chi2"][agree] - r["chi2"][agree, 0]) <= 1e-3 * np.maximum(1, r["nhits"][agree, 0]))
-    pscale = np.concatenate([np.full((agree.sum(), 3), 40.0),
-                             np.repeat(np.linalg.norm(r["par"][agree, 0, 3:], axis=1)[:, None], 3, axis=1)], axis=1)
-    assert np.all(np.abs(g["par"][agree] - r["par"][agree, 0]) <= 1e-4 * pscale)
-    return agree
+    return _check_agreeing(g, r, np.arange(n), label)
 
 
 @pytest.mark.parametrize("max_cands", [6, 1])
@@ -118,7 +132,10 @@ def test_build_config3_full_size_sampled(cuda_ctx_factory):
     """50 events x 5000 seeds, 15000 noise + 5000 track hits per layer, N = 6,
     building on layers 4-10, in the launch setting the benchmark times (the
     autotuner's choice on this batch): the same bits as the grouped per-lane
-    layout, and a sample of seeds checked against the oracle's all-hits build."""
+    layout, and 5000 seeds (100 from each of the 50 events) checked against
+    the oracle's all-hits build: best paths (near ties counted), and on the
+    agreeing paths the best candidate's hits, status, chi2, state and
+    covariance."""
     from paper_1605_05508_gb300 import kf
     det = S.barrel()
     ctx = cuda_ctx_factory(det.radii)
@@ -134,12 +151,15 @@ def test_build_config3_full_size_sampled(cuda_ctx_factory):
     for k in ("par", "chi2", "nhits", "status", "hits"):
         np.testing.assert_array_equal(g[k], g0[k], err_msg=k)
     rng = np.random.default_rng(1)
-    idx = np.sort(rng.choice(50 * 5000, 240, replace=False))
+    first = np.searchsorted(batch.seed_event, np.arange(51))
+    idx = np.sort(np.concatenate([first[e] + rng.choice(first[e + 1] - first[e], 100, replace=False)
+                                  for e in range(50)]))
     r = oracle_build(batch, 6, idx=idx)
     same, ties, bad = classify(batch, g, r, idx=idx)
     print(f"config3 sample: {same}/{len(idx)} identical, {len(ties)} near ties, {len(bad)} other")
     assert not bad, bad[:3]
     assert len(ties) <= max(2, 0.02 * len(idx))
+    _check_agreeing(g, r, idx, label="config3 sample")
     assert np.all(g["nhits"] >= 0) and np.all(g["nhits"] <= 7)
     # efficiency sanity: most seeds pick up most of the 7 layers
     assert np.mean(g["nhits"]) > 6.0

@@ -33,7 +33,7 @@ def test_sixty_four_layers(cuda_ctx_factory, mode):
     gs, rs = sel(g), sel(r)
     inner = {k: (v[:16] if k == "chi2" else v) for k, v in gs.items()}
     inner_r = {k: (v[:16] if k == "chi2" else v) for k, v in rs.items()}
-    stats = compare(inner, inner_r, det.radii[-1], chi2_frac=1e-3, label=f"64 layers {mode}")
+    stats = compare(inner, inner_r, det.radii[-1], label=f"64 layers {mode}")
     both = (gs["chi2"] >= 0) & (rs["chi2"] >= 0)
     rel = (np.abs(gs["chi2"] - rs["chi2"]) / np.maximum(rs["chi2"], 1.0))[both]
     print(mode, stats, "outer relative chi2 error max %.2e p99.9 %.2e" % (rel.max(), np.quantile(rel, 0.999)))
@@ -60,7 +60,7 @@ def test_layer_without_hits_single_track_and_block_edges(cuda_ctx_factory):
         for mode in ("graph", "fused"):
             g = gpu_fit(ctx, ev.seeds, ev.hits.xyz, valid, mode)
             r = oracle_fit(ev.seeds, ev.hits.xyz, valid, det)
-            compare(g, r, det.radii[-1], chi2_frac=1.0 / (10 * n), label=f"n={n} {mode}")
+            compare(g, r, det.radii[-1], label=f"n={n} {mode}")
             assert np.all(g["chi2"][5] == -1.0) and np.all(g["status"] & 16)
 
 

@@ -20,7 +20,7 @@ def test_config1_1000_tracks_graph(cuda_ctx_factory, det):
     ev = S.make_fit_batch(1605, 1000)
     g = gpu_fit(ctx, ev.seeds, ev.hits.xyz, ev.hits.valid, "graph")
     r = oracle_fit(ev.seeds, ev.hits.xyz, ev.hits.valid, det)
-    st = compare(g, r, det.radii[-1], chi2_frac=1e-3, label="config1")
+    st = compare(g, r, det.radii[-1], label="config1")
     print("config1", st)
 
 
@@ -31,7 +31,7 @@ def test_ragged_sizes(cuda_ctx_factory, det, n, mode):
     ev = S.make_fit_batch(2000 + n, n)
     g = gpu_fit(ctx, ev.seeds, ev.hits.xyz, ev.hits.valid, mode)
     r = oracle_fit(ev.seeds, ev.hits.xyz, ev.hits.valid, det)
-    compare(g, r, det.radii[-1], chi2_frac=max(1e-4, 2.0 / (10 * n)), label=f"{mode} n={n}")
+    compare(g, r, det.radii[-1], label=f"{mode} n={n}")
 
 
 def test_fused_equals_graph_and_host_equals_device(cuda_ctx_factory, det):
@@ -133,7 +133,7 @@ def test_missing_hits_and_loopers(cuda_ctx_factory, det):
     g = gpu_fit(ctx, ev.seeds, ev.hits.xyz, valid, "graph")
     r = oracle_fit(ev.seeds, ev.hits.xyz, valid, det)
     assert (r["status"] & 1).sum() > 50  # loopers present
-    compare(g, r, det.radii[-1], chi2_frac=1e-3, label="missing+loopers")
+    compare(g, r, det.radii[-1], label="missing+loopers")
 
 
 def test_plain_f64_per_event_matches_oracle(cuda_ctx_factory, det):
@@ -187,6 +187,6 @@ def test_full_size_config2_sampled(cuda_ctx_factory, det):
     g = gpu_fit(ctx, ev.seeds, ev.hits.xyz, ev.hits.valid, "autotune", sample=idx)
     sub = S.Seeds(ev.seeds.par[:, idx], ev.seeds.cov[:, idx], ev.seeds.charge[idx])
     r = oracle_fit(sub, ev.hits.xyz[:, :, idx], ev.hits.valid[:, idx], det)
-    compare(g, r, det.radii[-1], chi2_frac=1e-3, label="config2 sample")
+    compare(g, r, det.radii[-1], label="config2 sample")
     assert np.all(np.isfinite(g["par"])) and np.all(g["status"] == 0)
     assert np.all(g["chi2"] >= 0)

@@ -118,4 +118,4 @@ def test_mixed_form_on_the_standard_fit(cuda_ctx_factory):
     ev = S.make_fit_batch(1605, 3000)
     g = _run(ctx, kf, ev, kf.kf_fit_mixed)
     r = oracle_fit(ev.seeds, ev.hits.xyz, ev.hits.valid, det)
-    compare(g, r, det.radii[-1], chi2_frac=1e-3, label="mixed")
+    compare(g, r, det.radii[-1], label="mixed")
