@@ -238,9 +238,17 @@ def ncu_traffic(n_tracks, staged=False):
     return None if b is None else b * n_tracks
 
 
+# Algorithmic bytes of one track-layer step of the per-layer fit as the method
+# needs them: read the state (par 24 + cov 84), the hit (12) and the charge (1),
+# write the state (24 + 84) and the chi2 increment (4).
+FIT_METHOD_BYTES_PER_TRACK_LAYER = 233.0
+
+
 def fit_bytes_per_track_layer(L, seeds_have_lo, have_valid, have_chi2):
-    """Algorithmic HBM bytes of one track-layer step of the per-layer kernel,
-    averaged over the L launches of a step (first launch reads the seeds)."""
+    """Bytes one track-layer step of the per-layer kernel moves, averaged over
+    the L launches of a step (first launch reads the seeds): the method's bytes
+    plus this implementation's own, the low parts of the position pair, the
+    hit-valid flags and the status words."""
     rd = 24 + 84 + 1 + 12 + (1 if have_valid else 0)  # par, cov, charge, hit, valid
     rd_lo = 12 * ((L - 1) + (1 if seeds_have_lo else 0)) / L
     rd_status = 4 * (L - 1) / L
@@ -313,14 +321,20 @@ def run_ours(a):
     # roofline of the per-layer kernel: the graph holds only the L x chunks layer launches
     launch_s = ms_per_step / 1e3 / (L * chunks)
     bpt = fit_bytes_per_track_layer(L, False, True, True)
-    achieved = bpt * n / chunks / launch_s / 1e9
+    achieved = FIT_METHOD_BYTES_PER_TRACK_LAYER * n / chunks / launch_s / 1e9
+    achieved_moved = bpt * n / chunks / launch_s / 1e9
     peak, peak_kind = measured_peaks()
     traffic = ncu_traffic(n, bool(tuning.get("fit_stage")))
     kname = "fit_layer_stage_kernel" if tuning.get("fit_stage") else f"fit_layer_kernel<{tuning['fit_block']}>"
     roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic if chunks == 1 else None,
-            "peak_kind": peak_kind,
-            "algorithmic_bytes_per_track_layer": bpt, "launch_us": launch_s * 1e6}
+            "peak_kind": f"{peak_kind} (copy bandwidth)",
+            "algorithmic_bytes_per_track_layer": FIT_METHOD_BYTES_PER_TRACK_LAYER,
+            "launch_us": launch_s * 1e6,
+            "with_implementation_bytes": {
+                "bytes_per_track_layer": bpt, "achieved": achieved_moved, "frac": achieved_moved / peak,
+                "note": "the method's bytes plus the low parts of the position pair, hit-valid flags and status "
+                        "words this kernel also moves"}}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -328,14 +342,15 @@ def run_ours(a):
             "data": "synthetic (seeded generator, helix hits + Gaussian smear)",
             "config": workload_config(a), "roofline": roof, "clocks": clk, "gpu_launches": a.steps * L * chunks,
             "tuning": tuning}
+    line["peaks"] = peaks_leg(kf, ctx, stream, dev, smi_index)
 
     if not a.no_extras:
         line.update(extras(a, ctx, kf, torch, dev, det, ev, seeds, hits, out, chi2, status, stream, value,
-                           ms_per_step, rank, world, dist))
+                           ms_per_step, rank, world, dist, line["peaks"]))
     if not a.no_build:
         del seeds, hits, out, chi2, status
         torch.cuda.empty_cache()
-        line["build"] = build_leg(a, kf, torch, dev, stream, rank, world, dist)
+        line["build"] = build_leg(a, kf, torch, dev, stream, rank, world, dist, line["peaks"])
     if not a.no_extras:
         torch.cuda.empty_cache()
         line["precision"] = precision_leg(a, kf, torch, dev, stream, rank)
@@ -351,8 +366,68 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+def peaks_leg(kf, ctx, stream, dev, smi_index):
+    """Measured FP32 and FP64 fused multiply-add rates of this GPU (the
+    roofline denominators of the arithmetic-bound kernels), with the SM clock
+    sampled meanwhile; the rate per SM and cycle at that clock is the
+    clock-independent figure."""
+    import torch
+    props = torch.cuda.get_device_properties(dev)
+    res = {"how": "kf_measure_peak: independent FMA chains on a full-occupancy grid, best of 3 timed launches "
+                  "(CUDA events); an FMA counts as 2 flop"}
+    for name, kind in (("fp32", kf.PEAK_FP32), ("fp64", kf.PEAK_FP64)):
+        clocks = ClockSampler(smi_index)
+        clocks.start()
+        rate = kf.kf_measure_peak(ctx, kind, stream)
+        clk = clocks.stop()
+        res[f"{name}_tflops"] = rate / 1e12
+        res[f"{name}_clocks"] = clk
+        if clk and clk.get("sm_mhz"):
+            res[f"{name}_flop_per_sm_cycle"] = rate / (props.multi_processor_count * clk["sm_mhz"] * 1e6)
+    return res
+
+
+def f32(v):
+    """A configuration constant as the library receives it (float32)."""
+    return float(np.float32(v))
+
+
+CHI2_BINS = (0.0, 1.0, 3.0, 6.0, 10.0, 20.0, 30.0, np.inf)
+
+
+def chi2_error_table(g_chi2, o_chi2):
+    """|chi2_gpu - chi2_oracle| of every update both made, by the oracle's chi2:
+    count, median, p99, max, and the count above 1e-3 per bin."""
+    both = (g_chi2 >= 0) & (o_chi2 >= 0)
+    g, o = np.asarray(g_chi2, dtype=np.float64)[both], np.asarray(o_chi2, dtype=np.float64)[both]
+    err = np.abs(g - o)
+    rows = []
+    for lo, hi in zip(CHI2_BINS[:-1], CHI2_BINS[1:]):
+        sel = (o >= lo) & (o < hi)
+        e = err[sel]
+        rows.append({"chi2_from": lo, "chi2_to": None if np.isinf(hi) else hi, "n": int(sel.sum()),
+                     "median": float(np.median(e)) if e.size else None,
+                     "p99": float(np.quantile(e, 0.99)) if e.size else None,
+                     "max": float(e.max()) if e.size else None, "n_above_1e-3": int((e > 1e-3).sum())})
+    return {"increments": int(err.size), "n_above_1e-3": int((err > 1e-3).sum()),
+            "frac_above_1e-3": float((err > 1e-3).mean()) if err.size else 0.0,
+            "max": float(err.max()) if err.size else 0.0, "by_oracle_chi2": rows}
+
+
+def fp32_roofline(flop_per_unit, units, seconds, peaks, source):
+    """FP32 flop fraction of the measured FP32 peak for a kernel whose FP32
+    instruction counts per unit come from a committed ncu summary."""
+    if not flop_per_unit or not peaks or not peaks.get("fp32_tflops"):
+        return None
+    ach = flop_per_unit * units / seconds
+    return {"bound": "fp32", "achieved": ach / 1e12, "peak": peaks["fp32_tflops"], "unit": "TFLOP/s",
+            "frac": ach / (peaks["fp32_tflops"] * 1e12), "flop_per_unit": flop_per_unit,
+            "peak_kind": "measured (kf_measure_peak)",
+            "flop_source": f"ncu FFMA x2 + FADD + FMUL thread instructions ({source})"}
+
+
 def extras(a, ctx, kf, torch, dev, det, ev, seeds, hits, out, chi2, status, stream, value, ms_per_step, rank, world,
-           dist):
+           dist, peaks=None):
     n, L = ev.seeds.par.shape[1], det.n_layers
     res = {}
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -384,6 +459,10 @@ def extras(a, ctx, kf, torch, dev, det, ev, seeds, hits, out, chi2, status, stre
                                     "unit": "warp instructions/s", "frac": ach / peak,
                                     "warp_instructions_per_track_layer": ipt,
                                     "peak_kind": "4 issues per SM per cycle x SMs x max SM clock"}
+    fpt = profile_value("fit_fused_kernel.instructions.txt", "fp32_flop_per_track_layer")
+    f32r = fp32_roofline(fpt, n * L, ms_f / 1e3, peaks, "profiles/fit_fused_kernel.instructions.txt")
+    if f32r:
+        res["fused"]["fp32_roofline"] = dict(f32r, kernel="fit_fused_kernel<0>")
 
     # end to end through the public C ABI with pinned host buffers
     pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
@@ -424,12 +503,16 @@ def extras(a, ctx, kf, torch, dev, det, ev, seeds, hits, out, chi2, status, stre
         m = min(n, 50 * a.tracks)
         O.lib()
         t0 = time.perf_counter()
-        O.fit(ev.seeds.par[:, :m], ev.seeds.cov[:, :m], ev.seeds.charge[:m], ev.hits.xyz[:, :, :m],
-              ev.hits.valid[:, :m], det.radii, det.bz, det.sigma_xy, det.sigma_z, n_threads=cores)
+        orc = O.fit(ev.seeds.par[:, :m], ev.seeds.cov[:, :m], ev.seeds.charge[:m], ev.hits.xyz[:, :, :m],
+                    ev.hits.valid[:, :m], [f32(r) for r in det.radii], f32(det.bz), f32(det.sigma_xy),
+                    f32(det.sigma_z), n_threads=cores)
         dtc = time.perf_counter() - t0
         res["cpu_baseline"] = {"value": m * L / dtc, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": f"first {m} tracks ({m // a.tracks} events) x {L} layers, FP64 oracle, "
                                          f"{cores} OpenMP threads, {dtc:.2f} s wall"}
+        # the same sample's chi2 increments against the GPU fit's (outside any timed region)
+        res["chi2_error_vs_oracle"] = dict(chi2_error_table(chi2[:, :m].double().cpu().numpy(), orc["chi2"]),
+                                           sample=f"first {m} tracks of the workload x {L} layers")
     res["single_event"] = single_event_leg(a, kf, torch, dev, det, stream, rank)
     return res
 
@@ -468,6 +551,7 @@ def single_event_leg(a, kf, torch, dev, det, stream, rank):
             ts.append(e0.elapsed_time(e1))
         return float(np.median(ts))
     us32 = med(lambda: kf.kf_fit(ctx, s32, h, o32, c32, st, stream)) * 1e3
+    g_chi2 = c32.double().cpu().numpy()
     us64 = med(lambda: kf.kf_fit_f64(ctx, s64, h, o64, [0, n], c64, st, stream)) * 1e3
     ctx.close()
     res = {"workload": "1 event x 1000 tracks, 10 layers (seed 1605)", "unit": "us per event",
@@ -479,15 +563,40 @@ def single_event_leg(a, kf, torch, dev, det, stream, rank):
             ts = []
             for _ in range(5):
                 t0 = time.perf_counter()
-                O.fit(ev.seeds.par, ev.seeds.cov, ev.seeds.charge, ev.hits.xyz, ev.hits.valid, det.radii, det.bz,
-                      det.sigma_xy, det.sigma_z, n_threads=thr)
+                orc = O.fit(ev.seeds.par, ev.seeds.cov, ev.seeds.charge, ev.hits.xyz, ev.hits.valid,
+                            [f32(r) for r in det.radii], f32(det.bz), f32(det.sigma_xy), f32(det.sigma_z),
+                            n_threads=thr)
                 ts.append(time.perf_counter() - t0)
             res[name] = float(np.median(ts)) * 1e6
         res["oracle_cores"] = cores
+        res["chi2_error_vs_oracle"] = chi2_error_table(g_chi2, orc["chi2"])
     return res
 
 
-def build_leg(a, kf, torch, dev, stream, rank, world, dist):
+# The build's work per seed and building layer as the method needs it: about
+# 6 parents read (112 B of state each) and 6 children written (112 B + a 4 B
+# hit id) plus the hits of the windows, ~1.4 kB; and ~13 kflop (6 x
+# propagation ~440 FMA, S^-1 ~25, ~30 window hits x 12, update ~250).
+BUILD_METHOD_BYTES_PER_SEED_LAYER = 1400.0
+BUILD_METHOD_FLOP_PER_SEED_LAYER = 13000.0
+BUILD_LAYOUTS = ("lane", "coop", "packed128", "packed64", "resident")
+# How the build's seeds are made (the paper does not report realistic seeding);
+# every efficiency figure depends on this prior
+SEED_READING = ("vertex truth smeared by 0.01 cm (x, y), 1 cm (z) and 1 % of |p| per momentum component, "
+                "then fitted over layers 1-3; not 3-hit geometric seeds")
+
+
+def build_kernel_name(t, max_cands):
+    """The step kernel a build setting launches (kf_build.cu)."""
+    scan, lw = t["build_scan"], (4 if t["build_list_width"] == 4 and max_cands <= 4 else 8)
+    if scan in (2, 3):
+        return f"build_step_packed_kernel<{lw}, {128 if scan == 2 else 64}>"
+    if scan == 4:
+        return "build_resident_kernel"
+    return f"build_step_kernel<{t['build_hit_tile']}, {lw}, {int(scan == 1)}>"
+
+
+def build_leg(a, kf, torch, dev, stream, rank, world, dist, peaks=None):
     """Combinatorial build (clone engine, N = 6; and best-hit N = 1) on
     `build_events` events x `build_seeds` seeds with 3x noise hits per layer,
     64 x 256 bins, chi2 < 30; a step = seed fit over layers 1-3 + hit binning
@@ -549,7 +658,7 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist):
                     if (lw == 4 and N > 4) or (scan >= 2 and tile > 0):
                         continue
                     kf.kf_set_tuning(ctx, 128, tile, lw, scan)
-                    name = ("lane", "coop", "packed128", "packed64")[scan]
+                    name = BUILD_LAYOUTS[scan]
                     times[f"tile{tile}_list{lw}_{name}"] = float(run(N, 5)[1][2])
         return times, kf.kf_autotune_build(ctx, fo, seed_off, bins, N, out, stream)
 
@@ -564,6 +673,7 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist):
     tune6 = dict(tune6, bin_unordered=1)
     kf.kf_set_tuning(ctx, **tune6)
     tot6, t6 = run(6, k)
+    hidx6 = out.hit_idx.cpu().numpy()  # [Lb, n] best paths of the N = 6 build
     mean_hits = float(out.n_hits.float().mean())
     # build efficiency: best candidate with >= 80 % of its building-layer hits
     # from its own track (truth of the generator)
@@ -598,7 +708,8 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist):
     refit_ms = max_over_ranks(evs[0].elapsed_time(evs[1]) / k, dist, dev)
     full = torch.from_numpy(good == Lb).to(dev) & (rst == 0)
     rc = rchi2[:, full]
-    efficiency = {"best_candidate_ge_80pct_correct": float(np.mean(good >= 0.8 * Lb)),
+    efficiency = {"seeds": SEED_READING,
+                  "best_candidate_ge_80pct_correct": float(np.mean(good >= 0.8 * Lb)),
                   "all_hits_correct": float(np.mean(good == Lb)),
                   "refit_ms": refit_ms, "refit_track_layers_per_s": whole_job_rate(n * rchi2.shape[0], world,
                                                                                     refit_ms / 1e3),
@@ -620,7 +731,7 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist):
                       "all_hits_correct": float(np.mean(gN == Lb)),
                       "mean_hits_found": float(out.n_hits.float().mean()),
                       "setting": f"tile{tn['build_hit_tile']}_list{tn['build_list_width']}_"
-                                 f"{('lane', 'coop', 'packed128', 'packed64')[tn['build_scan']]}"})
+                                 f"{BUILD_LAYOUTS[tn['build_scan']]}"})
     res = {"workload": f"combinatorial build: {E} events x {T} seeds, {int(3 * T)} noise + <= {T} track hits per "
                        f"layer, 64x256 eta-phi bins, chi2 < 30, N = 6, seed fit on layers 1-3, build on 4-10",
            "value": world * n * Lb / (tot6 / 1e3), "unit": "seed-layer steps/s", "ms_per_step": tot6,
@@ -630,43 +741,79 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist):
            "best_hit_N1": {"ms_per_step": tot1, "value": world * n * Lb / (tot1 / 1e3), "build_ms": float(t1[2]),
                            "tuning": tune1, "build_ms_by_setting": sweep1},
            "tuning": tune6, "build_ms_by_setting": sweep6, "efficiency_and_refit": efficiency,
-           "clone_engine_curve": curve,
+           "clone_engine_curve": {"seeds": SEED_READING, "points": curve},
            "bin_order": "scatter order inside each bin (bin_unordered 1; the build's results are the same bits)",
            # seed fit (3 layer launches) + hit binning (count, scan, scatter) + kf_build (seed
            # binning: count, scan, scatter, sort; seed ids; initial candidates; Lb steps; final)
            "gpu_launches_per_step": 3 + 3 + (4 + 1 + 1 + Lb + 1)}
-    # issue roofline of the build steps: warp instructions of the Lb step
-    # launches of one build (committed ncu summary, same setting) over the whole
-    # build phase's time (which also holds seed ordering, init and final
-    # selection: a lower bound on the step kernels' rate)
+    # roofline of the build by the method's bytes: per seed and layer ~6 parents
+    # read (112 B of state each), ~6 children written (112 B + a 4 B hit id) and
+    # the hits of their windows, ~1.4 kB; over the build phase's CUDA-event time
+    # (seed ordering, initialisation and final selection included)
+    peak_hbm, peak_kind = measured_peaks()
+    t_build = float(t6[2]) / 1e3
+    ach = BUILD_METHOD_BYTES_PER_SEED_LAYER * n * Lb / t_build / 1e9
+    res["roofline"] = {"kernel": build_kernel_name(tune6, 6), "bound": "hbm", "achieved": ach, "peak": peak_hbm,
+                       "unit": "GB/s", "frac": ach / peak_hbm, "traffic": None,
+                       "peak_kind": f"{peak_kind} (copy bandwidth)",
+                       "algorithmic_bytes_per_seed_layer": BUILD_METHOD_BYTES_PER_SEED_LAYER,
+                       "seed_layers_per_launch_set": n * Lb, "build_ms": float(t6[2])}
+    fl = BUILD_METHOD_FLOP_PER_SEED_LAYER * n * Lb / t_build
+    if peaks and peaks.get("fp32_tflops"):
+        res["roofline"]["method_fp32"] = {"achieved": fl / 1e12, "peak": peaks["fp32_tflops"], "unit": "TFLOP/s",
+                                          "frac": fl / (peaks["fp32_tflops"] * 1e12),
+                                          "flop_per_seed_layer": BUILD_METHOD_FLOP_PER_SEED_LAYER}
+    # counted figures of the step kernels from a committed ncu summary of the
+    # same setting and kernel source: warp instructions (issue rate) and FP32
+    # flops (FFMA x 2 + FADD + FMUL) of one build
     prof = "build_step_kernel.instructions.txt"
-    wi = profile_value(prof, "warp_instructions_per_build", BUILD_SOURCES)
     setting = profile_value(prof, "setting_code", BUILD_SOURCES)
     code = tune6["build_hit_tile"] * 100 + tune6["build_list_width"] * 10 + tune6["build_scan"]
-    if wi and setting == code and E == profile_value(prof, "events", BUILD_SOURCES):
+    if setting == code and E == profile_value(prof, "events", BUILD_SOURCES):
         props = torch.cuda.get_device_properties(dev)
-        peak = 4.0 * props.multi_processor_count * float(line_clock_mhz(dev)) * 1e6
-        ach = wi / (float(t6[2]) / 1e3)
-        res["roofline"] = {"kernel": "build_step_kernel", "bound": "alu", "achieved": ach, "peak": peak,
-                           "unit": "warp instructions/s", "frac": ach / peak, "warp_instructions_per_build": wi,
-                           "active_lanes_per_warp_instruction": profile_value(prof, "active_lanes_per_warp_instruction",
-                                                                              BUILD_SOURCES),
-                           "peak_kind": "4 issues per SM per cycle x SMs x max SM clock"}
+        wi = profile_value(prof, "warp_instructions_per_build", BUILD_SOURCES)
+        if wi:
+            peak = 4.0 * props.multi_processor_count * float(line_clock_mhz(dev)) * 1e6
+            res["roofline"]["issue"] = {"achieved": wi / t_build, "peak": peak, "unit": "warp instructions/s",
+                                        "frac": wi / t_build / peak, "warp_instructions_per_build": wi,
+                                        "active_lanes_per_warp_instruction": profile_value(
+                                            prof, "active_lanes_per_warp_instruction", BUILD_SOURCES),
+                                        "peak_kind": "4 issues per SM per cycle x SMs x max SM clock"}
+        f32r = fp32_roofline(profile_value(prof, "fp32_flop_per_build", BUILD_SOURCES), 1, t_build, peaks,
+                             f"profiles/{prof}")
+        if f32r:
+            res["roofline"]["counted_fp32"] = f32r
     if rank == 0 and not a.no_extras:
         import oracle as O
         cores = os.cpu_count() or 1
+        from oracle import parity
         m = min(n, 1000)
         idx = np.arange(m)
+        Ls = len(batch.seed_layers)
+        radii_b = [f32(det.radii[l]) for l in batch.build_layers]
         fr = O.fit(batch.seeds.par[:, idx], batch.seeds.cov[:, idx], batch.seeds.charge[idx], batch.fit_hits.xyz[:, :, idx],
-                   batch.fit_hits.valid[:, idx], det.radii[:3], det.bz, det.sigma_xy, det.sigma_z, n_threads=cores)
+                   batch.fit_hits.valid[:, idx], [f32(r) for r in det.radii[:Ls]], f32(det.bz), f32(det.sigma_xy),
+                   f32(det.sigma_z), n_threads=cores)
         t0 = time.perf_counter()
-        O.build_tracks(fr["par"], fr["cov"], batch.seeds.charge[idx], batch.seed_event[idx], batch.layer_xyz,
-                       batch.layer_off, [det.radii[l] for l in batch.build_layers], det.bz, det.sigma_xy, det.sigma_z,
-                       30.0, 6, n_threads=cores)
+        ob = O.build_tracks(fr["par"], fr["cov"], batch.seeds.charge[idx], batch.seed_event[idx], batch.layer_xyz,
+                            batch.layer_off, radii_b, f32(det.bz), f32(det.sigma_xy), f32(det.sigma_z), 30.0, 6,
+                            n_threads=cores)
         dtc = time.perf_counter() - t0
         res["cpu_baseline"] = {"value": m * Lb / dtc, "unit": "seed-layer steps/s", "cores": cores, "kind": "oracle",
                                "sample": f"first {m} seeds of event 0 x {Lb} layers, N = 6, all-hits chi2 scan "
                                          f"(the oracle bins nothing), {cores} OpenMP threads, {dtc:.2f} s wall"}
+        # the same seeds' best paths against the GPU build's (N = 6): differing
+        # paths re-evaluated by the oracle and counted as near ties (same hit
+        # count, chi2_tot within 1e-4 relative, or a hit within 1e-3 of the cut)
+        V = np.array([f32(det.sigma_xy) ** 2, f32(det.sigma_xy) ** 2, f32(det.sigma_z) ** 2])
+
+        def hit_of(t, l, h):
+            return batch.layer_xyz[:, batch.layer_off[int(batch.seed_event[t]) * Lb + l] + h].astype(np.float64)
+        same, ties, bad = parity.classify(hidx6.T[idx], ob["hits"][:, 0], fr["par"], fr["cov"],
+                                          O.a_coef(batch.seeds.charge[idx], f32(det.bz)), hit_of, radii_b, V)
+        res["best_paths_vs_oracle"] = {"seeds": m, "identical": same, "near_ties": len(ties),
+                                       "other_differences": len(bad),
+                                       "sample": f"first {m} seeds of event 0, N = 6"}
     ctx.close()
     return res
 

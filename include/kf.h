@@ -420,6 +420,36 @@ int kf_serve_stats_get(kf_ctx *ctx, kf_serve_stats *out);
  * cancelled; unpolled results are dropped.  kf_destroy stops it too. */
 int kf_serve_stop(kf_ctx *ctx);
 
+/* Test hook for the bounded waits of the staged layer kernel of kf_fit
+ * (kf_tuning.fit_stage = 1).  The paper has no counterpart: it exists so that
+ * a test can make a wait for staged input run out without any GPU fault.
+ * After this call, kf_fit launches on this context do not issue the copies of
+ * the 32-track tile `skip_tile` of the batch (tracks 32 skip_tile ..
+ * 32 skip_tile + 31; -1 = none), so the warp that owns that tile waits in
+ * vain until its poll limit: those tracks, and the warp's later tiles in the
+ * same launch, get KF_ST_DEVICE_TIMEOUT; every other track's results are
+ * unchanged.  `wait_polls` bounds each wait for staged input (0 = the normal
+ * limit); the drain wait before a block exits keeps the normal limit, and
+ * waits only for copies actually issued.  Affects kf_fit only.
+ * Errors: KF_EINVAL (null context, skip_tile < -1). */
+int kf_test_stage_fault(kf_ctx *ctx, int64_t skip_tile, uint32_t wait_polls);
+
+/* ---------------------------------------------------------------------------
+ * Measured arithmetic peaks: the roofline denominators of the kernels bound by
+ * arithmetic.  The paper has no counterpart (it measures on CPUs).  Runs a
+ * fused multiply-add microbenchmark on the context's device -- every thread
+ * of a full-occupancy grid (8 blocks of 256 threads per SM) iterates
+ * independent FMA chains -- as one warm-up and three timed launches of about
+ * 10 ms on `stream` (synchronised), and writes the best rate in flop/s, an FMA
+ * counted as two flops.  The rate is that of the SM clock during the launches;
+ * callers that need a clock-independent figure sample the clock meanwhile.
+ * kind: KF_PEAK_FP32 (single-precision FFMA) or KF_PEAK_FP64 (DFMA).
+ * Allocates nothing.  Errors: KF_EINVAL (null, unknown kind), KF_ECUDA.
+ */
+#define KF_PEAK_FP32 0
+#define KF_PEAK_FP64 1
+int kf_measure_peak(kf_ctx *ctx, int32_t kind, void *stream, double *flop_per_s);
+
 /* Largest batch (tracks) that kf_fit_noalloc accepts. */
 #define KF_NOALLOC_MAX_TRACKS 262144
 

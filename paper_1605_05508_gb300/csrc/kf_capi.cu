@@ -80,6 +80,13 @@ const char* kf_strerror(int code) {
 
 int kf_last_cuda_error(const kf_ctx* ctx) { return ctx ? ctx->last_cuda : 0; }
 
+int kf_test_stage_fault(kf_ctx* ctx, int64_t skip_tile, uint32_t wait_polls) {
+  if (!ctx || skip_tile < -1) return KF_EINVAL;
+  ctx->test_skip_tile = skip_tile;
+  ctx->test_wait_polls = wait_polls;
+  return KF_OK;
+}
+
 int kf_create(kf_ctx** out, const kf_config* cfg, int device, size_t mem_budget_bytes) {
   if (!out || !cfg) return KF_EINVAL;
   *out = nullptr;
@@ -192,7 +199,9 @@ int kf_fit(kf_ctx* ctx, const kf_tracks* seeds, const kf_track_hits* hits, kf_tr
                                reinterpret_cast<uint64_t>(hits->xyz),
                                reinterpret_cast<uint64_t>(hits->valid),
                                reinterpret_cast<uint64_t>(chi2),
-                               reinterpret_cast<uint64_t>(st)};
+                               reinterpret_cast<uint64_t>(st),
+                               uint64_t(ctx->test_skip_tile),
+                               uint64_t(ctx->test_wait_polls)};
   cudaStream_t user = static_cast<cudaStream_t>(stream);
   GraphEntry* hit_entry = nullptr;
   for (auto& g : ctx->graphs)
@@ -227,6 +236,8 @@ int kf_fit(kf_ctx* ctx, const kf_tracks* seeds, const kf_track_hits* hits, kf_tr
       a.v2 = v2;
       a.first = l == 0;
       a.last = l == L - 1;
+      a.skip_tile = ctx->test_skip_tile;
+      a.wait_limit = ctx->test_wait_polls;
       FitStageMaps maps;
       if (ctx->tune.fit_stage && make_stage_maps(a, &maps))
         le = launch_fit_layer_stage(a, maps, ctx->num_sms, cs);

@@ -209,11 +209,20 @@ __global__ void __launch_bounds__(kStageThreads, kStageBlocksPerSM)
   if (t >= n_tiles) return;  // the whole warp
   const bool has_lo = A.in_lo != nullptr;
   const uint32_t bytes = uint32_t(sizeof(float)) * kStageTile * (6 + 21 + 3 + (has_lo ? 3 : 0));
+  // Test hook (kf_test_stage_fault): the copies of the batch's tile
+  // A.skip_tile are never issued, so the wait for it runs out; A.wait_limit
+  // (0: the normal limit) bounds the waits for staged input.  The drain wait
+  // before the block exits always keeps the normal limit.
+  // lane 0: bit b set while the pending phase of buffer b has copies in flight
+  uint32_t armed = 0;
   if (lane == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     mbar_init_fence();
-    stage_issue(M, has_lo, buf[0], &bar[0], int(A.begin + t * kStageTile), bytes);
+    if (A.begin / kStageTile + t != A.skip_tile) {
+      stage_issue(M, has_lo, buf[0], &bar[0], int(A.begin + t * kStageTile), bytes);
+      armed = 1u;
+    }
   }
   __syncwarp();
   uint32_t ph0 = 0, ph1 = 0;
@@ -227,15 +236,17 @@ __global__ void __launch_bounds__(kStageThreads, kStageBlocksPerSM)
     // the next tile into the other buffer (its previous tile was read by every
     // lane before the __syncwarp that closed the last iteration)
     const int64_t tn = t + nwarps;
-    if (tn < n_tiles && lane == 0) {
+    if (tn < n_tiles && lane == 0 && A.begin / kStageTile + tn != A.skip_tile) {
       fence_proxy_async_smem();
       stage_issue(M, has_lo, buf[s ^ 1], &bar[s ^ 1], int(A.begin + tn * kStageTile), bytes);
+      armed |= 1u << (s ^ 1);
     }
     // per-track inputs outside the tile, loaded while the copies land
     const int32_t st = A.first ? 0 : A.status[i];
     const int8_t q = A.charge[i];
     const bool has_hit = A.valid ? A.valid[i] != 0 : true;
-    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bar[s], s ? ph1 : ph0, kStageWaitLimit));
+    const bool ok = __all_sync(
+        0xffffffffu, mbar_wait_bounded(&bar[s], s ? ph1 : ph0, A.wait_limit ? A.wait_limit : kStageWaitLimit));
     if (!ok) {  // the phase stays pending: waited for once more below
       failed = true;
       A.status[i] = st | KF_ST_DEVICE_TIMEOUT;
@@ -245,6 +256,7 @@ __global__ void __launch_bounds__(kStageThreads, kStageBlocksPerSM)
       ph1 ^= 1u;
     else
       ph0 ^= 1u;
+    armed &= ~(1u << s);
     const StageTile& T = buf[s];
     float p[6], lo[3], C[21];
 #pragma unroll
@@ -263,8 +275,8 @@ __global__ void __launch_bounds__(kStageThreads, kStageBlocksPerSM)
   // not confined to this warp's tracks, which is why a KF_ST_DEVICE_TIMEOUT on
   // any track invalidates every result of the call (documented in kf.h).
   if (failed && lane == 0) {
-    mbar_wait_bounded(&bar[0], ph0, kStageWaitLimit);
-    mbar_wait_bounded(&bar[1], ph1, kStageWaitLimit);
+    if (armed & 1u) mbar_wait_bounded(&bar[0], ph0, kStageWaitLimit);
+    if (armed & 2u) mbar_wait_bounded(&bar[1], ph1, kStageWaitLimit);
   }
 }
 

@@ -62,6 +62,8 @@ struct kf_ctx {
   cudaEvent_t host_done[kfi::kHostStreams] = {};
   cudaEvent_t host_start = nullptr;
   kf_tuning tune = {128, 0, 8, 0, 0, 0, 0};  // launch parameters (kf_set_tuning, kf_autotune_*)
+  int64_t test_skip_tile = -1;   // kf_test_stage_fault
+  uint32_t test_wait_polls = 0;
 };
 
 namespace kfi {
@@ -105,6 +107,11 @@ struct FitLayerArgs {
   float x_x0, mass;  // this layer's thickness in radiation lengths (0: none); particle mass
   int first;  // 1: initialise status, always write the state
   int last;   // 1: run the positive-definite check
+  // test hook of the staged kernel (kf_test_stage_fault): batch index of a
+  // 32-track tile whose copies are not issued (-1: none); poll limit of the
+  // waits for staged input (0: the normal limit)
+  int64_t skip_tile = -1;
+  uint32_t wait_limit = 0;
 };
 
 struct FitFusedArgs {

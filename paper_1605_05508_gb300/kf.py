@@ -141,6 +141,8 @@ def lib() -> C.CDLL:
         L.kf_set_tuning.argtypes = [vp, C.POINTER(kf_tuning)]
         L.kf_autotune_fit.argtypes = [vp, C.POINTER(kf_tracks), C.POINTER(kf_track_hits), C.POINTER(kf_tracks),
                                       vp, vp, vp, C.POINTER(kf_tuning)]
+        L.kf_measure_peak.argtypes = [vp, i32, vp, C.POINTER(C.c_double)]
+        L.kf_test_stage_fault.argtypes = [vp, i64, C.c_uint32]
         L.kf_autotune_build.argtypes = [vp, C.POINTER(kf_tracks), vp, C.POINTER(kf_layer_hit_bins), i32,
                                         C.POINTER(kf_build_result), vp, C.POINTER(kf_tuning)]
         _lib = L
@@ -392,6 +394,23 @@ def kf_autotune_build(ctx, seeds: Tracks, seed_off, bins: HitBins, max_cands: in
     _check(lib().kf_autotune_build(_h(ctx), C.byref(s), _ptr(seed_off), C.byref(b), int(max_cands), C.byref(o),
                                    _stream(stream), C.byref(t)), "kf_autotune_build", _h(ctx))
     return _tuning_dict(t)
+
+
+def kf_test_stage_fault(ctx, skip_tile: int = -1, wait_polls: int = 0):
+    """Test hook of the staged fit kernel's bounded waits (see kf.h)."""
+    _check(lib().kf_test_stage_fault(_h(ctx), int(skip_tile), int(wait_polls)), "kf_test_stage_fault", _h(ctx))
+
+
+# --------------------------------------------------------------------------- measured peaks
+
+PEAK_FP32, PEAK_FP64 = 0, 1  # KF_PEAK_FP32, KF_PEAK_FP64
+
+
+def kf_measure_peak(ctx, kind: int, stream=None) -> float:
+    """Measured FMA rate of the device in flop/s (kind PEAK_FP32 or PEAK_FP64)."""
+    v = C.c_double()
+    _check(lib().kf_measure_peak(_h(ctx), int(kind), _stream(stream), C.byref(v)), "kf_measure_peak", _h(ctx))
+    return v.value
 
 
 # --------------------------------------------------------------------------- serving

@@ -79,60 +79,32 @@ def gpu_build(ctx, batch, max_cands, want_cands=True, build_fn=None):
     return res
 
 
-def path_chi2(batch, seed_par, seed_cov, charge, event, hits_seq, cut=30.0):
-    """Oracle chi2 increments along a given hit path (one seed): list of
-    per-layer chi2 (None for a layer without hit) and the state/cov."""
+def _path_args(batch):
     det = batch.det
     V = np.array([f32(det.sigma_xy) ** 2, f32(det.sigma_xy) ** 2, f32(det.sigma_z) ** 2])
-    a = float(charge) * O.C_LIGHT * f32(det.bz)
-    x, C = np.asarray(seed_par, dtype=np.float64), np.asarray(seed_cov, dtype=np.float64)
-    Lb = len(batch.build_layers)
-    out = []
-    for l in range(Lb):
-        R = f32(det.radii[batch.build_layers[l]])
-        xp, J, _, st = O.propagate(x, a, R)
-        if st:
-            out.append(None)
-            continue
-        Q = None
-        if det.has_material and det.x_x0[batch.build_layers[l]] > 0:
-            Q = O.scattering_q(xp, f32(det.x_x0[batch.build_layers[l]]), f32(det.mass))
-        Cp = O.transport_cov(J, C, Q)
-        h = int(hits_seq[l])
-        if h < 0:
-            x, C = xp, Cp
-            out.append(None)
-            continue
-        g = event * Lb + l
-        m = batch.layer_xyz[:, batch.layer_off[g] + h].astype(np.float64)
-        x, C, c2, _ = O.update(xp, Cp, m, V)
-        out.append(c2)
-    return out
+    radii = [f32(det.radii[l]) for l in batch.build_layers]
+    mat = material(det, batch.build_layers)
+    return radii, V, mat.get("x_x0"), mat.get("mass", O.PION_MASS)
 
 
 def classify(batch, g, r, idx=None, cut=30.0, rel=1e-4):
-    """Compare best paths seed by seed. Returns (n_same, near_ties, bad):
-    a differing path is a near tie when, evaluated by the oracle, it has the
-    oracle best's hit count and a chi2_tot within `rel` relative of it, or
-    when a hit on either path sits within 1e-3 of the chi2 cut."""
+    """Compare best paths seed by seed (oracle.parity.classify). Returns
+    (n_same, near_ties, bad) with GPU seed indices: a differing path is a near
+    tie when, evaluated by the oracle, it has the oracle best's hit count and a
+    chi2_tot within `rel` relative of it, or when a hit on either path sits
+    within 1e-3 of the chi2 cut."""
+    from oracle import parity
     n = len(r["n_cands"])
-    idx = np.arange(n) if idx is None else idx
-    same, ties, bad = 0, [], []
-    for t in range(n):
-        gi = idx[t]
-        pg, po = g["hits"][gi], r["hits"][t, 0]
-        if np.array_equal(pg, po):
-            same += 1
-            continue
-        ev = int(batch.seed_event[gi])
-        cg = path_chi2(batch, r["seed_par"][t], r["seed_cov"][t], batch.seeds.charge[gi], ev, pg, cut)
-        co = path_chi2(batch, r["seed_par"][t], r["seed_cov"][t], batch.seeds.charge[gi], ev, po, cut)
-        vg = [c for c in cg if c is not None]
-        vo = [c for c in co if c is not None]
-        near_cut = any(abs(c - cut) < 1e-3 for c in vg + vo) or any(c >= cut for c in vg)
-        tot_g, tot_o = sum(vg), sum(vo)
-        if near_cut or (len(vg) == len(vo) and abs(tot_g - tot_o) <= rel * max(tot_o, 1e-30)):
-            ties.append((gi, tot_g, tot_o))
-        else:
-            bad.append((gi, list(pg), list(po), tot_g, tot_o))
+    idx = np.arange(n) if idx is None else np.asarray(idx)
+    Lb = len(batch.build_layers)
+    radii, V, x_x0, mass = _path_args(batch)
+    a = O.a_coef(batch.seeds.charge[idx], f32(batch.det.bz))
+
+    def hit_of(t, l, h):
+        seg = int(batch.seed_event[idx[t]]) * Lb + l
+        return batch.layer_xyz[:, batch.layer_off[seg] + h].astype(np.float64)
+    same, ties, bad = parity.classify(g["hits"][idx], r["hits"][:, 0], r["seed_par"], r["seed_cov"], a, hit_of,
+                                      radii, V, x_x0, mass, cut, rel)
+    ties = [(int(idx[t]), ca, cb) for t, ca, cb in ties]
+    bad = [(int(idx[t]), pa, pb, ca, cb) for t, pa, pb, ca, cb in bad]
     return same, ties, bad

@@ -66,6 +66,10 @@ def test_strerror_and_argument_checks_need_no_gpu(libpath):
     assert lib.kf_set_tuning(None, ctypes.byref(t)) == kf.KF_EINVAL
     assert lib.kf_autotune_fit(None, None, None, None, None, None, None, None) == kf.KF_EINVAL
     assert lib.kf_autotune_build(None, None, None, None, 6, None, None, None) == kf.KF_EINVAL
+    # measured peaks and the staged-wait test hook
+    v = ctypes.c_double()
+    assert lib.kf_measure_peak(None, kf.PEAK_FP32, None, ctypes.byref(v)) == kf.KF_EINVAL
+    assert lib.kf_test_stage_fault(None, -1, 0) == kf.KF_EINVAL
 
 
 def test_binding_constants_match_the_header():
@@ -90,7 +94,8 @@ def test_binding_constants_match_the_header():
               "KF_ST_DEVICE_TIMEOUT": kf.ST_DEVICE_TIMEOUT, "KF_ST_STOPPED": kf.ST_STOPPED,
               "KF_BIN_ETA": kf.BIN_ETA, "KF_BIN_PHI": kf.BIN_PHI, "KF_BIN_ETA_MAX": kf.BIN_ETA_MAX,
               "KF_NBINS": kf.NBINS, "KF_MAX_HITS_PER_SEGMENT": kf.MAX_HITS_PER_SEGMENT,
-              "KF_MAX_SLOTS": kf.MAX_SLOTS, "KF_NOALLOC_MAX_TRACKS": kf.NOALLOC_MAX_TRACKS}
+              "KF_MAX_SLOTS": kf.MAX_SLOTS, "KF_NOALLOC_MAX_TRACKS": kf.NOALLOC_MAX_TRACKS,
+              "KF_PEAK_FP32": kf.PEAK_FP32, "KF_PEAK_FP64": kf.PEAK_FP64}
     for name, value in mirror.items():
         assert name in defs, name
         assert defs[name] == value, (name, defs[name], value)

@@ -120,3 +120,39 @@ def test_truncation_keeps_the_best_ranked_children():
         keys = [(-two["nhits"][i, k], two["chi2"][i, k]) for k in range(n)]
         assert keys == sorted(keys)
         assert (two["nhits"][i, 0], ) <= (full["nhits"][i, 0], )
+
+
+def test_parity_path_chi2_reproduces_the_oracle_build():
+    """oracle.parity (the near-tie classifier of the build parity checks):
+    the chi2 of the oracle's own best path, re-evaluated along that path,
+    equals the build's chi2_tot; the same paths compare as all identical; and
+    the second-ranked candidate's path, where it differs, never ranks better."""
+    from oracle import parity
+    b = S.make_build_batch(31, 1, 40)
+    det = b.det
+    r = O.fit(b.seeds.par, b.seeds.cov, b.seeds.charge, b.fit_hits.xyz, b.fit_hits.valid, det.radii[:3], det.bz,
+              det.sigma_xy, det.sigma_z)
+    radii = [det.radii[l] for l in b.build_layers]
+    ob = O.build_tracks(r["par"], r["cov"], b.seeds.charge, b.seed_event, b.layer_xyz, b.layer_off, radii, det.bz,
+                        det.sigma_xy, det.sigma_z, chi2_cut=30.0, max_cands=6)
+    V = np.array([det.sigma_xy ** 2, det.sigma_xy ** 2, det.sigma_z ** 2])
+    a = O.a_coef(b.seeds.charge, det.bz)
+    Lb = len(b.build_layers)
+
+    def hit_of(t, l, h):
+        return b.layer_xyz[:, b.layer_off[int(b.seed_event[t]) * Lb + l] + h].astype(np.float64)
+    for t in range(len(a)):
+        best = ob["hits"][t, 0]
+        hits = [hit_of(t, l, int(best[l])) if best[l] >= 0 else None for l in range(Lb)]
+        c = [x for x in parity.path_chi2(r["par"][t], r["cov"][t], a[t], hits, radii, V) if x is not None]
+        assert len(c) == ob["nhits"][t, 0]
+        assert sum(c) == pytest.approx(ob["chi2"][t, 0], rel=1e-12, abs=1e-12)
+    same, ties, bad = parity.classify(ob["hits"][:, 0], ob["hits"][:, 0], r["par"], r["cov"], a, hit_of, radii, V)
+    assert same == len(a) and not ties and not bad
+    two = ob["n_cands"] >= 2
+    _, ties, bad = parity.classify(ob["hits"][two, 1], ob["hits"][two, 0], r["par"][two], r["cov"][two], a[two],
+                                   lambda t, l, h: hit_of(np.nonzero(two)[0][t], l, h), radii, V)
+    for _, p_second, p_best, c_second, c_best in bad:  # ranked by (hits desc, chi2 asc)
+        n_second, n_best = sum(h >= 0 for h in p_second), sum(h >= 0 for h in p_best)
+        assert n_second < n_best or (n_second == n_best and c_second >= c_best)
+    assert len(bad) + len(ties) > 0
