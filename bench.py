@@ -224,7 +224,7 @@ def profile_value(name, key, files=FIT_SOURCES):
         if ":" in ln and not ln.lstrip().startswith("#"):
             k, v = ln.split(":", 1)
             kv[k.strip()] = v.strip()
-    if kv.get("source_hash") != kernel_source_hash(files):
+    if kv.get("source_hash") != kernel_source_hash(files) or key not in kv:
         return None
     return float(kv[key])
 

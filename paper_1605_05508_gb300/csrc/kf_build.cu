@@ -31,6 +31,7 @@
 #include "kf_math.cuh"
 #include "kf_tma.cuh"
 
+#include <algorithm>
 #include <climits>
 #include <vector>
 
@@ -83,19 +84,19 @@ __device__ __forceinline__ int wrap_phi(int d) {  // to [-KF_BIN_PHI/2, KF_BIN_P
 // Window of a predicted candidate: S^-1 = (C_pos + V)^-1, and the eta rows
 // e0..e1 and phi bins fa0..fa1, fb0..fb1 (second part when the window wraps
 // around phi = +-pi) that can hold a hit with chi2 < cut at radius R.
-__device__ __forceinline__ void hit_window(const float p[6], const float lo[3], const float C[21], float R,
-                                           const BuildStepArgs& Args, float Si[6], int& e0, int& e1, int& fa0,
+__device__ __forceinline__ void hit_window(const float p[6], const float lo[3], const float C[21], float R, float v0,
+                                           float v1, float v2, float cut, float Si[6], int& e0, int& e1, int& fa0,
                                            int& fa1, int& fb0, int& fb1) {
-  kf::inverse_S(C, Args.v0, Args.v1, Args.v2, Si);
+  kf::inverse_S(C, v0, v1, v2, Si);
   const float X = p[0] + lo[0], Y = p[1] + lo[1], Z = p[2] + lo[2];
   const float rr = sqrtf(X * X + Y * Y);
   const float cph = X / rr, sph = Y / rr;
-  const float s00 = C[0] + Args.v0, s10 = C[1], s11 = C[2] + Args.v1, s22 = C[5] + Args.v2;
+  const float s00 = C[0] + v0, s10 = C[1], s11 = C[2] + v1, s22 = C[5] + v2;
   const float Stt = sph * sph * s00 - 2.f * sph * cph * s10 + cph * cph * s11;
   const float Snn = cph * cph * s00 + 2.f * sph * cph * s10 + sph * sph * s11;
-  const float wt = sqrtf(Args.cut * fmaxf(Stt, 0.f));
-  const float wn = sqrtf(Args.cut * fmaxf(Snn, 0.f));
-  const float wz = sqrtf(Args.cut * fmaxf(s22, 0.f));
+  const float wt = sqrtf(cut * fmaxf(Stt, 0.f));
+  const float wn = sqrtf(cut * fmaxf(Snn, 0.f));
+  const float wz = sqrtf(cut * fmaxf(s22, 0.f));
   // A hit with chi2 < cut lies within wt of the prediction along the tangent,
   // wn along the normal and wz in z (chi2 >= (u.r)^2 / u^T S u for any unit
   // u), so its distance from the axis is between R - wn and
@@ -263,7 +264,7 @@ __global__ void __launch_bounds__(kBuildThreads, kBuildBlocksPerSM) build_step_k
   const bool scan = active && !stopped;
   float Si[6];
   int e0 = 0, e1 = -1, fa0 = 0, fa1 = KF_BIN_PHI - 1, fb0 = 0, fb1 = -1;
-  if (scan) hit_window(p, lo, C, D.R, Args, Si, e0, e1, fa0, fa1, fb0, fb1);
+  if (scan) hit_window(p, lo, C, D.R, Args.v0, Args.v1, Args.v2, Args.cut, Si, e0, e1, fa0, fa1, fb0, fb1);
   const int32_t* boff = D.bin_off + int64_t(seg) * (KF_NBINS + 1);
 
   // ---- warp union of the windows and staging (TILE > 0)
@@ -524,6 +525,60 @@ __global__ void __launch_bounds__(kBuildThreads, kBuildBlocksPerSM) build_step_k
   if (seed_ok && k == 0) D.out.ncand[j] = int8_t(n_win);
 }
 
+// Chi2 scan of one predicted candidate's window (one thread): rows e0..e1,
+// each the hits of bins fa0..fa1 then fb0..fb1 of the segment's binned hits
+// `hs` (bin offsets `boff`); the next row's bin offsets and the next hit are
+// loaded one step ahead.  Every hit with chi2 < cut (and an id below the
+// segment limit) becomes a child key (nh + 1, chi2tot + chi2, parent rank k,
+// id + 1) in the sorted list (L, P).  Returns whether any hit was compatible.
+template <int LW>
+__device__ __forceinline__ bool scan_window(const float p[6], const float lo[3], const float Si[6], int e0, int e1,
+                                            int fa0, int fa1, int fb0, int fb1, const int32_t* boff,
+                                            const float4* hs, float cut, int nh, float chi2tot, int k,
+                                            uint64_t (&L)[LW], int (&P)[LW]) {
+  bool any = false;
+  const bool two = fb1 >= fb0;
+  int na0 = 0, na1 = 0, nb0 = 0, nb1 = 0;
+  if (e0 <= e1) {
+    const int32_t* q = boff + e0 * KF_BIN_PHI;
+    na0 = q[fa0];
+    na1 = q[fa1 + 1];
+    if (two) {
+      nb0 = q[fb0];
+      nb1 = q[fb1 + 1];
+    }
+  }
+  for (int er = e0; er <= e1; ++er) {
+    const int a0 = na0, na = na1 - na0, b0 = nb0, n = na + (nb1 - nb0);
+    if (er < e1) {
+      const int32_t* q = boff + (er + 1) * KF_BIN_PHI;
+      na0 = q[fa0];
+      na1 = q[fa1 + 1];
+      if (two) {
+        nb0 = q[fb0];
+        nb1 = q[fb1 + 1];
+      }
+    }
+    float4 mn = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (n > 0) mn = hs[na > 0 ? a0 : b0];
+    for (int v = 0; v < n; ++v) {
+      const int u = v < na ? a0 + v : b0 + (v - na);
+      const float4 m = mn;
+      if (v + 1 < n) mn = hs[v + 1 < na ? a0 + v + 1 : b0 + (v + 1 - na)];
+      const float r0 = (m.x - p[0]) - lo[0], r1 = (m.y - p[1]) - lo[1], r2 = (m.z - p[2]) - lo[2];
+      const float c2 = kf::chi2_of(r0, r1, r2, Si);
+      if (c2 < cut) {
+        const int id = __float_as_int(m.w);
+        if (id < KF_MAX_HITS_PER_SEGMENT) {
+          list_insert(L, P, make_key(nh + 1, chi2tot + c2, k, id + 1), u);
+          any = true;
+        }
+      }
+    }
+  }
+  return any;
+}
+
 // ---- candidate-packed step (scan scheme 2)
 //
 // The same computation as build_step_kernel, with threads assigned to live
@@ -671,50 +726,9 @@ __global__ void __launch_bounds__(NT, kBuildBlocksPerSM * kBuildThreads / NT) bu
       if (!stopped) {
         float Si[6];
         int e0 = 0, e1 = -1, fa0 = 0, fa1 = KF_BIN_PHI - 1, fb0 = 0, fb1 = -1;
-        hit_window(p, lo, C, D.R, Args, Si, e0, e1, fa0, fa1, fb0, fb1);
-        const int32_t* boff = D.bin_off + int64_t(s_seg[sd]) * (KF_NBINS + 1);
-        const float4* hs = D.hits + s_h0[sd];
-        // rows e0..e1, each the hits of bins fa0..fa1 then fb0..fb1: the next
-        // row's bin offsets and the next hit are loaded one step ahead
-        const bool two = fb1 >= fb0;
-        int na0 = 0, na1 = 0, nb0 = 0, nb1 = 0;
-        if (e0 <= e1) {
-          const int32_t* q = boff + e0 * KF_BIN_PHI;
-          na0 = q[fa0];
-          na1 = q[fa1 + 1];
-          if (two) {
-            nb0 = q[fb0];
-            nb1 = q[fb1 + 1];
-          }
-        }
-        for (int er = e0; er <= e1; ++er) {
-          const int a0 = na0, na = na1 - na0, b0 = nb0, n = na + (nb1 - nb0);
-          if (er < e1) {
-            const int32_t* q = boff + (er + 1) * KF_BIN_PHI;
-            na0 = q[fa0];
-            na1 = q[fa1 + 1];
-            if (two) {
-              nb0 = q[fb0];
-              nb1 = q[fb1 + 1];
-            }
-          }
-          float4 mn = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (n > 0) mn = hs[na > 0 ? a0 : b0];
-          for (int v = 0; v < n; ++v) {
-            const int u = v < na ? a0 + v : b0 + (v - na);
-            const float4 m = mn;
-            if (v + 1 < n) mn = hs[v + 1 < na ? a0 + v + 1 : b0 + (v + 1 - na)];
-            const float r0 = (m.x - p[0]) - lo[0], r1 = (m.y - p[1]) - lo[1], r2 = (m.z - p[2]) - lo[2];
-            const float c2 = kf::chi2_of(r0, r1, r2, Si);
-            if (c2 < Args.cut) {
-              const int id = __float_as_int(m.w);
-              if (id < KF_MAX_HITS_PER_SEGMENT) {
-                list_insert(L, P, make_key(nh + 1, chi2tot + c2, k, id + 1), u);
-                any = true;
-              }
-            }
-          }
-        }
+        hit_window(p, lo, C, D.R, Args.v0, Args.v1, Args.v2, Args.cut, Si, e0, e1, fa0, fa1, fb0, fb1);
+        any = scan_window(p, lo, Si, e0, e1, fa0, fa1, fb0, fb1, D.bin_off + int64_t(s_seg[sd]) * (KF_NBINS + 1),
+                          D.hits + s_h0[sd], Args.cut, nh, chi2tot, k, L, P);
       }
       // no compatible hit (or a stopped candidate): one child without a hit
       if (!any) list_insert(L, P, make_key(nh, chi2tot, k, 0), -1);
@@ -813,6 +827,222 @@ __global__ void __launch_bounds__(NT, kBuildBlocksPerSM * kBuildThreads / NT) bu
   }
   __syncthreads();  // the next layer rewrites sD and the per-seed tables
   }
+}
+
+// ---- register-resident build (thread layout 4)
+//
+// The same computation per candidate as the other layouts, organised so that
+// a candidate's state never leaves the registers between layers and no
+// block-wide barrier is needed.  A warp takes a group of G = 32 / W seeds
+// (consecutive in (eta, phi) order, so their windows share cached bins and
+// hits); lane k of a seed's W lanes holds the seed's candidate of rank k.  Per
+// building layer, every live lane propagates its candidate, derives the window
+// and scans it (scan_window) into a sorted list of its best children's keys;
+// the seed's lanes merge their lists by segmented warp reductions over the
+// 64-bit keys (two 32-bit min-reductions on the lanes of the segment) into
+// the seed's best max_cands, ranked by the same total order; lane k then
+// pulls the predicted state and S^-1 of its winner's parent from that lane by
+// shuffles and applies the Kalman update with the winner's hit.  Only the
+// per-layer history (parent rank, hit id) goes to memory until the last
+// layer, whose candidates are written to the final buffer.  Groups are
+// independent, so warps run at their own pace (no block barrier).  The keys
+// are a total order and every candidate goes through the same functions as in
+// the other layouts, so the results are bitwise theirs.
+
+// Segmented merge: the W lanes of a seed (mask seg) hold sorted lists (L, P)
+// of their own children; the best max_cands keys of the union are found by
+// min-reductions on the high and low halves of the head keys.  Lane k of the
+// segment receives the k-th best (key, hit position); every lane the number
+// of children kept.
+template <int W, int LW>
+__device__ __forceinline__ void merge_segment(uint64_t (&L)[LW], int (&P)[LW], int max_cands, int k, unsigned seg,
+                                              uint64_t& my_key, int& my_pos, int& n_win) {
+#pragma unroll
+  for (int r = 0; r < W; ++r) {
+    if (r < max_cands) {  // uniform over the launch
+      const uint64_t head = L[0];
+      const unsigned hi = unsigned(head >> 32), lw = unsigned(head);
+      const unsigned mhi = __reduce_min_sync(seg, hi);
+      const unsigned mlo = __reduce_min_sync(seg, hi == mhi ? lw : 0xffffffffu);
+      const uint64_t m = (uint64_t(mhi) << 32) | mlo;
+      const bool mine = head == m && m != kNoKey;
+      const unsigned bal = __ballot_sync(seg, mine) & seg;
+      const int wl = bal ? __ffs(bal) - 1 : __ffs(seg) - 1;
+      const int wpos = __shfl_sync(seg, P[0], wl);
+      if (mine) {
+#pragma unroll
+        for (int t = 0; t < LW - 1; ++t) {
+          L[t] = L[t + 1];
+          P[t] = P[t + 1];
+        }
+        L[LW - 1] = kNoKey;
+        P[LW - 1] = -1;
+      }
+      if (m != kNoKey) {
+        if (k == r) {
+          my_key = m;
+          my_pos = wpos;
+        }
+        ++n_win;
+      }
+    }
+  }
+}
+
+template <int W>
+__global__ void __launch_bounds__(kResThreads, kResBlocksPerSM) build_resident_kernel(const BuildResidentArgs A) {
+  constexpr int G = 32 / W;  // seeds per group
+  const int lane = threadIdx.x & 31;
+  const int g = lane / W, k = lane - g * W;
+  // the seed's lanes; lanes past G * W form a segment of their own with no seed
+  const unsigned seg = g < G ? ((1u << W) - 1u) << (g * W) : (kFull << ((G * W) & 31));
+  const int64_t S8 = A.S * kGroup;
+  const int64_t n_groups = (A.S + G - 1) / G;
+  const int64_t n_warps = (int64_t(gridDim.x) * kResThreads) >> 5;
+  for (int64_t gi = (int64_t(blockIdx.x) * kResThreads + threadIdx.x) >> 5; gi < n_groups; gi += n_warps) {
+    const int64_t j = gi * G + g;
+    const bool seed_ok = g < G && j < A.S;
+    int e = 0, nc = 0;
+    float a = A.a_scale;
+    if (seed_ok) {
+      e = A.seed_evt ? A.seed_evt[j] : 0;
+      a = A.a_scale * float(A.charge[A.seed_perm[j]]);
+      nc = A.in.ncand[j];
+    }
+    bool active = seed_ok && k < nc;
+    float p[6], lo[3], C[21];
+    float chi2tot = 0.f;
+    int nh = 0;
+    int32_t st = 0;
+    if (active) {
+      const int64_t slot = cand_slot(j, k, A.S, A.in_rm);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) p[c] = A.in.par[c * S8 + slot];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) lo[c] = A.in.par[(6 + c) * S8 + slot];
+#pragma unroll
+      for (int c = 0; c < 21; ++c) C[c] = A.in.cov[c * S8 + slot];
+      chi2tot = A.in.chi2[slot];
+      const int32_t meta = A.in.meta[slot];
+      nh = meta & 0xff;
+      st = meta >> 8;
+    } else {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) p[c] = 0.f;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) lo[c] = 0.f;
+#pragma unroll
+      for (int c = 0; c < 21; ++c) C[c] = 0.f;
+    }
+    int n_win = nc;
+    for (int l = A.l0; l < A.n_layers; ++l) {
+      const int64_t sg = int64_t(e) * A.n_layers + l;
+      const int64_t h0 = seed_ok ? A.seg_off[sg] : 0;
+      bool stopped = (st & KF_ST_STOPPED) != 0;
+      if (active && !stopped) {
+        const int r = kf::propagate<float, kNewtonBuild, true>(p, lo, C, a, A.R[l]);
+        if (r) {
+          st |= r;
+          stopped = true;
+        } else if (A.x_x0[l] > 0.f) {
+          kf::scatter(p, lo, C, A.x_x0[l], A.mass);
+        }
+      }
+      float Si[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      uint64_t L[W];
+      int P[W];
+#pragma unroll
+      for (int t = 0; t < W; ++t) {
+        L[t] = kNoKey;
+        P[t] = -1;
+      }
+      if (active) {
+        bool any = false;
+        if (!stopped) {
+          int e0 = 0, e1 = -1, fa0 = 0, fa1 = KF_BIN_PHI - 1, fb0 = 0, fb1 = -1;
+          hit_window(p, lo, C, A.R[l], A.v0, A.v1, A.v2, A.cut, Si, e0, e1, fa0, fa1, fb0, fb1);
+          any = scan_window(p, lo, Si, e0, e1, fa0, fa1, fb0, fb1, A.bin_off + sg * (KF_NBINS + 1), A.hits + h0,
+                            A.cut, nh, chi2tot, k, L, P);
+        }
+        // no compatible hit (or a stopped candidate): one child without a hit
+        if (!any) list_insert(L, P, make_key(nh, chi2tot, k, 0), -1);
+      }
+      // clone engine: the seed's best max_cands children
+      uint64_t my_key = kNoKey;
+      int my_pos = -1;
+      n_win = 0;
+      merge_segment<W, W>(L, P, A.max_cands, k, seg, my_key, my_pos, n_win);
+      // materialise: lane k takes its winner's parent prediction and S^-1
+      const int src = k < n_win ? g * W + int((my_key >> 21) & 7u) : lane;
+      float q[6], ql[3], qC[21], qS[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) q[c] = __shfl_sync(seg, p[c], src);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) ql[c] = __shfl_sync(seg, lo[c], src);
+#pragma unroll
+      for (int c = 0; c < 21; ++c) qC[c] = __shfl_sync(seg, C[c], src);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) qS[c] = __shfl_sync(seg, Si[c], src);
+      const int32_t pst = __shfl_sync(seg, st, src);
+      const int pstopped = __shfl_sync(seg, int(stopped), src);
+      active = seed_ok && k < n_win;
+      if (active) {
+        const int nh_new = 255 - int(my_key >> 56);
+        const float chi2_new = __uint_as_float(uint32_t(my_key >> 24));
+        const int hit_plus1 = int(my_key & 0x1fffffu);
+        int32_t st_new = pst;
+        if (hit_plus1 > 0) {
+          const float4 m = A.hits[h0 + my_pos];
+          float r0, r1, r2;
+          kf::residual<float, true>(q, ql, m.x, m.y, m.z, r0, r1, r2);
+          kf::kalman_update<float, true>(q, ql, qC, qS, r0, r1, r2, A.v0, A.v1, A.v2);
+        } else if (!pstopped) {
+          st_new |= KF_ST_NO_HIT;
+        }
+        const int64_t hslot = int64_t(l) * S8 + cand_slot(j, k, A.S, l + 1 < A.rm_buffers);
+        A.hist_parent[hslot] = int8_t((my_key >> 21) & 7u);
+        A.hist_hit[hslot] = hit_plus1 - 1;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) p[c] = q[c];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) lo[c] = ql[c];
+#pragma unroll
+        for (int c = 0; c < 21; ++c) C[c] = qC[c];
+        chi2tot = chi2_new;
+        nh = nh_new;
+        st = st_new;
+      }
+    }
+    // the candidates after the last layer, for the final selection
+    if (active) {
+      const int64_t slot = cand_slot(j, k, A.S, A.out_rm);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) A.out.par[c * S8 + slot] = p[c];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) A.out.par[(6 + c) * S8 + slot] = lo[c];
+#pragma unroll
+      for (int c = 0; c < 21; ++c) A.out.cov[c * S8 + slot] = C[c];
+      A.out.chi2[slot] = chi2tot;
+      A.out.meta[slot] = nh | (st << 8);
+    }
+    if (seed_ok && k == 0) A.out.ncand[j] = int8_t(n_win);
+  }
+}
+
+cudaError_t launch_build_resident(const BuildResidentArgs& a, int num_sms, cudaStream_t st) {
+  if (a.S <= 0) return cudaSuccess;
+  const int W = resident_lanes(a.max_cands);
+  const int64_t groups = (a.S + (32 / W) - 1) / (32 / W);
+  const int64_t need = (groups + kResThreads / 32 - 1) / (kResThreads / 32);
+  const int grid = int(std::max<int64_t>(1, std::min<int64_t>(need, int64_t(num_sms) * kResBlocksPerSM)));
+  switch (W) {
+    case 1: build_resident_kernel<1><<<grid, kResThreads, 0, st>>>(a); break;
+    case 2: build_resident_kernel<2><<<grid, kResThreads, 0, st>>>(a); break;
+    case 4: build_resident_kernel<4><<<grid, kResThreads, 0, st>>>(a); break;
+    case 6: build_resident_kernel<6><<<grid, kResThreads, 0, st>>>(a); break;
+    default: build_resident_kernel<8><<<grid, kResThreads, 0, st>>>(a); break;
+  }
+  return cudaGetLastError();
 }
 
 __global__ void build_init_kernel(const BuildInitArgs A) {
@@ -1074,6 +1304,52 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
   // next buffer could overwrite what a block still on the previous layer
   // reads in the same memory.  Layers up to the switch run one launch each.
   // The grouped layouts launch once per layer.
+  if (ctx->tune.build_scan == 4) {
+    // register-resident layout: one launch takes every seed through all
+    // layers, from buffer 0 (the seeds) to the other buffer
+    BuildResidentArgs ra;
+    ra.in = bufA;
+    ra.out = bufB;
+    ra.hist_parent = hist_parent;
+    ra.hist_hit = hist_hit;
+    ra.seed_evt = evt;
+    ra.seed_perm = perm;
+    ra.charge = seeds->charge;
+    ra.hits = reinterpret_cast<const float4*>(bins->hits);
+    ra.bin_off = bins->bin_off;
+    ra.seg_off = bins->seg_off;
+    ra.S = S;
+    ra.n_layers = L;
+    ra.l0 = 0;
+    ra.rm_buffers = rm_buffers;
+    ra.max_cands = max_cands;
+    ra.in_rm = 0 < rm_buffers;
+    ra.out_rm = L < rm_buffers;
+    ra.a_scale = float(kCLight * double(ctx->cfg.bz_tesla));
+    ra.v0 = v0;
+    ra.v1 = v0;
+    ra.v2 = v2;
+    ra.cut = ctx->cfg.chi2_cut;
+    ra.mass = ctx->mass;
+    for (int l = 0; l < kMaxLayers; ++l) {
+      ra.R[l] = l < L ? ctx->radius[bins->first_layer + l] : 0.f;
+      ra.x_x0[l] = l < L ? ctx->x_x0[bins->first_layer + l] : 0.f;
+    }
+    KF_CUDA_TRY(ctx, launch_build_resident(ra, ctx->num_sms, s));
+    BuildFinalArgs fa;
+    fa.cand = bufB;
+    fa.hist_parent = hist_parent;
+    fa.hist_hit = hist_hit;
+    fa.seed_perm = perm;
+    fa.S = S;
+    fa.n_layers = L;
+    fa.max_cands = max_cands;
+    fa.rm_buffers = rm_buffers;
+    fa.out = *out;
+    build_final_kernel<<<int((S + 127) / 128), 128, 0, s>>>(fa);
+    KF_CUDA_TRY(ctx, cudaGetLastError());
+    return KF_OK;
+  }
   const int first_fused = ctx->tune.build_scan >= 2 ? (rm_buffers > L ? 0 : std::min(L, rm_buffers)) : L;
   for (int l = 0; l < (first_fused < L ? first_fused + 1 : L); ++l) {
     const bool fused = l == first_fused;

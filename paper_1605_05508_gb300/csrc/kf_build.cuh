@@ -7,6 +7,7 @@
 #include <cstdint>
 
 #include "../../include/kf.h"
+#include "kf_internal.h"
 
 namespace kfi {
 
@@ -135,6 +136,37 @@ inline int build_pack_seeds(int64_t seeds, int scan, int max_cands, int num_sms)
   const int64_t waves = ((seeds + per_block - 1) / per_block + wave - 1) / wave;
   return int((seeds + waves * wave - 1) / (waves * wave));
 }
+// Register-resident build (thread layout 4, build_resident_kernel): each warp
+// takes groups of 32 / W seeds, W lanes a seed (W >= max_cands, one candidate
+// slot a lane), through building layers l0 .. n_layers-1 with every
+// candidate's state in registers; it reads buffer l0 and writes only the
+// per-layer history and buffer n_layers.
+constexpr int kResThreads = 128;
+constexpr int kResBlocksPerSM = 4;
+struct BuildResidentArgs {
+  CandBuf in;                // buffer l0 (layout in_rm)
+  CandBuf out;               // buffer n_layers (layout out_rm); must not alias `in`
+  int8_t* hist_parent;       // [n_layers][S8]: layer l's slots in the layout of buffer l + 1
+  int32_t* hist_hit;         // [n_layers][S8]
+  const int32_t* seed_evt;   // [S] sorted position -> event, or null (event 0)
+  const int32_t* seed_perm;  // [S] sorted position -> seed index
+  const int8_t* charge;      // [S] by seed index
+  const float4* hits;
+  const int32_t* bin_off;
+  const int64_t* seg_off;
+  int64_t S;
+  int n_layers, l0, rm_buffers, max_cands;
+  int in_rm, out_rm;
+  float a_scale, v0, v1, v2, cut, mass;
+  float R[kMaxLayers];     // building layer radii
+  float x_x0[kMaxLayers];  // building layer thickness in radiation lengths (0: none)
+};
+// Lanes per seed of the resident layout for max_cands (1, 2, 4, 6 or 8).
+inline int resident_lanes(int max_cands) {
+  return max_cands <= 2 ? max_cands : max_cands <= 4 ? 4 : max_cands <= 6 ? 6 : 8;
+}
+cudaError_t launch_build_resident(const BuildResidentArgs& a, int num_sms, cudaStream_t st);
+
 cudaError_t launch_build_init(const BuildInitArgs& a, cudaStream_t st);
 cudaError_t launch_build_final(const BuildFinalArgs& a, cudaStream_t st);
 

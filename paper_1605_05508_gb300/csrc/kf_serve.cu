@@ -614,7 +614,9 @@ static void scheduler(Serve* sv) {
       // resident blocks x 80 seeds) a block's rounds hold too few parents and
       // the grouped layout, 8 lanes per seed, ends such a small step sooner
       // (the same bits either way).
-      int scan = sv->tune.build_scan;
+      // the register-resident layout takes a batch through all its layers in
+      // one launch; events stepped one layer at a time use the packed one
+      int scan = sv->tune.build_scan == 4 ? 2 : sv->tune.build_scan;
       const int64_t pack_min = sv->cfg.pack_min_seeds > 0
                                    ? sv->cfg.pack_min_seeds
                                    : int64_t(sv->ctx->num_sms) * kBuildBlocksPerSM * 80;
