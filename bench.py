@@ -654,8 +654,8 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist, peaks=None):
         times = {}
         for tile in (0, 512):
             for lw in (8, 4):
-                for scan in (0, 1, 2, 3):
-                    if (lw == 4 and N > 4) or (scan >= 2 and tile > 0):
+                for scan in (0, 1, 2, 3, 4):
+                    if (lw == 4 and N > 4) or (scan >= 2 and tile > 0) or (scan == 4 and lw == 4):
                         continue
                     kf.kf_set_tuning(ctx, 128, tile, lw, scan)
                     name = BUILD_LAYOUTS[scan]
@@ -689,6 +689,42 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist, peaks=None):
             good[ok] += batch.layer_truth[h[ok]] == own[ok]
         return good
     good = correct_hits()
+    # the plain per-event FP64 form of the same step: kf_fit_f64 over the
+    # seeding layers (one launch per event and layer), the same hit binning,
+    # kf_build_f64 (one launch per event and building layer)
+    f64 = dict(dtype=torch.float64, device=dev)
+    s64 = kf.Tracks(s.par.double(), s.cov.double(), s.charge)
+    fo64 = kf.Tracks(torch.empty((6, n), **f64), torch.empty((21, n), **f64), s.charge)
+    out64 = kf.BuildResultF64(best=kf.Tracks(torch.empty((6, n), **f64), torch.empty((21, n), **f64), s.charge),
+                              chi2_tot=torch.empty(n, **f64), n_hits=torch.empty(n, **i32),
+                              status=torch.empty(n, **i32), hit_idx=torch.empty((Lb, n), **i32))
+    event_off = [int(v) for v in np.searchsorted(batch.seed_event, np.arange(E + 1))]
+    t64 = np.zeros(3)
+    for it in range(3):  # one untimed step, two timed
+        evs[0].record(stream)
+        kf.kf_fit_f64(ctx, s64, fh, fo64, event_off, None, fst, stream)
+        evs[1].record(stream)
+        kf.kf_bin_hits(ctx, lh, bins, stream)
+        evs[2].record(stream)
+        kf.kf_build_f64(ctx, fo64, event_off, bins, 6, out64, stream)
+        evs[3].record(stream)
+        torch.cuda.synchronize()
+        if it:
+            t64 += [evs[0].elapsed_time(evs[1]), evs[1].elapsed_time(evs[2]), evs[2].elapsed_time(evs[3])]
+    t64 /= 2
+    tot64 = max_over_ranks(float(t64.sum()), dist, dev)
+    same64 = float((out64.hit_idx.cpu().numpy() == hidx6).all(axis=0).mean())
+    plain_f64 = {"ms_per_step": tot64, "phases_ms": {"seed_fit": float(t64[0]), "bin_hits": float(t64[1]),
+                                                     "build": float(t64[2])},
+                 "events_per_s": world * E / (tot64 / 1e3),
+                 "fp32_batched_events_per_s": world * E / (tot6 / 1e3),
+                 "speedup_events_per_s": tot64 / tot6,
+                 "build_phase_speedup": float(t64[2] / t6[2]),
+                 "launches_per_step": E * len(batch.seed_layers) + 3 + 1 + E * Lb + 1,
+                 "best_paths_equal_to_fp32_build": same64,
+                 "form": "kf_fit_f64 + kf_bin_hits + kf_build_f64: one thread per seed, one launch per event and "
+                         "layer, candidates in global memory, FP64 arithmetic"}
+    del s64, fo64, out64
     # re-fit of the built tracks over all 10 layers (kf_refit)
     ro = kf.Tracks(torch.empty((6, n), device=dev), torch.empty((21, n), device=dev), s.charge,
                    torch.empty((3, n), device=dev))
@@ -741,6 +777,7 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist, peaks=None):
            "best_hit_N1": {"ms_per_step": tot1, "value": world * n * Lb / (tot1 / 1e3), "build_ms": float(t1[2]),
                            "tuning": tune1, "build_ms_by_setting": sweep1},
            "tuning": tune6, "build_ms_by_setting": sweep6, "efficiency_and_refit": efficiency,
+           "plain_f64": plain_f64,
            "clone_engine_curve": {"seeds": SEED_READING, "points": curve},
            "bin_order": "scatter order inside each bin (bin_unordered 1; the build's results are the same bits)",
            # seed fit (3 layer launches) + hit binning (count, scan, scatter) + kf_build (seed
@@ -922,6 +959,52 @@ def precision_leg(a, kf, torch, dev, stream, rank):
     return res
 
 
+def serial_f64_events(kf, ctx, pool, dev):
+    """The plain per-event FP64 GPU form of a request, one event at a time:
+    the event's inputs copied from pinned host memory, kf_fit_f64 over the
+    seeding layers, kf_bin_hits, kf_build_f64 (N = 6), and the best
+    candidates' results copied back; wall-clock latency per event."""
+    import torch
+    pinned = []
+    for ev in pool:
+        pinned.append({k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in ev.items()})
+
+    def one(ev):
+        n, Lb = ev["seed_par"].shape[1], ev["layer_off"].shape[0] - 1
+        D = lambda t: t.to(dev, non_blocking=True)
+        f64 = dict(dtype=torch.float64, device=dev)
+        i32 = dict(dtype=torch.int32, device=dev)
+        q = D(ev["seed_charge"])
+        s64 = kf.Tracks(D(ev["seed_par"]).double(), D(ev["seed_cov"]).double(), q)
+        fo = kf.Tracks(torch.empty((6, n), **f64), torch.empty((21, n), **f64), q)
+        st = torch.empty(n, **i32)
+        kf.kf_fit_f64(ctx, s64, kf.TrackHits(D(ev["seed_hits"]), D(ev["seed_valid"])), fo, [0, n], None, st)
+        xyz = D(ev["layer_xyz"])
+        lh = kf.LayerHits(xyz, D(ev["layer_off"]), 1, Lb, ev["seed_hits"].shape[0])
+        bins = kf.HitBins(torch.empty((xyz.shape[1], 4), device=dev), torch.empty((Lb, kf.NBINS + 1), **i32))
+        kf.kf_bin_hits(ctx, lh, bins)
+        out = kf.BuildResultF64(best=kf.Tracks(torch.empty((6, n), **f64), torch.empty((21, n), **f64), q),
+                                chi2_tot=torch.empty(n, **f64), n_hits=torch.empty(n, **i32),
+                                status=torch.empty(n, **i32), hit_idx=torch.empty((Lb, n), **i32))
+        kf.kf_build_f64(ctx, fo, [0, n], bins, 6, out)
+        for t in (out.best.par, out.best.cov, out.chi2_tot, out.n_hits, out.status, out.hit_idx):
+            t.cpu()
+    for ev in pinned[:4]:
+        one(ev)
+    torch.cuda.synchronize()
+    lat = []
+    t0 = time.perf_counter()
+    for ev in pinned:
+        t1 = time.perf_counter()
+        one(ev)
+        lat.append((time.perf_counter() - t1) * 1e3)
+    wall = time.perf_counter() - t0
+    return {"events_per_s": len(pinned) / wall, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)),
+            "form": "one event at a time: H2D from pinned memory, kf_fit_f64, kf_bin_hits, kf_build_f64 (one launch "
+                    "per layer), D2H of the best candidates"}
+
+
 def serve_leg(a, kf, dev, rank, tuning=None):
     """Continuous-batching service (kf_submit / kf_poll) on a Poisson stream of
     events with log-uniform 500-50 000 tracks (3x noise hits per layer), the
@@ -938,6 +1021,7 @@ def serve_leg(a, kf, dev, rank, tuning=None):
                          layer_off=b.layer_off))
     det = S.barrel()
     ctx = kf.Context(det.radii, det.bz, det.sigma_xy, det.sigma_z, device=dev.index)
+    plain = serial_f64_events(kf, ctx, pool, dev)
     if tuning:  # the build leg's autotuned launch parameters (N = 6)
         kf.kf_set_tuning(ctx, **tuning)
     kf.kf_serve_start(ctx, 3, 7, 6, max_slots=kf.MAX_SLOTS, max_queue=1 << 16, device_arena_bytes=16 << 30,
@@ -1014,6 +1098,8 @@ def serve_leg(a, kf, dev, rank, tuning=None):
                                                               "p50_ms": float(np.percentile(lat_sat, 50)),
                                                               "p99_ms": float(np.percentile(lat_sat, 99))},
             "poisson": runs, "serial_one_at_a_time_events_per_s": serial,
+            "plain_f64_one_at_a_time": plain,
+            "served_over_plain_f64_events_per_s": sat / plain["events_per_s"],
             "continuous_batching_speedup": sat / serial,
             "with_refit": {"events_per_s": sat_r, "p50_ms": float(np.percentile(lat_r, 50)),
                            "p99_ms": float(np.percentile(lat_r, 99)),

@@ -250,6 +250,33 @@ typedef struct {
 int kf_build(kf_ctx *ctx, const kf_tracks *seeds, const int64_t *seed_off, const kf_layer_hit_bins *bins,
              int32_t max_cands, kf_build_result *out, void *stream);
 
+/* Result of kf_build_f64 (device pointers, caller-allocated). */
+typedef struct {
+    kf_tracks_f64 best;      /* [n_seeds] best candidate: par, cov (best.charge is not written) */
+    double *chi2_tot;        /* [n_seeds] sum of the chi2 increments of the kept hits */
+    int32_t *n_hits;         /* [n_seeds] hits added on the building layers */
+    int32_t *status;         /* [n_seeds] KF_ST_* bits of the best candidate */
+    int32_t *hit_idx;        /* [n_layers][n_seeds] hit id per build layer, -1 = none */
+} kf_build_result_f64;
+
+/*
+ * The plain double-precision form of the combinatorial build (Sec. 3): the
+ * comparison form of kf_build, computing the same result in FP64 the
+ * straightforward way -- one thread per seed taking its candidates in turn,
+ * one launch per event and building layer, candidates in global memory
+ * between layers, the window of every candidate derived and scanned in
+ * double, the seed's best max_cands children kept in one sorted list, and
+ * only those updated.  Seeds are processed in their given order (no
+ * ordering by bin).
+ * seeds: [n_seeds] double states (e.g. from kf_fit_f64 over the seeding
+ * layers), seeds of event e = event_off[e] .. event_off[e+1] (HOST array,
+ * [n_events + 1], event_off[0] = 0, event_off[n_events] = n_seeds); bins:
+ * from kf_bin_hits; max_cands: 1 .. 8.  Scratch from the context.
+ * Errors: KF_EINVAL, KF_ENOMEM, KF_ECUDA.
+ */
+int kf_build_f64(kf_ctx *ctx, const kf_tracks_f64 *seeds, const int64_t *event_off, const kf_layer_hit_bins *bins,
+                 int32_t max_cands, kf_build_result_f64 *out, void *stream);
+
 /*
  * Re-fit of built tracks: building (Sec. 3) followed by fitting (Sec. 2) over
  * all layers with the hits the build chose.  For seed i of event e, layer

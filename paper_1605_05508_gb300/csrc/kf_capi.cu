@@ -146,6 +146,7 @@ void kf_destroy(kf_ctx* ctx) {
   scratch_free(ctx, ctx->s_bin_id);
   scratch_free(ctx, ctx->s_build);
   scratch_free(ctx, ctx->s_refit);
+  scratch_free(ctx, ctx->s_build64);
   for (int k = 0; k < kHostStreams; ++k) {
     if (ctx->host_streams[k]) cudaStreamDestroy(ctx->host_streams[k]);
     if (ctx->host_done[k]) cudaEventDestroy(ctx->host_done[k]);

@@ -53,7 +53,7 @@ struct kf_ctx {
   cudaStream_t capture_stream = nullptr;
   // scratch pools
   kfi::Scratch s_status, s_lo, s_host_in, s_host_out;
-  kfi::Scratch s_bin_id, s_build, s_refit;
+  kfi::Scratch s_bin_id, s_build, s_refit, s_build64;
   // graph cache
   std::vector<kfi::GraphEntry> graphs;
   uint64_t use_clock = 0;

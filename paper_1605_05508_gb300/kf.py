@@ -135,6 +135,8 @@ def lib() -> C.CDLL:
         L.kf_serve_stats_get.argtypes = [vp, C.POINTER(kf_serve_stats)]
         L.kf_build.argtypes = [vp, C.POINTER(kf_tracks), vp, C.POINTER(kf_layer_hit_bins), i32,
                                C.POINTER(kf_build_result), vp]
+        L.kf_build_f64.argtypes = [vp, C.POINTER(kf_tracks_f64), vp, C.POINTER(kf_layer_hit_bins), i32,
+                                   C.POINTER(kf_build_result_f64), vp]
         L.kf_refit.argtypes = [vp, C.POINTER(kf_tracks), C.POINTER(kf_track_hits), vp, C.POINTER(kf_layer_hits), vp,
                                C.POINTER(kf_tracks), vp, vp, vp]
         L.kf_get_tuning.argtypes = [vp, C.POINTER(kf_tuning)]
@@ -340,6 +342,26 @@ class BuildResult:
                                _ptr(self.cand_chi2_tot), _ptr(self.cand_n_hits))
 
 
+class kf_build_result_f64(C.Structure):
+    _fields_ = [("best", kf_tracks_f64), ("chi2_tot", C.c_void_p), ("n_hits", C.c_void_p), ("status", C.c_void_p),
+                ("hit_idx", C.c_void_p)]
+
+
+@dataclass
+class BuildResultF64:
+    """Outputs of kf_build_f64: best (double par, cov), chi2_tot double, n_hits,
+    status int32 [n], hit_idx int32 [n_layers, n]."""
+    best: Tracks
+    chi2_tot: object
+    n_hits: object
+    status: object
+    hit_idx: object
+
+    def abi(self) -> kf_build_result_f64:
+        return kf_build_result_f64(self.best.abi_f64(), _ptr(self.chi2_tot), _ptr(self.n_hits), _ptr(self.status),
+                                   _ptr(self.hit_idx))
+
+
 def kf_bin_hits(ctx, hits: LayerHits, bins: HitBins, stream=None):
     i, o = hits.abi(), bins.abi()
     _check(lib().kf_bin_hits(_h(ctx), C.byref(i), C.byref(o), _stream(stream)), "kf_bin_hits", _h(ctx))
@@ -351,6 +373,15 @@ def kf_build(ctx, seeds: Tracks, seed_off, bins: HitBins, max_cands: int, out: B
     s, b, o = seeds.abi(), bins.abi(), out.abi()
     _check(lib().kf_build(_h(ctx), C.byref(s), _ptr(seed_off), C.byref(b), int(max_cands), C.byref(o),
                           _stream(stream)), "kf_build", _h(ctx))
+
+
+def kf_build_f64(ctx, seeds: Tracks, event_off, bins: HitBins, max_cands: int, out: BuildResultF64, stream=None):
+    """The plain FP64 build. seeds: double par/cov; event_off: sequence of
+    n_events + 1 seed offsets (host)."""
+    offs = (C.c_int64 * len(event_off))(*[int(v) for v in event_off])
+    s, b, o = seeds.abi_f64(), bins.abi(), out.abi()
+    _check(lib().kf_build_f64(_h(ctx), C.byref(s), offs, C.byref(b), int(max_cands), C.byref(o), _stream(stream)),
+           "kf_build_f64", _h(ctx))
 
 
 def kf_refit(ctx, seeds: Tracks, seed_hits: TrackHits, seed_off, build_hits: LayerHits, hit_idx, out: Tracks,

@@ -112,7 +112,7 @@ def test_binding_structures_match_the_header(tmp_path):
         pytest.skip("no C compiler")
     structs = [getattr(kf, n) for n in ("kf_config", "kf_tracks", "kf_tracks_f64", "kf_track_hits", "kf_layer_hits",
                                         "kf_layer_hit_bins", "kf_build_result", "kf_serve_config", "kf_event",
-                                        "kf_event_result", "kf_serve_stats", "kf_tuning")]
+                                        "kf_event_result", "kf_serve_stats", "kf_tuning", "kf_build_result_f64")]
     lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "kf.h"', "int main(void) {"]
     for st in structs:
         lines.append(f'  printf("{st.__name__} size %zu\\n", sizeof({st.__name__}));')
