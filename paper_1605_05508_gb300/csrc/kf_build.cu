@@ -838,8 +838,8 @@ __global__ void __launch_bounds__(NT, kBuildBlocksPerSM * kBuildThreads / NT) bu
 // hits); lane k of a seed's W lanes holds the seed's candidate of rank k.  Per
 // building layer, every live lane propagates its candidate, derives the window
 // and scans it (scan_window) into a sorted list of its best children's keys;
-// the seed's lanes merge their lists by segmented warp reductions over the
-// 64-bit keys (two 32-bit min-reductions on the lanes of the segment) into
+// the seed's lanes merge their lists by a minimum over the seed's lanes of the
+// 64-bit keys (full-warp shuffles rotating within each seed's lanes) into
 // the seed's best max_cands, ranked by the same total order; lane k then
 // pulls the predicted state and S^-1 of its winner's parent from that lane by
 // shuffles and applies the Kalman update with the winner's hit.  Only the
@@ -849,26 +849,44 @@ __global__ void __launch_bounds__(NT, kBuildBlocksPerSM * kBuildThreads / NT) bu
 // are a total order and every candidate goes through the same functions as in
 // the other layouts, so the results are bitwise theirs.
 
-// Segmented merge: the W lanes of a seed (mask seg) hold sorted lists (L, P)
-// of their own children; the best max_cands keys of the union are found by
-// min-reductions on the high and low halves of the head keys.  Lane k of the
-// segment receives the k-th best (key, hit position); every lane the number
-// of children kept.
+// Segmented merge: the W lanes of a seed (lanes gbase .. gbase + W - 1, mask
+// seg) hold sorted lists (L, P) of their own children; the best max_cands
+// keys of the union are found rank by rank by a minimum over the segment,
+// taken with full-warp shuffles that rotate within the segment (offsets 1, 2
+// and 4 reach every lane of a segment of up to 8): every lane executes the
+// same shuffle, so segments of different seeds proceed in one instruction
+// (warp intrinsics with a different member mask per segment are issued once
+// per segment).  Lane k of the segment receives the k-th best (key, hit
+// position); every lane the number of children kept.  Lanes outside any
+// seed's segment (seg == 0) rotate onto themselves.
 template <int W, int LW>
-__device__ __forceinline__ void merge_segment(uint64_t (&L)[LW], int (&P)[LW], int max_cands, int k, unsigned seg,
-                                              uint64_t& my_key, int& my_pos, int& n_win) {
+__device__ __forceinline__ void merge_segment(uint64_t (&L)[LW], int (&P)[LW], int max_cands, int k, int gbase,
+                                              unsigned seg, uint64_t& my_key, int& my_pos, int& n_win) {
+  const int lane = threadIdx.x & 31;
+  const bool in_seg = seg != 0u;
+  const int r1 = in_seg ? gbase + (k + 1) % W : lane;
+  const int r2 = in_seg ? gbase + (k + 2) % W : lane;
+  const int r4 = in_seg ? gbase + (k + 4) % W : lane;
 #pragma unroll
   for (int r = 0; r < W; ++r) {
     if (r < max_cands) {  // uniform over the launch
-      const uint64_t head = L[0];
-      const unsigned hi = unsigned(head >> 32), lw = unsigned(head);
-      const unsigned mhi = __reduce_min_sync(seg, hi);
-      const unsigned mlo = __reduce_min_sync(seg, hi == mhi ? lw : 0xffffffffu);
-      const uint64_t m = (uint64_t(mhi) << 32) | mlo;
-      const bool mine = head == m && m != kNoKey;
-      const unsigned bal = __ballot_sync(seg, mine) & seg;
-      const int wl = bal ? __ffs(bal) - 1 : __ffs(seg) - 1;
-      const int wpos = __shfl_sync(seg, P[0], wl);
+      uint64_t m = L[0];
+      if constexpr (W > 1) {
+        uint64_t o = __shfl_sync(kFull, m, r1);
+        m = o < m ? o : m;
+        if constexpr (W > 2) {
+          o = __shfl_sync(kFull, m, r2);
+          m = o < m ? o : m;
+        }
+        if constexpr (W > 4) {
+          o = __shfl_sync(kFull, m, r4);
+          m = o < m ? o : m;
+        }
+      }
+      const bool mine = L[0] == m && m != kNoKey;
+      const unsigned bal = __ballot_sync(kFull, mine) & seg;
+      const int wl = bal ? __ffs(bal) - 1 : lane;
+      const int wpos = __shfl_sync(kFull, P[0], wl);
       if (mine) {
 #pragma unroll
         for (int t = 0; t < LW - 1; ++t) {
@@ -894,8 +912,8 @@ __global__ void __launch_bounds__(kResThreads, kResBlocksPerSM) build_resident_k
   constexpr int G = 32 / W;  // seeds per group
   const int lane = threadIdx.x & 31;
   const int g = lane / W, k = lane - g * W;
-  // the seed's lanes; lanes past G * W form a segment of their own with no seed
-  const unsigned seg = g < G ? ((1u << W) - 1u) << (g * W) : (kFull << ((G * W) & 31));
+  // the seed's lanes (none for lanes past G * W)
+  const unsigned seg = g < G ? ((1u << W) - 1u) << (g * W) : 0u;
   const int64_t S8 = A.S * kGroup;
   const int64_t n_groups = (A.S + G - 1) / G;
   const int64_t n_warps = (int64_t(gridDim.x) * kResThreads) >> 5;
@@ -971,20 +989,20 @@ __global__ void __launch_bounds__(kResThreads, kResBlocksPerSM) build_resident_k
       uint64_t my_key = kNoKey;
       int my_pos = -1;
       n_win = 0;
-      merge_segment<W, W>(L, P, A.max_cands, k, seg, my_key, my_pos, n_win);
+      merge_segment<W, W>(L, P, A.max_cands, k, g * W, seg, my_key, my_pos, n_win);
       // materialise: lane k takes its winner's parent prediction and S^-1
       const int src = k < n_win ? g * W + int((my_key >> 21) & 7u) : lane;
       float q[6], ql[3], qC[21], qS[6];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) q[c] = __shfl_sync(seg, p[c], src);
+      for (int c = 0; c < 6; ++c) q[c] = __shfl_sync(kFull, p[c], src);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) ql[c] = __shfl_sync(seg, lo[c], src);
+      for (int c = 0; c < 3; ++c) ql[c] = __shfl_sync(kFull, lo[c], src);
 #pragma unroll
-      for (int c = 0; c < 21; ++c) qC[c] = __shfl_sync(seg, C[c], src);
+      for (int c = 0; c < 21; ++c) qC[c] = __shfl_sync(kFull, C[c], src);
 #pragma unroll
-      for (int c = 0; c < 6; ++c) qS[c] = __shfl_sync(seg, Si[c], src);
-      const int32_t pst = __shfl_sync(seg, st, src);
-      const int pstopped = __shfl_sync(seg, int(stopped), src);
+      for (int c = 0; c < 6; ++c) qS[c] = __shfl_sync(kFull, Si[c], src);
+      const int32_t pst = __shfl_sync(kFull, st, src);
+      const int pstopped = __shfl_sync(kFull, int(stopped), src);
       active = seed_ok && k < n_win;
       if (active) {
         const int nh_new = 255 - int(my_key >> 56);
