@@ -89,8 +89,10 @@ __device__ __forceinline__ void hit_window(const float p[6], const float lo[3], 
                                            int& fa1, int& fb0, int& fb1) {
   kf::inverse_S(C, v0, v1, v2, Si);
   const float X = p[0] + lo[0], Y = p[1] + lo[1], Z = p[2] + lo[2];
-  const float rr = sqrtf(X * X + Y * Y);
-  const float cph = X / rr, sph = Y / rr;
+  // direction cosines of the position: they only scale the widths below,
+  // which are widened by 0.1 %, so a reciprocal square root is exact enough
+  const float irr = rsqrtf(X * X + Y * Y);
+  const float cph = X * irr, sph = Y * irr;
   const float s00 = C[0] + v0, s10 = C[1], s11 = C[2] + v1, s22 = C[5] + v2;
   const float Stt = sph * sph * s00 - 2.f * sph * cph * s10 + cph * cph * s11;
   const float Snn = cph * cph * s00 + 2.f * sph * cph * s10 + sph * sph * s11;
@@ -103,11 +105,12 @@ __device__ __forceinline__ void hit_window(const float p[6], const float lo[3], 
   // sqrt((R + wn)^2 + wt^2) and its phi within atan(wt / (R - wn)) of the
   // prediction's.  The bounds are widened by 0.1 % plus a small absolute
   // term -- far above the float rounding of the window, of the chi2 and of
-  // the hits' own bins -- and cover exactly the bins they reach.
+  // the hits' own bins -- and cover exactly the bins they reach; the phi
+  // half-width takes atan(x) <= x (x >= 0), a bound from above.
   constexpr float kWiden = 1.001f;
   const float rin = R - wn * kWiden;
   const float phic = atan2f(Y, X);
-  const float dphi = (rin > 0.5f * R && wt * kWiden < rin) ? atanf(wt * kWiden / rin) * kWiden + 1e-6f : 10.f;
+  const float dphi = (rin > 0.5f * R && wt * kWiden < rin) ? (wt * kWiden / rin) * kWiden + 1e-6f : 10.f;
   if (dphi < 1.f && phic >= -kPi && phic <= kPi) {  // also false for NaN
     const float scale = float(KF_BIN_PHI) / (2.0f * kPi);
     const int f0 = __float2int_rd((phic - dphi + kPi) * scale);
@@ -579,6 +582,70 @@ __device__ __forceinline__ bool scan_window(const float p[6], const float lo[3],
   return any;
 }
 
+// The same scan with a row's hits loaded kScanBatch at a time: all loads of a
+// batch are in flight before the first chi2 (the scan is bound by the round
+// trips of its dependent loads, not by its arithmetic).  Used by the
+// register-resident step with one lane a seed.
+constexpr int kScanBatch = 4;
+
+template <int LW>
+__device__ __forceinline__ bool scan_window_batched(const float p[6], const float lo[3], const float Si[6], int e0, int e1,
+                                            int fa0, int fa1, int fb0, int fb1, const int32_t* boff,
+                                            const float4* hs, float cut, int nh, float chi2tot, int k,
+                                            uint64_t (&L)[LW], int (&P)[LW]) {
+  bool any = false;
+  const bool two = fb1 >= fb0;
+  int na0 = 0, na1 = 0, nb0 = 0, nb1 = 0;
+  if (e0 <= e1) {
+    const int32_t* q = boff + e0 * KF_BIN_PHI;
+    na0 = q[fa0];
+    na1 = q[fa1 + 1];
+    if (two) {
+      nb0 = q[fb0];
+      nb1 = q[fb1 + 1];
+    }
+  }
+  for (int er = e0; er <= e1; ++er) {
+    const int a0 = na0, na = na1 - na0, b0 = nb0, n = na + (nb1 - nb0);
+    if (er < e1) {
+      const int32_t* q = boff + (er + 1) * KF_BIN_PHI;
+      na0 = q[fa0];
+      na1 = q[fa1 + 1];
+      if (two) {
+        nb0 = q[fb0];
+        nb1 = q[fb1 + 1];
+      }
+    }
+    // the row's hits in batches of kScanBatch loads in flight
+    for (int v0 = 0; v0 < n; v0 += kScanBatch) {
+      float4 mb[kScanBatch];
+      int ub[kScanBatch];
+#pragma unroll
+      for (int i = 0; i < kScanBatch; ++i) {
+        const int v = v0 + i;
+        ub[i] = v < na ? a0 + v : b0 + (v - na);
+        if (v < n) mb[i] = hs[ub[i]];
+      }
+#pragma unroll
+      for (int i = 0; i < kScanBatch; ++i) {
+        if (v0 + i < n) {
+          const float4 m = mb[i];
+          const float r0 = (m.x - p[0]) - lo[0], r1 = (m.y - p[1]) - lo[1], r2 = (m.z - p[2]) - lo[2];
+          const float c2 = kf::chi2_of(r0, r1, r2, Si);
+          if (c2 < cut) {
+            const int id = __float_as_int(m.w);
+            if (id < KF_MAX_HITS_PER_SEGMENT) {
+              list_insert(L, P, make_key(nh + 1, chi2tot + c2, k, id + 1), ub[i]);
+              any = true;
+            }
+          }
+        }
+      }
+    }
+  }
+  return any;
+}
+
 // ---- candidate-packed step (scan scheme 2)
 //
 // The same computation as build_step_kernel, with threads assigned to live
@@ -634,9 +701,10 @@ __device__ __forceinline__ int packed_owner(const int* start, int lo, int hi, in
   return lo;
 }
 
-// NT threads per block, one seed per thread: 128 (5 blocks per SM) or 64 (10
-// blocks per SM: a block barrier holds two warps, not four); 20 warps per SM
-// either way, at most 96 registers.
+// NT threads per block, one seed per thread: 128 (5 blocks per SM), 64 (10
+// blocks per SM: a block barrier holds two warps, not four) or 32 (one warp: a
+// block barrier holds only its own warp); 20 warps per SM either way, at most
+// 96 registers.
 template <int LW, int NT>
 __global__ void __launch_bounds__(NT, kBuildBlocksPerSM * kBuildThreads / NT) build_step_packed_kernel(const BuildStepArgs Args) {
   __shared__ BuildSlot sD;
@@ -917,6 +985,8 @@ __global__ void __launch_bounds__(kResThreads, kResBlocksPerSM) build_resident_k
   const int64_t S8 = A.S * kGroup;
   const int64_t n_groups = (A.S + G - 1) / G;
   const int64_t n_warps = (int64_t(gridDim.x) * kResThreads) >> 5;
+  // groups dealt out with a grid stride: at any moment the warps of the GPU
+  // work on a narrow band of seeds (a few events), whose hits stay in L2
   for (int64_t gi = (int64_t(blockIdx.x) * kResThreads + threadIdx.x) >> 5; gi < n_groups; gi += n_warps) {
     const int64_t j = gi * G + g;
     const bool seed_ok = g < G && j < A.S;
@@ -974,17 +1044,22 @@ __global__ void __launch_bounds__(kResThreads, kResBlocksPerSM) build_resident_k
         L[t] = kNoKey;
         P[t] = -1;
       }
-      if (active) {
-        bool any = false;
-        if (!stopped) {
-          int e0 = 0, e1 = -1, fa0 = 0, fa1 = KF_BIN_PHI - 1, fb0 = 0, fb1 = -1;
-          hit_window(p, lo, C, A.R[l], A.v0, A.v1, A.v2, A.cut, Si, e0, e1, fa0, fa1, fb0, fb1);
+      const bool win = active && !stopped;
+      int e0 = 0, e1 = -1, fa0 = 0, fa1 = KF_BIN_PHI - 1, fb0 = 0, fb1 = -1;
+      if (win) hit_window(p, lo, C, A.R[l], A.v0, A.v1, A.v2, A.cut, Si, e0, e1, fa0, fa1, fb0, fb1);
+      // one lane a seed: a row's hits loaded in batches (measured faster at
+      // W = 1, slower at W = 6, where the registers are needed elsewhere)
+      bool any = false;
+      if (win) {
+        if constexpr (W == 1)
+          any = scan_window_batched(p, lo, Si, e0, e1, fa0, fa1, fb0, fb1, A.bin_off + sg * (KF_NBINS + 1),
+                                    A.hits + h0, A.cut, nh, chi2tot, k, L, P);
+        else
           any = scan_window(p, lo, Si, e0, e1, fa0, fa1, fb0, fb1, A.bin_off + sg * (KF_NBINS + 1), A.hits + h0,
                             A.cut, nh, chi2tot, k, L, P);
-        }
-        // no compatible hit (or a stopped candidate): one child without a hit
-        if (!any) list_insert(L, P, make_key(nh, chi2tot, k, 0), -1);
       }
+      // no compatible hit (or a stopped candidate): one child without a hit
+      if (active && !any) list_insert(L, P, make_key(nh, chi2tot, k, 0), -1);
       // clone engine: the seed's best max_cands children
       uint64_t my_key = kNoKey;
       int my_pos = -1;
@@ -1171,15 +1246,19 @@ static void launch_step_scan(const BuildStepArgs& a, int grid, cudaStream_t st, 
 cudaError_t launch_build_step(const BuildStepArgs& a, int grid, cudaStream_t st, int tile, int list, int scan) {
   if (grid <= 0) return cudaSuccess;
   const bool narrow = list == 4 && a.max_cands <= 4, coop = scan == 1;
-  if (scan >= 2) {  // candidate-packed (no hit staging)
+  if (is_packed(scan)) {  // candidate-packed (no hit staging)
     if (scan == 2 && narrow)
       build_step_packed_kernel<4, kPackSeeds><<<grid, kPackSeeds, 0, st>>>(a);
     else if (scan == 2)
       build_step_packed_kernel<kGroup, kPackSeeds><<<grid, kPackSeeds, 0, st>>>(a);
-    else if (narrow)
+    else if (scan == 3 && narrow)
       build_step_packed_kernel<4, kPackSeeds / 2><<<grid, kPackSeeds / 2, 0, st>>>(a);
-    else
+    else if (scan == 3)
       build_step_packed_kernel<kGroup, kPackSeeds / 2><<<grid, kPackSeeds / 2, 0, st>>>(a);
+    else if (narrow)
+      build_step_packed_kernel<4, kPackSeeds / 4><<<grid, kPackSeeds / 4, 0, st>>>(a);
+    else
+      build_step_packed_kernel<kGroup, kPackSeeds / 4><<<grid, kPackSeeds / 4, 0, st>>>(a);
     return cudaGetLastError();
   }
   if (tile > 0) {
@@ -1368,7 +1447,7 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
     KF_CUDA_TRY(ctx, cudaGetLastError());
     return KF_OK;
   }
-  const int first_fused = ctx->tune.build_scan >= 2 ? (rm_buffers > L ? 0 : std::min(L, rm_buffers)) : L;
+  const int first_fused = is_packed(ctx->tune.build_scan) ? (rm_buffers > L ? 0 : std::min(L, rm_buffers)) : L;
   for (int l = 0; l < (first_fused < L ? first_fused + 1 : L); ++l) {
     const bool fused = l == first_fused;
     BuildStepArgs a;

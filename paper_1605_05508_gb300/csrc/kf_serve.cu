@@ -620,7 +620,7 @@ static void scheduler(Serve* sv) {
       const int64_t pack_min = sv->cfg.pack_min_seeds > 0
                                    ? sv->cfg.pack_min_seeds
                                    : int64_t(sv->ctx->num_sms) * kBuildBlocksPerSM * 80;
-      if (scan >= 2 && seeds < pack_min) scan = 0;
+      if (is_packed(scan) && seeds < pack_min) scan = 0;
       const int pack_seeds = build_pack_seeds(seeds, scan, sv->cfg.max_cands, sv->ctx->num_sms);
       int blocks = 0;
       for (size_t i = 0; i < stepping.size(); ++i) {
