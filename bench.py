@@ -579,7 +579,7 @@ def single_event_leg(a, kf, torch, dev, det, stream, rank):
 # propagation ~440 FMA, S^-1 ~25, ~30 window hits x 12, update ~250).
 BUILD_METHOD_BYTES_PER_SEED_LAYER = 1400.0
 BUILD_METHOD_FLOP_PER_SEED_LAYER = 13000.0
-BUILD_LAYOUTS = ("lane", "coop", "packed128", "packed64", "resident", "packed32")
+BUILD_LAYOUTS = ("lane", "coop", "packed128", "packed64", "resident")
 # How the build's seeds are made (the paper does not report realistic seeding);
 # every efficiency figure depends on this prior
 SEED_READING = ("vertex truth smeared by 0.01 cm (x, y), 1 cm (z) and 1 % of |p| per momentum component, "
@@ -589,8 +589,8 @@ SEED_READING = ("vertex truth smeared by 0.01 cm (x, y), 1 cm (z) and 1 % of |p|
 def build_kernel_name(t, max_cands):
     """The step kernel a build setting launches (kf_build.cu)."""
     scan, lw = t["build_scan"], (4 if t["build_list_width"] == 4 and max_cands <= 4 else 8)
-    if scan in (2, 3, 5):
-        return f"build_step_packed_kernel<{lw}, {dict([(2, 128), (3, 64), (5, 32)])[scan]}>"
+    if scan in (2, 3):
+        return f"build_step_packed_kernel<{lw}, {128 if scan == 2 else 64}>"
     if scan == 4:
         return "build_resident_kernel"
     return f"build_step_kernel<{t['build_hit_tile']}, {lw}, {int(scan == 1)}>"
@@ -654,7 +654,7 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist, peaks=None):
         times = {}
         for tile in (0, 512):
             for lw in (8, 4):
-                for scan in (0, 1, 2, 3, 4, 5):
+                for scan in (0, 1, 2, 3, 4):
                     if (lw == 4 and N > 4) or (scan >= 2 and tile > 0) or (scan == 4 and lw == 4):
                         continue
                     kf.kf_set_tuning(ctx, 128, tile, lw, scan)

@@ -319,9 +319,8 @@ typedef struct {
                                  seeds per block; 4 = register-resident: each warp takes
                                  groups of 32 / W seeds (W = max_cands rounded up to 1, 2, 4,
                                  6 or 8 lanes a seed) through all building layers in one
-                                 launch, the candidates' states in registers between layers;
-                                 5 = as 2 with 32 seeds per block (one warp per block)
-                                 (2 .. 5 require build_hit_tile 0; a serving loop steps
+                                 launch, the candidates' states in registers between layers
+                                 (2, 3 and 4 require build_hit_tile 0; a serving loop steps
                                  one layer at a time and runs 4 as 2) */
     int32_t fit_chunk;        /* kf_fit: 0 = each layer step is one launch over the whole batch
                                  (default); 262144, 524288 or 1048576 = the batch is fitted in

@@ -701,10 +701,9 @@ __device__ __forceinline__ int packed_owner(const int* start, int lo, int hi, in
   return lo;
 }
 
-// NT threads per block, one seed per thread: 128 (5 blocks per SM), 64 (10
-// blocks per SM: a block barrier holds two warps, not four) or 32 (one warp: a
-// block barrier holds only its own warp); 20 warps per SM either way, at most
-// 96 registers.
+// NT threads per block, one seed per thread: 128 (5 blocks per SM) or 64 (10
+// blocks per SM: a block barrier holds two warps, not four); 20 warps per SM
+// either way, at most 96 registers.
 template <int LW, int NT>
 __global__ void __launch_bounds__(NT, kBuildBlocksPerSM * kBuildThreads / NT) build_step_packed_kernel(const BuildStepArgs Args) {
   __shared__ BuildSlot sD;
@@ -1251,14 +1250,10 @@ cudaError_t launch_build_step(const BuildStepArgs& a, int grid, cudaStream_t st,
       build_step_packed_kernel<4, kPackSeeds><<<grid, kPackSeeds, 0, st>>>(a);
     else if (scan == 2)
       build_step_packed_kernel<kGroup, kPackSeeds><<<grid, kPackSeeds, 0, st>>>(a);
-    else if (scan == 3 && narrow)
-      build_step_packed_kernel<4, kPackSeeds / 2><<<grid, kPackSeeds / 2, 0, st>>>(a);
-    else if (scan == 3)
-      build_step_packed_kernel<kGroup, kPackSeeds / 2><<<grid, kPackSeeds / 2, 0, st>>>(a);
     else if (narrow)
-      build_step_packed_kernel<4, kPackSeeds / 4><<<grid, kPackSeeds / 4, 0, st>>>(a);
+      build_step_packed_kernel<4, kPackSeeds / 2><<<grid, kPackSeeds / 2, 0, st>>>(a);
     else
-      build_step_packed_kernel<kGroup, kPackSeeds / 4><<<grid, kPackSeeds / 4, 0, st>>>(a);
+      build_step_packed_kernel<kGroup, kPackSeeds / 2><<<grid, kPackSeeds / 2, 0, st>>>(a);
     return cudaGetLastError();
   }
   if (tile > 0) {

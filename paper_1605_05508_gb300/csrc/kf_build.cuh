@@ -112,15 +112,12 @@ inline CandBuf cand_at(char* q, int64_t S) {
 // tile: 0 (scan global memory) or kBuildTile (stage the window hits per
 // warp); list: 4 (lane lists of 4 children, when max_cands <= 4) or 8;
 // scan: 0 (each lane scans its own candidate's window), 1 (the seed's
-// lanes scan each parent's window together), 2, 3 or 5 (candidate-packed, 128,
-// 64 or 32 seeds per block: grid of build_step_blocks(S, scan); tile is ignored)
+// lanes scan each parent's window together), 2 or 3 (candidate-packed, 128 or
+// 64 seeds per block: grid of build_step_blocks(S, scan); tile is ignored)
 cudaError_t launch_build_step(const BuildStepArgs& a, int grid, cudaStream_t st, int tile, int list, int scan);
 // Seeds (threads) per block of the candidate-packed layouts: scan 2: 128,
-// scan 3: 64, scan 5: 32 (one warp per block, so a block barrier never waits
-// for another warp); 0 for the other layouts.
-inline int packed_seeds_per_block(int scan) {
-  return scan == 2 ? kPackSeeds : scan == 3 ? kPackSeeds / 2 : scan == 5 ? kPackSeeds / 4 : 0;
-}
+// scan 3: 64; 0 for the other layouts.
+inline int packed_seeds_per_block(int scan) { return scan == 2 ? kPackSeeds : scan == 3 ? kPackSeeds / 2 : 0; }
 inline bool is_packed(int scan) { return packed_seeds_per_block(scan) > 0; }
 
 // Blocks of the build step for S seeds: 8 lanes per seed, 16 seeds per block,

@@ -7,8 +7,8 @@
 // of a lane's child list (4 suffices when at most 4 candidates are kept) and
 // the step's thread layout (8 lanes per seed, each lane scanning its own
 // candidate's window or the seed's lanes scanning each parent's window in
-// turn; or the live candidates packed onto consecutive threads, 128, 64 or
-// 32 seeds per block; or each warp taking small groups of seeds through all
+// turn; or the live candidates packed onto consecutive threads, 128 or 64
+// seeds per block; or each warp taking small groups of seeds through all
 // layers with the candidates in registers).  The autotuner runs the caller's own batch once per setting and keeps
 // the fastest, so the choice follows the workload (batch size, hit density,
 // max_cands) rather than a fixed table.
@@ -20,7 +20,7 @@ namespace {
 
 bool valid_tuning(const kf_tuning& t) {
   return (t.fit_block == 64 || t.fit_block == 128) && (t.build_hit_tile == 0 || t.build_hit_tile == 512) &&
-         (t.build_list_width == 4 || t.build_list_width == 8) && (t.build_scan == 0 || t.build_scan == 1 || ((t.build_scan >= 2 && t.build_scan <= 5) && t.build_hit_tile == 0)) &&
+         (t.build_list_width == 4 || t.build_list_width == 8) && (t.build_scan == 0 || t.build_scan == 1 || ((t.build_scan >= 2 && t.build_scan <= 4) && t.build_hit_tile == 0)) &&
          (t.fit_chunk == 0 || t.fit_chunk == 262144 || t.fit_chunk == 524288 || t.fit_chunk == 1048576) &&
          (t.fit_stage == 0 || t.fit_stage == 1) && (t.bin_unordered == 0 || t.bin_unordered == 1);
 }
@@ -119,7 +119,7 @@ int kf_autotune_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed_o
   std::vector<kf_tuning> cands;
   for (int tile : {0, 512})
     for (int list : {8, 4})
-      for (int scan : {0, 1, 2, 3, 4, 5}) {
+      for (int scan : {0, 1, 2, 3, 4}) {
         if (list == 4 && max_cands > 4) continue;
         if (scan >= 2 && tile > 0) continue;  // the packed and resident steps stage nothing
         if (scan == 4 && list == 4) continue;  // the resident step sizes its lists itself
