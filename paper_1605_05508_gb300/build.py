@@ -1,6 +1,7 @@
 """Build step of libkf: compiles csrc/*.cu for sm_103a (GB300) with nvcc into
 paper_1605_05508_gb300/_build/libkf.so.  Translation units compile in
-parallel; the library links against the CUDA runtime only."""
+parallel; the library links against the CUDA runtime only.  Also links the
+native serving driver (serve_driver.c) against it: _build/kf_serve_driver."""
 from __future__ import annotations
 
 import glob
@@ -31,7 +32,9 @@ def _stale(srcs, lib) -> bool:
         return True
     t = os.path.getmtime(lib)
     deps = srcs + glob.glob(os.path.join(SRC_DIR, "*.cuh")) + glob.glob(os.path.join(SRC_DIR, "*.h")) + \
-        glob.glob(os.path.join(INCLUDE, "*.h"))
+        glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.join(HERE, "serve_driver.c")]
+    if not os.path.exists(os.path.join(OUT_DIR, "kf_serve_driver")):
+        return True
     return any(os.path.getmtime(d) > t for d in deps)
 
 
@@ -61,7 +64,24 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     tmp = LIB + f".tmp{os.getpid()}"
     subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"], check=True)
     os.replace(tmp, LIB)
+    build_serve_driver(verbose)
     return LIB
+
+
+DRIVER_SRC = os.path.join(HERE, "serve_driver.c")
+DRIVER = os.path.join(OUT_DIR, "kf_serve_driver")
+
+
+def build_serve_driver(verbose: bool = False) -> str:
+    """The native serving driver (serve_driver.c) linked against libkf."""
+    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(nvcc())), "lib64")
+    cmd = ["gcc", "-O2", "-std=gnu11", "-I", INCLUDE, DRIVER_SRC, "-o", DRIVER + f".tmp{os.getpid()}",
+           "-L", OUT_DIR, "-lkf", f"-Wl,-rpath,{OUT_DIR}", f"-Wl,-rpath,{cuda_lib}", "-lpthread", "-lm"]
+    if verbose:
+        print(" ".join(cmd), file=sys.stderr)
+    subprocess.run(cmd, check=True)
+    os.replace(DRIVER + f".tmp{os.getpid()}", DRIVER)
+    return DRIVER
 
 
 if __name__ == "__main__":

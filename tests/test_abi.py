@@ -131,3 +131,16 @@ def test_binding_structures_match_the_header(tmp_path):
         assert got[(st.__name__, "size")] == ctypes.sizeof(st), st.__name__
         for f, *_ in st._fields_:
             assert got[(st.__name__, f)] == getattr(st, f).offset, (st.__name__, f)
+
+
+def test_serve_driver_is_built_and_rejects_a_bad_pool(libpath, tmp_path):
+    """The native serving driver links against libkf and refuses a file that
+    is not an event pool before any CUDA call (exit status 2)."""
+    from paper_1605_05508_gb300 import build as B
+    assert os.path.exists(B.DRIVER)
+    bad = tmp_path / "bad.kfpool"
+    bad.write_bytes(b"NOPE" + b"\0" * 64)
+    r = subprocess.run([B.DRIVER, str(bad), "4", "0", "1", "1"], capture_output=True, text=True)
+    assert r.returncode == 2, (r.returncode, r.stderr)
+    r = subprocess.run([B.DRIVER], capture_output=True, text=True)
+    assert r.returncode == 2 and "usage" in r.stderr

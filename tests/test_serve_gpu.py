@@ -181,3 +181,27 @@ def test_served_refit_equals_batch_refit(cuda_ctx_factory):
         np.testing.assert_array_equal(g["chi2"], r["refit_chi2"])
         np.testing.assert_array_equal(g["status"], r["refit_status"])
         assert np.mean(r["refit_chi2"][r["refit_chi2"] >= 0]) < 4.0
+
+
+def test_native_driver_serves_every_request(tmp_path):
+    """kf_serve_driver (the serving loop driven from native threads, as the
+    benchmark measures it) completes every request of a small pool at
+    saturation with two submitting threads and under Poisson arrivals, with
+    latencies that are positive and ordered (p50 <= p99)."""
+    import bench
+    from paper_1605_05508_gb300 import build as B
+    B.build()
+    det = S.barrel()
+    pool = []
+    for i, n in enumerate([300, 2500, 800, 60]):
+        b = S.make_build_batch(500 + i, 1, n)
+        pool.append(dict(seed_par=b.seeds.par, seed_cov=b.seeds.cov, seed_charge=b.seeds.charge,
+                         seed_hits=b.fit_hits.xyz, seed_valid=b.fit_hits.valid, layer_xyz=b.layer_xyz,
+                         layer_off=b.layer_off))
+    path = str(tmp_path / "pool.kfpool")
+    bench.write_serve_pool(path, pool, det, 8, 1 << 30, 1 << 28)
+    for rate, threads in ((0, 2), (400.0, 1)):
+        r = bench.run_serve_driver(path, 24, rate, threads, 3, tuning={"build_scan": 2, "build_list_width": 8})
+        assert r["requests"] == 24 and r["events_per_s"] > 0, r
+        assert 0 < r["p50_ms"] <= r["p99_ms"], r
+        assert r["max_resident"] >= 1 and r["step_launches"] >= 7, r
