@@ -7,17 +7,19 @@
 // arrive at random times.  The scheduler thread here
 //   * admits queued events in arrival order whenever a slot and a contiguous
 //     block of the device arena are free (memory-based admission),
-//   * prepares an admitted event on the serve stream: input copy, seed fit
-//     over the seeding layers, hit binning, seed ordering, first candidate,
+//   * prepares admitted events on preparation streams (several events at
+//     once): input copy, seed fit over the seeding layers, hit binning, seed
+//     ordering, first candidate,
 //   * issues ONE build-step launch per iteration over every resident event,
 //     each at its own layer (the slot table tells each block its event,
 //     layer, buffers and hit bins), so candidates stay resident on the device
 //     between layers and small events ride along with big ones,
 //   * selects the best candidate of finished events, copies their results to
 //     pinned host memory asynchronously and recycles their slot and memory.
-// All device work of the service is on one stream; the host never waits on a
-// device flag (it polls CUDA events) and runs at most kInflight iterations
-// ahead of the GPU.
+// Steps, final selections and result copies run on one stream, preparations on
+// their own; an event joins the steps only once the host has seen its
+// preparation complete.  The host never waits on a device flag (it polls CUDA
+// events) and runs at most kInflight iterations ahead of the GPU.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -279,6 +281,7 @@ struct Request {
 };
 
 constexpr int kInflight = 2;  // iterations the host may run ahead of the GPU
+constexpr int kPrepStreams = 4;
 constexpr int kRing = kInflight + 2;
 
 struct Serve {
@@ -291,7 +294,11 @@ struct Serve {
   bool stop = false;
   int cuda_error = 0;
   cudaStream_t stream = nullptr;       // build steps, final selection, results
-  cudaStream_t prep_stream = nullptr;  // preparation of admitted events (overlaps the steps)
+  // preparation of admitted events, round-robin over kPrepStreams streams:
+  // an event's preparation is a few small copies and launches, so several
+  // run at once, beside the steps
+  cudaStream_t prep_stream[kPrepStreams] = {};
+  int prep_next = 0;
   char* dmem = nullptr;
   char* hmem = nullptr;
   Arena darena, harena;
@@ -321,7 +328,8 @@ static cudaError_t prepare(Serve* sv, Request* r) {
   const EventLayout& L = r->lay;
   char* d = sv->dmem + r->d_off;
   char* h = sv->hmem + r->h_in_off;
-  cudaStream_t s = sv->prep_stream;
+  cudaStream_t s = sv->prep_stream[sv->prep_next];
+  sv->prep_next = (sv->prep_next + 1) % kPrepStreams;
   const int64_t n = L.n;
   // the host input block mirrors the first device pieces (par .. sval); the
   // raw hits and their offsets follow in the host block and go to their own
@@ -687,7 +695,8 @@ void kf_serve_shutdown_internal(kf_ctx* ctx) {
   sv->copier.stop();
   cudaSetDevice(ctx->device);
   if (sv->stream) cudaStreamSynchronize(sv->stream);
-  if (sv->prep_stream) cudaStreamSynchronize(sv->prep_stream);
+  for (cudaStream_t ps : sv->prep_stream)
+    if (ps) cudaStreamSynchronize(ps);
   for (auto& kv : sv->all) {
     if (kv.second->done) cudaEventDestroy(kv.second->done);
     if (kv.second->prepped) cudaEventDestroy(kv.second->prepped);
@@ -699,7 +708,8 @@ void kf_serve_shutdown_internal(kf_ctx* ctx) {
   if (sv->hmem) cudaFreeHost(sv->hmem);
   if (sv->h_table) cudaFreeHost(sv->h_table);
   if (sv->stream) cudaStreamDestroy(sv->stream);
-  if (sv->prep_stream) cudaStreamDestroy(sv->prep_stream);
+  for (cudaStream_t ps : sv->prep_stream)
+    if (ps) cudaStreamDestroy(ps);
   ctx->allocated -= sv->darena.size();
   delete sv;
   ctx->serve = nullptr;
@@ -734,7 +744,8 @@ int kf_serve_start(kf_ctx* ctx, const kf_serve_config* cfg) {
                            cudaHostAllocDefault) != cudaSuccess)
     rc = KF_ENOMEM;
   if (!rc && cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking) != cudaSuccess) rc = KF_ECUDA;
-  if (!rc && cudaStreamCreateWithFlags(&sv->prep_stream, cudaStreamNonBlocking) != cudaSuccess) rc = KF_ECUDA;
+  for (int i = 0; i < kPrepStreams && !rc; ++i)
+    if (cudaStreamCreateWithFlags(&sv->prep_stream[i], cudaStreamNonBlocking) != cudaSuccess) rc = KF_ECUDA;
   for (int i = 0; i < kRing && !rc; ++i)
     if (cudaEventCreateWithFlags(&sv->iter_ev[i], cudaEventDisableTiming) != cudaSuccess) rc = KF_ECUDA;
   if (rc) {
@@ -744,7 +755,8 @@ int kf_serve_start(kf_ctx* ctx, const kf_serve_config* cfg) {
     if (sv->hmem) cudaFreeHost(sv->hmem);
     if (sv->h_table) cudaFreeHost(sv->h_table);
     if (sv->stream) cudaStreamDestroy(sv->stream);
-    if (sv->prep_stream) cudaStreamDestroy(sv->prep_stream);
+    for (cudaStream_t ps : sv->prep_stream)
+      if (ps) cudaStreamDestroy(ps);
     for (int i = 0; i < kRing; ++i)
       if (sv->iter_ev[i]) cudaEventDestroy(sv->iter_ev[i]);
     delete sv;
