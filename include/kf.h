@@ -370,7 +370,7 @@ int kf_autotune_build(kf_ctx *ctx, const kf_tracks *seeds, const int64_t *seed_o
  * back asynchronously and their slots and memory reused.  Results do not
  * depend on what else is resident (per-seed arithmetic only).
  */
-#define KF_MAX_SLOTS 32
+#define KF_MAX_SLOTS 64
 
 typedef struct {
     int32_t n_seed_layers;      /* configuration layers 0 .. n_seed_layers-1 fit the seeds */

@@ -16,9 +16,10 @@
 //     between layers and small events ride along with big ones,
 //   * selects the best candidate of finished events, copies their results to
 //     pinned host memory asynchronously and recycles their slot and memory.
-// Steps, final selections and result copies run on one stream, preparations on
-// their own; an event joins the steps only once the host has seen its
-// preparation complete.  The host never waits on a device flag (it polls CUDA
+// Steps run on one stream, preparations and the finishing of events (final
+// selection, result copies) on their own; an event joins the steps only once
+// the host has seen its preparation complete, and its finishing waits for its
+// last step by a CUDA event.  The host never waits on a device flag (it polls CUDA
 // events) and runs at most kInflight iterations ahead of the GPU.
 #include <algorithm>
 #include <chrono>
@@ -293,7 +294,9 @@ struct Serve {
   std::thread thread;
   bool stop = false;
   int cuda_error = 0;
-  cudaStream_t stream = nullptr;       // build steps, final selection, results
+  cudaStream_t stream = nullptr;       // build steps
+  cudaStream_t finish_stream = nullptr;  // final selection, re-fit and result copies
+  cudaEvent_t step_ev[kRing] = {};       // after the step launch of an iteration
   // preparation of admitted events, round-robin over kPrepStreams streams:
   // an event's preparation is a few small copies and launches, so several
   // run at once, beside the steps
@@ -436,13 +439,15 @@ static BuildSlot slot_of(Serve* sv, Request* r) {
   return b;
 }
 
-// Final selection + asynchronous copy of the results to the pinned output block.
+// Final selection + asynchronous copy of the results to the pinned output block,
+// on the finish stream (ordered after the event's last step by the caller), so
+// that the next steps need not wait for it.
 static cudaError_t finish(Serve* sv, Request* r) {
   const EventLayout& L = r->lay;
   char* d = sv->dmem + r->d_off;
   char* o = sv->hmem + r->h_out_off;
   const int64_t n = L.n;
-  cudaStream_t s = sv->stream;
+  cudaStream_t s = sv->finish_stream;
   BuildFinalArgs fa;
   std::memset(&fa, 0, sizeof fa);
   fa.cand = cand_at(d + ((L.Lb % 2 == 0) ? L.d_candA : L.d_candB), n);
@@ -655,9 +660,15 @@ static void scheduler(Serve* sv) {
       sv->stats.step_launches++;
     }
     if (e == cudaSuccess) {
+      bool ordered = false;  // the finish stream waits for this iteration's step once
       for (Request* r : stepping)
         if (r->layer == r->lay.Lb && e == cudaSuccess) {
-          e = finish(sv, r);
+          if (!ordered) {
+            e = cudaEventRecord(sv->step_ev[ring], sv->stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(sv->finish_stream, sv->step_ev[ring], 0);
+            ordered = true;
+          }
+          if (e == cudaSuccess) e = finish(sv, r);
           std::lock_guard<std::mutex> lk(sv->mu);
           r->state = kFinishing;
         }
@@ -695,19 +706,23 @@ void kf_serve_shutdown_internal(kf_ctx* ctx) {
   sv->copier.stop();
   cudaSetDevice(ctx->device);
   if (sv->stream) cudaStreamSynchronize(sv->stream);
+  if (sv->finish_stream) cudaStreamSynchronize(sv->finish_stream);
   for (cudaStream_t ps : sv->prep_stream)
     if (ps) cudaStreamSynchronize(ps);
   for (auto& kv : sv->all) {
     if (kv.second->done) cudaEventDestroy(kv.second->done);
     if (kv.second->prepped) cudaEventDestroy(kv.second->prepped);
   }
-  for (int i = 0; i < kRing; ++i)
+  for (int i = 0; i < kRing; ++i) {
     if (sv->iter_ev[i]) cudaEventDestroy(sv->iter_ev[i]);
+    if (sv->step_ev[i]) cudaEventDestroy(sv->step_ev[i]);
+  }
   if (sv->dmem) cudaFree(sv->dmem);
   if (sv->d_table) cudaFree(sv->d_table);
   if (sv->hmem) cudaFreeHost(sv->hmem);
   if (sv->h_table) cudaFreeHost(sv->h_table);
   if (sv->stream) cudaStreamDestroy(sv->stream);
+  if (sv->finish_stream) cudaStreamDestroy(sv->finish_stream);
   for (cudaStream_t ps : sv->prep_stream)
     if (ps) cudaStreamDestroy(ps);
   ctx->allocated -= sv->darena.size();
@@ -744,10 +759,13 @@ int kf_serve_start(kf_ctx* ctx, const kf_serve_config* cfg) {
                            cudaHostAllocDefault) != cudaSuccess)
     rc = KF_ENOMEM;
   if (!rc && cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking) != cudaSuccess) rc = KF_ECUDA;
+  if (!rc && cudaStreamCreateWithFlags(&sv->finish_stream, cudaStreamNonBlocking) != cudaSuccess) rc = KF_ECUDA;
   for (int i = 0; i < kPrepStreams && !rc; ++i)
     if (cudaStreamCreateWithFlags(&sv->prep_stream[i], cudaStreamNonBlocking) != cudaSuccess) rc = KF_ECUDA;
   for (int i = 0; i < kRing && !rc; ++i)
-    if (cudaEventCreateWithFlags(&sv->iter_ev[i], cudaEventDisableTiming) != cudaSuccess) rc = KF_ECUDA;
+    if (cudaEventCreateWithFlags(&sv->iter_ev[i], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sv->step_ev[i], cudaEventDisableTiming) != cudaSuccess)
+      rc = KF_ECUDA;
   if (rc) {
     cudaGetLastError();
     if (sv->dmem) cudaFree(sv->dmem);
@@ -755,10 +773,13 @@ int kf_serve_start(kf_ctx* ctx, const kf_serve_config* cfg) {
     if (sv->hmem) cudaFreeHost(sv->hmem);
     if (sv->h_table) cudaFreeHost(sv->h_table);
     if (sv->stream) cudaStreamDestroy(sv->stream);
+    if (sv->finish_stream) cudaStreamDestroy(sv->finish_stream);
     for (cudaStream_t ps : sv->prep_stream)
       if (ps) cudaStreamDestroy(ps);
-    for (int i = 0; i < kRing; ++i)
+    for (int i = 0; i < kRing; ++i) {
       if (sv->iter_ev[i]) cudaEventDestroy(sv->iter_ev[i]);
+      if (sv->step_ev[i]) cudaEventDestroy(sv->step_ev[i]);
+    }
     delete sv;
     return rc;
   }

@@ -99,7 +99,7 @@ class kf_tuning(C.Structure):
                 ("bin_unordered", C.c_int32)]
 
 
-MAX_SLOTS = 32  # KF_MAX_SLOTS
+MAX_SLOTS = 64  # KF_MAX_SLOTS
 BIN_ETA, BIN_PHI, BIN_ETA_MAX = 64, 256, 1.5  # KF_BIN_ETA, KF_BIN_PHI, KF_BIN_ETA_MAX
 NBINS = BIN_ETA * BIN_PHI
 MAX_HITS_PER_SEGMENT = (1 << 21) - 2  # KF_MAX_HITS_PER_SEGMENT
