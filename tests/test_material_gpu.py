@@ -56,3 +56,12 @@ def test_build_with_material_matches_oracle(cuda_ctx_factory):
     assert not bad, bad[:3]
     assert len(ties) <= max(2, 0.02 * len(g["nhits"]))
     assert np.mean(g["nhits"]) > 6.0
+    # every thread layout applies the process noise identically: the packed and
+    # register-resident steps give the grouped step's bits
+    from paper_1605_05508_gb300 import kf
+    for layout in (2, 4):
+        kf.kf_set_tuning(ctx, 128, 0, 8, layout)
+        h = gpu_build(ctx, batch, 6, want_cands=False)
+        for k in ("par", "cov", "chi2", "nhits", "status", "hits"):
+            np.testing.assert_array_equal(h[k], g[k], err_msg=f"layout {layout} {k}")
+    kf.kf_set_tuning(ctx, 128, 0, 8, 0)
