@@ -139,8 +139,10 @@ __device__ __forceinline__ void hit_window(const float p[6], const float lo[3], 
     const float zlo = Z - wz * kWiden - 1e-5f, zhi = Z + wz * kWiden + 1e-5f;
     const float tmin = zlo >= 0.f ? zlo / rhi : zlo / rlo;
     const float tmax = zhi >= 0.f ? zhi / rlo : zhi / rhi;
-    e0 = eta_bin(asinhf(tmin));
-    e1 = eta_bin(asinhf(tmax));
+    // asinh by log(|t| + sqrt(t^2 + 1)) with the fast logarithm, widened by
+    // 1e-5 in eta (far above that form's error): still a superset
+    e0 = eta_bin(copysignf(__logf(fabsf(tmin) + sqrtf(fmaf(tmin, tmin, 1.f))), tmin) - 1e-5f);
+    e1 = eta_bin(copysignf(__logf(fabsf(tmax) + sqrtf(fmaf(tmax, tmax, 1.f))), tmax) + 1e-5f);
   }
 }
 
@@ -585,10 +587,10 @@ __device__ __forceinline__ bool scan_window(const float p[6], const float lo[3],
 // The same scan with a row's hits loaded kScanBatch at a time: all loads of a
 // batch are in flight before the first chi2 (the scan is bound by the round
 // trips of its dependent loads, not by its arithmetic).  Used by the
-// register-resident step with one lane a seed.
-constexpr int kScanBatch = 4;
+// register-resident step: batches of 4 with one lane a seed, of 2 otherwise
+// (where the registers are needed elsewhere).
 
-template <int LW>
+template <int LW, int kScanBatch = 4>
 __device__ __forceinline__ bool scan_window_batched(const float p[6], const float lo[3], const float Si[6], int e0, int e1,
                                             int fa0, int fa1, int fb0, int fb1, const int32_t* boff,
                                             const float4* hs, float cut, int nh, float chi2tot, int k,
@@ -1049,16 +1051,16 @@ __global__ void __launch_bounds__(kResThreads, kResBlocksPerSM) build_resident_k
       const bool win = active && !stopped;
       int e0 = 0, e1 = -1, fa0 = 0, fa1 = KF_BIN_PHI - 1, fb0 = 0, fb1 = -1;
       if (win) hit_window(p, lo, C, A.R[l], A.v0, A.v1, A.v2, A.cut, Si, e0, e1, fa0, fa1, fb0, fb1);
-      // one lane a seed: a row's hits loaded in batches (measured faster at
-      // W = 1, slower at W = 6, where the registers are needed elsewhere)
+      // a row's hits loaded in batches: 4 with one lane a seed, 2 with more
+      // (measured: 4 is slower at W = 6, where the registers are needed elsewhere)
       bool any = false;
       if (win) {
         if constexpr (W == 1)
           any = scan_window_batched(p, lo, Si, e0, e1, fa0, fa1, fb0, fb1, A.bin_off + sg * (KF_NBINS + 1),
                                     A.hits + h0, A.cut, nh, chi2tot, k, L, P);
         else
-          any = scan_window(p, lo, Si, e0, e1, fa0, fa1, fb0, fb1, A.bin_off + sg * (KF_NBINS + 1), A.hits + h0,
-                            A.cut, nh, chi2tot, k, L, P);
+          any = scan_window_batched<W, 2>(p, lo, Si, e0, e1, fa0, fa1, fb0, fb1, A.bin_off + sg * (KF_NBINS + 1),
+                                          A.hits + h0, A.cut, nh, chi2tot, k, L, P);
       }
       // no compatible hit (or a stopped candidate): one child without a hit
       if (active && !any) list_insert(L, P, make_key(nh, chi2tot, k, 0), -1);
