@@ -807,7 +807,7 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist, peaks=None):
     # counted figures of the step kernels from a committed ncu summary of the
     # same setting and kernel source: warp instructions (issue rate) and FP32
     # flops (FFMA x 2 + FADD + FMUL) of one build
-    prof = "build_step_kernel.instructions.txt"
+    prof = ("build_resident_kernel" if tune6["build_scan"] == 4 else "build_step_kernel") + ".instructions.txt"
     setting = profile_value(prof, "setting_code", BUILD_SOURCES)
     code = tune6["build_hit_tile"] * 100 + tune6["build_list_width"] * 10 + tune6["build_scan"]
     if setting == code and E == profile_value(prof, "events", BUILD_SOURCES):
