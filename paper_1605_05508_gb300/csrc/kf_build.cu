@@ -1126,6 +1126,115 @@ __global__ void __launch_bounds__(kResThreads, kResBlocksPerSM) build_resident_k
   }
 }
 
+// First building layer of the register-resident build, one thread per seed.
+// On that layer every seed holds one candidate (the seed itself), so the W
+// lanes a seed owns in build_resident_kernel would idle all but one; here a
+// thread propagates its seed, derives and scans the window, and updates the
+// seed's best max_cands children itself (the list of a single parent is the
+// seed's ranking), writing them to candidate buffer l0 + 1 and the layer's
+// history.  The same functions and keys as every other layout, so the same
+// bits; build_resident_kernel then continues from layer l0 + 1.
+__global__ void __launch_bounds__(kResThreads, kResBlocksPerSM) build_first_layer_kernel(const BuildResidentArgs A) {
+  const int64_t j = int64_t(blockIdx.x) * kResThreads + threadIdx.x;
+  if (j >= A.S) return;
+  const int64_t S8 = A.S * kGroup;
+  const int l = A.l0;
+  const int e = A.seed_evt ? A.seed_evt[j] : 0;
+  const float a = A.a_scale * float(A.charge[A.seed_perm[j]]);
+  const int64_t slot = cand_slot(j, 0, A.S, A.in_rm);  // the seed's only candidate
+  float p[6], lo[3], C[21];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) p[c] = A.in.par[c * S8 + slot];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) lo[c] = A.in.par[(6 + c) * S8 + slot];
+#pragma unroll
+  for (int c = 0; c < 21; ++c) C[c] = A.in.cov[c * S8 + slot];
+  const float chi2tot = A.in.chi2[slot];
+  const int32_t meta = A.in.meta[slot];
+  const int nh = meta & 0xff;
+  int32_t st = meta >> 8;
+  const int64_t sg = int64_t(e) * A.n_layers + l;
+  const int64_t h0 = A.seg_off[sg];
+  bool stopped = (st & KF_ST_STOPPED) != 0;
+  if (!stopped) {
+    const int r = kf::propagate<float, kNewtonBuild, true>(p, lo, C, a, A.R[l]);
+    if (r) {
+      st |= r;
+      stopped = true;
+    } else if (A.x_x0[l] > 0.f) {
+      kf::scatter(p, lo, C, A.x_x0[l], A.mass);
+    }
+  }
+  float Si[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  uint64_t L[kGroup];
+  int P[kGroup];
+#pragma unroll
+  for (int t = 0; t < kGroup; ++t) {
+    L[t] = kNoKey;
+    P[t] = -1;
+  }
+  bool any = false;
+  if (!stopped) {
+    int e0 = 0, e1 = -1, fa0 = 0, fa1 = KF_BIN_PHI - 1, fb0 = 0, fb1 = -1;
+    hit_window(p, lo, C, A.R[l], A.v0, A.v1, A.v2, A.cut, Si, e0, e1, fa0, fa1, fb0, fb1);
+    any = scan_window(p, lo, Si, e0, e1, fa0, fa1, fb0, fb1, A.bin_off + sg * (KF_NBINS + 1), A.hits + h0, A.cut,
+                      nh, chi2tot, 0, L, P);
+  }
+  // no compatible hit (or a stopped seed): one child without a hit
+  if (!any) list_insert(L, P, make_key(nh, chi2tot, 0, 0), -1);
+  int n_win = 0;
+#pragma unroll 1
+  for (int r = 0; r < A.max_cands; ++r) {
+    uint64_t key = kNoKey;
+    int pos = -1;
+#pragma unroll
+    for (int t = 0; t < kGroup; ++t)
+      if (t == r) {
+        key = L[t];
+        pos = P[t];
+      }
+    if (key == kNoKey) break;
+    ++n_win;
+    float q[6], ql[3], qC[21];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) q[c] = p[c];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) ql[c] = lo[c];
+#pragma unroll
+    for (int c = 0; c < 21; ++c) qC[c] = C[c];
+    const int nh_new = 255 - int(key >> 56);
+    const float chi2_new = __uint_as_float(uint32_t(key >> 24));
+    const int hit_plus1 = int(key & 0x1fffffu);
+    int32_t st_new = st;
+    if (hit_plus1 > 0) {
+      const float4 m = A.hits[h0 + pos];
+      float r0, r1, r2;
+      kf::residual<float, true>(q, ql, m.x, m.y, m.z, r0, r1, r2);
+      kf::kalman_update<float, true>(q, ql, qC, Si, r0, r1, r2, A.v0, A.v1, A.v2);
+    } else if (!stopped) {
+      st_new |= KF_ST_NO_HIT;
+    }
+    const int64_t os = cand_slot(j, r, A.S, A.out_rm);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) A.out.par[c * S8 + os] = q[c];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) A.out.par[(6 + c) * S8 + os] = ql[c];
+#pragma unroll
+    for (int c = 0; c < 21; ++c) A.out.cov[c * S8 + os] = qC[c];
+    A.out.chi2[os] = chi2_new;
+    A.out.meta[os] = nh_new | (st_new << 8);
+    A.hist_parent[int64_t(l) * S8 + os] = 0;
+    A.hist_hit[int64_t(l) * S8 + os] = hit_plus1 - 1;
+  }
+  A.out.ncand[j] = int8_t(n_win);
+}
+
+cudaError_t launch_build_first_layer(const BuildResidentArgs& a, cudaStream_t st) {
+  if (a.S <= 0) return cudaSuccess;
+  build_first_layer_kernel<<<int((a.S + kResThreads - 1) / kResThreads), kResThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_build_resident(const BuildResidentArgs& a, int num_sms, cudaStream_t st) {
   if (a.S <= 0) return cudaSuccess;
   const int W = resident_lanes(a.max_cands);
@@ -1403,7 +1512,9 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
   // The grouped layouts launch once per layer.
   if (ctx->tune.build_scan == 4) {
     // register-resident layout: one launch takes every seed through all
-    // layers, from buffer 0 (the seeds) to the other buffer
+    // layers, from buffer 0 (the seeds) to the other buffer; with several
+    // lanes a seed, the first layer (one candidate a seed) runs first with one
+    // thread per seed
     BuildResidentArgs ra;
     ra.in = bufA;
     ra.out = bufB;
@@ -1432,9 +1543,22 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
       ra.R[l] = l < L ? ctx->radius[bins->first_layer + l] : 0.f;
       ra.x_x0[l] = l < L ? ctx->x_x0[bins->first_layer + l] : 0.f;
     }
+    CandBuf last = bufB;
+    if (resident_lanes(max_cands) > 1 && L > 1) {
+      // the first layer with one thread per seed (buffer 0 -> buffer 1), then
+      // layers 1 .. L-1 from buffer 1 into the other buffer
+      BuildResidentArgs fl = ra;
+      fl.out_rm = 1 < rm_buffers;
+      KF_CUDA_TRY(ctx, launch_build_first_layer(fl, s));
+      ra.in = bufB;
+      ra.in_rm = 1 < rm_buffers;
+      ra.out = bufA;
+      ra.l0 = 1;
+      last = bufA;
+    }
     KF_CUDA_TRY(ctx, launch_build_resident(ra, ctx->num_sms, s));
     BuildFinalArgs fa;
-    fa.cand = bufB;
+    fa.cand = last;
     fa.hist_parent = hist_parent;
     fa.hist_hit = hist_hit;
     fa.seed_perm = perm;
