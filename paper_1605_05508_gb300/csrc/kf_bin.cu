@@ -10,6 +10,7 @@
 #include "kf_internal.h"
 
 #include <algorithm>
+#include <atomic>
 
 namespace kfi {
 
@@ -142,6 +143,8 @@ __global__ void __launch_bounds__(kPointThreads) bin_sort_kernel(const BinArgs A
   }
 }
 
+constexpr int kMaxDevices = 64;
+
 cudaError_t launch_bin_points(const BinArgs& a, int n_segments, cudaStream_t st) {
   if (n_segments <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(a.bin_off, 0, size_t(n_segments) * (KF_NBINS + 1) * sizeof(int32_t), st);
@@ -149,9 +152,18 @@ cudaError_t launch_bin_points(const BinArgs& a, int n_segments, cudaStream_t st)
   const int64_t pts = a.stride > 0 ? a.stride : 1;
   const int pgrid = int(std::min<int64_t>((pts + kPointThreads - 1) / kPointThreads, int64_t(1) << 20));
   bin_count_kernel<<<pgrid, kPointThreads, 0, st>>>(a, n_segments);
-  // per device and cheap: set on every call (no process-wide flag, no race)
-  e = cudaFuncSetAttribute(bin_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kScanSmem);
+  // the scan kernel's shared-memory attribute, set once per device (the
+  // serving loop bins two point sets per admitted event; setting it again from
+  // another thread is harmless, the value being the same)
+  int dev = 0;
+  e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
+  static std::atomic<bool> scan_attr_set[kMaxDevices];
+  if (dev < 0 || dev >= kMaxDevices || !scan_attr_set[dev].load(std::memory_order_acquire)) {
+    e = cudaFuncSetAttribute(bin_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kScanSmem);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < kMaxDevices) scan_attr_set[dev].store(true, std::memory_order_release);
+  }
   bin_scan_kernel<<<n_segments, kScanThreads, kScanSmem, st>>>(a);
   bin_scatter_kernel<<<pgrid, kPointThreads, 0, st>>>(a, n_segments);
   const int64_t bins = int64_t(n_segments) * KF_NBINS;

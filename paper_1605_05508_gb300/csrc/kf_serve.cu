@@ -219,8 +219,8 @@ struct EventLayout {
     d_fcov = take(21 * n * 4);
     d_fst = take(n * 4);
     d_xyz = take(3 * nh * 4);
-    d_segoff = take((Lb + 1) * 8);
-    d_sseg = take(2 * 8);
+    d_segoff = take((Lb + 1) * 8 + 2 * 8);  // layer offsets, then the seed segment {0, n}
+    d_sseg = d_segoff + (Lb + 1) * 8;
     d_bhits = take(nh * 16);
     d_boff = take(size_t(Lb) * (KF_NBINS + 1) * 4);
     d_bid = take(std::max<int64_t>(nh, n) * 4);
@@ -302,6 +302,10 @@ struct Serve {
   // run at once, beside the steps
   cudaStream_t prep_stream[kPrepStreams] = {};
   int prep_next = 0;
+  // events in the order their work was issued on each in-order stream: the
+  // scheduler queries only the oldest of each (scheduler thread only)
+  std::deque<Request*> prep_order[kPrepStreams];
+  std::deque<Request*> finish_order;
   char* dmem = nullptr;
   char* hmem = nullptr;
   Arena darena, harena;
@@ -332,6 +336,7 @@ static cudaError_t prepare(Serve* sv, Request* r) {
   char* d = sv->dmem + r->d_off;
   char* h = sv->hmem + r->h_in_off;
   cudaStream_t s = sv->prep_stream[sv->prep_next];
+  sv->prep_order[sv->prep_next].push_back(r);
   sv->prep_next = (sv->prep_next + 1) % kPrepStreams;
   const int64_t n = L.n;
   // the host input block mirrors the first device pieces (par .. sval); the
@@ -340,8 +345,8 @@ static cudaError_t prepare(Serve* sv, Request* r) {
   cudaError_t e = cudaMemcpyAsync(d, h, L.h_xyz, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d + L.d_xyz, h + L.h_xyz, size_t(3) * L.nh * 4, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d + L.d_segoff, h + L.h_segoff, size_t(L.Lb + 1) * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)  // the layer offsets and the seed segment {0, n} (host block filled by kf_submit)
+    e = cudaMemcpyAsync(d + L.d_segoff, h + L.h_segoff, size_t(L.Lb + 1) * 8 + 16, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return e;
   // seed fit over the seeding layers (one fused launch)
   FitFusedArgs fa;
@@ -382,10 +387,7 @@ static cudaError_t prepare(Serve* sv, Request* r) {
   hb.unordered = 1;  // the build's results do not depend on the order inside a bin
   e = launch_bin_points(hb, L.Lb, s);
   if (e != cudaSuccess) return e;
-  // seeds in (eta, phi) order: one segment [0, n)
-  const int64_t sseg[2] = {0, n};
-  e = cudaMemcpyAsync(d + L.d_sseg, h + L.h_segoff + size_t(L.Lb + 1) * 8, sizeof sseg, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return e;
+  // seeds in (eta, phi) order: one segment [0, n) (copied with the layer offsets)
   BinArgs sb;
   sb.xyz = reinterpret_cast<const float*>(d + L.d_fpar);
   sb.stride = n;
@@ -534,41 +536,46 @@ static void scheduler(Serve* sv) {
     admitted.clear();
     {
       std::unique_lock<std::mutex> lk(sv->mu);
-      // finished events: results are on the host
-      for (auto it = sv->resident.begin(); it != sv->resident.end();) {
-        Request* r = *it;
-        if (r->state == kFinishing) {
-          const cudaError_t q = cudaEventQuery(r->done);
-          if (q == cudaSuccess) {
-            r->state = kDone;
-            r->t_done = Clock::now();
-            if (r->has_d) sv->darena.release(r->d_off, r->lay.d_total);
-            r->has_d = false;
-            sv->stats.completed++;
-            it = sv->resident.erase(it);
-            sv->done_cv.notify_all();
-            continue;
-          }
-          if (q != cudaErrorNotReady) {
-            fail_all_locked(sv, int(q));
-          }
+      // finished events: results are on the host.  The finish stream runs in
+      // order, so the oldest unfinished event ends the look.
+      while (!sv->finish_order.empty() && !sv->cuda_error) {
+        Request* r = sv->finish_order.front();
+        const cudaError_t q = cudaEventQuery(r->done);
+        if (q == cudaErrorNotReady) break;
+        if (q != cudaSuccess) {
+          fail_all_locked(sv, int(q));
+          break;
         }
-        ++it;
+        sv->finish_order.pop_front();
+        r->state = kDone;
+        r->t_done = Clock::now();
+        if (r->has_d) sv->darena.release(r->d_off, r->lay.d_total);
+        r->has_d = false;
+        sv->stats.completed++;
+        sv->resident.erase(std::find(sv->resident.begin(), sv->resident.end(), r));
+        sv->done_cv.notify_all();
       }
-      // prepared events join the build steps (layer 0)
-      for (Request* r : sv->resident) {
-        if (r->state != kPreparing) continue;
-        const cudaError_t q = cudaEventQuery(r->prepped);
-        if (q == cudaSuccess) {
+      // prepared events join the build steps (layer 0); each preparation
+      // stream runs in order
+      for (int ps = 0; ps < kPrepStreams && !sv->cuda_error; ++ps) {
+        while (!sv->prep_order[ps].empty()) {
+          Request* r = sv->prep_order[ps].front();
+          const cudaError_t q = cudaEventQuery(r->prepped);
+          if (q == cudaErrorNotReady) break;
+          if (q != cudaSuccess) {
+            fail_all_locked(sv, int(q));
+            break;
+          }
+          sv->prep_order[ps].pop_front();
           r->state = kResident;
           r->layer = 0;
-        } else if (q != cudaErrorNotReady) {
-          fail_all_locked(sv, int(q));
         }
       }
       if (sv->cuda_error) {
         sv->resident.clear();
         sv->queue.clear();
+        sv->finish_order.clear();
+        for (auto& q : sv->prep_order) q.clear();
       }
       // admission in arrival order: a free slot and a device block
       while (!sv->queue.empty() && int(sv->resident.size()) < sv->cfg.max_slots && !sv->cuda_error) {
@@ -671,6 +678,7 @@ static void scheduler(Serve* sv) {
           if (e == cudaSuccess) e = finish(sv, r);
           std::lock_guard<std::mutex> lk(sv->mu);
           r->state = kFinishing;
+          sv->finish_order.push_back(r);
         }
     }
     if (e == cudaSuccess) e = cudaEventRecord(sv->iter_ev[ring], sv->stream);
@@ -681,6 +689,8 @@ static void scheduler(Serve* sv) {
       fail_all_locked(sv, int(e));
       sv->resident.clear();
       sv->queue.clear();
+      sv->finish_order.clear();
+      for (auto& q : sv->prep_order) q.clear();
     }
   }
 }
