@@ -320,8 +320,10 @@ typedef struct {
                                  groups of 32 / W seeds (W = max_cands rounded up to 1, 2, 4,
                                  6 or 8 lanes a seed) through all building layers in one
                                  launch, the candidates' states in registers between layers
-                                 (2, 3 and 4 require build_hit_tile 0; a serving loop steps
-                                 one layer at a time and runs 4 as 2) */
+                                 (2, 3 and 4 require build_hit_tile 0; a serving loop with 4
+                                 builds each prepared event through all its layers in one
+                                 resident launch shared with the events prepared with it, and
+                                 with 0 .. 3 steps all resident events one layer a launch) */
     int32_t fit_chunk;        /* kf_fit: 0 = each layer step is one launch over the whole batch
                                  (default); 262144, 524288 or 1048576 = the batch is fitted in
                                  chunks of that many tracks, all layers of a chunk before the

@@ -979,27 +979,32 @@ __device__ __forceinline__ void merge_segment(uint64_t (&L)[LW], int (&P)[LW], i
   }
 }
 
-template <int W>
-__global__ void __launch_bounds__(kResThreads, kResBlocksPerSM) build_resident_kernel(const BuildResidentArgs A) {
+template <int W, bool TABLE>
+__global__ void __launch_bounds__(kResThreads, kResBlocksPerSM)
+    build_resident_kernel(const __grid_constant__ BuildResidentArgs A) {
   constexpr int G = 32 / W;  // seeds per group
   const int lane = threadIdx.x & 31;
   const int g = lane / W, k = lane - g * W;
   // the seed's lanes (none for lanes past G * W)
   const unsigned seg = g < G ? ((1u << W) - 1u) << (g * W) : 0u;
-  const int64_t S8 = A.S * kGroup;
-  const int64_t n_groups = (A.S + G - 1) / G;
+  const int64_t n_groups = TABLE ? A.n_groups : (A.one.S + G - 1) / G;
   const int64_t n_warps = (int64_t(gridDim.x) * kResThreads) >> 5;
   // groups dealt out with a grid stride: at any moment the warps of the GPU
   // work on a narrow band of seeds (a few events), whose hits stay in L2
   for (int64_t gi = (int64_t(blockIdx.x) * kResThreads + threadIdx.x) >> 5; gi < n_groups; gi += n_warps) {
-    const int64_t j = gi * G + g;
-    const bool seed_ok = g < G && j < A.S;
+    int q = 0;  // the batch of this group (a served event), with a table
+    if constexpr (TABLE)
+      while (q + 1 < A.n_batches && A.table[q + 1].group_begin <= gi) ++q;
+    const ResidentBatch& B = TABLE ? A.table[q] : A.one;
+    const int64_t S8 = B.S * kGroup;
+    const int64_t j = (gi - (TABLE ? B.group_begin : 0)) * G + g;
+    const bool seed_ok = g < G && j < B.S;
     int e = 0, nc = 0;
     float a = A.a_scale;
     if (seed_ok) {
-      e = A.seed_evt ? A.seed_evt[j] : 0;
-      a = A.a_scale * float(A.charge[A.seed_perm[j]]);
-      nc = A.in.ncand[j];
+      e = B.seed_evt ? B.seed_evt[j] : 0;
+      a = A.a_scale * float(B.charge[B.seed_perm[j]]);
+      nc = B.in.ncand[j];
     }
     bool active = seed_ok && k < nc;
     float p[6], lo[3], C[21];
@@ -1007,15 +1012,15 @@ __global__ void __launch_bounds__(kResThreads, kResBlocksPerSM) build_resident_k
     int nh = 0;
     int32_t st = 0;
     if (active) {
-      const int64_t slot = cand_slot(j, k, A.S, A.in_rm);
+      const int64_t slot = cand_slot(j, k, B.S, A.in_rm);
 #pragma unroll
-      for (int c = 0; c < 6; ++c) p[c] = A.in.par[c * S8 + slot];
+      for (int c = 0; c < 6; ++c) p[c] = B.in.par[c * S8 + slot];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) lo[c] = A.in.par[(6 + c) * S8 + slot];
+      for (int c = 0; c < 3; ++c) lo[c] = B.in.par[(6 + c) * S8 + slot];
 #pragma unroll
-      for (int c = 0; c < 21; ++c) C[c] = A.in.cov[c * S8 + slot];
-      chi2tot = A.in.chi2[slot];
-      const int32_t meta = A.in.meta[slot];
+      for (int c = 0; c < 21; ++c) C[c] = B.in.cov[c * S8 + slot];
+      chi2tot = B.in.chi2[slot];
+      const int32_t meta = B.in.meta[slot];
       nh = meta & 0xff;
       st = meta >> 8;
     } else {
@@ -1029,7 +1034,7 @@ __global__ void __launch_bounds__(kResThreads, kResBlocksPerSM) build_resident_k
     int n_win = nc;
     for (int l = A.l0; l < A.n_layers; ++l) {
       const int64_t sg = int64_t(e) * A.n_layers + l;
-      const int64_t h0 = seed_ok ? A.seg_off[sg] : 0;
+      const int64_t h0 = seed_ok ? B.seg_off[sg] : 0;
       bool stopped = (st & KF_ST_STOPPED) != 0;
       if (active && !stopped) {
         const int r = kf::propagate<float, kNewtonBuild, true>(p, lo, C, a, A.R[l]);
@@ -1056,11 +1061,11 @@ __global__ void __launch_bounds__(kResThreads, kResBlocksPerSM) build_resident_k
       bool any = false;
       if (win) {
         if constexpr (W == 1)
-          any = scan_window_batched(p, lo, Si, e0, e1, fa0, fa1, fb0, fb1, A.bin_off + sg * (KF_NBINS + 1),
-                                    A.hits + h0, A.cut, nh, chi2tot, k, L, P);
+          any = scan_window_batched(p, lo, Si, e0, e1, fa0, fa1, fb0, fb1, B.bin_off + sg * (KF_NBINS + 1),
+                                    B.hits + h0, A.cut, nh, chi2tot, k, L, P);
         else
-          any = scan_window_batched<W, 2>(p, lo, Si, e0, e1, fa0, fa1, fb0, fb1, A.bin_off + sg * (KF_NBINS + 1),
-                                          A.hits + h0, A.cut, nh, chi2tot, k, L, P);
+          any = scan_window_batched<W, 2>(p, lo, Si, e0, e1, fa0, fa1, fb0, fb1, B.bin_off + sg * (KF_NBINS + 1),
+                                          B.hits + h0, A.cut, nh, chi2tot, k, L, P);
       }
       // no compatible hit (or a stopped candidate): one child without a hit
       if (active && !any) list_insert(L, P, make_key(nh, chi2tot, k, 0), -1);
@@ -1089,16 +1094,16 @@ __global__ void __launch_bounds__(kResThreads, kResBlocksPerSM) build_resident_k
         const int hit_plus1 = int(my_key & 0x1fffffu);
         int32_t st_new = pst;
         if (hit_plus1 > 0) {
-          const float4 m = A.hits[h0 + my_pos];
+          const float4 m = B.hits[h0 + my_pos];
           float r0, r1, r2;
           kf::residual<float, true>(q, ql, m.x, m.y, m.z, r0, r1, r2);
           kf::kalman_update<float, true>(q, ql, qC, qS, r0, r1, r2, A.v0, A.v1, A.v2);
         } else if (!pstopped) {
           st_new |= KF_ST_NO_HIT;
         }
-        const int64_t hslot = int64_t(l) * S8 + cand_slot(j, k, A.S, l + 1 < A.rm_buffers);
-        A.hist_parent[hslot] = int8_t((my_key >> 21) & 7u);
-        A.hist_hit[hslot] = hit_plus1 - 1;
+        const int64_t hslot = int64_t(l) * S8 + cand_slot(j, k, B.S, l + 1 < A.rm_buffers);
+        B.hist_parent[hslot] = int8_t((my_key >> 21) & 7u);
+        B.hist_hit[hslot] = hit_plus1 - 1;
 #pragma unroll
         for (int c = 0; c < 6; ++c) p[c] = q[c];
 #pragma unroll
@@ -1112,17 +1117,17 @@ __global__ void __launch_bounds__(kResThreads, kResBlocksPerSM) build_resident_k
     }
     // the candidates after the last layer, for the final selection
     if (active) {
-      const int64_t slot = cand_slot(j, k, A.S, A.out_rm);
+      const int64_t slot = cand_slot(j, k, B.S, A.out_rm);
 #pragma unroll
-      for (int c = 0; c < 6; ++c) A.out.par[c * S8 + slot] = p[c];
+      for (int c = 0; c < 6; ++c) B.out.par[c * S8 + slot] = p[c];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) A.out.par[(6 + c) * S8 + slot] = lo[c];
+      for (int c = 0; c < 3; ++c) B.out.par[(6 + c) * S8 + slot] = lo[c];
 #pragma unroll
-      for (int c = 0; c < 21; ++c) A.out.cov[c * S8 + slot] = C[c];
-      A.out.chi2[slot] = chi2tot;
-      A.out.meta[slot] = nh | (st << 8);
+      for (int c = 0; c < 21; ++c) B.out.cov[c * S8 + slot] = C[c];
+      B.out.chi2[slot] = chi2tot;
+      B.out.meta[slot] = nh | (st << 8);
     }
-    if (seed_ok && k == 0) A.out.ncand[j] = int8_t(n_win);
+    if (seed_ok && k == 0) B.out.ncand[j] = int8_t(n_win);
   }
 }
 
@@ -1134,27 +1139,28 @@ __global__ void __launch_bounds__(kResThreads, kResBlocksPerSM) build_resident_k
 // seed's ranking), writing them to candidate buffer l0 + 1 and the layer's
 // history.  The same functions and keys as every other layout, so the same
 // bits; build_resident_kernel then continues from layer l0 + 1.
-__global__ void __launch_bounds__(kResThreads, kResBlocksPerSM) build_first_layer_kernel(const BuildResidentArgs A) {
+__global__ void __launch_bounds__(kResThreads, kResBlocksPerSM) build_first_layer_kernel(const __grid_constant__ BuildResidentArgs A) {
+  const ResidentBatch& B = A.one;
   const int64_t j = int64_t(blockIdx.x) * kResThreads + threadIdx.x;
-  if (j >= A.S) return;
-  const int64_t S8 = A.S * kGroup;
+  if (j >= B.S) return;
+  const int64_t S8 = B.S * kGroup;
   const int l = A.l0;
-  const int e = A.seed_evt ? A.seed_evt[j] : 0;
-  const float a = A.a_scale * float(A.charge[A.seed_perm[j]]);
-  const int64_t slot = cand_slot(j, 0, A.S, A.in_rm);  // the seed's only candidate
+  const int e = B.seed_evt ? B.seed_evt[j] : 0;
+  const float a = A.a_scale * float(B.charge[B.seed_perm[j]]);
+  const int64_t slot = cand_slot(j, 0, B.S, A.in_rm);  // the seed's only candidate
   float p[6], lo[3], C[21];
 #pragma unroll
-  for (int c = 0; c < 6; ++c) p[c] = A.in.par[c * S8 + slot];
+  for (int c = 0; c < 6; ++c) p[c] = B.in.par[c * S8 + slot];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) lo[c] = A.in.par[(6 + c) * S8 + slot];
+  for (int c = 0; c < 3; ++c) lo[c] = B.in.par[(6 + c) * S8 + slot];
 #pragma unroll
-  for (int c = 0; c < 21; ++c) C[c] = A.in.cov[c * S8 + slot];
-  const float chi2tot = A.in.chi2[slot];
-  const int32_t meta = A.in.meta[slot];
+  for (int c = 0; c < 21; ++c) C[c] = B.in.cov[c * S8 + slot];
+  const float chi2tot = B.in.chi2[slot];
+  const int32_t meta = B.in.meta[slot];
   const int nh = meta & 0xff;
   int32_t st = meta >> 8;
   const int64_t sg = int64_t(e) * A.n_layers + l;
-  const int64_t h0 = A.seg_off[sg];
+  const int64_t h0 = B.seg_off[sg];
   bool stopped = (st & KF_ST_STOPPED) != 0;
   if (!stopped) {
     const int r = kf::propagate<float, kNewtonBuild, true>(p, lo, C, a, A.R[l]);
@@ -1177,7 +1183,7 @@ __global__ void __launch_bounds__(kResThreads, kResBlocksPerSM) build_first_laye
   if (!stopped) {
     int e0 = 0, e1 = -1, fa0 = 0, fa1 = KF_BIN_PHI - 1, fb0 = 0, fb1 = -1;
     hit_window(p, lo, C, A.R[l], A.v0, A.v1, A.v2, A.cut, Si, e0, e1, fa0, fa1, fb0, fb1);
-    any = scan_window(p, lo, Si, e0, e1, fa0, fa1, fb0, fb1, A.bin_off + sg * (KF_NBINS + 1), A.hits + h0, A.cut,
+    any = scan_window(p, lo, Si, e0, e1, fa0, fa1, fb0, fb1, B.bin_off + sg * (KF_NBINS + 1), B.hits + h0, A.cut,
                       nh, chi2tot, 0, L, P);
   }
   // no compatible hit (or a stopped seed): one child without a hit
@@ -1207,47 +1213,55 @@ __global__ void __launch_bounds__(kResThreads, kResBlocksPerSM) build_first_laye
     const int hit_plus1 = int(key & 0x1fffffu);
     int32_t st_new = st;
     if (hit_plus1 > 0) {
-      const float4 m = A.hits[h0 + pos];
+      const float4 m = B.hits[h0 + pos];
       float r0, r1, r2;
       kf::residual<float, true>(q, ql, m.x, m.y, m.z, r0, r1, r2);
       kf::kalman_update<float, true>(q, ql, qC, Si, r0, r1, r2, A.v0, A.v1, A.v2);
     } else if (!stopped) {
       st_new |= KF_ST_NO_HIT;
     }
-    const int64_t os = cand_slot(j, r, A.S, A.out_rm);
+    const int64_t os = cand_slot(j, r, B.S, A.out_rm);
 #pragma unroll
-    for (int c = 0; c < 6; ++c) A.out.par[c * S8 + os] = q[c];
+    for (int c = 0; c < 6; ++c) B.out.par[c * S8 + os] = q[c];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) A.out.par[(6 + c) * S8 + os] = ql[c];
+    for (int c = 0; c < 3; ++c) B.out.par[(6 + c) * S8 + os] = ql[c];
 #pragma unroll
-    for (int c = 0; c < 21; ++c) A.out.cov[c * S8 + os] = qC[c];
-    A.out.chi2[os] = chi2_new;
-    A.out.meta[os] = nh_new | (st_new << 8);
-    A.hist_parent[int64_t(l) * S8 + os] = 0;
-    A.hist_hit[int64_t(l) * S8 + os] = hit_plus1 - 1;
+    for (int c = 0; c < 21; ++c) B.out.cov[c * S8 + os] = qC[c];
+    B.out.chi2[os] = chi2_new;
+    B.out.meta[os] = nh_new | (st_new << 8);
+    B.hist_parent[int64_t(l) * S8 + os] = 0;
+    B.hist_hit[int64_t(l) * S8 + os] = hit_plus1 - 1;
   }
-  A.out.ncand[j] = int8_t(n_win);
+  B.out.ncand[j] = int8_t(n_win);
 }
 
 cudaError_t launch_build_first_layer(const BuildResidentArgs& a, cudaStream_t st) {
-  if (a.S <= 0) return cudaSuccess;
-  build_first_layer_kernel<<<int((a.S + kResThreads - 1) / kResThreads), kResThreads, 0, st>>>(a);
+  if (a.one.S <= 0) return cudaSuccess;
+  build_first_layer_kernel<<<int((a.one.S + kResThreads - 1) / kResThreads), kResThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
+template <bool TABLE>
+static void launch_resident_w(const BuildResidentArgs& a, int W, int grid, cudaStream_t st) {
+  switch (W) {
+    case 1: build_resident_kernel<1, TABLE><<<grid, kResThreads, 0, st>>>(a); break;
+    case 2: build_resident_kernel<2, TABLE><<<grid, kResThreads, 0, st>>>(a); break;
+    case 4: build_resident_kernel<4, TABLE><<<grid, kResThreads, 0, st>>>(a); break;
+    case 6: build_resident_kernel<6, TABLE><<<grid, kResThreads, 0, st>>>(a); break;
+    default: build_resident_kernel<8, TABLE><<<grid, kResThreads, 0, st>>>(a); break;
+  }
+}
+
 cudaError_t launch_build_resident(const BuildResidentArgs& a, int num_sms, cudaStream_t st) {
-  if (a.S <= 0) return cudaSuccess;
   const int W = resident_lanes(a.max_cands);
-  const int64_t groups = (a.S + (32 / W) - 1) / (32 / W);
+  const int64_t groups = a.table ? a.n_groups : (a.one.S + (32 / W) - 1) / (32 / W);
+  if (groups <= 0) return cudaSuccess;
   const int64_t need = (groups + kResThreads / 32 - 1) / (kResThreads / 32);
   const int grid = int(std::max<int64_t>(1, std::min<int64_t>(need, int64_t(num_sms) * kResBlocksPerSM)));
-  switch (W) {
-    case 1: build_resident_kernel<1><<<grid, kResThreads, 0, st>>>(a); break;
-    case 2: build_resident_kernel<2><<<grid, kResThreads, 0, st>>>(a); break;
-    case 4: build_resident_kernel<4><<<grid, kResThreads, 0, st>>>(a); break;
-    case 6: build_resident_kernel<6><<<grid, kResThreads, 0, st>>>(a); break;
-    default: build_resident_kernel<8><<<grid, kResThreads, 0, st>>>(a); break;
-  }
+  if (a.table)
+    launch_resident_w<true>(a, W, grid, st);
+  else
+    launch_resident_w<false>(a, W, grid, st);
   return cudaGetLastError();
 }
 
@@ -1516,17 +1530,21 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
     // lanes a seed, the first layer (one candidate a seed) runs first with one
     // thread per seed
     BuildResidentArgs ra;
-    ra.in = bufA;
-    ra.out = bufB;
-    ra.hist_parent = hist_parent;
-    ra.hist_hit = hist_hit;
-    ra.seed_evt = evt;
-    ra.seed_perm = perm;
-    ra.charge = seeds->charge;
-    ra.hits = reinterpret_cast<const float4*>(bins->hits);
-    ra.bin_off = bins->bin_off;
-    ra.seg_off = bins->seg_off;
-    ra.S = S;
+    ra.one.in = bufA;
+    ra.one.out = bufB;
+    ra.one.hist_parent = hist_parent;
+    ra.one.hist_hit = hist_hit;
+    ra.one.seed_evt = evt;
+    ra.one.seed_perm = perm;
+    ra.one.charge = seeds->charge;
+    ra.one.hits = reinterpret_cast<const float4*>(bins->hits);
+    ra.one.bin_off = bins->bin_off;
+    ra.one.seg_off = bins->seg_off;
+    ra.one.S = S;
+    ra.one.group_begin = 0;
+    ra.table = nullptr;
+    ra.n_batches = 1;
+    ra.n_groups = 0;
     ra.n_layers = L;
     ra.l0 = 0;
     ra.rm_buffers = rm_buffers;
@@ -1550,9 +1568,9 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
       BuildResidentArgs fl = ra;
       fl.out_rm = 1 < rm_buffers;
       KF_CUDA_TRY(ctx, launch_build_first_layer(fl, s));
-      ra.in = bufB;
+      ra.one.in = bufB;
       ra.in_rm = 1 < rm_buffers;
-      ra.out = bufA;
+      ra.one.out = bufA;
       ra.l0 = 1;
       last = bufA;
     }

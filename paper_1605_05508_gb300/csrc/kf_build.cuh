@@ -147,7 +147,9 @@ inline int build_pack_seeds(int64_t seeds, int scan, int max_cands, int num_sms)
 // per-layer history and buffer n_layers.
 constexpr int kResThreads = 128;
 constexpr int kResBlocksPerSM = 4;
-struct BuildResidentArgs {
+// One batch of seeds of a register-resident build: the whole batch of a
+// kf_build call, or one served event.
+struct ResidentBatch {
   CandBuf in;                // buffer l0 (layout in_rm)
   CandBuf out;               // buffer n_layers (layout out_rm); must not alias `in`
   int8_t* hist_parent;       // [n_layers][S8]: layer l's slots in the layout of buffer l + 1
@@ -159,6 +161,13 @@ struct BuildResidentArgs {
   const int32_t* bin_off;
   const int64_t* seg_off;
   int64_t S;
+  int64_t group_begin;       // with a table: the launch's first group of this batch
+};
+struct BuildResidentArgs {
+  ResidentBatch one;                 // the batch, when `table` is null
+  const ResidentBatch* table;        // device table of n_batches batches (served events), or null
+  int n_batches;
+  int64_t n_groups;                  // with a table: groups of all its batches
   int n_layers, l0, rm_buffers, max_cands;
   int in_rm, out_rm;
   float a_scale, v0, v1, v2, cut, mass;
@@ -169,7 +178,10 @@ struct BuildResidentArgs {
 inline int resident_lanes(int max_cands) {
   return max_cands <= 2 ? max_cands : max_cands <= 4 ? 4 : max_cands <= 6 ? 6 : 8;
 }
+// seeds per warp group of the resident layout (32 / lanes per seed)
+inline int resident_group(int max_cands) { return 32 / resident_lanes(max_cands); }
 cudaError_t launch_build_resident(const BuildResidentArgs& a, int num_sms, cudaStream_t st);
+cudaError_t launch_build_first_layer(const BuildResidentArgs& a, cudaStream_t st);
 
 cudaError_t launch_build_init(const BuildInitArgs& a, cudaStream_t st);
 cudaError_t launch_build_final(const BuildFinalArgs& a, cudaStream_t st);

@@ -13,7 +13,10 @@
 //   * issues ONE build-step launch per iteration over every resident event,
 //     each at its own layer (the slot table tells each block its event,
 //     layer, buffers and hit bins), so candidates stay resident on the device
-//     between layers and small events ride along with big ones,
+//     between layers and small events ride along with big ones -- or, with
+//     the register-resident layout, ONE launch per iteration that takes every
+//     event prepared since the last one through all its building layers (a
+//     table of batches tells each warp group its event),
 //   * selects the best candidate of finished events, copies their results to
 //     pinned host memory asynchronously and recycles their slot and memory.
 // Steps run on one stream, preparations and the finishing of events (final
@@ -284,6 +287,9 @@ struct Request {
 constexpr int kInflight = 2;  // iterations the host may run ahead of the GPU
 constexpr int kPrepStreams = 4;
 constexpr int kRing = kInflight + 2;
+// one ring entry of the launch tables: per-layer step slots, or the batches
+// of a register-resident launch
+constexpr size_t kTableBytes = std::max(sizeof(BuildSlot), sizeof(ResidentBatch)) * KF_MAX_SLOTS;
 
 struct Serve {
   kf_ctx* ctx = nullptr;
@@ -309,8 +315,8 @@ struct Serve {
   char* dmem = nullptr;
   char* hmem = nullptr;
   Arena darena, harena;
-  BuildSlot* d_table = nullptr;  // [kRing][KF_MAX_SLOTS]
-  BuildSlot* h_table = nullptr;  // pinned, same shape
+  char* d_table = nullptr;  // [kRing] entries of kTableBytes
+  char* h_table = nullptr;  // pinned, same shape
   cudaEvent_t iter_ev[kRing] = {};
   uint64_t next_ticket = 1;
   std::deque<Request*> queue;
@@ -441,6 +447,27 @@ static BuildSlot slot_of(Serve* sv, Request* r) {
   return b;
 }
 
+// An event as one batch of a register-resident launch: buffer A (filled by
+// the preparation) to buffer B through all building layers.
+static ResidentBatch resident_batch_of(Serve* sv, Request* r) {
+  const EventLayout& L = r->lay;
+  char* d = sv->dmem + r->d_off;
+  ResidentBatch b;
+  b.in = cand_at(d + L.d_candA, L.n);
+  b.out = cand_at(d + L.d_candB, L.n);
+  b.hist_parent = reinterpret_cast<int8_t*>(d + L.d_hp);
+  b.hist_hit = reinterpret_cast<int32_t*>(d + L.d_hh);
+  b.seed_evt = nullptr;
+  b.seed_perm = reinterpret_cast<const int32_t*>(d + L.d_perm);
+  b.charge = reinterpret_cast<const int8_t*>(d + L.d_q);
+  b.hits = reinterpret_cast<const float4*>(d + L.d_bhits);
+  b.bin_off = reinterpret_cast<const int32_t*>(d + L.d_boff);
+  b.seg_off = reinterpret_cast<const int64_t*>(d + L.d_segoff);
+  b.S = L.n;
+  b.group_begin = 0;
+  return b;
+}
+
 // Final selection + asynchronous copy of the results to the pinned output block,
 // on the finish stream (ordered after the event's last step by the caller), so
 // that the next steps need not wait for it.
@@ -452,7 +479,10 @@ static cudaError_t finish(Serve* sv, Request* r) {
   cudaStream_t s = sv->finish_stream;
   BuildFinalArgs fa;
   std::memset(&fa, 0, sizeof fa);
-  fa.cand = cand_at(d + ((L.Lb % 2 == 0) ? L.d_candA : L.d_candB), n);
+  // the last buffer: B after a register-resident launch, else the one the
+  // alternating steps ended on
+  const bool in_b = sv->tune.build_scan == 4 || L.Lb % 2 == 1;
+  fa.cand = cand_at(d + (in_b ? L.d_candB : L.d_candA), n);
   fa.hist_parent = reinterpret_cast<const int8_t*>(d + L.d_hp);
   fa.hist_hit = reinterpret_cast<const int32_t*>(d + L.d_hh);
   fa.seed_perm = reinterpret_cast<const int32_t*>(d + L.d_perm);
@@ -622,8 +652,47 @@ static void scheduler(Serve* sv) {
       for (Request* r : sv->resident)
         if (r->state == kResident && r->layer < r->lay.Lb) stepping.push_back(r);
     }
-    if (e == cudaSuccess && !stepping.empty()) {
-      BuildSlot* ht = sv->h_table + size_t(ring) * KF_MAX_SLOTS;
+    if (e == cudaSuccess && !stepping.empty() && sv->tune.build_scan == 4) {
+      // the register-resident layout: one launch takes every event prepared
+      // since the last one through all its building layers, each event one
+      // batch of the table (the others wait for the next launch)
+      ResidentBatch* ht = reinterpret_cast<ResidentBatch*>(sv->h_table + size_t(ring) * kTableBytes);
+      const int G = resident_group(sv->cfg.max_cands);
+      int64_t groups = 0;
+      for (size_t i = 0; i < stepping.size(); ++i) {
+        ht[i] = resident_batch_of(sv, stepping[i]);
+        ht[i].group_begin = groups;
+        groups += (ht[i].S + G - 1) / G;
+      }
+      ResidentBatch* dt = reinterpret_cast<ResidentBatch*>(sv->d_table + size_t(ring) * kTableBytes);
+      e = cudaMemcpyAsync(dt, ht, sizeof(ResidentBatch) * stepping.size(), cudaMemcpyHostToDevice, sv->stream);
+      BuildResidentArgs ra;
+      std::memset(&ra, 0, sizeof ra);
+      ra.table = dt;
+      ra.n_batches = int(stepping.size());
+      ra.n_groups = groups;
+      const int Lb = sv->cfg.n_build_layers, Ls = sv->cfg.n_seed_layers;
+      ra.n_layers = Lb;
+      ra.l0 = 0;
+      ra.max_cands = sv->cfg.max_cands;
+      ra.rm_buffers = rank_major_buffers(ra.max_cands, Lb);
+      ra.in_rm = 0 < ra.rm_buffers;
+      ra.out_rm = Lb < ra.rm_buffers;
+      ra.a_scale = float(kCLight * double(sv->ctx->cfg.bz_tesla));
+      ra.v0 = ra.v1 = sv->ctx->cfg.sigma_xy_cm * sv->ctx->cfg.sigma_xy_cm;
+      ra.v2 = sv->ctx->cfg.sigma_z_cm * sv->ctx->cfg.sigma_z_cm;
+      ra.cut = sv->ctx->cfg.chi2_cut;
+      ra.mass = sv->ctx->mass;
+      for (int l = 0; l < Lb; ++l) {
+        ra.R[l] = sv->ctx->radius[Ls + l];
+        ra.x_x0[l] = sv->ctx->x_x0[Ls + l];
+      }
+      if (e == cudaSuccess) e = launch_build_resident(ra, sv->ctx->num_sms, sv->stream);
+      for (Request* r : stepping) r->layer = r->lay.Lb;
+      std::lock_guard<std::mutex> lk(sv->mu);
+      sv->stats.step_launches++;
+    } else if (e == cudaSuccess && !stepping.empty()) {
+      BuildSlot* ht = reinterpret_cast<BuildSlot*>(sv->h_table + size_t(ring) * kTableBytes);
       int64_t seeds = 0;
       for (size_t i = 0; i < stepping.size(); ++i) {
         ht[i] = slot_of(sv, stepping[i]);
@@ -634,9 +703,7 @@ static void scheduler(Serve* sv) {
       // resident blocks x 80 seeds) a block's rounds hold too few parents and
       // the grouped layout, 8 lanes per seed, ends such a small step sooner
       // (the same bits either way).
-      // the register-resident layout takes a batch through all its layers in
-      // one launch; events stepped one layer at a time use the packed one
-      int scan = sv->tune.build_scan == 4 ? 2 : sv->tune.build_scan;
+      int scan = sv->tune.build_scan;
       const int64_t pack_min = sv->cfg.pack_min_seeds > 0
                                    ? sv->cfg.pack_min_seeds
                                    : int64_t(sv->ctx->num_sms) * kBuildBlocksPerSM * 80;
@@ -647,7 +714,7 @@ static void scheduler(Serve* sv) {
         ht[i].block_begin = blocks;
         blocks += pack_seeds > 0 ? int((ht[i].S + pack_seeds - 1) / pack_seeds) : build_step_blocks(ht[i].S, scan);
       }
-      BuildSlot* dt = sv->d_table + size_t(ring) * KF_MAX_SLOTS;
+      BuildSlot* dt = reinterpret_cast<BuildSlot*>(sv->d_table + size_t(ring) * kTableBytes);
       e = cudaMemcpyAsync(dt, ht, sizeof(BuildSlot) * stepping.size(), cudaMemcpyHostToDevice, sv->stream);
       BuildStepArgs a;
       a.slots = dt;
@@ -762,11 +829,10 @@ int kf_serve_start(kf_ctx* ctx, const kf_serve_config* cfg) {
   int rc = KF_OK;
   if (ctx->budget && ctx->allocated + dbytes > ctx->budget) rc = KF_ENOMEM;
   if (!rc && cudaMalloc(&sv->dmem, dbytes) != cudaSuccess) rc = KF_ENOMEM;
-  if (!rc && cudaMalloc(&sv->d_table, sizeof(BuildSlot) * kRing * KF_MAX_SLOTS) != cudaSuccess) rc = KF_ENOMEM;
+  if (!rc && cudaMalloc(&sv->d_table, kTableBytes * kRing) != cudaSuccess) rc = KF_ENOMEM;
   if (!rc && cudaHostAlloc(reinterpret_cast<void**>(&sv->hmem), hbytes, cudaHostAllocDefault) != cudaSuccess)
     rc = KF_ENOMEM;
-  if (!rc && cudaHostAlloc(reinterpret_cast<void**>(&sv->h_table), sizeof(BuildSlot) * kRing * KF_MAX_SLOTS,
-                           cudaHostAllocDefault) != cudaSuccess)
+  if (!rc && cudaHostAlloc(reinterpret_cast<void**>(&sv->h_table), kTableBytes * kRing, cudaHostAllocDefault) != cudaSuccess)
     rc = KF_ENOMEM;
   if (!rc && cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking) != cudaSuccess) rc = KF_ECUDA;
   if (!rc && cudaStreamCreateWithFlags(&sv->finish_stream, cudaStreamNonBlocking) != cudaSuccess) rc = KF_ECUDA;

@@ -200,8 +200,10 @@ def test_native_driver_serves_every_request(tmp_path):
                          layer_off=b.layer_off))
     path = str(tmp_path / "pool.kfpool")
     bench.write_serve_pool(path, pool, det, 8, 1 << 30, 1 << 28)
-    for rate, threads in ((0, 2), (400.0, 1)):
-        r = bench.run_serve_driver(path, 24, rate, threads, 3, tuning={"build_scan": 2, "build_list_width": 8})
+    # build_scan 2 steps events one layer a launch; 4 takes each prepared
+    # event through all 7 layers in one register-resident launch
+    for scan, rate, threads in ((2, 0, 2), (2, 400.0, 1), (4, 0, 2), (4, 400.0, 1)):
+        r = bench.run_serve_driver(path, 24, rate, threads, 3, tuning={"build_scan": scan, "build_list_width": 8})
         assert r["requests"] == 24 and r["events_per_s"] > 0, r
         assert 0 < r["p50_ms"] <= r["p99_ms"], r
-        assert r["max_resident"] >= 1 and r["step_launches"] >= 7, r
+        assert r["max_resident"] >= 1 and r["step_launches"] >= (7 if scan == 2 else 1), r
