@@ -979,6 +979,32 @@ __device__ __forceinline__ void merge_segment(uint64_t (&L)[LW], int (&P)[LW], i
   }
 }
 
+template <typename T>
+__device__ bool pd5_final(const T p[6], const T C[21]) {
+  using kf::sym;
+  const T r = sqrtf(p[0] * p[0] + p[1] * p[1]);
+  const T t0 = r > T(0) ? -p[1] / r : T(0), t1 = r > T(0) ? p[0] / r : T(1);
+  T M[5][5];
+  M[0][0] = t0 * t0 * C[sym(0, 0)] + T(2) * t0 * t1 * C[sym(1, 0)] + t1 * t1 * C[sym(1, 1)];
+  for (int jj = 1; jj < 5; ++jj) {
+    M[jj][0] = t0 * C[sym(0, jj + 1)] + t1 * C[sym(1, jj + 1)];
+    for (int kk = 1; kk <= jj; ++kk) M[jj][kk] = C[sym(jj + 1, kk + 1)];
+  }
+  T Lc[5][5];
+  for (int jj = 0; jj < 5; ++jj) {
+    T d = M[jj][jj];
+    for (int kk = 0; kk < jj; ++kk) d -= Lc[jj][kk] * Lc[jj][kk];
+    if (!(d > T(0))) return false;
+    Lc[jj][jj] = sqrtf(d);
+    for (int ii = jj + 1; ii < 5; ++ii) {
+      T v = M[ii][jj];
+      for (int kk = 0; kk < jj; ++kk) v -= Lc[ii][kk] * Lc[jj][kk];
+      Lc[ii][jj] = v / Lc[jj][jj];
+    }
+  }
+  return true;
+}
+
 template <int W, bool TABLE>
 __global__ void __launch_bounds__(kResThreads, kResBlocksPerSM)
     build_resident_kernel(const __grid_constant__ BuildResidentArgs A) {
@@ -1115,17 +1141,52 @@ __global__ void __launch_bounds__(kResThreads, kResBlocksPerSM)
         st = st_new;
       }
     }
-    // the candidates after the last layer, for the final selection
-    if (active) {
-      const int64_t slot = cand_slot(j, k, B.S, A.out_rm);
+    if (B.res.best.par) {
+      // the final selection in place: lane k holds rank k, so the seed's
+      // first lane writes the best candidate and every lane below max_cands
+      // its summary; the paths (a chain of dependent history loads a seed)
+      // are left to build_final_kernel in its paths-only form
+      const kf_build_result& o = B.res;
+      if (seed_ok && k < A.max_cands) {
+        const int64_t seed = B.seed_perm[j];
+        const bool have = k < n_win;
+        if (k == 0) {
 #pragma unroll
-      for (int c = 0; c < 6; ++c) B.out.par[c * S8 + slot] = p[c];
+          for (int c = 0; c < 6; ++c) o.best.par[c * B.S + seed] = p[c];
+          if (o.best.par_lo)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) B.out.par[(6 + c) * S8 + slot] = lo[c];
+            for (int c = 0; c < 3; ++c) o.best.par_lo[c * B.S + seed] = lo[c];
 #pragma unroll
-      for (int c = 0; c < 21; ++c) B.out.cov[c * S8 + slot] = C[c];
-      B.out.chi2[slot] = chi2tot;
-      B.out.meta[slot] = nh | (st << 8);
+          for (int c = 0; c < 21; ++c) o.best.cov[c * B.S + seed] = C[c];
+          float pf[6];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) pf[c] = p[c] + lo[c];
+#pragma unroll
+          for (int c = 3; c < 6; ++c) pf[c] = p[c];
+          int32_t sf = st;
+          if (!pd5_final(pf, C)) sf |= KF_ST_NOT_PD;
+          if (o.chi2_tot) o.chi2_tot[seed] = chi2tot;
+          if (o.n_hits) o.n_hits[seed] = nh;
+          if (o.status) o.status[seed] = sf;
+          if (o.n_cands) o.n_cands[seed] = n_win;
+        }
+        const int64_t oc = seed * A.max_cands + k;
+        if (o.cand_chi2_tot) o.cand_chi2_tot[oc] = have ? chi2tot : 0.f;
+        if (o.cand_n_hits) o.cand_n_hits[oc] = have ? nh : 0;
+      }
+    } else {
+      // the candidates after the last layer, for the final selection
+      if (active) {
+        const int64_t slot = cand_slot(j, k, B.S, A.out_rm);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) B.out.par[c * S8 + slot] = p[c];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) B.out.par[(6 + c) * S8 + slot] = lo[c];
+#pragma unroll
+        for (int c = 0; c < 21; ++c) B.out.cov[c * S8 + slot] = C[c];
+        B.out.chi2[slot] = chi2tot;
+        B.out.meta[slot] = nh | (st << 8);
+      }
     }
     if (seed_ok && k == 0) B.out.ncand[j] = int8_t(n_win);
   }
@@ -1278,32 +1339,6 @@ __global__ void build_init_kernel(const BuildInitArgs A) {
   A.out.ncand[j] = 1;
 }
 
-template <typename T>
-__device__ bool pd5_final(const T p[6], const T C[21]) {
-  using kf::sym;
-  const T r = sqrtf(p[0] * p[0] + p[1] * p[1]);
-  const T t0 = r > T(0) ? -p[1] / r : T(0), t1 = r > T(0) ? p[0] / r : T(1);
-  T M[5][5];
-  M[0][0] = t0 * t0 * C[sym(0, 0)] + T(2) * t0 * t1 * C[sym(1, 0)] + t1 * t1 * C[sym(1, 1)];
-  for (int jj = 1; jj < 5; ++jj) {
-    M[jj][0] = t0 * C[sym(0, jj + 1)] + t1 * C[sym(1, jj + 1)];
-    for (int kk = 1; kk <= jj; ++kk) M[jj][kk] = C[sym(jj + 1, kk + 1)];
-  }
-  T Lc[5][5];
-  for (int jj = 0; jj < 5; ++jj) {
-    T d = M[jj][jj];
-    for (int kk = 0; kk < jj; ++kk) d -= Lc[jj][kk] * Lc[jj][kk];
-    if (!(d > T(0))) return false;
-    Lc[jj][jj] = sqrtf(d);
-    for (int ii = jj + 1; ii < 5; ++ii) {
-      T v = M[ii][jj];
-      for (int kk = 0; kk < jj; ++kk) v -= Lc[ii][kk] * Lc[jj][kk];
-      Lc[ii][jj] = v / Lc[jj][jj];
-    }
-  }
-  return true;
-}
-
 __global__ void build_final_kernel(const BuildFinalArgs A) {
   const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j >= A.S) return;
@@ -1312,6 +1347,30 @@ __global__ void build_final_kernel(const BuildFinalArgs A) {
   const bool last_rm = A.n_layers < A.rm_buffers;  // layout of buffer n_layers
   const int nc = A.cand.ncand[j];
   const kf_build_result& o = A.out;
+  if (A.paths_only) {  // the build launch wrote the rest
+    if (o.hit_idx) {
+      int kk = 0;
+      for (int l = A.n_layers - 1; l >= 0; --l) {
+        const int64_t sl = int64_t(l) * S8 + cand_slot(j, kk, A.S, l + 1 < A.rm_buffers);
+        o.hit_idx[int64_t(l) * A.S + seed] = A.hist_hit[sl];
+        kk = A.hist_parent[sl];
+      }
+    }
+    if (o.cand_hit_idx)
+      for (int c = 0; c < A.max_cands; ++c) {
+        int kk = c;
+        for (int l = A.n_layers - 1; l >= 0; --l) {
+          int32_t h = -1;
+          if (c < nc) {
+            const int64_t sl = int64_t(l) * S8 + cand_slot(j, kk, A.S, l + 1 < A.rm_buffers);
+            h = A.hist_hit[sl];
+            kk = A.hist_parent[sl];
+          }
+          o.cand_hit_idx[int64_t(l) * A.S * A.max_cands + seed * A.max_cands + c] = h;
+        }
+      }
+    return;
+  }
   // best candidate: rank 0
   {
     const int64_t slot = cand_slot(j, 0, A.S, last_rm);
@@ -1526,9 +1585,9 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
   // The grouped layouts launch once per layer.
   if (ctx->tune.build_scan == 4) {
     // register-resident layout: one launch takes every seed through all
-    // layers, from buffer 0 (the seeds) to the other buffer; with several
-    // lanes a seed, the first layer (one candidate a seed) runs first with one
-    // thread per seed
+    // layers from buffer 0 (the seeds) and selects the best candidates; with
+    // several lanes a seed, the first layer (one candidate a seed) runs first
+    // with one thread per seed, into buffer 1
     BuildResidentArgs ra;
     ra.one.in = bufA;
     ra.one.out = bufB;
@@ -1542,6 +1601,7 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
     ra.one.seg_off = bins->seg_off;
     ra.one.S = S;
     ra.one.group_begin = 0;
+    std::memset(&ra.one.res, 0, sizeof ra.one.res);
     ra.table = nullptr;
     ra.n_batches = 1;
     ra.n_groups = 0;
@@ -1561,7 +1621,6 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
       ra.R[l] = l < L ? ctx->radius[bins->first_layer + l] : 0.f;
       ra.x_x0[l] = l < L ? ctx->x_x0[bins->first_layer + l] : 0.f;
     }
-    CandBuf last = bufB;
     if (resident_lanes(max_cands) > 1 && L > 1) {
       // the first layer with one thread per seed (buffer 0 -> buffer 1), then
       // layers 1 .. L-1 from buffer 1 into the other buffer
@@ -1572,11 +1631,13 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
       ra.in_rm = 1 < rm_buffers;
       ra.one.out = bufA;
       ra.l0 = 1;
-      last = bufA;
     }
+    // the last launch also selects the best candidates and writes `out`,
+    // all but the paths: those follow the history, one thread a seed
+    ra.one.res = *out;
     KF_CUDA_TRY(ctx, launch_build_resident(ra, ctx->num_sms, s));
     BuildFinalArgs fa;
-    fa.cand = last;
+    fa.cand = ra.one.out;
     fa.hist_parent = hist_parent;
     fa.hist_hit = hist_hit;
     fa.seed_perm = perm;
@@ -1584,9 +1645,12 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
     fa.n_layers = L;
     fa.max_cands = max_cands;
     fa.rm_buffers = rm_buffers;
+    fa.paths_only = 1;
     fa.out = *out;
-    build_final_kernel<<<int((S + 127) / 128), 128, 0, s>>>(fa);
-    KF_CUDA_TRY(ctx, cudaGetLastError());
+    if (out->hit_idx || out->cand_hit_idx) {
+      build_final_kernel<<<int((S + 127) / 128), 128, 0, s>>>(fa);
+      KF_CUDA_TRY(ctx, cudaGetLastError());
+    }
     return KF_OK;
   }
   const int first_fused = is_packed(ctx->tune.build_scan) ? (rm_buffers > L ? 0 : std::min(L, rm_buffers)) : L;
@@ -1616,6 +1680,7 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
   fa.n_layers = L;
   fa.max_cands = max_cands;
   fa.rm_buffers = rm_buffers;
+  fa.paths_only = 0;
   fa.out = *out;
   build_final_kernel<<<int((S + 127) / 128), 128, 0, s>>>(fa);
   KF_CUDA_TRY(ctx, cudaGetLastError());

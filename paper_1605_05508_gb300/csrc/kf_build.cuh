@@ -92,6 +92,7 @@ struct BuildFinalArgs {
   int64_t S;
   int n_layers, max_cands;
   int rm_buffers;  // rank_major_buffers(max_cands, n_layers)
+  int paths_only;  // 1: only the paths (hit_idx, cand_hit_idx; cand: ncand alone is read)
   kf_build_result out;
 };
 
@@ -162,6 +163,11 @@ struct ResidentBatch {
   const int64_t* seg_off;
   int64_t S;
   int64_t group_begin;       // with a table: the launch's first group of this batch
+  // the final selection, done by the kernel after the last layer when
+  // res.best.par is set (the best candidate and the optional per-candidate
+  // summaries, as build_final_kernel writes them, all but the paths; only
+  // out.ncand is then written); else the candidates go to `out`
+  kf_build_result res;
 };
 struct BuildResidentArgs {
   ResidentBatch one;                 // the batch, when `table` is null

@@ -465,24 +465,35 @@ static ResidentBatch resident_batch_of(Serve* sv, Request* r) {
   b.seg_off = reinterpret_cast<const int64_t*>(d + L.d_segoff);
   b.S = L.n;
   b.group_begin = 0;
+  // the launch also selects the best candidates into the event's results
+  std::memset(&b.res, 0, sizeof b.res);
+  b.res.best.n = L.n;
+  b.res.best.par = reinterpret_cast<float*>(d + L.d_rpar);
+  b.res.best.cov = reinterpret_cast<float*>(d + L.d_rcov);
+  b.res.chi2_tot = reinterpret_cast<float*>(d + L.d_rchi);
+  b.res.n_hits = reinterpret_cast<int32_t*>(d + L.d_rnh);
+  b.res.status = reinterpret_cast<int32_t*>(d + L.d_rst);
+  b.res.hit_idx = reinterpret_cast<int32_t*>(d + L.d_rhit);
   return b;
 }
 
-// Final selection + asynchronous copy of the results to the pinned output block,
-// on the finish stream (ordered after the event's last step by the caller), so
-// that the next steps need not wait for it.
+// Final selection (the paths alone after a register-resident launch) +
+// asynchronous copy of the results to the pinned output block, on the finish
+// stream (ordered after the event's last step by the caller), so that the
+// next steps need not wait for it.
 static cudaError_t finish(Serve* sv, Request* r) {
   const EventLayout& L = r->lay;
   char* d = sv->dmem + r->d_off;
   char* o = sv->hmem + r->h_out_off;
   const int64_t n = L.n;
   cudaStream_t s = sv->finish_stream;
+  // after a register-resident launch (which selected the best candidates
+  // itself and left the seeds' candidate counts in buffer B) only the paths;
+  // else the whole selection from the buffer the alternating steps ended on
+  const bool resident = sv->tune.build_scan == 4;
   BuildFinalArgs fa;
   std::memset(&fa, 0, sizeof fa);
-  // the last buffer: B after a register-resident launch, else the one the
-  // alternating steps ended on
-  const bool in_b = sv->tune.build_scan == 4 || L.Lb % 2 == 1;
-  fa.cand = cand_at(d + (in_b ? L.d_candB : L.d_candA), n);
+  fa.cand = cand_at(d + ((resident || L.Lb % 2 == 1) ? L.d_candB : L.d_candA), n);
   fa.hist_parent = reinterpret_cast<const int8_t*>(d + L.d_hp);
   fa.hist_hit = reinterpret_cast<const int32_t*>(d + L.d_hh);
   fa.seed_perm = reinterpret_cast<const int32_t*>(d + L.d_perm);
@@ -490,6 +501,7 @@ static cudaError_t finish(Serve* sv, Request* r) {
   fa.n_layers = L.Lb;
   fa.max_cands = sv->cfg.max_cands;
   fa.rm_buffers = rank_major_buffers(sv->cfg.max_cands, L.Lb);
+  fa.paths_only = resident;
   fa.out.best.n = n;
   fa.out.best.par = reinterpret_cast<float*>(d + L.d_rpar);
   fa.out.best.par_lo = nullptr;
