@@ -1026,18 +1026,27 @@ __global__ void __launch_bounds__(kResThreads, kResBlocksPerSM)
     const int64_t j = (gi - (TABLE ? B.group_begin : 0)) * G + g;
     const bool seed_ok = g < G && j < B.S;
     int e = 0, nc = 0;
+    int64_t si = 0;  // seed index
     float a = A.a_scale;
     if (seed_ok) {
       e = B.seed_evt ? B.seed_evt[j] : 0;
-      a = A.a_scale * float(B.charge[B.seed_perm[j]]);
-      nc = B.in.ncand[j];
+      si = B.seed_perm ? B.seed_perm[j] : j;
+      a = A.a_scale * float(B.charge[si]);
+      nc = B.seed_par ? 1 : B.in.ncand[j];
     }
     bool active = seed_ok && k < nc;
     float p[6], lo[3], C[21];
     float chi2tot = 0.f;
     int nh = 0;
     int32_t st = 0;
-    if (active) {
+    if (active && B.seed_par) {  // the seed itself
+#pragma unroll
+      for (int c = 0; c < 6; ++c) p[c] = B.seed_par[c * B.S + si];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) lo[c] = B.seed_lo ? B.seed_lo[c * B.S + si] : 0.f;
+#pragma unroll
+      for (int c = 0; c < 21; ++c) C[c] = B.seed_cov[c * B.S + si];
+    } else if (active) {
       const int64_t slot = cand_slot(j, k, B.S, A.in_rm);
 #pragma unroll
       for (int c = 0; c < 6; ++c) p[c] = B.in.par[c * S8 + slot];
@@ -1148,7 +1157,7 @@ __global__ void __launch_bounds__(kResThreads, kResBlocksPerSM)
       // are left to build_final_kernel in its paths-only form
       const kf_build_result& o = B.res;
       if (seed_ok && k < A.max_cands) {
-        const int64_t seed = B.seed_perm[j];
+        const int64_t seed = si;
         const bool have = k < n_win;
         if (k == 0) {
 #pragma unroll
@@ -1207,19 +1216,32 @@ __global__ void __launch_bounds__(kResThreads, kResBlocksPerSM) build_first_laye
   const int64_t S8 = B.S * kGroup;
   const int l = A.l0;
   const int e = B.seed_evt ? B.seed_evt[j] : 0;
-  const float a = A.a_scale * float(B.charge[B.seed_perm[j]]);
-  const int64_t slot = cand_slot(j, 0, B.S, A.in_rm);  // the seed's only candidate
+  const int64_t si = B.seed_perm ? B.seed_perm[j] : j;
+  const float a = A.a_scale * float(B.charge[si]);
   float p[6], lo[3], C[21];
+  float chi2tot = 0.f;
+  int nh = 0;
+  int32_t st = 0;
+  if (B.seed_par) {  // the seed itself
 #pragma unroll
-  for (int c = 0; c < 6; ++c) p[c] = B.in.par[c * S8 + slot];
+    for (int c = 0; c < 6; ++c) p[c] = B.seed_par[c * B.S + si];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) lo[c] = B.in.par[(6 + c) * S8 + slot];
+    for (int c = 0; c < 3; ++c) lo[c] = B.seed_lo ? B.seed_lo[c * B.S + si] : 0.f;
 #pragma unroll
-  for (int c = 0; c < 21; ++c) C[c] = B.in.cov[c * S8 + slot];
-  const float chi2tot = B.in.chi2[slot];
-  const int32_t meta = B.in.meta[slot];
-  const int nh = meta & 0xff;
-  int32_t st = meta >> 8;
+    for (int c = 0; c < 21; ++c) C[c] = B.seed_cov[c * B.S + si];
+  } else {
+    const int64_t slot = cand_slot(j, 0, B.S, A.in_rm);  // the seed's only candidate
+#pragma unroll
+    for (int c = 0; c < 6; ++c) p[c] = B.in.par[c * S8 + slot];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) lo[c] = B.in.par[(6 + c) * S8 + slot];
+#pragma unroll
+    for (int c = 0; c < 21; ++c) C[c] = B.in.cov[c * S8 + slot];
+    chi2tot = B.in.chi2[slot];
+    const int32_t meta = B.in.meta[slot];
+    nh = meta & 0xff;
+    st = meta >> 8;
+  }
   const int64_t sg = int64_t(e) * A.n_layers + l;
   const int64_t h0 = B.seg_off[sg];
   bool stopped = (st & KF_ST_STOPPED) != 0;
@@ -1342,7 +1364,7 @@ __global__ void build_init_kernel(const BuildInitArgs A) {
 __global__ void build_final_kernel(const BuildFinalArgs A) {
   const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j >= A.S) return;
-  const int64_t seed = A.seed_perm[j];
+  const int64_t seed = A.seed_perm ? A.seed_perm[j] : j;
   const int64_t S8 = A.S * kGroup;
   const bool last_rm = A.n_layers < A.rm_buffers;  // layout of buffer n_layers
   const int nc = A.cand.ncand[j];
@@ -1532,7 +1554,7 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
   // (the seeds of event e start at seed_off[e])
   globalise_perm_kernel<<<int((S + 255) / 256), 256, 0, s>>>(perm, evt, seed_off, S);
   KF_CUDA_TRY(ctx, cudaGetLastError());
-  {
+  if (ctx->tune.build_scan != 4) {  // (the register-resident build reads the seeds itself)
     BuildInitArgs ia;
     ia.out = bufA;
     ia.par = seeds->par;
@@ -1585,7 +1607,7 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
   // The grouped layouts launch once per layer.
   if (ctx->tune.build_scan == 4) {
     // register-resident layout: one launch takes every seed through all
-    // layers from buffer 0 (the seeds) and selects the best candidates; with
+    // layers from the seeds themselves and selects the best candidates; with
     // several lanes a seed, the first layer (one candidate a seed) runs first
     // with one thread per seed, into buffer 1
     BuildResidentArgs ra;
@@ -1602,6 +1624,9 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
     ra.one.S = S;
     ra.one.group_begin = 0;
     std::memset(&ra.one.res, 0, sizeof ra.one.res);
+    ra.one.seed_par = seeds->par;
+    ra.one.seed_lo = seeds->par_lo;
+    ra.one.seed_cov = seeds->cov;
     ra.table = nullptr;
     ra.n_batches = 1;
     ra.n_groups = 0;
@@ -1627,6 +1652,7 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
       BuildResidentArgs fl = ra;
       fl.out_rm = 1 < rm_buffers;
       KF_CUDA_TRY(ctx, launch_build_first_layer(fl, s));
+      ra.one.seed_par = ra.one.seed_lo = ra.one.seed_cov = nullptr;
       ra.one.in = bufB;
       ra.in_rm = 1 < rm_buffers;
       ra.one.out = bufA;

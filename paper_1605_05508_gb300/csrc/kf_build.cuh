@@ -51,7 +51,7 @@ struct BuildSlot {
   int8_t* hist_parent;       // [S8] of this layer (slots in the layout of `out`)
   int32_t* hist_hit;         // [S8] of this layer
   const int32_t* seed_evt;   // [S] sorted position -> event, or null (event 0)
-  const int32_t* seed_perm;  // [S] sorted position -> seed index
+  const int32_t* seed_perm;  // [S] sorted position -> seed index, or null (the identity)
   const int8_t* charge;      // [S] by seed index
   const float4* hits;
   const int32_t* bin_off;
@@ -88,7 +88,7 @@ struct BuildFinalArgs {
   CandBuf cand;
   const int8_t* hist_parent;  // [L][S8]
   const int32_t* hist_hit;    // [L][S8]
-  const int32_t* seed_perm;
+  const int32_t* seed_perm;  // or null (the identity)
   int64_t S;
   int n_layers, max_cands;
   int rm_buffers;  // rank_major_buffers(max_cands, n_layers)
@@ -156,13 +156,19 @@ struct ResidentBatch {
   int8_t* hist_parent;       // [n_layers][S8]: layer l's slots in the layout of buffer l + 1
   int32_t* hist_hit;         // [n_layers][S8]
   const int32_t* seed_evt;   // [S] sorted position -> event, or null (event 0)
-  const int32_t* seed_perm;  // [S] sorted position -> seed index
+  const int32_t* seed_perm;  // [S] sorted position -> seed index, or null (the identity)
   const int8_t* charge;      // [S] by seed index
   const float4* hits;
   const int32_t* bin_off;
   const int64_t* seg_off;
   int64_t S;
   int64_t group_begin;       // with a table: the launch's first group of this batch
+  // the seeds themselves ([6] / [3] (or null: zero) / [21] x S, by seed
+  // index), read in place of buffer `in` when set (then l0 = 0: every seed
+  // one candidate, chi2 0, no hit)
+  const float* seed_par;
+  const float* seed_lo;
+  const float* seed_cov;
   // the final selection, done by the kernel after the last layer when
   // res.best.par is set (the best candidate and the optional per-candidate
   // summaries, as build_final_kernel writes them, all but the paths; only

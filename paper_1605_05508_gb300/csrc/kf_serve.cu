@@ -8,8 +8,8 @@
 //   * admits queued events in arrival order whenever a slot and a contiguous
 //     block of the device arena are free (memory-based admission),
 //   * prepares admitted events on preparation streams (several events at
-//     once): input copy, seed fit over the seeding layers, hit binning, seed
-//     ordering, first candidate,
+//     once): input copy, seed fit over the seeding layers, hit binning (and
+//     for the layer-stepping layouts seed ordering and first candidates),
 //   * issues ONE build-step launch per iteration over every resident event,
 //     each at its own layer (the slot table tells each block its event,
 //     layer, buffers and hit bins), so candidates stay resident on the device
@@ -393,6 +393,8 @@ static cudaError_t prepare(Serve* sv, Request* r) {
   hb.unordered = 1;  // the build's results do not depend on the order inside a bin
   e = launch_bin_points(hb, L.Lb, s);
   if (e != cudaSuccess) return e;
+  // (a register-resident build takes the seeds in their order, from the fit)
+  if (sv->tune.build_scan == 4) return cudaEventRecord(r->prepped, s);
   // seeds in (eta, phi) order: one segment [0, n) (copied with the layer offsets)
   BinArgs sb;
   sb.xyz = reinterpret_cast<const float*>(d + L.d_fpar);
@@ -458,13 +460,18 @@ static ResidentBatch resident_batch_of(Serve* sv, Request* r) {
   b.hist_parent = reinterpret_cast<int8_t*>(d + L.d_hp);
   b.hist_hit = reinterpret_cast<int32_t*>(d + L.d_hh);
   b.seed_evt = nullptr;
-  b.seed_perm = reinterpret_cast<const int32_t*>(d + L.d_perm);
+  // seeds in their given order (one event's hits stay in L2 whatever the
+  // order), read straight from the seed fit's output
+  b.seed_perm = nullptr;
   b.charge = reinterpret_cast<const int8_t*>(d + L.d_q);
   b.hits = reinterpret_cast<const float4*>(d + L.d_bhits);
   b.bin_off = reinterpret_cast<const int32_t*>(d + L.d_boff);
   b.seg_off = reinterpret_cast<const int64_t*>(d + L.d_segoff);
   b.S = L.n;
   b.group_begin = 0;
+  b.seed_par = reinterpret_cast<const float*>(d + L.d_fpar);
+  b.seed_lo = reinterpret_cast<const float*>(d + L.d_flo);
+  b.seed_cov = reinterpret_cast<const float*>(d + L.d_fcov);
   // the launch also selects the best candidates into the event's results
   std::memset(&b.res, 0, sizeof b.res);
   b.res.best.n = L.n;
@@ -496,7 +503,7 @@ static cudaError_t finish(Serve* sv, Request* r) {
   fa.cand = cand_at(d + ((resident || L.Lb % 2 == 1) ? L.d_candB : L.d_candA), n);
   fa.hist_parent = reinterpret_cast<const int8_t*>(d + L.d_hp);
   fa.hist_hit = reinterpret_cast<const int32_t*>(d + L.d_hh);
-  fa.seed_perm = reinterpret_cast<const int32_t*>(d + L.d_perm);
+  fa.seed_perm = resident ? nullptr : reinterpret_cast<const int32_t*>(d + L.d_perm);
   fa.S = n;
   fa.n_layers = L.Lb;
   fa.max_cands = sv->cfg.max_cands;
