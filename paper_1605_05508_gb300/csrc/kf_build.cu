@@ -1209,9 +1209,17 @@ __global__ void __launch_bounds__(kResThreads, kResBlocksPerSM)
 // seed's ranking), writing them to candidate buffer l0 + 1 and the layer's
 // history.  The same functions and keys as every other layout, so the same
 // bits; build_resident_kernel then continues from layer l0 + 1.
-__global__ void __launch_bounds__(kResThreads, kResBlocksPerSM) build_first_layer_kernel(const __grid_constant__ BuildResidentArgs A) {
-  const ResidentBatch& B = A.one;
-  const int64_t j = int64_t(blockIdx.x) * kResThreads + threadIdx.x;
+template <bool TABLE>
+__global__ void __launch_bounds__(kResThreads, kResBlocksPerSM)
+    build_first_layer_kernel(const __grid_constant__ BuildResidentArgs A) {
+  const int64_t t = int64_t(blockIdx.x) * kResThreads + threadIdx.x;
+  int q = 0;  // the batch of this seed (a served event), with a table
+  if constexpr (TABLE) {
+    if (t >= A.n_seeds) return;
+    while (q + 1 < A.n_batches && A.table[q + 1].seed_begin <= t) ++q;
+  }
+  const ResidentBatch& B = TABLE ? A.table[q] : A.one;
+  const int64_t j = t - (TABLE ? B.seed_begin : 0);
   if (j >= B.S) return;
   const int64_t S8 = B.S * kGroup;
   const int l = A.l0;
@@ -1319,8 +1327,13 @@ __global__ void __launch_bounds__(kResThreads, kResBlocksPerSM) build_first_laye
 }
 
 cudaError_t launch_build_first_layer(const BuildResidentArgs& a, cudaStream_t st) {
-  if (a.one.S <= 0) return cudaSuccess;
-  build_first_layer_kernel<<<int((a.one.S + kResThreads - 1) / kResThreads), kResThreads, 0, st>>>(a);
+  const int64_t seeds = a.table ? a.n_seeds : a.one.S;
+  if (seeds <= 0) return cudaSuccess;
+  const int grid = int((seeds + kResThreads - 1) / kResThreads);
+  if (a.table)
+    build_first_layer_kernel<true><<<grid, kResThreads, 0, st>>>(a);
+  else
+    build_first_layer_kernel<false><<<grid, kResThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -1623,6 +1636,7 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
     ra.one.seg_off = bins->seg_off;
     ra.one.S = S;
     ra.one.group_begin = 0;
+    ra.one.seed_begin = 0;
     std::memset(&ra.one.res, 0, sizeof ra.one.res);
     ra.one.seed_par = seeds->par;
     ra.one.seed_lo = seeds->par_lo;
@@ -1630,6 +1644,7 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
     ra.table = nullptr;
     ra.n_batches = 1;
     ra.n_groups = 0;
+    ra.n_seeds = 0;
     ra.n_layers = L;
     ra.l0 = 0;
     ra.rm_buffers = rm_buffers;

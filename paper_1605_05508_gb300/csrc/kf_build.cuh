@@ -163,6 +163,7 @@ struct ResidentBatch {
   const int64_t* seg_off;
   int64_t S;
   int64_t group_begin;       // with a table: the launch's first group of this batch
+  int64_t seed_begin;        // with a table: the first-layer launch's first seed of this batch
   // the seeds themselves ([6] / [3] (or null: zero) / [21] x S, by seed
   // index), read in place of buffer `in` when set (then l0 = 0: every seed
   // one candidate, chi2 0, no hit)
@@ -180,6 +181,7 @@ struct BuildResidentArgs {
   const ResidentBatch* table;        // device table of n_batches batches (served events), or null
   int n_batches;
   int64_t n_groups;                  // with a table: groups of all its batches
+  int64_t n_seeds;                   // with a table: seeds of all its batches
   int n_layers, l0, rm_buffers, max_cands;
   int in_rm, out_rm;
   float a_scale, v0, v1, v2, cut, mass;

@@ -289,7 +289,14 @@ constexpr int kPrepStreams = 4;
 constexpr int kRing = kInflight + 2;
 // one ring entry of the launch tables: per-layer step slots, or the batches
 // of a register-resident launch
-constexpr size_t kTableBytes = std::max(sizeof(BuildSlot), sizeof(ResidentBatch)) * KF_MAX_SLOTS;
+constexpr size_t kTableBytes = std::max(sizeof(BuildSlot), 2 * sizeof(ResidentBatch)) * KF_MAX_SLOTS;
+
+// With more than one lane a seed, a register-resident build runs its first
+// layer (one candidate a seed) with one thread per seed, seeds -> buffer B,
+// and the rest from buffer B into buffer A; else one launch, seeds -> B.
+inline bool resident_split(const kf_serve_config& c) {
+  return resident_lanes(c.max_cands) > 1 && c.n_build_layers > 1;
+}
 
 struct Serve {
   kf_ctx* ctx = nullptr;
@@ -449,14 +456,17 @@ static BuildSlot slot_of(Serve* sv, Request* r) {
   return b;
 }
 
-// An event as one batch of a register-resident launch: buffer A (filled by
-// the preparation) to buffer B through all building layers.
-static ResidentBatch resident_batch_of(Serve* sv, Request* r) {
+// An event as one batch of a register-resident launch: of the first-layer
+// launch (first = true: the seeds -> buffer B), or of the launch over the
+// other layers (buffer B -> buffer A, or the seeds -> buffer B when the build
+// is not split), which also selects the best candidates.
+static ResidentBatch resident_batch_of(Serve* sv, Request* r, bool first) {
   const EventLayout& L = r->lay;
   char* d = sv->dmem + r->d_off;
+  const bool split = resident_split(sv->cfg);
   ResidentBatch b;
-  b.in = cand_at(d + L.d_candA, L.n);
-  b.out = cand_at(d + L.d_candB, L.n);
+  b.in = cand_at(d + L.d_candB, L.n);
+  b.out = cand_at(d + (split && !first ? L.d_candA : L.d_candB), L.n);
   b.hist_parent = reinterpret_cast<int8_t*>(d + L.d_hp);
   b.hist_hit = reinterpret_cast<int32_t*>(d + L.d_hh);
   b.seed_evt = nullptr;
@@ -469,11 +479,14 @@ static ResidentBatch resident_batch_of(Serve* sv, Request* r) {
   b.seg_off = reinterpret_cast<const int64_t*>(d + L.d_segoff);
   b.S = L.n;
   b.group_begin = 0;
-  b.seed_par = reinterpret_cast<const float*>(d + L.d_fpar);
-  b.seed_lo = reinterpret_cast<const float*>(d + L.d_flo);
-  b.seed_cov = reinterpret_cast<const float*>(d + L.d_fcov);
-  // the launch also selects the best candidates into the event's results
+  b.seed_begin = 0;
+  const bool seeds = first || !split;
+  b.seed_par = seeds ? reinterpret_cast<const float*>(d + L.d_fpar) : nullptr;
+  b.seed_lo = seeds ? reinterpret_cast<const float*>(d + L.d_flo) : nullptr;
+  b.seed_cov = seeds ? reinterpret_cast<const float*>(d + L.d_fcov) : nullptr;
+  // the last launch also selects the best candidates into the event's results
   std::memset(&b.res, 0, sizeof b.res);
+  if (first) return b;
   b.res.best.n = L.n;
   b.res.best.par = reinterpret_cast<float*>(d + L.d_rpar);
   b.res.best.cov = reinterpret_cast<float*>(d + L.d_rcov);
@@ -495,12 +508,14 @@ static cudaError_t finish(Serve* sv, Request* r) {
   const int64_t n = L.n;
   cudaStream_t s = sv->finish_stream;
   // after a register-resident launch (which selected the best candidates
-  // itself and left the seeds' candidate counts in buffer B) only the paths;
-  // else the whole selection from the buffer the alternating steps ended on
+  // itself and left the seeds' candidate counts in its last buffer) only the
+  // paths; else the whole selection from the buffer the alternating steps
+  // ended on
   const bool resident = sv->tune.build_scan == 4;
+  const bool in_b = resident ? !resident_split(sv->cfg) : L.Lb % 2 == 1;
   BuildFinalArgs fa;
   std::memset(&fa, 0, sizeof fa);
-  fa.cand = cand_at(d + ((resident || L.Lb % 2 == 1) ? L.d_candB : L.d_candA), n);
+  fa.cand = cand_at(d + (in_b ? L.d_candB : L.d_candA), n);
   fa.hist_parent = reinterpret_cast<const int8_t*>(d + L.d_hp);
   fa.hist_hit = reinterpret_cast<const int32_t*>(d + L.d_hh);
   fa.seed_perm = resident ? nullptr : reinterpret_cast<const int32_t*>(d + L.d_perm);
@@ -675,28 +690,35 @@ static void scheduler(Serve* sv) {
       // the register-resident layout: one launch takes every event prepared
       // since the last one through all its building layers, each event one
       // batch of the table (the others wait for the next launch)
+      // (the first layer by its own launch, one thread a seed, when split)
+      const bool split = resident_split(sv->cfg);
+      const size_t nb = stepping.size();
       ResidentBatch* ht = reinterpret_cast<ResidentBatch*>(sv->h_table + size_t(ring) * kTableBytes);
+      ResidentBatch* hf = ht + KF_MAX_SLOTS;  // the first-layer launch's table
       const int G = resident_group(sv->cfg.max_cands);
-      int64_t groups = 0;
-      for (size_t i = 0; i < stepping.size(); ++i) {
-        ht[i] = resident_batch_of(sv, stepping[i]);
+      int64_t groups = 0, seeds = 0;
+      for (size_t i = 0; i < nb; ++i) {
+        ht[i] = resident_batch_of(sv, stepping[i], false);
         ht[i].group_begin = groups;
         groups += (ht[i].S + G - 1) / G;
+        if (split) {
+          hf[i] = resident_batch_of(sv, stepping[i], true);
+          hf[i].seed_begin = seeds;
+          seeds += hf[i].S;
+        }
       }
       ResidentBatch* dt = reinterpret_cast<ResidentBatch*>(sv->d_table + size_t(ring) * kTableBytes);
-      e = cudaMemcpyAsync(dt, ht, sizeof(ResidentBatch) * stepping.size(), cudaMemcpyHostToDevice, sv->stream);
+      ResidentBatch* df = dt + KF_MAX_SLOTS;
+      e = cudaMemcpyAsync(dt, ht, sizeof(ResidentBatch) * nb, cudaMemcpyHostToDevice, sv->stream);
+      if (e == cudaSuccess && split)
+        e = cudaMemcpyAsync(df, hf, sizeof(ResidentBatch) * nb, cudaMemcpyHostToDevice, sv->stream);
       BuildResidentArgs ra;
       std::memset(&ra, 0, sizeof ra);
-      ra.table = dt;
-      ra.n_batches = int(stepping.size());
-      ra.n_groups = groups;
+      ra.n_batches = int(nb);
       const int Lb = sv->cfg.n_build_layers, Ls = sv->cfg.n_seed_layers;
       ra.n_layers = Lb;
-      ra.l0 = 0;
       ra.max_cands = sv->cfg.max_cands;
       ra.rm_buffers = rank_major_buffers(ra.max_cands, Lb);
-      ra.in_rm = 0 < ra.rm_buffers;
-      ra.out_rm = Lb < ra.rm_buffers;
       ra.a_scale = float(kCLight * double(sv->ctx->cfg.bz_tesla));
       ra.v0 = ra.v1 = sv->ctx->cfg.sigma_xy_cm * sv->ctx->cfg.sigma_xy_cm;
       ra.v2 = sv->ctx->cfg.sigma_z_cm * sv->ctx->cfg.sigma_z_cm;
@@ -706,6 +728,20 @@ static void scheduler(Serve* sv) {
         ra.R[l] = sv->ctx->radius[Ls + l];
         ra.x_x0[l] = sv->ctx->x_x0[Ls + l];
       }
+      if (e == cudaSuccess && split) {
+        BuildResidentArgs fl = ra;
+        fl.table = df;
+        fl.n_seeds = seeds;
+        fl.l0 = 0;
+        fl.in_rm = 1;  // (not read: the seeds themselves)
+        fl.out_rm = 1 < ra.rm_buffers;
+        e = launch_build_first_layer(fl, sv->stream);
+      }
+      ra.table = dt;
+      ra.n_groups = groups;
+      ra.l0 = split ? 1 : 0;
+      ra.in_rm = ra.l0 < ra.rm_buffers;
+      ra.out_rm = Lb < ra.rm_buffers;
       if (e == cudaSuccess) e = launch_build_resident(ra, sv->ctx->num_sms, sv->stream);
       for (Request* r : stepping) r->layer = r->lay.Lb;
       std::lock_guard<std::mutex> lk(sv->mu);
