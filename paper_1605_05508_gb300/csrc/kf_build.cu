@@ -1154,7 +1154,11 @@ __global__ void __launch_bounds__(kResThreads, kResBlocksPerSM)
       // the final selection in place: lane k holds rank k, so the seed's
       // first lane writes the best candidate and every lane below max_cands
       // its summary; the paths (a chain of dependent history loads a seed)
-      // are left to build_final_kernel in its paths-only form
+      // are left to build_final_kernel in its paths-only form, and with
+      // several lanes a seed so is the positive-definiteness check of the
+      // best covariance (its code here, run by one lane of W, cost 6 % of the
+      // N = 6 build): that kernel reads the position's low part from the
+      // candidate buffer
       const kf_build_result& o = B.res;
       if (seed_ok && k < A.max_cands) {
         const int64_t seed = si;
@@ -1167,16 +1171,21 @@ __global__ void __launch_bounds__(kResThreads, kResBlocksPerSM)
             for (int c = 0; c < 3; ++c) o.best.par_lo[c * B.S + seed] = lo[c];
 #pragma unroll
           for (int c = 0; c < 21; ++c) o.best.cov[c * B.S + seed] = C[c];
-          float pf[6];
-#pragma unroll
-          for (int c = 0; c < 3; ++c) pf[c] = p[c] + lo[c];
-#pragma unroll
-          for (int c = 3; c < 6; ++c) pf[c] = p[c];
-          int32_t sf = st;
-          if (!pd5_final(pf, C)) sf |= KF_ST_NOT_PD;
           if (o.chi2_tot) o.chi2_tot[seed] = chi2tot;
           if (o.n_hits) o.n_hits[seed] = nh;
-          if (o.status) o.status[seed] = sf;
+          if constexpr (W == 1) {
+            float pf[6];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) pf[c] = p[c] + lo[c];
+#pragma unroll
+            for (int c = 3; c < 6; ++c) pf[c] = p[c];
+            if (o.status) o.status[seed] = pd5_final(pf, C) ? st : st | KF_ST_NOT_PD;
+          } else if (o.status) {
+            o.status[seed] = st;
+            const int64_t slot = cand_slot(j, 0, B.S, A.out_rm);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) B.out.par[(6 + c) * S8 + slot] = lo[c];
+          }
           if (o.n_cands) o.n_cands[seed] = n_win;
         }
         const int64_t oc = seed * A.max_cands + k;
@@ -1382,7 +1391,15 @@ __global__ void build_final_kernel(const BuildFinalArgs A) {
   const bool last_rm = A.n_layers < A.rm_buffers;  // layout of buffer n_layers
   const int nc = A.cand.ncand[j];
   const kf_build_result& o = A.out;
-  if (A.paths_only) {  // the build launch wrote the rest
+  if (A.paths_only) {  // the build launch wrote the rest but these
+    if (A.paths_only == 2 && o.status) {  // the best covariance positive definite (low part from the buffer)
+      const int64_t slot = cand_slot(j, 0, A.S, last_rm);
+      float pf[6], C[21];
+      for (int c = 0; c < 6; ++c) pf[c] = o.best.par[c * A.S + seed];
+      for (int c = 0; c < 3; ++c) pf[c] = pf[c] + A.cand.par[(6 + c) * S8 + slot];
+      for (int c = 0; c < 21; ++c) C[c] = o.best.cov[c * A.S + seed];
+      if (!pd5_final(pf, C)) o.status[seed] |= KF_ST_NOT_PD;
+    }
     if (o.hit_idx) {
       int kk = 0;
       for (int l = A.n_layers - 1; l >= 0; --l) {
@@ -1674,7 +1691,8 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
       ra.l0 = 1;
     }
     // the last launch also selects the best candidates and writes `out`,
-    // all but the paths: those follow the history, one thread a seed
+    // all but the paths and the covariance check: those follow, one thread
+    // a seed
     ra.one.res = *out;
     KF_CUDA_TRY(ctx, launch_build_resident(ra, ctx->num_sms, s));
     BuildFinalArgs fa;
@@ -1686,9 +1704,9 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
     fa.n_layers = L;
     fa.max_cands = max_cands;
     fa.rm_buffers = rm_buffers;
-    fa.paths_only = 1;
+    fa.paths_only = resident_defers_pd(max_cands) ? 2 : 1;
     fa.out = *out;
-    if (out->hit_idx || out->cand_hit_idx) {
+    if (out->hit_idx || out->cand_hit_idx || (out->status && fa.paths_only == 2)) {
       build_final_kernel<<<int((S + 127) / 128), 128, 0, s>>>(fa);
       KF_CUDA_TRY(ctx, cudaGetLastError());
     }

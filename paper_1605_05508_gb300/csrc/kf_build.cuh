@@ -92,7 +92,8 @@ struct BuildFinalArgs {
   int64_t S;
   int n_layers, max_cands;
   int rm_buffers;  // rank_major_buffers(max_cands, n_layers)
-  int paths_only;  // 1: only the paths (hit_idx, cand_hit_idx; cand: ncand alone is read)
+  int paths_only;  // 1: only the paths (hit_idx, cand_hit_idx; of cand only ncand is read),
+                   // 2: also the best covariance check (status; cand: ncand, rank 0's low part)
   kf_build_result out;
 };
 
@@ -192,6 +193,9 @@ struct BuildResidentArgs {
 inline int resident_lanes(int max_cands) {
   return max_cands <= 2 ? max_cands : max_cands <= 4 ? 4 : max_cands <= 6 ? 6 : 8;
 }
+// With several lanes a seed, the resident layout leaves the best covariance's
+// positive-definiteness check to the final kernel (paths_only = 2).
+inline bool resident_defers_pd(int max_cands) { return resident_lanes(max_cands) > 1; }
 // seeds per warp group of the resident layout (32 / lanes per seed)
 inline int resident_group(int max_cands) { return 32 / resident_lanes(max_cands); }
 cudaError_t launch_build_resident(const BuildResidentArgs& a, int num_sms, cudaStream_t st);

@@ -523,7 +523,7 @@ static cudaError_t finish(Serve* sv, Request* r) {
   fa.n_layers = L.Lb;
   fa.max_cands = sv->cfg.max_cands;
   fa.rm_buffers = rank_major_buffers(sv->cfg.max_cands, L.Lb);
-  fa.paths_only = resident;
+  fa.paths_only = resident ? (resident_defers_pd(sv->cfg.max_cands) ? 2 : 1) : 0;
   fa.out.best.n = n;
   fa.out.best.par = reinterpret_cast<float*>(d + L.d_rpar);
   fa.out.best.par_lo = nullptr;
