@@ -1005,7 +1005,9 @@ __device__ bool pd5_final(const T p[6], const T C[21]) {
   return true;
 }
 
-template <int W, bool TABLE>
+// MAT: some building layer has material (the scattering code is compiled in
+// only then: present but never run, it cost 2 % of the build)
+template <int W, bool TABLE, bool MAT>
 __global__ void __launch_bounds__(kResThreads, kResBlocksPerSM)
     build_resident_kernel(const __grid_constant__ BuildResidentArgs A) {
   constexpr int G = 32 / W;  // seeds per group
@@ -1076,7 +1078,7 @@ __global__ void __launch_bounds__(kResThreads, kResBlocksPerSM)
         if (r) {
           st |= r;
           stopped = true;
-        } else if (A.x_x0[l] > 0.f) {
+        } else if (MAT && A.x_x0[l] > 0.f) {
           kf::scatter(p, lo, C, A.x_x0[l], A.mass);
         }
       }
@@ -1218,7 +1220,7 @@ __global__ void __launch_bounds__(kResThreads, kResBlocksPerSM)
 // seed's ranking), writing them to candidate buffer l0 + 1 and the layer's
 // history.  The same functions and keys as every other layout, so the same
 // bits; build_resident_kernel then continues from layer l0 + 1.
-template <bool TABLE>
+template <bool TABLE, bool MAT>
 __global__ void __launch_bounds__(kResThreads, kResBlocksPerSM)
     build_first_layer_kernel(const __grid_constant__ BuildResidentArgs A) {
   const int64_t t = int64_t(blockIdx.x) * kResThreads + threadIdx.x;
@@ -1267,7 +1269,7 @@ __global__ void __launch_bounds__(kResThreads, kResBlocksPerSM)
     if (r) {
       st |= r;
       stopped = true;
-    } else if (A.x_x0[l] > 0.f) {
+    } else if (MAT && A.x_x0[l] > 0.f) {
       kf::scatter(p, lo, C, A.x_x0[l], A.mass);
     }
   }
@@ -1339,21 +1341,24 @@ cudaError_t launch_build_first_layer(const BuildResidentArgs& a, cudaStream_t st
   const int64_t seeds = a.table ? a.n_seeds : a.one.S;
   if (seeds <= 0) return cudaSuccess;
   const int grid = int((seeds + kResThreads - 1) / kResThreads);
+  const bool mat = a.x_x0[a.l0] > 0.f;
   if (a.table)
-    build_first_layer_kernel<true><<<grid, kResThreads, 0, st>>>(a);
+    mat ? build_first_layer_kernel<true, true><<<grid, kResThreads, 0, st>>>(a)
+        : build_first_layer_kernel<true, false><<<grid, kResThreads, 0, st>>>(a);
   else
-    build_first_layer_kernel<false><<<grid, kResThreads, 0, st>>>(a);
+    mat ? build_first_layer_kernel<false, true><<<grid, kResThreads, 0, st>>>(a)
+        : build_first_layer_kernel<false, false><<<grid, kResThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
-template <bool TABLE>
+template <bool TABLE, bool MAT>
 static void launch_resident_w(const BuildResidentArgs& a, int W, int grid, cudaStream_t st) {
   switch (W) {
-    case 1: build_resident_kernel<1, TABLE><<<grid, kResThreads, 0, st>>>(a); break;
-    case 2: build_resident_kernel<2, TABLE><<<grid, kResThreads, 0, st>>>(a); break;
-    case 4: build_resident_kernel<4, TABLE><<<grid, kResThreads, 0, st>>>(a); break;
-    case 6: build_resident_kernel<6, TABLE><<<grid, kResThreads, 0, st>>>(a); break;
-    default: build_resident_kernel<8, TABLE><<<grid, kResThreads, 0, st>>>(a); break;
+    case 1: build_resident_kernel<1, TABLE, MAT><<<grid, kResThreads, 0, st>>>(a); break;
+    case 2: build_resident_kernel<2, TABLE, MAT><<<grid, kResThreads, 0, st>>>(a); break;
+    case 4: build_resident_kernel<4, TABLE, MAT><<<grid, kResThreads, 0, st>>>(a); break;
+    case 6: build_resident_kernel<6, TABLE, MAT><<<grid, kResThreads, 0, st>>>(a); break;
+    default: build_resident_kernel<8, TABLE, MAT><<<grid, kResThreads, 0, st>>>(a); break;
   }
 }
 
@@ -1363,10 +1368,12 @@ cudaError_t launch_build_resident(const BuildResidentArgs& a, int num_sms, cudaS
   if (groups <= 0) return cudaSuccess;
   const int64_t need = (groups + kResThreads / 32 - 1) / (kResThreads / 32);
   const int grid = int(std::max<int64_t>(1, std::min<int64_t>(need, int64_t(num_sms) * kResBlocksPerSM)));
+  bool mat = false;
+  for (int l = a.l0; l < a.n_layers; ++l) mat |= a.x_x0[l] > 0.f;
   if (a.table)
-    launch_resident_w<true>(a, W, grid, st);
+    mat ? launch_resident_w<true, true>(a, W, grid, st) : launch_resident_w<true, false>(a, W, grid, st);
   else
-    launch_resident_w<false>(a, W, grid, st);
+    mat ? launch_resident_w<false, true>(a, W, grid, st) : launch_resident_w<false, false>(a, W, grid, st);
   return cudaGetLastError();
 }
 
