@@ -1008,7 +1008,7 @@ __device__ bool pd5_final(const T p[6], const T C[21]) {
 // MAT: some building layer has material (the scattering code is compiled in
 // only then: present but never run, it cost 2 % of the build)
 template <int W, bool TABLE, bool MAT>
-__global__ void __launch_bounds__(kResThreads, kResBlocksPerSM)
+__global__ void __launch_bounds__(kResThreads, resident_blocks_per_sm(W))
     build_resident_kernel(const __grid_constant__ BuildResidentArgs A) {
   constexpr int G = 32 / W;  // seeds per group
   const int lane = threadIdx.x & 31;
@@ -1367,7 +1367,7 @@ cudaError_t launch_build_resident(const BuildResidentArgs& a, int num_sms, cudaS
   const int64_t groups = a.table ? a.n_groups : (a.one.S + (32 / W) - 1) / (32 / W);
   if (groups <= 0) return cudaSuccess;
   const int64_t need = (groups + kResThreads / 32 - 1) / (kResThreads / 32);
-  const int grid = int(std::max<int64_t>(1, std::min<int64_t>(need, int64_t(num_sms) * kResBlocksPerSM)));
+  const int grid = int(std::max<int64_t>(1, std::min<int64_t>(need, int64_t(num_sms) * resident_blocks_per_sm(W))));
   bool mat = false;
   for (int l = a.l0; l < a.n_layers; ++l) mat |= a.x_x0[l] > 0.f;
   if (a.table)

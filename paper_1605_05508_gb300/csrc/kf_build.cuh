@@ -149,6 +149,10 @@ inline int build_pack_seeds(int64_t seeds, int scan, int max_cands, int num_sms)
 // per-layer history and buffer n_layers.
 constexpr int kResThreads = 128;
 constexpr int kResBlocksPerSM = 4;
+// resident blocks per SM of build_resident_kernel<W>: 4 (128 registers a
+// thread); with one lane a seed 5 (measured: 3 % faster there, 6 % slower
+// at W = 6, where the registers are needed)
+constexpr int resident_blocks_per_sm(int W) { return W == 1 ? 5 : kResBlocksPerSM; }
 // One batch of seeds of a register-resident build: the whole batch of a
 // kf_build call, or one served event.
 struct ResidentBatch {
