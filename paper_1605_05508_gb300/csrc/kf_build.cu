@@ -1586,6 +1586,7 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
   ba.out_id = perm;
   ba.out_seg = evt;
   ba.cursor = reinterpret_cast<int32_t*>(base + b_perm + b_evt + 2 * b_cand + b_hp + b_hh + b_tab + b_sbin);
+  ba.unordered = 1;  // each seed's result is independent of the order of the seeds in a bin
   KF_CUDA_TRY(ctx, launch_bin_points(ba, bins->n_events, s));
   // perm holds ids within each event: make them global seed indices
   // (the seeds of event e start at seed_off[e])
