@@ -1133,7 +1133,8 @@ def serve_leg(a, kf, dev, rank, tuning=None):
         os.unlink(pool_path)
     mean_seeds = float(np.mean([pool[i % len(pool)]["seed_par"].shape[1] for i in range(M)]))
     keep = ("events_per_s", "p50_ms", "p99_ms", "mean_ms", "offered_events_per_s", "submit_threads",
-            "max_resident", "step_launches", "iterations", "load_fraction", "repeats_events_per_s")
+            "max_resident", "step_launches", "iterations", "load_fraction", "repeats_events_per_s",
+            "wall_s", "sched_busy_ms", "sched_gpu_wait_ms", "sched_idle_ms")
     sub = lambda d: {k: d[k] for k in keep if k in d}
     return {"workload": f"Poisson stream of events, tracks log-uniform 500-50000 (pool of {len(pool)} events, "
                         f"mean {int(sizes.mean())} tracks), 3x noise hits per layer, build N = 6 on layers 4-10 "

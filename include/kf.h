@@ -426,6 +426,11 @@ typedef struct {
     uint64_t submitted, admitted, completed, cancelled, iterations, step_launches;
     int32_t resident, queued, max_resident;
     size_t device_arena_bytes, device_arena_peak;
+    /* the scheduler thread's time since kf_serve_start [ms]: issuing work and
+     * bookkeeping, waiting for the GPU (the pacing wait on an iteration two
+     * behind), and idle (nothing to issue: waiting for submissions or for
+     * preparations and builds in flight) */
+    double sched_busy_ms, sched_gpu_wait_ms, sched_idle_ms;
 } kf_serve_stats;
 
 /* Start the scheduler thread (one per context).  Allocates the arenas.

@@ -595,6 +595,16 @@ static void release_locked(Serve* sv, Request* r) {
 static void scheduler(Serve* sv) {
   cudaSetDevice(sv->ctx->device);
   uint64_t iter = 0;
+  // the thread's time split (kf_serve_stats.sched_*), accumulated in ns and
+  // published with the other counters under the lock
+  const Clock::time_point t_start = Clock::now();
+  int64_t idle_ns = 0, gpu_wait_ns = 0;
+  auto publish = [&]() {
+    const int64_t all = std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now() - t_start).count();
+    sv->stats.sched_idle_ms = 1e-6 * double(idle_ns);
+    sv->stats.sched_gpu_wait_ms = 1e-6 * double(gpu_wait_ns);
+    sv->stats.sched_busy_ms = 1e-6 * double(all - idle_ns - gpu_wait_ns);
+  };
   std::vector<Request*> admitted;
   while (true) {
     admitted.clear();
@@ -662,10 +672,13 @@ static void scheduler(Serve* sv) {
       for (Request* r : sv->resident) finishing |= r->state == kFinishing || r->state == kPreparing;
       if (!active && admitted.empty()) {
         if (sv->stop && sv->queue.empty() && !finishing) break;
+        const Clock::time_point w0 = Clock::now();
         if (finishing)
           sv->cv.wait_for(lk, std::chrono::microseconds(20));
         else
           sv->cv.wait_for(lk, std::chrono::milliseconds(50));
+        idle_ns += std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now() - w0).count();
+        publish();
         continue;
       }
       sv->stats.resident = int(sv->resident.size());
@@ -678,8 +691,11 @@ static void scheduler(Serve* sv) {
       if (e == cudaSuccess) e = prepare(sv, r);
     // pace: at most kInflight iterations ahead of the GPU
     const int ring = int(iter % kRing);
-    if (e == cudaSuccess && iter >= uint64_t(kInflight))
+    if (e == cudaSuccess && iter >= uint64_t(kInflight)) {
+      const Clock::time_point w0 = Clock::now();
       e = cudaEventSynchronize(sv->iter_ev[(iter - kInflight) % kRing]);
+      gpu_wait_ns += std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now() - w0).count();
+    }
     std::vector<Request*> stepping;
     {
       std::lock_guard<std::mutex> lk(sv->mu);
@@ -807,6 +823,7 @@ static void scheduler(Serve* sv) {
     ++iter;
     std::lock_guard<std::mutex> lk(sv->mu);
     sv->stats.iterations++;
+    publish();
     if (e != cudaSuccess) {
       fail_all_locked(sv, int(e));
       sv->resident.clear();

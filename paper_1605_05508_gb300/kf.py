@@ -90,7 +90,8 @@ class kf_serve_stats(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("admitted", C.c_uint64), ("completed", C.c_uint64),
                 ("cancelled", C.c_uint64), ("iterations", C.c_uint64), ("step_launches", C.c_uint64),
                 ("resident", C.c_int32), ("queued", C.c_int32), ("max_resident", C.c_int32),
-                ("device_arena_bytes", C.c_size_t), ("device_arena_peak", C.c_size_t)]
+                ("device_arena_bytes", C.c_size_t), ("device_arena_peak", C.c_size_t),
+                ("sched_busy_ms", C.c_double), ("sched_gpu_wait_ms", C.c_double), ("sched_idle_ms", C.c_double)]
 
 
 class kf_tuning(C.Structure):

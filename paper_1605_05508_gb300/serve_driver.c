@@ -16,7 +16,8 @@
  *   LIST_WIDTH      context's launch parameters (kf_tuning; default 2 and 8)
  * One line of JSON on stdout: events/s over the whole run (first submit to
  * last result), p50 / p99 / mean latency (kf_submit to results on the host, as
- * the library measures it), and the loop's counters.
+ * the library measures it), and the loop's counters over the run (launches,
+ * iterations, the scheduler thread's busy / GPU-wait / idle time).
  *
  * Pool file (little-endian): "KFSP", int32 version (1), float bz_tesla,
  * int32 n_layers, float radius[n_layers], float sigma_xy, float sigma_z,
@@ -246,6 +247,8 @@ int main(int argc, char **argv)
         g_due[i] = t;
     }
     pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * g_threads);
+    kf_serve_stats st0;
+    kf_serve_stats_get(g_ctx, &st0);
     g_t0 = now_s();
     for (int k = 0; k < g_threads; ++k) pthread_create(&th[k], NULL, submitter, (void *)(intptr_t)k);
     /* this thread polls the requests in order */
@@ -275,8 +278,11 @@ int main(int argc, char **argv)
     const double p50 = g_lat[(int)(0.50 * (g_m - 1))], p99 = g_lat[(int)(0.99 * (g_m - 1))];
     printf("{\"requests\": %d, \"offered_events_per_s\": %.3f, \"submit_threads\": %d, \"wall_s\": %.6f, "
            "\"events_per_s\": %.3f, \"p50_ms\": %.4f, \"p99_ms\": %.4f, \"mean_ms\": %.4f, "
-           "\"max_resident\": %d, \"step_launches\": %llu, \"iterations\": %llu}\n",
+           "\"max_resident\": %d, \"step_launches\": %llu, \"iterations\": %llu, \"sched_busy_ms\": %.3f, "
+           "\"sched_gpu_wait_ms\": %.3f, \"sched_idle_ms\": %.3f}\n",
            g_m, rate, g_threads, wall, g_m / wall, p50, p99, mean, st.max_resident,
-           (unsigned long long)st.step_launches, (unsigned long long)st.iterations);
+           (unsigned long long)(st.step_launches - st0.step_launches),
+           (unsigned long long)(st.iterations - st0.iterations), st.sched_busy_ms - st0.sched_busy_ms,
+           st.sched_gpu_wait_ms - st0.sched_gpu_wait_ms, st.sched_idle_ms - st0.sched_idle_ms);
     return 0;
 }
