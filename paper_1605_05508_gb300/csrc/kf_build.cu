@@ -1528,6 +1528,21 @@ cudaError_t launch_build_final(const BuildFinalArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// evt[j] = the event of seed j: the last e with seed_off[e] <= j (binary search)
+__global__ void seed_event_kernel(int32_t* evt, const int64_t* seed_off, int64_t E, int64_t S) {
+  const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (j >= S) return;
+  int64_t lo = 0, hi = E;
+  while (hi - lo > 1) {
+    const int64_t m = (lo + hi) / 2;
+    if (seed_off[m] <= j)
+      lo = m;
+    else
+      hi = m;
+  }
+  evt[j] = int32_t(lo);
+}
+
 __global__ void globalise_perm_kernel(int32_t* perm, const int32_t* evt, const int64_t* seed_off, int64_t S) {
   const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j < S) perm[j] = int32_t(seed_off[evt[j]] + perm[j]);
@@ -1576,7 +1591,17 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
   int32_t* hist_hit = reinterpret_cast<int32_t*>(base + b_perm + b_evt + 2 * b_cand + b_hp);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
-  // seeds in (eta, phi) bin order within each event
+  // The layer-stepping layouts take the seeds in (eta, phi) bin order within
+  // each event (a block's seeds share hit tiles); the register-resident one
+  // in their given order, only their events looked up: measured, its build
+  // is as fast or faster unordered (no tiles are shared; a grid-stride band
+  // of seeds spans a few events whose hits stay in L2 either way), and the
+  // ordering launches are saved.
+  const bool ordered = ctx->tune.build_scan != 4;
+  if (!ordered) {
+    seed_event_kernel<<<int((S + 255) / 256), 256, 0, s>>>(evt, seed_off, bins->n_events, S);
+    KF_CUDA_TRY(ctx, cudaGetLastError());
+  }
   BinArgs ba;
   ba.xyz = seeds->par;
   ba.stride = S;
@@ -1587,11 +1612,13 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
   ba.out_seg = evt;
   ba.cursor = reinterpret_cast<int32_t*>(base + b_perm + b_evt + 2 * b_cand + b_hp + b_hh + b_tab + b_sbin);
   ba.unordered = 1;  // each seed's result is independent of the order of the seeds in a bin
-  KF_CUDA_TRY(ctx, launch_bin_points(ba, bins->n_events, s));
-  // perm holds ids within each event: make them global seed indices
-  // (the seeds of event e start at seed_off[e])
-  globalise_perm_kernel<<<int((S + 255) / 256), 256, 0, s>>>(perm, evt, seed_off, S);
-  KF_CUDA_TRY(ctx, cudaGetLastError());
+  if (ordered) {
+    KF_CUDA_TRY(ctx, launch_bin_points(ba, bins->n_events, s));
+    // perm holds ids within each event: make them global seed indices
+    // (the seeds of event e start at seed_off[e])
+    globalise_perm_kernel<<<int((S + 255) / 256), 256, 0, s>>>(perm, evt, seed_off, S);
+    KF_CUDA_TRY(ctx, cudaGetLastError());
+  }
   if (ctx->tune.build_scan != 4) {  // (the register-resident build reads the seeds itself)
     BuildInitArgs ia;
     ia.out = bufA;
@@ -1654,7 +1681,7 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
     ra.one.hist_parent = hist_parent;
     ra.one.hist_hit = hist_hit;
     ra.one.seed_evt = evt;
-    ra.one.seed_perm = perm;
+    ra.one.seed_perm = nullptr;  // the given order
     ra.one.charge = seeds->charge;
     ra.one.hits = reinterpret_cast<const float4*>(bins->hits);
     ra.one.bin_off = bins->bin_off;
@@ -1707,7 +1734,7 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
     fa.cand = ra.one.out;
     fa.hist_parent = hist_parent;
     fa.hist_hit = hist_hit;
-    fa.seed_perm = perm;
+    fa.seed_perm = nullptr;
     fa.S = S;
     fa.n_layers = L;
     fa.max_cands = max_cands;
