@@ -14,8 +14,8 @@
 
 namespace kfi {
 
-// A counting sort over all points of all segments at once, in four fully
-// parallel passes: (1) every point adds one to its segment's count of its
+// The ordered binning: a counting sort over all points of all segments at
+// once, in four fully parallel passes: (1) every point adds one to its segment's count of its
 // bin (global atomics into bin_off), (2) one block per segment turns the
 // counts into exclusive offsets (bin_off) and scatter cursors, (3) every
 // point takes the next slot of its bin, (4) one thread per (segment, bin)
@@ -55,16 +55,11 @@ __global__ void __launch_bounds__(kPointThreads) bin_count_kernel(const BinArgs 
 __device__ __forceinline__ int pad_idx(int b) { return b + (b >> 5); }
 constexpr int kScanSmem = (KF_NBINS + KF_NBINS / 32) * int(sizeof(int));
 
-__global__ void __launch_bounds__(kScanThreads) bin_scan_kernel(const BinArgs A) {
-  extern __shared__ int cnt[];  // counts, then offsets (padded layout)
-  __shared__ int warp_tot[32];
-  const int seg = blockIdx.x;
-  int32_t* off = A.bin_off + int64_t(seg) * (KF_NBINS + 1);
-  int32_t* cur = A.cursor + int64_t(seg) * KF_NBINS;
+// Exclusive scan, in place, of the KF_NBINS counts in cnt (padded layout)
+// by the block's kScanThreads threads, each owning kPerThread consecutive
+// bins; returns the total to every thread.  Ends with a barrier.
+__device__ __forceinline__ int scan_bins(int* cnt, int* warp_tot) {
   const int tid = threadIdx.x;
-  for (int b = tid; b < KF_NBINS; b += kScanThreads) cnt[pad_idx(b)] = off[b];  // coalesced
-  __syncthreads();
-  // exclusive scan: each thread owns kPerThread consecutive bins
   int local[kPerThread];
   int run = 0;
 #pragma unroll
@@ -92,14 +87,105 @@ __global__ void __launch_bounds__(kScanThreads) bin_scan_kernel(const BinArgs A)
   }
   __syncthreads();
   const int base = (incl - run) + (warp > 0 ? warp_tot[warp - 1] : 0);
+  const int total = warp_tot[kScanThreads / 32 - 1];
 #pragma unroll
   for (int t = 0; t < kPerThread; ++t) cnt[pad_idx(tid * kPerThread + t)] = base + local[t];
-  if (tid == kScanThreads - 1) off[KF_NBINS] = base + run;
   __syncthreads();
+  return total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) bin_scan_kernel(const BinArgs A) {
+  extern __shared__ int cnt[];  // counts, then offsets (padded layout)
+  __shared__ int warp_tot[32];
+  const int seg = blockIdx.x;
+  int32_t* off = A.bin_off + int64_t(seg) * (KF_NBINS + 1);
+  int32_t* cur = A.cursor + int64_t(seg) * KF_NBINS;
+  const int tid = threadIdx.x;
+  for (int b = tid; b < KF_NBINS; b += kScanThreads) cnt[pad_idx(b)] = off[b];  // coalesced
+  __syncthreads();
+  const int total = scan_bins(cnt, warp_tot);
+  if (tid == 0) off[KF_NBINS] = total;
   for (int b = tid; b < KF_NBINS; b += kScanThreads) {  // coalesced
     const int o = cnt[pad_idx(b)];
     off[b] = o;
     cur[b] = o;
+  }
+}
+
+// The unordered counting sort of one segment per block, its counts and
+// cursors in shared memory (one launch for all segments): (1) every point of
+// the segment adds one to its bin's count, (2) the block turns the counts
+// into exclusive offsets (written to bin_off) and cursors, (3) every point
+// takes the next slot of its bin.  The order inside a bin is that of the
+// shared-memory atomics: for kf_tuning.bin_unordered, whose users do not
+// depend on it.
+__global__ void __launch_bounds__(kScanThreads) bin_segment_kernel(const BinArgs A) {
+  extern __shared__ int cnt[];  // counts, then cursors (padded layout)
+  __shared__ int warp_tot[32];
+  const int seg = blockIdx.x;
+  const int64_t p0 = A.seg_off[seg], p1 = min(A.seg_off[seg + 1], A.stride);
+  int32_t* off = A.bin_off + int64_t(seg) * (KF_NBINS + 1);
+  const int tid = threadIdx.x;
+  for (int b = tid; b < KF_NBINS; b += kScanThreads) cnt[pad_idx(b)] = 0;
+  __syncthreads();
+  // the points in batches of kSegBatch a thread, their loads issued together
+  constexpr int kSegBatch = 4;
+  for (int64_t g0 = p0 + tid; g0 < p1; g0 += int64_t(kScanThreads) * kSegBatch) {
+    float x[kSegBatch], y[kSegBatch], z[kSegBatch];
+#pragma unroll
+    for (int u = 0; u < kSegBatch; ++u) {
+      const int64_t g = g0 + int64_t(u) * kScanThreads;
+      if (g < p1) {
+        x[u] = A.xyz[g];
+        y[u] = A.xyz[A.stride + g];
+        z[u] = A.xyz[2 * A.stride + g];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kSegBatch; ++u) {
+      const int64_t g = g0 + int64_t(u) * kScanThreads;
+      if (g < p1) {
+        const int b = bin_of(x[u], y[u], z[u]);
+        atomicAdd(&cnt[pad_idx(b)], 1);
+        // with points out (hits: their ids travel in .w), out_id is scratch:
+        // it keeps each point's bin for the second pass
+        if (A.out_pts) A.out_id[g] = b;
+      }
+    }
+  }
+  __syncthreads();
+  const int total = scan_bins(cnt, warp_tot);
+  if (tid == 0) off[KF_NBINS] = total;
+  for (int b = tid; b < KF_NBINS; b += kScanThreads) off[b] = cnt[pad_idx(b)];  // coalesced
+  for (int64_t g0 = p0 + tid; g0 < p1; g0 += int64_t(kScanThreads) * kSegBatch) {
+    float x[kSegBatch], y[kSegBatch], z[kSegBatch];
+    int bins[kSegBatch];
+#pragma unroll
+    for (int u = 0; u < kSegBatch; ++u) {
+      const int64_t g = g0 + int64_t(u) * kScanThreads;
+      if (g < p1) {
+        x[u] = A.xyz[g];
+        y[u] = A.xyz[A.stride + g];
+        z[u] = A.xyz[2 * A.stride + g];
+        bins[u] = A.out_pts ? A.out_id[g] : 0;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kSegBatch; ++u) {
+      const int64_t g = g0 + int64_t(u) * kScanThreads;
+      if (g < p1) {
+        const int i = int(g - p0);
+        if (A.out_pts) {  // the bin from the first pass; out_id stays scratch
+          const int64_t q = p0 + atomicAdd(&cnt[pad_idx(bins[u])], 1);
+          A.out_pts[q] = make_float4(x[u], y[u], z[u], __int_as_float(i));
+          if (A.out_seg) A.out_seg[q] = seg;
+        } else {
+          const int64_t q = p0 + atomicAdd(&cnt[pad_idx(bin_of(x[u], y[u], z[u]))], 1);
+          A.out_id[q] = i;
+          if (A.out_seg) A.out_seg[q] = seg;
+        }
+      }
+    }
   }
 }
 
@@ -147,17 +233,31 @@ constexpr int kMaxDevices = 64;
 
 cudaError_t launch_bin_points(const BinArgs& a, int n_segments, cudaStream_t st) {
   if (n_segments <= 0) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(a.bin_off, 0, size_t(n_segments) * (KF_NBINS + 1) * sizeof(int32_t), st);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (a.unordered) {  // one launch, one block per segment
+    static std::atomic<bool> seg_attr_set[kMaxDevices];
+    if (dev < 0 || dev >= kMaxDevices || !seg_attr_set[dev].load(std::memory_order_acquire)) {
+      e = cudaFuncSetAttribute(bin_segment_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kScanSmem);
+      // the largest shared-memory carveout: two blocks (2 x 68 KB) per SM
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(bin_segment_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 int(cudaSharedmemCarveoutMaxShared));
+      if (e != cudaSuccess) return e;
+      if (dev >= 0 && dev < kMaxDevices) seg_attr_set[dev].store(true, std::memory_order_release);
+    }
+    bin_segment_kernel<<<n_segments, kScanThreads, kScanSmem, st>>>(a);
+    return cudaGetLastError();
+  }
+  e = cudaMemsetAsync(a.bin_off, 0, size_t(n_segments) * (KF_NBINS + 1) * sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
   const int64_t pts = a.stride > 0 ? a.stride : 1;
   const int pgrid = int(std::min<int64_t>((pts + kPointThreads - 1) / kPointThreads, int64_t(1) << 20));
   bin_count_kernel<<<pgrid, kPointThreads, 0, st>>>(a, n_segments);
   // the scan kernel's shared-memory attribute, set once per device (the
-  // serving loop bins two point sets per admitted event; setting it again from
+  // serving loop bins point sets of many events; setting it again from
   // another thread is harmless, the value being the same)
-  int dev = 0;
-  e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
   static std::atomic<bool> scan_attr_set[kMaxDevices];
   if (dev < 0 || dev >= kMaxDevices || !scan_attr_set[dev].load(std::memory_order_acquire)) {
     e = cudaFuncSetAttribute(bin_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kScanSmem);

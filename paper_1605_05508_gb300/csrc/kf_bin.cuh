@@ -35,7 +35,8 @@ struct BinArgs {
   const int64_t* seg_off;  // [n_seg + 1]
   int32_t* bin_off;        // [n_seg][KF_NBINS + 1] required: bin starts within the segment, then the count
   float4* out_pts;         // [total] or null
-  int32_t* out_id;         // [total] required: id within the segment, bin order
+  int32_t* out_id;         // [total] required: id within the segment, bin order (unordered, with
+                           // out_pts: scratch, left holding each point's bin in input order)
   int32_t* out_seg;        // [total] or null
   int32_t* cursor;         // [n_seg][KF_NBINS] scratch
   int unordered = 0;       // 1: leave each bin in scatter order (no sort by id)

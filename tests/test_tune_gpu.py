@@ -148,8 +148,13 @@ def test_unordered_bins_give_the_same_build(cuda_ctx_factory):
         ids0 = b0.hits.cpu().numpy()[:, 3].view(np.int32)
         ids1 = b1.hits.cpu().numpy()[:, 3].view(np.int32)
         off = b0.bin_off.cpu().numpy()
+        pts1 = b1.hits.cpu().numpy()
         for s in range(off.shape[0]):  # per segment and bin: the same set of hits
             base = int(batch.layer_off[s])
+            n = int(batch.layer_off[s + 1]) - base
+            seg_ids = ids1[base:base + n]
+            assert np.array_equal(np.sort(seg_ids), np.arange(n)), (name, s)  # a permutation
+            np.testing.assert_array_equal(pts1[base:base + n, :3], batch.layer_xyz[:, base + seg_ids].T)
             for bb in np.nonzero(np.diff(off[s]) > 1)[0][:200]:
                 lo, hi = base + off[s, bb], base + off[s, bb + 1]
                 assert sorted(ids0[lo:hi]) == sorted(ids1[lo:hi]), (name, s, bb)
