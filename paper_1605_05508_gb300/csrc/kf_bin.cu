@@ -119,12 +119,11 @@ __global__ void __launch_bounds__(kScanThreads) bin_scan_kernel(const BinArgs A)
 // takes the next slot of its bin.  The order inside a bin is that of the
 // shared-memory atomics: for kf_tuning.bin_unordered, whose users do not
 // depend on it.
-__global__ void __launch_bounds__(kScanThreads) bin_segment_kernel(const BinArgs A) {
-  extern __shared__ int cnt[];  // counts, then cursors (padded layout)
-  __shared__ int warp_tot[32];
-  const int seg = blockIdx.x;
-  const int64_t p0 = A.seg_off[seg], p1 = min(A.seg_off[seg + 1], A.stride);
-  int32_t* off = A.bin_off + int64_t(seg) * (KF_NBINS + 1);
+// The points [p0, p1) of xyz ([3][stride]) of one segment, by the whole
+// block, with cnt (KF_NBINS padded ints of shared memory) and warp_tot.
+__device__ __forceinline__ void bin_one_segment(const float* xyz, int64_t stride, int64_t p0, int64_t p1,
+                                                int32_t* off, float4* out_pts, int32_t* out_id, int32_t* out_seg,
+                                                int seg, int* cnt, int* warp_tot) {
   const int tid = threadIdx.x;
   for (int b = tid; b < KF_NBINS; b += kScanThreads) cnt[pad_idx(b)] = 0;
   __syncthreads();
@@ -136,9 +135,9 @@ __global__ void __launch_bounds__(kScanThreads) bin_segment_kernel(const BinArgs
     for (int u = 0; u < kSegBatch; ++u) {
       const int64_t g = g0 + int64_t(u) * kScanThreads;
       if (g < p1) {
-        x[u] = A.xyz[g];
-        y[u] = A.xyz[A.stride + g];
-        z[u] = A.xyz[2 * A.stride + g];
+        x[u] = xyz[g];
+        y[u] = xyz[stride + g];
+        z[u] = xyz[2 * stride + g];
       }
     }
 #pragma unroll
@@ -149,7 +148,7 @@ __global__ void __launch_bounds__(kScanThreads) bin_segment_kernel(const BinArgs
         atomicAdd(&cnt[pad_idx(b)], 1);
         // with points out (hits: their ids travel in .w), out_id is scratch:
         // it keeps each point's bin for the second pass
-        if (A.out_pts) A.out_id[g] = b;
+        if (out_pts) out_id[g] = b;
       }
     }
   }
@@ -164,10 +163,10 @@ __global__ void __launch_bounds__(kScanThreads) bin_segment_kernel(const BinArgs
     for (int u = 0; u < kSegBatch; ++u) {
       const int64_t g = g0 + int64_t(u) * kScanThreads;
       if (g < p1) {
-        x[u] = A.xyz[g];
-        y[u] = A.xyz[A.stride + g];
-        z[u] = A.xyz[2 * A.stride + g];
-        bins[u] = A.out_pts ? A.out_id[g] : 0;
+        x[u] = xyz[g];
+        y[u] = xyz[stride + g];
+        z[u] = xyz[2 * stride + g];
+        bins[u] = out_pts ? out_id[g] : 0;
       }
     }
 #pragma unroll
@@ -175,18 +174,35 @@ __global__ void __launch_bounds__(kScanThreads) bin_segment_kernel(const BinArgs
       const int64_t g = g0 + int64_t(u) * kScanThreads;
       if (g < p1) {
         const int i = int(g - p0);
-        if (A.out_pts) {  // the bin from the first pass; out_id stays scratch
+        if (out_pts) {  // the bin from the first pass; out_id stays scratch
           const int64_t q = p0 + atomicAdd(&cnt[pad_idx(bins[u])], 1);
-          A.out_pts[q] = make_float4(x[u], y[u], z[u], __int_as_float(i));
-          if (A.out_seg) A.out_seg[q] = seg;
+          out_pts[q] = make_float4(x[u], y[u], z[u], __int_as_float(i));
+          if (out_seg) out_seg[q] = seg;
         } else {
           const int64_t q = p0 + atomicAdd(&cnt[pad_idx(bin_of(x[u], y[u], z[u]))], 1);
-          A.out_id[q] = i;
-          if (A.out_seg) A.out_seg[q] = seg;
+          out_id[q] = i;
+          if (out_seg) out_seg[q] = seg;
         }
       }
     }
   }
+}
+
+__global__ void __launch_bounds__(kScanThreads) bin_segment_kernel(const BinArgs A) {
+  extern __shared__ int cnt[];  // counts, then cursors (padded layout)
+  __shared__ int warp_tot[32];
+  const int seg = blockIdx.x;
+  bin_one_segment(A.xyz, A.stride, A.seg_off[seg], min(A.seg_off[seg + 1], A.stride),
+                  A.bin_off + int64_t(seg) * (KF_NBINS + 1), A.out_pts, A.out_id, A.out_seg, seg, cnt, warp_tot);
+}
+
+// The same over a table of segments of different point sets (the events a
+// serving iteration prepares), one block per entry.
+__global__ void __launch_bounds__(kScanThreads) bin_segment_table_kernel(const BinSegment* table) {
+  extern __shared__ int cnt[];
+  __shared__ int warp_tot[32];
+  const BinSegment& T = table[blockIdx.x];
+  bin_one_segment(T.xyz, T.stride, T.p0, T.p1, T.bin_off, T.out_pts, T.out_id, nullptr, 0, cnt, warp_tot);
 }
 
 __global__ void __launch_bounds__(kPointThreads) bin_scatter_kernel(const BinArgs A, int nseg) {
@@ -231,6 +247,32 @@ __global__ void __launch_bounds__(kPointThreads) bin_sort_kernel(const BinArgs A
 
 constexpr int kMaxDevices = 64;
 
+// a kernel's shared-memory attributes, set once per device (the serving loop
+// bins from several threads' calls; setting them again is harmless)
+template <class K>
+static cudaError_t segment_smem_attrs(K kernel, std::atomic<bool>* done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < kMaxDevices && done[dev].load(std::memory_order_acquire)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kScanSmem);
+  // the largest shared-memory carveout: two blocks (2 x 68 KB) per SM
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             int(cudaSharedmemCarveoutMaxShared));
+  if (e == cudaSuccess && dev >= 0 && dev < kMaxDevices) done[dev].store(true, std::memory_order_release);
+  return e;
+}
+
+cudaError_t launch_bin_segment_table(const BinSegment* table, int n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  static std::atomic<bool> attr_set[kMaxDevices];
+  cudaError_t e = segment_smem_attrs(bin_segment_table_kernel, attr_set);
+  if (e != cudaSuccess) return e;
+  bin_segment_table_kernel<<<n, kScanThreads, kScanSmem, st>>>(table);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_bin_points(const BinArgs& a, int n_segments, cudaStream_t st) {
   if (n_segments <= 0) return cudaSuccess;
   int dev = 0;
@@ -238,15 +280,8 @@ cudaError_t launch_bin_points(const BinArgs& a, int n_segments, cudaStream_t st)
   if (e != cudaSuccess) return e;
   if (a.unordered) {  // one launch, one block per segment
     static std::atomic<bool> seg_attr_set[kMaxDevices];
-    if (dev < 0 || dev >= kMaxDevices || !seg_attr_set[dev].load(std::memory_order_acquire)) {
-      e = cudaFuncSetAttribute(bin_segment_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kScanSmem);
-      // the largest shared-memory carveout: two blocks (2 x 68 KB) per SM
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(bin_segment_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 int(cudaSharedmemCarveoutMaxShared));
-      if (e != cudaSuccess) return e;
-      if (dev >= 0 && dev < kMaxDevices) seg_attr_set[dev].store(true, std::memory_order_release);
-    }
+    e = segment_smem_attrs(bin_segment_kernel, seg_attr_set);
+    if (e != cudaSuccess) return e;
     bin_segment_kernel<<<n_segments, kScanThreads, kScanSmem, st>>>(a);
     return cudaGetLastError();
   }

@@ -42,6 +42,20 @@ struct BinArgs {
   int unordered = 0;       // 1: leave each bin in scatter order (no sort by id)
 };
 
+// One segment of a table-driven unordered binning: points [p0, p1) of xyz
+// ([3][stride]), their offsets into bin_off ([KF_NBINS + 1]), points into
+// out_pts[p0 .. p1), out_id[p0 .. p1) scratch.
+struct BinSegment {
+  const float* xyz;
+  int64_t stride;
+  int64_t p0, p1;
+  int32_t* bin_off;
+  float4* out_pts;
+  int32_t* out_id;
+};
+// Bin the n segments of a device table in one launch (unordered).
+cudaError_t launch_bin_segment_table(const BinSegment* table, int n, cudaStream_t st);
+
 // Sort the points of every segment into bins (several launches on `st`);
 // stride is the number of points (the segments cover [seg_off[0],
 // seg_off[n_segments])).

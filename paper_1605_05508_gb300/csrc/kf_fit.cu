@@ -280,40 +280,60 @@ __global__ void __launch_bounds__(kStageThreads, kStageBlocksPerSM)
   }
 }
 
-template <bool UPD64>
-__global__ void __launch_bounds__(kFitThreads, UPD64 ? 1 : kFitMinBlocks) fit_fused_kernel(const FitFusedArgs A) {
-  const int64_t n = A.n;
-  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+// All layers of track i of the arrays of E (FitFusedArgs itself, or one
+// event of a table: the same field names), with the layers and constants of A.
+template <bool UPD64, class EV>
+__device__ __forceinline__ void fused_track(const EV& E, const FitFusedArgs& A, int64_t i) {
+  const int64_t n = E.n;
+  {
     float p[6], lo[3], C[21];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) p[c] = A.in_par[c * n + i];
+    for (int c = 0; c < 6; ++c) p[c] = E.in_par[c * n + i];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) lo[c] = A.in_lo ? A.in_lo[c * n + i] : 0.f;
+    for (int c = 0; c < 3; ++c) lo[c] = E.in_lo ? E.in_lo[c * n + i] : 0.f;
 #pragma unroll
-    for (int c = 0; c < 21; ++c) C[c] = A.in_cov[c * n + i];
-    const float a = A.a_scale * float(A.charge[i]);
+    for (int c = 0; c < 21; ++c) C[c] = E.in_cov[c * n + i];
+    const float a = A.a_scale * float(E.charge[i]);
     int32_t st = 0;
     for (int l = 0; l < A.n_layers; ++l) {
       float chi2 = -1.f;
       if (!(st & KF_ST_STOPPED)) {
-        const float* h = A.hits + int64_t(l) * 3 * n;
-        const bool has_hit = A.valid ? A.valid[int64_t(l) * n + i] != 0 : true;
+        const float* h = E.hits + int64_t(l) * 3 * n;
+        const bool has_hit = E.valid ? E.valid[int64_t(l) * n + i] != 0 : true;
         st |= track_step<float, kNewtonF32, true, UPD64>(p, lo, C, a, A.R[l], A.x_x0[l], A.mass, has_hit, h[i],
                                                          h[n + i], h[2 * n + i], A.v0, A.v1, A.v2, chi2);
       }
-      if (A.chi2) A.chi2[int64_t(l) * n + i] = chi2;
+      if (E.chi2) E.chi2[int64_t(l) * n + i] = chi2;
     }
     if (!pd5(p, C)) st |= KF_ST_NOT_PD;
 #pragma unroll
-    for (int c = 0; c < 6; ++c) A.out_par[c * n + i] = p[c];
-    if (A.out_lo) {
+    for (int c = 0; c < 6; ++c) E.out_par[c * n + i] = p[c];
+    if (E.out_lo) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) A.out_lo[c * n + i] = lo[c];
+      for (int c = 0; c < 3; ++c) E.out_lo[c * n + i] = lo[c];
     }
 #pragma unroll
-    for (int c = 0; c < 21; ++c) A.out_cov[c * n + i] = C[c];
-    if (A.status) A.status[i] = st;
+    for (int c = 0; c < 21; ++c) E.out_cov[c * n + i] = C[c];
+    if (E.status) E.status[i] = st;
+  }
+}
+
+template <bool UPD64>
+__global__ void __launch_bounds__(kFitThreads, UPD64 ? 1 : kFitMinBlocks) fit_fused_kernel(const FitFusedArgs A) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < A.n; i += stride) fused_track<UPD64>(A, A, i);
+}
+
+// The fused fit of several events in one launch (the events a serving
+// iteration prepares): thread t fits track t - table[q].begin of event q,
+// the last with table[q].begin <= t; the arithmetic of fit_fused_kernel.
+__global__ void __launch_bounds__(kFitThreads, kFitMinBlocks)
+    fit_fused_table_kernel(const FitFusedArgs A, const FitEvent* table, int n_events, int64_t n_total) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n_total; t += stride) {
+    int q = 0;
+    while (q + 1 < n_events && table[q + 1].begin <= t) ++q;
+    fused_track<false>(table[q], A, t - table[q].begin);
   }
 }
 
@@ -404,6 +424,14 @@ cudaError_t launch_fit_layer_stage(const FitLayerArgs& a, const FitStageMaps& m,
                                        int(kStageSmem));
   if (e != cudaSuccess) return e;
   fit_layer_stage_kernel<<<grid, kStageThreads, kStageSmem, st>>>(a, m);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fit_fused_table(const FitFusedArgs& a, const FitEvent* table, int n_events, int64_t n_total,
+                                   cudaStream_t st) {
+  if (n_total <= 0) return cudaSuccess;
+  const int grid = int((n_total + kFitThreads - 1) / kFitThreads);
+  fit_fused_table_kernel<<<grid, kFitThreads, 0, st>>>(a, table, n_events, n_total);
   return cudaGetLastError();
 }
 

@@ -167,6 +167,27 @@ cudaError_t launch_fit_layer(const FitLayerArgs& a, int block, cudaStream_t st);
 bool make_stage_maps(const FitLayerArgs& a, FitStageMaps* m);
 cudaError_t launch_fit_layer_stage(const FitLayerArgs& a, const FitStageMaps& m, int num_sms, cudaStream_t st);
 cudaError_t launch_fit_fused(const FitFusedArgs& a, cudaStream_t st, bool upd64 = false);
+// One event of a table-driven fused fit: its arrays, as in FitFusedArgs, and
+// the launch's first thread for it.
+struct FitEvent {
+  const float* in_par;
+  const float* in_lo;
+  const float* in_cov;
+  const int8_t* charge;
+  float* out_par;
+  float* out_lo;
+  float* out_cov;
+  const float* hits;
+  const uint8_t* valid;
+  float* chi2;
+  int32_t* status;
+  int64_t n;
+  int64_t begin;
+};
+// The fused fit of n_events events (device table, begins ascending) in one
+// launch; a's arrays are ignored, its layers and constants used.
+cudaError_t launch_fit_fused_table(const FitFusedArgs& a, const FitEvent* table, int n_events, int64_t n_total,
+                                   cudaStream_t st);
 cudaError_t launch_fit_f64(const FitF64Args& a, cudaStream_t st);
 
 // Hits of all layers per seed for a re-fit (kf_refit.cu): seeding layers from

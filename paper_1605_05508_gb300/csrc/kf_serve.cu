@@ -7,9 +7,11 @@
 // arrive at random times.  The scheduler thread here
 //   * admits queued events in arrival order whenever a slot and a contiguous
 //     block of the device arena are free (memory-based admission),
-//   * prepares admitted events on preparation streams (several events at
-//     once): input copy, seed fit over the seeding layers, hit binning (and
-//     for the layer-stepping layouts seed ordering and first candidates),
+//   * prepares the events admitted in one iteration together, on one of
+//     several preparation streams: their input copies, then one seed-fit
+//     launch over all their seeds and one binning launch over all their hit
+//     segments (and for the layer-stepping layouts each event's seed
+//     ordering and first candidates),
 //   * issues ONE build-step launch per iteration over every resident event,
 //     each at its own layer (the slot table tells each block its event,
 //     layer, buffers and hit bins), so candidates stay resident on the device
@@ -291,6 +293,14 @@ constexpr int kRing = kInflight + 2;
 // of a register-resident launch
 constexpr size_t kTableBytes = std::max(sizeof(BuildSlot), 2 * sizeof(ResidentBatch)) * KF_MAX_SLOTS;
 
+// The preparation of the events admitted in one iteration is batched: their
+// seed fits in one launch, their hit segments' binning in another, from
+// tables of per-event pointers (kPrepRing slots, each reused only once the
+// batch that last used it has completed, by its event).
+constexpr int kPrepRing = 8;
+constexpr size_t kPrepFitBytes = sizeof(FitEvent) * KF_MAX_SLOTS;
+constexpr size_t kPrepBytes = kPrepFitBytes + sizeof(BinSegment) * KF_MAX_SLOTS * kMaxLayers;
+
 // With more than one lane a seed, a register-resident build runs its first
 // layer (one candidate a seed) with one thread per seed, seeds -> buffer B,
 // and the rest from buffer B into buffer A; else one launch, seeds -> B.
@@ -322,8 +332,10 @@ struct Serve {
   char* dmem = nullptr;
   char* hmem = nullptr;
   Arena darena, harena;
-  char* d_table = nullptr;  // [kRing] entries of kTableBytes
+  char* d_table = nullptr;  // [kRing] entries of kTableBytes, then [kPrepRing] of kPrepBytes
   char* h_table = nullptr;  // pinned, same shape
+  cudaEvent_t prep_ev[kPrepRing] = {};  // after the batch that last used a preparation table slot
+  int prep_slot = 0;
   cudaEvent_t iter_ev[kRing] = {};
   uint64_t next_ticket = 1;
   std::deque<Request*> queue;
@@ -341,91 +353,130 @@ static void fail_all_locked(Serve* sv, int err) {
   sv->done_cv.notify_all();
 }
 
-// Enqueue the preparation of an admitted event on the preparation stream;
-// the event joins the build steps once r->prepped has completed.
-static cudaError_t prepare(Serve* sv, Request* r) {
+// Enqueue the preparation of the events admitted in one iteration on one
+// preparation stream (round-robin over kPrepStreams): each event's input
+// copies, then ONE fused seed-fit launch over all their seeds and ONE
+// binning launch over all their hit segments (tables of per-event pointers);
+// with the layer-stepping layouts also each event's seed ordering and first
+// candidates.  An event joins the builds once its r->prepped has completed.
+static cudaError_t prepare_batch(Serve* sv, const std::vector<Request*>& rs) {
+  if (rs.empty()) return cudaSuccess;
   kf_ctx* ctx = sv->ctx;
-  const EventLayout& L = r->lay;
-  char* d = sv->dmem + r->d_off;
-  char* h = sv->hmem + r->h_in_off;
-  cudaStream_t s = sv->prep_stream[sv->prep_next];
-  sv->prep_order[sv->prep_next].push_back(r);
-  sv->prep_next = (sv->prep_next + 1) % kPrepStreams;
-  const int64_t n = L.n;
-  // the host input block mirrors the first device pieces (par .. sval); the
-  // raw hits and their offsets follow in the host block and go to their own
-  // device pieces
-  cudaError_t e = cudaMemcpyAsync(d, h, L.h_xyz, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d + L.d_xyz, h + L.h_xyz, size_t(3) * L.nh * 4, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess)  // the layer offsets and the seed segment {0, n} (host block filled by kf_submit)
-    e = cudaMemcpyAsync(d + L.d_segoff, h + L.h_segoff, size_t(L.Lb + 1) * 8 + 16, cudaMemcpyHostToDevice, s);
+  const int ps = sv->prep_next;
+  sv->prep_next = (ps + 1) % kPrepStreams;
+  cudaStream_t s = sv->prep_stream[ps];
+  // the table slot, once the batch that last used it is done with it
+  const int slot = sv->prep_slot;
+  sv->prep_slot = (slot + 1) % kPrepRing;
+  cudaError_t e = cudaEventSynchronize(sv->prep_ev[slot]);
   if (e != cudaSuccess) return e;
-  // seed fit over the seeding layers (one fused launch)
+  char* hslot = sv->h_table + kTableBytes * kRing + kPrepBytes * size_t(slot);
+  char* dslot = sv->d_table + kTableBytes * kRing + kPrepBytes * size_t(slot);
+  FitEvent* hf = reinterpret_cast<FitEvent*>(hslot);
+  BinSegment* hb = reinterpret_cast<BinSegment*>(hslot + kPrepFitBytes);
+  int64_t tracks = 0;
+  int segs = 0;
+  for (size_t k = 0; k < rs.size(); ++k) {
+    Request* r = rs[k];
+    const EventLayout& L = r->lay;
+    char* d = sv->dmem + r->d_off;
+    const char* h = sv->hmem + r->h_in_off;
+    // the host input block mirrors the first device pieces (par .. sval); the
+    // raw hits and their offsets follow in the host block and go to their own
+    // device pieces
+    e = cudaMemcpyAsync(d, h, L.h_xyz, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d + L.d_xyz, h + L.h_xyz, size_t(3) * L.nh * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)  // the layer offsets and the seed segment {0, n} (host block filled by kf_submit)
+      e = cudaMemcpyAsync(d + L.d_segoff, h + L.h_segoff, size_t(L.Lb + 1) * 8 + 16, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    // seed fit over the seeding layers
+    FitEvent& f = hf[k];
+    f.in_par = reinterpret_cast<const float*>(d + L.d_par);
+    f.in_lo = nullptr;
+    f.in_cov = reinterpret_cast<const float*>(d + L.d_cov);
+    f.charge = reinterpret_cast<const int8_t*>(d + L.d_q);
+    f.out_par = reinterpret_cast<float*>(d + L.d_fpar);
+    f.out_lo = reinterpret_cast<float*>(d + L.d_flo);
+    f.out_cov = reinterpret_cast<float*>(d + L.d_fcov);
+    f.hits = reinterpret_cast<const float*>(d + L.d_shits);
+    f.valid = reinterpret_cast<const uint8_t*>(d + L.d_sval);
+    f.chi2 = nullptr;
+    f.status = reinterpret_cast<int32_t*>(d + L.d_fst);
+    f.n = L.n;
+    f.begin = tracks;
+    tracks += L.n;
+    // hits into eta x phi bins, one segment per build layer (its range from
+    // the host copy of the layer offsets)
+    const int64_t* hoff = reinterpret_cast<const int64_t*>(h + L.h_segoff);
+    for (int l = 0; l < L.Lb; ++l) {
+      BinSegment& b = hb[segs++];
+      b.xyz = reinterpret_cast<const float*>(d + L.d_xyz);
+      b.stride = L.nh;
+      b.p0 = hoff[l];
+      b.p1 = std::min<int64_t>(hoff[l + 1], L.nh);
+      b.bin_off = reinterpret_cast<int32_t*>(d + L.d_boff) + int64_t(l) * (KF_NBINS + 1);
+      b.out_pts = reinterpret_cast<float4*>(d + L.d_bhits);
+      b.out_id = reinterpret_cast<int32_t*>(d + L.d_bid);
+    }
+  }
+  FitEvent* df = reinterpret_cast<FitEvent*>(dslot);
+  BinSegment* db = reinterpret_cast<BinSegment*>(dslot + kPrepFitBytes);
+  e = cudaMemcpyAsync(df, hf, sizeof(FitEvent) * rs.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(db, hb, sizeof(BinSegment) * size_t(segs), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  const int Ls = sv->cfg.n_seed_layers;
   FitFusedArgs fa;
   std::memset(&fa, 0, sizeof fa);
-  fa.in_par = reinterpret_cast<const float*>(d + L.d_par);
-  fa.in_lo = nullptr;
-  fa.in_cov = reinterpret_cast<const float*>(d + L.d_cov);
-  fa.charge = reinterpret_cast<const int8_t*>(d + L.d_q);
-  fa.out_par = reinterpret_cast<float*>(d + L.d_fpar);
-  fa.out_lo = reinterpret_cast<float*>(d + L.d_flo);
-  fa.out_cov = reinterpret_cast<float*>(d + L.d_fcov);
-  fa.hits = reinterpret_cast<const float*>(d + L.d_shits);
-  fa.valid = reinterpret_cast<const uint8_t*>(d + L.d_sval);
-  fa.chi2 = nullptr;
-  fa.status = reinterpret_cast<int32_t*>(d + L.d_fst);
-  fa.n = n;
-  fa.n_layers = L.ns;
+  fa.n_layers = Ls;
   fa.a_scale = float(kCLight * double(ctx->cfg.bz_tesla));
   fa.v0 = fa.v1 = ctx->cfg.sigma_xy_cm * ctx->cfg.sigma_xy_cm;
   fa.v2 = ctx->cfg.sigma_z_cm * ctx->cfg.sigma_z_cm;
-  for (int l = 0; l < L.ns; ++l) {
+  for (int l = 0; l < Ls; ++l) {
     fa.R[l] = ctx->radius[l];
     fa.x_x0[l] = ctx->x_x0[l];
   }
   fa.mass = ctx->mass;
-  e = launch_fit_fused(fa, s);
-  if (e != cudaSuccess) return e;
-  // hits into eta x phi bins, one segment per build layer
-  BinArgs hb;
-  hb.xyz = reinterpret_cast<const float*>(d + L.d_xyz);
-  hb.stride = L.nh;
-  hb.seg_off = reinterpret_cast<const int64_t*>(d + L.d_segoff);
-  hb.bin_off = reinterpret_cast<int32_t*>(d + L.d_boff);
-  hb.out_pts = reinterpret_cast<float4*>(d + L.d_bhits);
-  hb.out_id = reinterpret_cast<int32_t*>(d + L.d_bid);
-  hb.out_seg = nullptr;
-  hb.cursor = reinterpret_cast<int32_t*>(d + L.d_bcur);
-  hb.unordered = 1;  // the build's results do not depend on the order inside a bin
-  e = launch_bin_points(hb, L.Lb, s);
+  e = launch_fit_fused_table(fa, df, int(rs.size()), tracks, s);
+  // the build's results do not depend on the order of the hits inside a bin
+  if (e == cudaSuccess) e = launch_bin_segment_table(db, segs, s);
   if (e != cudaSuccess) return e;
   // (a register-resident build takes the seeds in their order, from the fit)
-  if (sv->tune.build_scan == 4) return cudaEventRecord(r->prepped, s);
-  // seeds in (eta, phi) order: one segment [0, n) (copied with the layer offsets)
-  BinArgs sb;
-  sb.xyz = reinterpret_cast<const float*>(d + L.d_fpar);
-  sb.stride = n;
-  sb.seg_off = reinterpret_cast<const int64_t*>(d + L.d_sseg);
-  sb.bin_off = reinterpret_cast<int32_t*>(d + L.d_sboff);
-  sb.out_pts = nullptr;
-  sb.out_id = reinterpret_cast<int32_t*>(d + L.d_perm);
-  sb.out_seg = nullptr;
-  sb.cursor = reinterpret_cast<int32_t*>(d + L.d_bcur);
-  sb.unordered = 1;  // the build's results do not depend on the order inside a bin
-  e = launch_bin_points(sb, 1, s);
-  if (e != cudaSuccess) return e;
-  BuildInitArgs ia;
-  ia.out = cand_at(d + L.d_candA, n);
-  ia.par = reinterpret_cast<const float*>(d + L.d_fpar);
-  ia.lo = reinterpret_cast<const float*>(d + L.d_flo);
-  ia.cov = reinterpret_cast<const float*>(d + L.d_fcov);
-  ia.seed_perm = reinterpret_cast<const int32_t*>(d + L.d_perm);
-  ia.n = n;
-  ia.S = n;
-  e = launch_build_init(ia, s);
-  if (e != cudaSuccess) return e;
-  return cudaEventRecord(r->prepped, s);
+  for (size_t k = 0; k < rs.size() && sv->tune.build_scan != 4; ++k) {
+    Request* r = rs[k];
+    const EventLayout& L = r->lay;
+    char* d = sv->dmem + r->d_off;
+    const int64_t n = L.n;
+    // seeds in (eta, phi) order: one segment [0, n) (copied with the layer offsets)
+    BinArgs sb;
+    sb.xyz = reinterpret_cast<const float*>(d + L.d_fpar);
+    sb.stride = n;
+    sb.seg_off = reinterpret_cast<const int64_t*>(d + L.d_sseg);
+    sb.bin_off = reinterpret_cast<int32_t*>(d + L.d_sboff);
+    sb.out_pts = nullptr;
+    sb.out_id = reinterpret_cast<int32_t*>(d + L.d_perm);
+    sb.out_seg = nullptr;
+    sb.cursor = reinterpret_cast<int32_t*>(d + L.d_bcur);
+    sb.unordered = 1;  // the build's results do not depend on the order inside a bin
+    e = launch_bin_points(sb, 1, s);
+    if (e != cudaSuccess) return e;
+    BuildInitArgs ia;
+    ia.out = cand_at(d + L.d_candA, n);
+    ia.par = reinterpret_cast<const float*>(d + L.d_fpar);
+    ia.lo = reinterpret_cast<const float*>(d + L.d_flo);
+    ia.cov = reinterpret_cast<const float*>(d + L.d_fcov);
+    ia.seed_perm = reinterpret_cast<const int32_t*>(d + L.d_perm);
+    ia.n = n;
+    ia.S = n;
+    e = launch_build_init(ia, s);
+    if (e != cudaSuccess) return e;
+  }
+  e = cudaEventRecord(sv->prep_ev[slot], s);
+  for (Request* r : rs) {
+    if (e == cudaSuccess) e = cudaEventRecord(r->prepped, s);
+    sv->prep_order[ps].push_back(r);
+  }
+  return e;
 }
 
 static BuildSlot slot_of(Serve* sv, Request* r) {
@@ -687,8 +738,7 @@ static void scheduler(Serve* sv) {
     }
     // ---- device work of this iteration (serve stream, no lock held)
     cudaError_t e = cudaSuccess;
-    for (Request* r : admitted)
-      if (e == cudaSuccess) e = prepare(sv, r);
+    e = prepare_batch(sv, admitted);
     // pace: at most kInflight iterations ahead of the GPU
     const int ring = int(iter % kRing);
     if (e == cudaSuccess && iter >= uint64_t(kInflight)) {
@@ -866,6 +916,8 @@ void kf_serve_shutdown_internal(kf_ctx* ctx) {
     if (sv->iter_ev[i]) cudaEventDestroy(sv->iter_ev[i]);
     if (sv->step_ev[i]) cudaEventDestroy(sv->step_ev[i]);
   }
+  for (cudaEvent_t pe : sv->prep_ev)
+    if (pe) cudaEventDestroy(pe);
   if (sv->dmem) cudaFree(sv->dmem);
   if (sv->d_table) cudaFree(sv->d_table);
   if (sv->hmem) cudaFreeHost(sv->hmem);
@@ -901,10 +953,11 @@ int kf_serve_start(kf_ctx* ctx, const kf_serve_config* cfg) {
   int rc = KF_OK;
   if (ctx->budget && ctx->allocated + dbytes > ctx->budget) rc = KF_ENOMEM;
   if (!rc && cudaMalloc(&sv->dmem, dbytes) != cudaSuccess) rc = KF_ENOMEM;
-  if (!rc && cudaMalloc(&sv->d_table, kTableBytes * kRing) != cudaSuccess) rc = KF_ENOMEM;
+  const size_t table_bytes = kTableBytes * kRing + kPrepBytes * kPrepRing;
+  if (!rc && cudaMalloc(&sv->d_table, table_bytes) != cudaSuccess) rc = KF_ENOMEM;
   if (!rc && cudaHostAlloc(reinterpret_cast<void**>(&sv->hmem), hbytes, cudaHostAllocDefault) != cudaSuccess)
     rc = KF_ENOMEM;
-  if (!rc && cudaHostAlloc(reinterpret_cast<void**>(&sv->h_table), kTableBytes * kRing, cudaHostAllocDefault) != cudaSuccess)
+  if (!rc && cudaHostAlloc(reinterpret_cast<void**>(&sv->h_table), table_bytes, cudaHostAllocDefault) != cudaSuccess)
     rc = KF_ENOMEM;
   if (!rc && cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking) != cudaSuccess) rc = KF_ECUDA;
   if (!rc && cudaStreamCreateWithFlags(&sv->finish_stream, cudaStreamNonBlocking) != cudaSuccess) rc = KF_ECUDA;
@@ -914,6 +967,8 @@ int kf_serve_start(kf_ctx* ctx, const kf_serve_config* cfg) {
     if (cudaEventCreateWithFlags(&sv->iter_ev[i], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&sv->step_ev[i], cudaEventDisableTiming) != cudaSuccess)
       rc = KF_ECUDA;
+  for (int i = 0; i < kPrepRing && !rc; ++i)
+    if (cudaEventCreateWithFlags(&sv->prep_ev[i], cudaEventDisableTiming) != cudaSuccess) rc = KF_ECUDA;
   if (rc) {
     cudaGetLastError();
     if (sv->dmem) cudaFree(sv->dmem);
@@ -928,6 +983,8 @@ int kf_serve_start(kf_ctx* ctx, const kf_serve_config* cfg) {
       if (sv->iter_ev[i]) cudaEventDestroy(sv->iter_ev[i]);
       if (sv->step_ev[i]) cudaEventDestroy(sv->step_ev[i]);
     }
+    for (cudaEvent_t pe : sv->prep_ev)
+      if (pe) cudaEventDestroy(pe);
     delete sv;
     return rc;
   }
