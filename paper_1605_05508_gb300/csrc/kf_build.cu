@@ -903,17 +903,19 @@ __global__ void __launch_bounds__(NT, kBuildBlocksPerSM * kBuildThreads / NT) bu
 // The same computation per candidate as the other layouts, organised so that
 // a candidate's state never leaves the registers between layers and no
 // block-wide barrier is needed.  A warp takes a group of G = 32 / W seeds
-// (consecutive in (eta, phi) order, so their windows share cached bins and
-// hits); lane k of a seed's W lanes holds the seed's candidate of rank k.  Per
-// building layer, every live lane propagates its candidate, derives the window
-// and scans it (scan_window) into a sorted list of its best children's keys;
+// (consecutive in the order given; the warps of the GPU work on a narrow
+// band of seeds, whose events' hits stay in L2); lane k of a seed's W lanes
+// holds the seed's candidate of rank k.  Per building layer, every live lane
+// propagates its candidate, derives the window and scans it into a sorted
+// list of its best children's keys;
 // the seed's lanes merge their lists by a minimum over the seed's lanes of the
 // 64-bit keys (full-warp shuffles rotating within each seed's lanes) into
 // the seed's best max_cands, ranked by the same total order; lane k then
 // pulls the predicted state and S^-1 of its winner's parent from that lane by
 // shuffles and applies the Kalman update with the winner's hit.  Only the
-// per-layer history (parent rank, hit id) goes to memory until the last
-// layer, whose candidates are written to the final buffer.  Groups are
+// per-layer history (parent rank, hit id) goes to memory; after the last
+// layer the best candidates are written to the caller's result (or every
+// candidate to the last buffer, for a final selection).  Groups are
 // independent, so warps run at their own pace (no block barrier).  The keys
 // are a total order and every candidate goes through the same functions as in
 // the other layouts, so the results are bitwise theirs.
