@@ -600,6 +600,27 @@ def build_kernel_name(t, max_cands):
     return f"build_step_kernel<{t['build_hit_tile']}, {lw}, {int(scan == 1)}>"
 
 
+def build_step_launches(tune, Lb, max_cands, seed_layers=3):
+    """Kernel launches of one build step: the seed fit (one per seeding layer),
+    the hit binning (one launch unordered, else count, scan, scatter, sort) and
+    kf_build -- register-resident: the seeds' events, the first layer (with
+    more than one lane a seed), the other layers, the final pass; else the seed
+    ordering (count, scan, scatter), global ids, first candidates, the layer
+    steps and the final selection."""
+    binning = 1 if tune.get("bin_unordered") else 4
+    if tune["build_scan"] == 4:
+        lanes = max_cands if max_cands <= 2 else 4 if max_cands <= 4 else 6 if max_cands <= 6 else 8
+        build = 1 + (1 if lanes > 1 and Lb > 1 else 0) + 1 + 1
+    else:
+        steps = Lb
+        if tune["build_scan"] in (2, 3):  # packed: one launch per layer up to the layout switch, then one
+            rm = Lb + 1 if max_cands <= 2 else 2
+            first_fused = 0 if rm > Lb else min(Lb, rm)
+            steps = first_fused + 1 if first_fused < Lb else Lb
+        build = 3 + 1 + 1 + steps + 1
+    return seed_layers + binning + build
+
+
 def build_leg(a, kf, torch, dev, stream, rank, world, dist, peaks=None):
     """Combinatorial build (clone engine, N = 6; and best-hit N = 1) on
     `build_events` events x `build_seeds` seeds with 3x noise hits per layer,
@@ -784,9 +805,7 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist, peaks=None):
            "plain_f64": plain_f64,
            "clone_engine_curve": {"seeds": SEED_READING, "points": curve},
            "bin_order": "scatter order inside each bin (bin_unordered 1; the build's results are the same bits)",
-           # seed fit (3 layer launches) + hit binning (count, scan, scatter) + kf_build (seed
-           # binning: count, scan, scatter, sort; seed ids; initial candidates; Lb steps; final)
-           "gpu_launches_per_step": 3 + 3 + (4 + 1 + 1 + Lb + 1)}
+           "gpu_launches_per_step": build_step_launches(tune6, Lb, 6)}
     # roofline of the build by the method's bytes: per seed and layer ~6 parents
     # read (112 B of state each), ~6 children written (112 B + a 4 B hit id) and
     # the hits of their windows, ~1.4 kB; over the build phase's CUDA-event time
