@@ -809,7 +809,8 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist, peaks=None):
     # roofline of the build by the method's bytes: per seed and layer ~6 parents
     # read (112 B of state each), ~6 children written (112 B + a 4 B hit id) and
     # the hits of their windows, ~1.4 kB; over the build phase's CUDA-event time
-    # (seed ordering, initialisation and final selection included)
+    # (every launch of kf_build included: the seeds' events or ordering, the
+    # layers, the final pass)
     peak_hbm, peak_kind = measured_peaks()
     t_build = float(t6[2]) / 1e3
     ach = BUILD_METHOD_BYTES_PER_SEED_LAYER * n * Lb / t_build / 1e9
