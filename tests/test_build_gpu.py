@@ -324,3 +324,58 @@ def test_packed_layers_in_one_launch_match_with_skewed_blocks(cuda_ctx_factory):
                 np.testing.assert_array_equal(g[key], res[0][key], err_msg=f"layout {layout} {key}")
         res[layout] = g
     kf.kf_set_tuning(ctx, 128, 0, 8, 0)
+
+
+def _first_layer_only(batch):
+    """The batch with its first building layer alone (hits and offsets cut)."""
+    Lb = len(batch.build_layers)
+    keep = np.zeros(batch.layer_xyz.shape[1], dtype=bool)
+    counts = []
+    for e in range(batch.n_events):
+        lo, hi = batch.layer_off[e * Lb], batch.layer_off[e * Lb + 1]
+        keep[lo:hi] = True
+        counts.append(hi - lo)
+    batch.layer_xyz = np.ascontiguousarray(batch.layer_xyz[:, keep])
+    batch.layer_off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    batch.build_layers = batch.build_layers[:1]
+    return batch
+
+
+def _without_event_hits(batch, ev):
+    """The batch with every building-layer hit of event ev removed."""
+    Lb = len(batch.build_layers)
+    keep = np.ones(batch.layer_xyz.shape[1], dtype=bool)
+    offs = batch.layer_off
+    keep[offs[ev * Lb]:offs[(ev + 1) * Lb]] = False
+    counts = [0 if s // Lb == ev else offs[s + 1] - offs[s] for s in range(batch.n_events * Lb)]
+    batch.layer_xyz = np.ascontiguousarray(batch.layer_xyz[:, keep])
+    batch.layer_off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    return batch
+
+
+def test_resident_layout_edge_cases(cuda_ctx_factory):
+    """The register-resident layout (a first-layer launch with more than one
+    lane a seed, the seeds in their given order, the best candidates written
+    from the registers) on its edge cases -- a single building layer (no
+    first-layer launch), an event without hits, a batch of 7 seeds, N = 1, 3, 6
+    and 8: every result and candidate summary bitwise that of the grouped
+    per-lane layout, which the oracle checks at N = 6."""
+    from paper_1605_05508_gb300 import kf
+    det = S.barrel()
+    ctx = cuda_ctx_factory(det.radii, max_cands=8)
+    cases = {"one layer": _first_layer_only(S.make_build_batch(2101, 2, 300)),
+             "no hits in event 1": _without_event_hits(S.make_build_batch(2102, 3, 200), 1),
+             "7 seeds": S.make_build_batch(2103, 1, 7)}
+    for name, batch in cases.items():
+        for N in (1, 3, 6, 8):
+            kf.kf_set_tuning(ctx, 128, 0, 8, 0)
+            ref = gpu_build(ctx, batch, N)
+            if N == 6:
+                _check_build(batch, ref, oracle_build(batch, 6), label=name)
+            kf.kf_set_tuning(ctx, 128, 0, 8, 4)
+            g = gpu_build(ctx, batch, N)
+            for k in ("par", "cov", "chi2", "nhits", "status", "hits", "n_cands", "cand_hits", "cand_chi2",
+                      "cand_nhits"):
+                if k in ref:
+                    np.testing.assert_array_equal(g[k], ref[k], err_msg=f"{name} N={N} {k}")
+    kf.kf_set_tuning(ctx, 128, 0, 8, 0)
