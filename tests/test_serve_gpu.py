@@ -207,3 +207,35 @@ def test_native_driver_serves_every_request(tmp_path):
         assert r["requests"] == 24 and r["events_per_s"] > 0, r
         assert 0 < r["p50_ms"] <= r["p99_ms"], r
         assert r["max_resident"] >= 1 and r["step_launches"] >= (7 if scan == 2 else 1), r
+
+
+@pytest.mark.parametrize("n_build,max_cands", [(1, 6), (7, 1), (7, 3)])
+def test_register_resident_serving_without_a_split_and_narrow(cuda_ctx_factory, n_build, max_cands):
+    """Serving with the register-resident layout where it runs a single launch
+    per iteration (one building layer, or one lane a seed at N = 1) and with
+    W = 4 lanes (N = 3): each event's results are bitwise the batch build's."""
+    from paper_1605_05508_gb300 import kf
+    from test_build_gpu import _first_layer_only
+    det = S.barrel()
+    ctx = cuda_ctx_factory(det.radii, max_cands=8)
+    evs = []
+    for i, n in enumerate((400, 1500, 90)):
+        b = S.make_build_batch(700 + i, 1, n)
+        if n_build == 1:
+            b = _first_layer_only(b)
+        evs.append((b, dict(seed_par=b.seeds.par, seed_cov=b.seeds.cov, seed_charge=b.seeds.charge,
+                            seed_hits=b.fit_hits.xyz, seed_valid=b.fit_hits.valid, layer_xyz=b.layer_xyz,
+                            layer_off=b.layer_off)))
+    kf.kf_set_tuning(ctx, 128, 0, 8, 4)
+    kf.kf_serve_start(ctx, 3, n_build, max_cands, max_slots=8, device_arena_bytes=1 << 28,
+                      host_arena_bytes=1 << 27)
+    tickets = [kf.kf_submit(ctx, ev) for _, ev in evs]
+    served = [kf.kf_poll(ctx, t, b.seeds.par.shape[1], n_build, 60_000_000) for t, (b, _) in zip(tickets, evs)]
+    kf.kf_serve_stop(ctx)
+    kf.kf_set_tuning(ctx, 128, 0, 8, 0)
+    for (b, _), a in zip(evs, served):
+        g = gpu_build(ctx, b, max_cands, want_cands=False)
+        np.testing.assert_array_equal(g["hits"].T, a["hit_idx"])
+        np.testing.assert_array_equal(g["nhits"], a["n_hits"])
+        np.testing.assert_array_equal(g["status"], a["status"])
+        np.testing.assert_array_equal(g["chi2"].astype(np.float32), a["chi2_tot"])
