@@ -473,6 +473,20 @@ int kf_serve_stop(kf_ctx *ctx);
  * Errors: KF_EINVAL (null context, skip_tile < -1). */
 int kf_test_stage_fault(kf_ctx *ctx, int64_t skip_tile, uint32_t wait_polls);
 
+/* Test hook for the bounded waits of kf_build's hit staging (kf_tuning
+ * build_hit_tile > 0, grouped layouts 0 and 1).  The paper has no
+ * counterpart.  After this call, in every layer-step launch of kf_build on
+ * this context the warp of index `skip_warp` in the launch (seeds 4 skip_warp
+ * .. 4 skip_warp + 3 in the build's seed order; -1 = none) issues none of the
+ * copies of its window's hits and arms nothing, so its wait for them runs out:
+ * those seeds' candidates stop with KF_ST_DEVICE_TIMEOUT (a warp whose
+ * window does not fit its tile scans global memory and waits for nothing);
+ * every other seed's results are unchanged.  `wait_polls` bounds each wait for
+ * staged hits (0 = the normal limit); the drain before a warp ends waits only
+ * for copies actually issued.  Errors: KF_EINVAL (null context,
+ * skip_warp < -1). */
+int kf_test_build_stage_fault(kf_ctx *ctx, int64_t skip_warp, uint32_t wait_polls);
+
 /* ---------------------------------------------------------------------------
  * Measured arithmetic peaks: the roofline denominators of the kernels bound by
  * arithmetic.  The paper has no counterpart (it measures on CPUs).  Runs a

@@ -274,6 +274,7 @@ __global__ void __launch_bounds__(kBuildThreads, kBuildBlocksPerSM) build_step_k
 
   // ---- warp union of the windows and staging (TILE > 0)
   bool staged = false, timed_out = false;
+  bool armed = false;  // (lane 0) copies issued into this warp's tile
   int emin = 0, hs0a = 0, hs1a = KF_BIN_PHI - 1, hs1b = -1;
   if constexpr (TILE > 0) {
     // phi unwrapped around the bin of the warp's first seed; any reference is
@@ -329,7 +330,12 @@ __global__ void __launch_bounds__(kBuildThreads, kBuildBlocksPerSM) build_step_k
             if (len >= 2) nh_tot += s_off[ob + len - 1] - s_off[ob];
           }
           int st_flag = nh_tot <= TILE ? 1 : 0;
-          if (st_flag && nh_tot > 0) {
+          // test hook: this warp issues nothing, so its wait below runs out
+          const bool skip = (int64_t(blockIdx.x) * kBuildThreads + threadIdx.x) / 32 == Args.test_skip_warp;
+          if (st_flag && nh_tot > 0 && skip) {
+            st_flag = 2;
+          } else if (st_flag && nh_tot > 0) {
+            armed = true;
             mbar_arrive_expect_tx(s_bar, uint32_t(nh_tot) * uint32_t(sizeof(float4)));
             for (int q = 0; q < 2 * nrows; ++q) {
               const int len = (q & 1) ? lenb : lena;
@@ -345,7 +351,8 @@ __global__ void __launch_bounds__(kBuildThreads, kBuildBlocksPerSM) build_step_k
         __syncwarp();
         const int flag = s_stage_all[warp];
         staged = flag != 0;
-        if (flag == 2 && !mbar_wait_bounded(s_bar, 0, kBuildWaitLimit)) {
+        const uint32_t limit = Args.test_wait_limit ? Args.test_wait_limit : kBuildWaitLimit;
+        if (flag == 2 && !mbar_wait_bounded(s_bar, 0, limit)) {
           // a copy did not complete: stop the warp's candidates with the error bit
           st |= KF_ST_DEVICE_TIMEOUT;
           stopped = true;
@@ -483,7 +490,9 @@ __global__ void __launch_bounds__(kBuildThreads, kBuildBlocksPerSM) build_step_k
     // no compatible hit (or a stopped candidate): one child without a hit
     if (active && !any_mine) list_insert(L, P, make_key(nh, chi2tot, k, 0), -1);
   }
-  if (TILE > 0 && timed_out && lane == 0) mbar_wait_bounded(s_bar, 0, kBuildWaitLimit);  // nothing in flight at exit
+  // nothing in flight at exit: after a timeout, lane 0 waits (bounded) for the
+  // copies it issued, if it issued any
+  if (TILE > 0 && timed_out && lane == 0 && armed) mbar_wait_bounded(s_bar, 0, kBuildWaitLimit);
 
   // ---- clone engine: merge the group's lists into the best max_cands
   uint64_t my_key = kNoKey;
@@ -1756,6 +1765,8 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
     a.slots = dtable + l;
     a.n_slots = 1;
     a.layers = fused ? L - l : 0;
+    a.test_skip_warp = ctx->test_build_skip_warp;
+    a.test_wait_limit = ctx->test_build_wait_polls;
     a.max_cands = max_cands;
     a.a_scale = float(kCLight * double(ctx->cfg.bz_tesla));
     a.v0 = v0;

@@ -72,6 +72,12 @@ struct BuildStepArgs {
   int pack_seeds;        // candidate-packed layouts: seeds per block (<= the block's threads; 0: as many)
   int layers;            // candidate-packed layouts: > 1 = `slots` are that many consecutive layers of
                          // one batch and each block takes its seeds through all of them
+  // test hook (kf_test_build_stage_fault), grouped layouts with hit staging:
+  // the warp of this index in the launch issues no copies and arms nothing,
+  // and the waits for staged hits give up after test_wait_limit polls (0: the
+  // normal limit)
+  int64_t test_skip_warp = -1;
+  uint32_t test_wait_limit = 0;
 };
 
 struct BuildInitArgs {

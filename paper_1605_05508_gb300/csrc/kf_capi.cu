@@ -87,6 +87,13 @@ int kf_test_stage_fault(kf_ctx* ctx, int64_t skip_tile, uint32_t wait_polls) {
   return KF_OK;
 }
 
+int kf_test_build_stage_fault(kf_ctx* ctx, int64_t skip_warp, uint32_t wait_polls) {
+  if (!ctx || skip_warp < -1) return KF_EINVAL;
+  ctx->test_build_skip_warp = skip_warp;
+  ctx->test_build_wait_polls = wait_polls;
+  return KF_OK;
+}
+
 int kf_create(kf_ctx** out, const kf_config* cfg, int device, size_t mem_budget_bytes) {
   if (!out || !cfg) return KF_EINVAL;
   *out = nullptr;

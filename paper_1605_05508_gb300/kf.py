@@ -146,6 +146,7 @@ def lib() -> C.CDLL:
                                       vp, vp, vp, C.POINTER(kf_tuning)]
         L.kf_measure_peak.argtypes = [vp, i32, vp, C.POINTER(C.c_double)]
         L.kf_test_stage_fault.argtypes = [vp, i64, C.c_uint32]
+        L.kf_test_build_stage_fault.argtypes = [vp, i64, C.c_uint32]
         L.kf_autotune_build.argtypes = [vp, C.POINTER(kf_tracks), vp, C.POINTER(kf_layer_hit_bins), i32,
                                         C.POINTER(kf_build_result), vp, C.POINTER(kf_tuning)]
         _lib = L
@@ -431,6 +432,12 @@ def kf_autotune_build(ctx, seeds: Tracks, seed_off, bins: HitBins, max_cands: in
 def kf_test_stage_fault(ctx, skip_tile: int = -1, wait_polls: int = 0):
     """Test hook of the staged fit kernel's bounded waits (see kf.h)."""
     _check(lib().kf_test_stage_fault(_h(ctx), int(skip_tile), int(wait_polls)), "kf_test_stage_fault", _h(ctx))
+
+
+def kf_test_build_stage_fault(ctx, skip_warp: int = -1, wait_polls: int = 0):
+    """Test hook of the build's hit-staging waits (see kf.h)."""
+    _check(lib().kf_test_build_stage_fault(_h(ctx), int(skip_warp), int(wait_polls)), "kf_test_build_stage_fault",
+           _h(ctx))
 
 
 # --------------------------------------------------------------------------- measured peaks

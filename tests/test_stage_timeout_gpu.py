@@ -1,11 +1,12 @@
-"""The bounded waits of the staged fit layer kernel, made to run out without
-any GPU fault: the test hook kf_test_stage_fault keeps the copies of one
-32-track tile from being issued, so the warp owning that tile waits for
-nothing until its poll limit.  The kernel must then mark exactly the tracks it
-could not fit with KF_ST_DEVICE_TIMEOUT (that tile, and the warp's later tiles
-of the same launch), drain only the copies it really issued, and leave every
-other track's results bit for bit as without the fault; the context stays
-usable, and clearing the hook restores the plain result."""
+"""The bounded waits of the staged fit layer kernel and of the build's hit
+staging, made to run out without any GPU fault: the test hooks
+kf_test_stage_fault / kf_test_build_stage_fault keep the copies of one
+32-track tile (fit) or of one warp's window hits (build) from being issued,
+so the warp waits for nothing until its poll limit.  The kernel must then
+mark exactly the tracks or seeds it could not process with
+KF_ST_DEVICE_TIMEOUT, drain only the copies it really issued, and leave every
+other result bit for bit as without the fault; the context stays usable, and
+clearing the hook restores the plain result."""
 import numpy as np
 import pytest
 
@@ -61,4 +62,35 @@ def test_stage_wait_runs_out_and_marks_only_its_tracks(cuda_ctx_factory, n_tiles
     again = _fit(ctx, kf, ev)
     for a, b in zip(again, ref):
         np.testing.assert_array_equal(a, b)
+    kf.kf_set_tuning(ctx, 128, 0, 8, 0)
+
+
+@pytest.mark.parametrize("skip", [3, 40])
+def test_build_stage_wait_runs_out_and_marks_only_its_seeds(cuda_ctx_factory, skip):
+    """kf_build's hit staging (tile 512, grouped per-lane layout): the test hook
+    kf_test_build_stage_fault keeps one warp of every layer step from issuing
+    its copies, so that warp's wait for its staged hits runs out on the first
+    layer where it stages.  Exactly its seeds (four at most) stop with
+    KF_ST_DEVICE_TIMEOUT; every other seed's results are bit for bit those
+    without the hook; the context stays usable and, the hook cleared, gives
+    the plain results again."""
+    from buildutil import gpu_build
+    from paper_1605_05508_gb300 import kf
+    det = S.barrel()
+    ctx = cuda_ctx_factory(det.radii)
+    batch = S.make_build_batch(5150 + skip, 2, 400)
+    kf.kf_set_tuning(ctx, 128, 512, 8, 0)
+    keys = ("par", "chi2", "nhits", "status", "hits")
+    ref = gpu_build(ctx, batch, 6, want_cands=False)
+    assert not np.any(ref["status"] & kf.ST_DEVICE_TIMEOUT)
+    kf.kf_test_build_stage_fault(ctx, skip, WAIT_POLLS)
+    got = gpu_build(ctx, batch, 6, want_cands=False)
+    kf.kf_test_build_stage_fault(ctx, -1, 0)
+    hit = (got["status"] & kf.ST_DEVICE_TIMEOUT) != 0
+    assert 1 <= hit.sum() <= 4, hit.sum()
+    for k in keys:
+        np.testing.assert_array_equal(got[k][~hit], ref[k][~hit], err_msg=k)
+    again = gpu_build(ctx, batch, 6, want_cands=False)
+    for k in keys:
+        np.testing.assert_array_equal(again[k], ref[k], err_msg=k)
     kf.kf_set_tuning(ctx, 128, 0, 8, 0)
