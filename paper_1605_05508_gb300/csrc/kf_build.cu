@@ -1027,10 +1027,17 @@ __global__ void __launch_bounds__(kResThreads, resident_blocks_per_sm(W))
   // the seed's lanes (none for lanes past G * W)
   const unsigned seg = g < G ? ((1u << W) - 1u) << (g * W) : 0u;
   const int64_t n_groups = TABLE ? A.n_groups : (A.one.S + G - 1) / G;
-  const int64_t n_warps = (int64_t(gridDim.x) * kResThreads) >> 5;
-  // groups dealt out with a grid stride: at any moment the warps of the GPU
-  // work on a narrow band of seeds (a few events), whose hits stay in L2
-  for (int64_t gi = (int64_t(blockIdx.x) * kResThreads + threadIdx.x) >> 5; gi < n_groups; gi += n_warps) {
+  // groups dealt out in order, each warp fetching its next one from a
+  // counter: at any moment the warps of the GPU work on a narrow band of
+  // seeds (a few events), whose hits stay in L2, and a warp whose groups
+  // happened to be cheap takes more (measured: 2 % faster at N = 6, 6 % at
+  // N = 1 than a fixed grid stride)
+  auto next_group = [&]() {
+    unsigned long long v = 0;
+    if (lane == 0) v = atomicAdd(A.group_counter, 1ull);
+    return int64_t(__shfl_sync(kFull, v, 0));
+  };
+  for (int64_t gi = next_group(); gi < n_groups; gi = next_group()) {
     int q = 0;  // the batch of this group (a served event), with a table
     if constexpr (TABLE)
       while (q + 1 < A.n_batches && A.table[q + 1].group_begin <= gi) ++q;
@@ -1590,7 +1597,8 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
   const size_t b_tab = al256(sizeof(BuildSlot) * size_t(L));
   const int64_t E = bins->n_events;
   const size_t b_sbin = al256(size_t(E) * (KF_NBINS + 1) * 4), b_scur = al256(size_t(E) * KF_NBINS * 4);
-  const size_t total = b_perm + b_evt + 2 * b_cand + b_hp + b_hh + b_tab + b_sbin + b_scur;
+  const size_t b_ctr = 256;  // the resident build's group counter
+  const size_t total = b_perm + b_evt + 2 * b_cand + b_hp + b_hh + b_tab + b_sbin + b_scur + b_ctr;
   int rc = scratch_reserve(ctx, ctx->s_build, total);
   if (rc) return rc;
   char* base = static_cast<char*>(ctx->s_build.ptr);
@@ -1740,6 +1748,8 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
     // all but the paths and the covariance check: those follow, one thread
     // a seed
     ra.one.res = *out;
+    ra.group_counter = reinterpret_cast<unsigned long long*>(base + total - b_ctr);
+    KF_CUDA_TRY(ctx, cudaMemsetAsync(ra.group_counter, 0, sizeof(unsigned long long), s));
     KF_CUDA_TRY(ctx, launch_build_resident(ra, ctx->num_sms, s));
     BuildFinalArgs fa;
     fa.cand = ra.one.out;

@@ -198,6 +198,9 @@ struct BuildResidentArgs {
   float a_scale, v0, v1, v2, cut, mass;
   float R[kMaxLayers];     // building layer radii
   float x_x0[kMaxLayers];  // building layer thickness in radiation lengths (0: none)
+  // device counter, zero at launch: the warps fetch their next seed group
+  // from it (build_resident_kernel)
+  unsigned long long* group_counter;
 };
 // Lanes per seed of the resident layout for max_cands (1, 2, 4, 6 or 8).
 inline int resident_lanes(int max_cands) {

@@ -300,6 +300,7 @@ constexpr size_t kTableBytes = std::max(sizeof(BuildSlot), 2 * sizeof(ResidentBa
 constexpr int kPrepRing = 8;
 constexpr size_t kPrepFitBytes = sizeof(FitEvent) * KF_MAX_SLOTS;
 constexpr size_t kPrepBytes = kPrepFitBytes + sizeof(BinSegment) * KF_MAX_SLOTS * kMaxLayers;
+constexpr size_t kCounterBytes = 256;
 
 // With more than one lane a seed, a register-resident build runs its first
 // layer (one candidate a seed) with one thread per seed, seeds -> buffer B,
@@ -332,7 +333,8 @@ struct Serve {
   char* dmem = nullptr;
   char* hmem = nullptr;
   Arena darena, harena;
-  char* d_table = nullptr;  // [kRing] entries of kTableBytes, then [kPrepRing] of kPrepBytes
+  char* d_table = nullptr;  // [kRing] entries of kTableBytes, then [kPrepRing] of kPrepBytes, then
+                            // [kRing] resident-build group counters of kCounterBytes
   char* h_table = nullptr;  // pinned, same shape
   cudaEvent_t prep_ev[kPrepRing] = {};  // after the batch that last used a preparation table slot
   int prep_slot = 0;
@@ -805,6 +807,9 @@ static void scheduler(Serve* sv) {
       }
       ra.table = dt;
       ra.n_groups = groups;
+      ra.group_counter = reinterpret_cast<unsigned long long*>(sv->d_table + kTableBytes * kRing +
+                                                               kPrepBytes * kPrepRing + kCounterBytes * ring);
+      if (e == cudaSuccess) e = cudaMemsetAsync(ra.group_counter, 0, sizeof(unsigned long long), sv->stream);
       ra.l0 = split ? 1 : 0;
       ra.in_rm = ra.l0 < ra.rm_buffers;
       ra.out_rm = Lb < ra.rm_buffers;
@@ -953,7 +958,7 @@ int kf_serve_start(kf_ctx* ctx, const kf_serve_config* cfg) {
   int rc = KF_OK;
   if (ctx->budget && ctx->allocated + dbytes > ctx->budget) rc = KF_ENOMEM;
   if (!rc && cudaMalloc(&sv->dmem, dbytes) != cudaSuccess) rc = KF_ENOMEM;
-  const size_t table_bytes = kTableBytes * kRing + kPrepBytes * kPrepRing;
+  const size_t table_bytes = kTableBytes * kRing + kPrepBytes * kPrepRing + kCounterBytes * kRing;
   if (!rc && cudaMalloc(&sv->d_table, table_bytes) != cudaSuccess) rc = KF_ENOMEM;
   if (!rc && cudaHostAlloc(reinterpret_cast<void**>(&sv->hmem), hbytes, cudaHostAllocDefault) != cudaSuccess)
     rc = KF_ENOMEM;
