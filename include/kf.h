@@ -311,19 +311,22 @@ typedef struct {
     int32_t build_list_width; /* entries of a lane's child list in the kf_build step: 4 or 8
                                  (default 8); 4 takes effect only when max_cands <= 4 */
     int32_t build_scan;       /* thread layout of the kf_build step: 0 = 8 lanes per seed, each
-                                 scanning its own candidate's window (default), 1 = 8 lanes per
-                                 seed scanning each parent's window together (balanced when few
+                                 scanning its own candidate's window, 1 = 8 lanes per seed
+                                 scanning each parent's window together (balanced when few
                                  candidates), 2 = the live candidates packed onto consecutive
                                  threads for the propagation and scan, and the kept children
                                  for the update, 128 seeds per block; 3 = the same with 64
-                                 seeds per block; 4 = register-resident: each warp takes
-                                 groups of 32 / W seeds (W = max_cands rounded up to 1, 2, 4,
-                                 6 or 8 lanes a seed) through all building layers in one
-                                 launch, the candidates' states in registers between layers
-                                 (2, 3 and 4 require build_hit_tile 0; a serving loop with 4
-                                 builds each prepared event through all its layers in one
-                                 resident launch shared with the events prepared with it, and
-                                 with 0 .. 3 steps all resident events one layer a launch) */
+                                 seeds per block; 4 = register-resident (default): each warp
+                                 takes groups of 32 / W seeds (W = max_cands rounded up to 1,
+                                 2, 4, 6 or 8 lanes a seed, the groups fetched in order from a
+                                 counter) through the building layers, the candidates' states
+                                 in registers between layers, in two launches when W > 1 (the
+                                 first layer with one thread per seed, then the others) and
+                                 the best candidates written after the last layer (2, 3 and 4
+                                 require build_hit_tile 0; a serving loop with 4 builds each
+                                 prepared event through all its layers in the launches shared
+                                 with the events prepared with it, and with 0 .. 3 steps all
+                                 resident events one layer a launch) */
     int32_t fit_chunk;        /* kf_fit: 0 = each layer step is one launch over the whole batch
                                  (default); 262144, 524288 or 1048576 = the batch is fitted in
                                  chunks of that many tracks, all layers of a chunk before the

@@ -61,7 +61,7 @@ struct kf_ctx {
   cudaStream_t host_streams[kfi::kHostStreams] = {};  // kf_fit_host pipeline
   cudaEvent_t host_done[kfi::kHostStreams] = {};
   cudaEvent_t host_start = nullptr;
-  kf_tuning tune = {128, 0, 8, 0, 0, 0, 0};  // launch parameters (kf_set_tuning, kf_autotune_*)
+  kf_tuning tune = {128, 0, 8, 4, 0, 0, 0};  // launch parameters (kf_set_tuning, kf_autotune_*)
   int64_t test_skip_tile = -1;   // kf_test_stage_fault
   uint32_t test_wait_polls = 0;
   int64_t test_build_skip_warp = -1;  // kf_test_build_stage_fault

@@ -407,7 +407,7 @@ def kf_get_tuning(ctx) -> dict:
     return _tuning_dict(t)
 
 
-def kf_set_tuning(ctx, fit_block: int, build_hit_tile: int, build_list_width: int, build_scan: int = 0,
+def kf_set_tuning(ctx, fit_block: int, build_hit_tile: int, build_list_width: int, build_scan: int = 4,
                   fit_chunk: int = 0, fit_stage: int = 0, bin_unordered: int = 0):
     t = kf_tuning(int(fit_block), int(build_hit_tile), int(build_list_width), int(build_scan), int(fit_chunk),
                   int(fit_stage), int(bin_unordered))

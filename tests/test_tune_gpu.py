@@ -11,7 +11,7 @@ from fitutil import gpu_fit
 
 pytestmark = pytest.mark.gpu
 
-DEFAULT = {"fit_block": 128, "build_hit_tile": 0, "build_list_width": 8, "build_scan": 0, "fit_chunk": 0,
+DEFAULT = {"fit_block": 128, "build_hit_tile": 0, "build_list_width": 8, "build_scan": 4, "fit_chunk": 0,
            "fit_stage": 0, "bin_unordered": 0}
 BUILD_KEYS = ("par", "cov", "chi2", "nhits", "status", "hits", "n_cands", "cand_hits", "cand_chi2", "cand_nhits")
 
