@@ -239,7 +239,10 @@ typedef struct {
  * max_cands = 1 is the best-hit approach.  The window is the set of bins
  * that a hit with chi2 < cut can fall in (chi2 >= (u.r)^2 / (u^T S u) for
  * every direction u), each bound widened by 0.1 % plus 1e-6 rad / 1e-5 cm
- * against rounding, so binning never changes the result.  Seeds are processed in (eta, phi) bin order within each event.
+ * against rounding, so binning never changes the result.  The
+ * register-resident layout (kf_tuning.build_scan 4) takes the seeds in their
+ * given order, the others in (eta, phi) bin order within each event; the
+ * results do not depend on the order.
  *
  * seeds: [n_seeds] starting states at or inside the first build layer (the
  * seeds' charge is read); seeds of event e are seed_off[e] .. seed_off[e+1]
