@@ -514,6 +514,15 @@ def extras(a, ctx, kf, torch, dev, det, ev, seeds, hits, out, chi2, status, stre
         res["cpu_baseline"] = {"value": m * L / dtc, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": f"first {m} tracks ({m // a.tracks} events) x {L} layers, FP64 oracle, "
                                          f"{cores} OpenMP threads, {dtc:.2f} s wall"}
+        # and on one core (a smaller sample of the same tracks)
+        m1 = min(m, a.tracks)
+        t0 = time.perf_counter()
+        O.fit(ev.seeds.par[:, :m1], ev.seeds.cov[:, :m1], ev.seeds.charge[:m1], ev.hits.xyz[:, :, :m1],
+              ev.hits.valid[:, :m1], [f32(r) for r in det.radii], f32(det.bz), f32(det.sigma_xy),
+              f32(det.sigma_z), n_threads=1)
+        dt1 = time.perf_counter() - t0
+        res["cpu_baseline"]["single_thread"] = {"value": m1 * L / dt1, "unit": UNIT,
+                                                "sample": f"first {m1} tracks x {L} layers, 1 thread, {dt1:.2f} s"}
         # the same sample's chi2 increments against the GPU fit's (outside any timed region)
         res["chi2_error_vs_oracle"] = dict(chi2_error_table(chi2[:, :m].double().cpu().numpy(), orc["chi2"]),
                                            sample=f"first {m} tracks of the workload x {L} layers")
@@ -863,6 +872,16 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist, peaks=None):
         res["cpu_baseline"] = {"value": m * Lb / dtc, "unit": "seed-layer steps/s", "cores": cores, "kind": "oracle",
                                "sample": f"first {m} seeds of event 0 x {Lb} layers, N = 6, all-hits chi2 scan "
                                          f"(the oracle bins nothing), {cores} OpenMP threads, {dtc:.2f} s wall"}
+        # and on one core (the first tenth of those seeds)
+        m1 = max(1, m // 10)
+        i1 = np.arange(m1)
+        t0 = time.perf_counter()
+        O.build_tracks(fr["par"][i1], fr["cov"][i1], batch.seeds.charge[i1], batch.seed_event[i1], batch.layer_xyz,
+                       batch.layer_off, radii_b, f32(det.bz), f32(det.sigma_xy), f32(det.sigma_z), 30.0, 6,
+                       n_threads=1)
+        dt1 = time.perf_counter() - t0
+        res["cpu_baseline"]["single_thread"] = {"value": m1 * Lb / dt1, "unit": "seed-layer steps/s",
+                                                "sample": f"first {m1} seeds x {Lb} layers, 1 thread, {dt1:.2f} s"}
         # the same seeds' best paths against the GPU build's (N = 6): differing
         # paths re-evaluated by the oracle and counted as near ties (same hit
         # count, chi2_tot within 1e-4 relative, or a hit within 1e-3 of the cut)
