@@ -305,17 +305,22 @@ def run_ours(a):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(a.steps):
+    # an event before every step and after the last: the total over the K steps
+    # is the first to the last, and the per-step times give their spread
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
+    marks[0].record(stream)
+    for i in range(a.steps):
         step()
-    e1.record(stream)
+        marks[i + 1].record(stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    t_ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+    t_ms = max_over_ranks(marks[0].elapsed_time(marks[-1]), dist, dev)
     ms_per_step = t_ms / a.steps
+    per_step = np.array([marks[i].elapsed_time(marks[i + 1]) for i in range(a.steps)])
+    step_spread = {"median_ms": float(np.median(per_step)), "min_ms": float(per_step.min()),
+                   "max_ms": float(per_step.max()), "steps": int(a.steps)}
     value = whole_job_rate(n * L, world, ms_per_step / 1e3)
 
     # roofline of the per-layer kernel: the graph holds only the L x chunks layer launches
@@ -341,7 +346,7 @@ def run_ours(a):
             "vs_baseline": None, "dtype": "f32 (positions as float pairs)",
             "data": "synthetic (seeded generator, helix hits + Gaussian smear)",
             "config": workload_config(a), "roofline": roof, "clocks": clk, "gpu_launches": a.steps * L * chunks,
-            "tuning": tuning}
+            "tuning": tuning, "step_ms_spread": step_spread}
     line["peaks"] = peaks_leg(kf, ctx, stream, dev, smi_index)
 
     if not a.no_extras:
