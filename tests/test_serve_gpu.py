@@ -207,6 +207,12 @@ def test_native_driver_serves_every_request(tmp_path):
         assert r["requests"] == 24 and r["events_per_s"] > 0, r
         assert 0 < r["p50_ms"] <= r["p99_ms"], r
         assert r["max_resident"] >= 1 and r["step_launches"] >= (7 if scan == 2 else 1), r
+        # the scheduler thread's time split covers the run: each part >= 0,
+        # together about the run's wall time (its clock runs from the first
+        # submit; the scheduler's from the same counters read before and after)
+        parts = [r["sched_busy_ms"], r["sched_gpu_wait_ms"], r["sched_idle_ms"]]
+        assert all(p >= 0 for p in parts), r
+        assert 0.5 * r["wall_s"] * 1e3 <= sum(parts) <= 1.5 * r["wall_s"] * 1e3 + 5.0, r
 
 
 @pytest.mark.parametrize("n_build,max_cands", [(1, 6), (7, 1), (7, 3)])
