@@ -1074,7 +1074,7 @@ def write_serve_pool(path, pool, det, max_slots, device_arena_bytes, host_arena_
 def run_serve_driver(pool_path, requests, rate, threads, seed, refit=0, tuning=None):
     """One run of the native serving driver; its JSON line as a dict."""
     from paper_1605_05508_gb300 import build as B
-    scan = tuning["build_scan"] if tuning else 2
+    scan = tuning["build_scan"] if tuning else 4  # the library default
     lw = tuning["build_list_width"] if tuning else 8
     out = subprocess.run([B.DRIVER, pool_path, str(requests), str(rate), str(threads), str(seed), str(int(refit)),
                           str(scan), str(lw)], capture_output=True, text=True, timeout=600)
@@ -1164,15 +1164,15 @@ def serve_leg(a, kf, dev, rank, tuning=None):
         write_serve_pool(pool_path, pool, det, kf.MAX_SLOTS, 16 << 30, 3 << 30)
         drv = lambda rate, threads, refit=0: run_serve_driver(pool_path, M, rate, threads, a.seed + 7, refit, tuning)
 
-        def median3(rate, threads, refit=0):
-            # saturation varies from run to run by up to ~20 %: the median of
-            # three runs, the three rates recorded beside it
-            rs = sorted((drv(rate, threads, refit) for _ in range(3)), key=lambda r: r["events_per_s"])
-            return dict(rs[1], repeats_events_per_s=[r["events_per_s"] for r in rs])
-        sat1 = median3(0, 1)
-        sat = median3(0, 4)
+        def median_of(k, rate, threads, refit=0):
+            # saturation varies from run to run (by up to ~25 % with four
+            # submitting threads): the median of k runs, all k rates beside it
+            rs = sorted((drv(rate, threads, refit) for _ in range(k)), key=lambda r: r["events_per_s"])
+            return dict(rs[k // 2], repeats_events_per_s=[r["events_per_s"] for r in rs])
+        sat1 = median_of(3, 0, 1)
+        sat = median_of(5, 0, 4)
         runs = [dict(drv(frac * sat["events_per_s"], 4), load_fraction=frac) for frac in (0.5, 0.8)]
-        sat_r = median3(0, 4, refit=1)
+        sat_r = median_of(3, 0, 4, refit=1)
     finally:
         os.unlink(pool_path)
     mean_seeds = float(np.mean([pool[i % len(pool)]["seed_par"].shape[1] for i in range(M)]))

@@ -12,8 +12,8 @@
  *                   is submitted at its arrival time, or when the queue has room)
  *   SEED            seed of the arrival times
  *   REFIT           1: each request also re-fits its best candidates (default 0)
- *   BUILD_SCAN,     the build step's thread layout and child-list width in the
- *   LIST_WIDTH      context's launch parameters (kf_tuning; default 2 and 8)
+ *   BUILD_SCAN,     the build's thread layout and child-list width in the
+ *   LIST_WIDTH      context's launch parameters (kf_tuning; default 4 and 8)
  * One line of JSON on stdout: events/s over the whole run (first submit to
  * last result), p50 / p99 / mean latency (kf_submit to results on the host, as
  * the library measures it), and the loop's counters over the run (launches,
@@ -143,7 +143,7 @@ int main(int argc, char **argv)
     g_threads = atoi(argv[4]);
     uint64_t rng = (uint64_t)strtoull(argv[5], NULL, 10) * 0x9E3779B97F4A7C15ull + 1;
     const int refit = argc > 6 ? atoi(argv[6]) : 0;
-    const int build_scan = argc > 7 ? atoi(argv[7]) : 2, list_width = argc > 8 ? atoi(argv[8]) : 8;
+    const int build_scan = argc > 7 ? atoi(argv[7]) : 4, list_width = argc > 8 ? atoi(argv[8]) : 8;
     if (g_m < 1 || g_threads < 1 || rate < 0) return 2;
     FILE *f = fopen(argv[1], "rb");
     if (!f) {
