@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-build", action="store_true", help="skip the combinatorial-build leg")
     ap.add_argument("--build-events", type=int, default=50)
     ap.add_argument("--build-seeds", type=int, default=5000)
+    ap.add_argument("--build-windows", choices=["sub-bins", "bins"], default="sub-bins",
+                    help="the build's window look-up: by the 64 x 512 sub-bins the unordered binning also gives "
+                         "(default), or by the 64 x 256 bins alone")
     ap.add_argument("--build-tuning", default=None, metavar="TILE,LIST,SCAN",
                     help="fixed launch parameters of the N = 6 build (hit tile, child-list width, scan scheme) "
                          "instead of the sweep and the autotuner's choice")
@@ -657,6 +660,12 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist, peaks=None):
     nh = batch.layer_xyz.shape[1]
     bins = kf.HitBins(torch.empty((nh, 4), device=dev), torch.empty((E * Lb, kf.NBINS + 1), dtype=torch.int32,
                                                                      device=dev))
+    # the sub-bin starts, given by the unordered binning only
+    fine = (torch.empty((E * Lb, kf.NBINS_FINE + 1), dtype=torch.int32, device=dev)
+            if a.build_windows == "sub-bins" else None)
+
+    def set_bins():
+        bins.fine_off = fine if kf.kf_get_tuning(ctx)["bin_unordered"] else None
     seed_off = D(np.searchsorted(batch.seed_event, np.arange(E + 1)).astype(np.int64))
     i32 = dict(dtype=torch.int32, device=dev)
     out = kf.BuildResult(best=kf.Tracks(torch.empty((6, n), device=dev), torch.empty((21, n), device=dev), s.charge,
@@ -666,6 +675,7 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist, peaks=None):
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
 
     def run(N, k):
+        set_bins()
         for _ in range(3):
             kf.kf_fit(ctx, s, fh, fo, None, fst, stream)
             kf.kf_bin_hits(ctx, lh, bins, stream)
@@ -815,10 +825,13 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist, peaks=None):
            "build_ms_per_layer": float(t6[2]) / Lb, "mean_hits_found": mean_hits, "max_cands": 6,
            "best_hit_N1": {"ms_per_step": tot1, "value": world * n * Lb / (tot1 / 1e3), "build_ms": float(t1[2]),
                            "tuning": tune1, "build_ms_by_setting": sweep1},
-           "tuning": tune6, "build_ms_by_setting": sweep6, "efficiency_and_refit": efficiency,
+           "tuning": tune6, "build_windows": a.build_windows if tune6["build_scan"] == 4 else "bins",
+           "build_ms_by_setting": sweep6, "efficiency_and_refit": efficiency,
            "plain_f64": plain_f64,
            "clone_engine_curve": {"seeds": SEED_READING, "points": curve},
-           "bin_order": "scatter order inside each bin (bin_unordered 1; the build's results are the same bits)",
+           "bin_order": "scatter order inside each bin (bin_unordered 1; the build's results are the same bits)"
+                        + ("; by 64 x 512 sub-bins, whose starts the register-resident build's windows look up"
+                           if fine is not None else ""),
            "gpu_launches_per_step": build_step_launches(tune6, Lb, 6)}
     # roofline of the build by the method's bytes: per seed and layer ~6 parents
     # read (112 B of state each), ~6 children written (112 B + a 4 B hit id) and
@@ -844,7 +857,10 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist, peaks=None):
     prof = ("build_resident_kernel" if tune6["build_scan"] == 4 else "build_step_kernel") + ".instructions.txt"
     setting = profile_value(prof, "setting_code", BUILD_SOURCES)
     code = tune6["build_hit_tile"] * 100 + tune6["build_list_width"] * 10 + tune6["build_scan"]
-    if setting == code and E == profile_value(prof, "events", BUILD_SOURCES):
+    # (and the same window look-up: by sub-bin or by bin)
+    windows = 1.0 if res["build_windows"] == "sub-bins" else 0.0
+    if (setting == code and E == profile_value(prof, "events", BUILD_SOURCES)
+            and windows == profile_value(prof, "sub_bin_windows", BUILD_SOURCES)):
         props = torch.cuda.get_device_properties(dev)
         wi = profile_value(prof, "warp_instructions_per_build", BUILD_SOURCES)
         if wi:

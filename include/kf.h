@@ -173,6 +173,11 @@ int kf_fit_host(kf_ctx *ctx, const kf_tracks *seeds, const kf_track_hits *hits, 
 #define KF_BIN_PHI 256
 #define KF_BIN_ETA_MAX 1.5f
 #define KF_NBINS (KF_BIN_ETA * KF_BIN_PHI)
+/* An optional finer phi look-up inside each eta row: KF_BIN_PHI_FINE sub-bins
+ * over [-pi, pi) (sub-bin 2 iphi and 2 iphi + 1 split phi bin iphi in two).
+ * Sub-bin c = ieta * KF_BIN_PHI_FINE + iphi_fine. */
+#define KF_BIN_PHI_FINE (2 * KF_BIN_PHI)
+#define KF_NBINS_FINE (KF_BIN_ETA * KF_BIN_PHI_FINE)
 /* Largest number of hits in one (event, layer) segment. */
 #define KF_MAX_HITS_PER_SEGMENT ((1 << 21) - 2)
 
@@ -190,7 +195,8 @@ typedef struct {
 } kf_layer_hits;
 
 /* Binned hits (output of kf_bin_hits, input of kf_build; device pointers).
- * Within each segment the hits are ordered by bin, and by id inside a bin. */
+ * Within each segment the hits are ordered by bin, and by id inside a bin
+ * (by sub-bin, in no order inside a sub-bin, with kf_tuning.bin_unordered). */
 typedef struct {
     int32_t n_events;
     int32_t n_layers;
@@ -199,14 +205,20 @@ typedef struct {
     float *hits;             /* [n_hits][4]: x, y, z, and the hit id (int32 bits) */
     int32_t *bin_off;        /* [n_events * n_layers][KF_NBINS + 1]: bin starts within the segment */
     const int64_t *seg_off;  /* [n_events * n_layers + 1], as in kf_layer_hits */
+    int32_t *fine_off;       /* optional (NULL: none): [n_events * n_layers][KF_NBINS_FINE + 1]
+                                sub-bin starts within the segment; filled by kf_bin_hits (which
+                                then requires kf_tuning.bin_unordered = 1), used by kf_build to
+                                narrow each window row to the sub-bins it reaches */
 } kf_layer_hit_bins;
 
 /* Sort every segment's hits into the eta x phi bins (Sec. 3: hits sorted in
  * phi within eta bins per layer, phi bins for fast look-up): a counting sort
  * over all segments at once (count, per-segment scan, scatter, then an id
- * sort inside each bin, so the order is deterministic).  `out->hits` and `out->bin_off` are
- * caller-allocated with the sizes above; the other fields of `out` are set
- * from `in`.  Segments must hold at most KF_MAX_HITS_PER_SEGMENT hits (not
+ * sort inside each bin, so the order is deterministic), or with
+ * kf_tuning.bin_unordered one block per segment and no id sort (with
+ * `out->fine_off` set: by sub-bin, and the sub-bin starts written too).
+ * `out->hits`, `out->bin_off` (and `out->fine_off`) are caller-allocated with
+ * the sizes above; the other fields of `out` are set from `in`.  Segments must hold at most KF_MAX_HITS_PER_SEGMENT hits (not
  * checked here: seg_off is device memory; kf_build ignores hits beyond it).
  * Errors: KF_EINVAL (sizes, null pointers), KF_ECUDA. */
 int kf_bin_hits(kf_ctx *ctx, const kf_layer_hits *in, kf_layer_hit_bins *out, void *stream);

@@ -5,7 +5,10 @@
 // A counting sort of every segment (one event on one layer) into the 64 x 256
 // bins, with a final insertion sort by id inside each bin so that the output
 // is deterministic (skipped with kf_tuning.bin_unordered: the build's results
-// do not depend on the order of the hits inside a bin).
+// do not depend on the order of the hits inside a bin).  The unordered form
+// can sort by 64 x 512 sub-bins instead, each bin two of them, and give the
+// sub-bin starts as well: the build's windows then cover half as wide a
+// strip of phi beyond their edges.
 #include "kf_bin.cuh"
 #include "kf_internal.h"
 
@@ -22,8 +25,7 @@ namespace kfi {
 // sorts the bin's slots by id, so the output does not depend on the order
 // in which (3) took them.  A segment of any size spreads over the whole GPU.
 constexpr int kScanThreads = 1024;
-constexpr int kPerThread = KF_NBINS / kScanThreads;  // 16 consecutive bins per thread
-static_assert(KF_NBINS % kScanThreads == 0, "bins per thread");
+static_assert(KF_NBINS % kScanThreads == 0, "bins per thread");  // 16 consecutive bins a thread
 constexpr int kPointThreads = 256;
 
 // the segment s with seg_off[s] <= g < seg_off[s + 1], or -1
@@ -50,23 +52,24 @@ __global__ void __launch_bounds__(kPointThreads) bin_count_kernel(const BinArgs 
   }
 }
 
-// padded shared-memory index of bin b: a thread's 16 consecutive bins and a
-// warp's 32 threads fall in distinct banks
+// padded shared-memory index of bin b: a thread's 16 (or 32) consecutive
+// bins and a warp's 32 threads fall in distinct banks
 __device__ __forceinline__ int pad_idx(int b) { return b + (b >> 5); }
 constexpr int kScanSmem = (KF_NBINS + KF_NBINS / 32) * int(sizeof(int));
+// the sub-bin histogram: one block per SM
+constexpr int kFineSmem = (KF_NBINS_FINE + KF_NBINS_FINE / 32) * int(sizeof(int));
+static_assert(KF_NBINS_FINE % kScanThreads == 0, "sub-bins per thread");
 
-// Exclusive scan, in place, of the KF_NBINS counts in cnt (padded layout)
-// by the block's kScanThreads threads, each owning kPerThread consecutive
+// Exclusive scan, in place, of the NB counts in cnt (padded layout) by the
+// block's kScanThreads threads, each owning NB / kScanThreads consecutive
 // bins; returns the total to every thread.  Ends with a barrier.
+template <int NB = KF_NBINS>
 __device__ __forceinline__ int scan_bins(int* cnt, int* warp_tot) {
+  constexpr int kPer = NB / kScanThreads;
   const int tid = threadIdx.x;
-  int local[kPerThread];
   int run = 0;
 #pragma unroll
-  for (int t = 0; t < kPerThread; ++t) {
-    local[t] = run;
-    run += cnt[pad_idx(tid * kPerThread + t)];
-  }
+  for (int t = 0; t < kPer; ++t) run += cnt[pad_idx(tid * kPer + t)];
   const int lane = tid & 31, warp = tid >> 5;
   int incl = run;
 #pragma unroll
@@ -86,10 +89,15 @@ __device__ __forceinline__ int scan_bins(int* cnt, int* warp_tot) {
     warp_tot[lane] = w;  // inclusive over warps
   }
   __syncthreads();
-  const int base = (incl - run) + (warp > 0 ? warp_tot[warp - 1] : 0);
+  int acc = (incl - run) + (warp > 0 ? warp_tot[warp - 1] : 0);
   const int total = warp_tot[kScanThreads / 32 - 1];
 #pragma unroll
-  for (int t = 0; t < kPerThread; ++t) cnt[pad_idx(tid * kPerThread + t)] = base + local[t];
+  for (int t = 0; t < kPer; ++t) {
+    const int i = pad_idx(tid * kPer + t);
+    const int c = cnt[i];
+    cnt[i] = acc;
+    acc += c;
+  }
   __syncthreads();
   return total;
 }
@@ -121,11 +129,17 @@ __global__ void __launch_bounds__(kScanThreads) bin_scan_kernel(const BinArgs A)
 // depend on it.
 // The points [p0, p1) of xyz ([3][stride]) of one segment, by the whole
 // block, with cnt (KF_NBINS padded ints of shared memory) and warp_tot.
+// FINE: the counting sort runs over the KF_NBINS_FINE sub-bins (cnt holds
+// as many), whose starts go to fine_off, and the bin starts to `off` are
+// those of the even sub-bins (a bin is two consecutive sub-bins).
+template <bool FINE = false>
 __device__ __forceinline__ void bin_one_segment(const float* xyz, int64_t stride, int64_t p0, int64_t p1,
-                                                int32_t* off, float4* out_pts, int32_t* out_id, int32_t* out_seg,
-                                                int seg, int* cnt, int* warp_tot) {
+                                                int32_t* off, int32_t* fine_off, float4* out_pts, int32_t* out_id,
+                                                int32_t* out_seg, int seg, int* cnt, int* warp_tot) {
+  constexpr int NB = FINE ? KF_NBINS_FINE : KF_NBINS;
+  constexpr int NPHI = FINE ? KF_BIN_PHI_FINE : KF_BIN_PHI;
   const int tid = threadIdx.x;
-  for (int b = tid; b < KF_NBINS; b += kScanThreads) cnt[pad_idx(b)] = 0;
+  for (int b = tid; b < NB; b += kScanThreads) cnt[pad_idx(b)] = 0;
   __syncthreads();
   // the points in batches of kSegBatch a thread, their loads issued together
   constexpr int kSegBatch = 4;
@@ -144,7 +158,7 @@ __device__ __forceinline__ void bin_one_segment(const float* xyz, int64_t stride
     for (int u = 0; u < kSegBatch; ++u) {
       const int64_t g = g0 + int64_t(u) * kScanThreads;
       if (g < p1) {
-        const int b = bin_of(x[u], y[u], z[u]);
+        const int b = bin_of<NPHI>(x[u], y[u], z[u]);
         atomicAdd(&cnt[pad_idx(b)], 1);
         // with points out (hits: their ids travel in .w), out_id is scratch:
         // it keeps each point's bin for the second pass
@@ -153,9 +167,15 @@ __device__ __forceinline__ void bin_one_segment(const float* xyz, int64_t stride
     }
   }
   __syncthreads();
-  const int total = scan_bins(cnt, warp_tot);
+  const int total = scan_bins<NB>(cnt, warp_tot);
   if (tid == 0) off[KF_NBINS] = total;
-  for (int b = tid; b < KF_NBINS; b += kScanThreads) off[b] = cnt[pad_idx(b)];  // coalesced
+  if constexpr (FINE) {
+    if (tid == 0) fine_off[KF_NBINS_FINE] = total;
+    for (int b = tid; b < KF_NBINS_FINE; b += kScanThreads) fine_off[b] = cnt[pad_idx(b)];  // coalesced
+    for (int b = tid; b < KF_NBINS; b += kScanThreads) off[b] = cnt[pad_idx(2 * b)];
+  } else {
+    for (int b = tid; b < KF_NBINS; b += kScanThreads) off[b] = cnt[pad_idx(b)];  // coalesced
+  }
   for (int64_t g0 = p0 + tid; g0 < p1; g0 += int64_t(kScanThreads) * kSegBatch) {
     float x[kSegBatch], y[kSegBatch], z[kSegBatch];
     int bins[kSegBatch];
@@ -179,7 +199,7 @@ __device__ __forceinline__ void bin_one_segment(const float* xyz, int64_t stride
           out_pts[q] = make_float4(x[u], y[u], z[u], __int_as_float(i));
           if (out_seg) out_seg[q] = seg;
         } else {
-          const int64_t q = p0 + atomicAdd(&cnt[pad_idx(bin_of(x[u], y[u], z[u]))], 1);
+          const int64_t q = p0 + atomicAdd(&cnt[pad_idx(bin_of<NPHI>(x[u], y[u], z[u]))], 1);
           out_id[q] = i;
           if (out_seg) out_seg[q] = seg;
         }
@@ -188,21 +208,26 @@ __device__ __forceinline__ void bin_one_segment(const float* xyz, int64_t stride
   }
 }
 
+template <bool FINE>
 __global__ void __launch_bounds__(kScanThreads) bin_segment_kernel(const BinArgs A) {
   extern __shared__ int cnt[];  // counts, then cursors (padded layout)
   __shared__ int warp_tot[32];
   const int seg = blockIdx.x;
-  bin_one_segment(A.xyz, A.stride, A.seg_off[seg], min(A.seg_off[seg + 1], A.stride),
-                  A.bin_off + int64_t(seg) * (KF_NBINS + 1), A.out_pts, A.out_id, A.out_seg, seg, cnt, warp_tot);
+  bin_one_segment<FINE>(A.xyz, A.stride, A.seg_off[seg], min(A.seg_off[seg + 1], A.stride),
+                        A.bin_off + int64_t(seg) * (KF_NBINS + 1),
+                        FINE ? A.fine_off + int64_t(seg) * (KF_NBINS_FINE + 1) : nullptr, A.out_pts, A.out_id,
+                        A.out_seg, seg, cnt, warp_tot);
 }
 
 // The same over a table of segments of different point sets (the events a
 // serving iteration prepares), one block per entry.
+template <bool FINE>
 __global__ void __launch_bounds__(kScanThreads) bin_segment_table_kernel(const BinSegment* table) {
   extern __shared__ int cnt[];
   __shared__ int warp_tot[32];
   const BinSegment& T = table[blockIdx.x];
-  bin_one_segment(T.xyz, T.stride, T.p0, T.p1, T.bin_off, T.out_pts, T.out_id, nullptr, 0, cnt, warp_tot);
+  bin_one_segment<FINE>(T.xyz, T.stride, T.p0, T.p1, T.bin_off, T.fine_off, T.out_pts, T.out_id, nullptr, 0, cnt,
+                        warp_tot);
 }
 
 __global__ void __launch_bounds__(kPointThreads) bin_scatter_kernel(const BinArgs A, int nseg) {
@@ -250,13 +275,14 @@ constexpr int kMaxDevices = 64;
 // a kernel's shared-memory attributes, set once per device (the serving loop
 // bins from several threads' calls; setting them again is harmless)
 template <class K>
-static cudaError_t segment_smem_attrs(K kernel, std::atomic<bool>* done) {
+static cudaError_t segment_smem_attrs(K kernel, int smem, std::atomic<bool>* done) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev >= 0 && dev < kMaxDevices && done[dev].load(std::memory_order_acquire)) return cudaSuccess;
-  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kScanSmem);
-  // the largest shared-memory carveout: two blocks (2 x 68 KB) per SM
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  // the largest shared-memory carveout: two blocks (2 x 68 KB) per SM, or one
+  // with the sub-bins (135 KB)
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                              int(cudaSharedmemCarveoutMaxShared));
@@ -264,12 +290,18 @@ static cudaError_t segment_smem_attrs(K kernel, std::atomic<bool>* done) {
   return e;
 }
 
-cudaError_t launch_bin_segment_table(const BinSegment* table, int n, cudaStream_t st) {
+cudaError_t launch_bin_segment_table(const BinSegment* table, int n, bool fine, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  static std::atomic<bool> attr_set[kMaxDevices];
-  cudaError_t e = segment_smem_attrs(bin_segment_table_kernel, attr_set);
+  static std::atomic<bool> attr_set[kMaxDevices], fine_attr_set[kMaxDevices];
+  if (fine) {
+    cudaError_t e = segment_smem_attrs(bin_segment_table_kernel<true>, kFineSmem, fine_attr_set);
+    if (e != cudaSuccess) return e;
+    bin_segment_table_kernel<true><<<n, kScanThreads, kFineSmem, st>>>(table);
+    return cudaGetLastError();
+  }
+  cudaError_t e = segment_smem_attrs(bin_segment_table_kernel<false>, kScanSmem, attr_set);
   if (e != cudaSuccess) return e;
-  bin_segment_table_kernel<<<n, kScanThreads, kScanSmem, st>>>(table);
+  bin_segment_table_kernel<false><<<n, kScanThreads, kScanSmem, st>>>(table);
   return cudaGetLastError();
 }
 
@@ -279,12 +311,19 @@ cudaError_t launch_bin_points(const BinArgs& a, int n_segments, cudaStream_t st)
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (a.unordered) {  // one launch, one block per segment
-    static std::atomic<bool> seg_attr_set[kMaxDevices];
-    e = segment_smem_attrs(bin_segment_kernel, seg_attr_set);
+    static std::atomic<bool> seg_attr_set[kMaxDevices], fine_attr_set[kMaxDevices];
+    if (a.fine_off) {
+      e = segment_smem_attrs(bin_segment_kernel<true>, kFineSmem, fine_attr_set);
+      if (e != cudaSuccess) return e;
+      bin_segment_kernel<true><<<n_segments, kScanThreads, kFineSmem, st>>>(a);
+      return cudaGetLastError();
+    }
+    e = segment_smem_attrs(bin_segment_kernel<false>, kScanSmem, seg_attr_set);
     if (e != cudaSuccess) return e;
-    bin_segment_kernel<<<n_segments, kScanThreads, kScanSmem, st>>>(a);
+    bin_segment_kernel<false><<<n_segments, kScanThreads, kScanSmem, st>>>(a);
     return cudaGetLastError();
   }
+  if (a.fine_off) return cudaErrorInvalidValue;  // sub-bins only with the unordered binning
   e = cudaMemsetAsync(a.bin_off, 0, size_t(n_segments) * (KF_NBINS + 1) * sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
   const int64_t pts = a.stride > 0 ? a.stride : 1;
@@ -317,6 +356,7 @@ extern "C" int kf_bin_hits(kf_ctx* ctx, const kf_layer_hits* in, kf_layer_hit_bi
       in->first_layer + in->n_layers > ctx->cfg.n_layers || in->n_hits < 0)
     return KF_EINVAL;
   if (!in->seg_off || !out->bin_off || (in->n_hits > 0 && (!in->xyz || !out->hits))) return KF_EINVAL;
+  if (out->fine_off && !ctx->tune.bin_unordered) return KF_EINVAL;  // sub-bins: unordered binning only
   out->n_events = in->n_events;
   out->n_layers = in->n_layers;
   out->first_layer = in->first_layer;
@@ -338,6 +378,7 @@ extern "C" int kf_bin_hits(kf_ctx* ctx, const kf_layer_hits* in, kf_layer_hit_bi
   a.out_seg = nullptr;
   a.cursor = reinterpret_cast<int32_t*>(static_cast<char*>(ctx->s_bin_id.ptr) + id_bytes);
   a.unordered = ctx->tune.bin_unordered;
+  a.fine_off = out->fine_off;
   KF_CUDA_TRY(ctx, launch_bin_points(a, nseg, static_cast<cudaStream_t>(stream)));
   return KF_OK;
 }

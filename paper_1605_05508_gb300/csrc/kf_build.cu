@@ -83,10 +83,12 @@ __device__ __forceinline__ int wrap_phi(int d) {  // to [-KF_BIN_PHI/2, KF_BIN_P
 
 // Window of a predicted candidate: S^-1 = (C_pos + V)^-1, and the eta rows
 // e0..e1 and phi bins fa0..fa1, fb0..fb1 (second part when the window wraps
-// around phi = +-pi) that can hold a hit with chi2 < cut at radius R.
+// around phi = +-pi) that can hold a hit with chi2 < cut at radius R; the
+// phi bins are those of a row of nphi bins over [-pi, pi) (KF_BIN_PHI, or
+// KF_BIN_PHI_FINE for the sub-bins), fa1 preset by the caller to nphi - 1.
 __device__ __forceinline__ void hit_window(const float p[6], const float lo[3], const float C[21], float R, float v0,
                                            float v1, float v2, float cut, float Si[6], int& e0, int& e1, int& fa0,
-                                           int& fa1, int& fb0, int& fb1) {
+                                           int& fa1, int& fb0, int& fb1, int nphi = KF_BIN_PHI) {
   kf::inverse_S(C, v0, v1, v2, Si);
   const float X = p[0] + lo[0], Y = p[1] + lo[1], Z = p[2] + lo[2];
   // direction cosines of the position: they only scale the widths below,
@@ -112,18 +114,20 @@ __device__ __forceinline__ void hit_window(const float p[6], const float lo[3], 
   const float phic = atan2f(Y, X);
   const float dphi = (rin > 0.5f * R && wt * kWiden < rin) ? (wt * kWiden / rin) * kWiden + 1e-6f : 10.f;
   if (dphi < 1.f && phic >= -kPi && phic <= kPi) {  // also false for NaN
-    const float scale = float(KF_BIN_PHI) / (2.0f * kPi);
+    // the sub-bin scale is exactly twice the bin scale (a power of two), so a
+    // hit's sub-bin halved is its bin
+    const float scale = float(nphi) / (2.0f * kPi);
     const int f0 = __float2int_rd((phic - dphi + kPi) * scale);
     const int f1 = __float2int_rd((phic + dphi + kPi) * scale);
-    if (f1 - f0 + 1 < KF_BIN_PHI) {
+    if (f1 - f0 + 1 < nphi) {
       if (f0 < 0) {
-        fa0 = f0 + KF_BIN_PHI;
+        fa0 = f0 + nphi;
         fb0 = 0;
         fb1 = f1;
-      } else if (f1 >= KF_BIN_PHI) {
+      } else if (f1 >= nphi) {
         fa0 = f0;
         fb0 = 0;
-        fb1 = f1 - KF_BIN_PHI;
+        fb1 = f1 - nphi;
       } else {
         fa0 = f0;
         fa1 = f1;
@@ -541,7 +545,7 @@ __global__ void __launch_bounds__(kBuildThreads, kBuildBlocksPerSM) build_step_k
 
 // Chi2 scan of one predicted candidate's window (one thread): rows e0..e1,
 // each the hits of bins fa0..fa1 then fb0..fb1 of the segment's binned hits
-// `hs` (bin offsets `boff`); the next row's bin offsets and the next hit are
+// `hs` (bin offsets `boff`, nphi of them a row); the next row's bin offsets and the next hit are
 // loaded one step ahead.  Every hit with chi2 < cut (and an id below the
 // segment limit) becomes a child key (nh + 1, chi2tot + chi2, parent rank k,
 // id + 1) in the sorted list (L, P).  Returns whether any hit was compatible.
@@ -549,12 +553,12 @@ template <int LW>
 __device__ __forceinline__ bool scan_window(const float p[6], const float lo[3], const float Si[6], int e0, int e1,
                                             int fa0, int fa1, int fb0, int fb1, const int32_t* boff,
                                             const float4* hs, float cut, int nh, float chi2tot, int k,
-                                            uint64_t (&L)[LW], int (&P)[LW]) {
+                                            uint64_t (&L)[LW], int (&P)[LW], int nphi = KF_BIN_PHI) {
   bool any = false;
   const bool two = fb1 >= fb0;
   int na0 = 0, na1 = 0, nb0 = 0, nb1 = 0;
   if (e0 <= e1) {
-    const int32_t* q = boff + e0 * KF_BIN_PHI;
+    const int32_t* q = boff + e0 * nphi;
     na0 = q[fa0];
     na1 = q[fa1 + 1];
     if (two) {
@@ -565,7 +569,7 @@ __device__ __forceinline__ bool scan_window(const float p[6], const float lo[3],
   for (int er = e0; er <= e1; ++er) {
     const int a0 = na0, na = na1 - na0, b0 = nb0, n = na + (nb1 - nb0);
     if (er < e1) {
-      const int32_t* q = boff + (er + 1) * KF_BIN_PHI;
+      const int32_t* q = boff + (er + 1) * nphi;
       na0 = q[fa0];
       na1 = q[fa1 + 1];
       if (two) {
@@ -603,12 +607,12 @@ template <int LW, int kScanBatch = 4>
 __device__ __forceinline__ bool scan_window_batched(const float p[6], const float lo[3], const float Si[6], int e0, int e1,
                                             int fa0, int fa1, int fb0, int fb1, const int32_t* boff,
                                             const float4* hs, float cut, int nh, float chi2tot, int k,
-                                            uint64_t (&L)[LW], int (&P)[LW]) {
+                                            uint64_t (&L)[LW], int (&P)[LW], int nphi = KF_BIN_PHI) {
   bool any = false;
   const bool two = fb1 >= fb0;
   int na0 = 0, na1 = 0, nb0 = 0, nb1 = 0;
   if (e0 <= e1) {
-    const int32_t* q = boff + e0 * KF_BIN_PHI;
+    const int32_t* q = boff + e0 * nphi;
     na0 = q[fa0];
     na1 = q[fa1 + 1];
     if (two) {
@@ -619,7 +623,7 @@ __device__ __forceinline__ bool scan_window_batched(const float p[6], const floa
   for (int er = e0; er <= e1; ++er) {
     const int a0 = na0, na = na1 - na0, b0 = nb0, n = na + (nb1 - nb0);
     if (er < e1) {
-      const int32_t* q = boff + (er + 1) * KF_BIN_PHI;
+      const int32_t* q = boff + (er + 1) * nphi;
       na0 = q[fa0];
       na1 = q[fa1 + 1];
       if (two) {
@@ -1109,18 +1113,22 @@ __global__ void __launch_bounds__(kResThreads, resident_blocks_per_sm(W))
         P[t] = -1;
       }
       const bool win = active && !stopped;
-      int e0 = 0, e1 = -1, fa0 = 0, fa1 = KF_BIN_PHI - 1, fb0 = 0, fb1 = -1;
-      if (win) hit_window(p, lo, C, A.R[l], A.v0, A.v1, A.v2, A.cut, Si, e0, e1, fa0, fa1, fb0, fb1);
+      // the window's rows by sub-bin where the batch has them
+      const int nphi = B.fine_off ? KF_BIN_PHI_FINE : KF_BIN_PHI;
+      const int32_t* boff =
+          B.fine_off ? B.fine_off + sg * (KF_NBINS_FINE + 1) : B.bin_off + sg * (KF_NBINS + 1);
+      int e0 = 0, e1 = -1, fa0 = 0, fa1 = nphi - 1, fb0 = 0, fb1 = -1;
+      if (win) hit_window(p, lo, C, A.R[l], A.v0, A.v1, A.v2, A.cut, Si, e0, e1, fa0, fa1, fb0, fb1, nphi);
       // a row's hits loaded in batches: 4 with one lane a seed, 2 with more
       // (measured: 4 is slower at W = 6, where the registers are needed elsewhere)
       bool any = false;
       if (win) {
         if constexpr (W == 1)
-          any = scan_window_batched(p, lo, Si, e0, e1, fa0, fa1, fb0, fb1, B.bin_off + sg * (KF_NBINS + 1),
-                                    B.hits + h0, A.cut, nh, chi2tot, k, L, P);
+          any = scan_window_batched(p, lo, Si, e0, e1, fa0, fa1, fb0, fb1, boff, B.hits + h0, A.cut, nh, chi2tot, k,
+                                    L, P, nphi);
         else
-          any = scan_window_batched<W, 2>(p, lo, Si, e0, e1, fa0, fa1, fb0, fb1, B.bin_off + sg * (KF_NBINS + 1),
-                                          B.hits + h0, A.cut, nh, chi2tot, k, L, P);
+          any = scan_window_batched<W, 2>(p, lo, Si, e0, e1, fa0, fa1, fb0, fb1, boff, B.hits + h0, A.cut, nh,
+                                          chi2tot, k, L, P, nphi);
       }
       // no compatible hit (or a stopped candidate): one child without a hit
       if (active && !any) list_insert(L, P, make_key(nh, chi2tot, k, 0), -1);
@@ -1301,10 +1309,11 @@ __global__ void __launch_bounds__(kResThreads, kResBlocksPerSM)
   }
   bool any = false;
   if (!stopped) {
-    int e0 = 0, e1 = -1, fa0 = 0, fa1 = KF_BIN_PHI - 1, fb0 = 0, fb1 = -1;
-    hit_window(p, lo, C, A.R[l], A.v0, A.v1, A.v2, A.cut, Si, e0, e1, fa0, fa1, fb0, fb1);
-    any = scan_window(p, lo, Si, e0, e1, fa0, fa1, fb0, fb1, B.bin_off + sg * (KF_NBINS + 1), B.hits + h0, A.cut,
-                      nh, chi2tot, 0, L, P);
+    const int nphi = B.fine_off ? KF_BIN_PHI_FINE : KF_BIN_PHI;
+    const int32_t* boff = B.fine_off ? B.fine_off + sg * (KF_NBINS_FINE + 1) : B.bin_off + sg * (KF_NBINS + 1);
+    int e0 = 0, e1 = -1, fa0 = 0, fa1 = nphi - 1, fb0 = 0, fb1 = -1;
+    hit_window(p, lo, C, A.R[l], A.v0, A.v1, A.v2, A.cut, Si, e0, e1, fa0, fa1, fb0, fb1, nphi);
+    any = scan_window(p, lo, Si, e0, e1, fa0, fa1, fb0, fb1, boff, B.hits + h0, A.cut, nh, chi2tot, 0, L, P, nphi);
   }
   // no compatible hit (or a stopped seed): one child without a hit
   if (!any) list_insert(L, P, make_key(nh, chi2tot, 0, 0), -1);
@@ -1705,6 +1714,7 @@ extern "C" int kf_build(kf_ctx* ctx, const kf_tracks* seeds, const int64_t* seed
     ra.one.hits = reinterpret_cast<const float4*>(bins->hits);
     ra.one.bin_off = bins->bin_off;
     ra.one.seg_off = bins->seg_off;
+    ra.one.fine_off = bins->fine_off;
     ra.one.S = S;
     ra.one.group_begin = 0;
     ra.one.seed_begin = 0;

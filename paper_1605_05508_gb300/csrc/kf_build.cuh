@@ -172,6 +172,9 @@ struct ResidentBatch {
   const float4* hits;
   const int32_t* bin_off;
   const int64_t* seg_off;
+  // the segments' sub-bin starts ([n_seg][KF_NBINS_FINE + 1]), or null: the
+  // windows then look up the bins of bin_off
+  const int32_t* fine_off;
   int64_t S;
   int64_t group_begin;       // with a table: the launch's first group of this batch
   int64_t seed_begin;        // with a table: the first-layer launch's first seed of this batch

@@ -57,7 +57,7 @@ class kf_layer_hits(C.Structure):
 
 class kf_layer_hit_bins(C.Structure):
     _fields_ = [("n_events", C.c_int32), ("n_layers", C.c_int32), ("first_layer", C.c_int32), ("n_hits", C.c_int64),
-                ("hits", C.c_void_p), ("bin_off", C.c_void_p), ("seg_off", C.c_void_p)]
+                ("hits", C.c_void_p), ("bin_off", C.c_void_p), ("seg_off", C.c_void_p), ("fine_off", C.c_void_p)]
 
 
 class kf_build_result(C.Structure):
@@ -103,6 +103,8 @@ class kf_tuning(C.Structure):
 MAX_SLOTS = 64  # KF_MAX_SLOTS
 BIN_ETA, BIN_PHI, BIN_ETA_MAX = 64, 256, 1.5  # KF_BIN_ETA, KF_BIN_PHI, KF_BIN_ETA_MAX
 NBINS = BIN_ETA * BIN_PHI
+BIN_PHI_FINE = 2 * BIN_PHI  # KF_BIN_PHI_FINE
+NBINS_FINE = BIN_ETA * BIN_PHI_FINE
 MAX_HITS_PER_SEGMENT = (1 << 21) - 2  # KF_MAX_HITS_PER_SEGMENT
 
 _lib = None
@@ -313,17 +315,19 @@ class LayerHits:
 
 @dataclass
 class HitBins:
-    """hits [n_hits, 4] float32 (x, y, z, id bits), bin_off [n_seg, NBINS + 1] int32."""
+    """hits [n_hits, 4] float32 (x, y, z, id bits), bin_off [n_seg, NBINS + 1] int32, optional
+    fine_off [n_seg, NBINS_FINE + 1] int32 (sub-bin starts)."""
     hits: object
     bin_off: object
     seg_off: object = None
     n_events: int = 0
     n_layers: int = 0
     first_layer: int = 0
+    fine_off: object = None
 
     def abi(self) -> kf_layer_hit_bins:
         return kf_layer_hit_bins(self.n_events, self.n_layers, self.first_layer, int(self.hits.shape[0]),
-                                 _ptr(self.hits), _ptr(self.bin_off), _ptr(self.seg_off))
+                                 _ptr(self.hits), _ptr(self.bin_off), _ptr(self.seg_off), _ptr(self.fine_off))
 
 
 @dataclass

@@ -32,10 +32,11 @@ def oracle_build(batch, max_cands, idx=None, cut=30.0):
     return b
 
 
-def gpu_build(ctx, batch, max_cands, want_cands=True, build_fn=None):
+def gpu_build(ctx, batch, max_cands, want_cands=True, build_fn=None, fine=False):
     """Seed fit (kf_fit over the seeding layers) -> kf_bin_hits -> kf_build
-    (or build_fn with kf_build's arguments). Returns numpy arrays (hit_idx as
-    [n, L])."""
+    (or build_fn with kf_build's arguments); fine: the binning also gives the
+    sub-bin starts (unordered binning only), which the build then uses.
+    Returns numpy arrays (hit_idx as [n, L])."""
     import torch
     from paper_1605_05508_gb300 import kf
     n = batch.seeds.par.shape[1]
@@ -49,7 +50,9 @@ def gpu_build(ctx, batch, max_cands, want_cands=True, build_fn=None):
     lh = kf.LayerHits(to_dev(batch.layer_xyz), seg_off, E, Lb, batch.build_layers[0])
     nh = batch.layer_xyz.shape[1]
     bins = kf.HitBins(torch.empty((nh, 4), device="cuda"),
-                      torch.empty((E * Lb, kf.NBINS + 1), dtype=torch.int32, device="cuda"))
+                      torch.empty((E * Lb, kf.NBINS + 1), dtype=torch.int32, device="cuda"),
+                      fine_off=torch.empty((E * Lb, kf.NBINS_FINE + 1), dtype=torch.int32, device="cuda")
+                      if fine else None)
     kf.kf_bin_hits(ctx, lh, bins)
     seed_off = to_dev(np.searchsorted(batch.seed_event, np.arange(E + 1)).astype(np.int64))
     N = max_cands

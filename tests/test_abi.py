@@ -93,7 +93,8 @@ def test_binding_constants_match_the_header():
               "KF_ST_TANGENT": kf.ST_TANGENT, "KF_ST_NOT_PD": kf.ST_NOT_PD, "KF_ST_NO_HIT": kf.ST_NO_HIT,
               "KF_ST_DEVICE_TIMEOUT": kf.ST_DEVICE_TIMEOUT, "KF_ST_STOPPED": kf.ST_STOPPED,
               "KF_BIN_ETA": kf.BIN_ETA, "KF_BIN_PHI": kf.BIN_PHI, "KF_BIN_ETA_MAX": kf.BIN_ETA_MAX,
-              "KF_NBINS": kf.NBINS, "KF_MAX_HITS_PER_SEGMENT": kf.MAX_HITS_PER_SEGMENT,
+              "KF_NBINS": kf.NBINS, "KF_BIN_PHI_FINE": kf.BIN_PHI_FINE, "KF_NBINS_FINE": kf.NBINS_FINE,
+              "KF_MAX_HITS_PER_SEGMENT": kf.MAX_HITS_PER_SEGMENT,
               "KF_MAX_SLOTS": kf.MAX_SLOTS, "KF_NOALLOC_MAX_TRACKS": kf.NOALLOC_MAX_TRACKS,
               "KF_PEAK_FP32": kf.PEAK_FP32, "KF_PEAK_FP64": kf.PEAK_FP64}
     for name, value in mirror.items():

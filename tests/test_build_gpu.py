@@ -11,17 +11,18 @@ from paper_1605_05508_gb300 import synth as S
 pytestmark = pytest.mark.gpu
 
 
-def _ref_bins(x, y, z):
-    """Bins from FP64 eta, phi; and the distance to the nearest bin edge."""
+def _ref_bins(x, y, z, nphi=256):
+    """Bins (nphi a row: 256 bins or 512 sub-bins) from FP64 eta, phi; and the
+    distance to the nearest bin edge."""
     r = np.hypot(x, y)
     eta = np.arcsinh(z / r)
     phi = np.arctan2(y, x)
     fe = (eta + 1.5) * 64 / 3.0
-    fp = (phi + np.pi) * 256 / (2 * np.pi)
+    fp = (phi + np.pi) * nphi / (2 * np.pi)
     ie = np.clip(np.floor(fe), 0, 63).astype(int)
-    ip = np.clip(np.floor(fp), 0, 255).astype(int)
+    ip = np.clip(np.floor(fp), 0, nphi - 1).astype(int)
     edge = np.minimum(np.abs(fe - np.round(fe)), np.abs(fp - np.round(fp)))
-    return ie * 256 + ip, edge
+    return ie * nphi + ip, edge
 
 
 def test_bin_hits_is_a_deterministic_counting_sort(cuda_ctx_factory):
@@ -59,6 +60,53 @@ def test_bin_hits_is_a_deterministic_counting_sort(cuda_ctx_factory):
     kf.kf_bin_hits(ctx, lh, again)
     torch.cuda.synchronize()
     assert torch.equal(again.hits, bins.hits) and torch.equal(again.bin_off, bins.bin_off)
+
+
+def test_bin_hits_sub_bins(cuda_ctx_factory):
+    """The unordered binning with sub-bin starts: every segment's hits a
+    permutation ordered by sub-bin (64 x 512, each hit's the FP64 one away from
+    an edge), the sub-bin starts monotone and ending at the segment's size,
+    every bin start that of its even sub-bin; the bins hold the same hits as
+    without sub-bins; the ordered binning refuses sub-bins."""
+    import torch
+    from paper_1605_05508_gb300 import kf
+    det = S.barrel()
+    ctx = cuda_ctx_factory(det.radii)
+    b = S.make_build_batch(6, 3, 700)
+    E, Lb = b.n_events, len(b.build_layers)
+    lh = kf.LayerHits(to_dev(b.layer_xyz), to_dev(b.layer_off), E, Lb, b.build_layers[0])
+    nh = b.layer_xyz.shape[1]
+    i32 = dict(dtype=torch.int32, device="cuda")
+    mk = lambda fine: kf.HitBins(torch.empty((nh, 4), device="cuda"), torch.empty((E * Lb, kf.NBINS + 1), **i32),
+                                 fine_off=torch.empty((E * Lb, kf.NBINS_FINE + 1), **i32) if fine else None)
+    with pytest.raises(kf.KfError):  # ordered binning (the default): no sub-bins
+        kf.kf_bin_hits(ctx, lh, mk(True))
+    kf.kf_set_tuning(ctx, 128, 0, 8, 4, 0, 0, 1)
+    coarse, fine = mk(False), mk(True)
+    kf.kf_bin_hits(ctx, lh, coarse)
+    kf.kf_bin_hits(ctx, lh, fine)
+    torch.cuda.synchronize()
+    kf.kf_set_tuning(ctx, 128, 0, 8, 4)
+    np.testing.assert_array_equal(fine.bin_off.cpu().numpy(), coarse.bin_off.cpu().numpy())
+    hits, boff, foff = fine.hits.cpu().numpy(), fine.bin_off.cpu().numpy(), fine.fine_off.cpu().numpy()
+    ids = hits[:, 3].view(np.int32)
+    ids_c = coarse.hits.cpu().numpy()[:, 3].view(np.int32)
+    for s in range(E * Lb):
+        lo, hi = b.layer_off[s], b.layer_off[s + 1]
+        n = hi - lo
+        sid = ids[lo:hi]
+        assert np.array_equal(np.sort(sid), np.arange(n))  # a permutation
+        np.testing.assert_array_equal(hits[lo:hi, :3], b.layer_xyz[:, lo + sid].T)
+        off = foff[s]
+        assert off[0] == 0 and off[-1] == n and np.all(np.diff(off) >= 0)
+        np.testing.assert_array_equal(off[0:kf.NBINS_FINE:2], boff[s, :kf.NBINS])
+        assigned = np.repeat(np.arange(kf.NBINS_FINE), np.diff(off))
+        ref, edge = _ref_bins(*b.layer_xyz[:, lo + sid].astype(np.float64), nphi=kf.BIN_PHI_FINE)
+        ok = (assigned == ref) | (edge < 1e-4)
+        assert ok.all(), np.nonzero(~ok)
+        for bb in np.nonzero(np.diff(boff[s]) > 0)[0]:  # the same hits in every bin
+            u0, u1 = lo + boff[s, bb], lo + boff[s, bb + 1]
+            assert sorted(ids[u0:u1]) == sorted(ids_c[u0:u1]), (s, bb)
 
 
 def _check_agreeing(g, r, idx, label=""):
@@ -374,8 +422,11 @@ def test_resident_layout_edge_cases(cuda_ctx_factory):
                 _check_build(batch, ref, oracle_build(batch, 6), label=name)
             kf.kf_set_tuning(ctx, 128, 0, 8, 4)
             g = gpu_build(ctx, batch, N)
+            kf.kf_set_tuning(ctx, 128, 0, 8, 4, 0, 0, 1)  # windows by sub-bin
+            gf = gpu_build(ctx, batch, N, fine=True)
             for k in ("par", "cov", "chi2", "nhits", "status", "hits", "n_cands", "cand_hits", "cand_chi2",
                       "cand_nhits"):
                 if k in ref:
                     np.testing.assert_array_equal(g[k], ref[k], err_msg=f"{name} N={N} {k}")
+                    np.testing.assert_array_equal(gf[k], ref[k], err_msg=f"{name} N={N} {k} sub-bins")
     kf.kf_set_tuning(ctx, 128, 0, 8, 0)

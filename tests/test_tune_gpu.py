@@ -159,3 +159,19 @@ def test_unordered_bins_give_the_same_build(cuda_ctx_factory):
                 lo, hi = base + off[s, bb], base + off[s, bb + 1]
                 assert sorted(ids0[lo:hi]) == sorted(ids1[lo:hi]), (name, s, bb)
     kf.kf_set_tuning(ctx, 128, 0, 8, 0)
+
+
+@pytest.mark.parametrize("max_cands", [8, 6, 3, 1])
+def test_sub_bin_windows_give_the_same_build(cuda_ctx_factory, max_cands):
+    """The register-resident layout looking its windows up by sub-bin (the
+    unordered binning's 64 x 512 sub-bin starts) gives the same bits as by
+    bin, with the first-layer launch (N > 2) and without (N = 1)."""
+    from paper_1605_05508_gb300 import kf
+    det = S.barrel()
+    ctx = cuda_ctx_factory(det.radii, max_cands=8)
+    for name, batch in _batches().items():
+        kf.kf_set_tuning(ctx, 128, 0, 8, 4, 0, 0, 1)
+        ref = gpu_build(ctx, batch, max_cands)
+        g = gpu_build(ctx, batch, max_cands, fine=True)
+        _same(ref, g, BUILD_KEYS)
+    kf.kf_set_tuning(ctx, 128, 0, 8, 0)
