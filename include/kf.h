@@ -195,8 +195,9 @@ typedef struct {
 } kf_layer_hits;
 
 /* Binned hits (output of kf_bin_hits, input of kf_build; device pointers).
- * Within each segment the hits are ordered by bin, and by id inside a bin
- * (by sub-bin, in no order inside a sub-bin, with kf_tuning.bin_unordered). */
+ * Within each segment the hits are ordered by bin, and by id inside a bin;
+ * with kf_tuning.bin_unordered in no order inside a bin, or, with fine_off
+ * set, by sub-bin and in no order inside a sub-bin. */
 typedef struct {
     int32_t n_events;
     int32_t n_layers;
@@ -254,7 +255,10 @@ typedef struct {
  * against rounding, so binning never changes the result.  The
  * register-resident layout (kf_tuning.build_scan 4) takes the seeds in their
  * given order, the others in (eta, phi) bin order within each event; the
- * results do not depend on the order.
+ * results do not depend on the order.  With bins->fine_off set (the sub-bin
+ * starts kf_bin_hits wrote for these hits) the register-resident layout
+ * takes each window's phi range in sub-bins, scanning fewer hits beyond its
+ * edges; the other layouts use bin_off; the results are the same.
  *
  * seeds: [n_seeds] starting states at or inside the first build layer (the
  * seeds' charge is read); seeds of event e are seed_off[e] .. seed_off[e+1]
