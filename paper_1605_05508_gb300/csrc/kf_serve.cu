@@ -192,7 +192,7 @@ enum ReqState { kQueued, kPreparing, kResident, kFinishing, kDone, kFailed };
 struct EventLayout {
   int64_t n, nh;
   int ns, Lb;
-  bool refit;
+  bool refit, fine;
   // device offsets
   size_t d_par, d_cov, d_q, d_shits, d_sval, d_fpar, d_flo, d_fcov, d_fst, d_xyz, d_segoff, d_sseg, d_bhits, d_boff,
       d_bid, d_perm, d_candA, d_candB, d_hp, d_hh, d_rpar, d_rcov, d_rchi, d_rnh, d_rst, d_rhit, d_qpar, d_qcov,
@@ -201,12 +201,13 @@ struct EventLayout {
   size_t h_par, h_cov, h_q, h_shits, h_sval, h_xyz, h_segoff, h_in_total;
   size_t o_par, o_cov, o_chi, o_nh, o_st, o_hit, o_qpar, o_qcov, o_qchi, o_qst, h_out_total;
 
-  void make(int64_t n_, int64_t nh_, int ns_, int Lb_, bool refit_) {
+  void make(int64_t n_, int64_t nh_, int ns_, int Lb_, bool refit_, bool fine_) {
     n = n_;
     nh = nh_;
     ns = ns_;
     Lb = Lb_;
     refit = refit_;
+    fine = fine_;
     const size_t L = size_t(ns + Lb);
     size_t o = 0;
     auto take = [&](size_t b) {
@@ -249,7 +250,7 @@ struct EventLayout {
     d_gval = take(refit ? L * n : 0);
     d_bcur = take(size_t(Lb) * KF_NBINS * 4);     // binning cursors (hits, then seeds)
     d_sboff = take(size_t(KF_NBINS + 1) * 4);  // seed bin offsets
-    d_fine = take(size_t(Lb) * (KF_NBINS_FINE + 1) * 4);  // hit sub-bin offsets (register-resident build)
+    d_fine = take(fine ? size_t(Lb) * (KF_NBINS_FINE + 1) * 4 : 0);  // hit sub-bin starts (register-resident build)
     d_total = o;
     o = 0;
     h_par = take(6 * n * 4);
@@ -365,8 +366,9 @@ static void fail_all_locked(Serve* sv, int err) {
 static cudaError_t prepare_batch(Serve* sv, const std::vector<Request*>& rs) {
   if (rs.empty()) return cudaSuccess;
   kf_ctx* ctx = sv->ctx;
-  // the register-resident build looks its windows up by sub-bin
-  const bool resident = sv->tune.build_scan == 4;
+  // the register-resident build looks its windows up by sub-bin (every
+  // event's layout then holds their starts)
+  const bool sub_bins = sv->tune.build_scan == 4;
   const int ps = sv->prep_next;
   sv->prep_next = (ps + 1) % kPrepStreams;
   cudaStream_t s = sv->prep_stream[ps];
@@ -421,7 +423,7 @@ static cudaError_t prepare_batch(Serve* sv, const std::vector<Request*>& rs) {
       b.p0 = hoff[l];
       b.p1 = std::min<int64_t>(hoff[l + 1], L.nh);
       b.bin_off = reinterpret_cast<int32_t*>(d + L.d_boff) + int64_t(l) * (KF_NBINS + 1);
-      b.fine_off = resident ? reinterpret_cast<int32_t*>(d + L.d_fine) + int64_t(l) * (KF_NBINS_FINE + 1) : nullptr;
+      b.fine_off = L.fine ? reinterpret_cast<int32_t*>(d + L.d_fine) + int64_t(l) * (KF_NBINS_FINE + 1) : nullptr;
       b.out_pts = reinterpret_cast<float4*>(d + L.d_bhits);
       b.out_id = reinterpret_cast<int32_t*>(d + L.d_bid);
     }
@@ -445,7 +447,7 @@ static cudaError_t prepare_batch(Serve* sv, const std::vector<Request*>& rs) {
   fa.mass = ctx->mass;
   e = launch_fit_fused_table(fa, df, int(rs.size()), tracks, s);
   // the build's results do not depend on the order of the hits inside a bin
-  if (e == cudaSuccess) e = launch_bin_segment_table(db, segs, resident, s);
+  if (e == cudaSuccess) e = launch_bin_segment_table(db, segs, sub_bins, s);
   if (e != cudaSuccess) return e;
   // (a register-resident build takes the seeds in their order, from the fit)
   for (size_t k = 0; k < rs.size() && sv->tune.build_scan != 4; ++k) {
@@ -534,7 +536,7 @@ static ResidentBatch resident_batch_of(Serve* sv, Request* r, bool first) {
   b.hits = reinterpret_cast<const float4*>(d + L.d_bhits);
   b.bin_off = reinterpret_cast<const int32_t*>(d + L.d_boff);
   b.seg_off = reinterpret_cast<const int64_t*>(d + L.d_segoff);
-  b.fine_off = reinterpret_cast<const int32_t*>(d + L.d_fine);
+  b.fine_off = L.fine ? reinterpret_cast<const int32_t*>(d + L.d_fine) : nullptr;
   b.S = L.n;
   b.group_begin = 0;
   b.seed_begin = 0;
@@ -1031,7 +1033,7 @@ int kf_submit(kf_ctx* ctx, const kf_event* ev, uint64_t* ticket) {
   const int64_t nh = ev->layer_off[Lb];
   if (nh > 0 && !ev->layer_xyz) return KF_EINVAL;
   auto req = std::make_unique<Request>();
-  req->lay.make(n, nh, ns, Lb, sv->cfg.refit != 0);
+  req->lay.make(n, nh, ns, Lb, sv->cfg.refit != 0, sv->tune.build_scan == 4);
   const EventLayout& L = req->lay;
   {
     std::lock_guard<std::mutex> lk(sv->mu);
