@@ -19,6 +19,11 @@
  *    crosses this interface.  KF_ECUDA leaves the CUDA error in
  *    kf_last_cuda_error().
  *  - A kf_ctx is not thread-safe; use one per host thread.
+ *  - The fit calls, kf_bin_hits and kf_build draw on separate context
+ *    scratch: one call of each kind may be in flight at once, each on its own
+ *    stream (a call that grows its scratch -- the first of a larger size --
+ *    reallocates it, which synchronises the device).  Two fit calls, or two
+ *    calls of one kind, on different streams race on that kind's scratch.
  */
 #ifndef KF_H_
 #define KF_H_
