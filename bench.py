@@ -924,6 +924,17 @@ def build_leg(a, kf, torch, dev, stream, rank, world, dist, peaks=None):
                              f"profiles/{prof}")
         if f32r:
             res["roofline"]["counted_fp32"] = f32r
+    # DRAM bytes of kf_build's launches (one ncu capture of the same setting,
+    # window look-up and kernel source at this size)
+    tprof = "build_resident_kernel.traffic.txt"
+    if (profile_value(tprof, "setting_code", BUILD_SOURCES) == code
+            and profile_value(tprof, "sub_bin_windows", BUILD_SOURCES) == windows
+            and profile_value(tprof, "events", BUILD_SOURCES) == E):
+        tb = profile_value(tprof, "traffic_bytes_per_build", BUILD_SOURCES)
+        if tb:
+            res["roofline"]["traffic"] = tb
+            res["roofline"]["traffic_bytes_per_seed_layer"] = tb / (n * Lb)
+            res["roofline"]["traffic_source"] = f"profiles/{tprof}"
     if rank == 0 and not a.no_extras:
         import oracle as O
         cores = os.cpu_count() or 1

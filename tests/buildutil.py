@@ -32,11 +32,12 @@ def oracle_build(batch, max_cands, idx=None, cut=30.0):
     return b
 
 
-def gpu_build(ctx, batch, max_cands, want_cands=True, build_fn=None, fine=False):
+def gpu_build(ctx, batch, max_cands, want_cands=True, build_fn=None, fine=False, streams=False):
     """Seed fit (kf_fit over the seeding layers) -> kf_bin_hits -> kf_build
     (or build_fn with kf_build's arguments); fine: the binning also gives the
-    sub-bin starts (unordered binning only), which the build then uses.
-    Returns numpy arrays (hit_idx as [n, L])."""
+    sub-bin starts (unordered binning only), which the build then uses;
+    streams: the seed fit and the binning run at once on two side streams,
+    joined before the build.  Returns numpy arrays (hit_idx as [n, L])."""
     import torch
     from paper_1605_05508_gb300 import kf
     n = batch.seeds.par.shape[1]
@@ -45,7 +46,9 @@ def gpu_build(ctx, batch, max_cands, want_cands=True, build_fn=None, fine=False)
     fo = kf.Tracks(torch.empty((6, n), device="cuda"), torch.empty((21, n), device="cuda"), s.charge,
                    torch.empty((3, n), device="cuda"))
     fst = torch.empty(n, dtype=torch.int32, device="cuda")
-    kf.kf_fit(ctx, s, kf.TrackHits(to_dev(batch.fit_hits.xyz), to_dev(batch.fit_hits.valid)), fo, None, fst)
+    th = kf.TrackHits(to_dev(batch.fit_hits.xyz), to_dev(batch.fit_hits.valid))
+    if not streams:
+        kf.kf_fit(ctx, s, th, fo, None, fst)
     seg_off = to_dev(batch.layer_off)
     lh = kf.LayerHits(to_dev(batch.layer_xyz), seg_off, E, Lb, batch.build_layers[0])
     nh = batch.layer_xyz.shape[1]
@@ -53,7 +56,19 @@ def gpu_build(ctx, batch, max_cands, want_cands=True, build_fn=None, fine=False)
                       torch.empty((E * Lb, kf.NBINS + 1), dtype=torch.int32, device="cuda"),
                       fine_off=torch.empty((E * Lb, kf.NBINS_FINE + 1), dtype=torch.int32, device="cuda")
                       if fine else None)
-    kf.kf_bin_hits(ctx, lh, bins)
+    if streams:
+        main = torch.cuda.current_stream()
+        s_bin, s_fit = torch.cuda.Stream(), torch.cuda.Stream()
+        fork = torch.cuda.Event()
+        fork.record(main)
+        s_bin.wait_event(fork)
+        s_fit.wait_event(fork)
+        kf.kf_bin_hits(ctx, lh, bins, s_bin)
+        kf.kf_fit(ctx, s, th, fo, None, fst, s_fit)
+        main.wait_stream(s_bin)
+        main.wait_stream(s_fit)
+    else:
+        kf.kf_bin_hits(ctx, lh, bins)
     seed_off = to_dev(np.searchsorted(batch.seed_event, np.arange(E + 1)).astype(np.int64))
     N = max_cands
     i32 = dict(dtype=torch.int32, device="cuda")

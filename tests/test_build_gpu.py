@@ -430,3 +430,21 @@ def test_resident_layout_edge_cases(cuda_ctx_factory):
                     np.testing.assert_array_equal(g[k], ref[k], err_msg=f"{name} N={N} {k}")
                     np.testing.assert_array_equal(gf[k], ref[k], err_msg=f"{name} N={N} {k} sub-bins")
     kf.kf_set_tuning(ctx, 128, 0, 8, 0)
+
+
+def test_fit_and_binning_on_two_streams(cuda_ctx_factory):
+    """A build step's seed fit and hit binning in flight at once on two streams
+    of one context (they draw on separate context scratch), joined before the
+    build: every result bitwise that of the step on one stream, three times."""
+    from paper_1605_05508_gb300 import kf
+    det = S.barrel()
+    ctx = cuda_ctx_factory(det.radii, max_cands=8)
+    kf.kf_set_tuning(ctx, 128, 0, 8, 4, 0, 0, 1)
+    batch = S.make_build_batch(2201, 4, 1500)
+    ref = gpu_build(ctx, batch, 6, fine=True)
+    for _ in range(3):
+        got = gpu_build(ctx, batch, 6, fine=True, streams=True)
+        for k in ("par", "cov", "chi2", "nhits", "status", "hits", "fit_status", "n_cands", "cand_hits",
+                  "cand_chi2", "cand_nhits"):
+            np.testing.assert_array_equal(got[k], ref[k], err_msg=k)
+    kf.kf_set_tuning(ctx, 128, 0, 8, 0)
