@@ -281,8 +281,9 @@ static cudaError_t segment_smem_attrs(K kernel, int smem, std::atomic<bool>* don
   if (e != cudaSuccess) return e;
   if (dev >= 0 && dev < kMaxDevices && done[dev].load(std::memory_order_acquire)) return cudaSuccess;
   e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  // the largest shared-memory carveout: two blocks (2 x 68 KB) per SM, or one
-  // with the sub-bins (135 KB)
+  // the largest shared-memory carveout (a block takes 68 KB, or 135 KB with
+  // the sub-bins; its 1024 threads' registers already leave room for one
+  // block per SM)
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                              int(cudaSharedmemCarveoutMaxShared));

@@ -165,7 +165,9 @@ def test_unordered_bins_give_the_same_build(cuda_ctx_factory):
 def test_sub_bin_windows_give_the_same_build(cuda_ctx_factory, max_cands):
     """The register-resident layout looking its windows up by sub-bin (the
     unordered binning's 64 x 512 sub-bin starts) gives the same bits as by
-    bin, with the first-layer launch (N > 2) and without (N = 1)."""
+    bin, with the first-layer launch (N > 2) and without (N = 1); the
+    layer-stepping layouts, handed the sub-bin starts too, keep to the bins
+    and give the same bits."""
     from paper_1605_05508_gb300 import kf
     det = S.barrel()
     ctx = cuda_ctx_factory(det.radii, max_cands=8)
@@ -174,4 +176,7 @@ def test_sub_bin_windows_give_the_same_build(cuda_ctx_factory, max_cands):
         ref = gpu_build(ctx, batch, max_cands)
         g = gpu_build(ctx, batch, max_cands, fine=True)
         _same(ref, g, BUILD_KEYS)
+        for scan in (0, 2):
+            kf.kf_set_tuning(ctx, 128, 0, 8, scan, 0, 0, 1)
+            _same(ref, gpu_build(ctx, batch, max_cands, fine=True), BUILD_KEYS)
     kf.kf_set_tuning(ctx, 128, 0, 8, 0)
