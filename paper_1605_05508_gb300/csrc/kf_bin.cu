@@ -176,6 +176,8 @@ __device__ __forceinline__ void bin_one_segment(const float* xyz, int64_t stride
   } else {
     for (int b = tid; b < KF_NBINS; b += kScanThreads) off[b] = cnt[pad_idx(b)];  // coalesced
   }
+  // every start read before the scatter below moves the cursors on
+  __syncthreads();
   for (int64_t g0 = p0 + tid; g0 < p1; g0 += int64_t(kScanThreads) * kSegBatch) {
     float x[kSegBatch], y[kSegBatch], z[kSegBatch];
     int bins[kSegBatch];
