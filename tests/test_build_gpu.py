@@ -178,12 +178,13 @@ def test_build_phi_wraparound_and_eta_edges(cuda_ctx_factory):
 
 def test_build_config3_full_size_sampled(cuda_ctx_factory):
     """50 events x 5000 seeds, 15000 noise + 5000 track hits per layer, N = 6,
-    building on layers 4-10, in the launch setting the benchmark times (the
-    autotuner's choice on this batch): the same bits as the grouped per-lane
-    layout, and 5000 seeds (100 from each of the 50 events) checked against
-    the oracle's all-hits build: best paths (near ties counted), and on the
-    agreeing paths the best candidate's hits, status, chi2, state and
-    covariance."""
+    building on layers 4-10, in the launch configuration the benchmark times
+    (the autotuner's choice on this batch, the unordered binning with sub-bin
+    starts and the windows looked up by sub-bin): the same bits as the
+    autotuned setting on ordered bins and as the grouped per-lane layout, and
+    5000 seeds (100 from each of the 50 events) checked against the oracle's
+    all-hits build: best paths (near ties counted), and on the agreeing paths
+    the best candidate's hits, status, chi2, state and covariance."""
     from paper_1605_05508_gb300 import kf
     det = S.barrel()
     ctx = cuda_ctx_factory(det.radii)
@@ -192,12 +193,15 @@ def test_build_config3_full_size_sampled(cuda_ctx_factory):
 
     def tune(*args):
         chosen.update(kf.kf_autotune_build(*args))
-    g = gpu_build(ctx, batch, 6, want_cands=False, build_fn=tune)
+    gt = gpu_build(ctx, batch, 6, want_cands=False, build_fn=tune)
     print("autotuned build setting:", chosen)
+    kf.kf_set_tuning(ctx, **dict(chosen, bin_unordered=1))
+    g = gpu_build(ctx, batch, 6, want_cands=False, fine=chosen["build_scan"] == 4)
     kf.kf_set_tuning(ctx, 128, 0, 8, 0)
     g0 = gpu_build(ctx, batch, 6, want_cands=False)
     for k in ("par", "chi2", "nhits", "status", "hits"):
         np.testing.assert_array_equal(g[k], g0[k], err_msg=k)
+        np.testing.assert_array_equal(gt[k], g0[k], err_msg=k)
     rng = np.random.default_rng(1)
     first = np.searchsorted(batch.seed_event, np.arange(51))
     idx = np.sort(np.concatenate([first[e] + rng.choice(first[e + 1] - first[e], 100, replace=False)
